@@ -1,0 +1,127 @@
+/*
+ * FP64 CPU oracle for the block incomplete LU (BILU) factorization, its
+ * preconditioner application and restarted GMRES.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This is the plain, slow, obviously correct
+ * reference that the CUDA path is checked against.  Only the test suite, the
+ * smoke check and the benchmark's CPU-baseline leg may load it.  It shares no
+ * code, header, table or helper with the CUDA library, and never calls it.
+ *
+ * Source: Bollhoefer, Schenk, Verbosio, "High Performance Block Incomplete LU
+ * Factorization" (arXiv:1908.10169).
+ *   - Crout ILU, Algorithm 1 (Sec. 2.1); its block version (Sec. 2.2): drop
+ *     l_ik when ||l_ik l_kk^{-1}|| <= tau and u_ki when ||u_kk^{-1} u_ki|| <= tau,
+ *     l_ik <- l_ik l_kk^{-1}; hybrid storage: block columns of L and block rows
+ *     of U with scalar row / column index arrays, dense diagonal blocks in D.
+ *   - A ~ L D^{-1} U with L, U^T unit block lower triangular, the diagonal
+ *     blocks factored (LU with pivoting inside the block only) and inverted
+ *     (Sec. 2.2, end).
+ *   - Perturbation of singular diagonal blocks (Sec. 3.6).
+ *   - Simplified ILU(1,tau) block-pattern guess (Sec. 3.4).
+ *   - Restarted GMRES(30) (Sec. 4, Example setup).
+ *
+ * Readings where the paper is silent or garbled (all listed in the design notes):
+ *   R1 drop norm = Euclidean norm of one scalar row (1 x b_K) of the normalised
+ *      L block column, resp. one column (b_K x 1) of D_K * U;
+ *   R2 drop iff norm <= tau (so exact zeros are dropped even at tau = 0);
+ *   R3 L is stored normalised (unit), U is stored unnormalised (U-breve), D_K = P_K^{-1};
+ *   R4 getrf pivot = first index of the largest |.| in the column;
+ *   R5 perturbation: beta_j := 1, sign(0) := +1; triggers on an all-zero column
+ *      or row, and on a pivot with |u_jj| <= 1e-14 * max|P_K|;
+ *   R6 the candidate rows/cols are the structural union of touched indices;
+ *   R7 updates from earlier blocks J are applied in increasing J;
+ *   R8 GMRES: right preconditioning, modified Gram-Schmidt, Givens rotations,
+ *      stop when the Givens residual <= tol * ||b|| and the true residual agrees.
+ *   R9 ILU(1,tau) blocking bookkeeping: see orc_partition_ilu1t.
+ */
+#ifndef BILU_ORACLE_H
+#define BILU_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct orc_factor orc_factor;
+
+/* Status codes (same meaning as the library's, defined independently here). */
+#define ORC_OK 0
+#define ORC_NOT_CONVERGED 1
+#define ORC_PERTURBED 2
+#define ORC_ERR_ARG (-1)
+#define ORC_ERR_SINGULAR (-4)
+
+/* Counters filled by the factorization (algorithmic work, no padding). */
+enum {
+    ORC_C_FLOP_UPD_L = 0,   /* 2*m*n*b_J summed over L-side updates              */
+    ORC_C_FLOP_UPD_U,       /* 2*m*n*b_J summed over U-side updates              */
+    ORC_C_FLOP_GETRF,       /* (2/3) b_K^3 per diagonal block (nominal)          */
+    ORC_C_FLOP_INV,         /* (4/3) b_K^3 per diagonal block (nominal)          */
+    ORC_C_FLOP_SCALE,       /* 2 b_K^2 per candidate row and per candidate col   */
+    ORC_C_FLOP_NORM,        /* 2 b_K per candidate row and per candidate col     */
+    ORC_C_CAND_ROWS,        /* candidate (pre-drop) L rows outside the pivot     */
+    ORC_C_CAND_COLS,        /* candidate (pre-drop) U cols                       */
+    ORC_C_PANEL_READ_BYTES, /* 8*(m*b_J + n*b_J) per update: producer operands   */
+    ORC_C_NPAIRS_L,         /* number of (J,K) L-side updates                    */
+    ORC_C_NPAIRS_U,         /* number of (J,K) U-side updates                    */
+    ORC_C_NPERTURB,         /* perturbed entries                                 */
+    ORC_C_COUNT = 16
+};
+
+/* Partition into consecutive blocks of size b (the last one may be smaller).
+ * bstart must hold n/b + 2 entries; returns the number of blocks. */
+int32_t orc_partition_fixed(int64_t n, int32_t b, int32_t *bstart);
+
+/* Simplified ILU(1,tau) block-pattern guess, Sec. 3.4.  bstart holds n+1 entries;
+ * returns the number of blocks (< 0 on error). */
+int32_t orc_partition_ilu1t(int64_t n, const int64_t *rowptr, const int32_t *colind,
+                            const double *val, double tau, int32_t max_block,
+                            int32_t *bstart);
+
+/* Numeric Crout BILU.  A is CSR with sorted column indices.  On success (status >= 0)
+ * *out receives the factor, to be freed with orc_factor_free. */
+int32_t orc_bilu_factor(int64_t n, const int64_t *rowptr, const int32_t *colind,
+                        const double *val, int32_t nb, const int32_t *bstart, double droptol,
+                        int32_t perturb, double pert_tau, double pert_rho, orc_factor **out);
+
+/* sizes[0] = kept L rows, [1] = kept U cols, [2] = L values, [3] = U values,
+ * [4] = sum b_K^2, [5] = number of blocks, [6] = perturbations */
+void orc_factor_sizes(const orc_factor *F, int64_t sizes[8]);
+
+/* Exports the factor in the layout shared by the tests:
+ *   Lptr[nb+1]   kept-row offsets; Lrow[]: global row indices (sorted per block)
+ *   Lval[]       per block nL_K x b_K row-major (rows of unit L)
+ *   Uptr[nb+1]   kept-col offsets; Ucol[]: global column indices (sorted per block)
+ *   Uval[]       per block nU_K x b_K: entry (q, t) = U-breve(s_K + t, Ucol[q])
+ *   Dinv[]       per block b_K x b_K row-major, D_K = P_K^{-1}
+ *   Pblk[]       per block b_K x b_K row-major, the updated pivot block P_K
+ *   LUblk[]      per block: the getrf factors of P_K (unit L below, U on and above)
+ *   piv[]        per block b_K entries: row piv[i] of P_K is row i of P*P_K
+ * Any pointer may be NULL to skip that array. */
+void orc_factor_export(const orc_factor *F, int64_t *Lptr, int32_t *Lrow, double *Lval,
+                       int64_t *Uptr, int32_t *Ucol, double *Uval, double *Dinv,
+                       double *Pblk, double *LUblk, int32_t *piv);
+
+void orc_factor_counters(const orc_factor *F, double c[ORC_C_COUNT]);
+void orc_factor_free(orc_factor *F);
+
+/* z = M^{-1} r with M = L D^{-1} U (block forward then block backward substitution). */
+void orc_bilu_apply(const orc_factor *F, const double *r, double *z);
+
+/* y = A x (plain CSR). */
+void orc_spmv(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val,
+              const double *x, double *y);
+
+/* Right-preconditioned restarted GMRES(restart) with MGS.  M may be NULL (no
+ * preconditioner).  x holds x0 on entry.  hist (optional, maxit+1 entries) receives
+ * the Givens residual estimate |g_{j+1}| / ||b|| after each inner step.
+ * Returns ORC_OK or ORC_NOT_CONVERGED. */
+int32_t orc_gmres(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val,
+                  const orc_factor *M, const double *b, double *x, double tol, int32_t restart,
+                  int32_t maxit, int32_t *iters, double *relres_true, double *hist);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

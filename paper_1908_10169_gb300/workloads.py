@@ -1,0 +1,191 @@
+"""Seeded synthetic test matrices (convection-diffusion and elasticity stencils).
+
+This module only builds inputs: sparse matrices in CSR form, right-hand sides and
+the parameters a run uses.  It holds none of the factorization's arithmetic, so both
+the FP64 CPU oracle (through the tests) and the CUDA path consume the very same
+arrays.  The paper's own test matrices (SuiteSparse, n >= 50000, Sec. 4) are not
+available; these stencils stand in for them.
+
+Conventions shared by every generator:
+  * unknowns are grid nodes in natural lexicographic order, x fastest;
+  * Dirichlet boundary nodes are eliminated (the matrix covers interior nodes only);
+  * random numbers come from numpy's PCG64 with the stated seed;
+  * rows are scaled by h^2 so entries are O(1) (the drop test and the relative
+    GMRES residual are scale-invariant, so this changes no result);
+  * CSR: rowptr int64 (n+1), colind int32 sorted within each row, val float64.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class CSR:
+    n: int
+    rowptr: np.ndarray  # int64, n+1
+    colind: np.ndarray  # int32, nnz
+    val: np.ndarray     # float64, nnz
+
+    @property
+    def nnz(self) -> int:
+        return int(self.rowptr[-1])
+
+    def matvec(self, x: np.ndarray) -> np.ndarray:
+        """y = A x (input preparation only, e.g. the right-hand side b = A*1)."""
+        rows = np.repeat(np.arange(self.n), np.diff(self.rowptr))
+        return np.bincount(rows, weights=self.val * x[self.colind], minlength=self.n)
+
+    def to_dense(self) -> np.ndarray:
+        d = np.zeros((self.n, self.n))
+        rows = np.repeat(np.arange(self.n), np.diff(self.rowptr))
+        d[rows, self.colind] = self.val
+        return d
+
+
+def _from_coo(n: int, rows: np.ndarray, cols: np.ndarray, vals: np.ndarray) -> CSR:
+    order = np.lexsort((cols, rows))
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    # no duplicates are produced by the generators; guard anyway
+    if rows.size > 1:
+        dup = (rows[1:] == rows[:-1]) & (cols[1:] == cols[:-1])
+        if dup.any():
+            raise ValueError("duplicate entries in generated matrix")
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(np.bincount(rows, minlength=n), out=rowptr[1:])
+    return CSR(n, rowptr, cols.astype(np.int32), vals.astype(np.float64))
+
+
+def from_dense(d: np.ndarray, keep_zeros_on_diag: bool = True) -> CSR:
+    """CSR of a dense matrix (test helper): keeps nonzeros (and the diagonal)."""
+    n = d.shape[0]
+    mask = d != 0
+    if keep_zeros_on_diag:
+        mask |= np.eye(n, dtype=bool)
+    rows, cols = np.nonzero(mask)
+    return _from_coo(n, rows.astype(np.int64), cols.astype(np.int64), d[rows, cols])
+
+
+def convdiff2d_central(nx: int, ny: int, vmax: float = 10.0, seed: int = 0) -> CSR:
+    """-Laplace(u) + v.grad(u) on the unit square, 5-point, central differences.
+
+    Velocity (v_x, v_y) is drawn per node from U[-vmax, vmax] (seed).  h = 1/(nx+1)
+    (nx == ny assumed for h; the square grid is what the workloads use).
+    Row p (times h^2): diag 4, east/west -1 +/- v_x h/2, north/south -1 +/- v_y h/2.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = nx * ny
+    h = 1.0 / (nx + 1)
+    v = rng.uniform(-vmax, vmax, size=(2, n))
+    p = np.arange(n)
+    x, y = p % nx, p // nx
+    rows = [p]
+    cols = [p]
+    vals = [np.full(n, 4.0)]
+    for (dx, dy, comp, sgn) in ((1, 0, 0, +1), (-1, 0, 0, -1), (0, 1, 1, +1), (0, -1, 1, -1)):
+        m = (x + dx >= 0) & (x + dx < nx) & (y + dy >= 0) & (y + dy < ny)
+        q = p + dx + dy * nx
+        rows.append(p[m])
+        cols.append(q[m])
+        vals.append(-1.0 + sgn * v[comp, m] * h / 2.0)
+    return _from_coo(n, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
+
+
+def _harmonic(a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    return 2.0 * a * b / (a + b)
+
+
+def convdiff_upwind(dims: tuple, kappa_decades: tuple = (-3.0, 3.0), vel: tuple | None = None,
+                    seed: int = 1) -> CSR:
+    """-div(kappa grad u) + v.grad(u), 2D 5-point or 3D 7-point, first-order upwind.
+
+    kappa per node is log-uniform in [10^kappa_decades[0], 10^kappa_decades[1]] (seed);
+    the face coefficient between two interior nodes is the harmonic mean of theirs, a face
+    to an (eliminated) Dirichlet node uses the interior node's own kappa.  h = 1/(dims[0]+1).
+    Row p (times h^2): diag = sum_faces kappa_f + h * sum_d |v_d|;
+    off-diagonal to q = -kappa_f, minus h*|v_d| more when q is the upwind neighbour.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    dim = len(dims)
+    n = int(np.prod(dims))
+    h = 1.0 / (dims[0] + 1)
+    if vel is None:
+        vel = tuple([100.0 / math.sqrt(dim)] * dim)
+    kappa = 10.0 ** rng.uniform(kappa_decades[0], kappa_decades[1], size=n)
+    p = np.arange(n)
+    coords = []
+    rem = p.copy()
+    strides = []
+    s = 1
+    for d in range(dim):
+        coords.append(rem % dims[d])
+        rem = rem // dims[d]
+        strides.append(s)
+        s *= dims[d]
+    diag = np.zeros(n)
+    rows, cols, vals = [], [], []
+    for d in range(dim):
+        vd = vel[d]
+        for sgn in (-1, +1):
+            inside = (coords[d] + sgn >= 0) & (coords[d] + sgn < dims[d])
+            q = p + sgn * strides[d]
+            kf = kappa.copy()
+            kf[inside] = _harmonic(kappa[inside], kappa[q[inside]])
+            diag += kf
+            upwind = (sgn < 0) if vd >= 0 else (sgn > 0)
+            off = -kf[inside] - (h * abs(vd) if upwind else 0.0)
+            rows.append(p[inside])
+            cols.append(q[inside])
+            vals.append(off)
+        diag += h * abs(vd)
+    rows.append(p)
+    cols.append(p)
+    vals.append(diag)
+    return _from_coo(n, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
+
+
+def rhs_ones(A: CSR) -> np.ndarray:
+    """b = A * (1,...,1): the exact solution is the all-ones vector."""
+    return A.matvec(np.ones(A.n))
+
+
+def random_diag_dominant(n: int, density: float, seed: int, dominance: float = 1.5) -> CSR:
+    """Random sparse nonsymmetric matrix with a dominant diagonal (test input)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    mask = rng.random((n, n)) < density
+    d = np.where(mask, rng.uniform(-1.0, 1.0, size=(n, n)), 0.0)
+    np.fill_diagonal(d, 0.0)
+    rs = np.abs(d).sum(axis=1)
+    np.fill_diagonal(d, (rs + 1.0) * dominance * np.where(rng.random(n) < 0.5, -1.0, 1.0))
+    return from_dense(d)
+
+
+# --- named workloads --------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    A: CSR
+    b: np.ndarray
+    droptol: float
+    max_block: int
+    blocking: str        # "fixed" or "ilu1t"
+    fixed_block: int
+    gmres_tol: float = 1e-8
+    restart: int = 30
+
+
+def cd2d_32(seed: int = 0) -> Workload:
+    """2D convection-diffusion, 32x32 interior grid (n = 1024), central differences,
+    v per node uniform in [-10, 10], drop tolerance 1e-2, blocks of one grid line (32)."""
+    A = convdiff2d_central(32, 32, 10.0, seed)
+    return Workload("cd2d_5pt_32x32", A, rhs_ones(A), 1e-2, 32, "fixed", 32)
+
+
+def cd3d(side: int = 64, seed: int = 1, block: int = 64) -> Workload:
+    """3D convection-diffusion, side^3 interior grid, 7-point upwind, kappa log-uniform in
+    [1e-3, 1e3] per node, |v| = 100 along (1,1,1); drop tolerance 1e-2; blocks of `block`."""
+    A = convdiff_upwind((side, side, side), seed=seed)
+    return Workload(f"cd3d_7pt_{side}^3", A, rhs_ones(A), 1e-2, 64, "fixed", block)
