@@ -1,0 +1,181 @@
+/*
+ * bilu.h -- C ABI of the GB300 (sm_103a) block incomplete LU library.
+ *
+ * Method: Bollhoefer, Schenk, Verbosio, "High Performance Block Incomplete LU
+ * Factorization", arXiv:1908.10169.  The library computes the Crout-type block ILU
+ * A ~ L D^{-1} U of a sparse matrix (Sec. 2.2), applies it as a preconditioner by block
+ * forward / backward substitution, and solves A x = b with right-preconditioned
+ * restarted GMRES (Sec. 4).  Every numerical step runs in CUDA kernels on one GPU.
+ *
+ * Conventions (all entry points):
+ *   - The caller owns every array it passes; the library copies what it keeps and
+ *     never frees caller memory.  A context owns all device memory it allocates.
+ *   - Vectors passed to bilu_apply / gmres_solve may be device pointers or host
+ *     pointers (pageable or pinned); host vectors are staged through device buffers.
+ *     Work is issued on the context's stream; the calls that return numerical status
+ *     (bilu_factor, gmres_solve) synchronize that stream once before returning.
+ *   - Call order: bilu_create -> bilu_analyze -> bilu_factor -> bilu_apply /
+ *     gmres_solve.  A call out of order returns BILU_ERR_STATE.  bilu_factor may be
+ *     repeated (new drop tolerance); bilu_analyze may be repeated (new matrix).
+ *   - Status < 0 is an error (the context stays destroyable, bilu_last_error says
+ *     why); status > 0 is a warning with a valid result.  No exception, exit() or
+ *     device trap crosses this interface.
+ *   - A context is not thread-safe: use one per host thread.
+ *   - Real FP64 values, int32 column indices, int64 row pointers, 0-based.
+ */
+#ifndef BILU_H
+#define BILU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bilu_ctx bilu_ctx;
+
+typedef enum {
+    BILU_OK = 0,
+    BILU_NOT_CONVERGED = 1, /* gmres_solve reached maxit; x holds the last iterate      */
+    BILU_PERTURBED = 2,     /* some diagonal blocks were perturbed (Sec. 3.6)           */
+    BILU_ERR_ARG = -1,      /* invalid argument (bad CSR, NaN, size, null pointer)      */
+    BILU_ERR_OOM = -2,      /* device allocation failed                                 */
+    BILU_ERR_CUDA = -3,     /* a CUDA runtime call failed                               */
+    BILU_ERR_SINGULAR = -4, /* singular diagonal block with perturbation switched off   */
+    BILU_ERR_TIMEOUT = -5,  /* a device-side wait exceeded its iteration bound          */
+    BILU_ERR_STATE = -6     /* call out of order                                        */
+} bilu_status;
+
+enum { BILU_BLOCKING_FIXED = 0, BILU_BLOCKING_ILU1T = 1 };
+enum { BILU_PREC_FP64 = 0, BILU_PREC_FP32 = 1, BILU_PREC_BF16 = 2 };
+enum { BILU_SKIP_NONE = 0, BILU_SKIP_BOUND = 1, BILU_SKIP_LEARNED = 2 };
+
+/* Maximum diagonal block size supported by the kernels. */
+#define BILU_MAX_BLOCK 64
+
+typedef struct {
+    int32_t blocking;    /* BILU_BLOCKING_FIXED: consecutive blocks of fixed_block;
+                            BILU_BLOCKING_ILU1T: the simplified ILU(1,tau) guess of Sec. 3.4 */
+    int32_t max_block;   /* cap on the block size, 1..BILU_MAX_BLOCK (the paper asks for a
+                            limit, Sec. 3, without fixing one)                                 */
+    int32_t fixed_block; /* block size for BILU_BLOCKING_FIXED                                 */
+    double tau_analyze;  /* tau of the ILU(1,tau) simulation                                    */
+    int32_t perturb;     /* 1: perturb singular diagonal blocks (Sec. 3.6); 0: report singular */
+    double pert_tau;     /* absolute perturbation tolerance tau (paper: 1e-2)                  */
+    double pert_rho;     /* relative perturbation tolerance rho (paper: 1e-1)                  */
+    int32_t precision;   /* BILU_PREC_*: arithmetic of the Schur updates and panel scaling     */
+    int32_t skip;        /* BILU_SKIP_*: candidate-row skipping in the factorization           */
+} bilu_params;
+
+typedef struct {
+    int32_t iters;       /* inner Arnoldi steps taken                                  */
+    int32_t restarts;    /* completed restart cycles                                  */
+    double relres_true;  /* ||b - A x|| / ||b|| at exit                                */
+    double relres_est;   /* last Givens residual estimate |g_{j+1}| / ||b||            */
+    double t_solve_ms;   /* device time of the solve                                   */
+} gmres_info;
+
+typedef struct {
+    int64_t n, nnz_a;         /* matrix size and nonzeros                              */
+    int32_t nblocks;          /* number of diagonal blocks                             */
+    int32_t max_bsize;        /* largest block                                         */
+    double avg_bsize, std_bsize;
+    int64_t nnz_l, nnz_u;     /* stored values of L and U-breve (kept rows x block)    */
+    int64_t nnz_d;            /* sum of b_K^2                                          */
+    int64_t kept_rows, kept_cols;   /* kept scalar rows of L / columns of U            */
+    int64_t cand_rows, cand_cols;   /* candidate rows / columns before dropping        */
+    int64_t nperturb;         /* perturbed entries (Sec. 3.6)                          */
+    double flops_factor;      /* algorithmic flops of the last factorization           */
+    double t_analyze_ms, t_factor_ms;
+    int32_t pool_retries;     /* factor re-runs after growing the L/U pools             */
+} bilu_stats_t;
+
+/* Fills *p with the defaults: FIXED blocking of 32 (max 64), tau_analyze 1e-2,
+ * perturbation on with tau 1e-2 and rho 1e-1 (Sec. 3.6), FP64, no skipping. */
+bilu_status bilu_params_default(bilu_params *p);
+
+/* Creates a context on CUDA device `device`, issuing work on `cuda_stream` (a
+ * cudaStream_t).  NULL makes the context create and own a private non-blocking stream
+ * (the solver captures CUDA graphs, which the legacy default stream does not allow).
+ * Errors: BILU_ERR_ARG (no such device), BILU_ERR_CUDA (device lacks cooperative launch). */
+bilu_status bilu_create(bilu_ctx **ctx, int device, void *cuda_stream);
+
+/*
+ * Analysis (Sec. 2.2 setting up the structures; Sec. 3.4 blocking): validates and copies
+ * A (n x n CSR: rowptr[n+1] int64, colind[nnz] int32 sorted and unique within each row,
+ * val[nnz] finite FP64; host pointers if on_device == 0, device pointers otherwise),
+ * builds its CSC copy (access by columns, Sec. 2.1), computes the block partition and
+ * sizes the factor's memory.  Errors: BILU_ERR_ARG for a malformed matrix or
+ * parameters, BILU_ERR_OOM, BILU_ERR_CUDA.
+ */
+bilu_status bilu_analyze(bilu_ctx *ctx, int64_t n, const int64_t *rowptr, const int32_t *colind,
+                         const double *val, int32_t on_device, const bilu_params *p);
+
+/*
+ * Numeric factorization (Algorithm 1 with blocks, Sec. 2.2): for each diagonal block K,
+ * the block column of L and block row of U are loaded from A, updated by the earlier
+ * blocks (dense products scattered into the target rows), the diagonal block is
+ * factored with partial pivoting inside the block and inverted (perturbed if singular,
+ * Sec. 3.6), the off-diagonal rows l_i = T[i,:] D_K and columns D_K u_j are computed,
+ * and a scalar row / column is dropped when its Euclidean norm is <= droptol.
+ * Returns BILU_OK, BILU_PERTURBED, BILU_ERR_SINGULAR (perturb == 0), BILU_ERR_TIMEOUT,
+ * BILU_ERR_OOM, BILU_ERR_CUDA, BILU_ERR_STATE (no analysis), BILU_ERR_ARG (droptol < 0).
+ */
+bilu_status bilu_factor(bilu_ctx *ctx, double droptol);
+
+/*
+ * z = M^{-1} r with M = L D^{-1} U (Sec. 2.2: block forward substitution with unit L,
+ * then block backward substitution multiplying by the stored inverses D_K).
+ * r and z hold n doubles and must not overlap.  Stream-ordered; does not synchronize
+ * for device pointers.  Errors: BILU_ERR_STATE (no factor), BILU_ERR_ARG, BILU_ERR_CUDA.
+ */
+bilu_status bilu_apply(bilu_ctx *ctx, const double *r, double *z);
+
+/*
+ * Restarted GMRES(restart), right preconditioned with M (Sec. 4 uses GMRES(30)):
+ * solves A x = b; x holds x0 on entry and the solution on exit.  Stops when the Givens
+ * residual estimate is <= tol ||b|| and the true residual ||b - A x|| <= tol ||b||, or
+ * after maxit inner steps (BILU_NOT_CONVERGED).  info may be NULL.
+ */
+bilu_status gmres_solve(bilu_ctx *ctx, const double *b, double *x, double tol, int32_t restart,
+                        int32_t maxit, gmres_info *info);
+
+/* Statistics of the last analysis / factorization (fill, block sizes, work). */
+bilu_status bilu_stats(bilu_ctx *ctx, bilu_stats_t *out);
+
+/* Copies the partition to host memory: bstart[nblocks + 1] (nblocks from bilu_stats). */
+bilu_status bilu_get_partition(bilu_ctx *ctx, int32_t *bstart);
+
+/*
+ * Copies the factor to host memory in the layout:
+ *   Lptr[nb+1] kept-row offsets; Lrow[kept_rows] global rows (sorted per block);
+ *   Lval[nnz_l] per block kept_rows_K x b_K row-major (rows of unit L);
+ *   Uptr[nb+1]; Ucol[kept_cols]; Uval[nnz_u] per block kept_cols_K x b_K, entry (q,t) =
+ *   U-breve(s_K + t, Ucol[q]); Dinv[nnz_d] per block b_K x b_K row-major (D_K = P_K^{-1});
+ *   Pblk[nnz_d] the updated pivot blocks P_K.  Any pointer may be NULL.
+ */
+bilu_status bilu_export(bilu_ctx *ctx, int64_t *Lptr, int32_t *Lrow, double *Lval, int64_t *Uptr,
+                        int32_t *Ucol, double *Uval, double *Dinv, double *Pblk);
+
+/* Human-readable description of the last error on this context ("" if none). */
+const char *bilu_last_error(const bilu_ctx *ctx);
+
+/*
+ * Test hooks for the failure paths (not for production use).  Settings are global to the
+ * process and stay until changed.
+ *   BILU_DEBUG_EXTRA_CTA (value 0/1): the factorization's grid barrier waits for one CTA
+ *       more than the launch has, so every bounded wait expires and bilu_factor returns
+ *       BILU_ERR_TIMEOUT with the GPU still usable.
+ *   BILU_DEBUG_SPIN_LIMIT (value > 0): polls of one barrier wait before it gives up
+ *       (0 restores the default).
+ */
+enum { BILU_DEBUG_EXTRA_CTA = 1, BILU_DEBUG_SPIN_LIMIT = 2 };
+bilu_status bilu_debug_set(bilu_ctx *ctx, int32_t what, int64_t value);
+
+/* Releases the context and all device memory it owns.  NULL is ignored. */
+void bilu_destroy(bilu_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BILU_H */

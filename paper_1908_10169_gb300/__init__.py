@@ -1,0 +1,182 @@
+"""Python binding of the GB300 block incomplete LU library (libbilu.so).
+
+Thin ctypes marshalling of the C ABI declared in include/bilu.h: the functions keep the
+C names and take numpy arrays or torch tensors (host or CUDA) for the pointer arguments.
+Every numerical step runs in the library's CUDA kernels; there is no CPU fallback, and
+loading fails loudly when the compiled library is missing (run ``build.build()``).
+
+Method: Bollhoefer, Schenk, Verbosio, "High Performance Block Incomplete LU
+Factorization", arXiv:1908.10169 (Crout-type BILU, Sec. 2.2; GMRES(30), Sec. 4).
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbilu.so")
+
+BILU_OK, BILU_NOT_CONVERGED, BILU_PERTURBED = 0, 1, 2
+BILU_ERR_ARG, BILU_ERR_OOM, BILU_ERR_CUDA, BILU_ERR_SINGULAR, BILU_ERR_TIMEOUT, BILU_ERR_STATE = -1, -2, -3, -4, -5, -6
+BILU_BLOCKING_FIXED, BILU_BLOCKING_ILU1T = 0, 1
+BILU_PREC_FP64, BILU_PREC_FP32, BILU_PREC_BF16 = 0, 1, 2
+BILU_SKIP_NONE, BILU_SKIP_BOUND, BILU_SKIP_LEARNED = 0, 1, 2
+BILU_DEBUG_EXTRA_CTA, BILU_DEBUG_SPIN_LIMIT = 1, 2
+BILU_MAX_BLOCK = 64
+
+# every extern "C" symbol that include/bilu.h declares
+EXPORTED = ["bilu_params_default", "bilu_create", "bilu_analyze", "bilu_factor", "bilu_apply",
+            "gmres_solve", "bilu_stats", "bilu_get_partition", "bilu_export", "bilu_last_error",
+            "bilu_debug_set", "bilu_destroy"]
+
+
+class bilu_params(ct.Structure):
+    _fields_ = [("blocking", ct.c_int32), ("max_block", ct.c_int32), ("fixed_block", ct.c_int32),
+                ("tau_analyze", ct.c_double), ("perturb", ct.c_int32), ("pert_tau", ct.c_double),
+                ("pert_rho", ct.c_double), ("precision", ct.c_int32), ("skip", ct.c_int32)]
+
+
+class gmres_info(ct.Structure):
+    _fields_ = [("iters", ct.c_int32), ("restarts", ct.c_int32), ("relres_true", ct.c_double),
+                ("relres_est", ct.c_double), ("t_solve_ms", ct.c_double)]
+
+
+class bilu_stats_t(ct.Structure):
+    _fields_ = [("n", ct.c_int64), ("nnz_a", ct.c_int64), ("nblocks", ct.c_int32), ("max_bsize", ct.c_int32),
+                ("avg_bsize", ct.c_double), ("std_bsize", ct.c_double), ("nnz_l", ct.c_int64),
+                ("nnz_u", ct.c_int64), ("nnz_d", ct.c_int64), ("kept_rows", ct.c_int64),
+                ("kept_cols", ct.c_int64), ("cand_rows", ct.c_int64), ("cand_cols", ct.c_int64),
+                ("nperturb", ct.c_int64), ("flops_factor", ct.c_double), ("t_analyze_ms", ct.c_double),
+                ("t_factor_ms", ct.c_double), ("pool_retries", ct.c_int32)]
+
+
+class BiluError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"bilu status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library; raises if it has not been built (no fallback path exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with paper_1908_10169_gb300.build.build()")
+        L = ct.CDLL(LIB_PATH)
+        P, i32, i64, f64 = ct.c_void_p, ct.c_int32, ct.c_int64, ct.c_double
+        sig = {
+            "bilu_params_default": ([ct.POINTER(bilu_params)], i32),
+            "bilu_create": ([ct.POINTER(P), ct.c_int, P], i32),
+            "bilu_analyze": ([P, i64, P, P, P, i32, ct.POINTER(bilu_params)], i32),
+            "bilu_factor": ([P, f64], i32),
+            "bilu_apply": ([P, P, P], i32),
+            "gmres_solve": ([P, P, P, f64, i32, i32, ct.POINTER(gmres_info)], i32),
+            "bilu_stats": ([P, ct.POINTER(bilu_stats_t)], i32),
+            "bilu_get_partition": ([P, P], i32),
+            "bilu_export": ([P] * 9, i32),
+            "bilu_last_error": ([P], ct.c_char_p),
+            "bilu_debug_set": ([P, i32, i64], i32),
+            "bilu_destroy": ([P], None),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    """Raw address of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ct.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(ct.c_void_p)
+
+
+def _check(ctx, st: int, allow=(BILU_OK,)):
+    if st in allow or st > 0 and BILU_PERTURBED in allow:
+        return st
+    if st < 0 or st not in allow:
+        msg = lib().bilu_last_error(ctx).decode() if ctx else ""
+        raise BiluError(st, msg)
+    return st
+
+
+def bilu_params_default(**overrides) -> bilu_params:
+    p = bilu_params()
+    lib().bilu_params_default(ct.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def bilu_create(device: int = 0, stream=None):
+    """Context on `device`; `stream` is a torch.cuda.Stream, a raw cudaStream_t, or None."""
+    h = ct.c_void_p()
+    raw = None
+    if stream is not None:
+        raw = ct.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    st = lib().bilu_create(ct.byref(h), device, raw)
+    if st != BILU_OK:
+        raise BiluError(st, "bilu_create failed")
+    return h
+
+
+def bilu_destroy(ctx):
+    lib().bilu_destroy(ctx)
+
+
+def bilu_last_error(ctx) -> str:
+    return lib().bilu_last_error(ctx).decode()
+
+
+def bilu_analyze(ctx, n: int, rowptr, colind, val, params: bilu_params | None = None):
+    """rowptr int64[n+1], colind int32[nnz], val float64[nnz]; numpy / CPU tensors or CUDA tensors."""
+    on_dev = int(bool(getattr(val, "is_cuda", False)))
+    p = params if params is not None else bilu_params_default()
+    st = lib().bilu_analyze(ctx, n, _ptr(rowptr), _ptr(colind), _ptr(val), on_dev, ct.byref(p))
+    return _check(ctx, st)
+
+
+def bilu_factor(ctx, droptol: float) -> int:
+    st = lib().bilu_factor(ctx, droptol)
+    return _check(ctx, st, (BILU_OK, BILU_PERTURBED))
+
+
+def bilu_apply(ctx, r, z) -> int:
+    st = lib().bilu_apply(ctx, _ptr(r), _ptr(z))
+    return _check(ctx, st)
+
+
+def gmres_solve(ctx, b, x, tol: float = 1e-8, restart: int = 30, maxit: int = 10000) -> gmres_info:
+    info = gmres_info()
+    st = lib().gmres_solve(ctx, _ptr(b), _ptr(x), tol, restart, maxit, ct.byref(info))
+    _check(ctx, st, (BILU_OK, BILU_NOT_CONVERGED))
+    info.status = st
+    return info
+
+
+def bilu_stats(ctx) -> bilu_stats_t:
+    s = bilu_stats_t()
+    _check(ctx, lib().bilu_stats(ctx, ct.byref(s)))
+    return s
+
+
+def bilu_get_partition(ctx, out):
+    return _check(ctx, lib().bilu_get_partition(ctx, _ptr(out)))
+
+
+def bilu_export(ctx, Lptr=None, Lrow=None, Lval=None, Uptr=None, Ucol=None, Uval=None, Dinv=None, Pblk=None):
+    return _check(ctx, lib().bilu_export(ctx, _ptr(Lptr), _ptr(Lrow), _ptr(Lval), _ptr(Uptr), _ptr(Ucol),
+                                         _ptr(Uval), _ptr(Dinv), _ptr(Pblk)))
+
+
+def bilu_debug_set(ctx, what: int, value: int):
+    return _check(ctx, lib().bilu_debug_set(ctx, what, value))

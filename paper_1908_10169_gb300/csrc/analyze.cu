@@ -1,0 +1,266 @@
+// Analysis: validation and copy of A, its CSC copy, block partition (host side).
+//
+// Sec. 2.1: the Crout ILU needs A by rows and by columns, so a CSC copy is built once.
+// Sec. 3.4: the block partition is either fixed-size or the simplified ILU(1,tau) guess.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "bilu_internal.h"
+
+namespace {
+
+struct HostCSR {
+    int64_t n = 0;
+    std::vector<int64_t> rowptr;
+    std::vector<int32_t> colind;
+    std::vector<double> val;
+};
+
+// Column-major copy: for column j, rows ascending.
+void build_csc(const HostCSR &A, std::vector<int32_t> &colptr, std::vector<int32_t> &rowind,
+               std::vector<double> &cval) {
+    const int64_t n = A.n, nnz = A.rowptr[n];
+    colptr.assign(n + 1, 0);
+    rowind.resize(nnz);
+    cval.resize(nnz);
+    for (int64_t e = 0; e < nnz; ++e) colptr[A.colind[e] + 1]++;
+    for (int64_t j = 0; j < n; ++j) colptr[j + 1] += colptr[j];
+    std::vector<int32_t> next(colptr.begin(), colptr.end() - 1);
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t e = A.rowptr[i]; e < A.rowptr[i + 1]; ++e) {
+            int32_t pos = next[A.colind[e]]++;
+            rowind[pos] = (int32_t)i;
+            cval[pos] = A.val[e];
+        }
+}
+
+double diag_of(const int64_t *ptr, const int32_t *ind, const double *v, int64_t i) {
+    const int32_t *b = ind + ptr[i], *e = ind + ptr[i + 1];
+    const int32_t *p = std::lower_bound(b, e, (int32_t)i);
+    return (p != e && *p == i) ? v[p - ind] : 0.0;
+}
+
+// The estimated pattern of column k of L (rows > k) or of row k of U (columns > k) under
+// the simplified ILU(1,tau) of Sec. 3.4: the original entries with |a| >= tau |a_kk|, and
+// the fill a_ik = -a_ij a_jk / a_jj (j < k < i, all three original) when
+// |a_ij a_jk| >= tau |a_jj a_kk|.  `major` is the compressed orientation that lists the
+// entries of column k (CSC for L, CSR for U); the fill walks the same orientation at j.
+std::vector<int32_t> ilu1t_pattern(int64_t k, const int64_t *ptr, const int32_t *ind,
+                                   const double *v, const std::vector<double> &diag, double tau) {
+    std::vector<int32_t> out;
+    const double akk = diag[k];
+    for (int64_t e = ptr[k]; e < ptr[k + 1]; ++e) {
+        const int32_t i = ind[e];
+        if (i > k && std::fabs(v[e]) >= tau * std::fabs(akk)) out.push_back(i);
+    }
+    for (int64_t e = ptr[k]; e < ptr[k + 1]; ++e) {
+        const int32_t j = ind[e];
+        if (j >= k) break;  // sorted: the entries above the diagonal come first
+        const double ajk = v[e], ajj = diag[j];
+        for (int64_t f = ptr[j]; f < ptr[j + 1]; ++f) {
+            const int32_t i = ind[f];
+            if (i > k && std::fabs(v[f] * ajk) >= tau * std::fabs(ajj * akk)) out.push_back(i);
+        }
+    }
+    std::sort(out.begin(), out.end());
+    out.erase(std::unique(out.begin(), out.end()), out.end());
+    return out;
+}
+
+// Number of entries of the sorted union of a and b that are > bound.
+int64_t union_count_above(const std::vector<int32_t> &a, const std::vector<int32_t> &b, int64_t bound) {
+    auto ia = std::upper_bound(a.begin(), a.end(), (int32_t)bound);
+    auto ib = std::upper_bound(b.begin(), b.end(), (int32_t)bound);
+    int64_t cnt = 0;
+    while (ia != a.end() || ib != b.end()) {
+        if (ib == b.end() || (ia != a.end() && *ia < *ib)) { ++ia; }
+        else if (ia == a.end() || *ib < *ia) { ++ib; }
+        else { ++ia; ++ib; }
+        ++cnt;
+    }
+    return cnt;
+}
+
+std::vector<int32_t> sorted_union(const std::vector<int32_t> &a, const std::vector<int32_t> &b) {
+    std::vector<int32_t> out;
+    out.reserve(a.size() + b.size());
+    std::set_union(a.begin(), a.end(), b.begin(), b.end(), std::back_inserter(out));
+    return out;
+}
+
+// Sec. 3.4 growth rule: a block [k, k+l) with r rows below and s columns to the right
+// stores f = (r + s + l) l entries; the scalar count grows by |I~| + |J~| + 1 for every
+// added column.  Column k+l joins while f_{l+1} <= 4/3 s_{l+1} or f_{l+1} <= s_{l+1} + 4(l+1)
+// and the size stays <= max_block.  Indices inside the block are not counted in r, s.
+std::vector<int32_t> partition_ilu1t(const HostCSR &A, const std::vector<int32_t> &colptr,
+                                     const std::vector<int32_t> &rowind, const std::vector<double> &cval,
+                                     double tau, int max_block) {
+    const int64_t n = A.n;
+    std::vector<double> diag(n);
+    for (int64_t i = 0; i < n; ++i) diag[i] = diag_of(A.rowptr.data(), A.colind.data(), A.val.data(), i);
+    std::vector<int64_t> cp(colptr.begin(), colptr.end());
+    auto colpat = [&](int64_t k) { return ilu1t_pattern(k, cp.data(), rowind.data(), cval.data(), diag, tau); };
+    auto rowpat = [&](int64_t k) {
+        return ilu1t_pattern(k, A.rowptr.data(), A.colind.data(), A.val.data(), diag, tau);
+    };
+    std::vector<int32_t> bstart;
+    int64_t k = 0;
+    while (k < n) {
+        const int64_t start = k;
+        std::vector<int32_t> R = colpat(start), C = rowpat(start);
+        int64_t scalar = (int64_t)R.size() + (int64_t)C.size() + 1;
+        int64_t l = 1;
+        while (l < max_block && start + l < n) {
+            const int64_t cand = start + l;
+            std::vector<int32_t> I = colpat(cand), J = rowpat(cand);
+            const int64_t r2 = union_count_above(R, I, cand), s2 = union_count_above(C, J, cand);
+            const int64_t f2 = (r2 + s2 + l + 1) * (l + 1);
+            const int64_t scalar2 = scalar + (int64_t)I.size() + (int64_t)J.size() + 1;
+            if (!(3 * f2 <= 4 * scalar2 || f2 <= scalar2 + 4 * (l + 1))) break;
+            R = sorted_union(R, I);
+            C = sorted_union(C, J);
+            scalar = scalar2;
+            ++l;
+        }
+        bstart.push_back((int32_t)start);
+        k = start + l;
+    }
+    bstart.push_back((int32_t)n);
+    return bstart;
+}
+
+}  // namespace
+
+void matrix_free(bilu_ctx *c) {
+    dev_free(c->d_rowptr);
+    dev_free(c->d_colind);
+    dev_free(c->d_val);
+    dev_free(c->d_colptr);
+    dev_free(c->d_rowind);
+    dev_free(c->d_cval);
+    dev_free(c->d_bstart);
+    dev_free(c->d_blkof);
+    dev_free(c->d_Dptr);
+}
+
+bilu_status analyze_run(bilu_ctx *c, int64_t n, const int64_t *rowptr, const int32_t *colind,
+                        const double *val, int on_device, const bilu_params *p) {
+    if (!p) return set_err(c, BILU_ERR_ARG, "params is NULL");
+    if (n < 0 || n >= (int64_t)INT32_MAX) return set_err(c, BILU_ERR_ARG, "n out of range");
+    if (p->max_block < 1 || p->max_block > BILU_MAX_BLOCK)
+        return set_err(c, BILU_ERR_ARG, "max_block must be in 1..64");
+    if (p->blocking == BILU_BLOCKING_FIXED && (p->fixed_block < 1 || p->fixed_block > p->max_block))
+        return set_err(c, BILU_ERR_ARG, "fixed_block must be in 1..max_block");
+    if (p->blocking != BILU_BLOCKING_FIXED && p->blocking != BILU_BLOCKING_ILU1T)
+        return set_err(c, BILU_ERR_ARG, "unknown blocking");
+    if (!(p->tau_analyze >= 0.0) || !(p->pert_tau >= 0.0) || !(p->pert_rho >= 0.0))
+        return set_err(c, BILU_ERR_ARG, "negative or NaN tolerance");
+    if (p->precision != BILU_PREC_FP64 && p->precision != BILU_PREC_FP32 && p->precision != BILU_PREC_BF16)
+        return set_err(c, BILU_ERR_ARG, "unknown precision");
+    if (p->skip != BILU_SKIP_NONE && p->skip != BILU_SKIP_BOUND && p->skip != BILU_SKIP_LEARNED)
+        return set_err(c, BILU_ERR_ARG, "unknown skip mode");
+    if (n > 0 && (!rowptr || !colind || !val)) return set_err(c, BILU_ERR_ARG, "null CSR array");
+
+    const auto t_start = std::chrono::steady_clock::now();
+
+    HostCSR A;
+    A.n = n;
+    A.rowptr.assign(n + 1, 0);
+    if (n > 0) {
+        if (on_device) {
+            BILU_CUDA(c, cudaMemcpy(A.rowptr.data(), rowptr, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
+        } else {
+            std::memcpy(A.rowptr.data(), rowptr, (n + 1) * sizeof(int64_t));
+        }
+    }
+    if (A.rowptr[0] != 0) return set_err(c, BILU_ERR_ARG, "rowptr[0] != 0");
+    for (int64_t i = 0; i < n; ++i)
+        if (A.rowptr[i + 1] < A.rowptr[i]) return set_err(c, BILU_ERR_ARG, "rowptr not monotone");
+    const int64_t nnz = A.rowptr[n];
+    if (nnz >= (int64_t)INT32_MAX) return set_err(c, BILU_ERR_ARG, "nnz >= 2^31 not supported");
+    A.colind.resize(nnz);
+    A.val.resize(nnz);
+    if (nnz > 0) {
+        if (on_device) {
+            BILU_CUDA(c, cudaMemcpy(A.colind.data(), colind, nnz * sizeof(int32_t), cudaMemcpyDeviceToHost));
+            BILU_CUDA(c, cudaMemcpy(A.val.data(), val, nnz * sizeof(double), cudaMemcpyDeviceToHost));
+        } else {
+            std::memcpy(A.colind.data(), colind, nnz * sizeof(int32_t));
+            std::memcpy(A.val.data(), val, nnz * sizeof(double));
+        }
+    }
+    double alpha = 0.0;
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t e = A.rowptr[i]; e < A.rowptr[i + 1]; ++e) {
+            if (A.colind[e] < 0 || A.colind[e] >= n) return set_err(c, BILU_ERR_ARG, "column index out of range");
+            if (e > A.rowptr[i] && A.colind[e] <= A.colind[e - 1])
+                return set_err(c, BILU_ERR_ARG, "column indices not strictly increasing within a row");
+            if (!std::isfinite(A.val[e])) return set_err(c, BILU_ERR_ARG, "non-finite matrix value");
+            alpha = std::max(alpha, std::fabs(A.val[e]));
+        }
+
+    std::vector<int32_t> colptr, rowind;
+    std::vector<double> cval;
+    build_csc(A, colptr, rowind, cval);
+
+    std::vector<int32_t> bstart;
+    if (p->blocking == BILU_BLOCKING_FIXED) {
+        for (int64_t s = 0; s < n; s += p->fixed_block) bstart.push_back((int32_t)s);
+        bstart.push_back((int32_t)n);
+    } else {
+        bstart = partition_ilu1t(A, colptr, rowind, cval, p->tau_analyze, p->max_block);
+    }
+    if (n == 0) bstart.assign(1, 0);
+
+    // (re)build device state
+    factor_free(c);
+    apply_free(c);
+    gmres_free(c);
+    matrix_free(c);
+    c->state = 0;
+    c->p = *p;
+    c->n = n;
+    c->nnz = nnz;
+    c->alpha = alpha;
+    c->h_bstart = bstart;
+    c->nb = (int32_t)bstart.size() - 1;
+    c->bmax = 0;
+    c->bmin = n > 0 ? BILU_MAX_BLOCK : 0;
+    c->h_Dptr.assign(c->nb + 1, 0);
+    std::vector<int32_t> blkof(std::max<int64_t>(n, 1));
+    for (int32_t K = 0; K < c->nb; ++K) {
+        const int32_t b = bstart[K + 1] - bstart[K];
+        c->bmax = std::max(c->bmax, b);
+        c->bmin = std::min(c->bmin, b);
+        c->h_Dptr[K + 1] = c->h_Dptr[K] + (int64_t)b * b;
+        for (int32_t i = bstart[K]; i < bstart[K + 1]; ++i) blkof[i] = K;
+    }
+    std::vector<int32_t> rp32(n + 1);
+    for (int64_t i = 0; i <= n; ++i) rp32[i] = (int32_t)A.rowptr[i];
+
+    auto up = [&](auto *&dptr, const auto &vec) -> cudaError_t {
+        using T = std::remove_reference_t<decltype(*dptr)>;
+        cudaError_t e = dev_alloc(&dptr, (int64_t)vec.size());
+        if (e != cudaSuccess) return e;
+        if (vec.empty()) return cudaSuccess;
+        return cudaMemcpyAsync((void *)dptr, vec.data(), vec.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream);
+    };
+    cudaError_t e;
+    if ((e = up(c->d_rowptr, rp32)) != cudaSuccess || (e = up(c->d_colind, A.colind)) != cudaSuccess ||
+        (e = up(c->d_val, A.val)) != cudaSuccess || (e = up(c->d_colptr, colptr)) != cudaSuccess ||
+        (e = up(c->d_rowind, rowind)) != cudaSuccess || (e = up(c->d_cval, cval)) != cudaSuccess ||
+        (e = up(c->d_bstart, bstart)) != cudaSuccess || (e = up(c->d_blkof, blkof)) != cudaSuccess ||
+        (e = up(c->d_Dptr, c->h_Dptr)) != cudaSuccess) {
+        matrix_free(c);
+        return e == cudaErrorMemoryAllocation ? set_err(c, BILU_ERR_OOM, "device allocation failed in analyze")
+                                              : cuda_err(c, e, "analyze upload");
+    }
+    BILU_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->t_analyze_ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    c->state = 1;
+    return BILU_OK;
+}

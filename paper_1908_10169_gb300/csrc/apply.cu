@@ -1,0 +1,251 @@
+// Preconditioner application z = M^{-1} r, M = L D^{-1} U (Sec. 2.2).
+//
+// Forward:  y_K = r_K - sum_J L_J(rows in B_K, :) y_J    (unit block lower L, gather form)
+// Backward: z_K = D_K ( y_K - U-breve_K(:, C_K) z(C_K) ) (K from last to first)
+// Both sweeps are persistent kernels: CTAs claim blocks in sweep order from a ticket
+// counter and wait (bounded) on per-block completion flags of the blocks they read, so
+// independent blocks of the block-dependency DAG run concurrently.  Summation orders are
+// fixed (producers in increasing J, fixed per-thread partial sums), so results are
+// bitwise reproducible.
+#include <algorithm>
+
+#include "dev_common.cuh"
+
+namespace {
+
+constexpr int AT = 256;        // threads per CTA
+constexpr int AW = AT / 32;
+constexpr long long APPLY_SPIN = 1LL << 22;
+
+struct ApplyArgs {
+    int32_t nb;
+    const int32_t *bstart, *blkof;
+    const int64_t *Lptr, *Lvptr, *Uptr, *Uvptr, *Dptr;
+    const int32_t *Lrow, *Ucol;
+    const double *Lval, *Uval, *Dinv;
+    const int32_t *prodU, *prodUcnt;
+    int32_t prodcap;
+    const int2 *planF;     // per (K, t): L_J rows inside B_K
+    const double *r;
+    double *z;             // holds y after the forward sweep
+    int32_t *flagF, *flagB;
+    int32_t *st;           // [0] epoch, [1] forward ticket, [2] backward ticket, [3] status
+    const int32_t *skip;   // optional: nonzero -> return immediately
+};
+
+__device__ __forceinline__ bool wait_flag(const int32_t *flag, int epoch, int32_t *status) {
+    long long it = 0;
+    while (ld_acquire_s32(flag) < epoch) {
+        if (++it > APPLY_SPIN) {
+            atomicCAS(status, 0, DEV_TIMEOUT);
+            return false;
+        }
+        __nanosleep(32);
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(32) apply_begin_kernel(int32_t *st, const int32_t *skip) {
+    if (skip && *skip) return;
+    if (threadIdx.x == 0) {
+        st[0] += 1;
+        st[1] = 0;
+        st[2] = 0;
+    }
+}
+
+__global__ void __launch_bounds__(AT) apply_forward_kernel(ApplyArgs a) {
+    if (a.skip && ldcg(a.skip)) return;
+    __shared__ double acc[BILU_MAX_BLOCK];
+    __shared__ int s_K, s_ok;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int epoch = ldcg(a.st);
+    while (true) {
+        if (tid == 0) s_K = atomicAdd(a.st + 1, 1);
+        __syncthreads();
+        const int K = s_K;
+        __syncthreads();
+        if (K >= a.nb) return;
+        const int s0 = a.bstart[K], b = a.bstart[K + 1] - s0;
+        if (tid < b) acc[tid] = a.r[s0 + tid];
+        const int pc = ldcg(a.prodUcnt + K);
+        // wait for all producers (their y blocks)
+        if (tid == 0) {
+            int ok = 1;
+            for (int t = 0; t < pc && ok; ++t) {
+                const int J = ldcg(a.prodU + (int64_t)K * a.prodcap + t);
+                ok = wait_flag(a.flagF + J, epoch, a.st + 3);
+            }
+            s_ok = ok;
+        }
+        __syncthreads();
+        if (!s_ok) return;
+        for (int t = 0; t < pc; ++t) {
+            const int J = ldcg(a.prodU + (int64_t)K * a.prodcap + t);
+            const int2 rg = a.planF[(int64_t)K * a.prodcap + t];
+            const int sJ = a.bstart[J], bJ = a.bstart[J + 1] - sJ;
+            const double yJ0 = lane < bJ ? ldcg(a.z + sJ + lane) : 0.0;
+            const double yJ1 = lane + 32 < bJ ? ldcg(a.z + sJ + lane + 32) : 0.0;
+            const double *Lv = a.Lval + a.Lvptr[J] + (int64_t)(rg.x - a.Lptr[J]) * bJ;
+            for (int p = rg.x + warp; p < rg.y; p += AW) {
+                const double *row = Lv + (int64_t)(p - rg.x) * bJ;
+                double s = 0.0;
+                if (lane < bJ) s = row[lane] * yJ0;
+                if (lane + 32 < bJ) s = fma(row[lane + 32], yJ1, s);
+                s = warp_sum(s);
+                if (lane == 0) acc[a.Lrow[p] - s0] -= s;
+            }
+            __syncthreads();
+        }
+        if (tid < b) a.z[s0 + tid] = acc[tid];
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            st_release_s32(a.flagF + K, epoch);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(AT) apply_backward_kernel(ApplyArgs a) {
+    if (a.skip && ldcg(a.skip)) return;
+    __shared__ double part[AT / BILU_MAX_BLOCK][BILU_MAX_BLOCK];
+    __shared__ double tv[BILU_MAX_BLOCK];
+    __shared__ int s_K, s_ok;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NG = AT / BILU_MAX_BLOCK;  // column groups
+    const int epoch = ldcg(a.st);
+    while (true) {
+        if (tid == 0) s_K = atomicAdd(a.st + 2, 1);
+        __syncthreads();
+        const int K = a.nb - 1 - s_K;
+        __syncthreads();
+        if (K < 0) return;
+        const int s0 = a.bstart[K], b = a.bstart[K + 1] - s0;
+        const int64_t q0 = a.Uptr[K], q1 = a.Uptr[K + 1];
+        // wait for the blocks holding the kept columns of U-breve_K (sorted, so each block
+        // forms one run; the first lane of a run waits on its flag)
+        if (warp == 0) {
+            int ok = 1, last = -1;
+            for (int64_t qb = q0; qb < q1; qb += 32) {
+                const int64_t q = qb + lane;
+                const int blk = q < q1 ? a.blkof[a.Ucol[q]] : -1;
+                int prev = __shfl_up_sync(FULL_MASK, blk, 1);
+                if (lane == 0) prev = last;
+                const bool first = q < q1 && blk != prev;
+                int okl = 1;
+                if (first) okl = wait_flag(a.flagB + blk, epoch, a.st + 3) ? 1 : 0;
+                ok = ok && __all_sync(FULL_MASK, okl);
+                last = __shfl_sync(FULL_MASK, blk, 31);
+                if (!ok) break;
+            }
+            if (lane == 0) s_ok = ok;
+        }
+        __syncthreads();
+        if (!s_ok) return;
+        // t = y_K - U-breve_K z(C_K): group g handles columns q = q0 + g, q0 + g + NG, ...
+        const int g = tid / BILU_MAX_BLOCK, rr = tid % BILU_MAX_BLOCK;
+        double s = 0.0;
+        if (rr < b) {
+            const double *Uv = a.Uval + a.Uvptr[K];
+            for (int64_t q = q0 + g; q < q1; q += NG) s = fma(Uv[(q - q0) * b + rr], ldcg(a.z + a.Ucol[q]), s);
+        }
+        part[g][rr] = s;
+        __syncthreads();
+        if (tid < b) {
+            double t = ldcg(a.z + s0 + tid);
+            for (int gg = 0; gg < NG; ++gg) t -= part[gg][tid];
+            tv[tid] = t;
+        }
+        __syncthreads();
+        // z_K = D_K t: warp per row
+        const double *D = a.Dinv + a.Dptr[K];
+        const double t0 = lane < b ? tv[lane] : 0.0, t1 = lane + 32 < b ? tv[lane + 32] : 0.0;
+        for (int r = warp; r < b; r += AW) {
+            double v = 0.0;
+            if (lane < b) v = D[(int64_t)r * b + lane] * t0;
+            if (lane + 32 < b) v = fma(D[(int64_t)r * b + lane + 32], t1, v);
+            v = warp_sum(v);
+            if (lane == 0) a.z[s0 + r] = v;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            st_release_s32(a.flagB + K, epoch);
+        }
+    }
+}
+
+// Apply plan: for block K and its t-th forward producer J, the kept rows of L_J inside B_K.
+__global__ void apply_plan_kernel(int32_t nb, int32_t prodcap, const int32_t *bstart, const int64_t *Lptr,
+                                  const int32_t *Lrow, const int32_t *prodU, const int32_t *prodUcnt,
+                                  int2 *planF) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t total = (int64_t)nb * prodcap;
+    for (int64_t w = gw; w < total; w += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int K = (int)(w / prodcap), t = (int)(w % prodcap);
+        if (t >= prodUcnt[K]) continue;
+        const int J = prodU[(int64_t)K * prodcap + t];
+        const int s0 = bstart[K], s1 = bstart[K + 1];
+        const int ps = warp_lower_bound(Lrow, (int)Lptr[J], (int)Lptr[J + 1], s0);
+        const int pe = warp_lower_bound(Lrow, ps, (int)Lptr[J + 1], s1);
+        if (lane == 0) planF[w] = make_int2(ps, pe);
+    }
+}
+
+}  // namespace
+
+void apply_free(bilu_ctx *c) {
+    dev_free(c->d_planF);
+    dev_free(c->d_flagF);
+    dev_free(c->d_flagB);
+    dev_free(c->d_apst);
+    dev_free(c->d_stage_in);
+    dev_free(c->d_stage_out);
+}
+
+bilu_status apply_alloc(bilu_ctx *c) {
+    apply_free(c);
+    const int64_t nb = std::max<int64_t>(c->nb, 1);
+    if (dev_alloc(&c->d_flagF, nb) != cudaSuccess || dev_alloc(&c->d_flagB, nb) != cudaSuccess ||
+        dev_alloc(&c->d_planF, nb * (int64_t)c->prodcap) != cudaSuccess || dev_alloc(&c->d_apst, 8) != cudaSuccess) {
+        apply_free(c);
+        return set_err(c, BILU_ERR_OOM, "apply allocation failed");
+    }
+    BILU_CUDA(c, cudaMemsetAsync(c->d_flagF, 0, nb * sizeof(int32_t), c->stream));
+    BILU_CUDA(c, cudaMemsetAsync(c->d_flagB, 0, nb * sizeof(int32_t), c->stream));
+    BILU_CUDA(c, cudaMemsetAsync(c->d_apst, 0, 8 * sizeof(int32_t), c->stream));
+    const int64_t warps = nb * c->prodcap;
+    const int threads = 256;
+    const int64_t blocks = std::min<int64_t>((warps * 32 + threads - 1) / threads, 65535);
+    if (c->nb > 0)
+        apply_plan_kernel<<<(unsigned)blocks, threads, 0, c->stream>>>(c->nb, c->prodcap, c->d_bstart, c->d_Lptr, c->d_Lrow,
+                                                                     c->d_prodU, c->d_prodUcnt, c->d_planF);
+    BILU_CUDA(c, cudaGetLastError());
+    return BILU_OK;
+}
+
+bilu_status apply_launch(bilu_ctx *c, const double *d_r, double *d_z, const int32_t *skip) {
+    ApplyArgs a{};
+    a.nb = c->nb;
+    a.bstart = c->d_bstart;
+    a.blkof = c->d_blkof;
+    a.Lptr = c->d_Lptr; a.Lvptr = c->d_Lvptr; a.Uptr = c->d_Uptr; a.Uvptr = c->d_Uvptr; a.Dptr = c->d_Dptr;
+    a.Lrow = c->d_Lrow; a.Ucol = c->d_Ucol; a.Lval = c->d_Lval; a.Uval = c->d_Uval; a.Dinv = c->d_Dinv;
+    a.prodU = c->d_prodU; a.prodUcnt = c->d_prodUcnt; a.prodcap = c->prodcap;
+    a.planF = c->d_planF;
+    a.r = d_r;
+    a.z = d_z;
+    a.flagF = c->d_flagF;
+    a.flagB = c->d_flagB;
+    a.st = c->d_apst;
+    a.skip = skip;
+    const int G = c->nsm * 4;
+    apply_begin_kernel<<<1, 32, 0, c->stream>>>(c->d_apst, skip);
+    apply_forward_kernel<<<G, AT, 0, c->stream>>>(a);
+    apply_backward_kernel<<<G, AT, 0, c->stream>>>(a);
+    BILU_CUDA(c, cudaGetLastError());
+    return BILU_OK;
+}
+
+bilu_status apply_run(bilu_ctx *c, const double *d_r, double *d_z) { return apply_launch(c, d_r, d_z, nullptr); }

@@ -1,0 +1,147 @@
+// Internal state of a bilu context (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/bilu.h"
+
+// Device-side status codes of the persistent kernels (host maps them to bilu_status).
+enum {
+    DEV_OK = 0,
+    DEV_POOL_OVERFLOW = 1,   // L/U value or index pool full: host grows it and re-runs
+    DEV_PROD_OVERFLOW = 2,   // a producer list is full: host grows it and re-runs
+    DEV_TIMEOUT = 3,         // a bounded wait gave up
+    DEV_SINGULAR = 4,        // singular diagonal block, perturbation off or not curing it
+    DEV_INTERNAL = 5,        // an index check failed (never expected)
+};
+
+// Slots of the device info array written by the factor kernel.
+enum {
+    INFO_FAIL_BLOCK = 0,     // block at which a failure was recorded
+    INFO_NPERTURB = 1,       // perturbed entries
+    INFO_CAND_ROWS = 2,      // candidate rows (outside the pivot block), summed
+    INFO_CAND_COLS = 3,
+    INFO_MAX_PROD = 4,       // longest producer list seen
+    INFO_TIMEOUT_SITE = 5,   // which wait timed out
+    INFO_COUNT = 16
+};
+
+struct bilu_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int nsm = 0;
+    std::string err;
+    int state = 0;  // 0 created, 1 analyzed, 2 factored
+    bilu_params p{};
+
+    // matrix (device copies; int32 row pointers internally, nnz < 2^31 is checked)
+    int64_t n = 0, nnz = 0;
+    int32_t *d_rowptr = nullptr, *d_colind = nullptr;
+    double *d_val = nullptr;
+    int32_t *d_colptr = nullptr, *d_rowind = nullptr;
+    double *d_cval = nullptr;
+    double alpha = 0.0;  // max |a_ij| (Sec. 3.6)
+
+    // partition
+    int32_t nb = 0, bmax = 0, bmin = 0;
+    std::vector<int32_t> h_bstart;
+    int32_t *d_bstart = nullptr, *d_blkof = nullptr;
+    int64_t *d_Dptr = nullptr;
+    std::vector<int64_t> h_Dptr;
+
+    // factor pools
+    int64_t capLrow = 0, capLval = 0, capUcol = 0, capUval = 0;
+    int64_t *d_Lptr = nullptr, *d_Lvptr = nullptr, *d_Uptr = nullptr, *d_Uvptr = nullptr;
+    int32_t *d_Lrow = nullptr, *d_Ucol = nullptr;
+    double *d_Lval = nullptr, *d_Uval = nullptr;
+    double *d_Dinv = nullptr, *d_Pblk = nullptr;
+
+    // producer lists (blocks J whose kept U columns / L rows hit block K)
+    int32_t prodcap = 0;
+    int32_t *d_prodL = nullptr, *d_prodLcnt = nullptr, *d_prodU = nullptr, *d_prodUcnt = nullptr;
+    int32_t *d_lastL = nullptr, *d_lastU = nullptr;
+
+    // factor scratch
+    int64_t capT = 0;
+    double *d_TL = nullptr, *d_TU = nullptr;
+    int32_t *d_rowsL = nullptr, *d_rowsU = nullptr;
+    int32_t *d_keepL = nullptr, *d_keepU = nullptr;
+    uint32_t *d_bmL = nullptr, *d_bmU = nullptr;
+    int32_t *d_wbL = nullptr, *d_wbU = nullptr;        // bitmap word prefix counts
+    int32_t *d_xslotL = nullptr, *d_xslotU = nullptr;  // candidate slot per producer entry
+    int64_t *d_pinfoL = nullptr, *d_pinfoU = nullptr;  // per-producer update plan
+    int64_t capXS = 0;
+    double *d_LU = nullptr;
+    int32_t *d_perm = nullptr;
+    int32_t *d_kstate = nullptr;   // per-step scalars (candidate counts, pivot status)
+    int32_t *d_status = nullptr;
+    int64_t *d_info = nullptr;
+    uint32_t *d_bar = nullptr;     // grid barrier counter + generation
+
+    // apply
+    int32_t *d_flagF = nullptr, *d_flagB = nullptr;
+    int2 *d_planF = nullptr;       // per (block, forward producer): L rows inside the block
+    int32_t *d_apst = nullptr;     // epoch, forward ticket, backward ticket
+    double *d_stage_in = nullptr, *d_stage_out = nullptr;  // host-vector staging
+
+    // gmres workspace
+    int gm_restart = 0;
+    double *d_V = nullptr, *d_w = nullptr, *d_z = nullptr, *d_r = nullptr, *d_u = nullptr;
+    double *d_gb = nullptr, *d_gx = nullptr;   // right-hand side and iterate
+    double *d_part = nullptr;      // reduction partials
+    double *d_gm = nullptr;        // H, g, cs, sn, y, scalars
+    int32_t *d_gmi = nullptr;      // integer gmres state
+    double *h_gm_pinned = nullptr;
+    int32_t *h_gmi_pinned = nullptr;
+    cudaGraphExec_t gm_graph = nullptr;
+    int gm_graph_restart = 0;
+    const double *gm_graph_b = nullptr;
+    double *gm_graph_x = nullptr;
+
+    // results of the last factorization
+    int64_t kept_rows = 0, kept_cols = 0, nnz_l = 0, nnz_u = 0, cand_rows = 0, cand_cols = 0;
+    int64_t nperturb = 0;
+    int32_t pool_retries = 0;
+    double flops_factor = 0.0, t_analyze_ms = 0.0, t_factor_ms = 0.0;
+};
+
+// helpers shared by the translation units of the library
+bilu_status set_err(bilu_ctx *c, bilu_status st, const std::string &msg);
+bilu_status cuda_err(bilu_ctx *c, cudaError_t e, const char *where);
+#define BILU_CUDA(ctx, call)                                       \
+    do {                                                           \
+        cudaError_t _e = (call);                                   \
+        if (_e != cudaSuccess) return cuda_err((ctx), _e, #call);  \
+    } while (0)
+
+template <class T>
+cudaError_t dev_alloc(T **p, int64_t count) {
+    *p = nullptr;
+    if (count <= 0) count = 1;
+    return cudaMalloc((void **)p, (size_t)count * sizeof(T));
+}
+template <class T>
+void dev_free(T *&p) {
+    if (p) cudaFree((void *)p);
+    p = nullptr;
+}
+
+// Library-internal entry points implemented in the .cu files.
+bilu_status factor_run(bilu_ctx *c, double droptol);
+bilu_status factor_alloc(bilu_ctx *c);
+void factor_free(bilu_ctx *c);
+bilu_status apply_run(bilu_ctx *c, const double *d_r, double *d_z);
+bilu_status apply_launch(bilu_ctx *c, const double *d_r, double *d_z, const int32_t *skip);
+bilu_status apply_alloc(bilu_ctx *c);
+void apply_free(bilu_ctx *c);
+bilu_status gmres_run(bilu_ctx *c, const double *d_b, double *d_x, double tol, int restart,
+                      int maxit, gmres_info *info);
+void gmres_free(bilu_ctx *c);
+bilu_status analyze_run(bilu_ctx *c, int64_t n, const int64_t *rowptr, const int32_t *colind,
+                        const double *val, int on_device, const bilu_params *p);
+void matrix_free(bilu_ctx *c);

@@ -1,0 +1,229 @@
+// The C ABI (include/bilu.h): argument checking, call order, host-vector staging.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "bilu_internal.h"
+
+extern int g_debug_extra_cta;
+extern long long g_debug_spin_limit;
+
+bilu_status set_err(bilu_ctx *c, bilu_status st, const std::string &msg) {
+    if (c) c->err = msg;
+    return st;
+}
+
+bilu_status cuda_err(bilu_ctx *c, cudaError_t e, const char *where) {
+    if (c) c->err = std::string(where) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? BILU_ERR_OOM : BILU_ERR_CUDA;
+}
+
+namespace {
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" {
+
+bilu_status bilu_params_default(bilu_params *p) {
+    if (!p) return BILU_ERR_ARG;
+    std::memset(p, 0, sizeof(*p));
+    p->blocking = BILU_BLOCKING_FIXED;
+    p->max_block = 64;
+    p->fixed_block = 32;
+    p->tau_analyze = 1e-2;
+    p->perturb = 1;
+    p->pert_tau = 1e-2;  // Sec. 3.6
+    p->pert_rho = 1e-1;  // Sec. 3.6
+    p->precision = BILU_PREC_FP64;
+    p->skip = BILU_SKIP_NONE;
+    return BILU_OK;
+}
+
+bilu_status bilu_create(bilu_ctx **ctx, int device, void *cuda_stream) {
+    if (!ctx) return BILU_ERR_ARG;
+    *ctx = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return BILU_ERR_ARG;
+    }
+    bilu_ctx *c = new (std::nothrow) bilu_ctx();
+    if (!c) return BILU_ERR_OOM;
+    c->device = device;
+    if (cudaSetDevice(device) != cudaSuccess) { delete c; return BILU_ERR_CUDA; }
+    if (cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) { delete c; return BILU_ERR_CUDA; }
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device);
+    if (!coop) { delete c; return BILU_ERR_CUDA; }
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else {
+        // a private stream: graph capture is not possible on the legacy default stream
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) { delete c; return BILU_ERR_CUDA; }
+        c->own_stream = true;
+    }
+    *ctx = c;
+    return BILU_OK;
+}
+
+void bilu_destroy(bilu_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    gmres_free(c);
+    apply_free(c);
+    factor_free(c);
+    matrix_free(c);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+const char *bilu_last_error(const bilu_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+bilu_status bilu_analyze(bilu_ctx *c, int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val,
+                         int32_t on_device, const bilu_params *p) {
+    if (!c) return BILU_ERR_ARG;
+    c->err.clear();
+    BILU_CUDA(c, cudaSetDevice(c->device));
+    return analyze_run(c, n, rowptr, colind, val, on_device, p);
+}
+
+bilu_status bilu_factor(bilu_ctx *c, double droptol) {
+    if (!c) return BILU_ERR_ARG;
+    c->err.clear();
+    if (c->state < 1) return set_err(c, BILU_ERR_STATE, "bilu_factor before bilu_analyze");
+    if (!(droptol >= 0.0) || !std::isfinite(droptol)) return set_err(c, BILU_ERR_ARG, "droptol must be finite and >= 0");
+    if (c->p.precision != BILU_PREC_FP64 || c->p.skip != BILU_SKIP_NONE)
+        return set_err(c, BILU_ERR_ARG, "precision / skip mode not available in this build");
+    BILU_CUDA(c, cudaSetDevice(c->device));
+    c->state = 1;
+    gmres_free(c);  // captured graphs refer to the previous factor
+    bilu_status st = factor_run(c, droptol);
+    if (st < 0) return st;
+    bilu_status sa = apply_alloc(c);
+    if (sa != BILU_OK) return sa;
+    BILU_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->state = 2;
+    return st;
+}
+
+bilu_status bilu_apply(bilu_ctx *c, const double *r, double *z) {
+    if (!c) return BILU_ERR_ARG;
+    if (c->state < 2) return set_err(c, BILU_ERR_STATE, "bilu_apply before bilu_factor");
+    if (c->n > 0 && (!r || !z)) return set_err(c, BILU_ERR_ARG, "null vector");
+    if (c->n == 0) return BILU_OK;
+    if (r == z) return set_err(c, BILU_ERR_ARG, "r and z must not overlap");
+    BILU_CUDA(c, cudaSetDevice(c->device));
+    const bool dr = is_device_ptr(r), dz = is_device_ptr(z);
+    if (dr && dz) return apply_run(c, r, z);
+    if (!c->d_stage_in) {
+        BILU_CUDA(c, cudaMalloc((void **)&c->d_stage_in, c->n * sizeof(double)));
+        BILU_CUDA(c, cudaMalloc((void **)&c->d_stage_out, c->n * sizeof(double)));
+    }
+    const double *rin = r;
+    if (!dr) {
+        BILU_CUDA(c, cudaMemcpyAsync(c->d_stage_in, r, c->n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        rin = c->d_stage_in;
+    }
+    double *zout = dz ? z : c->d_stage_out;
+    bilu_status st = apply_run(c, rin, zout);
+    if (st != BILU_OK) return st;
+    if (!dz) {
+        BILU_CUDA(c, cudaMemcpyAsync(z, zout, c->n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        BILU_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    return BILU_OK;
+}
+
+bilu_status gmres_solve(bilu_ctx *c, const double *b, double *x, double tol, int32_t restart, int32_t maxit,
+                        gmres_info *info) {
+    if (!c) return BILU_ERR_ARG;
+    c->err.clear();
+    if (c->state < 2) return set_err(c, BILU_ERR_STATE, "gmres_solve before bilu_factor");
+    if (c->n > 0 && (!b || !x)) return set_err(c, BILU_ERR_ARG, "null vector");
+    if (info) std::memset(info, 0, sizeof(*info));
+    if (c->n == 0) return BILU_OK;
+    BILU_CUDA(c, cudaSetDevice(c->device));
+    return gmres_run(c, b, x, tol, restart, maxit, info);
+}
+
+bilu_status bilu_stats(bilu_ctx *c, bilu_stats_t *o) {
+    if (!c || !o) return BILU_ERR_ARG;
+    if (c->state < 1) return set_err(c, BILU_ERR_STATE, "no analysis");
+    std::memset(o, 0, sizeof(*o));
+    o->n = c->n;
+    o->nnz_a = c->nnz;
+    o->nblocks = c->nb;
+    o->max_bsize = c->bmax;
+    double s = 0.0, s2 = 0.0;
+    for (int32_t K = 0; K < c->nb; ++K) {
+        const double b = c->h_bstart[K + 1] - c->h_bstart[K];
+        s += b;
+        s2 += b * b;
+    }
+    o->avg_bsize = c->nb ? s / c->nb : 0.0;
+    o->std_bsize = c->nb ? std::sqrt(std::max(0.0, s2 / c->nb - o->avg_bsize * o->avg_bsize)) : 0.0;
+    o->nnz_d = c->h_Dptr.empty() ? 0 : c->h_Dptr.back();
+    o->t_analyze_ms = c->t_analyze_ms;
+    if (c->state >= 2) {
+        o->nnz_l = c->nnz_l;
+        o->nnz_u = c->nnz_u;
+        o->kept_rows = c->kept_rows;
+        o->kept_cols = c->kept_cols;
+        o->cand_rows = c->cand_rows;
+        o->cand_cols = c->cand_cols;
+        o->nperturb = c->nperturb;
+        o->t_factor_ms = c->t_factor_ms;
+        o->pool_retries = c->pool_retries;
+        o->flops_factor = c->flops_factor;
+    }
+    return BILU_OK;
+}
+
+bilu_status bilu_get_partition(bilu_ctx *c, int32_t *bstart) {
+    if (!c || !bstart) return BILU_ERR_ARG;
+    if (c->state < 1) return set_err(c, BILU_ERR_STATE, "no analysis");
+    std::memcpy(bstart, c->h_bstart.data(), c->h_bstart.size() * sizeof(int32_t));
+    return BILU_OK;
+}
+
+bilu_status bilu_export(bilu_ctx *c, int64_t *Lptr, int32_t *Lrow, double *Lval, int64_t *Uptr, int32_t *Ucol,
+                        double *Uval, double *Dinv, double *Pblk) {
+    if (!c) return BILU_ERR_ARG;
+    if (c->state < 2) return set_err(c, BILU_ERR_STATE, "no factor");
+    BILU_CUDA(c, cudaSetDevice(c->device));
+    const int64_t nb1 = c->nb + 1, nd = c->h_Dptr.back();
+    auto cp = [&](void *dst, const void *src, int64_t bytes) -> cudaError_t {
+        if (!dst || bytes <= 0) return cudaSuccess;
+        return cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost);
+    };
+    BILU_CUDA(c, cp(Lptr, c->d_Lptr, nb1 * sizeof(int64_t)));
+    BILU_CUDA(c, cp(Uptr, c->d_Uptr, nb1 * sizeof(int64_t)));
+    BILU_CUDA(c, cp(Lrow, c->d_Lrow, c->kept_rows * sizeof(int32_t)));
+    BILU_CUDA(c, cp(Ucol, c->d_Ucol, c->kept_cols * sizeof(int32_t)));
+    BILU_CUDA(c, cp(Lval, c->d_Lval, c->nnz_l * sizeof(double)));
+    BILU_CUDA(c, cp(Uval, c->d_Uval, c->nnz_u * sizeof(double)));
+    BILU_CUDA(c, cp(Dinv, c->d_Dinv, nd * sizeof(double)));
+    BILU_CUDA(c, cp(Pblk, c->d_Pblk, nd * sizeof(double)));
+    return BILU_OK;
+}
+
+bilu_status bilu_debug_set(bilu_ctx *c, int32_t what, int64_t value) {
+    if (!c) return BILU_ERR_ARG;
+    switch (what) {
+        case BILU_DEBUG_EXTRA_CTA: g_debug_extra_cta = value ? 1 : 0; return BILU_OK;
+        case BILU_DEBUG_SPIN_LIMIT: g_debug_spin_limit = value; return BILU_OK;
+        default: return set_err(c, BILU_ERR_ARG, "unknown debug setting");
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,137 @@
+// Device helpers shared by the library's kernels: cache-bypassing loads, warp and block
+// reductions / scans, a bounded grid barrier for cooperative persistent kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "bilu_internal.h"
+
+#define FULL_MASK 0xffffffffu
+
+// Loads of data written by other CTAs during the same launch: bypass L1 (which is not
+// coherent across SMs), read from L2.
+template <class T>
+__device__ __forceinline__ T ldcg(const T *p) {
+    return __ldcg(p);
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int32_t ld_acquire_s32(const int32_t *p) {
+    int32_t v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_s32(int32_t *p, int32_t v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
+    return v;
+}
+__device__ __forceinline__ int warp_sum_i(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
+    return v;
+}
+__device__ __forceinline__ int warp_incl_scan(int v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(FULL_MASK, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// Exclusive scan over the block; returns the thread's exclusive prefix and writes the
+// block total to *total.  `ws` is shared scratch of >= 33 ints.  All threads must call.
+__device__ __forceinline__ int block_excl_scan(int v, int *ws, int *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    int inc = warp_incl_scan(v);
+    if (lane == 31) ws[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        int x = lane < nw ? ws[lane] : 0;
+        int xi = warp_incl_scan(x);
+        if (lane < nw) ws[lane] = xi - x;
+        if (lane == nw - 1) ws[32] = xi;
+    }
+    __syncthreads();
+    int res = inc - v + ws[warp];
+    *total = ws[32];
+    __syncthreads();
+    return res;
+}
+
+// First position in sorted a[lo, hi) with a[pos] >= key, computed by a full warp
+// (32-ary search: two dependent L2 round trips for lists of up to ~1000 entries).
+__device__ __forceinline__ int warp_lower_bound(const int32_t *a, int lo, int hi, int key) {
+    const int lane = threadIdx.x & 31;
+    while (hi - lo > 32) {
+        const int step = (hi - lo + 31) >> 5;
+        const int pos = lo + lane * step;
+        const bool ge = (pos < hi) ? (ldcg(a + pos) >= key) : true;
+        const unsigned m = __ballot_sync(FULL_MASK, ge);
+        if (m == 0) {  // every probe < key: the answer lies after the last probe
+            lo = lo + 31 * step + 1;
+            continue;
+        }
+        const int f = __ffs(m) - 1;
+        if (f == 0) return lo;
+        const int nlo = lo + (f - 1) * step + 1;
+        const int nhi = min(hi, lo + f * step);
+        lo = nlo;
+        hi = nhi;
+    }
+    const int pos = lo + lane;
+    const bool ge = (pos < hi) ? (ldcg(a + pos) >= key) : true;
+    const unsigned m = __ballot_sync(FULL_MASK, ge);
+    return m ? lo + __ffs(m) - 1 : hi;
+}
+
+// Bounded grid barrier for a cooperative launch of G CTAs.  bar[0] counts arrivals,
+// bar[1] is the generation.  A wait that exceeds spin_limit polls records DEV_TIMEOUT.
+// Returns false (uniformly in the CTA) when the device status word holds an error,
+// in which case the caller returns.
+__device__ __forceinline__ bool grid_barrier(uint32_t *bar, uint32_t G, int32_t *status,
+                                             long long spin_limit, int64_t *info, int site) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const uint32_t gen = ld_acquire_u32(bar + 1);
+        __threadfence();
+        const uint32_t arrived = atomicAdd(bar, 1u);
+        if (arrived == G - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            long long it = 0;
+            while (ld_acquire_u32(bar + 1) == gen) {
+                if (++it > spin_limit) {
+                    if (atomicCAS(status, 0, DEV_TIMEOUT) == 0) info[INFO_TIMEOUT_SITE] = site;
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        if (ld_acquire_s32(status) != DEV_OK) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__device__ __forceinline__ void set_status(int32_t *status, int code, int64_t *info, int64_t where) {
+    if (atomicCAS(status, 0, code) == 0) info[INFO_FAIL_BLOCK] = where;
+}

@@ -1,0 +1,424 @@
+// Right-preconditioned restarted GMRES(m) on the GPU (Saad and Schultz; the paper's
+// experiments use GMRES(30), Sec. 4).
+//
+// A x = b is solved as A M^{-1} u = b, x = x0 + M^{-1} V y.  Arnoldi uses modified
+// Gram-Schmidt; the small least-squares problem is reduced with Givens rotations on the
+// device.  One restart cycle (m Arnoldi steps, the update of x and the true residual) is
+// captured once into a CUDA graph; every kernel of a step returns immediately once the
+// cycle has converged, so the host synchronizes once per cycle.  All reductions use
+// per-CTA partial sums combined in a fixed order, so results are bitwise reproducible.
+#include <algorithm>
+#include <cmath>
+
+#include "dev_common.cuh"
+
+namespace {
+
+constexpr int VT = 256;   // threads per CTA of the vector kernels
+enum { GI_ITS = 0, GI_JDONE, GI_DONE, GI_MAXIT, GI_M, GI_COUNT = 8 };
+enum { GS_BNORM = 0, GS_BETA, GS_TOL, GS_REL, GS_RELEST, GS_COUNT = 8 };
+
+struct GmLayout {
+    int m;
+    int64_t H, g, cs, sn, y, scal, total;
+    explicit GmLayout(int m_) : m(m_) {
+        H = 0;
+        g = H + (int64_t)(m + 1) * m;
+        cs = g + m + 1;
+        sn = cs + m;
+        y = sn + m;
+        scal = y + m;
+        total = scal + GS_COUNT;
+    }
+};
+
+// sum of G partials in a fixed order, by warp 0; result broadcast through shared memory
+__device__ double sum_partials(const double *part, int G) {
+    __shared__ double s_res;
+    if (threadIdx.x < 32) {
+        double v = 0.0;
+        for (int i = threadIdx.x; i < G; i += 32) v += ldcg(part + i);
+        v = warp_sum(v);
+        if (threadIdx.x == 0) s_res = v;
+    }
+    __syncthreads();
+    const double r = s_res;
+    __syncthreads();
+    return r;
+}
+
+// block reduction of one value per thread, fixed order; thread 0 gets the result
+__device__ double block_sum(double v) {
+    __shared__ double ws[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) ws[warp] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (warp == 0) {
+        r = lane < (int)(blockDim.x >> 5) ? ws[lane] : 0.0;
+        r = warp_sum(r);
+    }
+    __syncthreads();
+    return r;
+}
+
+struct Chunk {
+    int64_t lo, hi;
+};
+__device__ __forceinline__ Chunk chunk_of(int64_t n) {
+    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+    Chunk c;
+    c.lo = min(n, per * (int64_t)blockIdx.x);
+    c.hi = min(n, c.lo + per);
+    return c;
+}
+
+__device__ __forceinline__ bool skipped(const int32_t *gi) { return ldcg(gi + GI_DONE) != 0; }
+
+// y = A x (rows split in contiguous chunks; VL lanes per row)
+template <int VL>
+__device__ __forceinline__ double row_dot(const int32_t *rowptr, const int32_t *colind, const double *val,
+                                          const double *x, int64_t i, int sub) {
+    double s = 0.0;
+    for (int e = rowptr[i] + sub; e < rowptr[i + 1]; e += VL) s = fma(val[e], ldcg(x + colind[e]), s);
+#pragma unroll
+    for (int o = VL / 2; o > 0; o >>= 1) s += __shfl_xor_sync(FULL_MASK, s, o, VL);
+    return s;
+}
+
+template <int VL>
+__global__ void __launch_bounds__(VT) spmv_kernel(int64_t n, const int32_t *rowptr, const int32_t *colind,
+                                                  const double *val, const double *x, double *y,
+                                                  const double *b, double *part, const int32_t *gi) {
+    if (gi && skipped(gi)) return;
+    const Chunk c = chunk_of(n);
+    const int sub = threadIdx.x % VL, grp = threadIdx.x / VL, ngrp = VT / VL;
+    double acc = 0.0;
+    for (int64_t i0 = c.lo; i0 < c.hi; i0 += ngrp) {
+        const int64_t i = i0 + grp;
+        const bool valid = i < c.hi;
+        const double s = row_dot<VL>(rowptr, colind, val, x, valid ? i : c.lo, sub);
+        if (valid && sub == 0) {
+            if (b) {  // residual r = b - A x and its squared norm
+                const double r = b[i] - s;
+                y[i] = r;
+                acc = fma(r, r, acc);
+            } else {
+                y[i] = s;
+            }
+        }
+    }
+    if (part) {
+        const double t = block_sum(acc);
+        if (threadIdx.x == 0) part[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(VT) dot_kernel(int64_t n, const double *x, const double *y, double *part) {
+    const Chunk c = chunk_of(n);
+    double acc = 0.0;
+    for (int64_t i = c.lo + threadIdx.x; i < c.hi; i += VT) acc = fma(ldcg(x + i), ldcg(y + i), acc);
+    const double t = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// MGS step i of Arnoldi column j: apply the previous coefficient, start the next dot.
+__global__ void __launch_bounds__(VT) mgs_kernel(int64_t n, int i, int j, int m, double *V, double *w,
+                                                 double *part, double *gm, const int32_t *gi, int G) {
+    if (skipped(gi)) return;
+    const Chunk c = chunk_of(n);
+    const double *partPrev = part + ((i - 1) & 1) * G;
+    double *partCur = part + (i & 1) * G;
+    double h = 0.0;
+    if (i > 0) {
+        h = sum_partials(partPrev, G);
+        if (blockIdx.x == 0 && threadIdx.x == 0) gm[(int64_t)(i - 1) * m + j] = h;
+    }
+    const double *vp = V + (int64_t)(i > 0 ? i - 1 : 0) * n, *vi = V + (int64_t)i * n;
+    double acc = 0.0;
+    for (int64_t e = c.lo + threadIdx.x; e < c.hi; e += VT) {
+        double we = w[e];
+        if (i > 0) we = fma(-h, vp[e], we);
+        w[e] = we;
+        acc = fma(we, vi[e], acc);
+    }
+    const double t = block_sum(acc);
+    if (threadIdx.x == 0) partCur[blockIdx.x] = t;
+}
+
+// last MGS step of column j: subtract h_jj v_j, start ||w||^2
+__global__ void __launch_bounds__(VT) mgs_last_kernel(int64_t n, int j, int m, double *V, double *w,
+                                                      double *part, double *gm, const int32_t *gi, int G) {
+    if (skipped(gi)) return;
+    const Chunk c = chunk_of(n);
+    const double h = sum_partials(part + (j & 1) * G, G);
+    if (blockIdx.x == 0 && threadIdx.x == 0) gm[(int64_t)j * m + j] = h;
+    const double *vj = V + (int64_t)j * n;
+    double acc = 0.0;
+    for (int64_t e = c.lo + threadIdx.x; e < c.hi; e += VT) {
+        const double we = fma(-h, vj[e], w[e]);
+        w[e] = we;
+        acc = fma(we, we, acc);
+    }
+    const double t = block_sum(acc);
+    if (threadIdx.x == 0) part[2 * G + blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(VT) normalize_kernel(int64_t n, int j, double *V, const double *w,
+                                                       const double *part, const int32_t *gi, int G) {
+    if (skipped(gi)) return;
+    const Chunk c = chunk_of(n);
+    const double hn = sqrt(sum_partials(part + 2 * G, G));
+    if (hn == 0.0) return;
+    double *vn = V + (int64_t)(j + 1) * n;
+    for (int64_t e = c.lo + threadIdx.x; e < c.hi; e += VT) vn[e] = w[e] / hn;
+}
+
+// Givens rotations on column j of H, update of g, convergence test (one warp).
+__global__ void givens_kernel(int j, int m, double *gm, int32_t *gi, const double *part, int G, int64_t soff,
+                              int64_t goff, int64_t csoff, int64_t snoff) {
+    if (skipped(gi)) return;
+    const double hn = sqrt(sum_partials(part + 2 * G, G));
+    if (threadIdx.x != 0) return;
+    double *H = gm, *g = gm + goff, *cs = gm + csoff, *sn = gm + snoff, *sc = gm + soff;
+    H[(int64_t)(j + 1) * m + j] = hn;
+    for (int i = 0; i < j; ++i) {
+        const double a = H[(int64_t)i * m + j], b2 = H[(int64_t)(i + 1) * m + j];
+        H[(int64_t)i * m + j] = cs[i] * a + sn[i] * b2;
+        H[(int64_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * b2;
+    }
+    const double a = H[(int64_t)j * m + j], b2 = H[(int64_t)(j + 1) * m + j];
+    const double den = hypot(a, b2);
+    cs[j] = den == 0.0 ? 1.0 : a / den;
+    sn[j] = den == 0.0 ? 0.0 : b2 / den;
+    H[(int64_t)j * m + j] = den;
+    H[(int64_t)(j + 1) * m + j] = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    gi[GI_ITS] += 1;
+    gi[GI_JDONE] = j + 1;
+    sc[GS_RELEST] = fabs(g[j + 1]) / sc[GS_BNORM];
+    if (fabs(g[j + 1]) <= sc[GS_TOL] * sc[GS_BNORM] || hn == 0.0 || gi[GI_ITS] >= gi[GI_MAXIT]) gi[GI_DONE] = 1;
+}
+
+// y = H(0:jd, 0:jd)^{-1} g (back substitution, one thread)
+__global__ void solve_y_kernel(int m, double *gm, const int32_t *gi, int64_t goff, int64_t yoff) {
+    if (threadIdx.x != 0) return;
+    const int jd = gi[GI_JDONE];
+    const double *H = gm, *g = gm + goff;
+    double *y = gm + yoff;
+    for (int i = jd - 1; i >= 0; --i) {
+        double s = g[i];
+        for (int k = i + 1; k < jd; ++k) s -= H[(int64_t)i * m + k] * y[k];
+        y[i] = s / H[(int64_t)i * m + i];
+    }
+}
+
+// u = V(:, 0:jd) y
+__global__ void __launch_bounds__(VT) combine_kernel(int64_t n, const double *V, const double *gm, const int32_t *gi,
+                                                     int64_t yoff, double *u) {
+    const Chunk c = chunk_of(n);
+    const int jd = ldcg(gi + GI_JDONE);
+    const double *y = gm + yoff;
+    for (int64_t e = c.lo + threadIdx.x; e < c.hi; e += VT) {
+        double s = 0.0;
+        for (int k = 0; k < jd; ++k) s = fma(ldcg(y + k), V[(int64_t)k * n + e], s);
+        u[e] = s;
+    }
+}
+
+__global__ void __launch_bounds__(VT) axpy_kernel(int64_t n, const double *z, double *x) {
+    const Chunk c = chunk_of(n);
+    for (int64_t e = c.lo + threadIdx.x; e < c.hi; e += VT) x[e] += z[e];
+}
+
+// beta = ||r||, relative true residual; mirror for the host
+__global__ void cycle_end_kernel(double *gm, int32_t *gi, const double *part, int G, int64_t soff,
+                                 double *h_scal, int32_t *h_gi) {
+    const double beta = sqrt(sum_partials(part + 3 * G, G));
+    if (threadIdx.x != 0) return;
+    double *sc = gm + soff;
+    sc[GS_BETA] = beta;
+    sc[GS_REL] = sc[GS_BNORM] > 0.0 ? beta / sc[GS_BNORM] : 0.0;
+    for (int k = 0; k < GS_COUNT; ++k) h_scal[k] = sc[k];
+    for (int k = 0; k < GI_COUNT; ++k) h_gi[k] = gi[k];
+}
+
+// start of a cycle: v_0 = r / beta, g = beta e_1
+__global__ void __launch_bounds__(VT) cycle_begin_kernel(int64_t n, int m, const double *r, double *V, double *gm,
+                                                         int32_t *gi, int64_t soff, int64_t goff) {
+    const double beta = ldcg(gm + soff + GS_BETA);
+    const Chunk c = chunk_of(n);
+    for (int64_t e = c.lo + threadIdx.x; e < c.hi; e += VT) V[e] = r[e] / beta;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        double *g = gm + goff;
+        for (int k = 0; k <= m; ++k) g[k] = 0.0;
+        g[0] = beta;
+        gi[GI_JDONE] = 0;
+        gi[GI_DONE] = gi[GI_ITS] >= gi[GI_MAXIT] ? 1 : 0;
+    }
+}
+
+__global__ void setup_kernel(double *gm, int32_t *gi, const double *part, int G, int64_t soff, double tol, int maxit,
+                             int m) {
+    const double bn = sqrt(sum_partials(part + 3 * G, G));
+    if (threadIdx.x != 0) return;
+    double *sc = gm + soff;
+    sc[GS_BNORM] = bn;
+    sc[GS_TOL] = tol;
+    gi[GI_ITS] = 0;
+    gi[GI_JDONE] = 0;
+    gi[GI_DONE] = 0;
+    gi[GI_MAXIT] = maxit;
+    gi[GI_M] = m;
+}
+
+}  // namespace
+
+void gmres_free(bilu_ctx *c) {
+    if (c->gm_graph) cudaGraphExecDestroy(c->gm_graph);
+    c->gm_graph = nullptr;
+    dev_free(c->d_V);
+    dev_free(c->d_w);
+    dev_free(c->d_z);
+    dev_free(c->d_r);
+    dev_free(c->d_u);
+    dev_free(c->d_part);
+    dev_free(c->d_gm);
+    dev_free(c->d_gmi);
+    dev_free(c->d_gb);
+    dev_free(c->d_gx);
+    if (c->h_gm_pinned) cudaFreeHost(c->h_gm_pinned);
+    if (c->h_gmi_pinned) cudaFreeHost(c->h_gmi_pinned);
+    c->h_gm_pinned = nullptr;
+    c->h_gmi_pinned = nullptr;
+    c->gm_restart = 0;
+}
+
+namespace {
+
+int vector_grid(const bilu_ctx *c) { return 2 * c->nsm; }
+
+void launch_spmv(bilu_ctx *c, const double *x, double *y, const double *b, double *part, const int32_t *gi) {
+    const int G = vector_grid(c);
+    const double avg = c->n > 0 ? (double)c->nnz / (double)c->n : 0.0;
+    if (avg <= 12) spmv_kernel<8><<<G, VT, 0, c->stream>>>(c->n, c->d_rowptr, c->d_colind, c->d_val, x, y, b, part, gi);
+    else if (avg <= 40) spmv_kernel<16><<<G, VT, 0, c->stream>>>(c->n, c->d_rowptr, c->d_colind, c->d_val, x, y, b, part, gi);
+    else spmv_kernel<32><<<G, VT, 0, c->stream>>>(c->n, c->d_rowptr, c->d_colind, c->d_val, x, y, b, part, gi);
+}
+
+bilu_status gmres_alloc(bilu_ctx *c, int m) {
+    gmres_free(c);
+    const int64_t n = std::max<int64_t>(c->n, 1);
+    GmLayout L(m);
+    if (dev_alloc(&c->d_V, (int64_t)(m + 1) * n) != cudaSuccess || dev_alloc(&c->d_w, n) != cudaSuccess ||
+        dev_alloc(&c->d_z, n) != cudaSuccess || dev_alloc(&c->d_r, n) != cudaSuccess ||
+        dev_alloc(&c->d_u, n) != cudaSuccess || dev_alloc(&c->d_part, 4 * vector_grid(c)) != cudaSuccess ||
+        dev_alloc(&c->d_gm, L.total) != cudaSuccess || dev_alloc(&c->d_gmi, GI_COUNT) != cudaSuccess ||
+        dev_alloc(&c->d_gb, n) != cudaSuccess || dev_alloc(&c->d_gx, n) != cudaSuccess ||
+        cudaMallocHost((void **)&c->h_gm_pinned, GS_COUNT * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost((void **)&c->h_gmi_pinned, GI_COUNT * sizeof(int32_t)) != cudaSuccess) {
+        gmres_free(c);
+        return set_err(c, BILU_ERR_OOM, "gmres allocation failed");
+    }
+    BILU_CUDA(c, cudaMemsetAsync(c->d_gm, 0, L.total * sizeof(double), c->stream));
+    c->gm_restart = m;
+    return BILU_OK;
+}
+
+// Records one restart cycle on the context stream (used under stream capture).
+bilu_status record_cycle(bilu_ctx *c, int m) {
+    const int G = vector_grid(c);
+    GmLayout L(m);
+    const int64_t n = c->n;
+    int32_t *gi = c->d_gmi;
+    cycle_begin_kernel<<<G, VT, 0, c->stream>>>(n, m, c->d_r, c->d_V, c->d_gm, gi, L.scal, L.g);
+    for (int j = 0; j < m; ++j) {
+        bilu_status st = apply_launch(c, c->d_V + (int64_t)j * n, c->d_z, gi + GI_DONE);
+        if (st != BILU_OK) return st;
+        launch_spmv(c, c->d_z, c->d_w, nullptr, nullptr, gi);
+        for (int i = 0; i <= j; ++i)
+            mgs_kernel<<<G, VT, 0, c->stream>>>(n, i, j, m, c->d_V, c->d_w, c->d_part, c->d_gm, gi, G);
+        mgs_last_kernel<<<G, VT, 0, c->stream>>>(n, j, m, c->d_V, c->d_w, c->d_part, c->d_gm, gi, G);
+        normalize_kernel<<<G, VT, 0, c->stream>>>(n, j, c->d_V, c->d_w, c->d_part, gi, G);
+        givens_kernel<<<1, 32, 0, c->stream>>>(j, m, c->d_gm, gi, c->d_part, G, L.scal, L.g, L.cs, L.sn);
+    }
+    solve_y_kernel<<<1, 32, 0, c->stream>>>(m, c->d_gm, gi, L.g, L.y);
+    combine_kernel<<<G, VT, 0, c->stream>>>(n, c->d_V, c->d_gm, gi, L.y, c->d_u);
+    bilu_status st = apply_launch(c, c->d_u, c->d_z, nullptr);
+    if (st != BILU_OK) return st;
+    axpy_kernel<<<G, VT, 0, c->stream>>>(n, c->d_z, c->d_gx);
+    launch_spmv(c, c->d_gx, c->d_r, c->d_gb, c->d_part + 3 * G, nullptr);
+    cycle_end_kernel<<<1, 32, 0, c->stream>>>(c->d_gm, gi, c->d_part, G, L.scal, c->h_gm_pinned, c->h_gmi_pinned);
+    BILU_CUDA(c, cudaGetLastError());
+    return BILU_OK;
+}
+
+}  // namespace
+
+bilu_status gmres_run(bilu_ctx *c, const double *b, double *x, double tol, int m, int maxit, gmres_info *info) {
+    if (m < 1 || m > 1000 || maxit < 0 || !(tol >= 0.0)) return set_err(c, BILU_ERR_ARG, "bad gmres arguments");
+    if (c->gm_restart != m) {
+        bilu_status st = gmres_alloc(c, m);
+        if (st != BILU_OK) return st;
+    }
+    const int G = vector_grid(c);
+    const int64_t n = c->n;
+    GmLayout L(m);
+    cudaEvent_t e0, e1;
+    BILU_CUDA(c, cudaEventCreate(&e0));
+    BILU_CUDA(c, cudaEventCreate(&e1));
+    BILU_CUDA(c, cudaEventRecord(e0, c->stream));
+    BILU_CUDA(c, cudaMemcpyAsync(c->d_gb, b, n * sizeof(double), cudaMemcpyDefault, c->stream));
+    BILU_CUDA(c, cudaMemcpyAsync(c->d_gx, x, n * sizeof(double), cudaMemcpyDefault, c->stream));
+    dot_kernel<<<G, VT, 0, c->stream>>>(n, c->d_gb, c->d_gb, c->d_part + 3 * G);
+    setup_kernel<<<1, 32, 0, c->stream>>>(c->d_gm, c->d_gmi, c->d_part, G, L.scal, tol, maxit, m);
+    launch_spmv(c, c->d_gx, c->d_r, c->d_gb, c->d_part + 3 * G, nullptr);
+    cycle_end_kernel<<<1, 32, 0, c->stream>>>(c->d_gm, c->d_gmi, c->d_part, G, L.scal, c->h_gm_pinned, c->h_gmi_pinned);
+    BILU_CUDA(c, cudaGetLastError());
+    BILU_CUDA(c, cudaStreamSynchronize(c->stream));
+    double bnorm = c->h_gm_pinned[GS_BNORM];
+    double rel = c->h_gm_pinned[GS_REL];
+    int restarts = 0;
+    if (bnorm == 0.0) {
+        BILU_CUDA(c, cudaMemsetAsync(c->d_gx, 0, n * sizeof(double), c->stream));
+        rel = 0.0;
+    } else {
+        if (!c->gm_graph) {
+            cudaGraph_t graph;
+            BILU_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+            bilu_status st = record_cycle(c, m);
+            cudaError_t ce = cudaStreamEndCapture(c->stream, &graph);
+            if (st != BILU_OK) return st;
+            if (ce != cudaSuccess) return cuda_err(c, ce, "cudaStreamEndCapture");
+            ce = cudaGraphInstantiate(&c->gm_graph, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ce != cudaSuccess) return cuda_err(c, ce, "cudaGraphInstantiate");
+        }
+        while (rel > tol && c->h_gmi_pinned[GI_ITS] < maxit) {
+            BILU_CUDA(c, cudaGraphLaunch(c->gm_graph, c->stream));
+            BILU_CUDA(c, cudaStreamSynchronize(c->stream));
+            rel = c->h_gm_pinned[GS_REL];
+            ++restarts;
+        }
+    }
+    BILU_CUDA(c, cudaMemcpyAsync(x, c->d_gx, n * sizeof(double), cudaMemcpyDefault, c->stream));
+    BILU_CUDA(c, cudaEventRecord(e1, c->stream));
+    BILU_CUDA(c, cudaStreamSynchronize(c->stream));
+    int32_t apst[4];
+    BILU_CUDA(c, cudaMemcpy(apst, c->d_apst, sizeof(apst), cudaMemcpyDeviceToHost));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (info) {
+        info->iters = bnorm == 0.0 ? 0 : c->h_gmi_pinned[GI_ITS];
+        info->restarts = restarts;
+        info->relres_true = rel;
+        info->relres_est = c->h_gm_pinned[GS_RELEST];
+        info->t_solve_ms = ms;
+    }
+    if (apst[3] != 0) return set_err(c, BILU_ERR_TIMEOUT, "apply kernel: bounded wait gave up");
+    return rel <= tol ? BILU_OK : BILU_NOT_CONVERGED;
+}

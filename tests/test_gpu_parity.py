@@ -1,0 +1,204 @@
+"""GPU parity of the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Bar: identical partitions and kept row / column sets, values of L, U-breve, D_K and P_K to
+relative 1e-10 per block (the FP64 tolerance the method's target states), identical
+GMRES(30) iteration counts to relative residual 1e-8.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1908_10169_gb300 as B
+from paper_1908_10169_gb300 import workloads as W
+from tests.gpu_helpers import compare_factors, gpu_factor
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = B.bilu_create(0)
+    yield c
+    B.bilu_destroy(c)
+
+
+def _fixed(b, mx=64):
+    return B.bilu_params_default(blocking=B.BILU_BLOCKING_FIXED, fixed_block=b, max_block=mx)
+
+
+def _oracle(A, bstart, tau):
+    return O.bilu_factor(A, bstart, tau)
+
+
+def test_partition_fixed_and_ilu1t_match_oracle(ctx):
+    A = W.convdiff_upwind((10, 10, 10), seed=3)
+    g = gpu_factor(ctx, A, 1e-2, _fixed(7), export=False)
+    assert np.array_equal(g.bstart, O.partition_fixed(A.n, 7))
+    p = B.bilu_params_default(blocking=B.BILU_BLOCKING_ILU1T, max_block=16, tau_analyze=1e-2)
+    g = gpu_factor(ctx, A, 1e-2, p, export=False)
+    assert np.array_equal(g.bstart, O.partition_ilu1t(A, 1e-2, 16))
+    Ad = np.eye(50) * 100.0
+    Ad[10:40, 0] = 1.0
+    Ad[14:44, 1] = 1.0
+    A2 = W.from_dense(Ad)
+    p = B.bilu_params_default(blocking=B.BILU_BLOCKING_ILU1T, max_block=64, tau_analyze=1e-3)
+    g = gpu_factor(ctx, A2, 1e-2, p, export=False)
+    assert np.array_equal(g.bstart, O.partition_ilu1t(A2, 1e-3, 64))
+
+
+@pytest.mark.parametrize("blk", [1, 4, 32])
+def test_factor_parity_cd2d(ctx, blk):
+    w = W.cd2d_32()
+    g = gpu_factor(ctx, w.A, 1e-2, _fixed(blk))
+    o = _oracle(w.A, g.bstart, 1e-2)
+    rep = compare_factors(o, g)
+    assert rep.blocks == len(g.bstart) - 1
+
+
+@pytest.mark.parametrize("seed,maxb,tau", [(0, 8, 1e-2), (1, 3, 1e-3), (2, 16, 5e-2), (3, 64, 0.0)])
+def test_factor_parity_random(ctx, seed, maxb, tau):
+    A = W.random_diag_dominant(300, 0.02, 50 + seed, dominance=1.1)
+    p = B.bilu_params_default(blocking=B.BILU_BLOCKING_ILU1T, max_block=maxb, tau_analyze=1e-2)
+    g = gpu_factor(ctx, A, tau, p)
+    o = _oracle(A, g.bstart, tau)
+    compare_factors(o, g)
+
+
+@pytest.mark.parametrize("side,blk", [(12, 12), (16, 16), (16, 64), (20, 40)])
+def test_factor_parity_cd3d(ctx, side, blk):
+    A = W.convdiff_upwind((side, side, side), seed=1)
+    g = gpu_factor(ctx, A, 1e-2, _fixed(blk))
+    o = _oracle(A, g.bstart, 1e-2)
+    compare_factors(o, g)
+
+
+def test_factor_is_deterministic(ctx):
+    A = W.convdiff_upwind((16, 16, 16), seed=5)
+    g1 = gpu_factor(ctx, A, 1e-2, _fixed(32))
+    g2 = gpu_factor(ctx, A, 1e-2, _fixed(32))
+    for f in ("Lrow", "Lval", "Ucol", "Uval", "Dinv", "Pblk"):
+        assert np.array_equal(getattr(g1, f), getattr(g2, f)), f
+
+
+def test_apply_parity(ctx):
+    import torch
+    A = W.convdiff_upwind((16, 16, 16), seed=2)
+    g = gpu_factor(ctx, A, 1e-2, _fixed(16))
+    o = _oracle(A, g.bstart, 1e-2)
+    rng = np.random.default_rng(0)
+    for _ in range(3):
+        r = rng.standard_normal(A.n)
+        zo = O.bilu_apply(o, r)
+        rt = torch.from_numpy(r).cuda()
+        zt = torch.empty_like(rt)
+        B.bilu_apply(ctx, rt, zt)
+        torch.cuda.synchronize()
+        zg = zt.cpu().numpy()
+        assert np.abs(zg - zo).max() <= 1e-11 * np.abs(zo).max()
+    # host vectors through the same entry point
+    zh = np.zeros(A.n)
+    B.bilu_apply(ctx, r, zh)
+    assert np.abs(zh - zo).max() <= 1e-11 * np.abs(zo).max()
+
+
+@pytest.mark.parametrize("case", ["cd2d", "cd3d16", "cd3d24"])
+def test_gmres_parity(ctx, case):
+    import torch
+    if case == "cd2d":
+        w = W.cd2d_32()
+        A, b, blk = w.A, w.b, 32
+    else:
+        side = 16 if case == "cd3d16" else 24
+        A = W.convdiff_upwind((side,) * 3, seed=1)
+        b, blk = W.rhs_ones(A), side
+    g = gpu_factor(ctx, A, 1e-2, _fixed(blk), export=False)
+    o = _oracle(A, g.bstart, 1e-2)
+    ro = O.gmres(A, o, b, tol=1e-8, restart=30)
+    bt = torch.from_numpy(b).cuda()
+    xt = torch.zeros_like(bt)
+    info = B.gmres_solve(ctx, bt, xt, 1e-8, 30, 10000)
+    assert info.status == B.BILU_OK
+    assert info.iters == ro.iters, (info.iters, ro.iters)
+    assert info.relres_true <= 1e-8
+    x = xt.cpu().numpy()
+    assert np.abs(x - ro.x).max() <= 1e-6 * np.abs(ro.x).max()
+    # host vectors
+    xh = np.zeros(A.n)
+    info2 = B.gmres_solve(ctx, b, xh, 1e-8, 30, 10000)
+    assert info2.iters == ro.iters and np.array_equal(xh, x)
+
+
+def test_singular_block_status(ctx):
+    Ad = np.array([[2.0, 0.0, 1.0], [1.0, 0.0, 5.0], [0.5, 1.0, 4.0]])
+    A = W.from_dense(Ad)
+    p = B.bilu_params_default(blocking=B.BILU_BLOCKING_FIXED, fixed_block=2, max_block=2)
+    g = gpu_factor(ctx, A, 0.0, p)
+    assert g.status == B.BILU_PERTURBED
+    o = O.bilu_factor(A, np.array([0, 2, 3], np.int32), 0.0)
+    compare_factors(o, g)
+    p.perturb = 0
+    with pytest.raises(B.BiluError) as e:
+        gpu_factor(ctx, A, 0.0, p)
+    assert e.value.status == B.BILU_ERR_SINGULAR
+    # [[1,1],[1,1]]: breakdown at pivot 2, perturbed at the diagonal
+    A2 = W.from_dense(np.array([[1.0, 1.0], [1.0, 1.0]]))
+    g2 = gpu_factor(ctx, A2, 0.0, B.bilu_params_default(fixed_block=2, max_block=2))
+    o2 = O.bilu_factor(A2, np.array([0, 2], np.int32), 0.0)
+    compare_factors(o2, g2)
+
+
+def test_bounded_wait_timeout_leaves_context_usable(ctx):
+    A = W.convdiff_upwind((8, 8, 8), seed=1)
+    B.bilu_debug_set(ctx, B.BILU_DEBUG_SPIN_LIMIT, 20000)
+    B.bilu_debug_set(ctx, B.BILU_DEBUG_EXTRA_CTA, 1)
+    try:
+        with pytest.raises(B.BiluError) as e:
+            gpu_factor(ctx, A, 1e-2, _fixed(8), export=False)
+        assert e.value.status == B.BILU_ERR_TIMEOUT
+    finally:
+        B.bilu_debug_set(ctx, B.BILU_DEBUG_EXTRA_CTA, 0)
+        B.bilu_debug_set(ctx, B.BILU_DEBUG_SPIN_LIMIT, 0)
+    g = gpu_factor(ctx, A, 1e-2, _fixed(8))
+    compare_factors(O.bilu_factor(A, g.bstart, 1e-2), g)
+
+
+def test_argument_and_state_errors(ctx):
+    c = B.bilu_create(0)
+    try:
+        with pytest.raises(B.BiluError) as e:
+            B.bilu_factor(c, 1e-2)
+        assert e.value.status == B.BILU_ERR_STATE
+        A = W.convdiff_upwind((4, 4, 4), seed=1)
+        bad = A.val.copy()
+        bad[3] = np.nan
+        with pytest.raises(B.BiluError) as e:
+            B.bilu_analyze(c, A.n, A.rowptr, A.colind, bad)
+        assert e.value.status == B.BILU_ERR_ARG
+        ci = A.colind.copy()
+        ci[1], ci[2] = ci[2], ci[1]
+        with pytest.raises(B.BiluError) as e:
+            B.bilu_analyze(c, A.n, A.rowptr, ci, A.val)
+        assert e.value.status == B.BILU_ERR_ARG
+        with pytest.raises(B.BiluError) as e:
+            B.bilu_analyze(c, A.n, A.rowptr, A.colind, A.val, B.bilu_params_default(fixed_block=65, max_block=65))
+        assert e.value.status == B.BILU_ERR_ARG
+        B.bilu_analyze(c, A.n, A.rowptr, A.colind, A.val)
+        with pytest.raises(B.BiluError) as e:
+            B.bilu_factor(c, -1.0)
+        assert e.value.status == B.BILU_ERR_ARG
+    finally:
+        B.bilu_destroy(c)
+
+
+def test_empty_matrix(ctx):
+    c = B.bilu_create(0)
+    try:
+        B.bilu_analyze(c, 0, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0))
+        assert B.bilu_factor(c, 1e-2) == B.BILU_OK
+        info = B.gmres_solve(c, np.zeros(0), np.zeros(0))
+        assert info.iters == 0
+    finally:
+        B.bilu_destroy(c)
