@@ -1,0 +1,364 @@
+#!/usr/bin/env python
+"""Benchmark: block ILU factorization + preconditioned GMRES(30) to relative residual 1e-8.
+
+Workload: 3D convection-diffusion, 7-point first-order upwind stencil on a 64^3 interior grid
+(n = 262,144, nnz = 1,810,432), diffusion coefficients log-uniform in [1e-3, 1e3] per node
+(seed 1), |v| = 100 along (1,1,1), Dirichlet boundaries eliminated, b = A * ones, drop
+tolerance 1e-2, diagonal blocks of 64 consecutive unknowns (one grid line), FP64.
+
+One step = bilu_factor + gmres_solve (x0 = 0) through the C ABI, with the matrix and b
+already resident on the GPU (bilu_analyze runs once, outside the timed region).  L2 is
+flushed (512 MB write) before every timed step.  The JSON line also reports the end-to-end
+time through the same API from pinned host buffers (analyze + factor + solve + copy of x),
+the roofline of the dominant kernel, and the FP64 CPU oracle on the host.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import platform
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BILU factor+GMRES seconds to rel. residual 1e-8"
+UNIT = "s"
+FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12  # 152 SMs x 4 FP64 flop/clk/SM x 2070 MHz (see DESIGN)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--side", type=int, default=64)
+    ap.add_argument("--block", type=int, default=64)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(side, block):
+    from paper_1908_10169_gb300 import workloads as W
+    return W.cd3d(side=side, seed=1, block=block)
+
+
+def config(args, w, extra=None):
+    c = {"workload": f"cd3d_7pt_upwind_{args.side}^3", "n": w.A.n, "nnz": w.A.nnz, "droptol": w.droptol,
+         "blocking": f"fixed {args.block}", "gmres": f"GMRES({w.restart}) rtol {w.gmres_tol}, x0 = 0, b = A*1",
+         "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{args.gpus}"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        try:
+            rows = [l.strip().split(",") for l in open(self.path) if l.strip()]
+        except Exception:
+            return out
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except Exception:
+                continue
+        if sm:
+            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        return out
+
+
+def oracle_step(w, bstart):
+    """One full step of the FP64 CPU oracle (single thread): factor + GMRES(30)."""
+    import oracle as O
+    t0 = time.perf_counter()
+    F = O.bilu_factor(w.A, bstart, w.droptol)
+    t1 = time.perf_counter()
+    r = O.gmres(w.A, F, w.b, tol=w.gmres_tol, restart=w.restart)
+    t2 = time.perf_counter()
+    F.free()
+    return t2 - t0, t1 - t0, t2 - t1, r.iters
+
+
+def cpu_desc():
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except Exception:
+        cores = os.cpu_count()
+    model = platform.processor() or platform.machine()
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return cores, model
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle as O
+    oracle_cores, model = cpu_desc()
+    w = workload(args.side, args.block)
+    bs = O.partition_fixed(w.A.n, args.block)
+    small = workload(16, 16)
+    for _ in range(args.warmup):  # warm-up on a small case of the same kind
+        oracle_step(small, O.partition_fixed(small.A.n, 16))
+    times, iters = [], 0
+    for _ in range(args.steps):
+        t, tf, tg, iters = oracle_step(w, bs)
+        times.append(t)
+    v = sum(times) / len(times)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config(args, w, {"gmres_iters": iters}),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"full step (oracle factor + GMRES) on the same matrix; host {model}, "
+                                       f"{oracle_cores} cores visible, 1 used"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    import paper_1908_10169_gb300 as B
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = workload(args.side, args.block)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = B.bilu_create(local, stream)
+    params = B.bilu_params_default(blocking=B.BILU_BLOCKING_FIXED, fixed_block=args.block, max_block=64)
+    rp = torch.from_numpy(w.A.rowptr.astype(np.int64)).to(dev)
+    ci = torch.from_numpy(w.A.colind.astype(np.int32)).to(dev)
+    va = torch.from_numpy(w.A.val).to(dev)
+    b = torch.from_numpy(w.b).to(dev)
+    x = torch.zeros_like(b)
+    torch.cuda.synchronize()
+    B.bilu_analyze(ctx, w.A.n, rp, ci, va, params)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def step():
+        B.bilu_factor(ctx, w.droptol)
+        with torch.cuda.stream(stream):
+            x.zero_()
+        return B.gmres_solve(ctx, b, x, w.gmres_tol, w.restart, 10000)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    s0 = B.bilu_stats(ctx)
+    launches0 = s0.kernel_launches
+    times, tf, ts, infos = [], [], [], []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(1)
+            stream.synchronize()
+            barrier()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = step()
+            e1.record(stream)
+            e1.synchronize()
+            torch.cuda.synchronize()
+            barrier()
+            times.append(e0.elapsed_time(e1))
+            st = B.bilu_stats(ctx)
+            tf.append(st.t_factor_ms)
+            ts.append(info.t_solve_ms)
+            infos.append((info.iters, info.restarts, info.relres_true))
+    st = B.bilu_stats(ctx)
+    launches = (st.kernel_launches - launches0) / args.steps
+    ms = sum(times) / len(times)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    iters, restarts, relres = infos[-1]
+
+    # live kernel timings for the roofline: the factor kernel (library events) and one apply
+    t_factor = statistics.median(tf)
+    r = torch.randn(w.A.n, dtype=torch.float64, device=dev)
+    z = torch.empty_like(r)
+    for _ in range(3):
+        B.bilu_apply(ctx, r, z)
+    napply = 20
+    with torch.cuda.stream(stream):
+        flush.fill_(2)
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(napply):
+        B.bilu_apply(ctx, r, z)
+    a1.record(stream)
+    a1.synchronize()
+    t_apply = a0.elapsed_time(a1) / napply
+    n = w.A.n
+    apply_bytes = 8 * (st.nnz_l + st.nnz_u + st.nnz_d) + 4 * (st.kept_rows + st.kept_cols) + 8 * 3 * n
+    factor_tf = st.flops_factor / (t_factor * 1e-3) / 1e12
+    apply_gbs = apply_bytes / (t_apply * 1e-3) / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    applies_per_step = iters + restarts  # one per Arnoldi step, one per cycle for x
+    share_factor = t_factor / ms
+    share_apply = applies_per_step * t_apply / ms
+    traffic = {}
+    try:
+        traffic = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
+    except Exception:
+        pass
+    roof_factor = {"kernel": "bilu_factor_kernel", "bound": "alu", "achieved": factor_tf,
+                   "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": factor_tf / FP64_PEAK_TFLOPS,
+                   "peak_source": "derived FP64 DFMA peak (152 SMs x 4 flop/clk x 2070 MHz)",
+                   "traffic": traffic.get("bilu_factor_kernel", {}).get("bytes_per_launch"),
+                   "flops_per_launch": st.flops_factor, "ms_per_launch": t_factor, "share_of_step": share_factor}
+    roof_apply = {"kernel": "apply_forward_kernel+apply_backward_kernel", "bound": "hbm", "achieved": apply_gbs,
+                  "peak": hbm_peak, "unit": "GB/s", "frac": apply_gbs / hbm_peak, "peak_source": hbm_src,
+                  "traffic": traffic.get("apply", {}).get("bytes_per_launch"),
+                  "bytes_per_launch": apply_bytes, "ms_per_launch": t_apply, "share_of_step": share_apply}
+    dominant, other = (roof_factor, roof_apply) if share_factor >= share_apply else (roof_apply, roof_factor)
+
+    # end to end through the public API from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        h_rp = torch.from_numpy(w.A.rowptr.astype(np.int64)).pin_memory()
+        h_ci = torch.from_numpy(w.A.colind.astype(np.int32)).pin_memory()
+        h_va = torch.from_numpy(w.A.val).pin_memory()
+        h_b = torch.from_numpy(w.b).pin_memory()
+        h_x = torch.zeros(n, dtype=torch.float64).pin_memory()
+        ctx2 = B.bilu_create(local, stream)
+        et = []
+        for k in range(min(args.steps, 3) + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            B.bilu_analyze(ctx2, n, h_rp, h_ci, h_va, params)
+            B.bilu_factor(ctx2, w.droptol)
+            h_x.zero_()
+            B.gmres_solve(ctx2, h_b, h_x, w.gmres_tol, w.restart, 10000)
+            torch.cuda.synchronize()
+            if k > 0:
+                et.append(time.perf_counter() - t0)
+        B.bilu_destroy(ctx2)
+        bi = 8 * (n + 1) + 4 * w.A.nnz + 8 * w.A.nnz + 8 * n
+        e2e = {"value": sum(et) / len(et), "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": 8 * n}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+        cores, model = cpu_desc()
+        t, tfo, tgo, it_o = oracle_step(w, O.partition_fixed(n, args.block))
+        cpu = {"value": t, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one full step (oracle factor {tfo:.1f} s + GMRES {tgo:.1f} s, {it_o} iters) on the "
+                         f"same matrix; host {model}, {cores} cores visible, 1 used",
+               "gmres_iters": it_o}
+    B.bilu_destroy(ctx)
+    if rank == 0:
+        line = {"metric": METRIC, "value": ms / 1e3 / world, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": config(args, w, {"gmres_iters": iters, "gmres_restarts": restarts,
+                                           "relres_true": relres, "factor_ms": t_factor,
+                                           "solve_ms": statistics.median(ts), "apply_ms": t_apply,
+                                           "fill_nnz(L+U+D)/nnz(A)": (st.nnz_l + st.nnz_u + st.nnz_d) / w.A.nnz,
+                                           "nblocks": st.nblocks,
+                                           "factor_phase_ms": dict(zip(["candidates", "updates", "pivot_lu", "inverse",
+                                                                        "scale_drop", "compact", "cta0_inverse_work",
+                                                                        "cta0_update_work"],
+                                                                       [round(v, 3) for v in st.phase_ms]))}),
+                "roofline": dominant, "roofline_other": other,
+                "gpu_launches": launches, "clocks": clk.summary(), "e2e": e2e, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

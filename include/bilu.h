@@ -85,9 +85,21 @@ typedef struct {
     int64_t kept_rows, kept_cols;   /* kept scalar rows of L / columns of U            */
     int64_t cand_rows, cand_cols;   /* candidate rows / columns before dropping        */
     int64_t nperturb;         /* perturbed entries (Sec. 3.6)                          */
-    double flops_factor;      /* algorithmic flops of the last factorization           */
+    double flops_factor;      /* algorithmic flops of the last factorization: the sum of
+                                 the four counts below plus 2 b_K^3 per block (getrf 2/3,
+                                 inverse 4/3)                                           */
+    int64_t flop_upd_l;       /* 2 m n b_J summed over the L-side block updates        */
+    int64_t flop_upd_u;       /* 2 m n b_J summed over the U-side block updates        */
+    int64_t flop_scale;       /* 2 b_K^2 per candidate row and column (D_K products)   */
+    int64_t flop_norm;        /* 2 b_K per candidate row and column (drop norms)       */
     double t_analyze_ms, t_factor_ms;
     int32_t pool_retries;     /* factor re-runs after growing the L/U pools             */
+    int64_t kernel_launches;  /* kernels of this library launched on the context so far
+                                 (each node of a launched CUDA graph counts once)       */
+    double phase_ms[8];       /* factorization time by phase (candidate sets, updates,
+                                 pivot LU, inverse, scaling + dropping, compaction; each
+                                 up to the end of its grid barrier), then the time CTA 0
+                                 spends inside the inverse and the update work          */
 } bilu_stats_t;
 
 /* Fills *p with the defaults: FIXED blocking of 32 (max 64), tau_analyze 1e-2,
@@ -168,8 +180,11 @@ const char *bilu_last_error(const bilu_ctx *ctx);
  *       BILU_ERR_TIMEOUT with the GPU still usable.
  *   BILU_DEBUG_SPIN_LIMIT (value > 0): polls of one barrier wait before it gives up
  *       (0 restores the default).
+ *   BILU_DEBUG_SELFTEST_RECIP (value = sample count): checks the kernels' Newton-Raphson
+ *       reciprocal against the IEEE quotient 1/p on that many values over 200 binades;
+ *       BILU_OK when every result is within one ulp.
  */
-enum { BILU_DEBUG_EXTRA_CTA = 1, BILU_DEBUG_SPIN_LIMIT = 2 };
+enum { BILU_DEBUG_EXTRA_CTA = 1, BILU_DEBUG_SPIN_LIMIT = 2, BILU_DEBUG_SELFTEST_RECIP = 3 };
 bilu_status bilu_debug_set(bilu_ctx *ctx, int32_t what, int64_t value);
 
 /* Releases the context and all device memory it owns.  NULL is ignored. */

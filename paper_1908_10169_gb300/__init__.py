@@ -21,7 +21,7 @@ BILU_ERR_ARG, BILU_ERR_OOM, BILU_ERR_CUDA, BILU_ERR_SINGULAR, BILU_ERR_TIMEOUT, 
 BILU_BLOCKING_FIXED, BILU_BLOCKING_ILU1T = 0, 1
 BILU_PREC_FP64, BILU_PREC_FP32, BILU_PREC_BF16 = 0, 1, 2
 BILU_SKIP_NONE, BILU_SKIP_BOUND, BILU_SKIP_LEARNED = 0, 1, 2
-BILU_DEBUG_EXTRA_CTA, BILU_DEBUG_SPIN_LIMIT = 1, 2
+BILU_DEBUG_EXTRA_CTA, BILU_DEBUG_SPIN_LIMIT, BILU_DEBUG_SELFTEST_RECIP = 1, 2, 3
 BILU_MAX_BLOCK = 64
 
 # every extern "C" symbol that include/bilu.h declares
@@ -46,8 +46,11 @@ class bilu_stats_t(ct.Structure):
                 ("avg_bsize", ct.c_double), ("std_bsize", ct.c_double), ("nnz_l", ct.c_int64),
                 ("nnz_u", ct.c_int64), ("nnz_d", ct.c_int64), ("kept_rows", ct.c_int64),
                 ("kept_cols", ct.c_int64), ("cand_rows", ct.c_int64), ("cand_cols", ct.c_int64),
-                ("nperturb", ct.c_int64), ("flops_factor", ct.c_double), ("t_analyze_ms", ct.c_double),
-                ("t_factor_ms", ct.c_double), ("pool_retries", ct.c_int32)]
+                ("nperturb", ct.c_int64), ("flops_factor", ct.c_double), ("flop_upd_l", ct.c_int64),
+                ("flop_upd_u", ct.c_int64), ("flop_scale", ct.c_int64), ("flop_norm", ct.c_int64),
+                ("t_analyze_ms", ct.c_double),
+                ("t_factor_ms", ct.c_double), ("pool_retries", ct.c_int32),
+                ("kernel_launches", ct.c_int64), ("phase_ms", ct.c_double * 8)]
 
 
 class BiluError(RuntimeError):

@@ -13,7 +13,7 @@
 
 namespace {
 
-constexpr int AT = 256;        // threads per CTA
+constexpr int AT = 512;        // threads per CTA
 constexpr int AW = AT / 32;
 constexpr long long APPLY_SPIN = 1LL << 22;
 
@@ -54,10 +54,18 @@ __global__ void __launch_bounds__(32) apply_begin_kernel(int32_t *st, const int3
     }
 }
 
+// Forward sweep, block K: the producers' metadata is loaded and their flags are awaited in
+// parallel; every (producer, row) dot product is computed concurrently into dmat[t][r], and
+// the rows are then summed over the producers in increasing J (fixed order).
+constexpr int FCH = 32;  // producers per chunk
+
 __global__ void __launch_bounds__(AT) apply_forward_kernel(ApplyArgs a) {
     if (a.skip && ldcg(a.skip)) return;
     __shared__ double acc[BILU_MAX_BLOCK];
-    __shared__ int s_K, s_ok;
+    __shared__ double dmat[FCH][BILU_MAX_BLOCK];
+    __shared__ int sps[FCH], soff[FCH + 1], sbJ[FCH], ssJ[FCH];
+    __shared__ int64_t sLv[FCH];
+    __shared__ int s_K;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int epoch = ldcg(a.st);
     while (true) {
@@ -69,31 +77,60 @@ __global__ void __launch_bounds__(AT) apply_forward_kernel(ApplyArgs a) {
         const int s0 = a.bstart[K], b = a.bstart[K + 1] - s0;
         if (tid < b) acc[tid] = a.r[s0 + tid];
         const int pc = ldcg(a.prodUcnt + K);
-        // wait for all producers (their y blocks)
-        if (tid == 0) {
+        for (int c0 = 0; c0 < pc; c0 += FCH) {
+            const int cn = min(FCH, pc - c0);
             int ok = 1;
-            for (int t = 0; t < pc && ok; ++t) {
-                const int J = ldcg(a.prodU + (int64_t)K * a.prodcap + t);
-                ok = wait_flag(a.flagF + J, epoch, a.st + 3);
+            if (tid < cn) {
+                const int J = ldcg(a.prodU + (int64_t)K * a.prodcap + c0 + tid);
+                const int2 rg = a.planF[(int64_t)K * a.prodcap + c0 + tid];
+                sps[tid] = rg.x;
+                soff[tid + 1] = rg.y - rg.x;
+                const int sj = a.bstart[J];
+                ssJ[tid] = sj;
+                sbJ[tid] = a.bstart[J + 1] - sj;
+                sLv[tid] = a.Lvptr[J] + (int64_t)(rg.x - a.Lptr[J]) * (a.bstart[J + 1] - sj);
+                ok = wait_flag(a.flagF + J, epoch, a.st + 3) ? 1 : 0;
             }
-            s_ok = ok;
-        }
-        __syncthreads();
-        if (!s_ok) return;
-        for (int t = 0; t < pc; ++t) {
-            const int J = ldcg(a.prodU + (int64_t)K * a.prodcap + t);
-            const int2 rg = a.planF[(int64_t)K * a.prodcap + t];
-            const int sJ = a.bstart[J], bJ = a.bstart[J + 1] - sJ;
-            const double yJ0 = lane < bJ ? ldcg(a.z + sJ + lane) : 0.0;
-            const double yJ1 = lane + 32 < bJ ? ldcg(a.z + sJ + lane + 32) : 0.0;
-            const double *Lv = a.Lval + a.Lvptr[J] + (int64_t)(rg.x - a.Lptr[J]) * bJ;
-            for (int p = rg.x + warp; p < rg.y; p += AW) {
-                const double *row = Lv + (int64_t)(p - rg.x) * bJ;
-                double s = 0.0;
-                if (lane < bJ) s = row[lane] * yJ0;
-                if (lane + 32 < bJ) s = fma(row[lane + 32], yJ1, s);
-                s = warp_sum(s);
-                if (lane == 0) acc[a.Lrow[p] - s0] -= s;
+            if (!__syncthreads_and(ok)) return;
+            if (tid == 0) {
+                soff[0] = 0;
+                for (int t = 0; t < cn; ++t) soff[t + 1] += soff[t];
+            }
+            for (int e = tid; e < cn * BILU_MAX_BLOCK; e += AT) (&dmat[0][0])[e] = 0.0;
+            __syncthreads();
+            const int nrows = soff[cn];
+            // four rows per warp and iteration: their loads are in flight together
+            for (int it0 = warp * 4; it0 < nrows; it0 += AW * 4) {
+                double v[4];
+                int tt[4], pp[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int it = it0 + u;
+                    v[u] = 0.0;
+                    tt[u] = -1;
+                    if (it < nrows) {
+                        int t = 0;
+                        while (soff[t + 1] <= it) ++t;
+                        const int bJ = sbJ[t];
+                        const double *row = a.Lval + sLv[t] + (int64_t)(it - soff[t]) * bJ;
+                        const double *yJ = a.z + ssJ[t];
+                        if (lane < bJ) v[u] = row[lane] * ldcg(yJ + lane);
+                        if (lane + 32 < bJ) v[u] = fma(row[lane + 32], ldcg(yJ + lane + 32), v[u]);
+                        tt[u] = t;
+                        pp[u] = sps[t] + (it - soff[t]);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const double w = warp_sum(v[u]);
+                    if (lane == 0 && tt[u] >= 0) dmat[tt[u]][a.Lrow[pp[u]] - s0] = w;
+                }
+            }
+            __syncthreads();
+            if (tid < b) {
+                double s = acc[tid];
+                for (int t = 0; t < cn; ++t) s -= dmat[t][tid];
+                acc[tid] = s;
             }
             __syncthreads();
         }
@@ -147,7 +184,21 @@ __global__ void __launch_bounds__(AT) apply_backward_kernel(ApplyArgs a) {
         double s = 0.0;
         if (rr < b) {
             const double *Uv = a.Uval + a.Uvptr[K];
-            for (int64_t q = q0 + g; q < q1; q += NG) s = fma(Uv[(q - q0) * b + rr], ldcg(a.z + a.Ucol[q]), s);
+            int64_t q = q0 + g;
+            // four independent columns per iteration keep several loads in flight
+            double s1 = 0.0, s2 = 0.0, s3 = 0.0;
+            for (; q + 3 * NG < q1; q += 4 * NG) {
+                const double u0 = Uv[(q - q0) * b + rr], u1 = Uv[(q + NG - q0) * b + rr];
+                const double u2 = Uv[(q + 2 * NG - q0) * b + rr], u3 = Uv[(q + 3 * NG - q0) * b + rr];
+                const double z0 = ldcg(a.z + a.Ucol[q]), z1 = ldcg(a.z + a.Ucol[q + NG]);
+                const double z2 = ldcg(a.z + a.Ucol[q + 2 * NG]), z3 = ldcg(a.z + a.Ucol[q + 3 * NG]);
+                s = fma(u0, z0, s);
+                s1 = fma(u1, z1, s1);
+                s2 = fma(u2, z2, s2);
+                s3 = fma(u3, z3, s3);
+            }
+            for (; q < q1; q += NG) s = fma(Uv[(q - q0) * b + rr], ldcg(a.z + a.Ucol[q]), s);
+            s = (s + s1) + (s2 + s3);
         }
         part[g][rr] = s;
         __syncthreads();
@@ -160,12 +211,22 @@ __global__ void __launch_bounds__(AT) apply_backward_kernel(ApplyArgs a) {
         // z_K = D_K t: warp per row
         const double *D = a.Dinv + a.Dptr[K];
         const double t0 = lane < b ? tv[lane] : 0.0, t1 = lane + 32 < b ? tv[lane + 32] : 0.0;
-        for (int r = warp; r < b; r += AW) {
-            double v = 0.0;
-            if (lane < b) v = D[(int64_t)r * b + lane] * t0;
-            if (lane + 32 < b) v = fma(D[(int64_t)r * b + lane + 32], t1, v);
-            v = warp_sum(v);
-            if (lane == 0) a.z[s0 + r] = v;
+        for (int r0 = warp * 4; r0 < b; r0 += AW * 4) {
+            double v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int r = r0 + u;
+                v[u] = 0.0;
+                if (r < b) {
+                    if (lane < b) v[u] = D[(int64_t)r * b + lane] * t0;
+                    if (lane + 32 < b) v[u] = fma(D[(int64_t)r * b + lane + 32], t1, v[u]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const double w = warp_sum(v[u]);
+                if (lane == 0 && r0 + u < b) a.z[s0 + r0 + u] = w;
+            }
         }
         __syncthreads();
         if (tid == 0) {
@@ -218,9 +279,11 @@ bilu_status apply_alloc(bilu_ctx *c) {
     const int64_t warps = nb * c->prodcap;
     const int threads = 256;
     const int64_t blocks = std::min<int64_t>((warps * 32 + threads - 1) / threads, 65535);
-    if (c->nb > 0)
+    if (c->nb > 0) {
         apply_plan_kernel<<<(unsigned)blocks, threads, 0, c->stream>>>(c->nb, c->prodcap, c->d_bstart, c->d_Lptr, c->d_Lrow,
                                                                      c->d_prodU, c->d_prodUcnt, c->d_planF);
+        c->launches += 1;
+    }
     BILU_CUDA(c, cudaGetLastError());
     return BILU_OK;
 }
@@ -240,10 +303,11 @@ bilu_status apply_launch(bilu_ctx *c, const double *d_r, double *d_z, const int3
     a.flagB = c->d_flagB;
     a.st = c->d_apst;
     a.skip = skip;
-    const int G = c->nsm * 4;
+    const int G = c->nsm * 2;
     apply_begin_kernel<<<1, 32, 0, c->stream>>>(c->d_apst, skip);
     apply_forward_kernel<<<G, AT, 0, c->stream>>>(a);
     apply_backward_kernel<<<G, AT, 0, c->stream>>>(a);
+    c->launches += 3;
     BILU_CUDA(c, cudaGetLastError());
     return BILU_OK;
 }

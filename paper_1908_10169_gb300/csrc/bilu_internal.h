@@ -27,7 +27,14 @@ enum {
     INFO_CAND_COLS = 3,
     INFO_MAX_PROD = 4,       // longest producer list seen
     INFO_TIMEOUT_SITE = 5,   // which wait timed out
-    INFO_COUNT = 16
+    INFO_FLOP_UPD_L = 6,     // 2 m n b_J over the L-side updates
+    INFO_FLOP_UPD_U = 7,     // 2 m n b_J over the U-side updates
+    INFO_FLOP_SCALE = 8,     // 2 b_K^2 per candidate row / column
+    INFO_FLOP_NORM = 9,      // 2 b_K per candidate row / column
+    INFO_PHASE_NS = 10,      // 6 slots: time of the phases A, B, C, C2, D, E (CTA 0)
+    INFO_C2_WORK_NS = 16,    // time CTA 0 spends inside phase C2 (excluding the barrier)
+    INFO_B_WORK_NS = 17,     // time CTA 0 spends inside phase B tiles
+    INFO_COUNT = 24
 };
 
 struct bilu_ctx {
@@ -107,7 +114,11 @@ struct bilu_ctx {
     int64_t kept_rows = 0, kept_cols = 0, nnz_l = 0, nnz_u = 0, cand_rows = 0, cand_cols = 0;
     int64_t nperturb = 0;
     int32_t pool_retries = 0;
+    int64_t launches = 0;          // kernels of this library launched on the context (graph nodes included)
+    int64_t gm_graph_kernels = 0;  // kernel nodes of the captured GMRES cycle
     double flops_factor = 0.0, t_analyze_ms = 0.0, t_factor_ms = 0.0;
+    int64_t flop_upd_l = 0, flop_upd_u = 0, flop_scale = 0, flop_norm = 0;
+    double phase_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 };
 
 // helpers shared by the translation units of the library

@@ -7,6 +7,7 @@
 
 extern int g_debug_extra_cta;
 extern long long g_debug_spin_limit;
+int recip_selftest(int n);
 
 bilu_status set_err(bilu_ctx *c, bilu_status st, const std::string &msg) {
     if (c) c->err = msg;
@@ -174,6 +175,7 @@ bilu_status bilu_stats(bilu_ctx *c, bilu_stats_t *o) {
     o->std_bsize = c->nb ? std::sqrt(std::max(0.0, s2 / c->nb - o->avg_bsize * o->avg_bsize)) : 0.0;
     o->nnz_d = c->h_Dptr.empty() ? 0 : c->h_Dptr.back();
     o->t_analyze_ms = c->t_analyze_ms;
+    o->kernel_launches = c->launches;
     if (c->state >= 2) {
         o->nnz_l = c->nnz_l;
         o->nnz_u = c->nnz_u;
@@ -185,6 +187,11 @@ bilu_status bilu_stats(bilu_ctx *c, bilu_stats_t *o) {
         o->t_factor_ms = c->t_factor_ms;
         o->pool_retries = c->pool_retries;
         o->flops_factor = c->flops_factor;
+        o->flop_upd_l = c->flop_upd_l;
+        o->flop_upd_u = c->flop_upd_u;
+        o->flop_scale = c->flop_scale;
+        o->flop_norm = c->flop_norm;
+        for (int k = 0; k < 8; ++k) o->phase_ms[k] = c->phase_ms[k];
     }
     return BILU_OK;
 }
@@ -222,6 +229,12 @@ bilu_status bilu_debug_set(bilu_ctx *c, int32_t what, int64_t value) {
     switch (what) {
         case BILU_DEBUG_EXTRA_CTA: g_debug_extra_cta = value ? 1 : 0; return BILU_OK;
         case BILU_DEBUG_SPIN_LIMIT: g_debug_spin_limit = value; return BILU_OK;
+        case BILU_DEBUG_SELFTEST_RECIP: {
+            cudaSetDevice(c->device);
+            const int bad = recip_selftest((int)value);
+            if (bad == 0) return BILU_OK;
+            return set_err(c, BILU_ERR_CUDA, "reciprocal self-test: " + std::to_string(bad) + " results off by more than one ulp");
+        }
         default: return set_err(c, BILU_ERR_ARG, "unknown debug setting");
     }
 }

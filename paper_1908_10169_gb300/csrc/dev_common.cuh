@@ -100,6 +100,15 @@ __device__ __forceinline__ int warp_lower_bound(const int32_t *a, int lo, int hi
 // bar[1] is the generation.  A wait that exceeds spin_limit polls records DEV_TIMEOUT.
 // Returns false (uniformly in the CTA) when the device status word holds an error,
 // in which case the caller returns.
+__device__ __forceinline__ uint32_t atom_add_release_u32(uint32_t *p, uint32_t v) {
+    uint32_t old;
+    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ void red_add_release_u32(uint32_t *p, uint32_t v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ bool grid_barrier(uint32_t *bar, uint32_t G, int32_t *status,
                                              long long spin_limit, int64_t *info, int site) {
     __shared__ int s_ok;
@@ -107,12 +116,11 @@ __device__ __forceinline__ bool grid_barrier(uint32_t *bar, uint32_t G, int32_t 
     if (threadIdx.x == 0) {
         int ok = 1;
         const uint32_t gen = ld_acquire_u32(bar + 1);
-        __threadfence();
-        const uint32_t arrived = atomicAdd(bar, 1u);
+        // release: this CTA's writes (ordered before by __syncthreads) become visible first
+        const uint32_t arrived = atom_add_release_u32(bar, 1u);
         if (arrived == G - 1) {
             atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
+            red_add_release_u32(bar + 1, 1u);
         } else {
             long long it = 0;
             while (ld_acquire_u32(bar + 1) == gen) {
@@ -121,15 +129,33 @@ __device__ __forceinline__ bool grid_barrier(uint32_t *bar, uint32_t G, int32_t 
                     ok = 0;
                     break;
                 }
-                __nanosleep(64);
+                if (it > 64) __nanosleep(32);
             }
         }
-        __threadfence();
         if (ld_acquire_s32(status) != DEV_OK) ok = 0;
         s_ok = ok;
     }
     __syncthreads();
     return s_ok != 0;
+}
+
+// 1/p by Newton-Raphson iteration on f(x) = 1/x - p (x <- x + x (1 - p x), each step about
+// doubles the number of correct bits), started from the single-precision reciprocal of the
+// mantissa; the exponent is handled exactly by bit manipulation.  Within about one ulp of
+// the IEEE quotient; four dependent FP64 FMAs instead of a full division (a divide has a
+// ~650-cycle latency on this GPU).  Values far from 1 in magnitude (including 0, inf, NaN)
+// use the IEEE division.
+__device__ __forceinline__ double recip_nr(double p) {
+    const long long bits = __double_as_longlong(p);
+    const int ex = (int)((bits >> 52) & 0x7ff);
+    if (ex < 64 || ex > 1982) return 1.0 / p;
+    const double m = __longlong_as_double((bits & ~(0x7ffLL << 52)) | (1023LL << 52));  // |m| in [1, 2)
+    double x = (double)__frcp_rn((float)m);
+    double e = fma(-m, x, 1.0);
+    x = fma(x, e, x);
+    e = fma(-m, x, 1.0);
+    x = fma(x, e, x);
+    return x * __longlong_as_double((long long)(2046 - ex) << 52);  // times 2^(1023 - ex)
 }
 
 __device__ __forceinline__ void set_status(int32_t *status, int code, int64_t *info, int64_t where) {

@@ -29,7 +29,7 @@ constexpr int NW = NT / 32;      // warps per CTA
 constexpr int TRMAX = 32;        // max candidate slots per accumulation tile
 constexpr int PS = BILU_MAX_BLOCK + 1;  // padded row stride (doubles) of staged panels
 constexpr int PMAX = 1024;       // max producers per block handled by the kernel
-constexpr int SMEM_BYTES = 80 * 1024;
+constexpr int SMEM_BYTES = 112 * 1024;
 
 struct FactorArgs {
     int32_t n, nb, G, perturb;
@@ -71,13 +71,26 @@ __device__ __forceinline__ double perturbed(double d, double ptau, double prho, 
 
 // ---------------------------------------------------------------- phase A
 // Candidate set and update plan of one side (L: rows of the block column, U: columns of
-// the block row) of block K; executed by one whole CTA.
+// the block row) of block K; executed by one whole CTA.  All loops over the producers'
+// entries are flat (one pass over every entry of every producer) so that the global
+// loads are issued together instead of one producer after another.
+__device__ __forceinline__ int find_owner(const int32_t *off, int pcnt, int f) {
+    // largest t with off[t] <= f (off is the exclusive prefix of the producers' counts)
+    int lo = 0, hi = pcnt - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= f) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 __device__ void phase_A(const FactorArgs &a, int K, bool Lside, char *smem) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int s0 = a.bstart[K], s1 = a.bstart[K + 1], b = s1 - s0;
     int32_t *xcnt = (int32_t *)smem;            // PMAX
     int32_t *off = xcnt + PMAX;                  // PMAX + 1
-    int32_t *ws = off + PMAX + 1;                // 33
+    int32_t *xposs = off + PMAX + 1;             // PMAX
+    int32_t *ws = xposs + PMAX;                  // 40
     int32_t *lohi = ws + 40;                     // 2
 
     const int32_t *plist = (Lside ? a.prodL : a.prodU) + (int64_t)K * a.prodcap;
@@ -99,6 +112,7 @@ __device__ void phase_A(const FactorArgs &a, int K, bool Lside, char *smem) {
         const int bJ = a.bstart[J + 1] - a.bstart[J];
         const int l0 = (int)ldcg(a.Lptr + J), l1 = (int)ldcg(a.Lptr + J + 1);
         const int u0 = (int)ldcg(a.Uptr + J), u1 = (int)ldcg(a.Uptr + J + 1);
+        const int64_t lv = ldcg(a.Lvptr + J), uv = ldcg(a.Uvptr + J);
         int xbeg, xend, ybeg, yend;
         int64_t xval, yval;
         if (Lside) {  // X: L_J rows >= s0, Y: U-breve_J columns in [s0, s1)
@@ -106,15 +120,15 @@ __device__ void phase_A(const FactorArgs &a, int K, bool Lside, char *smem) {
             xend = l1;
             ybeg = warp_lower_bound(a.Ucol, u0, u1, s0);
             yend = warp_lower_bound(a.Ucol, ybeg, u1, s1);
-            xval = ldcg(a.Lvptr + J) + (int64_t)(xbeg - l0) * bJ;
-            yval = ldcg(a.Uvptr + J) + (int64_t)(ybeg - u0) * bJ;
+            xval = lv + (int64_t)(xbeg - l0) * bJ;
+            yval = uv + (int64_t)(ybeg - u0) * bJ;
         } else {      // X: U-breve_J columns >= s1, Y: L_J rows in [s0, s1)
             xbeg = warp_lower_bound(a.Ucol, u0, u1, s1);
             xend = u1;
             ybeg = warp_lower_bound(a.Lrow, l0, l1, s0);
             yend = warp_lower_bound(a.Lrow, ybeg, l1, s1);
-            xval = ldcg(a.Uvptr + J) + (int64_t)(xbeg - u0) * bJ;
-            yval = ldcg(a.Lvptr + J) + (int64_t)(ybeg - l0) * bJ;
+            xval = uv + (int64_t)(xbeg - u0) * bJ;
+            yval = lv + (int64_t)(ybeg - l0) * bJ;
         }
         if (lane == 0) {
             int64_t *pi = pinfo + PIS * t;
@@ -127,49 +141,51 @@ __device__ void phase_A(const FactorArgs &a, int K, bool Lside, char *smem) {
             pi[PI_YVAL] = yval;
             pi[PI_YPOS] = ybeg;
             xcnt[t] = xend - xbeg;
+            xposs[t] = xbeg;
         }
     }
     __syncthreads();
-    if (tid == 0) {
-        int acc = 0;
-        for (int t = 0; t < pcnt; ++t) { off[t] = acc; acc += xcnt[t]; }
-        off[pcnt] = acc;
+    // exclusive prefix of the producers' X counts
+    {
+        int carry = 0;
+        for (int c0 = 0; c0 < pcnt; c0 += NT) {
+            const int t = c0 + tid;
+            int tot;
+            const int ex = block_excl_scan(t < pcnt ? xcnt[t] : 0, ws, &tot);
+            if (t < pcnt) off[t] = carry + ex;
+            carry += tot;
+        }
+        if (tid == 0) off[pcnt] = carry;
+        __syncthreads();
     }
-    __syncthreads();
-    if ((int64_t)off[pcnt] > a.capXS) {
+    const int total = off[pcnt];
+    if ((int64_t)total > a.capXS) {
         if (tid == 0) set_status(a.status, DEV_PROD_OVERFLOW, a.info, K);
         return;
     }
     for (int t = tid; t < pcnt; t += NT) pinfo[PIS * t + PI_OFF] = off[t];
 
-    // mark candidates >= s1 in the bitmap
+    // mark candidates >= s1 in the bitmap: entries of A, then every producer X entry
     int lo = INT32_MAX, hi = -1;
-    if (Lside) {
-        const int e0 = a.colptr[s0], e1 = a.colptr[s1];
+    {
+        const int e0 = Lside ? a.colptr[s0] : a.rowptr[s0];
+        const int e1 = Lside ? a.colptr[s1] : a.rowptr[s1];
+        const int32_t *ind = Lside ? a.rowind : a.colind;
         for (int e = e0 + tid; e < e1; e += NT) {
-            const int i = a.rowind[e];
+            const int i = ind[e];
             if (i >= s1) { atomicOr(bm + (i >> 5), 1u << (i & 31)); lo = min(lo, i); hi = max(hi, i); }
-        }
-    } else {
-        const int e0 = a.rowptr[s0], e1 = a.rowptr[s1];
-        for (int e = e0 + tid; e < e1; e += NT) {
-            const int j = a.colind[e];
-            if (j >= s1) { atomicOr(bm + (j >> 5), 1u << (j & 31)); lo = min(lo, j); hi = max(hi, j); }
         }
     }
     const int32_t *Xidx = Lside ? a.Lrow : a.Ucol;
-    for (int t = 0; t < pcnt; ++t) {
-        const int xpos = (int)ldcg(pinfo + PIS * t + PI_XPOS);
-        for (int f = tid; f < xcnt[t]; f += NT) {
-            const int i = ldcg(Xidx + xpos + f);
-            if (i >= s1) { atomicOr(bm + (i >> 5), 1u << (i & 31)); lo = min(lo, i); hi = max(hi, i); }
-        }
+    for (int f = tid; f < total; f += NT) {
+        const int t = find_owner(off, pcnt, f);
+        const int i = ldcg(Xidx + xposs[t] + (f - off[t]));
+        if (i >= s1) { atomicOr(bm + (i >> 5), 1u << (i & 31)); lo = min(lo, i); hi = max(hi, i); }
     }
     lo = __reduce_min_sync(FULL_MASK, lo);
     hi = __reduce_max_sync(FULL_MASK, hi);
     if (lane == 0) { atomicMin(lohi, lo); atomicMax(lohi + 1, hi); }
     __syncthreads();
-    __threadfence_block();
     const int glo = lohi[0], ghi = lohi[1];
     const int pre = Lside ? b : 0;  // L: the b pivot rows come first
     int count = 0;
@@ -207,19 +223,17 @@ __device__ void phase_A(const FactorArgs &a, int K, bool Lside, char *smem) {
 
     // candidate slot of every producer X entry (monotone in the index)
     const int wlo = glo >> 5;
-    for (int t = 0; t < pcnt; ++t) {
-        const int xpos = (int)ldcg(pinfo + PIS * t + PI_XPOS);
-        for (int f = tid; f < xcnt[t]; f += NT) {
-            const int i = ldcg(Xidx + xpos + f);
-            int slot;
-            if (i < s1) {
-                slot = i - s0;  // pivot rows (L side only)
-            } else {
-                const uint32_t word = ldcg(bm + (i >> 5));
-                slot = pre + ldcg(wb + ((i >> 5) - wlo)) + __popc(word & ((1u << (i & 31)) - 1u));
-            }
-            xslot[off[t] + f] = slot;
+    for (int f = tid; f < total; f += NT) {
+        const int t = find_owner(off, pcnt, f);
+        const int i = ldcg(Xidx + xposs[t] + (f - off[t]));
+        int slot;
+        if (i < s1) {
+            slot = i - s0;  // pivot rows (L side only)
+        } else {
+            const uint32_t word = ldcg(bm + (i >> 5));
+            slot = pre + ldcg(wb + ((i >> 5) - wlo)) + __popc(word & ((1u << (i & 31)) - 1u));
         }
+        xslot[f] = slot;
     }
     __syncthreads();
     if (ghi >= 0)
@@ -232,21 +246,75 @@ __device__ void phase_A(const FactorArgs &a, int K, bool Lside, char *smem) {
 
 // ---------------------------------------------------------------- phase B
 // One tile: candidate slots [sa, sa + cnt) of one side, accumulated in shared memory.
+// The producers are processed in increasing J (fixed summation order); while producer t
+// is multiplied, the X rows and Y rows of producer t+1 are already loading into registers.
+constexpr int PF = (TRMAX * BILU_MAX_BLOCK + BILU_MAX_BLOCK * BILU_MAX_BLOCK + NT - 1) / NT;
+
+struct ProdStage {
+    int nx, ny, bJ;
+    double v[PF];
+    int xl, yc;
+};
+
+__device__ __forceinline__ void prefetch_producer(const FactorArgs &a, bool Lside, int t, int sa, int cnt, int s0,
+                                                  int b, const int32_t *sxs, const int32_t *sxe,
+                                                  const int32_t *pbJ, const int32_t *pny, const int32_t *poff,
+                                                  const int64_t *pxv, const int64_t *pyv, const int32_t *pyp,
+                                                  ProdStage &st) {
+    const int tid = threadIdx.x;
+    st.nx = sxe[t] - sxs[t];
+    st.ny = pny[t];
+    st.bJ = pbJ[t];
+    if (st.nx <= 0 || st.ny <= 0) { st.nx = 0; return; }
+    const double *Xpool = Lside ? a.Lval : a.Uval;
+    const double *Ypool = Lside ? a.Uval : a.Lval;
+    const int32_t *Yidx = Lside ? a.Ucol : a.Lrow;
+    const int32_t *xslot = Lside ? a.xslotL : a.xslotU;
+    const int nxv = st.nx * st.bJ, tot = nxv + st.ny * st.bJ;
+    const int64_t xval = pxv[t] + (int64_t)sxs[t] * st.bJ, yval = pyv[t];
+#pragma unroll
+    for (int k = 0; k < PF; ++k) {
+        const int e = tid + k * NT;
+        st.v[k] = e < nxv ? ldcg(Xpool + xval + e) : (e < tot ? ldcg(Ypool + yval + (e - nxv)) : 0.0);
+    }
+    st.xl = tid < st.nx ? ldcg(xslot + poff[t] + sxs[t] + tid) - sa : 0;
+    st.yc = (tid >= 64 && tid - 64 < st.ny) ? ldcg(Yidx + pyp[t] + (tid - 64)) - s0 : 0;
+}
+
 __device__ void phase_B_tile(const FactorArgs &a, int K, bool Lside, int sa, int cnt, char *smem) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int s0 = a.bstart[K], s1 = a.bstart[K + 1], b = s1 - s0;
     double *T = (double *)smem;                  // TRMAX * 64
     double *Xs = T + TRMAX * BILU_MAX_BLOCK;     // TRMAX * PS
     double *Ys = Xs + TRMAX * PS;                // 64 * PS
-    int32_t *g = (int32_t *)(Ys + BILU_MAX_BLOCK * PS);  // TRMAX
+    int64_t *pxv = (int64_t *)(Ys + BILU_MAX_BLOCK * PS);  // PMAX: X value offset
+    int64_t *pyv = pxv + PMAX;                   // PMAX: Y value offset
+    int32_t *g = (int32_t *)(pyv + PMAX);        // TRMAX
     int32_t *xl = g + TRMAX;                     // TRMAX: local slot of staged X rows
     int32_t *yc = xl + TRMAX;                    // 64: column of staged Y rows
     int32_t *sxs = yc + BILU_MAX_BLOCK;          // PMAX
     int32_t *sxe = sxs + PMAX;                   // PMAX
+    int32_t *pbJ = sxe + PMAX;                   // PMAX
+    int32_t *pny = pbJ + PMAX;                   // PMAX
+    int32_t *poff = pny + PMAX;                  // PMAX
+    int32_t *pyp = poff + PMAX;                  // PMAX
+    int32_t *pxc = pyp + PMAX;                   // PMAX
 
     const int32_t *rows = Lside ? a.rowsL : a.rowsU;
+    const int pcnt = ldcg(a.kst + (Lside ? 2 : 3));
+    const int64_t *pinfo = Lside ? a.pinfoL : a.pinfoU;
     for (int r = tid; r < cnt; r += NT) g[r] = ldcg(rows + sa + r);
     for (int e = tid; e < cnt * b; e += NT) T[e] = 0.0;
+    for (int t = tid; t < pcnt; t += NT) {
+        const int64_t *pi = pinfo + PIS * t;
+        pbJ[t] = (int)ldcg(pi + PI_BJ);
+        pny[t] = (int)ldcg(pi + PI_YCNT);
+        poff[t] = (int)ldcg(pi + PI_OFF);
+        pyp[t] = (int)ldcg(pi + PI_YPOS);
+        pxc[t] = (int)ldcg(pi + PI_XCNT);
+        pxv[t] = ldcg(pi + PI_XVAL);
+        pyv[t] = ldcg(pi + PI_YVAL);
+    }
     __syncthreads();
     // load A: L side rows i of A restricted to columns B_K; U side columns j restricted to rows B_K
     for (int r = warp; r < cnt; r += NW) {
@@ -263,79 +331,148 @@ __device__ void phase_B_tile(const FactorArgs &a, int K, bool Lside, int sa, int
             }
         }
     }
-    const int pcnt = ldcg(a.kst + (Lside ? 2 : 3));
-    const int64_t *pinfo = Lside ? a.pinfoL : a.pinfoU;
-    const int32_t *xslot = Lside ? a.xslotL : a.xslotU;
     // X entries of each producer that fall into this tile (slots are sorted)
+    const int32_t *xslot = Lside ? a.xslotL : a.xslotU;
     for (int t = warp; t < pcnt; t += NW) {
-        const int xc = (int)ldcg(pinfo + PIS * t + PI_XCNT);
-        const int o = (int)ldcg(pinfo + PIS * t + PI_OFF);
-        const int xs = warp_lower_bound(xslot + o, 0, xc, sa);
-        const int xe = warp_lower_bound(xslot + o, xs, xc, sa + cnt);
+        const int xs = warp_lower_bound(xslot + poff[t], 0, pxc[t], sa);
+        const int xe = warp_lower_bound(xslot + poff[t], xs, pxc[t], sa + cnt);
         if (lane == 0) { sxs[t] = xs; sxe[t] = xe; }
     }
     __syncthreads();
-    const double *Xpool = Lside ? a.Lval : a.Uval;
-    const double *Ypool = Lside ? a.Uval : a.Lval;
-    const int32_t *Yidx = Lside ? a.Ucol : a.Lrow;
+    long long flops = 0;
+    ProdStage st;
+    if (pcnt > 0) prefetch_producer(a, Lside, 0, sa, cnt, s0, b, sxs, sxe, pbJ, pny, poff, pxv, pyv, pyp, st);
     for (int t = 0; t < pcnt; ++t) {
-        const int nx = sxe[t] - sxs[t];
-        const int ny = (int)ldcg(pinfo + PIS * t + PI_YCNT);
-        if (nx <= 0 || ny <= 0) continue;  // uniform across the CTA
-        if (nx > TRMAX || ny > b) {
-            if (tid == 0) set_status(a.status, DEV_INTERNAL, a.info, K);
-            return;
-        }
-        const int bJ = (int)ldcg(pinfo + PIS * t + PI_BJ);
-        const int o = (int)ldcg(pinfo + PIS * t + PI_OFF);
-        const int64_t xval = ldcg(pinfo + PIS * t + PI_XVAL) + (int64_t)sxs[t] * bJ;
-        const int64_t yval = ldcg(pinfo + PIS * t + PI_YVAL);
-        // Y position: for the L side the U-breve columns in B_K, for the U side the L rows in B_K
-        for (int e = tid; e < nx * bJ; e += NT) {
-            const int x = e / bJ, k = e - x * bJ;
-            Xs[x * PS + k] = ldcg(Xpool + xval + e);
-        }
-        for (int e = tid; e < ny * bJ; e += NT) {
-            const int y = e / bJ, k = e - y * bJ;
-            Ys[y * PS + k] = ldcg(Ypool + yval + e);
-        }
-        if (tid < nx) {
-            int v = ldcg(xslot + o + sxs[t] + tid) - sa;
-            if (v < 0 || v >= cnt) { set_status(a.status, DEV_INTERNAL, a.info, K); v = 0; }
-            xl[tid] = v;
-        }
-        if (tid >= 64 && tid - 64 < ny) {
-            const int y = tid - 64;
-            const int64_t ypos = ldcg(pinfo + PIS * t + PI_YPOS);
-            int v = ldcg(Yidx + ypos + y) - s0;
-            if (v < 0 || v >= b) { set_status(a.status, DEV_INTERNAL, a.info, K); v = 0; }
-            yc[y] = v;
+        const int nx = st.nx, ny = st.ny, bJ = st.bJ;
+        if (nx > 0) {
+            if (nx > TRMAX || ny > b) {
+                if (tid == 0) set_status(a.status, DEV_INTERNAL, a.info, K);
+                return;
+            }
+            // stage producer t
+            const int nxv = nx * bJ, tot = nxv + ny * bJ;
+#pragma unroll
+            for (int k = 0; k < PF; ++k) {
+                const int e = tid + k * NT;
+                if (e < nxv) {
+                    const int x = e / bJ;
+                    Xs[x * PS + (e - x * bJ)] = st.v[k];
+                } else if (e < tot) {
+                    const int ee = e - nxv, y = ee / bJ;
+                    Ys[y * PS + (ee - y * bJ)] = st.v[k];
+                }
+            }
+            if (tid < nx) {
+                int v = st.xl;
+                if (v < 0 || v >= cnt) { set_status(a.status, DEV_INTERNAL, a.info, K); v = 0; }
+                xl[tid] = v;
+            }
+            if (tid >= 64 && tid - 64 < ny) {
+                int v = st.yc;
+                if (v < 0 || v >= b) { set_status(a.status, DEV_INTERNAL, a.info, K); v = 0; }
+                yc[tid - 64] = v;
+            }
         }
         __syncthreads();
-        for (int e = tid; e < nx * ny; e += NT) {
-            const int x = e / ny, y = e - x * ny;
-            const double *xr = Xs + x * PS, *yr = Ys + y * PS;
-            double s = 0.0;
-            for (int k = 0; k < bJ; ++k) s = fma(xr[k], yr[k], s);
-            T[xl[x] * b + yc[y]] -= s;
+        // the next producer's panels load while this one is multiplied
+        if (t + 1 < pcnt) prefetch_producer(a, Lside, t + 1, sa, cnt, s0, b, sxs, sxe, pbJ, pny, poff, pxv, pyv, pyp, st);
+        if (nx > 0) {
+            flops += 2LL * nx * ny * bJ;
+            for (int e = tid; e < nx * ny; e += NT) {
+                const int x = e / ny, y = e - x * ny;
+                const double *xr = Xs + x * PS, *yr = Ys + y * PS;
+                // four independent partial sums: a dependent FP64 FMA takes ~64 cycles here
+                double s0a = 0.0, s1a = 0.0, s2a = 0.0, s3a = 0.0;
+                int k = 0;
+                for (; k + 3 < bJ; k += 4) {
+                    s0a = fma(xr[k], yr[k], s0a);
+                    s1a = fma(xr[k + 1], yr[k + 1], s1a);
+                    s2a = fma(xr[k + 2], yr[k + 2], s2a);
+                    s3a = fma(xr[k + 3], yr[k + 3], s3a);
+                }
+                for (; k < bJ; ++k) s0a = fma(xr[k], yr[k], s0a);
+                T[xl[x] * b + yc[y]] -= (s0a + s1a) + (s2a + s3a);
+            }
         }
         __syncthreads();
     }
     double *out = (Lside ? a.TL : a.TU) + (int64_t)sa * b;
     for (int e = tid; e < cnt * b; e += NT) out[e] = T[e];
+    if (tid == 0 && flops)
+        atomicAdd((unsigned long long *)(a.info + (Lside ? INFO_FLOP_UPD_L : INFO_FLOP_UPD_U)),
+                  (unsigned long long)flops);
 }
 
 // ---------------------------------------------------------------- phase C
 // LU with partial pivoting of the pivot block in shared memory (one CTA), with the
 // perturbation of Sec. 3.6.  Writes P (possibly perturbed) to Pblk, LU and perm to scratch.
+//
+// On this GPU every FP64 instruction (compares included) issues on a pipe with 1/64 of the
+// FP32 rate, so the step is organised to keep FP64 instructions off the critical path:
+//  * rows stay in place; a logical permutation phys[] (physical row at each position,
+//    double-buffered) replaces the row swaps;
+//  * pivot search compares |values| as 64-bit integers (the ordering of non-negative
+//    doubles is the ordering of their bit patterns), ties go to the smaller logical position
+//    (LAPACK's first index of the largest |.| in the swapped order);
+//  * lookahead: while warps 1.. update the trailing columns j+2.. with column j, warp 0
+//    updates column j+1, picks its pivot, forms 1/pivot and the multipliers of column j+1,
+//    so a column step costs one CTA barrier.
+__device__ __forceinline__ unsigned long long absbits(double v) {
+    return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL;
+}
+
+// Warp 0: choose the pivot of column col among logical positions [from, b) of phys_in,
+// write the swapped permutation to phys_out, 1/pivot to *srp, and the multipliers
+// M[i][col] *= 1/pivot for the rows below.  Returns (through *sbad) col when the pivot
+// magnitude is <= thresh.
+__device__ __forceinline__ void lu_pivot_column(double *M, const int32_t *phys_in, int32_t *phys_out, int b,
+                                                int col, double thresh, double *srp, int *sp, int *sbad) {
+    const int lane = threadIdx.x & 31;
+    // each lane: best candidate among its two positions (ties: smaller position); an empty
+    // lane offers |0| at position b, which never beats a real candidate
+    unsigned long long bv = 0ULL;
+    int bk = b;
+    double bval = 0.0;
+    for (int k = col + lane; k < b; k += 32) {
+        const double x = M[phys_in[k] * PS + col];
+        const unsigned long long v = absbits(x);
+        if (bk == b || v > bv) { bv = v; bk = k; bval = x; }
+    }
+    // the reciprocal of every lane's candidate starts now and overlaps the reduction
+    const double rloc = (bk < b && bv != 0ULL) ? recip_nr(bval) : 0.0;
+    const unsigned hi = (unsigned)(bv >> 32), lo = (unsigned)bv;
+    const unsigned mhi = __reduce_max_sync(FULL_MASK, hi);
+    const unsigned mlo = __reduce_max_sync(FULL_MASK, hi == mhi ? lo : 0u);
+    const unsigned kk = (hi == mhi && lo == mlo) ? (unsigned)bk : 0xffffffffu;
+    const int q = (int)__reduce_min_sync(FULL_MASK, kk);
+    const int owner = (q - col) & 31;
+    const double pv = __shfl_sync(FULL_MASK, bval, owner);
+    const double rp = __shfl_sync(FULL_MASK, rloc, owner);
+    const int p = phys_in[q], rj = phys_in[col];
+    const bool bad = !(absbits(pv) > absbits(thresh));
+    for (int k = lane; k < b; k += 32) phys_out[k] = k == col ? p : (k == q ? rj : phys_in[k]);
+    if (!bad)
+        for (int k = col + 1 + lane; k < b; k += 32) {
+            const int i = k == q ? rj : phys_in[k];
+            M[i * PS + col] *= rp;
+        }
+    if (lane == 0) {
+        *srp = rp;
+        *sp = p;
+        if (bad) *sbad = col;
+    }
+}
+
 __device__ void phase_C(const FactorArgs &a, int K, char *smem) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int s0 = a.bstart[K], s1 = a.bstart[K + 1], b = s1 - s0;
     double *P = (double *)smem;                 // b x b (stride PS), current P (perturbed)
-    double *M = P + BILU_MAX_BLOCK * PS;        // LU work
-    int32_t *prm = (int32_t *)(M + BILU_MAX_BLOCK * PS);  // 64
-    int32_t *sh = prm + BILU_MAX_BLOCK;         // [0] pivot row, [1] bad column, [2] count
-    double *shd = (double *)(sh + 8);           // [0] amax, [1] pmax
+    double *M = P + BILU_MAX_BLOCK * PS;        // LU work, physical rows
+    double *srp = M + BILU_MAX_BLOCK * PS;      // 2: 1/pivot per step parity
+    int32_t *phys = (int32_t *)(srp + 2);       // 2 x 64: physical row at logical position
+    int32_t *sp = phys + 2 * BILU_MAX_BLOCK;    // 2: pivot row per step parity
+    int32_t *sh = sp + 2;                       // [0] bad column, [2] perturbation count
+    unsigned long long *smax = (unsigned long long *)(sh + 4);
     for (int e = tid; e < b * b; e += NT) {
         const int r = e / b, c = e - r * b;
         P[r * PS + c] = ldcg(a.TL + (int64_t)r * b + c);
@@ -343,93 +480,99 @@ __device__ void phase_C(const FactorArgs &a, int K, char *smem) {
     if (tid == 0) sh[2] = 0;
     __syncthreads();
     if (a.perturb) {
-        // all-zero columns, then all-zero rows: perturb the diagonal entry
-        if (tid == 0) {
-            int cnt = 0;
-            for (int j = 0; j < b; ++j) {
-                bool zero = true;
-                for (int i = 0; i < b; ++i) zero &= (P[i * PS + j] == 0.0);
-                if (zero) { P[j * PS + j] = perturbed(P[j * PS + j], a.pert_tau, a.pert_rho, a.alpha); ++cnt; }
+        // Sec. 3.6: all-zero columns, then all-zero rows, get their diagonal entry perturbed
+        // (the diagonal wins the tie with the other, zero, entries).  Each column / row check
+        // is independent of the others, so thread j takes column j, then row j.
+        if (tid < b) {
+            bool zero = true;
+            for (int i = 0; i < b; ++i) zero &= (absbits(P[i * PS + tid]) == 0ULL);
+            if (zero) {
+                P[tid * PS + tid] = perturbed(P[tid * PS + tid], a.pert_tau, a.pert_rho, a.alpha);
+                atomicAdd(sh + 2, 1);
             }
-            for (int i = 0; i < b; ++i) {
-                bool zero = true;
-                for (int j = 0; j < b; ++j) zero &= (P[i * PS + j] == 0.0);
-                if (zero) { P[i * PS + i] = perturbed(P[i * PS + i], a.pert_tau, a.pert_rho, a.alpha); ++cnt; }
+        }
+        __syncthreads();
+        if (tid < b) {
+            bool zero = true;
+            for (int j = 0; j < b; ++j) zero &= (absbits(P[tid * PS + j]) == 0ULL);
+            if (zero) {
+                P[tid * PS + tid] = perturbed(P[tid * PS + tid], a.pert_tau, a.pert_rho, a.alpha);
+                atomicAdd(sh + 2, 1);
             }
-            sh[2] = cnt;
         }
         __syncthreads();
     }
     bool done = false;
     for (int attempt = 0; attempt <= 2 * b && !done; ++attempt) {
-        // max |P| and copy to the work array
-        double mx = 0.0;
+        // copy P, max |P| (integer view), identity permutation
+        unsigned long long mx = 0ULL;
         for (int e = tid; e < b * b; e += NT) {
             const int r = e / b, c = e - r * b;
             const double v = P[r * PS + c];
             M[r * PS + c] = v;
-            mx = fmax(mx, fabs(v));
+            mx = max(mx, absbits(v));
         }
-        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(FULL_MASK, mx, o));
-        if (tid == 0) shd[1] = 0.0;
+        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(FULL_MASK, mx, o));
+        if (tid == 0) { *smax = 0ULL; sh[0] = -1; }
+        if (tid < b) phys[tid] = tid;
         __syncthreads();
-        if (lane == 0) {
-            // atomicMax on doubles via the ordered int64 view of non-negative values
-            atomicMax((unsigned long long *)&shd[1], (unsigned long long)__double_as_longlong(mx));
-        }
-        for (int i = tid; i < b; i += NT) prm[i] = i;
-        if (tid == 0) sh[1] = -1;
+        if (lane == 0) atomicMax(smax, mx);
         __syncthreads();
-        const double thresh = 1e-14 * shd[1];
+        const double thresh = 1e-14 * __longlong_as_double((long long)*smax);
+        // column 0: pivot and multipliers (warp 0)
+        if (warp == 0) lu_pivot_column(M, phys, phys + BILU_MAX_BLOCK, b, 0, thresh, srp, sp, sh);
+        __syncthreads();
         for (int j = 0; j < b; ++j) {
+            if (sh[0] >= 0) break;  // uniform: written before the last barrier
+            const int cur = (j + 1) & 1;  // permutation after the swap of step j
+            const int32_t *ph = phys + cur * BILU_MAX_BLOCK;
+            const int p = sp[j & 1];
+            const int m = b - j - 1;  // rows below the pivot (logical positions j+1..b-1)
             if (warp == 0) {
-                // first index of the largest |.| in column j, rows j..b-1
-                double best = -1.0;
-                int bi = b;
-                for (int i = j + lane; i < b; i += 32) {
-                    const double v = fabs(M[i * PS + j]);
-                    if (v > best) { best = v; bi = i; }
+                if (m > 0) {
+                    // lookahead: column j+1 of the rows below, then its pivot and multipliers
+                    const double upj1 = M[p * PS + j + 1];
+                    for (int k = j + 1 + lane; k < b; k += 32) {
+                        const int i = ph[k];
+                        M[i * PS + j + 1] = fma(-M[i * PS + j], upj1, M[i * PS + j + 1]);
+                    }
+                    __syncwarp();
+                    lu_pivot_column(M, ph, phys + (cur ^ 1) * BILU_MAX_BLOCK, b, j + 1, thresh, srp + ((j + 1) & 1),
+                                    sp + ((j + 1) & 1), sh);
                 }
-                for (int o = 16; o > 0; o >>= 1) {
-                    const double ov = __shfl_xor_sync(FULL_MASK, best, o);
-                    const int oi = __shfl_xor_sync(FULL_MASK, bi, o);
-                    if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+            } else if (m > 1) {
+                // trailing update of columns j+2.. with the multipliers of column j
+                const int w = m - 1, tot = m * w;
+                for (int e = tid - 32; e < tot; e += NT - 32) {
+                    const int r = e / w, c = j + 2 + (e - r * w);
+                    const int i = ph[j + 1 + r];
+                    M[i * PS + c] = fma(-M[i * PS + j], M[p * PS + c], M[i * PS + c]);
                 }
-                if (lane == 0) { sh[0] = bi; shd[0] = best; }
-            }
-            __syncthreads();
-            if (!(shd[0] > thresh)) {  // singular / ill-conditioned pivot
-                if (tid == 0) sh[1] = j;
-                __syncthreads();
-                break;
-            }
-            const int p = sh[0];
-            if (p != j) {
-                for (int c = tid; c < b; c += NT) {
-                    const double t = M[j * PS + c];
-                    M[j * PS + c] = M[p * PS + c];
-                    M[p * PS + c] = t;
-                }
-                if (tid == 0) { const int t = prm[j]; prm[j] = prm[p]; prm[p] = t; }
-            }
-            __syncthreads();
-            const double piv = M[j * PS + j];
-            for (int i = j + 1 + tid; i < b; i += NT) M[i * PS + j] /= piv;
-            __syncthreads();
-            const int m = b - j - 1;
-            for (int e = tid; e < m * m; e += NT) {
-                const int i = j + 1 + e / m, c = j + 1 + e % m;
-                M[i * PS + c] -= M[i * PS + j] * M[j * PS + c];
             }
             __syncthreads();
         }
-        const int bad = sh[1];
-        if (bad < 0) { done = true; break; }
+        const int bad = sh[0];
+        if (bad < 0) {
+            done = true;
+            const int fin = b & 1;  // buffer holding the final permutation
+            const int64_t dofs = a.Dptr[K];
+            for (int e = tid; e < b * b; e += NT) {
+                const int r = e / b, c = e - r * b;
+                a.Pblk[dofs + e] = P[r * PS + c];
+                a.LU[e] = M[phys[fin * BILU_MAX_BLOCK + r] * PS + c];
+            }
+            for (int i = tid; i < b; i += NT) {
+                const int pr = phys[fin * BILU_MAX_BLOCK + i];
+                a.perm[i] = pr;
+                a.LU[BILU_MAX_BLOCK * BILU_MAX_BLOCK + i] = recip_nr(M[pr * PS + i]);  // for the back substitutions
+            }
+            break;
+        }
         if (!a.perturb) break;
         if (tid == 0) {
             int k = 0;
             for (int i = 1; i < b; ++i)
-                if (fabs(P[i * PS + bad]) > fabs(P[k * PS + bad])) k = i;
+                if (absbits(P[i * PS + bad]) > absbits(P[k * PS + bad])) k = i;
             if (2.0 * fabs(P[bad * PS + bad]) >= fabs(P[k * PS + bad])) k = bad;
             P[k * PS + bad] = perturbed(P[k * PS + bad], a.pert_tau, a.pert_rho, a.alpha);
             sh[2] += 1;
@@ -440,33 +583,32 @@ __device__ void phase_C(const FactorArgs &a, int K, char *smem) {
         if (tid == 0) set_status(a.status, DEV_SINGULAR, a.info, K);
         return;
     }
-    const int64_t dofs = a.Dptr[K];
-    for (int e = tid; e < b * b; e += NT) {
-        const int r = e / b, c = e - r * b;
-        a.Pblk[dofs + e] = P[r * PS + c];
-        a.LU[e] = M[r * PS + c];
-    }
-    for (int i = tid; i < b; i += NT) a.perm[i] = prm[i];
     if (tid == 0 && sh[2] > 0) atomicAdd((unsigned long long *)(a.info + INFO_NPERTURB), (unsigned long long)sh[2]);
 }
 
 // ---------------------------------------------------------------- phase C2
 // Column c of D_K = P_K^{-1}: solve L U x = e_{perm^{-1}(c)} (P_K X = I), one warp per column.
 __device__ void phase_C2(const FactorArgs &a, int K, char *smem) {
+    // two columns per CTA (warps 0 and 1): the solves are chains of dependent FP64
+    // operations, so spreading the columns over many SMs shortens the phase
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int s0 = a.bstart[K], s1 = a.bstart[K + 1], b = s1 - s0;
-    const int first = blockIdx.x * NW;
+    const int first = blockIdx.x * 2;
     if (first >= b) return;
     double *M = (double *)smem;
     int32_t *prm = (int32_t *)(M + BILU_MAX_BLOCK * PS);
+    double *rdiag = (double *)(prm + BILU_MAX_BLOCK);
     for (int e = tid; e < b * b; e += NT) {
         const int r = e / b, c = e - r * b;
         M[r * PS + c] = ldcg(a.LU + e);
     }
-    for (int i = tid; i < b; i += NT) prm[i] = ldcg(a.perm + i);
+    for (int i = tid; i < b; i += NT) {
+        prm[i] = ldcg(a.perm + i);
+        rdiag[i] = ldcg(a.LU + BILU_MAX_BLOCK * BILU_MAX_BLOCK + i);
+    }
     __syncthreads();
     const int c = first + warp;
-    if (c >= b) return;
+    if (warp >= 2 || c >= b) return;
     // lane owns rows lane and lane + 32
     double y0 = (lane < b && prm[lane] == c) ? 1.0 : 0.0;
     double y1 = (lane + 32 < b && prm[lane + 32] == c) ? 1.0 : 0.0;
@@ -477,7 +619,7 @@ __device__ void phase_C2(const FactorArgs &a, int K, char *smem) {
     }
     for (int k = b - 1; k >= 0; --k) {  // backward, upper
         double own = k < 32 ? y0 : y1;
-        if ((k & 31) == lane) own = own / M[k * PS + k];
+        if ((k & 31) == lane) own = own * rdiag[k];
         const double xk = __shfl_sync(FULL_MASK, own, k & 31);
         if (k < 32) { if (lane == k) y0 = xk; } else { if (lane + 32 == k) y1 = xk; }
         if (lane < k) y0 -= M[lane * PS + k] * xk;
@@ -509,12 +651,21 @@ __device__ void phase_D(const FactorArgs &a, int K, char *smem) {
             double *t = a.TL + (int64_t)slot * b;
             const double t0 = lane < b ? ldcg(t + lane) : 0.0;
             const double t1 = lane + 32 < b ? ldcg(t + lane + 32) : 0.0;
-            double l0 = 0.0, l1 = 0.0;
-            for (int k = 0; k < b; ++k) {
+            double l0 = 0.0, l1 = 0.0, l0b = 0.0, l1b = 0.0;
+            int k = 0;
+            for (; k + 1 < b; k += 2) {
+                const double tk = __shfl_sync(FULL_MASK, k < 32 ? t0 : t1, k & 31);
+                const double tk1 = __shfl_sync(FULL_MASK, k + 1 < 32 ? t0 : t1, (k + 1) & 31);
+                if (lane < b) { l0 = fma(tk, Ds[k * PS + lane], l0); l0b = fma(tk1, Ds[(k + 1) * PS + lane], l0b); }
+                if (lane + 32 < b) { l1 = fma(tk, Ds[k * PS + lane + 32], l1); l1b = fma(tk1, Ds[(k + 1) * PS + lane + 32], l1b); }
+            }
+            if (k < b) {
                 const double tk = __shfl_sync(FULL_MASK, k < 32 ? t0 : t1, k & 31);
                 if (lane < b) l0 = fma(tk, Ds[k * PS + lane], l0);
                 if (lane + 32 < b) l1 = fma(tk, Ds[k * PS + lane + 32], l1);
             }
+            l0 += l0b;
+            l1 += l1b;
             const double nrm2 = warp_sum(l0 * l0 + l1 * l1);
             if (lane < b) t[lane] = l0;
             if (lane + 32 < b) t[lane + 32] = l1;
@@ -524,12 +675,21 @@ __device__ void phase_D(const FactorArgs &a, int K, char *smem) {
             const double *t = a.TU + (int64_t)slot * b;
             const double t0 = lane < b ? ldcg(t + lane) : 0.0;
             const double t1 = lane + 32 < b ? ldcg(t + lane + 32) : 0.0;
-            double u0 = 0.0, u1 = 0.0;
-            for (int k = 0; k < b; ++k) {
+            double u0 = 0.0, u1 = 0.0, u0b = 0.0, u1b = 0.0;
+            int k = 0;
+            for (; k + 1 < b; k += 2) {
+                const double tk = __shfl_sync(FULL_MASK, k < 32 ? t0 : t1, k & 31);
+                const double tk1 = __shfl_sync(FULL_MASK, k + 1 < 32 ? t0 : t1, (k + 1) & 31);
+                if (lane < b) { u0 = fma(Ds[lane * PS + k], tk, u0); u0b = fma(Ds[lane * PS + k + 1], tk1, u0b); }
+                if (lane + 32 < b) { u1 = fma(Ds[(lane + 32) * PS + k], tk, u1); u1b = fma(Ds[(lane + 32) * PS + k + 1], tk1, u1b); }
+            }
+            if (k < b) {
                 const double tk = __shfl_sync(FULL_MASK, k < 32 ? t0 : t1, k & 31);
                 if (lane < b) u0 = fma(Ds[lane * PS + k], tk, u0);
                 if (lane + 32 < b) u1 = fma(Ds[(lane + 32) * PS + k], tk, u1);
             }
+            u0 += u0b;
+            u1 += u1b;
             const double nrm2 = warp_sum(u0 * u0 + u1 * u1);
             if (lane == 0) a.keepU[slot] = sqrt(nrm2) > a.tau ? 1 : 0;
         }
@@ -538,20 +698,23 @@ __device__ void phase_D(const FactorArgs &a, int K, char *smem) {
 
 // ---------------------------------------------------------------- phase E
 // Compaction of the kept rows / columns (sorted) into the pools and producer appends.
-// Candidate slots are cut into tiles of 32; one warp per tile ranks its kept slots with a
-// ballot.  Every CTA with work computes the tile prefix sums itself (no extra barrier).
+// Candidate slots are cut into tiles of 32; tile T goes to CTA T % G, one warp per tile.
+// A ballot ranks the tile's kept slots; the metadata of all kept slots is handled lane-
+// parallel and their rows are copied by one flat loop, so the loads are issued together.
+// Every CTA with a tile computes the tile prefix sums itself (no extra barrier).
 __device__ void phase_E(const FactorArgs &a, int K, char *smem) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int s0 = a.bstart[K], s1 = a.bstart[K + 1], b = s1 - s0;
     const int mL = ldcg(a.kst + 0), mU = ldcg(a.kst + 1);
     const int nLc = mL - b;
     const int tL = (nLc + 31) >> 5, tU = (mU + 31) >> 5;
+    const bool has_work = blockIdx.x == 0 || (int)blockIdx.x < max(tL, tU);
+    if (!has_work) return;
     int32_t *cnt = (int32_t *)smem;  // NT tile offsets of the current chunk
-    int32_t *ws = cnt + NT;          // scan scratch
+    int32_t *ws = cnt + NT;          // scan scratch (40)
+    int32_t *sl = ws + 40;           // NW x 32: slot of the r-th kept entry of a warp's tile
     const int64_t Lbase = ldcg(a.Lptr + K), LVbase = ldcg(a.Lvptr + K);
     const int64_t Ubase = ldcg(a.Uptr + K), UVbase = ldcg(a.Uvptr + K);
-    const bool has_work = blockIdx.x == 0 || blockIdx.x * NW < max(tL, tU);
-    if (!has_work) return;
     int keptL, keptU;
     {
         int lk = 0, uk = 0;
@@ -573,53 +736,79 @@ __device__ void phase_E(const FactorArgs &a, int K, char *smem) {
         a.Uvptr[K + 1] = UVbase + (int64_t)keptU * b;
         atomicAdd((unsigned long long *)(a.info + INFO_CAND_ROWS), (unsigned long long)nLc);
         atomicAdd((unsigned long long *)(a.info + INFO_CAND_COLS), (unsigned long long)mU);
+        atomicAdd((unsigned long long *)(a.info + INFO_FLOP_SCALE), 2ULL * b * b * (unsigned long long)(nLc + mU));
+        atomicAdd((unsigned long long *)(a.info + INFO_FLOP_NORM), 2ULL * b * (unsigned long long)(nLc + mU));
     }
+    int32_t *wsl = sl + warp * 32;
     for (int side = 0; side < 2; ++side) {
         const bool isL = side == 0;
         const int ntile = isL ? tL : tU;
+        if ((int)blockIdx.x >= ntile) continue;  // uniform in the CTA
         const int sfirst = isL ? b : 0, send = isL ? mL : mU;
         const int32_t *kp = isL ? a.keepL : a.keepU;
+        const int32_t *rows = isL ? a.rowsL : a.rowsU;
+        const double *Tb = isL ? a.TL : a.TU;
+        double *pool = isL ? a.Lval + LVbase : a.Uval + UVbase;
+        int32_t *idxpool = isL ? a.Lrow + Lbase : a.Ucol + Ubase;
+        int32_t *last = isL ? a.lastU : a.lastL;
+        int32_t *pc = isL ? a.prodUcnt : a.prodLcnt;
+        int32_t *pl = isL ? a.prodU : a.prodL;
         int carry = 0;
         for (int c0 = 0; c0 < ntile; c0 += NT) {
             const int cn = min(NT, ntile - c0);
-            int my = 0;
-            if (tid < cn) {
-                const int sb = sfirst + (c0 + tid) * 32, se = min(send, sb + 32);
-                for (int s = sb; s < se; ++s) my += ldcg(kp + s);
+            // tile counts: one warp per tile, a ballot over its 32 keep flags
+            for (int T = warp; T < cn; T += NW) {
+                const int sb = sfirst + (c0 + T) * 32, se = min(send, sb + 32);
+                const bool kept = sb + lane < se && ldcg(kp + sb + lane) != 0;
+                const unsigned m = __ballot_sync(FULL_MASK, kept);
+                if (lane == 0) cnt[T] = __popc(m);
             }
+            __syncthreads();
+            const int my = tid < cn ? cnt[tid] : 0;
             int tot;
             const int ex = block_excl_scan(my, ws, &tot);
             if (tid < cn) cnt[tid] = carry + ex;
             __syncthreads();
-            for (int T = c0 + blockIdx.x * NW + warp; T < c0 + cn; T += a.G * NW) {
+            for (int T = c0 + (int)blockIdx.x + warp * a.G; T < c0 + cn; T += a.G * NW) {
                 const int sb = sfirst + T * 32, se = min(send, sb + 32);
-                const int s = sb + lane;
-                const bool kept = s < se && ldcg(kp + s) != 0;
+                const bool kept = sb + lane < se && ldcg(kp + sb + lane) != 0;
                 const unsigned m = __ballot_sync(FULL_MASK, kept);
+                const int nk = __popc(m);
                 const int64_t base = cnt[T - c0];
-                unsigned mm = m;
-                while (mm) {
-                    const int l = __ffs(mm) - 1;
-                    mm &= mm - 1;
-                    const int slot = sb + l;
-                    const int64_t o = base + __popc(m & ((1u << l) - 1u));
-                    const int idx = ldcg((isL ? a.rowsL : a.rowsU) + slot);
-                    const double *src = (isL ? a.TL : a.TU) + (int64_t)slot * b;
-                    double *dst = isL ? a.Lval + LVbase + o * b : a.Uval + UVbase + o * b;
-                    for (int c = lane; c < b; c += 32) dst[c] = ldcg(src + c);
-                    if (lane == 0) {
-                        const int tb = a.blkof[idx];
-                        int32_t *last = isL ? a.lastU : a.lastL;
-                        int32_t *pc = isL ? a.prodUcnt : a.prodLcnt;
-                        int32_t *pl = isL ? a.prodU : a.prodL;
-                        if (isL) a.Lrow[Lbase + o] = idx; else a.Ucol[Ubase + o] = idx;
-                        if (atomicExch(last + tb, K) != K) {
-                            const int pos = atomicAdd(pc + tb, 1);
-                            if (pos < a.prodcap) pl[(int64_t)tb * a.prodcap + pos] = K;
-                            else set_status(a.status, DEV_PROD_OVERFLOW, a.info, K);
-                        }
+                if (kept) {
+                    const int rank = __popc(m & ((1u << lane) - 1u));
+                    const int slot = sb + lane;
+                    wsl[rank] = slot;
+                    const int idx = ldcg(rows + slot);
+                    idxpool[base + rank] = idx;
+                    const int tb = a.blkof[idx];
+                    if (atomicExch(last + tb, K) != K) {
+                        const int pos = atomicAdd(pc + tb, 1);
+                        if (pos < a.prodcap) pl[(int64_t)tb * a.prodcap + pos] = K;
+                        else set_status(a.status, DEV_PROD_OVERFLOW, a.info, K);
                     }
                 }
+                __syncwarp();
+                // copy the nk kept rows (b values each), four elements in flight per lane
+                const int tot_e = nk * b;
+                for (int e0 = lane; e0 < tot_e; e0 += 128) {
+                    double v[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int e = e0 + u * 32;
+                        v[u] = 0.0;
+                        if (e < tot_e) {
+                            const int r = e / b, cc = e - r * b;
+                            v[u] = ldcg(Tb + (int64_t)wsl[r] * b + cc);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int e = e0 + u * 32;
+                        if (e < tot_e) pool[(base + e / b) * b + (e % b)] = v[u];
+                    }
+                }
+                __syncwarp();
             }
             carry += tot;
             __syncthreads();
@@ -627,12 +816,26 @@ __device__ void phase_E(const FactorArgs &a, int K, char *smem) {
     }
 }
 
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 __global__ void __launch_bounds__(NT, 1) bilu_factor_kernel(FactorArgs a) {
     extern __shared__ __align__(16) char smem[];
     const uint32_t G = a.G + a.debug_extra_cta;
+    // per-phase time of CTA 0 (ns, summed over the blocks): A, B, C, C2, D, E
+    uint64_t tacc[6] = {0, 0, 0, 0, 0, 0};
+    uint64_t tprev = gtimer(), tc2 = 0, tbw = 0;
+    auto lap = [&](int ph) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            const uint64_t t = gtimer();
+            tacc[ph] += t - tprev;
+            tprev = t;
+        }
+    };
     for (int K = 0; K < a.nb; ++K) {
-        const int s0 = a.bstart[K], s1 = a.bstart[K + 1];
-        const int b = s1 - s0;
         // A: candidate sets (CTA 0: L side, CTA 1 % G: U side)
         if (blockIdx.x == 0) phase_A(a, K, true, smem);
         if (blockIdx.x == (1 % a.G)) {
@@ -640,6 +843,7 @@ __global__ void __launch_bounds__(NT, 1) bilu_factor_kernel(FactorArgs a) {
             phase_A(a, K, false, smem);
         }
         if (!grid_barrier(a.bar, G, a.status, a.spin_limit, a.info, 1)) return;
+        lap(0);
         // B: accumulation tiles
         {
             const int mL = ldcg(a.kst + 0), mU = ldcg(a.kst + 1);
@@ -650,24 +854,65 @@ __global__ void __launch_bounds__(NT, 1) bilu_factor_kernel(FactorArgs a) {
                 const bool Ls = it < nLt;
                 const int sa = (Ls ? it : it - nLt) * TR;
                 const int cnt = min(TR, (Ls ? mL : mU) - sa);
+                const uint64_t t0 = gtimer();
                 phase_B_tile(a, K, Ls, sa, cnt, smem);
                 __syncthreads();
+                if (blockIdx.x == 0 && threadIdx.x == 0) tbw += gtimer() - t0;
             }
         }
         if (!grid_barrier(a.bar, G, a.status, a.spin_limit, a.info, 2)) return;
+        lap(1);
         if (blockIdx.x == 0) phase_C(a, K, smem);
         if (!grid_barrier(a.bar, G, a.status, a.spin_limit, a.info, 3)) return;
-        phase_C2(a, K, smem);
+        lap(2);
+        {
+            const uint64_t t0 = gtimer();
+            phase_C2(a, K, smem);
+            if (blockIdx.x == 0 && threadIdx.x == 0) tc2 += gtimer() - t0;
+        }
         if (!grid_barrier(a.bar, G, a.status, a.spin_limit, a.info, 4)) return;
+        lap(3);
         phase_D(a, K, smem);
         if (!grid_barrier(a.bar, G, a.status, a.spin_limit, a.info, 5)) return;
+        lap(4);
         phase_E(a, K, smem);
         if (!grid_barrier(a.bar, G, a.status, a.spin_limit, a.info, 6)) return;
-        (void)b;
+        lap(5);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+    {
+        for (int p = 0; p < 6; ++p) a.info[INFO_PHASE_NS + p] = (int64_t)tacc[p];
+        a.info[INFO_C2_WORK_NS] = (int64_t)tc2;
+        a.info[INFO_B_WORK_NS] = (int64_t)tbw;
+    }
+}
+
+// Self-test of recip_nr against the IEEE quotient 1.0 / p on n values spread over many
+// binades (test hook).  out[0] = number of results more than one ulp away.
+__global__ void recip_selftest_kernel(int n, unsigned long long seed, int *out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        unsigned long long h = seed + 0x9E3779B97F4A7C15ULL * (unsigned long long)(i + 1);
+        h ^= h >> 31; h *= 0xBF58476D1CE4E5B9ULL; h ^= h >> 29;
+        const double mant = 1.0 + (double)(h & ((1ULL << 52) - 1)) / 4503599627370496.0;
+        const int e = (int)((h >> 52) % 200) - 100;
+        const double p = ((h >> 63) ? -1.0 : 1.0) * ldexp(mant, e);
+        const double r = recip_nr(p), q = 1.0 / p;
+        const long long d = __double_as_longlong(r) - __double_as_longlong(q);
+        if (d > 1 || d < -1) atomicAdd(out, 1);
     }
 }
 
 }  // namespace
+
+int recip_selftest(int n) {
+    int *d = nullptr, h = -1;
+    if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) return -1;
+    cudaMemset(d, 0, sizeof(int));
+    recip_selftest_kernel<<<128, 256>>>(n, 12345ULL, d);
+    cudaMemcpy(&h, d, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    return cudaGetLastError() == cudaSuccess ? h : -1;
+}
 
 // ---------------------------------------------------------------- host side
 
@@ -737,7 +982,7 @@ bilu_status factor_alloc(bilu_ctx *c) {
         (e = dev_alloc(&c->d_keepL, c->capT)) != cudaSuccess || (e = dev_alloc(&c->d_keepU, c->capT)) != cudaSuccess ||
         (e = dev_alloc(&c->d_bmL, n / 32 + 2)) != cudaSuccess || (e = dev_alloc(&c->d_bmU, n / 32 + 2)) != cudaSuccess ||
         (e = dev_alloc(&c->d_wbL, n / 32 + 2)) != cudaSuccess || (e = dev_alloc(&c->d_wbU, n / 32 + 2)) != cudaSuccess ||
-        (e = dev_alloc(&c->d_LU, BILU_MAX_BLOCK * BILU_MAX_BLOCK)) != cudaSuccess ||
+        (e = dev_alloc(&c->d_LU, BILU_MAX_BLOCK * BILU_MAX_BLOCK + BILU_MAX_BLOCK)) != cudaSuccess ||
         (e = dev_alloc(&c->d_perm, BILU_MAX_BLOCK)) != cudaSuccess || (e = dev_alloc(&c->d_kstate, 16)) != cudaSuccess ||
         (e = dev_alloc(&c->d_status, 4)) != cudaSuccess || (e = dev_alloc(&c->d_info, INFO_COUNT)) != cudaSuccess ||
         (e = dev_alloc(&c->d_bar, 4)) != cudaSuccess || (e = alloc_pools(c)) != cudaSuccess ||
@@ -805,9 +1050,11 @@ bilu_status factor_run(bilu_ctx *c, double droptol) {
 
         void *args[] = {&a};
         BILU_CUDA(c, cudaEventRecord(e0, c->stream));
-        if (c->nb > 0)
+        if (c->nb > 0) {
             BILU_CUDA(c, cudaLaunchCooperativeKernel((void *)bilu_factor_kernel, dim3(G), dim3(NT), args,
                                                      SMEM_BYTES, c->stream));
+            c->launches += 1;
+        }
         BILU_CUDA(c, cudaEventRecord(e1, c->stream));
         int32_t status = 0;
         int64_t info[INFO_COUNT];
@@ -848,6 +1095,20 @@ bilu_status factor_run(bilu_ctx *c, double droptol) {
         c->kept_rows = tails[0]; c->nnz_l = tails[1]; c->kept_cols = tails[2]; c->nnz_u = tails[3];
         c->cand_rows = info[INFO_CAND_ROWS]; c->cand_cols = info[INFO_CAND_COLS];
         c->nperturb = info[INFO_NPERTURB];
+        c->flop_upd_l = info[INFO_FLOP_UPD_L];
+        c->flop_upd_u = info[INFO_FLOP_UPD_U];
+        c->flop_scale = info[INFO_FLOP_SCALE];
+        c->flop_norm = info[INFO_FLOP_NORM];
+        for (int p = 0; p < 6; ++p) c->phase_ms[p] = info[INFO_PHASE_NS + p] * 1e-6;
+        c->phase_ms[6] = info[INFO_C2_WORK_NS] * 1e-6;
+        c->phase_ms[7] = info[INFO_B_WORK_NS] * 1e-6;
+        double f_lu = 0.0;  // getrf (2/3 b^3) and inverse (4/3 b^3) per diagonal block
+        for (int32_t K = 0; K < c->nb; ++K) {
+            const double b = c->h_bstart[K + 1] - c->h_bstart[K];
+            f_lu += 2.0 * b * b * b;
+        }
+        c->flops_factor = (double)c->flop_upd_l + (double)c->flop_upd_u + (double)c->flop_scale +
+                          (double)c->flop_norm + f_lu;
         return c->nperturb > 0 ? BILU_PERTURBED : BILU_OK;
     }
     cudaEventDestroy(e0);

@@ -9,6 +9,7 @@
 // per-CTA partial sums combined in a fixed order, so results are bitwise reproducible.
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "dev_common.cuh"
 
@@ -171,8 +172,9 @@ __global__ void __launch_bounds__(VT) normalize_kernel(int64_t n, int j, double 
     const Chunk c = chunk_of(n);
     const double hn = sqrt(sum_partials(part + 2 * G, G));
     if (hn == 0.0) return;
+    const double rh = 1.0 / hn;  // one divide, then multiplies (FP64 divides are slow here)
     double *vn = V + (int64_t)(j + 1) * n;
-    for (int64_t e = c.lo + threadIdx.x; e < c.hi; e += VT) vn[e] = w[e] / hn;
+    for (int64_t e = c.lo + threadIdx.x; e < c.hi; e += VT) vn[e] = w[e] * rh;
 }
 
 // Givens rotations on column j of H, update of g, convergence test (one warp).
@@ -250,7 +252,8 @@ __global__ void __launch_bounds__(VT) cycle_begin_kernel(int64_t n, int m, const
                                                          int32_t *gi, int64_t soff, int64_t goff) {
     const double beta = ldcg(gm + soff + GS_BETA);
     const Chunk c = chunk_of(n);
-    for (int64_t e = c.lo + threadIdx.x; e < c.hi; e += VT) V[e] = r[e] / beta;
+    const double rb = 1.0 / beta;
+    for (int64_t e = c.lo + threadIdx.x; e < c.hi; e += VT) V[e] = r[e] * rb;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         double *g = gm + goff;
         for (int k = 0; k <= m; ++k) g[k] = 0.0;
@@ -376,6 +379,7 @@ bilu_status gmres_run(bilu_ctx *c, const double *b, double *x, double tol, int m
     setup_kernel<<<1, 32, 0, c->stream>>>(c->d_gm, c->d_gmi, c->d_part, G, L.scal, tol, maxit, m);
     launch_spmv(c, c->d_gx, c->d_r, c->d_gb, c->d_part + 3 * G, nullptr);
     cycle_end_kernel<<<1, 32, 0, c->stream>>>(c->d_gm, c->d_gmi, c->d_part, G, L.scal, c->h_gm_pinned, c->h_gmi_pinned);
+    c->launches += 4;
     BILU_CUDA(c, cudaGetLastError());
     BILU_CUDA(c, cudaStreamSynchronize(c->stream));
     double bnorm = c->h_gm_pinned[GS_BNORM];
@@ -388,16 +392,28 @@ bilu_status gmres_run(bilu_ctx *c, const double *b, double *x, double tol, int m
         if (!c->gm_graph) {
             cudaGraph_t graph;
             BILU_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+            const int64_t before = c->launches;
             bilu_status st = record_cycle(c, m);
+            c->launches = before;  // captured, not launched: counted per graph launch
             cudaError_t ce = cudaStreamEndCapture(c->stream, &graph);
             if (st != BILU_OK) return st;
             if (ce != cudaSuccess) return cuda_err(c, ce, "cudaStreamEndCapture");
+            size_t nn = 0;
+            cudaGraphGetNodes(graph, nullptr, &nn);
+            std::vector<cudaGraphNode_t> nodes(nn);
+            cudaGraphGetNodes(graph, nodes.data(), &nn);
+            c->gm_graph_kernels = 0;
+            for (auto nd : nodes) {
+                cudaGraphNodeType ty;
+                if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) c->gm_graph_kernels++;
+            }
             ce = cudaGraphInstantiate(&c->gm_graph, graph, 0);
             cudaGraphDestroy(graph);
             if (ce != cudaSuccess) return cuda_err(c, ce, "cudaGraphInstantiate");
         }
         while (rel > tol && c->h_gmi_pinned[GI_ITS] < maxit) {
             BILU_CUDA(c, cudaGraphLaunch(c->gm_graph, c->stream));
+            c->launches += c->gm_graph_kernels;
             BILU_CUDA(c, cudaStreamSynchronize(c->stream));
             rel = c->h_gm_pinned[GS_REL];
             ++restarts;

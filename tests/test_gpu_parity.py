@@ -202,3 +202,23 @@ def test_empty_matrix(ctx):
         assert info.iters == 0
     finally:
         B.bilu_destroy(c)
+
+
+def test_algorithmic_flop_counters_match_oracle(ctx):
+    """The factor kernel counts its algorithmic work on the device; the integer counts
+    equal the oracle's (same candidate sets, same update shapes)."""
+    A = W.convdiff_upwind((16, 16, 16), seed=1)
+    g = gpu_factor(ctx, A, 1e-2, _fixed(32), export=False)
+    o = _oracle(A, g.bstart, 1e-2)
+    c, s = o.counters, g.stats
+    assert s.flop_upd_l == c["flop_upd_L"] and s.flop_upd_u == c["flop_upd_U"]
+    assert s.flop_scale == c["flop_scale"] and s.flop_norm == c["flop_norm"]
+    assert s.cand_rows == c["cand_rows"] and s.cand_cols == c["cand_cols"]
+    total = sum(c[k] for k in ("flop_upd_L", "flop_upd_U", "flop_getrf", "flop_inv", "flop_scale", "flop_norm"))
+    assert abs(s.flops_factor - total) <= 1e-9 * total
+
+
+def test_newton_reciprocal_within_one_ulp_of_ieee(ctx):
+    """The kernels replace FP64 divisions on critical paths by a Newton-Raphson reciprocal;
+    it must stay within one ulp of CUDA's IEEE quotient."""
+    B.bilu_debug_set(ctx, B.BILU_DEBUG_SELFTEST_RECIP, 1 << 20)
