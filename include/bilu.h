@@ -187,6 +187,27 @@ const char *bilu_last_error(const bilu_ctx *ctx);
 enum { BILU_DEBUG_EXTRA_CTA = 1, BILU_DEBUG_SPIN_LIMIT = 2, BILU_DEBUG_SELFTEST_RECIP = 3 };
 bilu_status bilu_debug_set(bilu_ctx *ctx, int32_t what, int64_t value);
 
+/*
+ * bilu_apply without any device allocation.  The paper has no counterpart: this entry point
+ * serves callers that cannot allocate device memory when they apply the preconditioner --
+ * code running while a CUDA graph is being captured, programs whose device memory belongs
+ * to a fixed pool or to another framework's allocator, real-time loops that must not enter
+ * the allocator.  bilu_apply itself allocates nothing per call, but it relies on buffers
+ * created with the factor and stages host vectors through buffers allocated on first use.
+ *
+ * Same result as bilu_apply (z = M^{-1} r, same summation order), for device pointers only
+ * (host pointers: BILU_ERR_ARG).  Its scratch (per-block completion flags and sweep state)
+ * is one fixed array of 512 KB in device memory that every GPU loading the library holds
+ * until the process exits; it serves factors of at most 65536 diagonal blocks (more:
+ * BILU_ERR_ARG).  The first call on a device looks up that array's device address (a CUDA
+ * runtime query, no allocation): make the first call on each device before any stream
+ * capture.  All calls on a device share the array and each call clears the part it uses:
+ * calls whose work overlaps on the GPU (other streams, other contexts) race and must be
+ * ordered by the caller.  Stream-ordered on the context's stream; does not synchronize, so
+ * a device-side wait that gives up is not reported.  Calls no cudaMalloc / cudaFree.
+ */
+bilu_status bilu_apply_noalloc(bilu_ctx *ctx, const double *r, double *z);
+
 /* Releases the context and all device memory it owns.  NULL is ignored. */
 void bilu_destroy(bilu_ctx *ctx);
 

@@ -27,7 +27,7 @@ BILU_MAX_BLOCK = 64
 # every extern "C" symbol that include/bilu.h declares
 EXPORTED = ["bilu_params_default", "bilu_create", "bilu_analyze", "bilu_factor", "bilu_apply",
             "gmres_solve", "bilu_stats", "bilu_get_partition", "bilu_export", "bilu_last_error",
-            "bilu_debug_set", "bilu_destroy"]
+            "bilu_debug_set", "bilu_apply_noalloc", "bilu_destroy"]
 
 
 class bilu_params(ct.Structure):
@@ -82,6 +82,7 @@ def lib():
             "bilu_export": ([P] * 9, i32),
             "bilu_last_error": ([P], ct.c_char_p),
             "bilu_debug_set": ([P, i32, i64], i32),
+            "bilu_apply_noalloc": ([P, P, P], i32),
             "bilu_destroy": ([P], None),
         }
         for name, (args, res) in sig.items():
@@ -155,6 +156,12 @@ def bilu_factor(ctx, droptol: float) -> int:
 
 def bilu_apply(ctx, r, z) -> int:
     st = lib().bilu_apply(ctx, _ptr(r), _ptr(z))
+    return _check(ctx, st)
+
+
+def bilu_apply_noalloc(ctx, r, z) -> int:
+    """bilu_apply for callers that cannot allocate: device vectors only, fixed scratch."""
+    st = lib().bilu_apply_noalloc(ctx, _ptr(r), _ptr(z))
     return _check(ctx, st)
 
 
