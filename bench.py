@@ -362,9 +362,9 @@ def run_gpu(args):
                                            "solve_ms": statistics.median(ts), "apply_ms": t_apply,
                                            "fill_nnz(L+U+D)/nnz(A)": (st.nnz_l + st.nnz_u + st.nnz_d) / w.A.nnz,
                                            "nblocks": st.nblocks,
-                                           "factor_phase_ms": dict(zip(["candidates", "updates", "pivot_lu", "inverse",
-                                                                        "scale_drop", "compact", "cta0_inverse_work",
-                                                                        "cta0_update_work"],
+                                           "factor_phase_ms": dict(zip(["candidates", "pivot_rows+lu", "inverse",
+                                                                        "bound_skip_updates", "scale_drop", "compact",
+                                                                        "cta0_lu_work", "cta0_pivot_tile_wait"],
                                                                        [round(v, 3) for v in st.phase_ms]))}),
                 "roofline": dominant, "roofline_other": other,
                 "gpu_launches": launches, "clocks": clk.summary(), "e2e": e2e, "cpu_baseline": cpu}

@@ -64,7 +64,11 @@ typedef struct {
     double pert_tau;     /* absolute perturbation tolerance tau (paper: 1e-2)                  */
     double pert_rho;     /* relative perturbation tolerance rho (paper: 1e-1)                  */
     int32_t precision;   /* BILU_PREC_*: arithmetic of the Schur updates and panel scaling     */
-    int32_t skip;        /* BILU_SKIP_*: candidate-row skipping in the factorization           */
+    int32_t skip;        /* BILU_SKIP_*: candidate-row skipping in the factorization.
+                            BILU_SKIP_BOUND: after D_K is known, a candidate row i is skipped
+                            when (||A(i,B_K)|| + sum_J ||L_J(i,:)|| ||U_J(:,B_K)||_F) ||D_K||_F
+                            <= tau (1 - 1e-10), which proves ||l_i|| <= tau (triangle inequality,
+                            ||D_K||_2 <= ||D_K||_F); columns likewise.  Same factor as without. */
 } bilu_params;
 
 typedef struct {
@@ -96,10 +100,14 @@ typedef struct {
     int32_t pool_retries;     /* factor re-runs after growing the L/U pools             */
     int64_t kernel_launches;  /* kernels of this library launched on the context so far
                                  (each node of a launched CUDA graph counts once)       */
-    double phase_ms[8];       /* factorization time by phase (candidate sets, updates,
-                                 pivot LU, inverse, scaling + dropping, compaction; each
-                                 up to the end of its grid barrier), then the time CTA 0
-                                 spends inside the inverse and the update work          */
+    double phase_ms[8];       /* factorization time by phase, each up to the end of its
+                                 grid barrier: candidate sets; pivot-row updates + pivot
+                                 LU (other updates overlap); inverse; bound-tested
+                                 updates (norm-bound skip only); scaling + dropping;
+                                 compaction.  Then CTA 0's time inside the pivot LU and
+                                 waiting for the pivot-row updates                      */
+    int64_t skipped_rows;     /* candidate rows / columns the norm bound proved dropped  */
+    int64_t skipped_cols;     /* (BILU_SKIP_BOUND), whose products were not computed     */
 } bilu_stats_t;
 
 /* Fills *p with the defaults: FIXED blocking of 32 (max 64), tau_analyze 1e-2,

@@ -50,7 +50,8 @@ class bilu_stats_t(ct.Structure):
                 ("flop_upd_u", ct.c_int64), ("flop_scale", ct.c_int64), ("flop_norm", ct.c_int64),
                 ("t_analyze_ms", ct.c_double),
                 ("t_factor_ms", ct.c_double), ("pool_retries", ct.c_int32),
-                ("kernel_launches", ct.c_int64), ("phase_ms", ct.c_double * 8)]
+                ("kernel_launches", ct.c_int64), ("phase_ms", ct.c_double * 8),
+                ("skipped_rows", ct.c_int64), ("skipped_cols", ct.c_int64)]
 
 
 class BiluError(RuntimeError):

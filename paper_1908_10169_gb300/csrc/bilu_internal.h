@@ -32,8 +32,10 @@ enum {
     INFO_FLOP_SCALE = 8,     // 2 b_K^2 per candidate row / column
     INFO_FLOP_NORM = 9,      // 2 b_K per candidate row / column
     INFO_PHASE_NS = 10,      // 6 slots: time of the phases A, B, C, C2, D, E (CTA 0)
-    INFO_C2_WORK_NS = 16,    // time CTA 0 spends inside phase C2 (excluding the barrier)
-    INFO_B_WORK_NS = 17,     // time CTA 0 spends inside phase B tiles
+    INFO_C2_WORK_NS = 16,    // time CTA 0 spends inside the pivot LU
+    INFO_B_WORK_NS = 17,     // time CTA 0 waits for the pivot-row tiles
+    INFO_SKIP_ROWS = 18,     // candidate rows skipped by the norm bound
+    INFO_SKIP_COLS = 19,     // candidate columns skipped by the norm bound
     INFO_COUNT = 24
 };
 
@@ -67,6 +69,7 @@ struct bilu_ctx {
     int32_t *d_Lrow = nullptr, *d_Ucol = nullptr;
     double *d_Lval = nullptr, *d_Uval = nullptr;
     double *d_Dinv = nullptr, *d_Pblk = nullptr;
+    double *d_Lnrm = nullptr, *d_Unrm = nullptr;  // norms of the kept rows of L / columns of U-breve
 
     // producer lists (blocks J whose kept U columns / L rows hit block K)
     int32_t prodcap = 0;
@@ -84,6 +87,8 @@ struct bilu_ctx {
     int64_t *d_pinfoL = nullptr, *d_pinfoU = nullptr;  // per-producer update plan
     int64_t capXS = 0;
     double *d_LU = nullptr;
+    double *d_nrmL = nullptr, *d_nrmU = nullptr, *d_dcolsq = nullptr;
+    uint32_t *d_pivdone = nullptr;
     int32_t *d_perm = nullptr;
     int32_t *d_kstate = nullptr;   // per-step scalars (candidate counts, pivot status)
     int32_t *d_status = nullptr;
@@ -112,7 +117,7 @@ struct bilu_ctx {
 
     // results of the last factorization
     int64_t kept_rows = 0, kept_cols = 0, nnz_l = 0, nnz_u = 0, cand_rows = 0, cand_cols = 0;
-    int64_t nperturb = 0;
+    int64_t nperturb = 0, skipped_rows = 0, skipped_cols = 0;
     int32_t pool_retries = 0;
     int64_t launches = 0;          // kernels of this library launched on the context (graph nodes included)
     int64_t gm_graph_kernels = 0;  // kernel nodes of the captured GMRES cycle

@@ -103,7 +103,7 @@ bilu_status bilu_factor(bilu_ctx *c, double droptol) {
     c->err.clear();
     if (c->state < 1) return set_err(c, BILU_ERR_STATE, "bilu_factor before bilu_analyze");
     if (!(droptol >= 0.0) || !std::isfinite(droptol)) return set_err(c, BILU_ERR_ARG, "droptol must be finite and >= 0");
-    if (c->p.precision != BILU_PREC_FP64 || c->p.skip != BILU_SKIP_NONE)
+    if (c->p.precision != BILU_PREC_FP64 || c->p.skip == BILU_SKIP_LEARNED)
         return set_err(c, BILU_ERR_ARG, "precision / skip mode not available in this build");
     BILU_CUDA(c, cudaSetDevice(c->device));
     c->state = 1;
@@ -192,6 +192,8 @@ bilu_status bilu_stats(bilu_ctx *c, bilu_stats_t *o) {
         o->flop_scale = c->flop_scale;
         o->flop_norm = c->flop_norm;
         for (int k = 0; k < 8; ++k) o->phase_ms[k] = c->phase_ms[k];
+        o->skipped_rows = c->skipped_rows;
+        o->skipped_cols = c->skipped_cols;
     }
     return BILU_OK;
 }

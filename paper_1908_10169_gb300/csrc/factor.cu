@@ -26,10 +26,10 @@ namespace {
 
 constexpr int NT = 512;          // threads per CTA
 constexpr int NW = NT / 32;      // warps per CTA
-constexpr int TRMAX = 32;        // max candidate slots per accumulation tile
+constexpr int TRMAX = 16;        // max candidate slots per accumulation tile
 constexpr int PS = BILU_MAX_BLOCK + 1;  // padded row stride (doubles) of staged panels
 constexpr int PMAX = 1024;       // max producers per block handled by the kernel
-constexpr int SMEM_BYTES = 112 * 1024;
+constexpr int SMEM_BYTES = 128 * 1024;
 
 struct FactorArgs {
     int32_t n, nb, G, perturb;
@@ -59,10 +59,15 @@ struct FactorArgs {
     int64_t *info;
     uint32_t *bar;
     int32_t debug_extra_cta;     // test hook: the barrier waits for one CTA that never comes
+    int32_t skip_bound;          // 1: skip candidates that the norm bound proves dropped
+    double *Lnrm, *Unrm;         // per kept row of L: ||l_i||; per kept column of U-breve: ||u_j||
+    double *dcolsq;              // squared column norms of D_K (b entries)
+    uint32_t *pivdone;           // pivot-row tiles finished for the current block
+    double *nrmL, *nrmU;         // per candidate slot: ||l_i|| and ||T_U[:,j]|| (phase D -> E)
 };
 
 // pinfo layout (per producer t of the current block)
-enum { PI_J = 0, PI_BJ, PI_XCNT, PI_YCNT, PI_OFF, PI_XPOS, PI_XVAL, PI_YVAL, PI_YPOS, PIS };
+enum { PI_J = 0, PI_BJ, PI_XCNT, PI_YCNT, PI_OFF, PI_XPOS, PI_XVAL, PI_YVAL, PI_YPOS, PI_YF, PIS };
 
 __device__ __forceinline__ double perturbed(double d, double ptau, double prho, double alpha) {
     // Sec. 3.6: d (1 + rho beta_j) + sign(d) tau alpha with beta_j := 1 and sign(0) := +1
@@ -130,8 +135,19 @@ __device__ void phase_A(const FactorArgs &a, int K, bool Lside, char *smem) {
             xval = uv + (int64_t)(xbeg - u0) * bJ;
             yval = lv + (int64_t)(ybeg - l0) * bJ;
         }
+        double yf = 0.0;  // Frobenius norm of the producer's Y block (norm-bound skip)
+        if (a.skip_bound) {
+            const double *nrm = Lside ? a.Unrm : a.Lnrm;
+            double acc = 0.0;
+            for (int y = ybeg + lane; y < yend; y += 32) {
+                const double v = ldcg(nrm + y);
+                acc = fma(v, v, acc);
+            }
+            yf = sqrt(warp_sum(acc));
+        }
         if (lane == 0) {
             int64_t *pi = pinfo + PIS * t;
+            pi[PI_YF] = __double_as_longlong(yf);
             pi[PI_J] = J;
             pi[PI_BJ] = bJ;
             pi[PI_XCNT] = xend - xbeg;
@@ -281,7 +297,11 @@ __device__ __forceinline__ void prefetch_producer(const FactorArgs &a, bool Lsid
     st.yc = (tid >= 64 && tid - 64 < st.ny) ? ldcg(Yidx + pyp[t] + (tid - 64)) - s0 : 0;
 }
 
-__device__ void phase_B_tile(const FactorArgs &a, int K, bool Lside, int sa, int cnt, char *smem) {
+// bound = true (norm-bound skip, after D_K is known): every candidate row of the tile first
+// gets an upper bound of ||T[i,:]||: ||A part|| + sum_J ||X row of J|| * ||Y block of J||_F.
+// Rows with bound * ||D_K||_F <= tau (1 - 1e-10) are provably dropped (||l_i|| <= ||T[i,:]||
+// ||D_K||_2): their products and scaling are skipped and their keep flag is set to -1.
+__device__ void phase_B_tile(const FactorArgs &a, int K, bool Lside, int sa, int cnt, char *smem, bool bound) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int s0 = a.bstart[K], s1 = a.bstart[K + 1], b = s1 - s0;
     double *T = (double *)smem;                  // TRMAX * 64
@@ -299,6 +319,12 @@ __device__ void phase_B_tile(const FactorArgs &a, int K, bool Lside, int sa, int
     int32_t *poff = pny + PMAX;                  // PMAX
     int32_t *pyp = poff + PMAX;                  // PMAX
     int32_t *pxc = pyp + PMAX;                   // PMAX
+    int32_t *pxp = pxc + PMAX;                   // PMAX: X index position
+    int32_t *act = pxp + PMAX;                   // TRMAX: row active (not provably dropped)
+    double *pyf = (double *)(act + TRMAX);       // PMAX: Frobenius norm of the Y block
+    double *bnd = pyf + PMAX;                    // TRMAX: bound of ||T[i,:]||
+    double *sdf = bnd + TRMAX;                   // [0] ||D_K||_F
+    int32_t *sskip = (int32_t *)(sdf + 2);       // [0] skipped rows of the tile
 
     const int32_t *rows = Lside ? a.rowsL : a.rowsU;
     const int pcnt = ldcg(a.kst + (Lside ? 2 : 3));
@@ -314,21 +340,37 @@ __device__ void phase_B_tile(const FactorArgs &a, int K, bool Lside, int sa, int
         pxc[t] = (int)ldcg(pi + PI_XCNT);
         pxv[t] = ldcg(pi + PI_XVAL);
         pyv[t] = ldcg(pi + PI_YVAL);
+        pxp[t] = (int)ldcg(pi + PI_XPOS);
+        pyf[t] = __longlong_as_double(ldcg(pi + PI_YF));
+    }
+    if (bound) {
+        for (int r = tid; r < cnt; r += NT) { act[r] = 1; bnd[r] = 0.0; }
+        if (warp == 0) {
+            double acc = 0.0;
+            for (int c = lane; c < b; c += 32) acc += ldcg(a.dcolsq + c);
+            acc = warp_sum(acc);
+            if (lane == 0) { sdf[0] = sqrt(acc); sskip[0] = 0; }
+        }
     }
     __syncthreads();
     // load A: L side rows i of A restricted to columns B_K; U side columns j restricted to rows B_K
     for (int r = warp; r < cnt; r += NW) {
         const int idx = g[r];
+        double sq = 0.0;
         if (Lside) {
             for (int e = a.rowptr[idx] + lane; e < a.rowptr[idx + 1]; e += 32) {
                 const int c = a.colind[e];
-                if (c >= s0 && c < s1) T[r * b + (c - s0)] = a.val[e];
+                if (c >= s0 && c < s1) { const double v = a.val[e]; T[r * b + (c - s0)] = v; sq = fma(v, v, sq); }
             }
         } else {
             for (int e = a.colptr[idx] + lane; e < a.colptr[idx + 1]; e += 32) {
                 const int rr = a.rowind[e];
-                if (rr >= s0 && rr < s1) T[r * b + (rr - s0)] = a.cval[e];
+                if (rr >= s0 && rr < s1) { const double v = a.cval[e]; T[r * b + (rr - s0)] = v; sq = fma(v, v, sq); }
             }
+        }
+        if (bound) {
+            sq = warp_sum(sq);
+            if (lane == 0) bnd[r] = sqrt(sq);
         }
     }
     // X entries of each producer that fall into this tile (slots are sorted)
@@ -339,6 +381,28 @@ __device__ void phase_B_tile(const FactorArgs &a, int K, bool Lside, int sa, int
         if (lane == 0) { sxs[t] = xs; sxe[t] = xe; }
     }
     __syncthreads();
+    if (bound) {
+        // bound of ||T[i,:]||; the order of the additions does not matter: rows with a bound
+        // near the threshold are kept (margin 1e-10), the exact test then decides
+        const double *Xn = Lside ? a.Lnrm : a.Unrm;
+        for (int t = 0; t < pcnt; ++t) {
+            const int nx = sxe[t] - sxs[t];
+            for (int x = tid; x < nx; x += NT) {
+                const int r = ldcg(xslot + poff[t] + sxs[t] + x) - sa;
+                if (r >= 0 && r < cnt) atomicAdd(bnd + r, ldcg(Xn + pxp[t] + sxs[t] + x) * pyf[t]);
+            }
+        }
+        __syncthreads();
+        int32_t *kp = Lside ? a.keepL : a.keepU;
+        for (int r = tid; r < cnt; r += NT) {
+            const bool pivot_row = Lside && sa + r < b;
+            const bool drop = !pivot_row && bnd[r] * sdf[0] <= a.tau * (1.0 - 1e-10);
+            act[r] = drop ? 0 : 1;
+            kp[sa + r] = drop ? -1 : 0;
+            if (drop) atomicAdd(sskip, 1);
+        }
+        __syncthreads();
+    }
     long long flops = 0;
     ProdStage st;
     if (pcnt > 0) prefetch_producer(a, Lside, 0, sa, cnt, s0, b, sxs, sxe, pbJ, pny, poff, pxv, pyv, pyp, st);
@@ -377,9 +441,10 @@ __device__ void phase_B_tile(const FactorArgs &a, int K, bool Lside, int sa, int
         // the next producer's panels load while this one is multiplied
         if (t + 1 < pcnt) prefetch_producer(a, Lside, t + 1, sa, cnt, s0, b, sxs, sxe, pbJ, pny, poff, pxv, pyv, pyp, st);
         if (nx > 0) {
-            flops += 2LL * nx * ny * bJ;
             for (int e = tid; e < nx * ny; e += NT) {
                 const int x = e / ny, y = e - x * ny;
+                if (bound && !act[xl[x]]) continue;
+                flops += 2LL * bJ;
                 const double *xr = Xs + x * PS, *yr = Ys + y * PS;
                 // four independent partial sums: a dependent FP64 FMA takes ~64 cycles here
                 double s0a = 0.0, s1a = 0.0, s2a = 0.0, s3a = 0.0;
@@ -398,9 +463,25 @@ __device__ void phase_B_tile(const FactorArgs &a, int K, bool Lside, int sa, int
     }
     double *out = (Lside ? a.TL : a.TU) + (int64_t)sa * b;
     for (int e = tid; e < cnt * b; e += NT) out[e] = T[e];
-    if (tid == 0 && flops)
-        atomicAdd((unsigned long long *)(a.info + (Lside ? INFO_FLOP_UPD_L : INFO_FLOP_UPD_U)),
-                  (unsigned long long)flops);
+    // per-thread counts of the products computed, summed over the CTA
+    {
+        long long f = flops;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(FULL_MASK, f, o);
+        __syncthreads();
+        long long *wsum = (long long *)Xs;  // staging area is free now
+        if (lane == 0) wsum[warp] = f;
+        __syncthreads();
+        if (tid == 0) {
+            long long tot = 0;
+            for (int w = 0; w < NW; ++w) tot += wsum[w];
+            if (tot) atomicAdd((unsigned long long *)(a.info + (Lside ? INFO_FLOP_UPD_L : INFO_FLOP_UPD_U)),
+                               (unsigned long long)tot);
+            if (bound && sskip[0])
+                atomicAdd((unsigned long long *)(a.info + (Lside ? INFO_SKIP_ROWS : INFO_SKIP_COLS)),
+                          (unsigned long long)sskip[0]);
+        }
+    }
 }
 
 // ---------------------------------------------------------------- phase C
@@ -628,6 +709,8 @@ __device__ void phase_C2(const FactorArgs &a, int K, char *smem) {
     double *D = a.Dinv + a.Dptr[K];
     if (lane < b) D[lane * b + c] = y0;
     if (lane + 32 < b) D[(lane + 32) * b + c] = y1;
+    const double csq = warp_sum((lane < b ? y0 * y0 : 0.0) + (lane + 32 < b ? y1 * y1 : 0.0));
+    if (lane == 0) a.dcolsq[c] = csq;
 }
 
 // ---------------------------------------------------------------- phase D
@@ -648,6 +731,7 @@ __device__ void phase_D(const FactorArgs &a, int K, char *smem) {
     for (int item = blockIdx.x * NW + warp; item < total; item += a.G * NW) {
         if (item < nLc) {
             const int slot = b + item;
+            if (a.skip_bound && ldcg(a.keepL + slot) < 0) continue;  // proved dropped
             double *t = a.TL + (int64_t)slot * b;
             const double t0 = lane < b ? ldcg(t + lane) : 0.0;
             const double t1 = lane + 32 < b ? ldcg(t + lane + 32) : 0.0;
@@ -669,9 +753,14 @@ __device__ void phase_D(const FactorArgs &a, int K, char *smem) {
             const double nrm2 = warp_sum(l0 * l0 + l1 * l1);
             if (lane < b) t[lane] = l0;
             if (lane + 32 < b) t[lane + 32] = l1;
-            if (lane == 0) a.keepL[slot] = sqrt(nrm2) > a.tau ? 1 : 0;
+            if (lane == 0) {
+                const double nr = sqrt(nrm2);
+                a.keepL[slot] = nr > a.tau ? 1 : 0;
+                a.nrmL[slot] = nr;
+            }
         } else {
             const int slot = item - nLc;
+            if (a.skip_bound && ldcg(a.keepU + slot) < 0) continue;  // proved dropped
             const double *t = a.TU + (int64_t)slot * b;
             const double t0 = lane < b ? ldcg(t + lane) : 0.0;
             const double t1 = lane + 32 < b ? ldcg(t + lane + 32) : 0.0;
@@ -691,7 +780,11 @@ __device__ void phase_D(const FactorArgs &a, int K, char *smem) {
             u0 += u0b;
             u1 += u1b;
             const double nrm2 = warp_sum(u0 * u0 + u1 * u1);
-            if (lane == 0) a.keepU[slot] = sqrt(nrm2) > a.tau ? 1 : 0;
+            const double tn2 = warp_sum(t0 * t0 + t1 * t1);
+            if (lane == 0) {
+                a.keepU[slot] = sqrt(nrm2) > a.tau ? 1 : 0;
+                a.nrmU[slot] = sqrt(tn2);  // norm of the stored (unnormalised) column
+            }
         }
     }
 }
@@ -718,8 +811,8 @@ __device__ void phase_E(const FactorArgs &a, int K, char *smem) {
     int keptL, keptU;
     {
         int lk = 0, uk = 0;
-        for (int s = tid; s < nLc; s += NT) lk += ldcg(a.keepL + b + s);
-        for (int s = tid; s < mU; s += NT) uk += ldcg(a.keepU + s);
+        for (int s = tid; s < nLc; s += NT) lk += ldcg(a.keepL + b + s) == 1;
+        for (int s = tid; s < mU; s += NT) uk += ldcg(a.keepU + s) == 1;
         block_excl_scan(lk, ws, &keptL);
         block_excl_scan(uk, ws, &keptU);
     }
@@ -750,6 +843,8 @@ __device__ void phase_E(const FactorArgs &a, int K, char *smem) {
         const double *Tb = isL ? a.TL : a.TU;
         double *pool = isL ? a.Lval + LVbase : a.Uval + UVbase;
         int32_t *idxpool = isL ? a.Lrow + Lbase : a.Ucol + Ubase;
+        double *nrmpool = isL ? a.Lnrm + Lbase : a.Unrm + Ubase;
+        const double *nrmslot = isL ? a.nrmL : a.nrmU;
         int32_t *last = isL ? a.lastU : a.lastL;
         int32_t *pc = isL ? a.prodUcnt : a.prodLcnt;
         int32_t *pl = isL ? a.prodU : a.prodL;
@@ -759,7 +854,7 @@ __device__ void phase_E(const FactorArgs &a, int K, char *smem) {
             // tile counts: one warp per tile, a ballot over its 32 keep flags
             for (int T = warp; T < cn; T += NW) {
                 const int sb = sfirst + (c0 + T) * 32, se = min(send, sb + 32);
-                const bool kept = sb + lane < se && ldcg(kp + sb + lane) != 0;
+                const bool kept = sb + lane < se && ldcg(kp + sb + lane) == 1;
                 const unsigned m = __ballot_sync(FULL_MASK, kept);
                 if (lane == 0) cnt[T] = __popc(m);
             }
@@ -771,7 +866,7 @@ __device__ void phase_E(const FactorArgs &a, int K, char *smem) {
             __syncthreads();
             for (int T = c0 + (int)blockIdx.x + warp * a.G; T < c0 + cn; T += a.G * NW) {
                 const int sb = sfirst + T * 32, se = min(send, sb + 32);
-                const bool kept = sb + lane < se && ldcg(kp + sb + lane) != 0;
+                const bool kept = sb + lane < se && ldcg(kp + sb + lane) == 1;
                 const unsigned m = __ballot_sync(FULL_MASK, kept);
                 const int nk = __popc(m);
                 const int64_t base = cnt[T - c0];
@@ -781,6 +876,7 @@ __device__ void phase_E(const FactorArgs &a, int K, char *smem) {
                     wsl[rank] = slot;
                     const int idx = ldcg(rows + slot);
                     idxpool[base + rank] = idx;
+                    nrmpool[base + rank] = ldcg(nrmslot + slot);
                     const int tb = a.blkof[idx];
                     if (atomicExch(last + tb, K) != K) {
                         const int pos = atomicAdd(pc + tb, 1);
@@ -822,12 +918,25 @@ __device__ __forceinline__ uint64_t gtimer() {
     return t;
 }
 
+__device__ __forceinline__ void red_add_release(uint32_t *p, uint32_t v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// One block step (per block K, five or six grid-barrier phases):
+//   A           candidate sets and update plans (CTA 0: L side, CTA 1: U side)
+//   B1 + C      pivot-row tiles (two rows each, every producer hits them) on CTAs 1.., then
+//               the pivot LU on CTA 0 as soon as those tiles are done, while the remaining
+//               update tiles run on the other CTAs (skipped here under the norm-bound skip)
+//   C2          D_K = P_K^{-1}
+//   Bs          (norm-bound skip only) the remaining update tiles, bound-tested
+//   D           scaling, norms, drop decisions
+//   E           compaction and producer lists
 __global__ void __launch_bounds__(NT, 1) bilu_factor_kernel(FactorArgs a) {
     extern __shared__ __align__(16) char smem[];
     const uint32_t G = a.G + a.debug_extra_cta;
-    // per-phase time of CTA 0 (ns, summed over the blocks): A, B, C, C2, D, E
+    // CTA 0 times (ns, summed over the blocks): A, B1+C, C2, Bs, D, E; LU work; pivot-tile wait
     uint64_t tacc[6] = {0, 0, 0, 0, 0, 0};
-    uint64_t tprev = gtimer(), tc2 = 0, tbw = 0;
+    uint64_t tprev = gtimer(), tlu = 0, twait = 0;
     auto lap = [&](int ph) {
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             const uint64_t t = gtimer();
@@ -835,8 +944,9 @@ __global__ void __launch_bounds__(NT, 1) bilu_factor_kernel(FactorArgs a) {
             tprev = t;
         }
     };
+    constexpr int TRP = 2;  // rows per pivot-row tile
     for (int K = 0; K < a.nb; ++K) {
-        // A: candidate sets (CTA 0: L side, CTA 1 % G: U side)
+        const int b = a.bstart[K + 1] - a.bstart[K];
         if (blockIdx.x == 0) phase_A(a, K, true, smem);
         if (blockIdx.x == (1 % a.G)) {
             __syncthreads();
@@ -844,33 +954,79 @@ __global__ void __launch_bounds__(NT, 1) bilu_factor_kernel(FactorArgs a) {
         }
         if (!grid_barrier(a.bar, G, a.status, a.spin_limit, a.info, 1)) return;
         lap(0);
-        // B: accumulation tiles
+        const int mL = ldcg(a.kst + 0), mU = ldcg(a.kst + 1);
+        const int nrestL = mL - b, nrest = nrestL + mU;
+        const int npt = (b + TRP - 1) / TRP;
         {
-            const int mL = ldcg(a.kst + 0), mU = ldcg(a.kst + 1);
-            int TR = (mL + mU + a.G - 1) / a.G;
+            const int W = a.G > 1 ? a.G - 1 : 1;  // CTAs taking tiles (CTA 0 factors the pivot block)
+            int TR = (nrest + W - 1) / W;
             TR = max(4, min(TRMAX, TR));
-            const int nLt = (mL + TR - 1) / TR, nUt = (mU + TR - 1) / TR;
-            for (int it = blockIdx.x; it < nLt + nUt; it += a.G) {
-                const bool Ls = it < nLt;
-                const int sa = (Ls ? it : it - nLt) * TR;
-                const int cnt = min(TR, (Ls ? mL : mU) - sa);
-                const uint64_t t0 = gtimer();
-                phase_B_tile(a, K, Ls, sa, cnt, smem);
+            const int nLt = (nrestL + TR - 1) / TR, nUt = (mU + TR - 1) / TR;
+            const int ntiles = npt + (a.skip_bound ? 0 : nLt + nUt);
+            if (a.G == 1 || blockIdx.x > 0) {
+                const int wid = a.G > 1 ? (int)blockIdx.x - 1 : 0;
+                for (int it = wid; it < ntiles; it += W) {
+                    if (it < npt) {
+                        const int sa = it * TRP;
+                        phase_B_tile(a, K, true, sa, min(TRP, b - sa), smem, false);
+                        __syncthreads();
+                        if (threadIdx.x == 0) red_add_release(a.pivdone, 1u);
+                    } else {
+                        const int r = it - npt;
+                        const bool Ls = r < nLt;
+                        const int sa = Ls ? b + r * TR : (r - nLt) * TR;
+                        const int cnt = Ls ? min(TR, mL - sa) : min(TR, mU - sa);
+                        phase_B_tile(a, K, Ls, sa, cnt, smem, false);
+                        __syncthreads();
+                    }
+                }
+            }
+            if (blockIdx.x == 0) {
+                __shared__ int s_go;
+                const uint64_t tw = gtimer();
+                if (threadIdx.x == 0) {
+                    int go = 1;
+                    if (a.G > 1) {
+                        long long itn = 0;
+                        while (ld_acquire_u32(a.pivdone) < (uint32_t)npt) {
+                            if (++itn > a.spin_limit) {
+                                if (atomicCAS(a.status, 0, DEV_TIMEOUT) == 0) a.info[INFO_TIMEOUT_SITE] = 7;
+                                go = 0;
+                                break;
+                            }
+                            if (itn > 64) __nanosleep(32);
+                        }
+                        atomicExch(a.pivdone, 0u);
+                    }
+                    s_go = go;
+                    twait += gtimer() - tw;
+                }
                 __syncthreads();
-                if (blockIdx.x == 0 && threadIdx.x == 0) tbw += gtimer() - t0;
+                if (s_go) {
+                    const uint64_t t0 = gtimer();
+                    phase_C(a, K, smem);
+                    if (threadIdx.x == 0) tlu += gtimer() - t0;
+                }
             }
         }
         if (!grid_barrier(a.bar, G, a.status, a.spin_limit, a.info, 2)) return;
         lap(1);
-        if (blockIdx.x == 0) phase_C(a, K, smem);
+        phase_C2(a, K, smem);
         if (!grid_barrier(a.bar, G, a.status, a.spin_limit, a.info, 3)) return;
         lap(2);
-        {
-            const uint64_t t0 = gtimer();
-            phase_C2(a, K, smem);
-            if (blockIdx.x == 0 && threadIdx.x == 0) tc2 += gtimer() - t0;
+        if (a.skip_bound) {
+            int TR = (nrest + a.G - 1) / a.G;
+            TR = max(4, min(TRMAX, TR));
+            const int nLt = (nrestL + TR - 1) / TR, nUt = (mU + TR - 1) / TR;
+            for (int it = blockIdx.x; it < nLt + nUt; it += a.G) {
+                const bool Ls = it < nLt;
+                const int sa = Ls ? b + it * TR : (it - nLt) * TR;
+                const int cnt = Ls ? min(TR, mL - sa) : min(TR, mU - sa);
+                phase_B_tile(a, K, Ls, sa, cnt, smem, true);
+                __syncthreads();
+            }
+            if (!grid_barrier(a.bar, G, a.status, a.spin_limit, a.info, 4)) return;
         }
-        if (!grid_barrier(a.bar, G, a.status, a.spin_limit, a.info, 4)) return;
         lap(3);
         phase_D(a, K, smem);
         if (!grid_barrier(a.bar, G, a.status, a.spin_limit, a.info, 5)) return;
@@ -879,11 +1035,10 @@ __global__ void __launch_bounds__(NT, 1) bilu_factor_kernel(FactorArgs a) {
         if (!grid_barrier(a.bar, G, a.status, a.spin_limit, a.info, 6)) return;
         lap(5);
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0)
-    {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
         for (int p = 0; p < 6; ++p) a.info[INFO_PHASE_NS + p] = (int64_t)tacc[p];
-        a.info[INFO_C2_WORK_NS] = (int64_t)tc2;
-        a.info[INFO_B_WORK_NS] = (int64_t)tbw;
+        a.info[INFO_C2_WORK_NS] = (int64_t)tlu;
+        a.info[INFO_B_WORK_NS] = (int64_t)twait;
     }
 }
 
@@ -928,6 +1083,8 @@ void factor_free(bilu_ctx *c) {
     dev_free(c->d_info); dev_free(c->d_bar);
     dev_free(c->d_wbL); dev_free(c->d_wbU); dev_free(c->d_xslotL); dev_free(c->d_xslotU);
     dev_free(c->d_pinfoL); dev_free(c->d_pinfoU);
+    dev_free(c->d_Lnrm); dev_free(c->d_Unrm); dev_free(c->d_nrmL); dev_free(c->d_nrmU);
+    dev_free(c->d_dcolsq); dev_free(c->d_pivdone);
     c->capLrow = c->capLval = c->capUcol = c->capUval = 0;
 }
 
@@ -936,6 +1093,9 @@ namespace {
 cudaError_t alloc_pools(bilu_ctx *c) {
     cudaError_t e;
     dev_free(c->d_Lrow); dev_free(c->d_Ucol); dev_free(c->d_Lval); dev_free(c->d_Uval);
+    dev_free(c->d_Lnrm); dev_free(c->d_Unrm);
+    if ((e = dev_alloc(&c->d_Lnrm, c->capLrow)) != cudaSuccess) return e;
+    if ((e = dev_alloc(&c->d_Unrm, c->capUcol)) != cudaSuccess) return e;
     if ((e = dev_alloc(&c->d_Lrow, c->capLrow)) != cudaSuccess) return e;
     if ((e = dev_alloc(&c->d_Ucol, c->capUcol)) != cudaSuccess) return e;
     if ((e = dev_alloc(&c->d_Lval, c->capLval)) != cudaSuccess) return e;
@@ -985,7 +1145,10 @@ bilu_status factor_alloc(bilu_ctx *c) {
         (e = dev_alloc(&c->d_LU, BILU_MAX_BLOCK * BILU_MAX_BLOCK + BILU_MAX_BLOCK)) != cudaSuccess ||
         (e = dev_alloc(&c->d_perm, BILU_MAX_BLOCK)) != cudaSuccess || (e = dev_alloc(&c->d_kstate, 16)) != cudaSuccess ||
         (e = dev_alloc(&c->d_status, 4)) != cudaSuccess || (e = dev_alloc(&c->d_info, INFO_COUNT)) != cudaSuccess ||
-        (e = dev_alloc(&c->d_bar, 4)) != cudaSuccess || (e = alloc_pools(c)) != cudaSuccess ||
+        (e = dev_alloc(&c->d_bar, 4)) != cudaSuccess || (e = dev_alloc(&c->d_nrmL, c->capT)) != cudaSuccess ||
+        (e = dev_alloc(&c->d_nrmU, c->capT)) != cudaSuccess ||
+        (e = dev_alloc(&c->d_dcolsq, BILU_MAX_BLOCK)) != cudaSuccess ||
+        (e = dev_alloc(&c->d_pivdone, 4)) != cudaSuccess || (e = alloc_pools(c)) != cudaSuccess ||
         (e = alloc_prod(c)) != cudaSuccess) {
         factor_free(c);
         return e == cudaErrorMemoryAllocation ? set_err(c, BILU_ERR_OOM, "device allocation failed in factor")
@@ -1026,6 +1189,7 @@ bilu_status factor_run(bilu_ctx *c, double droptol) {
         BILU_CUDA(c, cudaMemsetAsync(c->d_status, 0, 4 * sizeof(int32_t), c->stream));
         BILU_CUDA(c, cudaMemsetAsync(c->d_info, 0, INFO_COUNT * sizeof(int64_t), c->stream));
         BILU_CUDA(c, cudaMemsetAsync(c->d_bar, 0, 4 * sizeof(uint32_t), c->stream));
+        BILU_CUDA(c, cudaMemsetAsync(c->d_pivdone, 0, 4 * sizeof(uint32_t), c->stream));
 
         FactorArgs a{};
         a.n = (int32_t)c->n; a.nb = c->nb; a.G = G; a.perturb = c->p.perturb;
@@ -1047,6 +1211,9 @@ bilu_status factor_run(bilu_ctx *c, double droptol) {
         a.LU = c->d_LU; a.perm = c->d_perm; a.kst = c->d_kstate; a.status = c->d_status; a.info = c->d_info;
         a.bar = c->d_bar;
         a.debug_extra_cta = g_debug_extra_cta;
+        a.skip_bound = c->p.skip == BILU_SKIP_BOUND ? 1 : 0;
+        a.Lnrm = c->d_Lnrm; a.Unrm = c->d_Unrm; a.nrmL = c->d_nrmL; a.nrmU = c->d_nrmU;
+        a.dcolsq = c->d_dcolsq; a.pivdone = c->d_pivdone;
 
         void *args[] = {&a};
         BILU_CUDA(c, cudaEventRecord(e0, c->stream));
@@ -1102,6 +1269,8 @@ bilu_status factor_run(bilu_ctx *c, double droptol) {
         for (int p = 0; p < 6; ++p) c->phase_ms[p] = info[INFO_PHASE_NS + p] * 1e-6;
         c->phase_ms[6] = info[INFO_C2_WORK_NS] * 1e-6;
         c->phase_ms[7] = info[INFO_B_WORK_NS] * 1e-6;
+        c->skipped_rows = info[INFO_SKIP_ROWS];
+        c->skipped_cols = info[INFO_SKIP_COLS];
         double f_lu = 0.0;  // getrf (2/3 b^3) and inverse (4/3 b^3) per diagonal block
         for (int32_t K = 0; K < c->nb; ++K) {
             const double b = c->h_bstart[K + 1] - c->h_bstart[K];

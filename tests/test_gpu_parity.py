@@ -222,3 +222,20 @@ def test_newton_reciprocal_within_one_ulp_of_ieee(ctx):
     """The kernels replace FP64 divisions on critical paths by a Newton-Raphson reciprocal;
     it must stay within one ulp of CUDA's IEEE quotient."""
     B.bilu_debug_set(ctx, B.BILU_DEBUG_SELFTEST_RECIP, 1 << 20)
+
+
+@pytest.mark.parametrize("side,blk", [(16, 16), (20, 40), (24, 64)])
+def test_norm_bound_skip_gives_identical_factor(ctx, side, blk):
+    """BILU_SKIP_BOUND skips the products of candidate rows / columns that the triangle
+    inequality proves dropped (||l_i|| <= ||T_L[i,:]|| ||D_K||_F <= tau); the factor is the
+    same bit for bit, and the skip does fire on these stencils."""
+    A = W.convdiff_upwind((side, side, side), seed=1)
+    g0 = gpu_factor(ctx, A, 1e-2, _fixed(blk))
+    p = _fixed(blk)
+    p.skip = B.BILU_SKIP_BOUND
+    g1 = gpu_factor(ctx, A, 1e-2, p)
+    for f in ("Lptr", "Lrow", "Lval", "Uptr", "Ucol", "Uval", "Dinv", "Pblk"):
+        assert np.array_equal(getattr(g0, f), getattr(g1, f)), f
+    assert g1.stats.skipped_rows + g1.stats.skipped_cols > 0
+    assert g1.stats.flop_upd_l + g1.stats.flop_upd_u < g0.stats.flop_upd_l + g0.stats.flop_upd_u
+    compare_factors(_oracle(A, g1.bstart, 1e-2), g1)
