@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--side", type=int, default=64)
     ap.add_argument("--block", type=int, default=64)
+    ap.add_argument("--precision", choices=["fp64", "fp32", "bf16"], default="fp64")
+    ap.add_argument("--skip", choices=["none", "bound"], default="none")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -61,6 +63,7 @@ def workload(side, block):
 def config(args, w, extra=None):
     c = {"workload": f"cd3d_7pt_upwind_{args.side}^3", "n": w.A.n, "nnz": w.A.nnz, "droptol": w.droptol,
          "blocking": f"fixed {args.block}", "gmres": f"GMRES({w.restart}) rtol {w.gmres_tol}, x0 = 0, b = A*1",
+         "updates": getattr(args, "precision", "fp64"), "skip": getattr(args, "skip", "none"),
          "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{args.gpus}"}
     if extra:
         c.update(extra)
@@ -216,7 +219,10 @@ def run_gpu(args):
     w = workload(args.side, args.block)
     stream = torch.cuda.Stream(device=dev)
     ctx = B.bilu_create(local, stream)
-    params = B.bilu_params_default(blocking=B.BILU_BLOCKING_FIXED, fixed_block=args.block, max_block=64)
+    params = B.bilu_params_default(blocking=B.BILU_BLOCKING_FIXED, fixed_block=args.block, max_block=64,
+                                   precision={"fp64": B.BILU_PREC_FP64, "fp32": B.BILU_PREC_FP32,
+                                              "bf16": B.BILU_PREC_BF16}[args.precision],
+                                   skip={"none": B.BILU_SKIP_NONE, "bound": B.BILU_SKIP_BOUND}[args.skip])
     rp = torch.from_numpy(w.A.rowptr.astype(np.int64)).to(dev)
     ci = torch.from_numpy(w.A.colind.astype(np.int32)).to(dev)
     va = torch.from_numpy(w.A.val).to(dev)
@@ -291,7 +297,8 @@ def run_gpu(args):
     a1.synchronize()
     t_apply = a0.elapsed_time(a1) / napply
     n = w.A.n
-    apply_bytes = 8 * (st.nnz_l + st.nnz_u + st.nnz_d) + 4 * (st.kept_rows + st.kept_cols) + 8 * 3 * n
+    vbytes = {"fp64": 8, "fp32": 4, "bf16": 2}[args.precision]
+    apply_bytes = vbytes * (st.nnz_l + st.nnz_u) + 8 * st.nnz_d + 4 * (st.kept_rows + st.kept_cols) + 8 * 3 * n
     factor_tf = st.flops_factor / (t_factor * 1e-3) / 1e12
     apply_gbs = apply_bytes / (t_apply * 1e-3) / 1e9
     peaks = {}
@@ -356,7 +363,8 @@ def run_gpu(args):
     if rank == 0:
         line = {"metric": METRIC, "value": ms / 1e3 / world, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32+f64", "bf16": "bf16+f32+f64"}[args.precision],
+                "data": "synthetic",
                 "config": config(args, w, {"gmres_iters": iters, "gmres_restarts": restarts,
                                            "relres_true": relres, "factor_ms": t_factor,
                                            "solve_ms": statistics.median(ts), "apply_ms": t_apply,

@@ -22,7 +22,8 @@ struct ApplyArgs {
     const int32_t *bstart, *blkof;
     const int64_t *Lptr, *Lvptr, *Uptr, *Uvptr, *Dptr;
     const int32_t *Lrow, *Ucol;
-    const double *Lval, *Uval, *Dinv;
+    const void *Lval, *Uval;  // factor values, storage type TS of the kernel instance
+    const double *Dinv;
     const int32_t *prodU, *prodUcnt;
     int32_t prodcap;
     const int2 *planF;     // per (K, t): L_J rows inside B_K
@@ -59,6 +60,7 @@ __global__ void __launch_bounds__(32) apply_begin_kernel(int32_t *st, const int3
 // the rows are then summed over the producers in increasing J (fixed order).
 constexpr int FCH = 32;  // producers per chunk
 
+template <class TS>
 __global__ void __launch_bounds__(AT) apply_forward_kernel(ApplyArgs a) {
     if (a.skip && ldcg(a.skip)) return;
     __shared__ double acc[BILU_MAX_BLOCK];
@@ -112,10 +114,10 @@ __global__ void __launch_bounds__(AT) apply_forward_kernel(ApplyArgs a) {
                         int t = 0;
                         while (soff[t + 1] <= it) ++t;
                         const int bJ = sbJ[t];
-                        const double *row = a.Lval + sLv[t] + (int64_t)(it - soff[t]) * bJ;
+                        const TS *row = (const TS *)a.Lval + sLv[t] + (int64_t)(it - soff[t]) * bJ;
                         const double *yJ = a.z + ssJ[t];
-                        if (lane < bJ) v[u] = row[lane] * ldcg(yJ + lane);
-                        if (lane + 32 < bJ) v[u] = fma(row[lane + 32], ldcg(yJ + lane + 32), v[u]);
+                        if (lane < bJ) v[u] = dval(row[lane]) * ldcg(yJ + lane);
+                        if (lane + 32 < bJ) v[u] = fma(dval(row[lane + 32]), ldcg(yJ + lane + 32), v[u]);
                         tt[u] = t;
                         pp[u] = sps[t] + (it - soff[t]);
                     }
@@ -143,6 +145,7 @@ __global__ void __launch_bounds__(AT) apply_forward_kernel(ApplyArgs a) {
     }
 }
 
+template <class TS>
 __global__ void __launch_bounds__(AT) apply_backward_kernel(ApplyArgs a) {
     if (a.skip && ldcg(a.skip)) return;
     __shared__ double part[AT / BILU_MAX_BLOCK][BILU_MAX_BLOCK];
@@ -183,13 +186,13 @@ __global__ void __launch_bounds__(AT) apply_backward_kernel(ApplyArgs a) {
         const int g = tid / BILU_MAX_BLOCK, rr = tid % BILU_MAX_BLOCK;
         double s = 0.0;
         if (rr < b) {
-            const double *Uv = a.Uval + a.Uvptr[K];
+            const TS *Uv = (const TS *)a.Uval + a.Uvptr[K];
             int64_t q = q0 + g;
             // four independent columns per iteration keep several loads in flight
             double s1 = 0.0, s2 = 0.0, s3 = 0.0;
             for (; q + 3 * NG < q1; q += 4 * NG) {
-                const double u0 = Uv[(q - q0) * b + rr], u1 = Uv[(q + NG - q0) * b + rr];
-                const double u2 = Uv[(q + 2 * NG - q0) * b + rr], u3 = Uv[(q + 3 * NG - q0) * b + rr];
+                const double u0 = dval(Uv[(q - q0) * b + rr]), u1 = dval(Uv[(q + NG - q0) * b + rr]);
+                const double u2 = dval(Uv[(q + 2 * NG - q0) * b + rr]), u3 = dval(Uv[(q + 3 * NG - q0) * b + rr]);
                 const double z0 = ldcg(a.z + a.Ucol[q]), z1 = ldcg(a.z + a.Ucol[q + NG]);
                 const double z2 = ldcg(a.z + a.Ucol[q + 2 * NG]), z3 = ldcg(a.z + a.Ucol[q + 3 * NG]);
                 s = fma(u0, z0, s);
@@ -197,7 +200,7 @@ __global__ void __launch_bounds__(AT) apply_backward_kernel(ApplyArgs a) {
                 s2 = fma(u2, z2, s2);
                 s3 = fma(u3, z3, s3);
             }
-            for (; q < q1; q += NG) s = fma(Uv[(q - q0) * b + rr], ldcg(a.z + a.Ucol[q]), s);
+            for (; q < q1; q += NG) s = fma(dval(Uv[(q - q0) * b + rr]), ldcg(a.z + a.Ucol[q]), s);
             s = (s + s1) + (s2 + s3);
         }
         part[g][rr] = s;
@@ -305,8 +308,16 @@ bilu_status apply_launch(bilu_ctx *c, const double *d_r, double *d_z, const int3
     a.skip = skip;
     const int G = c->nsm * 2;
     apply_begin_kernel<<<1, 32, 0, c->stream>>>(c->d_apst, skip);
-    apply_forward_kernel<<<G, AT, 0, c->stream>>>(a);
-    apply_backward_kernel<<<G, AT, 0, c->stream>>>(a);
+    if (c->p.precision == BILU_PREC_FP32) {
+        apply_forward_kernel<float><<<G, AT, 0, c->stream>>>(a);
+        apply_backward_kernel<float><<<G, AT, 0, c->stream>>>(a);
+    } else if (c->p.precision == BILU_PREC_BF16) {
+        apply_forward_kernel<__nv_bfloat16><<<G, AT, 0, c->stream>>>(a);
+        apply_backward_kernel<__nv_bfloat16><<<G, AT, 0, c->stream>>>(a);
+    } else {
+        apply_forward_kernel<double><<<G, AT, 0, c->stream>>>(a);
+        apply_backward_kernel<double><<<G, AT, 0, c->stream>>>(a);
+    }
     c->launches += 3;
     BILU_CUDA(c, cudaGetLastError());
     return BILU_OK;

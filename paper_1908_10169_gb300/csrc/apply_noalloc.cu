@@ -222,6 +222,8 @@ extern "C" bilu_status bilu_apply_noalloc(bilu_ctx *c, const double *r, double *
     if (c->n == 0) return BILU_OK;
     if (!r || !z) return set_err(c, BILU_ERR_ARG, "null vector");
     if (r == z) return set_err(c, BILU_ERR_ARG, "r and z must not overlap");
+    if (c->p.precision != BILU_PREC_FP64)
+        return set_err(c, BILU_ERR_ARG, "bilu_apply_noalloc serves FP64 factors (use bilu_apply)");
     if (c->nb > NA_MAX_BLOCKS)
         return set_err(c, BILU_ERR_ARG, "bilu_apply_noalloc serves at most 65536 diagonal blocks; this factor has " +
                                             std::to_string(c->nb) + " (use bilu_apply)");

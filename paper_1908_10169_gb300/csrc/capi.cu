@@ -2,6 +2,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "bilu_internal.h"
 
@@ -103,8 +104,8 @@ bilu_status bilu_factor(bilu_ctx *c, double droptol) {
     c->err.clear();
     if (c->state < 1) return set_err(c, BILU_ERR_STATE, "bilu_factor before bilu_analyze");
     if (!(droptol >= 0.0) || !std::isfinite(droptol)) return set_err(c, BILU_ERR_ARG, "droptol must be finite and >= 0");
-    if (c->p.precision != BILU_PREC_FP64 || c->p.skip == BILU_SKIP_LEARNED)
-        return set_err(c, BILU_ERR_ARG, "precision / skip mode not available in this build");
+    if (c->p.skip == BILU_SKIP_LEARNED)
+        return set_err(c, BILU_ERR_ARG, "skip mode not available in this build");
     BILU_CUDA(c, cudaSetDevice(c->device));
     c->state = 1;
     gmres_free(c);  // captured graphs refer to the previous factor
@@ -219,8 +220,37 @@ bilu_status bilu_export(bilu_ctx *c, int64_t *Lptr, int32_t *Lrow, double *Lval,
     BILU_CUDA(c, cp(Uptr, c->d_Uptr, nb1 * sizeof(int64_t)));
     BILU_CUDA(c, cp(Lrow, c->d_Lrow, c->kept_rows * sizeof(int32_t)));
     BILU_CUDA(c, cp(Ucol, c->d_Ucol, c->kept_cols * sizeof(int32_t)));
-    BILU_CUDA(c, cp(Lval, c->d_Lval, c->nnz_l * sizeof(double)));
-    BILU_CUDA(c, cp(Uval, c->d_Uval, c->nnz_u * sizeof(double)));
+    if (c->p.precision == BILU_PREC_FP64) {
+        BILU_CUDA(c, cp(Lval, c->d_Lval, c->nnz_l * sizeof(double)));
+        BILU_CUDA(c, cp(Uval, c->d_Uval, c->nnz_u * sizeof(double)));
+    } else {
+        // reduced-precision storage: widen to FP64 on the host
+        const bool f32 = c->p.precision == BILU_PREC_FP32;
+        const size_t es = f32 ? 4 : 2;
+        auto widen = [&](double *dst, const void *src, int64_t cnt) -> cudaError_t {
+            if (!dst || cnt <= 0) return cudaSuccess;
+            std::vector<unsigned char> tmp((size_t)cnt * es);
+            cudaError_t e = cudaMemcpy(tmp.data(), src, tmp.size(), cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return e;
+            for (int64_t i = 0; i < cnt; ++i) {
+                if (f32) {
+                    float v;
+                    std::memcpy(&v, tmp.data() + i * 4, 4);
+                    dst[i] = v;
+                } else {
+                    uint16_t h;
+                    std::memcpy(&h, tmp.data() + i * 2, 2);
+                    const uint32_t w = (uint32_t)h << 16;
+                    float v;
+                    std::memcpy(&v, &w, 4);
+                    dst[i] = v;
+                }
+            }
+            return cudaSuccess;
+        };
+        BILU_CUDA(c, widen(Lval, c->d_Lval, c->nnz_l));
+        BILU_CUDA(c, widen(Uval, c->d_Uval, c->nnz_u));
+    }
     BILU_CUDA(c, cp(Dinv, c->d_Dinv, nd * sizeof(double)));
     BILU_CUDA(c, cp(Pblk, c->d_Pblk, nd * sizeof(double)));
     return BILU_OK;

@@ -2,6 +2,7 @@
 // reductions / scans, a bounded grid barrier for cooperative persistent kernels.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -15,6 +16,11 @@ template <class T>
 __device__ __forceinline__ T ldcg(const T *p) {
     return __ldcg(p);
 }
+
+// factor values of any storage precision, widened to FP64
+__device__ __forceinline__ double dval(double v) { return v; }
+__device__ __forceinline__ double dval(float v) { return (double)v; }
+__device__ __forceinline__ double dval(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
 
 __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
     uint32_t v;

@@ -20,9 +20,38 @@
 #include <cmath>
 #include <cstring>
 
+#include <cuda_bf16.h>
+
 #include "dev_common.cuh"
 
 namespace {
+
+// Value types of one kernel instance: TS stores the L / U-breve values, TA accumulates the
+// updates and the scaling.  FP64: double/double; FP32: float/float; BF16: bf16 storage with
+// FP32 accumulation.  The pivot LU, the inverse D_K and the drop norms are always FP64.
+template <class TS> struct Prec;
+template <> struct Prec<double> { using TA = double; };
+template <> struct Prec<float> { using TA = float; };
+template <> struct Prec<__nv_bfloat16> { using TA = float; };
+
+__device__ __forceinline__ double to_acc_d(double v) { return v; }
+__device__ __forceinline__ float to_acc_f(float v) { return v; }
+__device__ __forceinline__ float to_acc_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <class TA, class TS> __device__ __forceinline__ TA acc_of(TS v);
+template <> __device__ __forceinline__ double acc_of<double, double>(double v) { return v; }
+template <> __device__ __forceinline__ float acc_of<float, float>(float v) { return v; }
+template <> __device__ __forceinline__ float acc_of<float, __nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <class TS> __device__ __forceinline__ TS store_of(double v);
+template <> __device__ __forceinline__ double store_of<double>(double v) { return v; }
+template <> __device__ __forceinline__ float store_of<float>(double v) { return (float)v; }
+template <> __device__ __forceinline__ __nv_bfloat16 store_of<__nv_bfloat16>(double v) { return __float2bfloat16((float)v); }
+
+// L2 loads of data written by other CTAs during the launch, for every value type
+__device__ __forceinline__ double ldv(const double *p) { return __ldcg(p); }
+__device__ __forceinline__ float ldv(const float *p) { return __ldcg(p); }
+__device__ __forceinline__ __nv_bfloat16 ldv(const __nv_bfloat16 *p) {
+    return __ushort_as_bfloat16(__ldcg((const unsigned short *)p));
+}
 
 constexpr int NT = 512;          // threads per CTA
 constexpr int NW = NT / 32;      // warps per CTA
@@ -40,11 +69,12 @@ struct FactorArgs {
     const int64_t *Dptr;
     int64_t *Lptr, *Lvptr, *Uptr, *Uvptr;
     int32_t *Lrow, *Ucol;
-    double *Lval, *Uval, *Dinv, *Pblk;
+    void *Lval, *Uval;           // factor values, storage type TS of the kernel instance
+    double *Dinv, *Pblk;
     int64_t capLrow, capLval, capUcol, capUval;
     int32_t prodcap;
     int32_t *prodL, *prodLcnt, *prodU, *prodUcnt, *lastL, *lastU;
-    double *TL, *TU;
+    void *TL, *TU;               // candidate accumulators, type TA of the kernel instance
     int32_t *rowsL, *rowsU, *keepL, *keepU;
     uint32_t *bmL, *bmU;
     int32_t *wbL, *wbU;          // bitmap word prefix counts
@@ -266,24 +296,27 @@ __device__ void phase_A(const FactorArgs &a, int K, bool Lside, char *smem) {
 // is multiplied, the X rows and Y rows of producer t+1 are already loading into registers.
 constexpr int PF = (TRMAX * BILU_MAX_BLOCK + BILU_MAX_BLOCK * BILU_MAX_BLOCK + NT - 1) / NT;
 
+template <class TA>
 struct ProdStage {
     int nx, ny, bJ;
-    double v[PF];
+    TA v[PF];
     int xl, yc;
 };
 
+template <class TS>
 __device__ __forceinline__ void prefetch_producer(const FactorArgs &a, bool Lside, int t, int sa, int cnt, int s0,
                                                   int b, const int32_t *sxs, const int32_t *sxe,
                                                   const int32_t *pbJ, const int32_t *pny, const int32_t *poff,
                                                   const int64_t *pxv, const int64_t *pyv, const int32_t *pyp,
-                                                  ProdStage &st) {
+                                                  ProdStage<typename Prec<TS>::TA> &st) {
+    using TA = typename Prec<TS>::TA;
     const int tid = threadIdx.x;
     st.nx = sxe[t] - sxs[t];
     st.ny = pny[t];
     st.bJ = pbJ[t];
     if (st.nx <= 0 || st.ny <= 0) { st.nx = 0; return; }
-    const double *Xpool = Lside ? a.Lval : a.Uval;
-    const double *Ypool = Lside ? a.Uval : a.Lval;
+    const TS *Xpool = (const TS *)(Lside ? a.Lval : a.Uval);
+    const TS *Ypool = (const TS *)(Lside ? a.Uval : a.Lval);
     const int32_t *Yidx = Lside ? a.Ucol : a.Lrow;
     const int32_t *xslot = Lside ? a.xslotL : a.xslotU;
     const int nxv = st.nx * st.bJ, tot = nxv + st.ny * st.bJ;
@@ -291,7 +324,8 @@ __device__ __forceinline__ void prefetch_producer(const FactorArgs &a, bool Lsid
 #pragma unroll
     for (int k = 0; k < PF; ++k) {
         const int e = tid + k * NT;
-        st.v[k] = e < nxv ? ldcg(Xpool + xval + e) : (e < tot ? ldcg(Ypool + yval + (e - nxv)) : 0.0);
+        st.v[k] = e < nxv ? acc_of<TA, TS>(ldv(Xpool + xval + e))
+                          : (e < tot ? acc_of<TA, TS>(ldv(Ypool + yval + (e - nxv))) : TA(0));
     }
     st.xl = tid < st.nx ? ldcg(xslot + poff[t] + sxs[t] + tid) - sa : 0;
     st.yc = (tid >= 64 && tid - 64 < st.ny) ? ldcg(Yidx + pyp[t] + (tid - 64)) - s0 : 0;
@@ -301,12 +335,14 @@ __device__ __forceinline__ void prefetch_producer(const FactorArgs &a, bool Lsid
 // gets an upper bound of ||T[i,:]||: ||A part|| + sum_J ||X row of J|| * ||Y block of J||_F.
 // Rows with bound * ||D_K||_F <= tau (1 - 1e-10) are provably dropped (||l_i|| <= ||T[i,:]||
 // ||D_K||_2): their products and scaling are skipped and their keep flag is set to -1.
+template <class TS>
 __device__ void phase_B_tile(const FactorArgs &a, int K, bool Lside, int sa, int cnt, char *smem, bool bound) {
+    using TA = typename Prec<TS>::TA;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int s0 = a.bstart[K], s1 = a.bstart[K + 1], b = s1 - s0;
-    double *T = (double *)smem;                  // TRMAX * 64
-    double *Xs = T + TRMAX * BILU_MAX_BLOCK;     // TRMAX * PS
-    double *Ys = Xs + TRMAX * PS;                // 64 * PS
+    TA *T = (TA *)smem;                          // TRMAX * 64
+    TA *Xs = T + TRMAX * BILU_MAX_BLOCK;         // TRMAX * PS
+    TA *Ys = Xs + TRMAX * PS;                    // 64 * PS
     int64_t *pxv = (int64_t *)(Ys + BILU_MAX_BLOCK * PS);  // PMAX: X value offset
     int64_t *pyv = pxv + PMAX;                   // PMAX: Y value offset
     int32_t *g = (int32_t *)(pyv + PMAX);        // TRMAX
@@ -360,12 +396,12 @@ __device__ void phase_B_tile(const FactorArgs &a, int K, bool Lside, int sa, int
         if (Lside) {
             for (int e = a.rowptr[idx] + lane; e < a.rowptr[idx + 1]; e += 32) {
                 const int c = a.colind[e];
-                if (c >= s0 && c < s1) { const double v = a.val[e]; T[r * b + (c - s0)] = v; sq = fma(v, v, sq); }
+                if (c >= s0 && c < s1) { const double v = a.val[e]; T[r * b + (c - s0)] = (TA)v; sq = fma(v, v, sq); }
             }
         } else {
             for (int e = a.colptr[idx] + lane; e < a.colptr[idx + 1]; e += 32) {
                 const int rr = a.rowind[e];
-                if (rr >= s0 && rr < s1) { const double v = a.cval[e]; T[r * b + (rr - s0)] = v; sq = fma(v, v, sq); }
+                if (rr >= s0 && rr < s1) { const double v = a.cval[e]; T[r * b + (rr - s0)] = (TA)v; sq = fma(v, v, sq); }
             }
         }
         if (bound) {
@@ -404,8 +440,8 @@ __device__ void phase_B_tile(const FactorArgs &a, int K, bool Lside, int sa, int
         __syncthreads();
     }
     long long flops = 0;
-    ProdStage st;
-    if (pcnt > 0) prefetch_producer(a, Lside, 0, sa, cnt, s0, b, sxs, sxe, pbJ, pny, poff, pxv, pyv, pyp, st);
+    ProdStage<TA> st;
+    if (pcnt > 0) prefetch_producer<TS>(a, Lside, 0, sa, cnt, s0, b, sxs, sxe, pbJ, pny, poff, pxv, pyv, pyp, st);
     for (int t = 0; t < pcnt; ++t) {
         const int nx = st.nx, ny = st.ny, bJ = st.bJ;
         if (nx > 0) {
@@ -439,15 +475,15 @@ __device__ void phase_B_tile(const FactorArgs &a, int K, bool Lside, int sa, int
         }
         __syncthreads();
         // the next producer's panels load while this one is multiplied
-        if (t + 1 < pcnt) prefetch_producer(a, Lside, t + 1, sa, cnt, s0, b, sxs, sxe, pbJ, pny, poff, pxv, pyv, pyp, st);
+        if (t + 1 < pcnt) prefetch_producer<TS>(a, Lside, t + 1, sa, cnt, s0, b, sxs, sxe, pbJ, pny, poff, pxv, pyv, pyp, st);
         if (nx > 0) {
             for (int e = tid; e < nx * ny; e += NT) {
                 const int x = e / ny, y = e - x * ny;
                 if (bound && !act[xl[x]]) continue;
                 flops += 2LL * bJ;
-                const double *xr = Xs + x * PS, *yr = Ys + y * PS;
+                const TA *xr = Xs + x * PS, *yr = Ys + y * PS;
                 // four independent partial sums: a dependent FP64 FMA takes ~64 cycles here
-                double s0a = 0.0, s1a = 0.0, s2a = 0.0, s3a = 0.0;
+                TA s0a = 0, s1a = 0, s2a = 0, s3a = 0;
                 int k = 0;
                 for (; k + 3 < bJ; k += 4) {
                     s0a = fma(xr[k], yr[k], s0a);
@@ -461,7 +497,7 @@ __device__ void phase_B_tile(const FactorArgs &a, int K, bool Lside, int sa, int
         }
         __syncthreads();
     }
-    double *out = (Lside ? a.TL : a.TU) + (int64_t)sa * b;
+    TA *out = (TA *)(Lside ? a.TL : a.TU) + (int64_t)sa * b;
     for (int e = tid; e < cnt * b; e += NT) out[e] = T[e];
     // per-thread counts of the products computed, summed over the CTA
     {
@@ -544,7 +580,9 @@ __device__ __forceinline__ void lu_pivot_column(double *M, const int32_t *phys_i
     }
 }
 
+template <class TS>
 __device__ void phase_C(const FactorArgs &a, int K, char *smem) {
+    using TA = typename Prec<TS>::TA;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int s0 = a.bstart[K], s1 = a.bstart[K + 1], b = s1 - s0;
     double *P = (double *)smem;                 // b x b (stride PS), current P (perturbed)
@@ -556,7 +594,7 @@ __device__ void phase_C(const FactorArgs &a, int K, char *smem) {
     unsigned long long *smax = (unsigned long long *)(sh + 4);
     for (int e = tid; e < b * b; e += NT) {
         const int r = e / b, c = e - r * b;
-        P[r * PS + c] = ldcg(a.TL + (int64_t)r * b + c);
+        P[r * PS + c] = (double)ldv((const TA *)a.TL + (int64_t)r * b + c);
     }
     if (tid == 0) sh[2] = 0;
     __syncthreads();
@@ -715,42 +753,44 @@ __device__ void phase_C2(const FactorArgs &a, int K, char *smem) {
 
 // ---------------------------------------------------------------- phase D
 // Normalised rows l_i = T_L[i,:] D_K and columns u^_j = D_K T_U[:,j]; keep iff ||.||_2 > tau.
+template <class TS>
 __device__ void phase_D(const FactorArgs &a, int K, char *smem) {
+    using TA = typename Prec<TS>::TA;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int s0 = a.bstart[K], s1 = a.bstart[K + 1], b = s1 - s0;
     const int mL = ldcg(a.kst + 0), mU = ldcg(a.kst + 1);
     const int nLc = mL - b, total = nLc + mU;
     if (blockIdx.x * NW >= total) return;
-    double *Ds = (double *)smem;
+    TA *Ds = (TA *)smem;
     const double *D = a.Dinv + a.Dptr[K];
     for (int e = tid; e < b * b; e += NT) {
         const int r = e / b, c = e - r * b;
-        Ds[r * PS + c] = ldcg(D + e);
+        Ds[r * PS + c] = (TA)ldcg(D + e);
     }
     __syncthreads();
     for (int item = blockIdx.x * NW + warp; item < total; item += a.G * NW) {
         if (item < nLc) {
             const int slot = b + item;
             if (a.skip_bound && ldcg(a.keepL + slot) < 0) continue;  // proved dropped
-            double *t = a.TL + (int64_t)slot * b;
-            const double t0 = lane < b ? ldcg(t + lane) : 0.0;
-            const double t1 = lane + 32 < b ? ldcg(t + lane + 32) : 0.0;
-            double l0 = 0.0, l1 = 0.0, l0b = 0.0, l1b = 0.0;
+            TA *t = (TA *)a.TL + (int64_t)slot * b;
+            const TA t0 = lane < b ? ldv(t + lane) : TA(0);
+            const TA t1 = lane + 32 < b ? ldv(t + lane + 32) : TA(0);
+            TA l0 = 0, l1 = 0, l0b = 0, l1b = 0;
             int k = 0;
             for (; k + 1 < b; k += 2) {
-                const double tk = __shfl_sync(FULL_MASK, k < 32 ? t0 : t1, k & 31);
-                const double tk1 = __shfl_sync(FULL_MASK, k + 1 < 32 ? t0 : t1, (k + 1) & 31);
+                const TA tk = __shfl_sync(FULL_MASK, k < 32 ? t0 : t1, k & 31);
+                const TA tk1 = __shfl_sync(FULL_MASK, k + 1 < 32 ? t0 : t1, (k + 1) & 31);
                 if (lane < b) { l0 = fma(tk, Ds[k * PS + lane], l0); l0b = fma(tk1, Ds[(k + 1) * PS + lane], l0b); }
                 if (lane + 32 < b) { l1 = fma(tk, Ds[k * PS + lane + 32], l1); l1b = fma(tk1, Ds[(k + 1) * PS + lane + 32], l1b); }
             }
             if (k < b) {
-                const double tk = __shfl_sync(FULL_MASK, k < 32 ? t0 : t1, k & 31);
+                const TA tk = __shfl_sync(FULL_MASK, k < 32 ? t0 : t1, k & 31);
                 if (lane < b) l0 = fma(tk, Ds[k * PS + lane], l0);
                 if (lane + 32 < b) l1 = fma(tk, Ds[k * PS + lane + 32], l1);
             }
             l0 += l0b;
             l1 += l1b;
-            const double nrm2 = warp_sum(l0 * l0 + l1 * l1);
+            const double nrm2 = warp_sum((double)l0 * (double)l0 + (double)l1 * (double)l1);
             if (lane < b) t[lane] = l0;
             if (lane + 32 < b) t[lane + 32] = l1;
             if (lane == 0) {
@@ -761,26 +801,26 @@ __device__ void phase_D(const FactorArgs &a, int K, char *smem) {
         } else {
             const int slot = item - nLc;
             if (a.skip_bound && ldcg(a.keepU + slot) < 0) continue;  // proved dropped
-            const double *t = a.TU + (int64_t)slot * b;
-            const double t0 = lane < b ? ldcg(t + lane) : 0.0;
-            const double t1 = lane + 32 < b ? ldcg(t + lane + 32) : 0.0;
-            double u0 = 0.0, u1 = 0.0, u0b = 0.0, u1b = 0.0;
+            const TA *t = (const TA *)a.TU + (int64_t)slot * b;
+            const TA t0 = lane < b ? ldv(t + lane) : TA(0);
+            const TA t1 = lane + 32 < b ? ldv(t + lane + 32) : TA(0);
+            TA u0 = 0, u1 = 0, u0b = 0, u1b = 0;
             int k = 0;
             for (; k + 1 < b; k += 2) {
-                const double tk = __shfl_sync(FULL_MASK, k < 32 ? t0 : t1, k & 31);
-                const double tk1 = __shfl_sync(FULL_MASK, k + 1 < 32 ? t0 : t1, (k + 1) & 31);
+                const TA tk = __shfl_sync(FULL_MASK, k < 32 ? t0 : t1, k & 31);
+                const TA tk1 = __shfl_sync(FULL_MASK, k + 1 < 32 ? t0 : t1, (k + 1) & 31);
                 if (lane < b) { u0 = fma(Ds[lane * PS + k], tk, u0); u0b = fma(Ds[lane * PS + k + 1], tk1, u0b); }
                 if (lane + 32 < b) { u1 = fma(Ds[(lane + 32) * PS + k], tk, u1); u1b = fma(Ds[(lane + 32) * PS + k + 1], tk1, u1b); }
             }
             if (k < b) {
-                const double tk = __shfl_sync(FULL_MASK, k < 32 ? t0 : t1, k & 31);
+                const TA tk = __shfl_sync(FULL_MASK, k < 32 ? t0 : t1, k & 31);
                 if (lane < b) u0 = fma(Ds[lane * PS + k], tk, u0);
                 if (lane + 32 < b) u1 = fma(Ds[(lane + 32) * PS + k], tk, u1);
             }
             u0 += u0b;
             u1 += u1b;
-            const double nrm2 = warp_sum(u0 * u0 + u1 * u1);
-            const double tn2 = warp_sum(t0 * t0 + t1 * t1);
+            const double nrm2 = warp_sum((double)u0 * (double)u0 + (double)u1 * (double)u1);
+            const double tn2 = warp_sum((double)t0 * (double)t0 + (double)t1 * (double)t1);
             if (lane == 0) {
                 a.keepU[slot] = sqrt(nrm2) > a.tau ? 1 : 0;
                 a.nrmU[slot] = sqrt(tn2);  // norm of the stored (unnormalised) column
@@ -795,7 +835,9 @@ __device__ void phase_D(const FactorArgs &a, int K, char *smem) {
 // A ballot ranks the tile's kept slots; the metadata of all kept slots is handled lane-
 // parallel and their rows are copied by one flat loop, so the loads are issued together.
 // Every CTA with a tile computes the tile prefix sums itself (no extra barrier).
+template <class TS>
 __device__ void phase_E(const FactorArgs &a, int K, char *smem) {
+    using TA = typename Prec<TS>::TA;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int s0 = a.bstart[K], s1 = a.bstart[K + 1], b = s1 - s0;
     const int mL = ldcg(a.kst + 0), mU = ldcg(a.kst + 1);
@@ -840,8 +882,8 @@ __device__ void phase_E(const FactorArgs &a, int K, char *smem) {
         const int sfirst = isL ? b : 0, send = isL ? mL : mU;
         const int32_t *kp = isL ? a.keepL : a.keepU;
         const int32_t *rows = isL ? a.rowsL : a.rowsU;
-        const double *Tb = isL ? a.TL : a.TU;
-        double *pool = isL ? a.Lval + LVbase : a.Uval + UVbase;
+        const TA *Tb = (const TA *)(isL ? a.TL : a.TU);
+        TS *pool = (TS *)(isL ? a.Lval : a.Uval) + (isL ? LVbase : UVbase);
         int32_t *idxpool = isL ? a.Lrow + Lbase : a.Ucol + Ubase;
         double *nrmpool = isL ? a.Lnrm + Lbase : a.Unrm + Ubase;
         const double *nrmslot = isL ? a.nrmL : a.nrmU;
@@ -888,20 +930,20 @@ __device__ void phase_E(const FactorArgs &a, int K, char *smem) {
                 // copy the nk kept rows (b values each), four elements in flight per lane
                 const int tot_e = nk * b;
                 for (int e0 = lane; e0 < tot_e; e0 += 128) {
-                    double v[4];
+                    TA v[4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         const int e = e0 + u * 32;
-                        v[u] = 0.0;
+                        v[u] = 0;
                         if (e < tot_e) {
                             const int r = e / b, cc = e - r * b;
-                            v[u] = ldcg(Tb + (int64_t)wsl[r] * b + cc);
+                            v[u] = ldv(Tb + (int64_t)wsl[r] * b + cc);
                         }
                     }
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         const int e = e0 + u * 32;
-                        if (e < tot_e) pool[(base + e / b) * b + (e % b)] = v[u];
+                        if (e < tot_e) pool[(base + e / b) * b + (e % b)] = store_of<TS>((double)v[u]);
                     }
                 }
                 __syncwarp();
@@ -931,6 +973,7 @@ __device__ __forceinline__ void red_add_release(uint32_t *p, uint32_t v) {
 //   Bs          (norm-bound skip only) the remaining update tiles, bound-tested
 //   D           scaling, norms, drop decisions
 //   E           compaction and producer lists
+template <class TS>
 __global__ void __launch_bounds__(NT, 1) bilu_factor_kernel(FactorArgs a) {
     extern __shared__ __align__(16) char smem[];
     const uint32_t G = a.G + a.debug_extra_cta;
@@ -968,7 +1011,7 @@ __global__ void __launch_bounds__(NT, 1) bilu_factor_kernel(FactorArgs a) {
                 for (int it = wid; it < ntiles; it += W) {
                     if (it < npt) {
                         const int sa = it * TRP;
-                        phase_B_tile(a, K, true, sa, min(TRP, b - sa), smem, false);
+                        phase_B_tile<TS>(a, K, true, sa, min(TRP, b - sa), smem, false);
                         __syncthreads();
                         if (threadIdx.x == 0) red_add_release(a.pivdone, 1u);
                     } else {
@@ -976,7 +1019,7 @@ __global__ void __launch_bounds__(NT, 1) bilu_factor_kernel(FactorArgs a) {
                         const bool Ls = r < nLt;
                         const int sa = Ls ? b + r * TR : (r - nLt) * TR;
                         const int cnt = Ls ? min(TR, mL - sa) : min(TR, mU - sa);
-                        phase_B_tile(a, K, Ls, sa, cnt, smem, false);
+                        phase_B_tile<TS>(a, K, Ls, sa, cnt, smem, false);
                         __syncthreads();
                     }
                 }
@@ -1004,7 +1047,7 @@ __global__ void __launch_bounds__(NT, 1) bilu_factor_kernel(FactorArgs a) {
                 __syncthreads();
                 if (s_go) {
                     const uint64_t t0 = gtimer();
-                    phase_C(a, K, smem);
+                    phase_C<TS>(a, K, smem);
                     if (threadIdx.x == 0) tlu += gtimer() - t0;
                 }
             }
@@ -1022,16 +1065,16 @@ __global__ void __launch_bounds__(NT, 1) bilu_factor_kernel(FactorArgs a) {
                 const bool Ls = it < nLt;
                 const int sa = Ls ? b + it * TR : (it - nLt) * TR;
                 const int cnt = Ls ? min(TR, mL - sa) : min(TR, mU - sa);
-                phase_B_tile(a, K, Ls, sa, cnt, smem, true);
+                phase_B_tile<TS>(a, K, Ls, sa, cnt, smem, true);
                 __syncthreads();
             }
             if (!grid_barrier(a.bar, G, a.status, a.spin_limit, a.info, 4)) return;
         }
         lap(3);
-        phase_D(a, K, smem);
+        phase_D<TS>(a, K, smem);
         if (!grid_barrier(a.bar, G, a.status, a.spin_limit, a.info, 5)) return;
         lap(4);
-        phase_E(a, K, smem);
+        phase_E<TS>(a, K, smem);
         if (!grid_barrier(a.bar, G, a.status, a.spin_limit, a.info, 6)) return;
         lap(5);
     }
@@ -1165,9 +1208,13 @@ bilu_status factor_run(bilu_ctx *c, double droptol) {
         bilu_status st = factor_alloc(c);
         if (st != BILU_OK) return st;
     }
-    BILU_CUDA(c, cudaFuncSetAttribute(bilu_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    // kernel instance by the precision of the updates and the stored factor values
+    const void *kfn = c->p.precision == BILU_PREC_FP32   ? (const void *)bilu_factor_kernel<float>
+                      : c->p.precision == BILU_PREC_BF16 ? (const void *)bilu_factor_kernel<__nv_bfloat16>
+                                                         : (const void *)bilu_factor_kernel<double>;
+    BILU_CUDA(c, cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
     int per_sm = 0;
-    BILU_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bilu_factor_kernel, NT, SMEM_BYTES));
+    BILU_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, NT, SMEM_BYTES));
     if (per_sm < 1) return set_err(c, BILU_ERR_CUDA, "factor kernel cannot be resident");
     const int G = c->nsm;  // one CTA per SM
 
@@ -1218,7 +1265,7 @@ bilu_status factor_run(bilu_ctx *c, double droptol) {
         void *args[] = {&a};
         BILU_CUDA(c, cudaEventRecord(e0, c->stream));
         if (c->nb > 0) {
-            BILU_CUDA(c, cudaLaunchCooperativeKernel((void *)bilu_factor_kernel, dim3(G), dim3(NT), args,
+            BILU_CUDA(c, cudaLaunchCooperativeKernel(kfn, dim3(G), dim3(NT), args,
                                                      SMEM_BYTES, c->stream));
             c->launches += 1;
         }

@@ -239,3 +239,49 @@ def test_norm_bound_skip_gives_identical_factor(ctx, side, blk):
     assert g1.stats.skipped_rows + g1.stats.skipped_cols > 0
     assert g1.stats.flop_upd_l + g1.stats.flop_upd_u < g0.stats.flop_upd_l + g0.stats.flop_upd_u
     compare_factors(_oracle(A, g1.bstart, 1e-2), g1)
+
+
+def _rel_err_common(Fo, g):
+    """Max relative error of L / U-breve values over the blocks whose kept sets agree with the
+    oracle, and the number of blocks whose kept sets differ."""
+    from tests.gpu_helpers import _vptr
+    oLv, oUv, gLv, gUv = Fo.Lvptr(), Fo.Uvptr(), _vptr(g.Lptr, g.bstart), _vptr(g.Uptr, g.bstart)
+    err, differ = 0.0, 0
+    for K in range(len(Fo.bstart) - 1):
+        ro, rg = Fo.Lrow[Fo.Lptr[K]:Fo.Lptr[K + 1]], g.Lrow[g.Lptr[K]:g.Lptr[K + 1]]
+        co, cg = Fo.Ucol[Fo.Uptr[K]:Fo.Uptr[K + 1]], g.Ucol[g.Uptr[K]:g.Uptr[K + 1]]
+        if not (np.array_equal(ro, rg) and np.array_equal(co, cg)):
+            differ += 1
+            continue
+        for a, bb in ((Fo.Lval[oLv[K]:oLv[K + 1]], g.Lval[gLv[K]:gLv[K + 1]]),
+                      (Fo.Uval[oUv[K]:oUv[K + 1]], g.Uval[gUv[K]:gUv[K + 1]])):
+            if a.size:
+                err = max(err, float(np.abs(a - bb).max() / np.abs(a).max()))
+    return err, differ
+
+
+@pytest.mark.parametrize("prec,bound,max_differ", [(B.BILU_PREC_FP32, 1e-5, 0.05), (B.BILU_PREC_BF16, 1e-1, 1.0)])
+def test_mixed_precision_factor_and_gmres(ctx, prec, bound, max_differ):
+    """Updates and scaling in FP32 (or BF16 storage with FP32 accumulation); pivot LU, inverse,
+    drop norms and GMRES in FP64.  GMRES(30) reaches 1e-8 within 10 % of the FP64 iterations;
+    the factor's error against the FP64 oracle is bounded by the storage precision (BF16 rounds
+    at 2^-9 relative, and the rounding of earlier blocks enters later ones through the updates,
+    so the bound is 10 %).  With BF16 the rounding moves many rows across the drop threshold,
+    so the kept sets of later blocks differ from the oracle's; only FP32 bounds that count."""
+    import torch
+    A = W.convdiff_upwind((20, 20, 20), seed=1)
+    b = W.rhs_ones(A)
+    g64 = gpu_factor(ctx, A, 1e-2, _fixed(20), export=False)
+    bt = torch.from_numpy(b).cuda()
+    x64 = torch.zeros_like(bt)
+    it64 = B.gmres_solve(ctx, bt, x64, 1e-8, 30, 10000).iters
+    p = _fixed(20)
+    p.precision = prec
+    g = gpu_factor(ctx, A, 1e-2, p)
+    xm = torch.zeros_like(bt)
+    info = B.gmres_solve(ctx, bt, xm, 1e-8, 30, 10000)
+    assert info.status == B.BILU_OK and info.relres_true <= 1e-8
+    assert info.iters <= 1.1 * it64 + 1, (info.iters, it64)
+    err, differ = _rel_err_common(_oracle(A, g.bstart, 1e-2), g)
+    assert err <= bound, err
+    assert differ <= max_differ * (len(g.bstart) - 1), differ
