@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--block", type=int, default=64)
     ap.add_argument("--precision", choices=["fp64", "fp32", "bf16"], default="fp64")
     ap.add_argument("--skip", choices=["none", "bound"], default="none")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="factor + solve this many uneven 2D/3D matrices in one batched launch instead")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -383,10 +385,107 @@ def run_gpu(args):
     return 0
 
 
+def run_batch(args):
+    """Batched workload: `args.batch` uneven convection-diffusion matrices (2D 5-point and 3D
+    7-point, n log-uniform in [1e4, 2e5]) factored in one persistent launch and solved with one
+    graph per restart cycle; compared with factoring and solving them one by one."""
+    import numpy as np
+    import torch
+
+    import paper_1908_10169_gb300 as B
+    from paper_1908_10169_gb300 import workloads as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    t_start = time.time()
+
+    def progress(msg):
+        print(f"[batch {time.time() - t_start:7.1f} s] {msg}", file=sys.stderr, flush=True)
+
+    ws = W.cd_batch(count=args.batch, seed0=100)
+    prec = {"fp64": B.BILU_PREC_FP64, "fp32": B.BILU_PREC_FP32, "bf16": B.BILU_PREC_BF16}[args.precision]
+    stream = torch.cuda.Stream(device=dev)
+    ctxs, bs, xs = [], [], []
+    for w in ws:
+        c = B.bilu_create(local, stream if not ctxs else None)
+        B.bilu_analyze(c, w.A.n, torch.from_numpy(w.A.rowptr).to(dev), torch.from_numpy(w.A.colind).to(dev),
+                       torch.from_numpy(w.A.val).to(dev),
+                       B.bilu_params_default(fixed_block=w.fixed_block, max_block=64, precision=prec))
+        ctxs.append(c)
+        bs.append(torch.from_numpy(w.b).to(dev))
+        xs.append(torch.zeros(w.A.n, dtype=torch.float64, device=dev))
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    progress(f"{len(ws)} systems analysed")
+
+    def step():
+        B.bilu_factor_batch(ctxs, 1e-2)
+        for x in xs:
+            x.zero_()
+        torch.cuda.synchronize()
+        return B.gmres_solve_batch(ctxs, bs, xs, 1e-8, 30, 10000)
+
+    for k in range(max(3, args.warmup)):  # the group size is tuned on the second call
+        infos = step()
+        progress(f"warm-up step {k} done, GMRES iterations max {max(i.iters for i in infos)}")
+    l0 = sum(B.bilu_stats(c).kernel_launches for c in ctxs)
+    times = []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            infos = step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+            progress(f"timed step: {times[-1]:.1f} ms")
+    launches = (sum(B.bilu_stats(c).kernel_launches for c in ctxs) - l0) / args.steps
+    ms = sum(times) / len(times)
+    iters_b = [i.iters for i in infos]
+    # the same systems one by one, plain FP64
+    t_seq, iters_s = 0.0, []
+    one = B.bilu_create(local, stream)
+    for w, bvec in zip(ws, bs):
+        B.bilu_analyze(one, w.A.n, torch.from_numpy(w.A.rowptr).to(dev), torch.from_numpy(w.A.colind).to(dev),
+                       torch.from_numpy(w.A.val).to(dev), B.bilu_params_default(fixed_block=w.fixed_block, max_block=64))
+        x = torch.zeros_like(bvec)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        B.bilu_factor(one, 1e-2)
+        iters_s.append(B.gmres_solve(one, bvec, x, 1e-8, 30, 10000).iters)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_seq += e0.elapsed_time(e1)
+        progress(f"one by one: {w.name} {e0.elapsed_time(e1):.1f} ms")
+    B.bilu_destroy(one)
+    for c in ctxs:
+        B.bilu_destroy(c)
+    line = {"metric": f"batched BILU factor+GMRES seconds for {len(ws)} systems to rel. residual 1e-8",
+            "value": ms / 1e3, "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup),
+            "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp32": "f32+f64", "bf16": "bf16+f32+f64"}[args.precision], "data": "synthetic",
+            "config": {"workload": f"cd_batch_{len(ws)}", "sum_n": int(sum(w.A.n for w in ws)),
+                       "n_range": [int(min(w.A.n for w in ws)), int(max(w.A.n for w in ws))],
+                       "updates": args.precision, "gmres_iters_batched": iters_b, "gmres_iters_plain_fp64": iters_s,
+                       "max_iter_ratio": max(a / max(1, b2) for a, b2 in zip(iters_b, iters_s)),
+                       "plain_fp64_one_by_one_s": t_seq / 1e3, "speedup_vs_plain_one_by_one": t_seq / ms,
+                       "l2": "flushed (512 MB write) before every timed step"},
+            "gpu_launches": launches, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.batch:
+        return run_batch(args)
     return run_gpu(args)
 
 

@@ -160,6 +160,29 @@ bilu_status bilu_apply(bilu_ctx *ctx, const double *r, double *z);
 bilu_status gmres_solve(bilu_ctx *ctx, const double *b, double *x, double tol, int32_t restart,
                         int32_t maxit, gmres_info *info);
 
+/*
+ * Batched factorization of many independent matrices in one persistent launch.  Every
+ * context holds one analysed matrix (bilu_analyze); all must live on the same device and
+ * share precision, skip and perturbation settings; work is issued on ctxs[0]'s stream.
+ * The grid is split into groups of CTAs; each group takes the next matrix from a device
+ * work queue (largest first) and runs the block recurrence of Algorithm 1 (Sec. 2.2) on
+ * it.  The group size is tuned by timing candidates on the second call for a given (matrix
+ * count, largest block, precision) and cached; the first call uses a size from the count.  Each context ends as after bilu_factor on it;
+ * statuses as bilu_factor (the worst one is returned, details in bilu_last_error of ctxs[0]).
+ * Allocates and frees small device buffers per call.  Synchronizes the device.
+ */
+bilu_status bilu_factor_batch(bilu_ctx *const *ctxs, int32_t count, double droptol);
+
+/*
+ * Restarted GMRES(restart) on the systems of a batch (Sec. 4), as gmres_solve on each
+ * context: b[i], x[i] (device or host) of ctxs[i]'s size; info (count entries) may be NULL.
+ * One CUDA graph holds a restart cycle of every system as a parallel branch; converged
+ * systems are stopped between cycles.  Returns BILU_NOT_CONVERGED if any system did not
+ * converge within maxit inner steps.  Work on ctxs[0]'s stream; synchronizes it.
+ */
+bilu_status gmres_solve_batch(bilu_ctx *const *ctxs, int32_t count, const double *const *b, double *const *x,
+                              double tol, int32_t restart, int32_t maxit, gmres_info *info);
+
 /* Statistics of the last analysis / factorization (fill, block sizes, work). */
 bilu_status bilu_stats(bilu_ctx *ctx, bilu_stats_t *out);
 
@@ -191,8 +214,22 @@ const char *bilu_last_error(const bilu_ctx *ctx);
  *   BILU_DEBUG_SELFTEST_RECIP (value = sample count): checks the kernels' Newton-Raphson
  *       reciprocal against the IEEE quotient 1/p on that many values over 200 binades;
  *       BILU_OK when every result is within one ulp.
+ *   BILU_DEBUG_BATCH_GROUP (value >= 0): bilu_factor_batch uses groups of this many CTAs
+ *       (capped at the SM count) instead of the tuned size; 0 restores tuning.
+ *   BILU_DEBUG_SMALL_POOLS (value 0/1): factor storage allocated from then on starts at
+ *       1024 entries per pool and 4 producers per block, so that the factorization runs
+ *       again with grown storage several times (the result does not change).
+ *   BILU_DEBUG_POISON (value 0/1): every factorization first fills the factor's value
+ *       arrays and work arrays with NaN, so that a value the kernels fail to write shows.
  */
-enum { BILU_DEBUG_EXTRA_CTA = 1, BILU_DEBUG_SPIN_LIMIT = 2, BILU_DEBUG_SELFTEST_RECIP = 3 };
+enum {
+    BILU_DEBUG_EXTRA_CTA = 1,
+    BILU_DEBUG_SPIN_LIMIT = 2,
+    BILU_DEBUG_SELFTEST_RECIP = 3,
+    BILU_DEBUG_BATCH_GROUP = 4,
+    BILU_DEBUG_SMALL_POOLS = 5,
+    BILU_DEBUG_POISON = 6
+};
 bilu_status bilu_debug_set(bilu_ctx *ctx, int32_t what, int64_t value);
 
 /*

@@ -21,13 +21,15 @@ BILU_ERR_ARG, BILU_ERR_OOM, BILU_ERR_CUDA, BILU_ERR_SINGULAR, BILU_ERR_TIMEOUT, 
 BILU_BLOCKING_FIXED, BILU_BLOCKING_ILU1T = 0, 1
 BILU_PREC_FP64, BILU_PREC_FP32, BILU_PREC_BF16 = 0, 1, 2
 BILU_SKIP_NONE, BILU_SKIP_BOUND, BILU_SKIP_LEARNED = 0, 1, 2
-BILU_DEBUG_EXTRA_CTA, BILU_DEBUG_SPIN_LIMIT, BILU_DEBUG_SELFTEST_RECIP = 1, 2, 3
+(BILU_DEBUG_EXTRA_CTA, BILU_DEBUG_SPIN_LIMIT, BILU_DEBUG_SELFTEST_RECIP, BILU_DEBUG_BATCH_GROUP,
+ BILU_DEBUG_SMALL_POOLS, BILU_DEBUG_POISON) = 1, 2, 3, 4, 5, 6
 BILU_MAX_BLOCK = 64
 
 # every extern "C" symbol that include/bilu.h declares
 EXPORTED = ["bilu_params_default", "bilu_create", "bilu_analyze", "bilu_factor", "bilu_apply",
             "gmres_solve", "bilu_stats", "bilu_get_partition", "bilu_export", "bilu_last_error",
-            "bilu_debug_set", "bilu_apply_noalloc", "bilu_destroy"]
+            "bilu_debug_set", "bilu_apply_noalloc", "bilu_factor_batch", "gmres_solve_batch",
+            "bilu_destroy"]
 
 
 class bilu_params(ct.Structure):
@@ -84,6 +86,8 @@ def lib():
             "bilu_last_error": ([P], ct.c_char_p),
             "bilu_debug_set": ([P, i32, i64], i32),
             "bilu_apply_noalloc": ([P, P, P], i32),
+            "bilu_factor_batch": ([P, i32, f64], i32),
+            "gmres_solve_batch": ([P, i32, P, P, f64, i32, i32, P], i32),
             "bilu_destroy": ([P], None),
         }
         for name, (args, res) in sig.items():
@@ -172,6 +176,25 @@ def gmres_solve(ctx, b, x, tol: float = 1e-8, restart: int = 30, maxit: int = 10
     _check(ctx, st, (BILU_OK, BILU_NOT_CONVERGED))
     info.status = st
     return info
+
+
+def bilu_factor_batch(ctxs, droptol: float) -> int:
+    """Factor the analysed matrices of several contexts in one persistent launch."""
+    arr = (ct.c_void_p * len(ctxs))(*[c.value if hasattr(c, "value") else c for c in ctxs])
+    st = lib().bilu_factor_batch(arr, len(ctxs), droptol)
+    return _check(ctxs[0], st, (BILU_OK, BILU_PERTURBED))
+
+
+def gmres_solve_batch(ctxs, bs, xs, tol: float = 1e-8, restart: int = 30, maxit: int = 10000):
+    """GMRES on every system of a batch; returns the gmres_info of each system."""
+    n = len(ctxs)
+    arr = (ct.c_void_p * n)(*[c.value if hasattr(c, "value") else c for c in ctxs])
+    pb = (ct.c_void_p * n)(*[_ptr(v).value for v in bs])
+    px = (ct.c_void_p * n)(*[_ptr(v).value for v in xs])
+    infos = (gmres_info * n)()
+    st = lib().gmres_solve_batch(arr, n, pb, px, tol, restart, maxit, infos)
+    _check(ctxs[0], st, (BILU_OK, BILU_NOT_CONVERGED))
+    return list(infos)
 
 
 def bilu_stats(ctx) -> bilu_stats_t:

@@ -306,7 +306,7 @@ bilu_status apply_launch(bilu_ctx *c, const double *d_r, double *d_z, const int3
     a.flagB = c->d_flagB;
     a.st = c->d_apst;
     a.skip = skip;
-    const int G = c->nsm * 2;
+    const int G = c->apply_grid > 0 ? c->apply_grid : c->nsm * 2;
     apply_begin_kernel<<<1, 32, 0, c->stream>>>(c->d_apst, skip);
     if (c->p.precision == BILU_PREC_FP32) {
         apply_forward_kernel<float><<<G, AT, 0, c->stream>>>(a);

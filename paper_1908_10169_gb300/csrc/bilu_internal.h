@@ -44,6 +44,7 @@ struct bilu_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int nsm = 0;
+    int apply_grid = 0;  // CTAs of the apply sweeps (0: two per SM); batched solves use a share
     std::string err;
     int state = 0;  // 0 created, 1 analyzed, 2 factored
     bilu_params p{};
@@ -158,6 +159,9 @@ void apply_free(bilu_ctx *c);
 bilu_status gmres_run(bilu_ctx *c, const double *d_b, double *d_x, double tol, int restart,
                       int maxit, gmres_info *info);
 void gmres_free(bilu_ctx *c);
+bilu_status gmres_batch_run(bilu_ctx *const *ctxs, int count, const double *const *b, double *const *x, double tol,
+                            int m, int maxit, gmres_info *info);
+bilu_status factor_batch_run(bilu_ctx *const *ctxs, int count, double droptol, double *ms_out);
 bilu_status analyze_run(bilu_ctx *c, int64_t n, const int64_t *rowptr, const int32_t *colind,
                         const double *val, int on_device, const bilu_params *p);
 void matrix_free(bilu_ctx *c);

@@ -8,6 +8,9 @@
 
 extern int g_debug_extra_cta;
 extern long long g_debug_spin_limit;
+extern long long g_debug_batch_group;
+extern int g_debug_small_pools;
+extern int g_debug_poison;
 int recip_selftest(int n);
 
 bilu_status set_err(bilu_ctx *c, bilu_status st, const std::string &msg) {
@@ -158,6 +161,57 @@ bilu_status gmres_solve(bilu_ctx *c, const double *b, double *x, double tol, int
     return gmres_run(c, b, x, tol, restart, maxit, info);
 }
 
+bilu_status bilu_factor_batch(bilu_ctx *const *ctxs, int32_t count, double droptol) {
+    if (!ctxs || count < 1) return BILU_ERR_ARG;
+    bilu_ctx *c0 = ctxs[0];
+    if (!c0) return BILU_ERR_ARG;
+    for (int32_t i = 0; i < count; ++i) {
+        bilu_ctx *c = ctxs[i];
+        if (!c) return set_err(c0, BILU_ERR_ARG, "null context in batch");
+        c->err.clear();
+        if (c->state < 1) return set_err(c0, BILU_ERR_STATE, "bilu_factor_batch: a context has no analysis");
+        if (c->device != c0->device) return set_err(c0, BILU_ERR_ARG, "bilu_factor_batch: contexts on different devices");
+        if (c->p.precision != c0->p.precision || c->p.skip != c0->p.skip || c->p.perturb != c0->p.perturb)
+            return set_err(c0, BILU_ERR_ARG, "bilu_factor_batch: contexts need the same precision, skip and perturbation settings");
+        for (int32_t k = 0; k < i; ++k)
+            if (ctxs[k] == c) return set_err(c0, BILU_ERR_ARG, "bilu_factor_batch: a context appears twice");
+    }
+    if (!(droptol >= 0.0) || !std::isfinite(droptol)) return set_err(c0, BILU_ERR_ARG, "droptol must be finite and >= 0");
+    if (c0->p.skip == BILU_SKIP_LEARNED) return set_err(c0, BILU_ERR_ARG, "skip mode not available in this build");
+    BILU_CUDA(c0, cudaSetDevice(c0->device));
+    for (int32_t i = 0; i < count; ++i) {
+        ctxs[i]->state = 1;
+        gmres_free(ctxs[i]);
+    }
+    double ms = 0.0;
+    bilu_status st = factor_batch_run(ctxs, count, droptol, &ms);
+    if (st < 0) return st;
+    for (int32_t i = 0; i < count; ++i) {
+        bilu_status sa = apply_alloc(ctxs[i]);
+        if (sa != BILU_OK) return sa;
+    }
+    BILU_CUDA(c0, cudaDeviceSynchronize());
+    for (int32_t i = 0; i < count; ++i) ctxs[i]->state = 2;
+    return st;
+}
+
+bilu_status gmres_solve_batch(bilu_ctx *const *ctxs, int32_t count, const double *const *b, double *const *x,
+                              double tol, int32_t restart, int32_t maxit, gmres_info *info) {
+    if (!ctxs || count < 1 || !b || !x) return BILU_ERR_ARG;
+    bilu_ctx *c0 = ctxs[0];
+    if (!c0) return BILU_ERR_ARG;
+    for (int32_t i = 0; i < count; ++i) {
+        bilu_ctx *c = ctxs[i];
+        if (!c) return set_err(c0, BILU_ERR_ARG, "null context in batch");
+        if (c->state < 2) return set_err(c0, BILU_ERR_STATE, "gmres_solve_batch: a context has no factor");
+        if (c->device != c0->device) return set_err(c0, BILU_ERR_ARG, "gmres_solve_batch: contexts on different devices");
+        if (c->n == 0 || !b[i] || !x[i]) return set_err(c0, BILU_ERR_ARG, "gmres_solve_batch: empty system or null vector");
+    }
+    if (info) std::memset(info, 0, sizeof(gmres_info) * (size_t)count);
+    BILU_CUDA(c0, cudaSetDevice(c0->device));
+    return gmres_batch_run(ctxs, count, b, x, tol, restart, maxit, info);
+}
+
 bilu_status bilu_stats(bilu_ctx *c, bilu_stats_t *o) {
     if (!c || !o) return BILU_ERR_ARG;
     if (c->state < 1) return set_err(c, BILU_ERR_STATE, "no analysis");
@@ -261,6 +315,9 @@ bilu_status bilu_debug_set(bilu_ctx *c, int32_t what, int64_t value) {
     switch (what) {
         case BILU_DEBUG_EXTRA_CTA: g_debug_extra_cta = value ? 1 : 0; return BILU_OK;
         case BILU_DEBUG_SPIN_LIMIT: g_debug_spin_limit = value; return BILU_OK;
+        case BILU_DEBUG_BATCH_GROUP: g_debug_batch_group = value > 0 ? value : 0; return BILU_OK;
+        case BILU_DEBUG_SMALL_POOLS: g_debug_small_pools = value ? 1 : 0; return BILU_OK;
+        case BILU_DEBUG_POISON: g_debug_poison = value ? 1 : 0; return BILU_OK;
         case BILU_DEBUG_SELFTEST_RECIP: {
             cudaSetDevice(c->device);
             const int bad = recip_selftest((int)value);

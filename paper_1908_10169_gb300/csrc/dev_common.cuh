@@ -103,16 +103,27 @@ __device__ __forceinline__ int warp_lower_bound(const int32_t *a, int lo, int hi
 }
 
 // Bounded grid barrier for a cooperative launch of G CTAs.  bar[0] counts arrivals,
-// bar[1] is the generation.  A wait that exceeds spin_limit polls records DEV_TIMEOUT.
-// Returns false (uniformly in the CTA) when the device status word holds an error,
-// in which case the caller returns.
-__device__ __forceinline__ uint32_t atom_add_release_u32(uint32_t *p, uint32_t v) {
+// bar[1] is the generation, bar[2] the status word as the last arriving CTA read it.  Every
+// CTA takes its exit decision from that snapshot, so all of them leave at the same barrier
+// even when one CTA raises an error in the next phase while another is still on its way out
+// of this one.  A wait that exceeds spin_limit polls records DEV_TIMEOUT (after which the
+// barrier's state is undefined: a timeout ends the launch).  Returns false (uniformly in the
+// CTA, and across the CTAs) when the status snapshot holds an error.
+__device__ __forceinline__ uint32_t atom_add_acqrel_u32(uint32_t *p, uint32_t v) {
     uint32_t old;
-    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
     return old;
 }
 __device__ __forceinline__ void red_add_release_u32(uint32_t *p, uint32_t v) {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_u32(uint32_t *p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 __device__ __forceinline__ bool grid_barrier(uint32_t *bar, uint32_t G, int32_t *status,
@@ -122,11 +133,15 @@ __device__ __forceinline__ bool grid_barrier(uint32_t *bar, uint32_t G, int32_t 
     if (threadIdx.x == 0) {
         int ok = 1;
         const uint32_t gen = ld_acquire_u32(bar + 1);
-        // release: this CTA's writes (ordered before by __syncthreads) become visible first
-        const uint32_t arrived = atom_add_release_u32(bar, 1u);
+        // acq_rel: this CTA's writes (ordered before by __syncthreads) are released, and the
+        // last arriver acquires everything the others released, including their status writes
+        const uint32_t arrived = atom_add_acqrel_u32(bar, 1u);
         if (arrived == G - 1) {
+            const int32_t st = ld_acquire_s32(status);
+            st_relaxed_u32(bar + 2, (uint32_t)st);
             atomicExch(bar, 0u);
-            red_add_release_u32(bar + 1, 1u);
+            red_add_release_u32(bar + 1, 1u);  // publishes the snapshot with the new generation
+            ok = st == DEV_OK;
         } else {
             long long it = 0;
             while (ld_acquire_u32(bar + 1) == gen) {
@@ -137,8 +152,9 @@ __device__ __forceinline__ bool grid_barrier(uint32_t *bar, uint32_t G, int32_t 
                 }
                 if (it > 64) __nanosleep(32);
             }
+            // the snapshot cannot be overwritten before this CTA arrives at the next barrier
+            if (ok) ok = (int32_t)ld_relaxed_u32(bar + 2) == DEV_OK;
         }
-        if (ld_acquire_s32(status) != DEV_OK) ok = 0;
         s_ok = ok;
     }
     __syncthreads();

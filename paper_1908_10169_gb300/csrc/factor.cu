@@ -99,6 +99,10 @@ struct FactorArgs {
 // pinfo layout (per producer t of the current block)
 enum { PI_J = 0, PI_BJ, PI_XCNT, PI_YCNT, PI_OFF, PI_XPOS, PI_XVAL, PI_YVAL, PI_YPOS, PI_YF, PIS };
 
+// Rank of this CTA inside its group of a.G CTAs (the whole grid for one matrix; a slice of
+// the grid when a batch of matrices is factored in one launch).
+__device__ __forceinline__ int crank(const FactorArgs &a) { return (int)(blockIdx.x % (unsigned)a.G); }
+
 __device__ __forceinline__ double perturbed(double d, double ptau, double prho, double alpha) {
     // Sec. 3.6: d (1 + rho beta_j) + sign(d) tau alpha with beta_j := 1 and sign(0) := +1
     return d * (1.0 + prho) + (d >= 0.0 ? 1.0 : -1.0) * ptau * alpha;
@@ -708,12 +712,13 @@ __device__ void phase_C(const FactorArgs &a, int K, char *smem) {
 // ---------------------------------------------------------------- phase C2
 // Column c of D_K = P_K^{-1}: solve L U x = e_{perm^{-1}(c)} (P_K X = I), one warp per column.
 __device__ void phase_C2(const FactorArgs &a, int K, char *smem) {
-    // two columns per CTA (warps 0 and 1): the solves are chains of dependent FP64
-    // operations, so spreading the columns over many SMs shortens the phase
+    // The solves are chains of dependent FP64 operations, so the columns are spread over the
+    // group's CTAs: `per` columns per CTA and round (warps 0 .. per-1), at least two, and
+    // more (up to one per warp, then further rounds) when the group has fewer than b/2 CTAs.
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int s0 = a.bstart[K], s1 = a.bstart[K + 1], b = s1 - s0;
-    const int first = blockIdx.x * 2;
-    if (first >= b) return;
+    const int per = min(NW, max(2, (b + a.G - 1) / a.G));
+    if (crank(a) * per >= b) return;
     double *M = (double *)smem;
     int32_t *prm = (int32_t *)(M + BILU_MAX_BLOCK * PS);
     double *rdiag = (double *)(prm + BILU_MAX_BLOCK);
@@ -726,29 +731,30 @@ __device__ void phase_C2(const FactorArgs &a, int K, char *smem) {
         rdiag[i] = ldcg(a.LU + BILU_MAX_BLOCK * BILU_MAX_BLOCK + i);
     }
     __syncthreads();
-    const int c = first + warp;
-    if (warp >= 2 || c >= b) return;
-    // lane owns rows lane and lane + 32
-    double y0 = (lane < b && prm[lane] == c) ? 1.0 : 0.0;
-    double y1 = (lane + 32 < b && prm[lane + 32] == c) ? 1.0 : 0.0;
-    for (int k = 0; k < b; ++k) {  // forward, unit lower
-        const double yk = __shfl_sync(FULL_MASK, k < 32 ? y0 : y1, k & 31);
-        if (lane > k && lane < b) y0 -= M[lane * PS + k] * yk;
-        if (lane + 32 > k && lane + 32 < b) y1 -= M[(lane + 32) * PS + k] * yk;
-    }
-    for (int k = b - 1; k >= 0; --k) {  // backward, upper
-        double own = k < 32 ? y0 : y1;
-        if ((k & 31) == lane) own = own * rdiag[k];
-        const double xk = __shfl_sync(FULL_MASK, own, k & 31);
-        if (k < 32) { if (lane == k) y0 = xk; } else { if (lane + 32 == k) y1 = xk; }
-        if (lane < k) y0 -= M[lane * PS + k] * xk;
-        if (lane + 32 < k) y1 -= M[(lane + 32) * PS + k] * xk;
-    }
+    if (warp >= per) return;
     double *D = a.Dinv + a.Dptr[K];
-    if (lane < b) D[lane * b + c] = y0;
-    if (lane + 32 < b) D[(lane + 32) * b + c] = y1;
-    const double csq = warp_sum((lane < b ? y0 * y0 : 0.0) + (lane + 32 < b ? y1 * y1 : 0.0));
-    if (lane == 0) a.dcolsq[c] = csq;
+    for (int c = crank(a) * per + warp; c < b; c += a.G * per) {
+        // lane owns rows lane and lane + 32
+        double y0 = (lane < b && prm[lane] == c) ? 1.0 : 0.0;
+        double y1 = (lane + 32 < b && prm[lane + 32] == c) ? 1.0 : 0.0;
+        for (int k = 0; k < b; ++k) {  // forward, unit lower
+            const double yk = __shfl_sync(FULL_MASK, k < 32 ? y0 : y1, k & 31);
+            if (lane > k && lane < b) y0 -= M[lane * PS + k] * yk;
+            if (lane + 32 > k && lane + 32 < b) y1 -= M[(lane + 32) * PS + k] * yk;
+        }
+        for (int k = b - 1; k >= 0; --k) {  // backward, upper
+            double own = k < 32 ? y0 : y1;
+            if ((k & 31) == lane) own = own * rdiag[k];
+            const double xk = __shfl_sync(FULL_MASK, own, k & 31);
+            if (k < 32) { if (lane == k) y0 = xk; } else { if (lane + 32 == k) y1 = xk; }
+            if (lane < k) y0 -= M[lane * PS + k] * xk;
+            if (lane + 32 < k) y1 -= M[(lane + 32) * PS + k] * xk;
+        }
+        if (lane < b) D[lane * b + c] = y0;
+        if (lane + 32 < b) D[(lane + 32) * b + c] = y1;
+        const double csq = warp_sum((lane < b ? y0 * y0 : 0.0) + (lane + 32 < b ? y1 * y1 : 0.0));
+        if (lane == 0) a.dcolsq[c] = csq;
+    }
 }
 
 // ---------------------------------------------------------------- phase D
@@ -760,7 +766,7 @@ __device__ void phase_D(const FactorArgs &a, int K, char *smem) {
     const int s0 = a.bstart[K], s1 = a.bstart[K + 1], b = s1 - s0;
     const int mL = ldcg(a.kst + 0), mU = ldcg(a.kst + 1);
     const int nLc = mL - b, total = nLc + mU;
-    if (blockIdx.x * NW >= total) return;
+    if (crank(a) * NW >= total) return;
     TA *Ds = (TA *)smem;
     const double *D = a.Dinv + a.Dptr[K];
     for (int e = tid; e < b * b; e += NT) {
@@ -768,7 +774,7 @@ __device__ void phase_D(const FactorArgs &a, int K, char *smem) {
         Ds[r * PS + c] = (TA)ldcg(D + e);
     }
     __syncthreads();
-    for (int item = blockIdx.x * NW + warp; item < total; item += a.G * NW) {
+    for (int item = crank(a) * NW + warp; item < total; item += a.G * NW) {
         if (item < nLc) {
             const int slot = b + item;
             if (a.skip_bound && ldcg(a.keepL + slot) < 0) continue;  // proved dropped
@@ -843,7 +849,8 @@ __device__ void phase_E(const FactorArgs &a, int K, char *smem) {
     const int mL = ldcg(a.kst + 0), mU = ldcg(a.kst + 1);
     const int nLc = mL - b;
     const int tL = (nLc + 31) >> 5, tU = (mU + 31) >> 5;
-    const bool has_work = blockIdx.x == 0 || (int)blockIdx.x < max(tL, tU);
+    const int cr = crank(a);
+    const bool has_work = cr == 0 || cr < max(tL, tU);
     if (!has_work) return;
     int32_t *cnt = (int32_t *)smem;  // NT tile offsets of the current chunk
     int32_t *ws = cnt + NT;          // scan scratch (40)
@@ -861,10 +868,10 @@ __device__ void phase_E(const FactorArgs &a, int K, char *smem) {
     const bool overflow = Lbase + keptL > a.capLrow || LVbase + (int64_t)keptL * b > a.capLval ||
                           Ubase + keptU > a.capUcol || UVbase + (int64_t)keptU * b > a.capUval;
     if (overflow) {
-        if (blockIdx.x == 0 && tid == 0) set_status(a.status, DEV_POOL_OVERFLOW, a.info, K);
+        if (cr == 0 && tid == 0) set_status(a.status, DEV_POOL_OVERFLOW, a.info, K);
         return;
     }
-    if (blockIdx.x == 0 && tid == 0) {
+    if (cr == 0 && tid == 0) {
         a.Lptr[K + 1] = Lbase + keptL;
         a.Lvptr[K + 1] = LVbase + (int64_t)keptL * b;
         a.Uptr[K + 1] = Ubase + keptU;
@@ -878,7 +885,7 @@ __device__ void phase_E(const FactorArgs &a, int K, char *smem) {
     for (int side = 0; side < 2; ++side) {
         const bool isL = side == 0;
         const int ntile = isL ? tL : tU;
-        if ((int)blockIdx.x >= ntile) continue;  // uniform in the CTA
+        if (cr >= ntile) continue;  // uniform in the CTA
         const int sfirst = isL ? b : 0, send = isL ? mL : mU;
         const int32_t *kp = isL ? a.keepL : a.keepU;
         const int32_t *rows = isL ? a.rowsL : a.rowsU;
@@ -906,7 +913,7 @@ __device__ void phase_E(const FactorArgs &a, int K, char *smem) {
             const int ex = block_excl_scan(my, ws, &tot);
             if (tid < cn) cnt[tid] = carry + ex;
             __syncthreads();
-            for (int T = c0 + (int)blockIdx.x + warp * a.G; T < c0 + cn; T += a.G * NW) {
+            for (int T = c0 + cr + warp * a.G; T < c0 + cn; T += a.G * NW) {
                 const int sb = sfirst + T * 32, se = min(send, sb + 32);
                 const bool kept = sb + lane < se && ldcg(kp + sb + lane) == 1;
                 const unsigned m = __ballot_sync(FULL_MASK, kept);
@@ -974,14 +981,14 @@ __device__ __forceinline__ void red_add_release(uint32_t *p, uint32_t v) {
 //   D           scaling, norms, drop decisions
 //   E           compaction and producer lists
 template <class TS>
-__global__ void __launch_bounds__(NT, 1) bilu_factor_kernel(FactorArgs a) {
-    extern __shared__ __align__(16) char smem[];
+__device__ void factor_chain(const FactorArgs &a, char *smem) {
     const uint32_t G = a.G + a.debug_extra_cta;
+    const int cr = crank(a);
     // CTA 0 times (ns, summed over the blocks): A, B1+C, C2, Bs, D, E; LU work; pivot-tile wait
     uint64_t tacc[6] = {0, 0, 0, 0, 0, 0};
     uint64_t tprev = gtimer(), tlu = 0, twait = 0;
     auto lap = [&](int ph) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (cr == 0 && threadIdx.x == 0) {
             const uint64_t t = gtimer();
             tacc[ph] += t - tprev;
             tprev = t;
@@ -990,8 +997,8 @@ __global__ void __launch_bounds__(NT, 1) bilu_factor_kernel(FactorArgs a) {
     constexpr int TRP = 2;  // rows per pivot-row tile
     for (int K = 0; K < a.nb; ++K) {
         const int b = a.bstart[K + 1] - a.bstart[K];
-        if (blockIdx.x == 0) phase_A(a, K, true, smem);
-        if (blockIdx.x == (1 % a.G)) {
+        if (cr == 0) phase_A(a, K, true, smem);
+        if (cr == (1 % a.G)) {
             __syncthreads();
             phase_A(a, K, false, smem);
         }
@@ -1006,8 +1013,8 @@ __global__ void __launch_bounds__(NT, 1) bilu_factor_kernel(FactorArgs a) {
             TR = max(4, min(TRMAX, TR));
             const int nLt = (nrestL + TR - 1) / TR, nUt = (mU + TR - 1) / TR;
             const int ntiles = npt + (a.skip_bound ? 0 : nLt + nUt);
-            if (a.G == 1 || blockIdx.x > 0) {
-                const int wid = a.G > 1 ? (int)blockIdx.x - 1 : 0;
+            if (a.G == 1 || cr > 0) {
+                const int wid = a.G > 1 ? cr - 1 : 0;
                 for (int it = wid; it < ntiles; it += W) {
                     if (it < npt) {
                         const int sa = it * TRP;
@@ -1024,7 +1031,7 @@ __global__ void __launch_bounds__(NT, 1) bilu_factor_kernel(FactorArgs a) {
                     }
                 }
             }
-            if (blockIdx.x == 0) {
+            if (cr == 0) {
                 __shared__ int s_go;
                 const uint64_t tw = gtimer();
                 if (threadIdx.x == 0) {
@@ -1061,7 +1068,7 @@ __global__ void __launch_bounds__(NT, 1) bilu_factor_kernel(FactorArgs a) {
             int TR = (nrest + a.G - 1) / a.G;
             TR = max(4, min(TRMAX, TR));
             const int nLt = (nrestL + TR - 1) / TR, nUt = (mU + TR - 1) / TR;
-            for (int it = blockIdx.x; it < nLt + nUt; it += a.G) {
+            for (int it = cr; it < nLt + nUt; it += a.G) {
                 const bool Ls = it < nLt;
                 const int sa = Ls ? b + it * TR : (it - nLt) * TR;
                 const int cnt = Ls ? min(TR, mL - sa) : min(TR, mU - sa);
@@ -1078,10 +1085,65 @@ __global__ void __launch_bounds__(NT, 1) bilu_factor_kernel(FactorArgs a) {
         if (!grid_barrier(a.bar, G, a.status, a.spin_limit, a.info, 6)) return;
         lap(5);
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (cr == 0 && threadIdx.x == 0) {
         for (int p = 0; p < 6; ++p) a.info[INFO_PHASE_NS + p] = (int64_t)tacc[p];
         a.info[INFO_C2_WORK_NS] = (int64_t)tlu;
         a.info[INFO_B_WORK_NS] = (int64_t)twait;
+    }
+}
+
+template <class TS>
+__global__ void __launch_bounds__(NT, 1) bilu_factor_kernel(FactorArgs a) {
+    extern __shared__ __align__(16) char smem[];
+    factor_chain<TS>(a, smem);
+}
+
+// Batch of independent matrices in one launch: the grid is cut into groups of G CTAs, each
+// group takes the next matrix from a work queue (sorted largest first by the host), runs its
+// block chain with the group's own barrier, and repeats until the queue is empty.
+template <class TS>
+__global__ void __launch_bounds__(NT, 1) bilu_factor_batch_kernel(const FactorArgs *all, int nmat, int *queue,
+                                                                  uint32_t *gbar, uint32_t *gpiv, int32_t *gslot,
+                                                                  int32_t *gstat, int64_t *ginfo, int G,
+                                                                  long long spin) {
+    extern __shared__ __align__(16) char smem[];
+    __shared__ FactorArgs s_a;
+    __shared__ int s_m;
+    const int grp = blockIdx.x / G, cr = blockIdx.x % G;
+    uint32_t *bar = gbar + 4 * grp;
+    int taken = nmat;  // CTA 0, thread 0: the matrix this group took last
+    while (true) {
+        if (cr == 0 && threadIdx.x == 0) {
+            taken = atomicAdd(queue, 1);
+            st_release_s32(gslot + grp, taken);
+        }
+        if (!grid_barrier(bar, (uint32_t)G, gstat + grp, spin, ginfo + grp * INFO_COUNT, 8)) {
+            // the group is stuck: the matrix it took is reported as timed out, not as factored
+            if (cr == 0 && threadIdx.x == 0 && taken < nmat) atomicCAS(all[taken].status, 0, DEV_TIMEOUT);
+            return;
+        }
+        if (threadIdx.x == 0) s_m = ld_acquire_s32(gslot + grp);
+        __syncthreads();
+        const int m = s_m;
+        if (m >= nmat) return;
+        if (threadIdx.x == 0) {
+            s_a = all[m];
+            s_a.G = G;
+            s_a.bar = bar;
+            s_a.pivdone = gpiv + grp;
+            s_a.spin_limit = spin;
+        }
+        __syncthreads();
+        factor_chain<TS>(s_a, smem);
+        __syncthreads();
+        // other errors end the chain at the same barrier on every CTA of the group, and the
+        // group goes on with the next matrix; after a timeout its barrier state is undefined
+        if (threadIdx.x == 0) s_m = ld_acquire_s32(s_a.status);
+        __syncthreads();
+        if (s_m == DEV_TIMEOUT) {
+            if (threadIdx.x == 0) atomicCAS(gstat + grp, 0, DEV_TIMEOUT);
+            return;
+        }
     }
 }
 
@@ -1162,6 +1224,13 @@ cudaError_t alloc_prod(bilu_ctx *c) {
 
 }  // namespace
 
+// test hooks (bilu_debug_set)
+int g_debug_extra_cta = 0;          // the barrier waits for a CTA that never arrives
+long long g_debug_spin_limit = 0;   // polls before a bounded wait gives up (0: default)
+long long g_debug_batch_group = 0;  // batch group size (0: tuned)
+int g_debug_small_pools = 0;        // factorizations start from minimal pools and producer lists
+int g_debug_poison = 0;             // factor storage is filled with NaN before every run
+
 bilu_status factor_alloc(bilu_ctx *c) {
     factor_free(c);
     const int64_t n = std::max<int64_t>(c->n, 1), nb = std::max<int64_t>(c->nb, 1);
@@ -1173,6 +1242,11 @@ bilu_status factor_alloc(bilu_ctx *c) {
     c->capT = n + BILU_MAX_BLOCK;
     c->prodcap = 64;
     c->capXS = 4 * c->capT;
+    if (g_debug_small_pools) {  // test hook: exercise the re-run paths
+        c->capLval = c->capUval = c->capLrow = c->capUcol = 1024;
+        c->prodcap = 4;
+        c->capXS = c->capT;
+    }
     cudaError_t e = cudaSuccess;
     if ((e = dev_alloc(&c->d_Lptr, nb + 1)) != cudaSuccess || (e = dev_alloc(&c->d_Lvptr, nb + 1)) != cudaSuccess ||
         (e = dev_alloc(&c->d_Uptr, nb + 1)) != cudaSuccess || (e = dev_alloc(&c->d_Uvptr, nb + 1)) != cudaSuccess ||
@@ -1200,8 +1274,135 @@ bilu_status factor_alloc(bilu_ctx *c) {
     return BILU_OK;
 }
 
-int g_debug_extra_cta = 0;  // test hook (bilu_debug_set): barrier waits for a CTA that never arrives
-long long g_debug_spin_limit = 0;
+
+namespace {
+
+const void *factor_kernel_for(int precision) {
+    return precision == BILU_PREC_FP32   ? (const void *)bilu_factor_kernel<float>
+           : precision == BILU_PREC_BF16 ? (const void *)bilu_factor_kernel<__nv_bfloat16>
+                                         : (const void *)bilu_factor_kernel<double>;
+}
+const void *batch_kernel_for(int precision) {
+    return precision == BILU_PREC_FP32   ? (const void *)bilu_factor_batch_kernel<float>
+           : precision == BILU_PREC_BF16 ? (const void *)bilu_factor_batch_kernel<__nv_bfloat16>
+                                         : (const void *)bilu_factor_batch_kernel<double>;
+}
+
+// Reset of the per-run device state of one context (stream-ordered on `st`).
+cudaError_t prepare_run(bilu_ctx *c, cudaStream_t st) {
+    const int64_t nb = std::max<int64_t>(c->nb, 1), n = std::max<int64_t>(c->n, 1);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(c->d_Lptr, 0, (nb + 1) * sizeof(int64_t), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(c->d_Lvptr, 0, (nb + 1) * sizeof(int64_t), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(c->d_Uptr, 0, (nb + 1) * sizeof(int64_t), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(c->d_Uvptr, 0, (nb + 1) * sizeof(int64_t), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(c->d_prodLcnt, 0, nb * sizeof(int32_t), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(c->d_prodUcnt, 0, nb * sizeof(int32_t), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(c->d_lastL, 0xff, nb * sizeof(int32_t), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(c->d_lastU, 0xff, nb * sizeof(int32_t), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(c->d_bmL, 0, (n / 32 + 2) * sizeof(uint32_t), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(c->d_bmU, 0, (n / 32 + 2) * sizeof(uint32_t), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(c->d_status, 0, 4 * sizeof(int32_t), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(c->d_info, 0, INFO_COUNT * sizeof(int64_t), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(c->d_bar, 0, 4 * sizeof(uint32_t), st)) != cudaSuccess) return e;
+    if (g_debug_poison) {  // test hook: every value array (no index array) starts as NaN
+        const int64_t nd = std::max<int64_t>(c->h_Dptr.back(), 1);
+        const size_t vs = c->p.precision == BILU_PREC_FP64 ? 8 : c->p.precision == BILU_PREC_FP32 ? 4 : 2;
+        const size_t as = c->p.precision == BILU_PREC_FP64 ? 8 : 4;
+        struct { void *p; size_t bytes; } fill[] = {
+            {c->d_Dinv, nd * 8}, {c->d_Pblk, nd * 8}, {c->d_Lval, c->capLval * vs}, {c->d_Uval, c->capUval * vs},
+            {c->d_Lnrm, c->capLrow * 8},
+            {c->d_Unrm, c->capUcol * 8}, {c->d_TL, c->capT * (int64_t)std::max(c->bmax, 1) * as},
+            {c->d_TU, c->capT * (int64_t)std::max(c->bmax, 1) * as}, {c->d_LU, (BILU_MAX_BLOCK * BILU_MAX_BLOCK + BILU_MAX_BLOCK) * 8},
+            {c->d_dcolsq, BILU_MAX_BLOCK * 8}, {c->d_nrmL, c->capT * 8}, {c->d_nrmU, c->capT * 8}};
+        for (auto &f : fill)
+            if ((e = cudaMemsetAsync(f.p, 0xff, f.bytes, st)) != cudaSuccess) return e;
+    }
+    return cudaMemsetAsync(c->d_pivdone, 0, 4 * sizeof(uint32_t), st);
+}
+
+FactorArgs make_args(bilu_ctx *c, double droptol, int G) {
+    FactorArgs a{};
+    a.n = (int32_t)c->n; a.nb = c->nb; a.G = G; a.perturb = c->p.perturb;
+    a.tau = droptol; a.alpha = c->alpha; a.pert_tau = c->p.pert_tau; a.pert_rho = c->p.pert_rho;
+    a.spin_limit = g_debug_spin_limit > 0 ? g_debug_spin_limit : (1LL << 24);
+    a.rowptr = c->d_rowptr; a.colind = c->d_colind; a.colptr = c->d_colptr; a.rowind = c->d_rowind;
+    a.bstart = c->d_bstart; a.blkof = c->d_blkof; a.val = c->d_val; a.cval = c->d_cval; a.Dptr = c->d_Dptr;
+    a.Lptr = c->d_Lptr; a.Lvptr = c->d_Lvptr; a.Uptr = c->d_Uptr; a.Uvptr = c->d_Uvptr;
+    a.Lrow = c->d_Lrow; a.Ucol = c->d_Ucol; a.Lval = c->d_Lval; a.Uval = c->d_Uval;
+    a.Dinv = c->d_Dinv; a.Pblk = c->d_Pblk;
+    a.capLrow = c->capLrow; a.capLval = c->capLval; a.capUcol = c->capUcol; a.capUval = c->capUval;
+    a.prodcap = c->prodcap;
+    a.prodL = c->d_prodL; a.prodLcnt = c->d_prodLcnt; a.prodU = c->d_prodU; a.prodUcnt = c->d_prodUcnt;
+    a.lastL = c->d_lastL; a.lastU = c->d_lastU;
+    a.TL = c->d_TL; a.TU = c->d_TU; a.rowsL = c->d_rowsL; a.rowsU = c->d_rowsU;
+    a.keepL = c->d_keepL; a.keepU = c->d_keepU; a.bmL = c->d_bmL; a.bmU = c->d_bmU;
+    a.wbL = c->d_wbL; a.wbU = c->d_wbU; a.xslotL = c->d_xslotL; a.xslotU = c->d_xslotU;
+    a.capXS = c->capXS; a.pinfoL = c->d_pinfoL; a.pinfoU = c->d_pinfoU; a.capT = c->capT;
+    a.LU = c->d_LU; a.perm = c->d_perm; a.kst = c->d_kstate; a.status = c->d_status; a.info = c->d_info;
+    a.bar = c->d_bar;
+    a.debug_extra_cta = g_debug_extra_cta;
+    a.skip_bound = c->p.skip == BILU_SKIP_BOUND ? 1 : 0;
+    a.Lnrm = c->d_Lnrm; a.Unrm = c->d_Unrm; a.nrmL = c->d_nrmL; a.nrmU = c->d_nrmU;
+    a.dcolsq = c->d_dcolsq; a.pivdone = c->d_pivdone;
+    return a;
+}
+
+// After a run: 0 = done, 1 = re-run (pools or producer lists were grown), < 0 = error status.
+int finish_run(bilu_ctx *c, int32_t status, const int64_t *info, bilu_status *err) {
+    if (status == DEV_POOL_OVERFLOW) {
+        c->capLval *= 2; c->capUval *= 2; c->capLrow *= 2; c->capUcol *= 2;
+        if (alloc_pools(c) != cudaSuccess) { *err = set_err(c, BILU_ERR_OOM, "growing L/U pools failed"); return -1; }
+        c->pool_retries++;
+        return 1;
+    }
+    if (status == DEV_PROD_OVERFLOW) {
+        if (c->prodcap * 2 > PMAX) { *err = set_err(c, BILU_ERR_OOM, "more than 1024 producer blocks for one block"); return -1; }
+        c->prodcap *= 2;
+        c->capXS *= 2;
+        if (alloc_prod(c) != cudaSuccess) { *err = set_err(c, BILU_ERR_OOM, "growing producer lists failed"); return -1; }
+        c->pool_retries++;
+        return 1;
+    }
+    if (status == DEV_TIMEOUT) { *err = set_err(c, BILU_ERR_TIMEOUT, "factor kernel: bounded wait gave up (site " + std::to_string(info[INFO_TIMEOUT_SITE]) + ")"); return -1; }
+    if (status == DEV_SINGULAR) { *err = set_err(c, BILU_ERR_SINGULAR, "singular diagonal block " + std::to_string(info[INFO_FAIL_BLOCK])); return -1; }
+    if (status == DEV_INTERNAL) { *err = set_err(c, BILU_ERR_CUDA, "factor kernel index check failed at block " + std::to_string(info[INFO_FAIL_BLOCK])); return -1; }
+    if (status != DEV_OK) { *err = set_err(c, BILU_ERR_CUDA, "factor kernel status " + std::to_string(status)); return -1; }
+    int64_t tails[4] = {0, 0, 0, 0};
+    cudaError_t e = cudaSuccess;
+    if (c->nb > 0) {
+        if ((e = cudaMemcpy(&tails[0], c->d_Lptr + c->nb, sizeof(int64_t), cudaMemcpyDeviceToHost)) != cudaSuccess ||
+            (e = cudaMemcpy(&tails[1], c->d_Lvptr + c->nb, sizeof(int64_t), cudaMemcpyDeviceToHost)) != cudaSuccess ||
+            (e = cudaMemcpy(&tails[2], c->d_Uptr + c->nb, sizeof(int64_t), cudaMemcpyDeviceToHost)) != cudaSuccess ||
+            (e = cudaMemcpy(&tails[3], c->d_Uvptr + c->nb, sizeof(int64_t), cudaMemcpyDeviceToHost)) != cudaSuccess) {
+            *err = cuda_err(c, e, "reading factor sizes");
+            return -1;
+        }
+    }
+    c->kept_rows = tails[0]; c->nnz_l = tails[1]; c->kept_cols = tails[2]; c->nnz_u = tails[3];
+    c->cand_rows = info[INFO_CAND_ROWS]; c->cand_cols = info[INFO_CAND_COLS];
+    c->nperturb = info[INFO_NPERTURB];
+    c->flop_upd_l = info[INFO_FLOP_UPD_L];
+    c->flop_upd_u = info[INFO_FLOP_UPD_U];
+    c->flop_scale = info[INFO_FLOP_SCALE];
+    c->flop_norm = info[INFO_FLOP_NORM];
+    for (int p = 0; p < 6; ++p) c->phase_ms[p] = info[INFO_PHASE_NS + p] * 1e-6;
+    c->phase_ms[6] = info[INFO_C2_WORK_NS] * 1e-6;
+    c->phase_ms[7] = info[INFO_B_WORK_NS] * 1e-6;
+    c->skipped_rows = info[INFO_SKIP_ROWS];
+    c->skipped_cols = info[INFO_SKIP_COLS];
+    double f_lu = 0.0;  // getrf (2/3 b^3) and inverse (4/3 b^3) per diagonal block
+    for (int32_t K = 0; K < c->nb; ++K) {
+        const double b = c->h_bstart[K + 1] - c->h_bstart[K];
+        f_lu += 2.0 * b * b * b;
+    }
+    c->flops_factor = (double)c->flop_upd_l + (double)c->flop_upd_u + (double)c->flop_scale +
+                      (double)c->flop_norm + f_lu;
+    *err = c->nperturb > 0 ? BILU_PERTURBED : BILU_OK;
+    return 0;
+}
+
+}  // namespace
 
 bilu_status factor_run(bilu_ctx *c, double droptol) {
     if (c->d_Lptr == nullptr) {
@@ -1209,9 +1410,7 @@ bilu_status factor_run(bilu_ctx *c, double droptol) {
         if (st != BILU_OK) return st;
     }
     // kernel instance by the precision of the updates and the stored factor values
-    const void *kfn = c->p.precision == BILU_PREC_FP32   ? (const void *)bilu_factor_kernel<float>
-                      : c->p.precision == BILU_PREC_BF16 ? (const void *)bilu_factor_kernel<__nv_bfloat16>
-                                                         : (const void *)bilu_factor_kernel<double>;
+    const void *kfn = factor_kernel_for(c->p.precision);
     BILU_CUDA(c, cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
     int per_sm = 0;
     BILU_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, NT, SMEM_BYTES));
@@ -1221,52 +1420,15 @@ bilu_status factor_run(bilu_ctx *c, double droptol) {
     cudaEvent_t e0, e1;
     BILU_CUDA(c, cudaEventCreate(&e0));
     BILU_CUDA(c, cudaEventCreate(&e1));
+    bilu_status result = BILU_ERR_OOM;
+    bool finished = false;
     for (int attempt = 0; attempt < 12; ++attempt) {
-        const int64_t nb = std::max<int64_t>(c->nb, 1), n = std::max<int64_t>(c->n, 1);
-        BILU_CUDA(c, cudaMemsetAsync(c->d_Lptr, 0, (nb + 1) * sizeof(int64_t), c->stream));
-        BILU_CUDA(c, cudaMemsetAsync(c->d_Lvptr, 0, (nb + 1) * sizeof(int64_t), c->stream));
-        BILU_CUDA(c, cudaMemsetAsync(c->d_Uptr, 0, (nb + 1) * sizeof(int64_t), c->stream));
-        BILU_CUDA(c, cudaMemsetAsync(c->d_Uvptr, 0, (nb + 1) * sizeof(int64_t), c->stream));
-        BILU_CUDA(c, cudaMemsetAsync(c->d_prodLcnt, 0, nb * sizeof(int32_t), c->stream));
-        BILU_CUDA(c, cudaMemsetAsync(c->d_prodUcnt, 0, nb * sizeof(int32_t), c->stream));
-        BILU_CUDA(c, cudaMemsetAsync(c->d_lastL, 0xff, nb * sizeof(int32_t), c->stream));
-        BILU_CUDA(c, cudaMemsetAsync(c->d_lastU, 0xff, nb * sizeof(int32_t), c->stream));
-        BILU_CUDA(c, cudaMemsetAsync(c->d_bmL, 0, (n / 32 + 2) * sizeof(uint32_t), c->stream));
-        BILU_CUDA(c, cudaMemsetAsync(c->d_bmU, 0, (n / 32 + 2) * sizeof(uint32_t), c->stream));
-        BILU_CUDA(c, cudaMemsetAsync(c->d_status, 0, 4 * sizeof(int32_t), c->stream));
-        BILU_CUDA(c, cudaMemsetAsync(c->d_info, 0, INFO_COUNT * sizeof(int64_t), c->stream));
-        BILU_CUDA(c, cudaMemsetAsync(c->d_bar, 0, 4 * sizeof(uint32_t), c->stream));
-        BILU_CUDA(c, cudaMemsetAsync(c->d_pivdone, 0, 4 * sizeof(uint32_t), c->stream));
-
-        FactorArgs a{};
-        a.n = (int32_t)c->n; a.nb = c->nb; a.G = G; a.perturb = c->p.perturb;
-        a.tau = droptol; a.alpha = c->alpha; a.pert_tau = c->p.pert_tau; a.pert_rho = c->p.pert_rho;
-        a.spin_limit = g_debug_spin_limit > 0 ? g_debug_spin_limit : (1LL << 24);
-        a.rowptr = c->d_rowptr; a.colind = c->d_colind; a.colptr = c->d_colptr; a.rowind = c->d_rowind;
-        a.bstart = c->d_bstart; a.blkof = c->d_blkof; a.val = c->d_val; a.cval = c->d_cval; a.Dptr = c->d_Dptr;
-        a.Lptr = c->d_Lptr; a.Lvptr = c->d_Lvptr; a.Uptr = c->d_Uptr; a.Uvptr = c->d_Uvptr;
-        a.Lrow = c->d_Lrow; a.Ucol = c->d_Ucol; a.Lval = c->d_Lval; a.Uval = c->d_Uval;
-        a.Dinv = c->d_Dinv; a.Pblk = c->d_Pblk;
-        a.capLrow = c->capLrow; a.capLval = c->capLval; a.capUcol = c->capUcol; a.capUval = c->capUval;
-        a.prodcap = c->prodcap;
-        a.prodL = c->d_prodL; a.prodLcnt = c->d_prodLcnt; a.prodU = c->d_prodU; a.prodUcnt = c->d_prodUcnt;
-        a.lastL = c->d_lastL; a.lastU = c->d_lastU;
-        a.TL = c->d_TL; a.TU = c->d_TU; a.rowsL = c->d_rowsL; a.rowsU = c->d_rowsU;
-        a.keepL = c->d_keepL; a.keepU = c->d_keepU; a.bmL = c->d_bmL; a.bmU = c->d_bmU;
-        a.wbL = c->d_wbL; a.wbU = c->d_wbU; a.xslotL = c->d_xslotL; a.xslotU = c->d_xslotU;
-        a.capXS = c->capXS; a.pinfoL = c->d_pinfoL; a.pinfoU = c->d_pinfoU; a.capT = c->capT;
-        a.LU = c->d_LU; a.perm = c->d_perm; a.kst = c->d_kstate; a.status = c->d_status; a.info = c->d_info;
-        a.bar = c->d_bar;
-        a.debug_extra_cta = g_debug_extra_cta;
-        a.skip_bound = c->p.skip == BILU_SKIP_BOUND ? 1 : 0;
-        a.Lnrm = c->d_Lnrm; a.Unrm = c->d_Unrm; a.nrmL = c->d_nrmL; a.nrmU = c->d_nrmU;
-        a.dcolsq = c->d_dcolsq; a.pivdone = c->d_pivdone;
-
+        BILU_CUDA(c, prepare_run(c, c->stream));
+        FactorArgs a = make_args(c, droptol, G);
         void *args[] = {&a};
         BILU_CUDA(c, cudaEventRecord(e0, c->stream));
         if (c->nb > 0) {
-            BILU_CUDA(c, cudaLaunchCooperativeKernel(kfn, dim3(G), dim3(NT), args,
-                                                     SMEM_BYTES, c->stream));
+            BILU_CUDA(c, cudaLaunchCooperativeKernel(kfn, dim3(G), dim3(NT), args, SMEM_BYTES, c->stream));
             c->launches += 1;
         }
         BILU_CUDA(c, cudaEventRecord(e1, c->stream));
@@ -1278,56 +1440,180 @@ bilu_status factor_run(bilu_ctx *c, double droptol) {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
         c->t_factor_ms = ms;
-        if (status == DEV_POOL_OVERFLOW) {
-            c->capLval *= 2; c->capUval *= 2; c->capLrow *= 2; c->capUcol *= 2;
-            cudaError_t ee = alloc_pools(c);
-            if (ee != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return set_err(c, BILU_ERR_OOM, "growing L/U pools failed"); }
-            c->pool_retries++;
-            continue;
-        }
-        if (status == DEV_PROD_OVERFLOW) {
-            if (c->prodcap * 2 > PMAX) { cudaEventDestroy(e0); cudaEventDestroy(e1); return set_err(c, BILU_ERR_OOM, "more than 1024 producer blocks for one block"); }
-            c->prodcap *= 2;
-            c->capXS *= 2;
-            cudaError_t ee = alloc_prod(c);
-            if (ee != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return set_err(c, BILU_ERR_OOM, "growing producer lists failed"); }
-            c->pool_retries++;
-            continue;
-        }
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        if (status == DEV_TIMEOUT) return set_err(c, BILU_ERR_TIMEOUT, "factor kernel: bounded wait gave up (site " + std::to_string(info[INFO_TIMEOUT_SITE]) + ")");
-        if (status == DEV_SINGULAR) return set_err(c, BILU_ERR_SINGULAR, "singular diagonal block " + std::to_string(info[INFO_FAIL_BLOCK]));
-        if (status == DEV_INTERNAL) return set_err(c, BILU_ERR_CUDA, "factor kernel index check failed at block " + std::to_string(info[INFO_FAIL_BLOCK]));
-        if (status != DEV_OK) return set_err(c, BILU_ERR_CUDA, "factor kernel status " + std::to_string(status));
-        // results
-        int64_t tails[4];
-        BILU_CUDA(c, cudaMemcpy(&tails[0], c->d_Lptr + c->nb, sizeof(int64_t), cudaMemcpyDeviceToHost));
-        BILU_CUDA(c, cudaMemcpy(&tails[1], c->d_Lvptr + c->nb, sizeof(int64_t), cudaMemcpyDeviceToHost));
-        BILU_CUDA(c, cudaMemcpy(&tails[2], c->d_Uptr + c->nb, sizeof(int64_t), cudaMemcpyDeviceToHost));
-        BILU_CUDA(c, cudaMemcpy(&tails[3], c->d_Uvptr + c->nb, sizeof(int64_t), cudaMemcpyDeviceToHost));
-        c->kept_rows = tails[0]; c->nnz_l = tails[1]; c->kept_cols = tails[2]; c->nnz_u = tails[3];
-        c->cand_rows = info[INFO_CAND_ROWS]; c->cand_cols = info[INFO_CAND_COLS];
-        c->nperturb = info[INFO_NPERTURB];
-        c->flop_upd_l = info[INFO_FLOP_UPD_L];
-        c->flop_upd_u = info[INFO_FLOP_UPD_U];
-        c->flop_scale = info[INFO_FLOP_SCALE];
-        c->flop_norm = info[INFO_FLOP_NORM];
-        for (int p = 0; p < 6; ++p) c->phase_ms[p] = info[INFO_PHASE_NS + p] * 1e-6;
-        c->phase_ms[6] = info[INFO_C2_WORK_NS] * 1e-6;
-        c->phase_ms[7] = info[INFO_B_WORK_NS] * 1e-6;
-        c->skipped_rows = info[INFO_SKIP_ROWS];
-        c->skipped_cols = info[INFO_SKIP_COLS];
-        double f_lu = 0.0;  // getrf (2/3 b^3) and inverse (4/3 b^3) per diagonal block
-        for (int32_t K = 0; K < c->nb; ++K) {
-            const double b = c->h_bstart[K + 1] - c->h_bstart[K];
-            f_lu += 2.0 * b * b * b;
-        }
-        c->flops_factor = (double)c->flop_upd_l + (double)c->flop_upd_u + (double)c->flop_scale +
-                          (double)c->flop_norm + f_lu;
-        return c->nperturb > 0 ? BILU_PERTURBED : BILU_OK;
+        bilu_status err = BILU_OK;
+        const int r = finish_run(c, status, info, &err);
+        if (r == 1) continue;
+        result = err;
+        finished = true;
+        break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    return set_err(c, BILU_ERR_OOM, "factor: too many pool re-runs");
+    if (!finished) return set_err(c, BILU_ERR_OOM, "factor: too many pool re-runs");
+    return result;
+}
+
+// ---------------------------------------------------------------- batched factorization
+
+namespace {
+
+struct BatchTune {
+    int nsm, nmat, bmax, precision, G, tuned;
+};
+std::vector<BatchTune> g_batch_tune;  // group sizes chosen by the autotuner
+
+}  // namespace
+
+// Factors every context's matrix in one cooperative launch: groups of G CTAs take matrices
+// from a queue, largest first.  G is chosen by timing candidate group sizes on the second
+// call for a given (matrix count, largest block, precision) and cached.
+bilu_status factor_batch_run(bilu_ctx *const *ctxs, int count, double droptol, double *ms_out) {
+    bilu_ctx *c0 = ctxs[0];
+    const int prec = c0->p.precision;
+    int bmax = 0;
+    for (int i = 0; i < count; ++i) {
+        bilu_ctx *c = ctxs[i];
+        if (!c->d_Lptr) {
+            bilu_status st = factor_alloc(c);
+            if (st != BILU_OK) return st;
+        }
+        bmax = std::max(bmax, c->bmax);
+    }
+    const void *kfn = batch_kernel_for(prec);
+    BILU_CUDA(c0, cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    int per_sm = 0;
+    BILU_CUDA(c0, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, NT, SMEM_BYTES));
+    if (per_sm < 1) return set_err(c0, BILU_ERR_CUDA, "batch factor kernel cannot be resident");
+    const int nsm = c0->nsm;
+    // matrices in the queue: largest first
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return ctxs[x]->nnz > ctxs[y]->nnz; });
+    // device buffers of this call (the batch API allocates per call)
+    FactorArgs *d_args = nullptr;
+    int *d_queue = nullptr;
+    uint32_t *d_gbar = nullptr, *d_gpiv = nullptr;
+    int32_t *d_gslot = nullptr, *d_gstat = nullptr;
+    int64_t *d_ginfo = nullptr;
+    auto release = [&]() {
+        dev_free(d_args); dev_free(d_queue); dev_free(d_gbar); dev_free(d_gpiv); dev_free(d_gslot);
+        dev_free(d_gstat); dev_free(d_ginfo);
+    };
+    if (dev_alloc(&d_args, count) != cudaSuccess || dev_alloc(&d_queue, 4) != cudaSuccess ||
+        dev_alloc(&d_gbar, 4 * nsm) != cudaSuccess || dev_alloc(&d_gpiv, 4 * nsm) != cudaSuccess ||
+        dev_alloc(&d_gslot, nsm) != cudaSuccess || dev_alloc(&d_gstat, nsm) != cudaSuccess ||
+        dev_alloc(&d_ginfo, (int64_t)INFO_COUNT * nsm) != cudaSuccess) {
+        release();
+        return set_err(c0, BILU_ERR_OOM, "batch allocation failed");
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    // one launch over the matrices in `todo`; returns the kernel time
+    auto launch = [&](const std::vector<int> &todo, int G, float *ms) -> cudaError_t {
+        cudaError_t e;
+        std::vector<FactorArgs> h(todo.size());
+        for (size_t k = 0; k < todo.size(); ++k) {
+            bilu_ctx *c = ctxs[todo[k]];
+            if ((e = prepare_run(c, c0->stream)) != cudaSuccess) return e;
+            h[k] = make_args(c, droptol, G);
+        }
+        if ((e = cudaMemcpyAsync(d_args, h.data(), h.size() * sizeof(FactorArgs), cudaMemcpyHostToDevice, c0->stream)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(d_queue, 0, 4 * sizeof(int), c0->stream)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(d_gbar, 0, 4 * nsm * sizeof(uint32_t), c0->stream)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(d_gpiv, 0, 4 * nsm * sizeof(uint32_t), c0->stream)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(d_gstat, 0, nsm * sizeof(int32_t), c0->stream)) != cudaSuccess) return e;
+        int nmat = (int)todo.size(), Gv = G;
+        long long spin = g_debug_spin_limit > 0 ? g_debug_spin_limit : (1LL << 24);
+        const int ngroups = nsm / G;
+        void *args[] = {&d_args, &nmat, &d_queue, &d_gbar, &d_gpiv, &d_gslot, &d_gstat, &d_ginfo, &Gv, &spin};
+        cudaEventRecord(e0, c0->stream);
+        if ((e = cudaLaunchCooperativeKernel(kfn, dim3(ngroups * G), dim3(NT), args, SMEM_BYTES, c0->stream)) != cudaSuccess)
+            return e;
+        cudaEventRecord(e1, c0->stream);
+        c0->launches += 1;
+        if ((e = cudaStreamSynchronize(c0->stream)) != cudaSuccess) return e;
+        cudaEventElapsedTime(ms, e0, e1);
+        return cudaSuccess;
+    };
+    // Group size.  Candidates split the SMs into a power-of-two number of groups g (G = nsm / g
+    // CTAs each), from about count / 8 groups (several matrices per group, larger groups) to
+    // about 2 count (every matrix at once, smallest groups), G >= 2 so that the pivot LU of a
+    // block overlaps its update tiles.  The first call for a (SM count, matrix count, largest
+    // block, precision) runs with g = the power of two >= count / 4 (and grows the pools); the
+    // next call times the candidates, largest G first, until one is slower than the one
+    // before, and caches the fastest.
+    std::vector<int> cands;
+    for (int g = 1; g <= nsm; g *= 2) {
+        const int Gc = nsm / g;
+        if (Gc < 2 && nsm >= 2) break;
+        if (8 * g < count && Gc > 2) continue;
+        if (g > 2 * count) break;
+        cands.push_back(Gc);
+    }
+    if (cands.empty()) cands.push_back(std::max(1, nsm / 2));
+    int G = 0;
+    BatchTune *entry = nullptr;
+    for (auto &t : g_batch_tune)
+        if (t.nsm == nsm && t.nmat == count && t.bmax == bmax && t.precision == prec) entry = &t;
+    std::vector<int> todo(order);
+    float best_ms = 0.f;
+    if (g_debug_batch_group > 0) {
+        G = (int)std::min<long long>(g_debug_batch_group, nsm);
+    } else if (!entry) {
+        int g = 1;
+        while (4 * g < count && 2 * g <= nsm / 2) g *= 2;
+        G = std::max(1, nsm / g);
+        g_batch_tune.push_back({nsm, count, bmax, prec, G, 0});
+    } else if (!entry->tuned) {
+        float best = 1e30f;
+        int bestG = entry->G;
+        bool ok = true;
+        for (int Gc : cands) {
+            float ms = 0.f;
+            cudaError_t e = launch(todo, Gc, &ms);
+            if (e != cudaSuccess) { release(); cudaEventDestroy(e0); cudaEventDestroy(e1); return cuda_err(c0, e, "batch factor launch"); }
+            for (int i : todo) {
+                int32_t st = 0;
+                cudaMemcpy(&st, ctxs[i]->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost);
+                ok = ok && st == DEV_OK;
+            }
+            if (!ok) break;  // pools still growing: tune on a later call
+            if (ms < best) { best = ms; bestG = Gc; }
+            else break;  // past the minimum
+        }
+        G = bestG;
+        if (ok) { entry->G = bestG; entry->tuned = 1; }
+    } else {
+        G = entry->G;
+    }
+    bilu_status result = BILU_OK;
+    for (int attempt = 0; attempt < 12 && !todo.empty(); ++attempt) {
+        float ms = 0.f;
+        cudaError_t e = launch(todo, G, &ms);
+        if (e != cudaSuccess) { release(); cudaEventDestroy(e0); cudaEventDestroy(e1); return cuda_err(c0, e, "batch factor launch"); }
+        best_ms += ms;
+        std::vector<int> again;
+        for (int i : todo) {
+            bilu_ctx *c = ctxs[i];
+            int32_t status = 0;
+            int64_t info[INFO_COUNT];
+            cudaMemcpy(&status, c->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost);
+            cudaMemcpy(info, c->d_info, sizeof(info), cudaMemcpyDeviceToHost);
+            c->t_factor_ms = ms;
+            bilu_status err = BILU_OK;
+            const int r = finish_run(c, status, info, &err);
+            if (r == 1) again.push_back(i);
+            else if (r < 0) result = err;
+            else if (err == BILU_PERTURBED && result == BILU_OK) result = BILU_PERTURBED;
+        }
+        if (result < 0) break;
+        todo.swap(again);
+    }
+    if (!todo.empty() && result >= 0) result = set_err(c0, BILU_ERR_OOM, "batch factor: too many pool re-runs");
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    release();
+    if (ms_out) *ms_out = best_ms;
+    return result;
 }

@@ -16,7 +16,7 @@
 namespace {
 
 constexpr int VT = 256;   // threads per CTA of the vector kernels
-enum { GI_ITS = 0, GI_JDONE, GI_DONE, GI_MAXIT, GI_M, GI_COUNT = 8 };
+enum { GI_ITS = 0, GI_JDONE, GI_DONE, GI_MAXIT, GI_M, GI_STOP, GI_COUNT = 8 };
 enum { GS_BNORM = 0, GS_BETA, GS_TOL, GS_REL, GS_RELEST, GS_COUNT = 8 };
 
 struct GmLayout {
@@ -76,6 +76,8 @@ __device__ __forceinline__ Chunk chunk_of(int64_t n) {
 }
 
 __device__ __forceinline__ bool skipped(const int32_t *gi) { return ldcg(gi + GI_DONE) != 0; }
+// a batched solve stops the cycles of matrices that have converged
+__device__ __forceinline__ bool stopped(const int32_t *gi) { return gi && ldcg(gi + GI_STOP) != 0; }
 
 // y = A x (rows split in contiguous chunks; VL lanes per row)
 template <int VL>
@@ -91,8 +93,9 @@ __device__ __forceinline__ double row_dot(const int32_t *rowptr, const int32_t *
 template <int VL>
 __global__ void __launch_bounds__(VT) spmv_kernel(int64_t n, const int32_t *rowptr, const int32_t *colind,
                                                   const double *val, const double *x, double *y,
-                                                  const double *b, double *part, const int32_t *gi) {
-    if (gi && skipped(gi)) return;
+                                                  const double *b, double *part, const int32_t *gi,
+                                                  const int32_t *stop) {
+    if ((gi && skipped(gi)) || stopped(stop)) return;
     const Chunk c = chunk_of(n);
     const int sub = threadIdx.x % VL, grp = threadIdx.x / VL, ngrp = VT / VL;
     double acc = 0.0;
@@ -206,7 +209,7 @@ __global__ void givens_kernel(int j, int m, double *gm, int32_t *gi, const doubl
 
 // y = H(0:jd, 0:jd)^{-1} g (back substitution, one thread)
 __global__ void solve_y_kernel(int m, double *gm, const int32_t *gi, int64_t goff, int64_t yoff) {
-    if (threadIdx.x != 0) return;
+    if (threadIdx.x != 0 || stopped(gi)) return;
     const int jd = gi[GI_JDONE];
     const double *H = gm, *g = gm + goff;
     double *y = gm + yoff;
@@ -220,6 +223,7 @@ __global__ void solve_y_kernel(int m, double *gm, const int32_t *gi, int64_t gof
 // u = V(:, 0:jd) y
 __global__ void __launch_bounds__(VT) combine_kernel(int64_t n, const double *V, const double *gm, const int32_t *gi,
                                                      int64_t yoff, double *u) {
+    if (stopped(gi)) return;
     const Chunk c = chunk_of(n);
     const int jd = ldcg(gi + GI_JDONE);
     const double *y = gm + yoff;
@@ -230,7 +234,8 @@ __global__ void __launch_bounds__(VT) combine_kernel(int64_t n, const double *V,
     }
 }
 
-__global__ void __launch_bounds__(VT) axpy_kernel(int64_t n, const double *z, double *x) {
+__global__ void __launch_bounds__(VT) axpy_kernel(int64_t n, const double *z, double *x, const int32_t *gi) {
+    if (stopped(gi)) return;
     const Chunk c = chunk_of(n);
     for (int64_t e = c.lo + threadIdx.x; e < c.hi; e += VT) x[e] += z[e];
 }
@@ -259,7 +264,7 @@ __global__ void __launch_bounds__(VT) cycle_begin_kernel(int64_t n, int m, const
         for (int k = 0; k <= m; ++k) g[k] = 0.0;
         g[0] = beta;
         gi[GI_JDONE] = 0;
-        gi[GI_DONE] = gi[GI_ITS] >= gi[GI_MAXIT] ? 1 : 0;
+        gi[GI_DONE] = (gi[GI_ITS] >= gi[GI_MAXIT] || gi[GI_STOP]) ? 1 : 0;
     }
 }
 
@@ -275,6 +280,7 @@ __global__ void setup_kernel(double *gm, int32_t *gi, const double *part, int G,
     gi[GI_DONE] = 0;
     gi[GI_MAXIT] = maxit;
     gi[GI_M] = m;
+    gi[GI_STOP] = 0;
 }
 
 }  // namespace
@@ -303,12 +309,13 @@ namespace {
 
 int vector_grid(const bilu_ctx *c) { return 2 * c->nsm; }
 
-void launch_spmv(bilu_ctx *c, const double *x, double *y, const double *b, double *part, const int32_t *gi) {
+void launch_spmv(bilu_ctx *c, const double *x, double *y, const double *b, double *part, const int32_t *gi,
+                 const int32_t *stop = nullptr) {
     const int G = vector_grid(c);
     const double avg = c->n > 0 ? (double)c->nnz / (double)c->n : 0.0;
-    if (avg <= 12) spmv_kernel<8><<<G, VT, 0, c->stream>>>(c->n, c->d_rowptr, c->d_colind, c->d_val, x, y, b, part, gi);
-    else if (avg <= 40) spmv_kernel<16><<<G, VT, 0, c->stream>>>(c->n, c->d_rowptr, c->d_colind, c->d_val, x, y, b, part, gi);
-    else spmv_kernel<32><<<G, VT, 0, c->stream>>>(c->n, c->d_rowptr, c->d_colind, c->d_val, x, y, b, part, gi);
+    if (avg <= 12) spmv_kernel<8><<<G, VT, 0, c->stream>>>(c->n, c->d_rowptr, c->d_colind, c->d_val, x, y, b, part, gi, stop);
+    else if (avg <= 40) spmv_kernel<16><<<G, VT, 0, c->stream>>>(c->n, c->d_rowptr, c->d_colind, c->d_val, x, y, b, part, gi, stop);
+    else spmv_kernel<32><<<G, VT, 0, c->stream>>>(c->n, c->d_rowptr, c->d_colind, c->d_val, x, y, b, part, gi, stop);
 }
 
 bilu_status gmres_alloc(bilu_ctx *c, int m) {
@@ -349,16 +356,162 @@ bilu_status record_cycle(bilu_ctx *c, int m) {
     }
     solve_y_kernel<<<1, 32, 0, c->stream>>>(m, c->d_gm, gi, L.g, L.y);
     combine_kernel<<<G, VT, 0, c->stream>>>(n, c->d_V, c->d_gm, gi, L.y, c->d_u);
-    bilu_status st = apply_launch(c, c->d_u, c->d_z, nullptr);
+    bilu_status st = apply_launch(c, c->d_u, c->d_z, gi + GI_STOP);
     if (st != BILU_OK) return st;
-    axpy_kernel<<<G, VT, 0, c->stream>>>(n, c->d_z, c->d_gx);
-    launch_spmv(c, c->d_gx, c->d_r, c->d_gb, c->d_part + 3 * G, nullptr);
+    axpy_kernel<<<G, VT, 0, c->stream>>>(n, c->d_z, c->d_gx, gi);
+    launch_spmv(c, c->d_gx, c->d_r, c->d_gb, c->d_part + 3 * G, nullptr, gi);
     cycle_end_kernel<<<1, 32, 0, c->stream>>>(c->d_gm, gi, c->d_part, G, L.scal, c->h_gm_pinned, c->h_gmi_pinned);
     BILU_CUDA(c, cudaGetLastError());
     return BILU_OK;
 }
 
+// initial residual and state of one solve (stream-ordered on c->stream)
+void gmres_start(bilu_ctx *c, double tol, int m, int maxit) {
+    const int G = vector_grid(c);
+    GmLayout L(m);
+    dot_kernel<<<G, VT, 0, c->stream>>>(c->n, c->d_gb, c->d_gb, c->d_part + 3 * G);
+    setup_kernel<<<1, 32, 0, c->stream>>>(c->d_gm, c->d_gmi, c->d_part, G, L.scal, tol, maxit, m);
+    launch_spmv(c, c->d_gx, c->d_r, c->d_gb, c->d_part + 3 * G, nullptr);
+    cycle_end_kernel<<<1, 32, 0, c->stream>>>(c->d_gm, c->d_gmi, c->d_part, G, L.scal, c->h_gm_pinned, c->h_gmi_pinned);
+    c->launches += 4;
+}
+
+int64_t count_kernel_nodes(cudaGraph_t graph) {
+    size_t nn = 0;
+    cudaGraphGetNodes(graph, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    cudaGraphGetNodes(graph, nodes.data(), &nn);
+    int64_t k = 0;
+    for (auto nd : nodes) {
+        cudaGraphNodeType ty;
+        if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++k;
+    }
+    return k;
+}
+
 }  // namespace
+
+// Restarted GMRES on many independent systems at once: one CUDA graph holds a restart cycle
+// of every system as a parallel branch; systems that have converged are stopped by a device
+// flag, so every kernel of their branch returns at once.
+bilu_status gmres_batch_run(bilu_ctx *const *ctxs, int count, const double *const *b, double *const *x, double tol,
+                            int m, int maxit, gmres_info *info) {
+    bilu_ctx *c0 = ctxs[0];
+    const cudaStream_t master = c0->stream;  // every context is redirected to it below
+    if (m < 1 || m > 1000 || maxit < 0 || !(tol >= 0.0)) return set_err(c0, BILU_ERR_ARG, "bad gmres arguments");
+    cudaEvent_t e0, e1;
+    BILU_CUDA(c0, cudaEventCreate(&e0));
+    BILU_CUDA(c0, cudaEventCreate(&e1));
+    BILU_CUDA(c0, cudaEventRecord(e0, master));
+    std::vector<cudaStream_t> own(count);
+    for (int i = 0; i < count; ++i) own[i] = ctxs[i]->stream;
+    // the contexts get their own streams back on every exit path
+    struct Restore {
+        bilu_ctx *const *ctxs;
+        std::vector<cudaStream_t> &own;
+        ~Restore() {
+            for (size_t i = 0; i < own.size(); ++i) {
+                ctxs[i]->stream = own[i];
+                ctxs[i]->apply_grid = 0;
+            }
+        }
+    } restore{ctxs, own};
+    // The sweeps are chains of dependent blocks (latency-bound): each system's sweeps get an
+    // equal share of the resident CTA slots, so that the branches of the graph run side by
+    // side instead of one whole-GPU sweep after another.
+    for (int i = 0; i < count; ++i) ctxs[i]->apply_grid = std::max(2, 2 * c0->nsm / count);
+    for (int i = 0; i < count; ++i) {
+        bilu_ctx *c = ctxs[i];
+        if (c->gm_restart != m) {
+            bilu_status st = gmres_alloc(c, m);
+            if (st != BILU_OK) return st;
+        }
+        c->stream = master;
+        BILU_CUDA(c0, cudaMemcpyAsync(c->d_gb, b[i], c->n * sizeof(double), cudaMemcpyDefault, master));
+        BILU_CUDA(c0, cudaMemcpyAsync(c->d_gx, x[i], c->n * sizeof(double), cudaMemcpyDefault, master));
+        gmres_start(c, tol, m, maxit);
+    }
+    BILU_CUDA(c0, cudaStreamSynchronize(master));
+    // one graph: a branch per system, forked from and joined to c0's stream
+    std::vector<cudaStream_t> br(count);
+    std::vector<cudaEvent_t> ev(count + 1);
+    for (int i = 0; i < count; ++i) BILU_CUDA(c0, cudaStreamCreateWithFlags(&br[i], cudaStreamNonBlocking));
+    for (int i = 0; i <= count; ++i) BILU_CUDA(c0, cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming));
+    cudaGraph_t graph;
+    BILU_CUDA(c0, cudaStreamBeginCapture(master, cudaStreamCaptureModeThreadLocal));
+    BILU_CUDA(c0, cudaEventRecord(ev[count], master));
+    bilu_status rst = BILU_OK;
+    for (int i = 0; i < count && rst == BILU_OK; ++i) {
+        bilu_ctx *c = ctxs[i];
+        cudaStreamWaitEvent(br[i], ev[count], 0);
+        c->stream = br[i];
+        const int64_t before = c->launches;
+        rst = record_cycle(c, m);
+        c->launches = before;
+        cudaEventRecord(ev[i], br[i]);
+        cudaStreamWaitEvent(master, ev[i], 0);
+        c->stream = master;
+    }
+    cudaError_t ce = cudaStreamEndCapture(master, &graph);
+    if (rst != BILU_OK) return rst;
+    if (ce != cudaSuccess) return cuda_err(c0, ce, "cudaStreamEndCapture (batch)");
+    cudaGraphExec_t exec = nullptr;
+    const int64_t nodes = count_kernel_nodes(graph);
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return cuda_err(c0, ce, "cudaGraphInstantiate (batch)");
+    std::vector<int> restarts(count, 0);
+    for (int cycle = 0; cycle < maxit + 1; ++cycle) {
+        bool any = false;
+        for (int i = 0; i < count; ++i) {
+            bilu_ctx *c = ctxs[i];
+            const bool active = c->h_gm_pinned[GS_BNORM] > 0.0 && c->h_gm_pinned[GS_REL] > tol &&
+                                c->h_gmi_pinned[GI_ITS] < maxit;
+            if (active) { any = true; ++restarts[i]; }
+            const int32_t stop = active ? 0 : 1;
+            BILU_CUDA(c0, cudaMemcpyAsync(c->d_gmi + GI_STOP, &stop, sizeof(int32_t), cudaMemcpyHostToDevice, master));
+        }
+        if (!any) break;
+        BILU_CUDA(c0, cudaGraphLaunch(exec, master));
+        c0->launches += nodes;
+        BILU_CUDA(c0, cudaStreamSynchronize(master));
+    }
+    cudaGraphExecDestroy(exec);
+    for (int i = 0; i < count; ++i) {
+        cudaStreamDestroy(br[i]);
+        cudaEventDestroy(ev[i]);
+    }
+    cudaEventDestroy(ev[count]);
+    bilu_status result = BILU_OK;
+    for (int i = 0; i < count; ++i) {
+        bilu_ctx *c = ctxs[i];
+        if (c->h_gm_pinned[GS_BNORM] == 0.0) BILU_CUDA(c0, cudaMemsetAsync(c->d_gx, 0, c->n * sizeof(double), master));
+        BILU_CUDA(c0, cudaMemcpyAsync(x[i], c->d_gx, c->n * sizeof(double), cudaMemcpyDefault, master));
+    }
+    BILU_CUDA(c0, cudaEventRecord(e1, master));
+    BILU_CUDA(c0, cudaStreamSynchronize(master));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (int i = 0; i < count; ++i) {
+        bilu_ctx *c = ctxs[i];
+        const bool zero = c->h_gm_pinned[GS_BNORM] == 0.0;
+        const double rel = zero ? 0.0 : c->h_gm_pinned[GS_REL];
+        if (info) {
+            info[i].iters = zero ? 0 : c->h_gmi_pinned[GI_ITS];
+            info[i].restarts = restarts[i];
+            info[i].relres_true = rel;
+            info[i].relres_est = c->h_gm_pinned[GS_RELEST];
+            info[i].t_solve_ms = ms;
+        }
+        int32_t apst[4];
+        BILU_CUDA(c0, cudaMemcpy(apst, c->d_apst, sizeof(apst), cudaMemcpyDeviceToHost));
+        if (apst[3] != 0) return set_err(c0, BILU_ERR_TIMEOUT, "apply kernel: bounded wait gave up");
+        if (rel > tol) result = BILU_NOT_CONVERGED;
+    }
+    return result;
+}
 
 bilu_status gmres_run(bilu_ctx *c, const double *b, double *x, double tol, int m, int maxit, gmres_info *info) {
     if (m < 1 || m > 1000 || maxit < 0 || !(tol >= 0.0)) return set_err(c, BILU_ERR_ARG, "bad gmres arguments");
@@ -375,11 +528,7 @@ bilu_status gmres_run(bilu_ctx *c, const double *b, double *x, double tol, int m
     BILU_CUDA(c, cudaEventRecord(e0, c->stream));
     BILU_CUDA(c, cudaMemcpyAsync(c->d_gb, b, n * sizeof(double), cudaMemcpyDefault, c->stream));
     BILU_CUDA(c, cudaMemcpyAsync(c->d_gx, x, n * sizeof(double), cudaMemcpyDefault, c->stream));
-    dot_kernel<<<G, VT, 0, c->stream>>>(n, c->d_gb, c->d_gb, c->d_part + 3 * G);
-    setup_kernel<<<1, 32, 0, c->stream>>>(c->d_gm, c->d_gmi, c->d_part, G, L.scal, tol, maxit, m);
-    launch_spmv(c, c->d_gx, c->d_r, c->d_gb, c->d_part + 3 * G, nullptr);
-    cycle_end_kernel<<<1, 32, 0, c->stream>>>(c->d_gm, c->d_gmi, c->d_part, G, L.scal, c->h_gm_pinned, c->h_gmi_pinned);
-    c->launches += 4;
+    gmres_start(c, tol, m, maxit);
     BILU_CUDA(c, cudaGetLastError());
     BILU_CUDA(c, cudaStreamSynchronize(c->stream));
     double bnorm = c->h_gm_pinned[GS_BNORM];
@@ -398,15 +547,7 @@ bilu_status gmres_run(bilu_ctx *c, const double *b, double *x, double tol, int m
             cudaError_t ce = cudaStreamEndCapture(c->stream, &graph);
             if (st != BILU_OK) return st;
             if (ce != cudaSuccess) return cuda_err(c, ce, "cudaStreamEndCapture");
-            size_t nn = 0;
-            cudaGraphGetNodes(graph, nullptr, &nn);
-            std::vector<cudaGraphNode_t> nodes(nn);
-            cudaGraphGetNodes(graph, nodes.data(), &nn);
-            c->gm_graph_kernels = 0;
-            for (auto nd : nodes) {
-                cudaGraphNodeType ty;
-                if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) c->gm_graph_kernels++;
-            }
+            c->gm_graph_kernels = count_kernel_nodes(graph);
             ce = cudaGraphInstantiate(&c->gm_graph, graph, 0);
             cudaGraphDestroy(graph);
             if (ce != cudaSuccess) return cuda_err(c, ce, "cudaGraphInstantiate");

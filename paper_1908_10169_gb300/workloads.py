@@ -189,3 +189,22 @@ def cd3d(side: int = 64, seed: int = 1, block: int = 64) -> Workload:
     [1e-3, 1e3] per node, |v| = 100 along (1,1,1); drop tolerance 1e-2; blocks of `block`."""
     A = convdiff_upwind((side, side, side), seed=seed)
     return Workload(f"cd3d_7pt_{side}^3", A, rhs_ones(A), 1e-2, 64, "fixed", block)
+
+
+def cd_batch(count: int = 64, seed0: int = 100, n_lo: float = 1e4, n_hi: float = 2e5, block: int = 64):
+    """Batch of uneven convection-diffusion matrices.  Matrix k has seed seed0 + k: even seeds
+    give 2D 5-point, odd seeds 3D 7-point upwind problems; the target size is log-uniform in
+    [n_lo, n_hi] (drawn from the seed), the grid side round(n^(1/2)) or round(n^(1/3)); kappa
+    log-uniform in [1e-3, 1e3] per node, |v| = 10 (Peclet 10 against kappa = 1).  Returns a list
+    of Workloads (fixed blocks of `block`, drop tolerance 1e-2)."""
+    out = []
+    for k in range(count):
+        seed = seed0 + k
+        rng = np.random.Generator(np.random.PCG64(seed))
+        n_target = math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))
+        dim = 2 if seed % 2 == 0 else 3
+        side = max(2, int(round(n_target ** (1.0 / dim))))
+        vel = tuple([10.0 / math.sqrt(dim)] * dim)
+        A = convdiff_upwind(tuple([side] * dim), vel=vel, seed=seed)
+        out.append(Workload(f"cd{dim}d_{side}_s{seed}", A, rhs_ones(A), 1e-2, 64, "fixed", min(block, side)))
+    return out

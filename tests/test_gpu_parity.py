@@ -285,3 +285,128 @@ def test_mixed_precision_factor_and_gmres(ctx, prec, bound, max_differ):
     err, differ = _rel_err_common(_oracle(A, g.bstart, 1e-2), g)
     assert err <= bound, err
     assert differ <= max_differ * (len(g.bstart) - 1), differ
+
+
+def test_batched_factor_and_gmres_match_one_by_one(ctx):
+    """Several uneven matrices factored in one launch (groups of CTAs, work queue) give the
+    same factors, bit for bit, as one-by-one factorizations -- on the first call (group size
+    from the count), the second (candidates timed), the third (tuned size) and with forced
+    group sizes of 1 and 3 CTAs -- and the batched GMRES (one graph, a branch per system) the
+    same iteration counts and solutions."""
+    import torch
+    ws = W.cd_batch(count=6, seed0=100, n_lo=300, n_hi=3000, block=16)
+    ctxs = [B.bilu_create(0) for _ in ws]
+    B.bilu_debug_set(ctxs[0], B.BILU_DEBUG_POISON, 1)  # an unwritten value shows as NaN
+    try:
+        for c, w in zip(ctxs, ws):
+            B.bilu_analyze(c, w.A.n, w.A.rowptr, w.A.colind, w.A.val,
+                           B.bilu_params_default(fixed_block=w.fixed_block, max_block=64))
+        singles, xsingle, ref = [], [], []
+        for w in ws:
+            g1 = gpu_factor(ctx, w.A, 1e-2, B.bilu_params_default(fixed_block=w.fixed_block, max_block=64))
+            ref.append(g1)
+            bt = torch.from_numpy(w.b).cuda()
+            x1 = torch.zeros_like(bt)
+            singles.append(B.gmres_solve(ctx, bt, x1, 1e-8, 30, 10000).iters)
+            xsingle.append(x1.cpu().numpy())
+
+        def check_factors(tag):
+            for c, w, g1 in zip(ctxs, ws, ref):
+                s = B.bilu_stats(c)
+                arrs = dict(Lptr=np.zeros(s.nblocks + 1, np.int64), Lrow=np.zeros(s.kept_rows, np.int32),
+                            Lval=np.zeros(s.nnz_l), Uptr=np.zeros(s.nblocks + 1, np.int64),
+                            Ucol=np.zeros(s.kept_cols, np.int32), Uval=np.zeros(s.nnz_u),
+                            Dinv=np.zeros(s.nnz_d), Pblk=np.zeros(s.nnz_d))
+                B.bilu_export(c, **arrs)
+                for k, v in arrs.items():
+                    assert np.array_equal(v, getattr(g1, k)), (tag, w.name, k)
+
+        for call in range(3):
+            B.bilu_factor_batch(ctxs, 1e-2)
+            check_factors(f"call {call}")
+        try:
+            for G in (1, 3):
+                B.bilu_debug_set(ctxs[0], B.BILU_DEBUG_BATCH_GROUP, G)
+                B.bilu_factor_batch(ctxs, 1e-2)
+                check_factors(f"G={G}")
+        finally:
+            B.bilu_debug_set(ctxs[0], B.BILU_DEBUG_BATCH_GROUP, 0)
+        # from minimal storage: every matrix is re-run (inside the batch launch) with grown
+        # pools and producer lists, the factors are still the same
+        small = [B.bilu_create(0) for _ in ws]
+        try:
+            B.bilu_debug_set(small[0], B.BILU_DEBUG_SMALL_POOLS, 1)
+            for c, w in zip(small, ws):
+                B.bilu_analyze(c, w.A.n, w.A.rowptr, w.A.colind, w.A.val,
+                               B.bilu_params_default(fixed_block=w.fixed_block, max_block=64))
+            B.bilu_factor_batch(small, 1e-2)
+            assert all(B.bilu_stats(c).pool_retries > 0 for c in small)
+            ctxs, kept = small, ctxs
+            check_factors("small pools")
+            ctxs = kept
+        finally:
+            B.bilu_debug_set(small[0], B.BILU_DEBUG_SMALL_POOLS, 0)
+            for c in small:
+                B.bilu_destroy(c)
+        bs = [torch.from_numpy(w.b).cuda() for w in ws]
+        for rep in range(2):
+            xs = [torch.zeros_like(v) for v in bs]
+            infos = B.gmres_solve_batch(ctxs, bs, xs, 1e-8, 30, 10000)
+            assert [i.iters for i in infos] == singles
+            assert all(i.relres_true <= 1e-8 for i in infos)
+            for x, x1 in zip(xs, xsingle):  # same kernels, same order: the same solution
+                assert np.array_equal(x.cpu().numpy(), x1)
+    finally:
+        B.bilu_debug_set(ctxs[0], B.BILU_DEBUG_POISON, 0)
+        for c in ctxs:
+            B.bilu_destroy(c)
+
+
+@pytest.mark.parametrize("G", [1, 2, 5])
+def test_batched_small_groups_large_blocks(ctx, G):
+    """Groups with fewer CTAs than half a block's columns (the inverse D_K = P_K^{-1} then
+    takes several columns per CTA and several rounds): same factors as one by one, with every
+    value array filled with NaN before each run."""
+    ws = W.cd_batch(count=3, seed0=200, n_lo=1500, n_hi=4000, block=48)
+    ctxs = [B.bilu_create(0) for _ in ws]
+    B.bilu_debug_set(ctxs[0], B.BILU_DEBUG_POISON, 1)
+    B.bilu_debug_set(ctxs[0], B.BILU_DEBUG_BATCH_GROUP, G)
+    try:
+        for c, w in zip(ctxs, ws):
+            B.bilu_analyze(c, w.A.n, w.A.rowptr, w.A.colind, w.A.val,
+                           B.bilu_params_default(fixed_block=w.fixed_block, max_block=64))
+        B.bilu_factor_batch(ctxs, 1e-2)
+        for c, w in zip(ctxs, ws):
+            g1 = gpu_factor(ctx, w.A, 1e-2, B.bilu_params_default(fixed_block=w.fixed_block, max_block=64))
+            s = B.bilu_stats(c)
+            assert s.nblocks == len(g1.bstart) - 1
+            arrs = dict(Lptr=np.zeros(s.nblocks + 1, np.int64), Lrow=np.zeros(s.kept_rows, np.int32),
+                        Lval=np.zeros(s.nnz_l), Uptr=np.zeros(s.nblocks + 1, np.int64),
+                        Ucol=np.zeros(s.kept_cols, np.int32), Uval=np.zeros(s.nnz_u),
+                        Dinv=np.zeros(s.nnz_d), Pblk=np.zeros(s.nnz_d))
+            B.bilu_export(c, **arrs)
+            for k, v in arrs.items():
+                assert np.array_equal(v, getattr(g1, k)), (w.name, k)
+    finally:
+        B.bilu_debug_set(ctxs[0], B.BILU_DEBUG_BATCH_GROUP, 0)
+        B.bilu_debug_set(ctxs[0], B.BILU_DEBUG_POISON, 0)
+        for c in ctxs:
+            B.bilu_destroy(c)
+
+
+def test_factor_rerun_from_minimal_storage(ctx):
+    """A factorization that starts from minimal pools and producer lists runs again with
+    grown storage until it fits, and ends with the same factor, bit for bit."""
+    A = W.cd3d(side=12, seed=3, block=12).A
+    p = B.bilu_params_default(fixed_block=12, max_block=64)
+    ref = gpu_factor(ctx, A, 1e-2, p)
+    c = B.bilu_create(0)
+    try:
+        B.bilu_debug_set(c, B.BILU_DEBUG_SMALL_POOLS, 1)
+        g = gpu_factor(c, A, 1e-2, p)
+        assert B.bilu_stats(c).pool_retries >= 2
+    finally:
+        B.bilu_debug_set(c, B.BILU_DEBUG_SMALL_POOLS, 0)
+        B.bilu_destroy(c)
+    for k in ("Lptr", "Lrow", "Lval", "Uptr", "Ucol", "Uval", "Dinv", "Pblk"):
+        assert np.array_equal(getattr(g, k), getattr(ref, k)), k
