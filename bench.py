@@ -42,7 +42,10 @@ def parse():
     ap.add_argument("--side", type=int, default=64)
     ap.add_argument("--block", type=int, default=64)
     ap.add_argument("--precision", choices=["fp64", "fp32", "bf16"], default="fp64")
-    ap.add_argument("--skip", choices=["none", "bound"], default="none")
+    ap.add_argument("--skip", choices=["none", "bound", "learned"], default="none")
+    ap.add_argument("--train-count", type=int, default=200,
+                    help="learned skip: training problems (3D 7-point, sides 32..48, Peclet 1..1000)")
+    ap.add_argument("--train-rate", type=float, default=0.05, help="learned skip: share of candidates recorded")
     ap.add_argument("--batch", type=int, default=0,
                     help="factor + solve this many uneven 2D/3D matrices in one batched launch instead")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -224,7 +227,20 @@ def run_gpu(args):
     params = B.bilu_params_default(blocking=B.BILU_BLOCKING_FIXED, fixed_block=args.block, max_block=64,
                                    precision={"fp64": B.BILU_PREC_FP64, "fp32": B.BILU_PREC_FP32,
                                               "bf16": B.BILU_PREC_BF16}[args.precision],
-                                   skip={"none": B.BILU_SKIP_NONE, "bound": B.BILU_SKIP_BOUND}[args.skip])
+                                   skip={"none": B.BILU_SKIP_NONE, "bound": B.BILU_SKIP_BOUND,
+                                         "learned": B.BILU_SKIP_LEARNED}[args.skip])
+    learned = None
+    if args.skip == "learned":  # train the classifier first (not timed)
+        from paper_1908_10169_gb300 import learned_skip as LS
+        from paper_1908_10169_gb300 import workloads as W
+        t0 = time.time()
+        xs, ys = LS.record(W.cd3d_skip_train(count=args.train_count), device=local, rate=args.train_rate)
+        t1 = time.time()
+        sm = LS.train(xs, ys, device=local, epochs=4, batch=4096, lr=2e-3, seed=1, max_false_drop=2e-3)
+        learned = {"train_problems": args.train_count, "samples": sm.samples, "drop_fraction": sm.drop_fraction,
+                   "train_loss": sm.train_loss, "logit_hi": sm.logit_hi, "train_skip_rate": sm.skip_rate,
+                   "train_false_drop_rate": sm.false_drop_rate, "record_s": t1 - t0, "train_s": time.time() - t1}
+        B.bilu_set_skip_model(ctx, sm.model, sm.logit_hi)
     rp = torch.from_numpy(w.A.rowptr.astype(np.int64)).to(dev)
     ci = torch.from_numpy(w.A.colind.astype(np.int32)).to(dev)
     va = torch.from_numpy(w.A.val).to(dev)
@@ -337,6 +353,8 @@ def run_gpu(args):
         h_b = torch.from_numpy(w.b).pin_memory()
         h_x = torch.zeros(n, dtype=torch.float64).pin_memory()
         ctx2 = B.bilu_create(local, stream)
+        if learned is not None:
+            B.bilu_set_skip_model(ctx2, sm.model, sm.logit_hi)
         et = []
         for k in range(min(args.steps, 3) + 1):
             torch.cuda.synchronize()
@@ -361,6 +379,22 @@ def run_gpu(args):
                "sample": f"one full step (oracle factor {tfo:.1f} s + GMRES {tgo:.1f} s, {it_o} iters) on the "
                          f"same matrix; host {model}, {cores} cores visible, 1 used",
                "gmres_iters": it_o}
+    if learned is not None:  # the method without the skip on the same matrix, for the gain
+        learned.update({"skipped": st.skipped_rows + st.skipped_cols, "candidates": st.cand_rows + st.cand_cols,
+                        "kept": st.kept_rows + st.kept_cols, "flops_factor": st.flops_factor})
+        ctx3 = B.bilu_create(local, stream)
+        params.skip = B.BILU_SKIP_NONE
+        B.bilu_analyze(ctx3, w.A.n, rp, ci, va, params)
+        for _ in range(2):
+            B.bilu_factor(ctx3, w.droptol)
+        s3 = B.bilu_stats(ctx3)
+        with torch.cuda.stream(stream):
+            x.zero_()
+        i3 = B.gmres_solve(ctx3, b, x, w.gmres_tol, w.restart, 10000)
+        learned.update({"exact_factor_ms": s3.t_factor_ms, "exact_flops_factor": s3.flops_factor,
+                        "exact_kept": s3.kept_rows + s3.kept_cols, "exact_gmres_iters": i3.iters,
+                        "exact_solve_ms": i3.t_solve_ms})
+        B.bilu_destroy(ctx3)
     B.bilu_destroy(ctx)
     if rank == 0:
         line = {"metric": METRIC, "value": ms / 1e3 / world, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -375,7 +409,8 @@ def run_gpu(args):
                                            "factor_phase_ms": dict(zip(["candidates", "pivot_rows+lu", "inverse",
                                                                         "bound_skip_updates", "scale_drop", "compact",
                                                                         "cta0_lu_work", "cta0_pivot_tile_wait"],
-                                                                       [round(v, 3) for v in st.phase_ms]))}),
+                                                                       [round(v, 3) for v in st.phase_ms])),
+                                           **({"learned_skip": learned} if learned is not None else {})}),
                 "roofline": dominant, "roofline_other": other,
                 "gpu_launches": launches, "clocks": clk.summary(), "e2e": e2e, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
@@ -406,12 +441,23 @@ def run_batch(args):
     ws = W.cd_batch(count=args.batch, seed0=100)
     prec = {"fp64": B.BILU_PREC_FP64, "fp32": B.BILU_PREC_FP32, "bf16": B.BILU_PREC_BF16}[args.precision]
     stream = torch.cuda.Stream(device=dev)
+    skip = {"none": B.BILU_SKIP_NONE, "bound": B.BILU_SKIP_BOUND, "learned": B.BILU_SKIP_LEARNED}[args.skip]
+    learned = None
+    if args.skip == "learned":  # train the classifier first (not timed)
+        from paper_1908_10169_gb300 import learned_skip as LS
+        xtr, ytr = LS.record(W.cd3d_skip_train(count=args.train_count), device=local, rate=args.train_rate)
+        sm = LS.train(xtr, ytr, device=local, epochs=4, batch=4096, lr=2e-3, seed=1, max_false_drop=2e-3)
+        learned = {"train_problems": args.train_count, "samples": sm.samples, "logit_hi": sm.logit_hi,
+                   "train_skip_rate": sm.skip_rate}
+        progress(f"classifier trained on {sm.samples} samples")
     ctxs, bs, xs = [], [], []
     for w in ws:
         c = B.bilu_create(local, stream if not ctxs else None)
         B.bilu_analyze(c, w.A.n, torch.from_numpy(w.A.rowptr).to(dev), torch.from_numpy(w.A.colind).to(dev),
                        torch.from_numpy(w.A.val).to(dev),
-                       B.bilu_params_default(fixed_block=w.fixed_block, max_block=64, precision=prec))
+                       B.bilu_params_default(fixed_block=w.fixed_block, max_block=64, precision=prec, skip=skip))
+        if learned is not None:
+            B.bilu_set_skip_model(c, sm.model, sm.logit_hi)
         ctxs.append(c)
         bs.append(torch.from_numpy(w.b).to(dev))
         xs.append(torch.zeros(w.A.n, dtype=torch.float64, device=dev))
@@ -443,6 +489,10 @@ def run_batch(args):
             times.append(e0.elapsed_time(e1))
             progress(f"timed step: {times[-1]:.1f} ms")
     launches = (sum(B.bilu_stats(c).kernel_launches for c in ctxs) - l0) / args.steps
+    batch_factor_ms, batch_gmres_ms = B.bilu_stats(ctxs[0]).t_factor_ms, infos[0].t_solve_ms
+    if learned is not None:
+        learned.update({"skipped": sum(B.bilu_stats(c).skipped_rows + B.bilu_stats(c).skipped_cols for c in ctxs),
+                        "candidates": sum(B.bilu_stats(c).cand_rows + B.bilu_stats(c).cand_cols for c in ctxs)})
     ms = sum(times) / len(times)
     iters_b = [i.iters for i in infos]
     # the same systems one by one, plain FP64
@@ -474,7 +524,9 @@ def run_batch(args):
                        "updates": args.precision, "gmres_iters_batched": iters_b, "gmres_iters_plain_fp64": iters_s,
                        "max_iter_ratio": max(a / max(1, b2) for a, b2 in zip(iters_b, iters_s)),
                        "plain_fp64_one_by_one_s": t_seq / 1e3, "speedup_vs_plain_one_by_one": t_seq / ms,
-                       "l2": "flushed (512 MB write) before every timed step"},
+                       "l2": "flushed (512 MB write) before every timed step", "skip": args.skip,
+                       "batch_factor_ms": batch_factor_ms, "batch_gmres_ms": batch_gmres_ms,
+                       **({"learned_skip": learned} if learned is not None else {})},
             "gpu_launches": launches, "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
     return 0

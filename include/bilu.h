@@ -68,7 +68,9 @@ typedef struct {
                             BILU_SKIP_BOUND: after D_K is known, a candidate row i is skipped
                             when (||A(i,B_K)|| + sum_J ||L_J(i,:)|| ||U_J(:,B_K)||_F) ||D_K||_F
                             <= tau (1 - 1e-10), which proves ||l_i|| <= tau (triangle inequality,
-                            ||D_K||_2 <= ||D_K||_F); columns likewise.  Same factor as without. */
+                            ||D_K||_2 <= ||D_K||_F); columns likewise.  Same factor as without.
+                            BILU_SKIP_LEARNED: a classifier decides before the updates (see
+                            bilu_set_skip_model); needs a model.                                */
 } bilu_params;
 
 typedef struct {
@@ -94,8 +96,9 @@ typedef struct {
                                  inverse 4/3)                                           */
     int64_t flop_upd_l;       /* 2 m n b_J summed over the L-side block updates        */
     int64_t flop_upd_u;       /* 2 m n b_J summed over the U-side block updates        */
-    int64_t flop_scale;       /* 2 b_K^2 per candidate row and column (D_K products)   */
-    int64_t flop_norm;        /* 2 b_K per candidate row and column (drop norms)       */
+    int64_t flop_scale;       /* 2 b_K^2 per candidate row and column (D_K products),
+                                 skipped candidates excluded                            */
+    int64_t flop_norm;        /* 2 b_K per candidate row and column (drop norms), ditto */
     double t_analyze_ms, t_factor_ms;
     int32_t pool_retries;     /* factor re-runs after growing the L/U pools             */
     int64_t kernel_launches;  /* kernels of this library launched on the context so far
@@ -106,8 +109,8 @@ typedef struct {
                                  updates (norm-bound skip only); scaling + dropping;
                                  compaction.  Then CTA 0's time inside the pivot LU and
                                  waiting for the pivot-row updates                      */
-    int64_t skipped_rows;     /* candidate rows / columns the norm bound proved dropped  */
-    int64_t skipped_cols;     /* (BILU_SKIP_BOUND), whose products were not computed     */
+    int64_t skipped_rows;     /* candidate rows / columns skipped (norm bound proved them */
+    int64_t skipped_cols;     /* dropped, or the classifier predicted it): not computed  */
 } bilu_stats_t;
 
 /* Fills *p with the defaults: FIXED blocking of 32 (max 64), tau_analyze 1e-2,
@@ -252,6 +255,81 @@ bilu_status bilu_debug_set(bilu_ctx *ctx, int32_t what, int64_t value);
  * a device-side wait that gives up is not reported.  Calls no cudaMalloc / cudaFree.
  */
 bilu_status bilu_apply_noalloc(bilu_ctx *ctx, const double *r, double *z);
+
+/*
+ * ---- Learned skip (BILU_SKIP_LEARNED) ----------------------------------------------------
+ * The paper drops a row of L (a column of U) after computing it, when its norm is <= tau
+ * (Sec. 3).  The learned skip predicts that outcome before the row's Schur updates are
+ * computed: a classifier maps features of candidate row i of block K (column j on the U
+ * side) to a logit z of P(dropped); rows with z >= logit_hi are neither updated nor scaled
+ * and count as dropped, all others are computed and tested exactly.  The paper has no such
+ * predictor; a wrong "drop" changes the factor (a row that would have been kept is lost),
+ * so logit_hi is chosen for a small false-drop rate on training data.
+ *
+ * Features (FP32, BILU_MLP_FEATURES per candidate), with lg(x) = log10(max(x, 1e-30)), the
+ * candidate's producers J (blocks whose kept rows of L (columns of U-breve) contain it) and
+ * X_J = its row of L_J (column of U-breve_J), Y_J = L_J's rows in B_K / U-breve_J's columns
+ * in B_K:
+ *   0 lg a, a = ||A(i, B_K)||           1 1 if A(i, B_K) has a nonzero, else 0
+ *   2 lg s, s = sum_J ||X_J|| ||Y_J||_F   3 lg max_J ||X_J|| ||Y_J||_F
+ *   4 log2(1 + number of producers)      5 lg d, d = ||D_{K-1}||_F (1/alpha for K = 0)
+ *   6 lg ((a + s) d)                     7 lg tau
+ *   8 b_K / 64                           9 mean b_J over the producers / 64 (0 if none)
+ *   10 log2(1 + max(0, i - s_K) / 64)    11 side: 0 row of L, 1 column of U
+ * Classifier: x' = (x - mean) / std, h1 = relu(W1 x' + b1), h2 = relu(W2 h1 + b2),
+ * z = w3 . h2 + b3; 64 hidden units per layer; weights and biases stored in FP16, products
+ * accumulated in FP32.  Model array (FP32, BILU_MLP_PARAMS entries, host memory):
+ *   mean[F] std[F] W1[64][F] b1[64] W2[64][64] b2[64] w3[64] b3   (F = BILU_MLP_FEATURES)
+ * the weights are rounded to FP16 wherever they are used.
+ */
+#define BILU_MLP_FEATURES 12
+#define BILU_MLP_HIDDEN 64
+#define BILU_MLP_PARAMS (2 * BILU_MLP_FEATURES + BILU_MLP_HIDDEN * BILU_MLP_FEATURES + BILU_MLP_HIDDEN + \
+                         BILU_MLP_HIDDEN * BILU_MLP_HIDDEN + BILU_MLP_HIDDEN + BILU_MLP_HIDDEN + 1)
+
+typedef struct {
+    int32_t epochs;      /* passes over the samples                                     */
+    int32_t batch;       /* samples per Adam step (drawn with replacement), 1..65536   */
+    float lr;            /* Adam step size (beta1 0.9, beta2 0.999, eps 1e-8)           */
+    uint64_t seed;       /* initial weights and sample draws                            */
+} bilu_mlp_train_cfg;
+
+/*
+ * Records training samples during the following factorizations of ctx (exact ones: no
+ * skipping while recording): each candidate row / column is taken with probability `rate`
+ * (a counter-based hash of seed, K and slot decides), its features and its label (1 dropped,
+ * 0 kept) appended until `capacity` samples are held.  capacity 0 stops recording and frees
+ * the buffer.  bilu_get_samples copies up to cap samples (x: cap x F row-major, y: cap, tags:
+ * cap or NULL; host or device memory) and the number held in *count.  A tag identifies the
+ * candidate: K * 2^33 + side * 2^32 + its global row (side 0) or column (side 1) index.
+ * Sample order is not deterministic; a factorization that re-runs with grown storage keeps
+ * only the samples of its final run.
+ */
+bilu_status bilu_record_samples(bilu_ctx *ctx, int64_t capacity, double rate, uint64_t seed);
+bilu_status bilu_get_samples(bilu_ctx *ctx, float *x, float *y, int64_t *tags, int64_t cap, int64_t *count);
+
+/*
+ * Trains the classifier on n samples (x: n x F row-major, y: n labels in {0, 1}; host or
+ * device memory) with the binary cross-entropy of the logits, mean over each batch: feature
+ * mean / std from the samples, weights uniform in +-1/sqrt(fan-in), Adam on FP32 master
+ * weights whose FP16 roundings are used in the forward and backward passes.  Deterministic
+ * for a given seed.  Writes the model (host, BILU_MLP_PARAMS) and, if final_loss is not NULL,
+ * the mean cross-entropy over all n samples at the end.  Runs on ctx's device and stream
+ * (ctx needs no matrix); synchronizes.
+ */
+bilu_status bilu_mlp_train(bilu_ctx *ctx, const float *x, const float *y, int64_t n, const bilu_mlp_train_cfg *cfg,
+                           float *model, double *final_loss);
+
+/* Logits of n samples (x host or device; logits host or device, n entries). */
+bilu_status bilu_mlp_forward(bilu_ctx *ctx, const float *model, const float *x, int64_t n, float *logits);
+
+/* Gradient of the mean cross-entropy over n samples with respect to the model entries
+ * (host, BILU_MLP_PARAMS; zero for mean and std), at the FP16-rounded weights. */
+bilu_status bilu_mlp_grad(bilu_ctx *ctx, const float *model, const float *x, const float *y, int64_t n, float *grad);
+
+/* Installs the model used by BILU_SKIP_LEARNED factorizations of ctx: a candidate is skipped
+ * when its logit is >= logit_hi (the pivot rows of a block are never skipped). */
+bilu_status bilu_set_skip_model(bilu_ctx *ctx, const float *model, double logit_hi);
 
 /* Releases the context and all device memory it owns.  NULL is ignored. */
 void bilu_destroy(bilu_ctx *ctx);

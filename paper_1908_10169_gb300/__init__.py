@@ -29,7 +29,14 @@ BILU_MAX_BLOCK = 64
 EXPORTED = ["bilu_params_default", "bilu_create", "bilu_analyze", "bilu_factor", "bilu_apply",
             "gmres_solve", "bilu_stats", "bilu_get_partition", "bilu_export", "bilu_last_error",
             "bilu_debug_set", "bilu_apply_noalloc", "bilu_factor_batch", "gmres_solve_batch",
-            "bilu_destroy"]
+            "bilu_record_samples", "bilu_get_samples", "bilu_mlp_train", "bilu_mlp_forward", "bilu_mlp_grad",
+            "bilu_set_skip_model", "bilu_destroy"]
+
+# learned skip classifier (layout of the model array: mean[F] std[F] W1[64][F] b1[64] W2[64][64]
+# b2[64] w3[64] b3)
+BILU_MLP_FEATURES = 12
+BILU_MLP_HIDDEN = 64
+BILU_MLP_PARAMS = 2 * 12 + 64 * 12 + 64 + 64 * 64 + 64 + 64 + 1
 
 
 class bilu_params(ct.Structure):
@@ -54,6 +61,10 @@ class bilu_stats_t(ct.Structure):
                 ("t_factor_ms", ct.c_double), ("pool_retries", ct.c_int32),
                 ("kernel_launches", ct.c_int64), ("phase_ms", ct.c_double * 8),
                 ("skipped_rows", ct.c_int64), ("skipped_cols", ct.c_int64)]
+
+
+class bilu_mlp_train_cfg(ct.Structure):
+    _fields_ = [("epochs", ct.c_int32), ("batch", ct.c_int32), ("lr", ct.c_float), ("seed", ct.c_uint64)]
 
 
 class BiluError(RuntimeError):
@@ -88,6 +99,12 @@ def lib():
             "bilu_apply_noalloc": ([P, P, P], i32),
             "bilu_factor_batch": ([P, i32, f64], i32),
             "gmres_solve_batch": ([P, i32, P, P, f64, i32, i32, P], i32),
+            "bilu_record_samples": ([P, i64, f64, ct.c_uint64], i32),
+            "bilu_get_samples": ([P, P, P, P, i64, ct.POINTER(i64)], i32),
+            "bilu_mlp_train": ([P, P, P, i64, ct.POINTER(bilu_mlp_train_cfg), P, ct.POINTER(f64)], i32),
+            "bilu_mlp_forward": ([P, P, P, i64, P], i32),
+            "bilu_mlp_grad": ([P, P, P, P, i64, P], i32),
+            "bilu_set_skip_model": ([P, P, f64], i32),
             "bilu_destroy": ([P], None),
         }
         for name, (args, res) in sig.items():
@@ -214,3 +231,44 @@ def bilu_export(ctx, Lptr=None, Lrow=None, Lval=None, Uptr=None, Ucol=None, Uval
 
 def bilu_debug_set(ctx, what: int, value: int):
     return _check(ctx, lib().bilu_debug_set(ctx, what, value))
+
+
+# ---- learned skip --------------------------------------------------------------------------
+
+def bilu_record_samples(ctx, capacity: int, rate: float = 1.0, seed: int = 0):
+    """Record (features, label) samples of the candidates in the following factorizations."""
+    return _check(ctx, lib().bilu_record_samples(ctx, capacity, rate, seed))
+
+
+def bilu_get_samples(ctx, x=None, y=None, tags=None, cap: int = 0) -> int:
+    """Copies up to cap samples into x (cap x F float32), y (cap float32), tags (cap int64 or
+    None); returns the number of samples held."""
+    cnt = ct.c_int64()
+    _check(ctx, lib().bilu_get_samples(ctx, _ptr(x), _ptr(y), _ptr(tags), cap, ct.byref(cnt)))
+    return cnt.value
+
+
+def bilu_mlp_train(ctx, x, y, epochs: int = 4, batch: int = 4096, lr: float = 2e-3, seed: int = 0):
+    """Trains the classifier on n samples (x n x F float32, y n float32); returns (model, loss)."""
+    import numpy as np
+    n = int(y.shape[0])
+    cfg = bilu_mlp_train_cfg(epochs, batch, lr, seed)
+    model = np.zeros(BILU_MLP_PARAMS, np.float32)
+    loss = ct.c_double()
+    _check(ctx, lib().bilu_mlp_train(ctx, _ptr(x), _ptr(y), n, ct.byref(cfg), _ptr(model), ct.byref(loss)))
+    return model, loss.value
+
+
+def bilu_mlp_forward(ctx, model, x, logits):
+    return _check(ctx, lib().bilu_mlp_forward(ctx, _ptr(model), _ptr(x), int(logits.shape[0]), _ptr(logits)))
+
+
+def bilu_mlp_grad(ctx, model, x, y):
+    import numpy as np
+    g = np.zeros(BILU_MLP_PARAMS, np.float32)
+    _check(ctx, lib().bilu_mlp_grad(ctx, _ptr(model), _ptr(x), _ptr(y), int(y.shape[0]), _ptr(g)))
+    return g
+
+
+def bilu_set_skip_model(ctx, model, logit_hi: float):
+    return _check(ctx, lib().bilu_set_skip_model(ctx, _ptr(model), logit_hi))

@@ -34,8 +34,8 @@ enum {
     INFO_PHASE_NS = 10,      // 6 slots: time of the phases A, B, C, C2, D, E (CTA 0)
     INFO_C2_WORK_NS = 16,    // time CTA 0 spends inside the pivot LU
     INFO_B_WORK_NS = 17,     // time CTA 0 waits for the pivot-row tiles
-    INFO_SKIP_ROWS = 18,     // candidate rows skipped by the norm bound
-    INFO_SKIP_COLS = 19,     // candidate columns skipped by the norm bound
+    INFO_SKIP_ROWS = 18,     // candidate rows skipped (norm bound or classifier)
+    INFO_SKIP_COLS = 19,     // candidate columns skipped
     INFO_COUNT = 24
 };
 
@@ -116,6 +116,20 @@ struct bilu_ctx {
     const double *gm_graph_b = nullptr;
     double *gm_graph_x = nullptr;
 
+    // learned skip: classifier (FP32 normalisation, FP16 weights) and sample recording
+    float *d_mlp_norm = nullptr;
+    void *d_mlp_w = nullptr;       // __half[MW]
+    double mlp_logit_hi = 0.0;
+    int64_t rec_cap = 0;           // > 0: recording samples
+    uint32_t rec_thresh = 0;       // a candidate is taken when its hash (32 bits) < rec_thresh
+    uint64_t rec_seed = 0;
+    float *d_rec_x = nullptr, *d_rec_y = nullptr;
+    int64_t *d_rec_tag = nullptr;
+    unsigned long long *d_rec_count = nullptr;
+    unsigned long long rec_base = 0;  // samples held before the current factorization
+    float *d_featL = nullptr, *d_featU = nullptr;  // capT x F features of the current block's candidates
+    int64_t feat_cap = 0;
+
     // results of the last factorization
     int64_t kept_rows = 0, kept_cols = 0, nnz_l = 0, nnz_u = 0, cand_rows = 0, cand_cols = 0;
     int64_t nperturb = 0, skipped_rows = 0, skipped_cols = 0;
@@ -165,3 +179,4 @@ bilu_status factor_batch_run(bilu_ctx *const *ctxs, int count, double droptol, d
 bilu_status analyze_run(bilu_ctx *c, int64_t n, const int64_t *rowptr, const int32_t *colind,
                         const double *val, int on_device, const bilu_params *p);
 void matrix_free(bilu_ctx *c);
+void mlp_free(bilu_ctx *c);

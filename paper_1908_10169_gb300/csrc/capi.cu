@@ -88,6 +88,7 @@ void bilu_destroy(bilu_ctx *c) {
     apply_free(c);
     factor_free(c);
     matrix_free(c);
+    mlp_free(c);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -107,8 +108,8 @@ bilu_status bilu_factor(bilu_ctx *c, double droptol) {
     c->err.clear();
     if (c->state < 1) return set_err(c, BILU_ERR_STATE, "bilu_factor before bilu_analyze");
     if (!(droptol >= 0.0) || !std::isfinite(droptol)) return set_err(c, BILU_ERR_ARG, "droptol must be finite and >= 0");
-    if (c->p.skip == BILU_SKIP_LEARNED)
-        return set_err(c, BILU_ERR_ARG, "skip mode not available in this build");
+    if (c->p.skip == BILU_SKIP_LEARNED && !c->d_mlp_w && c->rec_cap == 0)
+        return set_err(c, BILU_ERR_STATE, "BILU_SKIP_LEARNED needs a model (bilu_set_skip_model)");
     BILU_CUDA(c, cudaSetDevice(c->device));
     c->state = 1;
     gmres_free(c);  // captured graphs refer to the previous factor
@@ -177,7 +178,9 @@ bilu_status bilu_factor_batch(bilu_ctx *const *ctxs, int32_t count, double dropt
             if (ctxs[k] == c) return set_err(c0, BILU_ERR_ARG, "bilu_factor_batch: a context appears twice");
     }
     if (!(droptol >= 0.0) || !std::isfinite(droptol)) return set_err(c0, BILU_ERR_ARG, "droptol must be finite and >= 0");
-    if (c0->p.skip == BILU_SKIP_LEARNED) return set_err(c0, BILU_ERR_ARG, "skip mode not available in this build");
+    for (int32_t i = 0; i < count; ++i)
+        if (ctxs[i]->p.skip == BILU_SKIP_LEARNED && !ctxs[i]->d_mlp_w && ctxs[i]->rec_cap == 0)
+            return set_err(c0, BILU_ERR_STATE, "BILU_SKIP_LEARNED needs a model on every context (bilu_set_skip_model)");
     BILU_CUDA(c0, cudaSetDevice(c0->device));
     for (int32_t i = 0; i < count; ++i) {
         ctxs[i]->state = 1;

@@ -23,6 +23,7 @@
 #include <cuda_bf16.h>
 
 #include "dev_common.cuh"
+#include "mlp.cuh"
 
 namespace {
 
@@ -94,6 +95,21 @@ struct FactorArgs {
     double *dcolsq;              // squared column norms of D_K (b entries)
     uint32_t *pivdone;           // pivot-row tiles finished for the current block
     double *nrmL, *nrmU;         // per candidate slot: ||l_i|| and ||T_U[:,j]|| (phase D -> E)
+    // learned skip: classifier (FP32 normalisation, FP16 weights) and its logit threshold
+    int32_t learned;
+    float zhi;
+    const float *mlp_norm;
+    const __half *mlp_w;
+    // sample recording: features per candidate slot of the current block (phase B -> D),
+    // the sample arrays and their fill count
+    int32_t record;
+    uint32_t rec_thresh;
+    uint64_t rec_seed;
+    long long rec_cap;
+    float *featL, *featU;
+    float *rec_x, *rec_y;
+    long long *rec_tag;
+    unsigned long long *rec_count;
 };
 
 // pinfo layout (per producer t of the current block)
@@ -169,8 +185,8 @@ __device__ void phase_A(const FactorArgs &a, int K, bool Lside, char *smem) {
             xval = uv + (int64_t)(xbeg - u0) * bJ;
             yval = lv + (int64_t)(ybeg - l0) * bJ;
         }
-        double yf = 0.0;  // Frobenius norm of the producer's Y block (norm-bound skip)
-        if (a.skip_bound) {
+        double yf = 0.0;  // Frobenius norm of the producer's Y block (norm-bound skip, features)
+        if (a.skip_bound || a.learned || a.record) {
             const double *nrm = Lside ? a.Unrm : a.Lnrm;
             double acc = 0.0;
             for (int y = ybeg + lane; y < yend; y += 32) {
@@ -339,8 +355,118 @@ __device__ __forceinline__ void prefetch_producer(const FactorArgs &a, bool Lsid
 // gets an upper bound of ||T[i,:]||: ||A part|| + sum_J ||X row of J|| * ||Y block of J||_F.
 // Rows with bound * ||D_K||_F <= tau (1 - 1e-10) are provably dropped (||l_i|| <= ||T[i,:]||
 // ||D_K||_2): their products and scaling are skipped and their keep flag is set to -1.
+// feat = true (candidate tiles with the learned skip or sample recording): the tile's rows get
+// their classifier features (written out when recording); with the learned skip, rows whose
+// logit reaches the threshold are skipped the same way.
+// log10(max(x, 1e-30)) in FP32 (x rounded to FP32 first, then clamped)
+__device__ __forceinline__ float lg30f(double x) { return log10f(fmaxf((float)x, 1e-30f)); }
+
+// Features of the tile's candidate rows (learned skip, recording) and, with the learned skip,
+// the classifier's decisions.  Kept out of line so that it adds no register pressure to the
+// update loop of the tile.
+__device__ __noinline__ void tile_features(const FactorArgs &a, int K, bool Lside, int sa, int cnt, int b, int s1,
+                                           int pcnt, const int32_t *xslot, const int32_t *poff, const int32_t *sxs,
+                                           const int32_t *sxe, const int32_t *pxp, const int32_t *pbJ,
+                                           const double *pyf, const int32_t *g, const double *bnd, const double *sdf,
+                                           const int32_t *sina, double *pn, float *sfeat, float *sh1, float *sh2,
+                                           int32_t *act, int32_t *sskip) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // per tile row, over its producers in a fixed order (chunks of 32 producers, lane t of
+    // a chunk takes producer c0 + t, lanes combined by a butterfly): sum, max and count of
+    // ||X row of J|| ||Y block of J||_F and the sum of b_J
+    const double *Xn = Lside ? a.Lnrm : a.Unrm;
+    double Sl = 0.0, Ml = 0.0;
+    int Cl = 0, Bl = 0;
+    for (int c0 = 0; c0 < pcnt; c0 += 32) {
+        for (int e = tid; e < TRMAX * 32; e += NT) pn[e] = -1.0;
+        __syncthreads();
+        for (int t = c0 + warp; t < min(pcnt, c0 + 32); t += NW) {
+            const int nx = sxe[t] - sxs[t];
+            for (int x = lane; x < nx; x += 32) {
+                const int r = ldcg(xslot + poff[t] + sxs[t] + x) - sa;
+                if (r >= 0 && r < cnt) pn[r * 32 + (t - c0)] = ldcg(Xn + pxp[t] + sxs[t] + x) * pyf[t];
+            }
+        }
+        __syncthreads();
+        if (warp < cnt) {
+            const double v = pn[warp * 32 + lane];
+            if (v >= 0.0) {
+                Sl += v;
+                Ml = fmax(Ml, v);
+                ++Cl;
+                Bl += pbJ[c0 + lane];
+            }
+        }
+        __syncthreads();
+    }
+    if (warp < cnt) {
+        const double S = warp_sum(Sl);
+        double M = Ml;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) M = fmax(M, __shfl_xor_sync(FULL_MASK, M, o));
+        const int C = warp_sum_i(Cl), SB = warp_sum_i(Bl);
+        // lane k forms feature k; the logarithms in FP32 (FP64 transcendentals are slow here)
+        const int r = warp;
+        const double av = bnd[r], d = sdf[1];
+        float f = 0.f;
+        switch (lane) {
+            case 0: f = lg30f(av); break;
+            case 1: f = sina[r] ? 1.f : 0.f; break;
+            case 2: f = lg30f(S); break;
+            case 3: f = lg30f(M); break;
+            case 4: f = log2f(1.f + (float)C); break;
+            case 5: f = lg30f(d); break;
+            case 6: f = lg30f((av + S) * d); break;
+            case 7: f = lg30f(a.tau); break;
+            case 8: f = (float)b / 64.f; break;
+            case 9: f = C > 0 ? (float)SB / (float)C / 64.f : 0.f; break;
+            case 10: f = log2f(1.f + (float)max(0, g[r] - s1) / 64.f); break;
+            case 11: f = Lside ? 0.f : 1.f; break;
+            default: break;
+        }
+        if (lane < MF) sfeat[r * MF + lane] = f;
+    }
+    __syncthreads();
+    if (a.record) {
+        float *fo = (Lside ? a.featL : a.featU) + (int64_t)sa * MF;
+        for (int e = tid; e < cnt * MF; e += NT) fo[e] = sfeat[e];
+    }
+    if (a.learned) {
+        // the classifier, in the summation order of the sequential inference
+        for (int e = tid; e < cnt * MF; e += NT) sfeat[e] = mlp_std(a.mlp_norm, e % MF, sfeat[e]);
+        __syncthreads();
+        for (int e = tid; e < cnt * MH; e += NT) {
+            const int r = e / MH, u = e - r * MH;
+            float acc = mlp_w(a.mlp_w, MO_B1 + u);
+            for (int k = 0; k < MF; ++k) acc = fmaf(mlp_w(a.mlp_w, MO_W1 + u * MF + k), sfeat[r * MF + k], acc);
+            sh1[e] = fmaxf(acc, 0.f);
+        }
+        __syncthreads();
+        for (int e = tid; e < cnt * MH; e += NT) {
+            const int r = e / MH, u = e - r * MH;
+            float acc = mlp_w(a.mlp_w, MO_B2 + u);
+            for (int k = 0; k < MH; ++k) acc = fmaf(mlp_w(a.mlp_w, MO_W2 + u * MH + k), sh1[r * MH + k], acc);
+            sh2[e] = fmaxf(acc, 0.f);
+        }
+        __syncthreads();
+        int32_t *kp = Lside ? a.keepL : a.keepU;
+        for (int r = tid; r < cnt; r += NT) {
+            float z = mlp_w(a.mlp_w, MO_B3);
+            for (int u = 0; u < MH; ++u) z = fmaf(mlp_w(a.mlp_w, MO_W3 + u), sh2[r * MH + u], z);
+            const bool pivot_row = Lside && sa + r < b;
+            const bool drop = !pivot_row && z >= a.zhi;
+            act[r] = drop ? 0 : 1;
+            kp[sa + r] = drop ? -1 : 0;
+            if (drop) atomicAdd(sskip, 1);
+        }
+        __syncthreads();
+    }
+    }
+
 template <class TS>
-__device__ void phase_B_tile(const FactorArgs &a, int K, bool Lside, int sa, int cnt, char *smem, bool bound) {
+__device__ void phase_B_tile(const FactorArgs &a, int K, bool Lside, int sa, int cnt, char *smem, bool bound,
+                             bool feat = false) {
+    static_assert(TRMAX <= NW, "one warp per tile row in the feature pass");
     using TA = typename Prec<TS>::TA;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int s0 = a.bstart[K], s1 = a.bstart[K + 1], b = s1 - s0;
@@ -363,8 +489,14 @@ __device__ void phase_B_tile(const FactorArgs &a, int K, bool Lside, int sa, int
     int32_t *act = pxp + PMAX;                   // TRMAX: row active (not provably dropped)
     double *pyf = (double *)(act + TRMAX);       // PMAX: Frobenius norm of the Y block
     double *bnd = pyf + PMAX;                    // TRMAX: bound of ||T[i,:]||
-    double *sdf = bnd + TRMAX;                   // [0] ||D_K||_F
+    double *sdf = bnd + TRMAX;                   // [0] ||D_K||_F, [1] ||D_{K-1}||_F
     int32_t *sskip = (int32_t *)(sdf + 2);       // [0] skipped rows of the tile
+    double *pn = sdf + 4;                        // TRMAX x 32: ||X|| ||Y||_F per (row, producer of a chunk)
+    float *sfeat = (float *)(pn + TRMAX * 32);   // TRMAX x MF features
+    float *sh1 = sfeat + TRMAX * MF;             // TRMAX x MH hidden layer 1
+    float *sh2 = sh1 + TRMAX * MH;               // TRMAX x MH hidden layer 2
+    int32_t *sina = (int32_t *)(sh2 + TRMAX * MH);  // TRMAX: A has an entry in the row's part
+    const bool useact = bound || (feat && a.learned);
 
     const int32_t *rows = Lside ? a.rowsL : a.rowsU;
     const int pcnt = ldcg(a.kst + (Lside ? 2 : 3));
@@ -383,13 +515,24 @@ __device__ void phase_B_tile(const FactorArgs &a, int K, bool Lside, int sa, int
         pxp[t] = (int)ldcg(pi + PI_XPOS);
         pyf[t] = __longlong_as_double(ldcg(pi + PI_YF));
     }
-    if (bound) {
+    if (useact || feat) {
         for (int r = tid; r < cnt; r += NT) { act[r] = 1; bnd[r] = 0.0; }
         if (warp == 0) {
             double acc = 0.0;
-            for (int c = lane; c < b; c += 32) acc += ldcg(a.dcolsq + c);
-            acc = warp_sum(acc);
+            if (bound) {
+                for (int c = lane; c < b; c += 32) acc += ldcg(a.dcolsq + c);
+                acc = warp_sum(acc);
+            }
             if (lane == 0) { sdf[0] = sqrt(acc); sskip[0] = 0; }
+        }
+        if (feat && warp == 1) {  // ||D_{K-1}||_F from the column norms of the previous inverse
+            double acc = 0.0;
+            if (K > 0) {
+                const int bp = a.bstart[K] - a.bstart[K - 1];
+                for (int c = lane; c < bp; c += 32) acc += ldcg(a.dcolsq + c);
+                acc = warp_sum(acc);
+            }
+            if (lane == 0) sdf[1] = K > 0 ? sqrt(acc) : (a.alpha > 0.0 ? 1.0 / a.alpha : 1.0);
         }
     }
     __syncthreads();
@@ -397,20 +540,35 @@ __device__ void phase_B_tile(const FactorArgs &a, int K, bool Lside, int sa, int
     for (int r = warp; r < cnt; r += NW) {
         const int idx = g[r];
         double sq = 0.0;
+        bool found = false;
         if (Lside) {
             for (int e = a.rowptr[idx] + lane; e < a.rowptr[idx + 1]; e += 32) {
                 const int c = a.colind[e];
-                if (c >= s0 && c < s1) { const double v = a.val[e]; T[r * b + (c - s0)] = (TA)v; sq = fma(v, v, sq); }
+                if (c >= s0 && c < s1) {
+                    const double v = a.val[e];
+                    T[r * b + (c - s0)] = (TA)v;
+                    sq = fma(v, v, sq);
+                    found = true;
+                }
             }
         } else {
             for (int e = a.colptr[idx] + lane; e < a.colptr[idx + 1]; e += 32) {
                 const int rr = a.rowind[e];
-                if (rr >= s0 && rr < s1) { const double v = a.cval[e]; T[r * b + (rr - s0)] = (TA)v; sq = fma(v, v, sq); }
+                if (rr >= s0 && rr < s1) {
+                    const double v = a.cval[e];
+                    T[r * b + (rr - s0)] = (TA)v;
+                    sq = fma(v, v, sq);
+                    found = true;
+                }
             }
         }
-        if (bound) {
+        if (bound || feat) {
             sq = warp_sum(sq);
-            if (lane == 0) bnd[r] = sqrt(sq);
+            const bool any = __any_sync(FULL_MASK, found);
+            if (lane == 0) {
+                bnd[r] = sqrt(sq);
+                sina[r] = any ? 1 : 0;
+            }
         }
     }
     // X entries of each producer that fall into this tile (slots are sorted)
@@ -421,6 +579,9 @@ __device__ void phase_B_tile(const FactorArgs &a, int K, bool Lside, int sa, int
         if (lane == 0) { sxs[t] = xs; sxe[t] = xe; }
     }
     __syncthreads();
+    if (feat)
+        tile_features(a, K, Lside, sa, cnt, b, s1, pcnt, xslot, poff, sxs, sxe, pxp, pbJ, pyf, g, bnd, sdf, sina, pn,
+                      sfeat, sh1, sh2, act, sskip);
     if (bound) {
         // bound of ||T[i,:]||; the order of the additions does not matter: rows with a bound
         // near the threshold are kept (margin 1e-10), the exact test then decides
@@ -483,7 +644,7 @@ __device__ void phase_B_tile(const FactorArgs &a, int K, bool Lside, int sa, int
         if (nx > 0) {
             for (int e = tid; e < nx * ny; e += NT) {
                 const int x = e / ny, y = e - x * ny;
-                if (bound && !act[xl[x]]) continue;
+                if (useact && !act[xl[x]]) continue;
                 flops += 2LL * bJ;
                 const TA *xr = Xs + x * PS, *yr = Ys + y * PS;
                 // four independent partial sums: a dependent FP64 FMA takes ~64 cycles here
@@ -517,7 +678,7 @@ __device__ void phase_B_tile(const FactorArgs &a, int K, bool Lside, int sa, int
             for (int w = 0; w < NW; ++w) tot += wsum[w];
             if (tot) atomicAdd((unsigned long long *)(a.info + (Lside ? INFO_FLOP_UPD_L : INFO_FLOP_UPD_U)),
                                (unsigned long long)tot);
-            if (bound && sskip[0])
+            if (useact && sskip[0])
                 atomicAdd((unsigned long long *)(a.info + (Lside ? INFO_SKIP_ROWS : INFO_SKIP_COLS)),
                           (unsigned long long)sskip[0]);
         }
@@ -758,6 +919,25 @@ __device__ void phase_C2(const FactorArgs &a, int K, char *smem) {
 }
 
 // ---------------------------------------------------------------- phase D
+// Sample recording (whole warp): a candidate is taken when a counter-based hash of (seed, K,
+// side, slot) falls below the rate threshold; its features (written by its tile in phase B)
+// and its label (1 dropped, 0 kept) go to the next free sample.
+__device__ __forceinline__ void record_sample(const FactorArgs &a, int K, int side, int slot, int gidx, bool kept) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t h = mix64(a.rec_seed ^ mix64(((uint64_t)K << 34) ^ ((uint64_t)side << 33) ^ (uint64_t)(uint32_t)slot));
+    if (!(a.rec_thresh == 0xffffffffu || (uint32_t)(h >> 32) < a.rec_thresh)) return;
+    unsigned long long pos = 0;
+    if (lane == 0) pos = atomicAdd(a.rec_count, 1ULL);
+    pos = __shfl_sync(FULL_MASK, pos, 0);
+    if (pos >= (unsigned long long)a.rec_cap) return;
+    const float *f = (side ? a.featU : a.featL) + (int64_t)slot * MF;
+    if (lane < MF) a.rec_x[pos * MF + lane] = ldcg(f + lane);
+    if (lane == 0) {
+        a.rec_y[pos] = kept ? 0.f : 1.f;
+        a.rec_tag[pos] = ((long long)K << 33) | ((long long)side << 32) | (long long)(uint32_t)gidx;
+    }
+}
+
 // Normalised rows l_i = T_L[i,:] D_K and columns u^_j = D_K T_U[:,j]; keep iff ||.||_2 > tau.
 template <class TS>
 __device__ void phase_D(const FactorArgs &a, int K, char *smem) {
@@ -777,7 +957,7 @@ __device__ void phase_D(const FactorArgs &a, int K, char *smem) {
     for (int item = crank(a) * NW + warp; item < total; item += a.G * NW) {
         if (item < nLc) {
             const int slot = b + item;
-            if (a.skip_bound && ldcg(a.keepL + slot) < 0) continue;  // proved dropped
+            if ((a.skip_bound || a.learned) && ldcg(a.keepL + slot) < 0) continue;  // skipped: dropped
             TA *t = (TA *)a.TL + (int64_t)slot * b;
             const TA t0 = lane < b ? ldv(t + lane) : TA(0);
             const TA t1 = lane + 32 < b ? ldv(t + lane + 32) : TA(0);
@@ -804,9 +984,10 @@ __device__ void phase_D(const FactorArgs &a, int K, char *smem) {
                 a.keepL[slot] = nr > a.tau ? 1 : 0;
                 a.nrmL[slot] = nr;
             }
+            if (a.record) record_sample(a, K, 0, slot, ldcg(a.rowsL + slot), sqrt(nrm2) > a.tau);
         } else {
             const int slot = item - nLc;
-            if (a.skip_bound && ldcg(a.keepU + slot) < 0) continue;  // proved dropped
+            if ((a.skip_bound || a.learned) && ldcg(a.keepU + slot) < 0) continue;  // skipped: dropped
             const TA *t = (const TA *)a.TU + (int64_t)slot * b;
             const TA t0 = lane < b ? ldv(t + lane) : TA(0);
             const TA t1 = lane + 32 < b ? ldv(t + lane + 32) : TA(0);
@@ -831,6 +1012,7 @@ __device__ void phase_D(const FactorArgs &a, int K, char *smem) {
                 a.keepU[slot] = sqrt(nrm2) > a.tau ? 1 : 0;
                 a.nrmU[slot] = sqrt(tn2);  // norm of the stored (unnormalised) column
             }
+            if (a.record) record_sample(a, K, 1, slot, ldcg(a.rowsU + slot), sqrt(nrm2) > a.tau);
         }
     }
 }
@@ -857,13 +1039,22 @@ __device__ void phase_E(const FactorArgs &a, int K, char *smem) {
     int32_t *sl = ws + 40;           // NW x 32: slot of the r-th kept entry of a warp's tile
     const int64_t Lbase = ldcg(a.Lptr + K), LVbase = ldcg(a.Lvptr + K);
     const int64_t Ubase = ldcg(a.Uptr + K), UVbase = ldcg(a.Uvptr + K);
-    int keptL, keptU;
+    int keptL, keptU, skipped = 0;
     {
-        int lk = 0, uk = 0;
-        for (int s = tid; s < nLc; s += NT) lk += ldcg(a.keepL + b + s) == 1;
-        for (int s = tid; s < mU; s += NT) uk += ldcg(a.keepU + s) == 1;
+        int lk = 0, uk = 0, sk = 0;
+        for (int s = tid; s < nLc; s += NT) {
+            const int k = ldcg(a.keepL + b + s);
+            lk += k == 1;
+            sk += k < 0;
+        }
+        for (int s = tid; s < mU; s += NT) {
+            const int k = ldcg(a.keepU + s);
+            uk += k == 1;
+            sk += k < 0;
+        }
         block_excl_scan(lk, ws, &keptL);
         block_excl_scan(uk, ws, &keptU);
+        if (a.skip_bound || a.learned) block_excl_scan(sk, ws, &skipped);  // skipped: neither scaled nor normed
     }
     const bool overflow = Lbase + keptL > a.capLrow || LVbase + (int64_t)keptL * b > a.capLval ||
                           Ubase + keptU > a.capUcol || UVbase + (int64_t)keptU * b > a.capUval;
@@ -878,8 +1069,8 @@ __device__ void phase_E(const FactorArgs &a, int K, char *smem) {
         a.Uvptr[K + 1] = UVbase + (int64_t)keptU * b;
         atomicAdd((unsigned long long *)(a.info + INFO_CAND_ROWS), (unsigned long long)nLc);
         atomicAdd((unsigned long long *)(a.info + INFO_CAND_COLS), (unsigned long long)mU);
-        atomicAdd((unsigned long long *)(a.info + INFO_FLOP_SCALE), 2ULL * b * b * (unsigned long long)(nLc + mU));
-        atomicAdd((unsigned long long *)(a.info + INFO_FLOP_NORM), 2ULL * b * (unsigned long long)(nLc + mU));
+        atomicAdd((unsigned long long *)(a.info + INFO_FLOP_SCALE), 2ULL * b * b * (unsigned long long)(nLc + mU - skipped));
+        atomicAdd((unsigned long long *)(a.info + INFO_FLOP_NORM), 2ULL * b * (unsigned long long)(nLc + mU - skipped));
     }
     int32_t *wsl = sl + warp * 32;
     for (int side = 0; side < 2; ++side) {
@@ -1026,7 +1217,7 @@ __device__ void factor_chain(const FactorArgs &a, char *smem) {
                         const bool Ls = r < nLt;
                         const int sa = Ls ? b + r * TR : (r - nLt) * TR;
                         const int cnt = Ls ? min(TR, mL - sa) : min(TR, mU - sa);
-                        phase_B_tile<TS>(a, K, Ls, sa, cnt, smem, false);
+                        phase_B_tile<TS>(a, K, Ls, sa, cnt, smem, false, a.learned || a.record);
                         __syncthreads();
                     }
                 }
@@ -1318,6 +1509,18 @@ cudaError_t prepare_run(bilu_ctx *c, cudaStream_t st) {
         for (auto &f : fill)
             if ((e = cudaMemsetAsync(f.p, 0xff, f.bytes, st)) != cudaSuccess) return e;
     }
+    if (c->rec_cap > 0) {  // recording: per-slot feature rows, the sample count of this run's start
+        if (c->feat_cap < c->capT) {
+            dev_free(c->d_featL);
+            dev_free(c->d_featU);
+            c->feat_cap = 0;
+            if ((e = dev_alloc(&c->d_featL, c->capT * MF)) != cudaSuccess) return e;
+            if ((e = dev_alloc(&c->d_featU, c->capT * MF)) != cudaSuccess) return e;
+            c->feat_cap = c->capT;
+        }
+        if ((e = cudaMemcpyAsync(c->d_rec_count, &c->rec_base, sizeof(unsigned long long), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return e;
+    }
     return cudaMemsetAsync(c->d_pivdone, 0, 4 * sizeof(uint32_t), st);
 }
 
@@ -1342,7 +1545,23 @@ FactorArgs make_args(bilu_ctx *c, double droptol, int G) {
     a.LU = c->d_LU; a.perm = c->d_perm; a.kst = c->d_kstate; a.status = c->d_status; a.info = c->d_info;
     a.bar = c->d_bar;
     a.debug_extra_cta = g_debug_extra_cta;
-    a.skip_bound = c->p.skip == BILU_SKIP_BOUND ? 1 : 0;
+    // recording takes exact samples: no skipping while it is on
+    const bool rec = c->rec_cap > 0;
+    a.skip_bound = c->p.skip == BILU_SKIP_BOUND && !rec ? 1 : 0;
+    a.learned = c->p.skip == BILU_SKIP_LEARNED && !rec && c->d_mlp_w ? 1 : 0;
+    a.zhi = (float)c->mlp_logit_hi;
+    a.mlp_norm = c->d_mlp_norm;
+    a.mlp_w = (const __half *)c->d_mlp_w;
+    a.record = rec ? 1 : 0;
+    a.rec_thresh = c->rec_thresh;
+    a.rec_seed = c->rec_seed;
+    a.rec_cap = c->rec_cap;
+    a.featL = c->d_featL;
+    a.featU = c->d_featU;
+    a.rec_x = c->d_rec_x;
+    a.rec_y = c->d_rec_y;
+    a.rec_tag = (long long *)c->d_rec_tag;
+    a.rec_count = c->d_rec_count;
     a.Lnrm = c->d_Lnrm; a.Unrm = c->d_Unrm; a.nrmL = c->d_nrmL; a.nrmU = c->d_nrmU;
     a.dcolsq = c->d_dcolsq; a.pivdone = c->d_pivdone;
     return a;
@@ -1404,11 +1623,21 @@ int finish_run(bilu_ctx *c, int32_t status, const int64_t *info, bilu_status *er
 
 }  // namespace
 
+// Recording: samples held before this factorization (a re-run restarts from there).
+static cudaError_t record_begin(bilu_ctx *c) {
+    if (c->rec_cap <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemcpyAsync(&c->rec_base, c->d_rec_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (c->rec_base > (unsigned long long)c->rec_cap) c->rec_base = (unsigned long long)c->rec_cap;
+    return e;
+}
+
 bilu_status factor_run(bilu_ctx *c, double droptol) {
     if (c->d_Lptr == nullptr) {
         bilu_status st = factor_alloc(c);
         if (st != BILU_OK) return st;
     }
+    BILU_CUDA(c, record_begin(c));
     // kernel instance by the precision of the updates and the stored factor values
     const void *kfn = factor_kernel_for(c->p.precision);
     BILU_CUDA(c, cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
@@ -1478,6 +1707,7 @@ bilu_status factor_batch_run(bilu_ctx *const *ctxs, int count, double droptol, d
             if (st != BILU_OK) return st;
         }
         bmax = std::max(bmax, c->bmax);
+        BILU_CUDA(c0, record_begin(c));
     }
     const void *kfn = batch_kernel_for(prec);
     BILU_CUDA(c0, cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));

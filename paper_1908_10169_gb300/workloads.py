@@ -208,3 +208,17 @@ def cd_batch(count: int = 64, seed0: int = 100, n_lo: float = 1e4, n_hi: float =
         A = convdiff_upwind(tuple([side] * dim), vel=vel, seed=seed)
         out.append(Workload(f"cd{dim}d_{side}_s{seed}", A, rhs_ones(A), 1e-2, 64, "fixed", min(block, side)))
     return out
+
+
+def cd3d_skip_train(count: int = 200, seed0: int = 1000, side_lo: int = 32, side_hi: int = 48, block: int = 64):
+    """Training problems of the learned skip: 3D 7-point upwind convection-diffusion, matrix k
+    with seed seed0 + k, side uniform in {side_lo..side_hi} and Peclet number log-uniform in
+    [1, 1000] (|v| = Pe along (1,1,1), kappa log-uniform in [1e-3, 1e3] per node), drop
+    tolerance 1e-2, fixed blocks of `block`.  Yields Workloads (generated lazily)."""
+    for k in range(count):
+        seed = seed0 + k
+        rng = np.random.Generator(np.random.PCG64(seed))
+        side = int(rng.integers(side_lo, side_hi + 1))
+        pe = 10.0 ** rng.uniform(0.0, 3.0)
+        A = convdiff_upwind((side, side, side), vel=tuple([pe / math.sqrt(3.0)] * 3), seed=seed)
+        yield Workload(f"cd3d_train_{side}_pe{pe:.0f}_s{seed}", A, rhs_ones(A), 1e-2, 64, "fixed", min(block, side * side))
