@@ -162,17 +162,24 @@ __device__ __forceinline__ bool grid_barrier(uint32_t *bar, uint32_t G, int32_t 
 }
 
 // 1/p by Newton-Raphson iteration on f(x) = 1/x - p (x <- x + x (1 - p x), each step about
-// doubles the number of correct bits), started from the single-precision reciprocal of the
-// mantissa; the exponent is handled exactly by bit manipulation.  Within about one ulp of
-// the IEEE quotient; four dependent FP64 FMAs instead of a full division (a divide has a
-// ~650-cycle latency on this GPU).  Values far from 1 in magnitude (including 0, inf, NaN)
-// use the IEEE division.
+// doubles the number of correct bits).  The start value is the single-precision reciprocal of
+// the top 23 bits of p's mantissa, formed and widened by integer bit operations (FP64 <-> FP32
+// conversions issue on the slow FP64 pipe of this GPU); its relative error is below 2^-22, so
+// two steps reach double precision.  The exponent is handled exactly by bit manipulation.
+// Within about one ulp of the IEEE quotient; four dependent FP64 FMAs instead of a full
+// division (a divide has a ~650-cycle latency on this GPU).  Values far from 1 in magnitude
+// (including 0, inf, NaN) use the IEEE division.
 __device__ __forceinline__ double recip_nr(double p) {
     const long long bits = __double_as_longlong(p);
     const int ex = (int)((bits >> 52) & 0x7ff);
     if (ex < 64 || ex > 1982) return 1.0 / p;
-    const double m = __longlong_as_double((bits & ~(0x7ffLL << 52)) | (1023LL << 52));  // |m| in [1, 2)
-    double x = (double)__frcp_rn((float)m);
+    const long long mb = bits & 0xfffffffffffffLL;
+    const double m = __longlong_as_double(mb | (1023LL << 52) | (bits & (1LL << 63)));  // |m| in [1, 2), sign of p
+    const float m32 = __int_as_float((int)(0x3f800000u | (unsigned)(mb >> 29) | ((unsigned)(bits >> 32) & 0x80000000u)));
+    const unsigned xb = (unsigned)__float_as_int(__frcp_rn(m32));
+    double x = __longlong_as_double(((long long)(xb & 0x80000000u) << 32) |
+                                    ((long long)(((xb >> 23) & 0xff) - 127 + 1023) << 52) |
+                                    ((long long)(xb & 0x7fffff) << 29));
     double e = fma(-m, x, 1.0);
     x = fma(x, e, x);
     e = fma(-m, x, 1.0);

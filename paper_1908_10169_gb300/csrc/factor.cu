@@ -56,6 +56,7 @@ __device__ __forceinline__ __nv_bfloat16 ldv(const __nv_bfloat16 *p) {
 
 constexpr int NT = 512;          // threads per CTA
 constexpr int NW = NT / 32;      // warps per CTA
+static_assert(NW == 16, "the pivot LU's trailing update maps 12 of the 16 warps");
 constexpr int TRMAX = 16;        // max candidate slots per accumulation tile
 constexpr int PS = BILU_MAX_BLOCK + 1;  // padded row stride (doubles) of staged panels
 constexpr int PMAX = 1024;       // max producers per block handled by the kernel
@@ -703,25 +704,38 @@ __device__ __forceinline__ unsigned long long absbits(double v) {
     return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL;
 }
 
-// Warp 0: choose the pivot of column col among logical positions [from, b) of phys_in,
-// write the swapped permutation to phys_out, 1/pivot to *srp, and the multipliers
-// M[i][col] *= 1/pivot for the rows below.  Returns (through *sbad) col when the pivot
-// magnitude is <= thresh.
-__device__ __forceinline__ void lu_pivot_column(double *M, const int32_t *phys_in, int32_t *phys_out, int b,
-                                                int col, double thresh, double *srp, int *sp, int *sbad) {
+// Warp 0, one column step: the column `col` of the rows at logical positions col..b-1 of
+// phys_in gets the last rank-1 update (multipliers of column col-1 times the pivot row's value
+// u) in registers; the pivot is chosen among those values (largest |.|, ties to the smaller
+// position: LAPACK's first index in the swapped order); phys_out = phys_in with positions col
+// and q swapped (copied while the reductions run); the column is written back as multipliers
+// v * (1/pivot) for every row but the pivot row, which keeps its value.  *sbad = col when the
+// pivot magnitude is <= thresh (then nothing is scaled).
+__device__ __forceinline__ void lu_column_step(double *M, const int32_t *phys_in, int32_t *phys_out, int b, int col,
+                                               bool update, double u, double thresh, double *srp, int *sp,
+                                               int *sbad) {
     const int lane = threadIdx.x & 31;
-    // each lane: best candidate among its two positions (ties: smaller position); an empty
-    // lane offers |0| at position b, which never beats a real candidate
-    unsigned long long bv = 0ULL;
-    int bk = b;
-    double bval = 0.0;
-    for (int k = col + lane; k < b; k += 32) {
-        const double x = M[phys_in[k] * PS + col];
-        const unsigned long long v = absbits(x);
-        if (bk == b || v > bv) { bv = v; bk = k; bval = x; }
+    const int k0 = col + lane, k1 = k0 + 32;
+    const int i0 = k0 < b ? phys_in[k0] : 0, i1 = k1 < b ? phys_in[k1] : 0;
+    double v0 = 0.0, v1 = 0.0;
+    if (k0 < b) {
+        v0 = M[i0 * PS + col];
+        if (update) v0 = fma(-M[i0 * PS + col - 1], u, v0);
     }
+    if (k1 < b) {
+        v1 = M[i1 * PS + col];
+        if (update) v1 = fma(-M[i1 * PS + col - 1], u, v1);
+    }
+    // each lane: its candidate (|value| compared as the integer bit pattern); an empty lane
+    // offers |0| at position b, which never beats a real candidate
+    const unsigned long long a0 = k0 < b ? absbits(v0) : 0ULL, a1 = k1 < b ? absbits(v1) : 0ULL;
+    unsigned long long bv = a0;
+    int bk = k0 < b ? k0 : b;
+    double bval = v0;
+    if (k1 < b && a1 > bv) { bv = a1; bk = k1; bval = v1; }
     // the reciprocal of every lane's candidate starts now and overlaps the reduction
     const double rloc = (bk < b && bv != 0ULL) ? recip_nr(bval) : 0.0;
+    for (int k = lane; k < b; k += 32) phys_out[k] = phys_in[k];
     const unsigned hi = (unsigned)(bv >> 32), lo = (unsigned)bv;
     const unsigned mhi = __reduce_max_sync(FULL_MASK, hi);
     const unsigned mlo = __reduce_max_sync(FULL_MASK, hi == mhi ? lo : 0u);
@@ -730,19 +744,18 @@ __device__ __forceinline__ void lu_pivot_column(double *M, const int32_t *phys_i
     const int owner = (q - col) & 31;
     const double pv = __shfl_sync(FULL_MASK, bval, owner);
     const double rp = __shfl_sync(FULL_MASK, rloc, owner);
-    const int p = phys_in[q], rj = phys_in[col];
+    const int p = __shfl_sync(FULL_MASK, q < col + 32 ? i0 : i1, owner);
     const bool bad = !(absbits(pv) > absbits(thresh));
-    for (int k = lane; k < b; k += 32) phys_out[k] = k == col ? p : (k == q ? rj : phys_in[k]);
-    if (!bad)
-        for (int k = col + 1 + lane; k < b; k += 32) {
-            const int i = k == q ? rj : phys_in[k];
-            M[i * PS + col] *= rp;
-        }
+    __syncwarp();
     if (lane == 0) {
+        phys_out[col] = p;
+        phys_out[q] = i0;  // the row that was at position col
         *srp = rp;
         *sp = p;
         if (bad) *sbad = col;
     }
+    if (k0 < b) M[i0 * PS + col] = (!bad && i0 != p) ? v0 * rp : v0;
+    if (k1 < b) M[i1 * PS + col] = (!bad && i1 != p) ? v1 * rp : v1;
 }
 
 template <class TS>
@@ -765,22 +778,22 @@ __device__ void phase_C(const FactorArgs &a, int K, char *smem) {
     __syncthreads();
     if (a.perturb) {
         // Sec. 3.6: all-zero columns, then all-zero rows, get their diagonal entry perturbed
-        // (the diagonal wins the tie with the other, zero, entries).  Each column / row check
-        // is independent of the others, so thread j takes column j, then row j.
-        if (tid < b) {
-            bool zero = true;
-            for (int i = 0; i < b; ++i) zero &= (absbits(P[i * PS + tid]) == 0ULL);
-            if (zero) {
-                P[tid * PS + tid] = perturbed(P[tid * PS + tid], a.pert_tau, a.pert_rho, a.alpha);
+        // (the diagonal wins the tie with the other, zero, entries).
+        // One warp per column (then per row), its lanes over the entries.
+        for (int c = warp; c < b; c += NW) {
+            const bool nz = (lane < b && absbits(P[lane * PS + c]) != 0ULL) ||
+                            (lane + 32 < b && absbits(P[(lane + 32) * PS + c]) != 0ULL);
+            if (!__any_sync(FULL_MASK, nz) && lane == 0) {
+                P[c * PS + c] = perturbed(P[c * PS + c], a.pert_tau, a.pert_rho, a.alpha);
                 atomicAdd(sh + 2, 1);
             }
         }
         __syncthreads();
-        if (tid < b) {
-            bool zero = true;
-            for (int j = 0; j < b; ++j) zero &= (absbits(P[tid * PS + j]) == 0ULL);
-            if (zero) {
-                P[tid * PS + tid] = perturbed(P[tid * PS + tid], a.pert_tau, a.pert_rho, a.alpha);
+        for (int r = warp; r < b; r += NW) {
+            const bool nz = (lane < b && absbits(P[r * PS + lane]) != 0ULL) ||
+                            (lane + 32 < b && absbits(P[r * PS + lane + 32]) != 0ULL);
+            if (!__any_sync(FULL_MASK, nz) && lane == 0) {
+                P[r * PS + r] = perturbed(P[r * PS + r], a.pert_tau, a.pert_rho, a.alpha);
                 atomicAdd(sh + 2, 1);
             }
         }
@@ -804,7 +817,7 @@ __device__ void phase_C(const FactorArgs &a, int K, char *smem) {
         __syncthreads();
         const double thresh = 1e-14 * __longlong_as_double((long long)*smax);
         // column 0: pivot and multipliers (warp 0)
-        if (warp == 0) lu_pivot_column(M, phys, phys + BILU_MAX_BLOCK, b, 0, thresh, srp, sp, sh);
+        if (warp == 0) lu_column_step(M, phys, phys + BILU_MAX_BLOCK, b, 0, false, 0.0, thresh, srp, sp, sh);
         __syncthreads();
         for (int j = 0; j < b; ++j) {
             if (sh[0] >= 0) break;  // uniform: written before the last barrier
@@ -813,21 +826,16 @@ __device__ void phase_C(const FactorArgs &a, int K, char *smem) {
             const int p = sp[j & 1];
             const int m = b - j - 1;  // rows below the pivot (logical positions j+1..b-1)
             if (warp == 0) {
-                if (m > 0) {
-                    // lookahead: column j+1 of the rows below, then its pivot and multipliers
-                    const double upj1 = M[p * PS + j + 1];
-                    for (int k = j + 1 + lane; k < b; k += 32) {
-                        const int i = ph[k];
-                        M[i * PS + j + 1] = fma(-M[i * PS + j], upj1, M[i * PS + j + 1]);
-                    }
-                    __syncwarp();
-                    lu_pivot_column(M, ph, phys + (cur ^ 1) * BILU_MAX_BLOCK, b, j + 1, thresh, srp + ((j + 1) & 1),
-                                    sp + ((j + 1) & 1), sh);
-                }
-            } else if (m > 1) {
-                // trailing update of columns j+2.. with the multipliers of column j
+                // lookahead: column j+1 of the rows below, its pivot and multipliers
+                if (m > 0)
+                    lu_column_step(M, ph, phys + (cur ^ 1) * BILU_MAX_BLOCK, b, j + 1, true, M[p * PS + j + 1], thresh,
+                                   srp + ((j + 1) & 1), sp + ((j + 1) & 1), sh);
+            } else if (m > 1 && (warp & 3) != 0) {
+                // trailing update of columns j+2.. with the multipliers of column j, by the 12
+                // warps off warp 0's scheduler partition (warps 4, 8, 12 would delay its chain)
+                const int rank = warp - 1 - (warp >> 2);
                 const int w = m - 1, tot = m * w;
-                for (int e = tid - 32; e < tot; e += NT - 32) {
+                for (int e = rank * 32 + lane; e < tot; e += 12 * 32) {
                     const int r = e / w, c = j + 2 + (e - r * w);
                     const int i = ph[j + 1 + r];
                     M[i * PS + c] = fma(-M[i * PS + j], M[p * PS + c], M[i * PS + c]);
