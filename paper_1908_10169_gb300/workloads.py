@@ -222,3 +222,128 @@ def cd3d_skip_train(count: int = 200, seed0: int = 1000, side_lo: int = 32, side
         pe = 10.0 ** rng.uniform(0.0, 3.0)
         A = convdiff_upwind((side, side, side), vel=tuple([pe / math.sqrt(3.0)] * 3), seed=seed)
         yield Workload(f"cd3d_train_{side}_pe{pe:.0f}_s{seed}", A, rhs_ones(A), 1e-2, 64, "fixed", min(block, side * side))
+
+
+# --- trilinear (Q1) hexahedral finite elements --------------------------------------------
+
+_GAUSS = (-1.0 / math.sqrt(3.0), 1.0 / math.sqrt(3.0))
+_CORNERS = [(i, j, k) for k in (0, 1) for j in (0, 1) for i in (0, 1)]  # local node a = i + 2j + 4k
+
+
+def _q1_grads():
+    """Gradients (x, y, z) of the 8 trilinear shape functions on the unit cube at the 2x2x2
+    Gauss points: array [8 points][8 nodes][3]."""
+    out = []
+    for gz in _GAUSS:
+        for gy in _GAUSS:
+            for gx in _GAUSS:
+                p = [(1 + gx) / 2, (1 + gy) / 2, (1 + gz) / 2]
+                gr = []
+                for (i, j, k) in _CORNERS:
+                    f = [p[0] if i else 1 - p[0], p[1] if j else 1 - p[1], p[2] if k else 1 - p[2]]
+                    s = [1 if i else -1, 1 if j else -1, 1 if k else -1]
+                    gr.append([s[0] * f[1] * f[2], f[0] * s[1] * f[2], f[0] * f[1] * s[2]])
+                out.append(gr)
+    return np.array(out)  # Gauss weights are 1/8 each on the unit cube
+
+
+def q1_laplace_element() -> np.ndarray:
+    """8 x 8 element matrix of -div(grad u) for Q1 on the unit cube (2x2x2 Gauss)."""
+    G = _q1_grads()
+    return sum(g @ g.T for g in G) / 8.0
+
+
+def q1_elasticity_element(nu: float = 0.3) -> np.ndarray:
+    """24 x 24 element stiffness of isotropic linear elasticity (E = 1) for Q1 on the unit
+    cube, 2x2x2 Gauss; dof order (node a, component d) -> 3a + d."""
+    lam = nu / ((1 + nu) * (1 - 2 * nu))
+    mu = 1.0 / (2 * (1 + nu))
+    D = np.zeros((6, 6))
+    D[:3, :3] = lam
+    D[np.arange(3), np.arange(3)] += 2 * mu
+    D[3:, 3:] = np.eye(3) * mu
+    Ke = np.zeros((24, 24))
+    for g in _q1_grads():
+        Bm = np.zeros((6, 24))
+        for a in range(8):
+            gx, gy, gz = g[a]
+            c = 3 * a
+            Bm[0, c], Bm[1, c + 1], Bm[2, c + 2] = gx, gy, gz
+            Bm[3, c], Bm[3, c + 1] = gy, gx          # gamma_xy
+            Bm[4, c + 1], Bm[4, c + 2] = gz, gy      # gamma_yz
+            Bm[5, c], Bm[5, c + 2] = gz, gx          # gamma_xz
+        Ke += Bm.T @ D @ Bm / 8.0
+    return Ke
+
+
+def _assemble_q1(side: int, dof: int, Ke: np.ndarray, coef: np.ndarray) -> CSR:
+    """Assemble a Q1 operator on the (side+1)^3 elements of a grid with side^3 interior nodes
+    (Dirichlet nodes eliminated), dof unknowns per node interleaved, element matrix Ke scaled
+    by coef[element]."""
+    import scipy.sparse as sp
+    ne = side + 1
+    e = np.arange(ne ** 3)
+    ex, ey, ez = e % ne, (e // ne) % ne, e // (ne * ne)
+    nodes = []
+    for (i, j, k) in _CORNERS:  # interior node index or -1
+        x, y, z = ex + i - 1, ey + j - 1, ez + k - 1  # interior coordinates 0..side-1
+        inside = (x >= 0) & (x < side) & (y >= 0) & (y < side) & (z >= 0) & (z < side)
+        nodes.append(np.where(inside, x + side * (y + side * z), -1))
+    nodes = np.stack(nodes, axis=1)  # ne^3 x 8
+    ld = Ke.shape[0]
+    la = np.arange(ld)
+    gdof = np.where(nodes[:, la // dof] >= 0, nodes[:, la // dof] * dof + la % dof, -1)  # ne^3 x ld
+    n = side ** 3 * dof
+    rows, cols, vals = [], [], []
+    for a in range(ld):
+        ra = gdof[:, a]
+        m = ra >= 0
+        for b_ in range(ld):
+            if Ke[a, b_] == 0.0:
+                continue
+            cb = gdof[:, b_]
+            mm = m & (cb >= 0)
+            rows.append(ra[mm])
+            cols.append(cb[mm])
+            vals.append(coef[mm] * Ke[a, b_])
+    M = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n)).tocsr()
+    M.sum_duplicates()
+    M.sort_indices()
+    return CSR(n, M.indptr.astype(np.int64), M.indices.astype(np.int32), M.data.astype(np.float64))
+
+
+def elasticity3d(side: int = 48, seed: int = 2, block: int = 63) -> Workload:
+    """Q1 hexahedral linear elasticity, side^3 interior nodes (Dirichlet boundary), 3 dof per
+    node interleaved: n = 3 side^3 (331,776 for side 48); Poisson ratio 0.3; Young's modulus
+    E = 10^(4u), u ~ U[0, 1] per macro-cell of 8^3 elements (jumps 1 .. 1e4, seed); 2x2x2
+    Gauss quadrature; drop tolerance 1e-2, fixed blocks of `block` (a multiple of 3)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ne = side + 1
+    nm = (ne + 7) // 8
+    u = rng.uniform(0.0, 1.0, size=nm ** 3)
+    e = np.arange(ne ** 3)
+    ex, ey, ez = e % ne, (e // ne) % ne, e // (ne * ne)
+    E = 10.0 ** (4.0 * u[(ex // 8) + nm * ((ey // 8) + nm * (ez // 8))])
+    A = _assemble_q1(side, 3, q1_elasticity_element(0.3), E)
+    return Workload(f"elasticity_q1_{side}^3x3", A, rhs_ones(A), 1e-2, 63, "fixed", block)
+
+
+def laplace27_4dof(side: int = 64, seed: int = 3, block: int = 64) -> Workload:
+    """Q1 27-point scalar diffusion operator (kappa log-uniform in [1e-3, 1e3] per element,
+    seed) on side^3 interior nodes, coupled across 4 unknowns per node by the Kronecker product
+    with C = I + 0.3 R (R uniform in [-1, 1], rows scaled so that C is diagonally dominant):
+    n = 4 side^3 (1,048,576 for side 64), interleaved; drop tolerance 1e-2, blocks of `block`."""
+    import scipy.sparse as sp
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ne = side + 1
+    kappa = 10.0 ** rng.uniform(-3.0, 3.0, size=ne ** 3)
+    K = _assemble_q1(side, 1, q1_laplace_element(), kappa)
+    R = rng.uniform(-1.0, 1.0, size=(4, 4))
+    np.fill_diagonal(R, 0.0)
+    R *= 0.9 / np.maximum(np.abs(R).sum(axis=1, keepdims=True), 1e-12)
+    C = np.eye(4) + 0.3 * R
+    Ks = sp.csr_matrix((K.val, K.colind, K.rowptr), shape=(K.n, K.n))
+    M = sp.kron(Ks, sp.csr_matrix(C), format="csr")
+    M.sort_indices()
+    A = CSR(M.shape[0], M.indptr.astype(np.int64), M.indices.astype(np.int32), M.data.astype(np.float64))
+    return Workload(f"laplace27_4dof_{side}^3", A, rhs_ones(A), 1e-2, 64, "fixed", block)
