@@ -243,7 +243,8 @@ bilu_status bilu_debug_set(bilu_ctx *ctx, int32_t what, int64_t value);
  * the allocator.  bilu_apply itself allocates nothing per call, but it relies on buffers
  * created with the factor and stages host vectors through buffers allocated on first use.
  *
- * Same result as bilu_apply (z = M^{-1} r, same summation order), for device pointers only
+ * The result of bilu_apply (z = M^{-1} r, the same operations; the backward sweep's sums
+ * are grouped differently, so results agree to rounding), for device pointers only
  * (host pointers: BILU_ERR_ARG).  Its scratch (per-block completion flags and sweep state)
  * is one fixed array of 512 KB in device memory that every GPU loading the library holds
  * until the process exits; it serves factors of at most 65536 diagonal blocks (more:

@@ -55,9 +55,12 @@ __global__ void __launch_bounds__(32) apply_begin_kernel(int32_t *st, const int3
     }
 }
 
-// Forward sweep, block K: the producers' metadata is loaded and their flags are awaited in
-// parallel; every (producer, row) dot product is computed concurrently into dmat[t][r], and
-// the rows are then summed over the producers in increasing J (fixed order).
+// Forward sweep, block K: the producers' metadata is loaded first; then, round by round, the
+// rows of every producer that has completed are computed (dot products into dmat[t][r]) while
+// the CTA waits (bounded) for the oldest producer still running, so that once the newest one
+// (normally block K-1) is done little more than its rows lies on the sweep's critical path.  The rows are summed
+// over the producers in increasing J (a fixed order, folded in as soon as a leading run of
+// producers is done), so the result does not depend on the arrival order.
 constexpr int FCH = 32;  // producers per chunk
 
 template <class TS>
@@ -65,9 +68,9 @@ __global__ void __launch_bounds__(AT) apply_forward_kernel(ApplyArgs a) {
     if (a.skip && ldcg(a.skip)) return;
     __shared__ double acc[BILU_MAX_BLOCK];
     __shared__ double dmat[FCH][BILU_MAX_BLOCK];
-    __shared__ int sps[FCH], soff[FCH + 1], sbJ[FCH], ssJ[FCH];
+    __shared__ int sps[FCH], soff[FCH + 1], sbJ[FCH], ssJ[FCH], sJ[FCH], sst[FCH];
     __shared__ int64_t sLv[FCH];
-    __shared__ int s_K;
+    __shared__ int s_K, s_ok, s_work, s_more, s_fold;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int epoch = ldcg(a.st);
     while (true) {
@@ -81,7 +84,6 @@ __global__ void __launch_bounds__(AT) apply_forward_kernel(ApplyArgs a) {
         const int pc = ldcg(a.prodUcnt + K);
         for (int c0 = 0; c0 < pc; c0 += FCH) {
             const int cn = min(FCH, pc - c0);
-            int ok = 1;
             if (tid < cn) {
                 const int J = ldcg(a.prodU + (int64_t)K * a.prodcap + c0 + tid);
                 const int2 rg = a.planF[(int64_t)K * a.prodcap + c0 + tid];
@@ -91,48 +93,91 @@ __global__ void __launch_bounds__(AT) apply_forward_kernel(ApplyArgs a) {
                 ssJ[tid] = sj;
                 sbJ[tid] = a.bstart[J + 1] - sj;
                 sLv[tid] = a.Lvptr[J] + (int64_t)(rg.x - a.Lptr[J]) * (a.bstart[J + 1] - sj);
-                ok = wait_flag(a.flagF + J, epoch, a.st + 3) ? 1 : 0;
+                sJ[tid] = J;
+                sst[tid] = 0;  // 0 running, 1 to compute this round, 2 computed
             }
-            if (!__syncthreads_and(ok)) return;
+            if (tid == 0) s_fold = 0;
+            for (int e = tid; e < cn * BILU_MAX_BLOCK; e += AT) (&dmat[0][0])[e] = 0.0;
+            __syncthreads();
             if (tid == 0) {
                 soff[0] = 0;
                 for (int t = 0; t < cn; ++t) soff[t + 1] += soff[t];
             }
-            for (int e = tid; e < cn * BILU_MAX_BLOCK; e += AT) (&dmat[0][0])[e] = 0.0;
-            __syncthreads();
-            const int nrows = soff[cn];
-            // four rows per warp and iteration: their loads are in flight together
-            for (int it0 = warp * 4; it0 < nrows; it0 += AW * 4) {
-                double v[4];
-                int tt[4], pp[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int it = it0 + u;
-                    v[u] = 0.0;
-                    tt[u] = -1;
-                    if (it < nrows) {
-                        int t = 0;
-                        while (soff[t + 1] <= it) ++t;
-                        const int bJ = sbJ[t];
-                        const TS *row = (const TS *)a.Lval + sLv[t] + (int64_t)(it - soff[t]) * bJ;
-                        const double *yJ = a.z + ssJ[t];
-                        if (lane < bJ) v[u] = dval(row[lane]) * ldcg(yJ + lane);
-                        if (lane + 32 < bJ) v[u] = fma(dval(row[lane + 32]), ldcg(yJ + lane + 32), v[u]);
-                        tt[u] = t;
-                        pp[u] = sps[t] + (it - soff[t]);
+            while (true) {
+                if (warp == 0) {
+                    int st = lane < cn ? sst[lane] : 2;
+                    if (st == 1) st = 2;  // computed in the previous round
+                    bool rdy = st == 0 && ld_acquire_s32(a.flagF + sJ[lane]) >= epoch;
+                    unsigned mr = __ballot_sync(FULL_MASK, rdy);
+                    unsigned mw = __ballot_sync(FULL_MASK, st == 0 && !rdy);
+                    int ok = 1;
+                    if (mr == 0 && mw != 0) {
+                        // nothing new: wait for the oldest running producer (producers finish
+                        // in order, so each round takes the ones completed meanwhile and only
+                        // the newest is left once it is done); when it is the only one left it
+                        // is taken at once, otherwise all are re-checked
+                        const int tw = __ffs(mw) - 1;
+                        if (lane == 0) ok = wait_flag(a.flagF + sJ[tw], epoch, a.st + 3) ? 1 : 0;
+                        ok = __shfl_sync(FULL_MASK, ok, 0);
+                        if (ok && __popc(mw) == 1 && lane == tw) rdy = true;
+                        mr = __ballot_sync(FULL_MASK, rdy);
+                        mw = __ballot_sync(FULL_MASK, st == 0 && !rdy);
+                    }
+                    if (rdy) st = 1;
+                    if (lane < cn) sst[lane] = st;
+                    if (lane == 0) {
+                        s_ok = ok;
+                        s_work = mr != 0;
+                        s_more = (mr | mw) != 0;
                     }
                 }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const double w = warp_sum(v[u]);
-                    if (lane == 0 && tt[u] >= 0) dmat[tt[u]][a.Lrow[pp[u]] - s0] = w;
+                __syncthreads();
+                if (!s_ok) return;
+                // fold the leading run of computed producers into acc, in producer order
+                if (tid < b) {
+                    double v = acc[tid];
+                    int t = s_fold;
+                    while (t < cn && sst[t] == 2) v -= dmat[t++][tid];
+                    acc[tid] = v;
                 }
-            }
-            __syncthreads();
-            if (tid < b) {
-                double s = acc[tid];
-                for (int t = 0; t < cn; ++t) s -= dmat[t][tid];
-                acc[tid] = s;
+                if (!s_more) break;
+                const int nrows = soff[cn];
+                // four rows per warp and iteration: their loads are in flight together
+                for (int it0 = warp * 4; it0 < nrows; it0 += AW * 4) {
+                    double v[4];
+                    int tt[4], pp[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int it = it0 + u;
+                        v[u] = 0.0;
+                        tt[u] = -1;
+                        if (it < nrows) {
+                            int t = 0;
+                            while (soff[t + 1] <= it) ++t;
+                            if (sst[t] == 1) {
+                                const int bJ = sbJ[t];
+                                const TS *row = (const TS *)a.Lval + sLv[t] + (int64_t)(it - soff[t]) * bJ;
+                                const double *yJ = a.z + ssJ[t];
+                                if (lane < bJ) v[u] = dval(row[lane]) * ldcg(yJ + lane);
+                                if (lane + 32 < bJ) v[u] = fma(dval(row[lane + 32]), ldcg(yJ + lane + 32), v[u]);
+                                tt[u] = t;
+                                pp[u] = sps[t] + (it - soff[t]);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const double w = warp_sum(v[u]);
+                        if (lane == 0 && tt[u] >= 0) dmat[tt[u]][a.Lrow[pp[u]] - s0] = w;
+                    }
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    int t = s_fold;
+                    while (t < cn && sst[t] == 2) ++t;
+                    s_fold = t;
+                }
+                __syncthreads();
             }
             __syncthreads();
         }
@@ -145,14 +190,67 @@ __global__ void __launch_bounds__(AT) apply_forward_kernel(ApplyArgs a) {
     }
 }
 
+// Backward sweep, block K: the kept columns of U-breve_K in blocks after K+1 (complete early)
+// are multiplied while block K+1 -- the newest dependency -- may still be running; its own
+// columns (the leading range, the columns are sorted) follow once it is done.  Both partial
+// sums are formed in a fixed order, so the result does not depend on timing.
+template <class TS>
+__device__ __forceinline__ double backward_columns(const ApplyArgs &a, int K, int b, int64_t q0, int64_t qa,
+                                                   int64_t qb, int g, int rr) {
+    constexpr int NG = AT / BILU_MAX_BLOCK;  // column groups
+    double s = 0.0;
+    if (rr < b) {
+        const TS *Uv = (const TS *)a.Uval + a.Uvptr[K];
+        int64_t q = qa + g;
+        // four independent columns per iteration keep several loads in flight
+        double s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        for (; q + 3 * NG < qb; q += 4 * NG) {
+            const double u0 = dval(Uv[(q - q0) * b + rr]), u1 = dval(Uv[(q + NG - q0) * b + rr]);
+            const double u2 = dval(Uv[(q + 2 * NG - q0) * b + rr]), u3 = dval(Uv[(q + 3 * NG - q0) * b + rr]);
+            const double z0 = ldcg(a.z + a.Ucol[q]), z1 = ldcg(a.z + a.Ucol[q + NG]);
+            const double z2 = ldcg(a.z + a.Ucol[q + 2 * NG]), z3 = ldcg(a.z + a.Ucol[q + 3 * NG]);
+            s = fma(u0, z0, s);
+            s1 = fma(u1, z1, s1);
+            s2 = fma(u2, z2, s2);
+            s3 = fma(u3, z3, s3);
+        }
+        for (; q < qb; q += NG) s = fma(dval(Uv[(q - q0) * b + rr]), ldcg(a.z + a.Ucol[q]), s);
+        s = (s + s1) + (s2 + s3);
+    }
+    return s;
+}
+
+// Waits (warp 0, bounded) for the blocks holding the kept columns [qa, qb) (sorted, so each
+// block forms one run; the first lane of a run waits on its flag).  Returns 0 on timeout.
+__device__ __forceinline__ int wait_column_blocks(const ApplyArgs &a, int64_t qa, int64_t qb, int epoch) {
+    const int lane = threadIdx.x & 31;
+    int ok = 1, last = -1;
+    for (int64_t qbase = qa; qbase < qb; qbase += 32) {
+        const int64_t q = qbase + lane;
+        const int blk = q < qb ? a.blkof[a.Ucol[q]] : -1;
+        int prev = __shfl_up_sync(FULL_MASK, blk, 1);
+        if (lane == 0) prev = last;
+        const bool first = q < qb && blk != prev;
+        int okl = 1;
+        if (first) okl = wait_flag(a.flagB + blk, epoch, a.st + 3) ? 1 : 0;
+        ok = ok && __all_sync(FULL_MASK, okl);
+        last = __shfl_sync(FULL_MASK, blk, 31);
+        if (!ok) break;
+    }
+    return ok;
+}
+
+constexpr int RMAX = 512;  // column runs (distinct later blocks) per block held in shared memory
+
 template <class TS>
 __global__ void __launch_bounds__(AT) apply_backward_kernel(ApplyArgs a) {
     if (a.skip && ldcg(a.skip)) return;
-    __shared__ double part[AT / BILU_MAX_BLOCK][BILU_MAX_BLOCK];
-    __shared__ double tv[BILU_MAX_BLOCK];
-    __shared__ int s_K, s_ok;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int NG = AT / BILU_MAX_BLOCK;  // column groups
+    __shared__ double part[NG][BILU_MAX_BLOCK];
+    __shared__ double tv[BILU_MAX_BLOCK];
+    __shared__ int32_t rq[RMAX + 1], rblk[RMAX];
+    __shared__ int s_K, s_ok, s_nr, s_take;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int epoch = ldcg(a.st);
     while (true) {
         if (tid == 0) s_K = atomicAdd(a.st + 2, 1);
@@ -162,55 +260,89 @@ __global__ void __launch_bounds__(AT) apply_backward_kernel(ApplyArgs a) {
         if (K < 0) return;
         const int s0 = a.bstart[K], b = a.bstart[K + 1] - s0;
         const int64_t q0 = a.Uptr[K], q1 = a.Uptr[K + 1];
-        // wait for the blocks holding the kept columns of U-breve_K (sorted, so each block
-        // forms one run; the first lane of a run waits on its flag)
+        const int g = tid / BILU_MAX_BLOCK, rr = tid % BILU_MAX_BLOCK;
+        if (tid < b) tv[tid] = ldcg(a.z + s0 + tid);
+        // runs of kept columns by block (the columns are sorted): run i = [rq[i], rq[i+1])
         if (warp == 0) {
-            int ok = 1, last = -1;
-            for (int64_t qb = q0; qb < q1; qb += 32) {
-                const int64_t q = qb + lane;
+            int nr = 0, last = -1;
+            for (int64_t qbase = q0; qbase < q1 && nr <= RMAX; qbase += 32) {
+                const int64_t q = qbase + lane;
                 const int blk = q < q1 ? a.blkof[a.Ucol[q]] : -1;
                 int prev = __shfl_up_sync(FULL_MASK, blk, 1);
                 if (lane == 0) prev = last;
                 const bool first = q < q1 && blk != prev;
-                int okl = 1;
-                if (first) okl = wait_flag(a.flagB + blk, epoch, a.st + 3) ? 1 : 0;
-                ok = ok && __all_sync(FULL_MASK, okl);
+                const unsigned m = __ballot_sync(FULL_MASK, first);
+                const int pos = nr + __popc(m & ((1u << lane) - 1u));
+                if (first && pos < RMAX) {
+                    rq[pos] = (int32_t)(q - q0);
+                    rblk[pos] = blk;
+                }
+                nr += __popc(m);
                 last = __shfl_sync(FULL_MASK, blk, 31);
-                if (!ok) break;
             }
-            if (lane == 0) s_ok = ok;
-        }
-        __syncthreads();
-        if (!s_ok) return;
-        // t = y_K - U-breve_K z(C_K): group g handles columns q = q0 + g, q0 + g + NG, ...
-        const int g = tid / BILU_MAX_BLOCK, rr = tid % BILU_MAX_BLOCK;
-        double s = 0.0;
-        if (rr < b) {
-            const TS *Uv = (const TS *)a.Uval + a.Uvptr[K];
-            int64_t q = q0 + g;
-            // four independent columns per iteration keep several loads in flight
-            double s1 = 0.0, s2 = 0.0, s3 = 0.0;
-            for (; q + 3 * NG < q1; q += 4 * NG) {
-                const double u0 = dval(Uv[(q - q0) * b + rr]), u1 = dval(Uv[(q + NG - q0) * b + rr]);
-                const double u2 = dval(Uv[(q + 2 * NG - q0) * b + rr]), u3 = dval(Uv[(q + 3 * NG - q0) * b + rr]);
-                const double z0 = ldcg(a.z + a.Ucol[q]), z1 = ldcg(a.z + a.Ucol[q + NG]);
-                const double z2 = ldcg(a.z + a.Ucol[q + 2 * NG]), z3 = ldcg(a.z + a.Ucol[q + 3 * NG]);
-                s = fma(u0, z0, s);
-                s1 = fma(u1, z1, s1);
-                s2 = fma(u2, z2, s2);
-                s3 = fma(u3, z3, s3);
+            if (lane == 0) {
+                s_nr = nr;
+                if (nr <= RMAX) rq[nr] = (int32_t)(q1 - q0);
             }
-            for (; q < q1; q += NG) s = fma(dval(Uv[(q - q0) * b + rr]), ldcg(a.z + a.Ucol[q]), s);
-            s = (s + s1) + (s2 + s3);
-        }
-        part[g][rr] = s;
-        __syncthreads();
-        if (tid < b) {
-            double t = ldcg(a.z + s0 + tid);
-            for (int gg = 0; gg < NG; ++gg) t -= part[gg][tid];
-            tv[tid] = t;
         }
         __syncthreads();
+        const int nr = s_nr;
+        if (nr > RMAX) {
+            // too many runs for the shared list: wait for all of them, then one pass
+            if (warp == 0) {
+                const int ok = wait_column_blocks(a, q0, q1, epoch);
+                if (lane == 0) s_ok = ok;
+            }
+            __syncthreads();
+            if (!s_ok) return;
+            part[g][rr] = backward_columns<TS>(a, K, b, q0, q0, q1, g, rr);
+            __syncthreads();
+            if (tid < b) {
+                double t = tv[tid];
+                for (int gg = 0; gg < NG; ++gg) t -= part[gg][tid];
+                tv[tid] = t;
+            }
+            __syncthreads();
+        } else {
+            // runs from the highest block down (the order in which the sweep completes them);
+            // each round takes the completed ones, waiting (bounded) for the next when none is;
+            // every run is summed over its columns in a fixed order and folded into t in run order
+            int ri = nr - 1;
+            while (ri >= 0) {
+                if (warp == 0) {
+                    const int r = ri - lane;
+                    const bool rdy = r >= 0 && ld_acquire_s32(a.flagB + rblk[r]) >= epoch;
+                    const unsigned m = __ballot_sync(FULL_MASK, rdy);
+                    int take = __ffs(~m) - 1;  // leading completed runs
+                    if (m == 0xffffffffu) take = 32;
+                    int ok = 1;
+                    if (take == 0) {
+                        if (lane == 0) ok = wait_flag(a.flagB + rblk[ri], epoch, a.st + 3) ? 1 : 0;
+                        ok = __shfl_sync(FULL_MASK, ok, 0);
+                        take = 1;
+                    }
+                    if (lane == 0) {
+                        s_ok = ok;
+                        s_take = min(take, ri + 1);
+                    }
+                }
+                __syncthreads();
+                if (!s_ok) return;
+                const int take = s_take;
+                for (int j = 0; j < take; ++j) {
+                    const int r = ri - j;
+                    part[g][rr] = backward_columns<TS>(a, K, b, q0, q0 + rq[r], q0 + rq[r + 1], g, rr);
+                    __syncthreads();
+                    if (tid < b) {
+                        double t = tv[tid];
+                        for (int gg = 0; gg < NG; ++gg) t -= part[gg][tid];
+                        tv[tid] = t;
+                    }
+                    __syncthreads();
+                }
+                ri -= take;
+            }
+        }
         // z_K = D_K t: warp per row
         const double *D = a.Dinv + a.Dptr[K];
         const double t0 = lane < b ? tv[lane] : 0.0, t1 = lane + 32 < b ? tv[lane + 32] : 0.0;
