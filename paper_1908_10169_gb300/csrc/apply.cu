@@ -69,8 +69,9 @@ __global__ void __launch_bounds__(AT) apply_forward_kernel(ApplyArgs a) {
     __shared__ double acc[BILU_MAX_BLOCK];
     __shared__ double dmat[FCH][BILU_MAX_BLOCK];
     __shared__ int sps[FCH], soff[FCH + 1], sbJ[FCH], ssJ[FCH], sJ[FCH], sst[FCH];
+    __shared__ int srl[FCH], sro[FCH + 1];  // producers computed this round and their row offsets
     __shared__ int64_t sLv[FCH];
-    __shared__ int s_K, s_ok, s_work, s_more, s_fold;
+    __shared__ int s_K, s_ok, s_work, s_more, s_fold, s_nrd;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int epoch = ldcg(a.st);
     while (true) {
@@ -103,6 +104,7 @@ __global__ void __launch_bounds__(AT) apply_forward_kernel(ApplyArgs a) {
                 soff[0] = 0;
                 for (int t = 0; t < cn; ++t) soff[t + 1] += soff[t];
             }
+            __syncthreads();
             while (true) {
                 if (warp == 0) {
                     int st = lane < cn ? sst[lane] : 2;
@@ -125,6 +127,18 @@ __global__ void __launch_bounds__(AT) apply_forward_kernel(ApplyArgs a) {
                     }
                     if (rdy) st = 1;
                     if (lane < cn) sst[lane] = st;
+                    // the round's producers in order, with their row offsets
+                    const int rows_l = rdy ? soff[lane + 1] - soff[lane] : 0;
+                    const int inc = warp_incl_scan(rows_l);
+                    const int k = __popc(mr & ((1u << lane) - 1u));
+                    if (rdy) {
+                        srl[k] = lane;
+                        sro[k] = inc - rows_l;
+                    }
+                    if (lane == 31) {
+                        s_nrd = __popc(mr);
+                        sro[__popc(mr)] = inc;
+                    }
                     if (lane == 0) {
                         s_ok = ok;
                         s_work = mr != 0;
@@ -141,9 +155,10 @@ __global__ void __launch_bounds__(AT) apply_forward_kernel(ApplyArgs a) {
                     acc[tid] = v;
                 }
                 if (!s_more) break;
-                const int nrows = soff[cn];
-                // four rows per warp and iteration: their loads are in flight together
-                for (int it0 = warp * 4; it0 < nrows; it0 += AW * 4) {
+                // the rows of this round's producers only: four per warp and iteration, their
+                // loads in flight together; row -> producer by binary search over the offsets
+                const int nrd = s_nrd, nrr = sro[nrd];
+                for (int it0 = warp * 4; it0 < nrr; it0 += AW * 4) {
                     double v[4];
                     int tt[4], pp[4];
 #pragma unroll
@@ -151,18 +166,20 @@ __global__ void __launch_bounds__(AT) apply_forward_kernel(ApplyArgs a) {
                         const int it = it0 + u;
                         v[u] = 0.0;
                         tt[u] = -1;
-                        if (it < nrows) {
-                            int t = 0;
-                            while (soff[t + 1] <= it) ++t;
-                            if (sst[t] == 1) {
-                                const int bJ = sbJ[t];
-                                const TS *row = (const TS *)a.Lval + sLv[t] + (int64_t)(it - soff[t]) * bJ;
-                                const double *yJ = a.z + ssJ[t];
-                                if (lane < bJ) v[u] = dval(row[lane]) * ldcg(yJ + lane);
-                                if (lane + 32 < bJ) v[u] = fma(dval(row[lane + 32]), ldcg(yJ + lane + 32), v[u]);
-                                tt[u] = t;
-                                pp[u] = sps[t] + (it - soff[t]);
+                        if (it < nrr) {
+                            int lo = 0, hi = nrd - 1;  // largest k with sro[k] <= it
+                            while (lo < hi) {
+                                const int mid = (lo + hi + 1) >> 1;
+                                if (sro[mid] <= it) lo = mid; else hi = mid - 1;
                             }
+                            const int t = srl[lo], ir = it - sro[lo];
+                            const int bJ = sbJ[t];
+                            const TS *row = (const TS *)a.Lval + sLv[t] + (int64_t)ir * bJ;
+                            const double *yJ = a.z + ssJ[t];
+                            if (lane < bJ) v[u] = dval(row[lane]) * ldcg(yJ + lane);
+                            if (lane + 32 < bJ) v[u] = fma(dval(row[lane + 32]), ldcg(yJ + lane + 32), v[u]);
+                            tt[u] = t;
+                            pp[u] = sps[t] + ir;
                         }
                     }
 #pragma unroll
