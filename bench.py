@@ -339,8 +339,9 @@ def run_gpu(args):
                    "flops_per_launch": st.flops_factor, "ms_per_launch": t_factor, "share_of_step": share_factor}
     roof_apply = {"kernel": "apply_forward_kernel+apply_backward_kernel", "bound": "hbm", "achieved": apply_gbs,
                   "peak": hbm_peak, "unit": "GB/s", "frac": apply_gbs / hbm_peak, "peak_source": hbm_src,
-                  "traffic": (traffic["apply_backward_kernel"] * nvals) if "apply_backward_kernel" in traffic else None,
-                  "traffic_note": "backward sweep only (the forward sweep's multi-pass capture returned no counters)",
+                  "traffic": ((traffic["apply_forward_kernel"] + traffic["apply_backward_kernel"]) * nvals
+                              if "apply_forward_kernel" in traffic and "apply_backward_kernel" in traffic else None),
+                  "traffic_note": "forward + backward sweep",
                   "bytes_per_launch": apply_bytes, "ms_per_launch": t_apply, "share_of_step": share_apply}
     dominant, other = (roof_factor, roof_apply) if share_factor >= share_apply else (roof_apply, roof_factor)
 
