@@ -80,6 +80,7 @@ struct bilu_ctx {
     // factor scratch
     int64_t capT = 0;
     double *d_TL = nullptr, *d_TU = nullptr;
+    double *d_TLP = nullptr;       // partial accumulators of the pivot rows (4 x 64 x 64)
     int32_t *d_rowsL = nullptr, *d_rowsU = nullptr;
     int32_t *d_keepL = nullptr, *d_keepU = nullptr;
     uint32_t *d_bmL = nullptr, *d_bmU = nullptr;

@@ -61,6 +61,11 @@ constexpr int TRMAX = 16;        // max candidate slots per accumulation tile
 constexpr int PS = BILU_MAX_BLOCK + 1;  // padded row stride (doubles) of staged panels
 constexpr int PMAX = 1024;       // max producers per block handled by the kernel
 constexpr int SMEM_BYTES = 128 * 1024;
+constexpr int TRP = 2;           // rows per pivot-row tile
+// Producer slices per pivot-row tile: the pivot rows' updates are on the critical path (the LU
+// waits for them), so each tile's producer list is split into PPART slices computed side by
+// side and summed in slice order when the LU loads the pivot block.
+constexpr int PPART = 4;
 
 struct FactorArgs {
     int32_t n, nb, G, perturb;
@@ -77,6 +82,7 @@ struct FactorArgs {
     int32_t prodcap;
     int32_t *prodL, *prodLcnt, *prodU, *prodUcnt, *lastL, *lastU;
     void *TL, *TU;               // candidate accumulators, type TA of the kernel instance
+    void *TLP;                   // pivot rows: PPART partial accumulators of b x b (type TA)
     int32_t *rowsL, *rowsU, *keepL, *keepU;
     uint32_t *bmL, *bmU;
     int32_t *wbL, *wbU;          // bitmap word prefix counts
@@ -112,6 +118,10 @@ struct FactorArgs {
     long long *rec_tag;
     unsigned long long *rec_count;
 };
+
+// (always PPART: the factor must not depend on the launch configuration, so that a batched
+// factorization equals the one-by-one factorization bit for bit)
+__device__ __forceinline__ int pivot_parts(int W, int npt) { return PPART; }
 
 // pinfo layout (per producer t of the current block)
 enum { PI_J = 0, PI_BJ, PI_XCNT, PI_YCNT, PI_OFF, PI_XPOS, PI_XVAL, PI_YVAL, PI_YPOS, PI_YF, PIS };
@@ -466,7 +476,10 @@ __device__ __noinline__ void tile_features(const FactorArgs &a, int K, bool Lsid
 
 template <class TS>
 __device__ void phase_B_tile(const FactorArgs &a, int K, bool Lside, int sa, int cnt, char *smem, bool bound,
-                             bool feat = false) {
+                             bool feat = false, int part = -1, int nparts = 1) {
+    // part >= 0: one of nparts slices of the producer list of pivot-row tile rows [sa, sa+cnt):
+    // producers [pcnt * part / nparts, pcnt * (part + 1) / nparts), A's values only in part 0,
+    // the partial accumulator written to the pivot-part buffer (summed in part order by the LU)
     static_assert(TRMAX <= NW, "one warp per tile row in the feature pass");
     using TA = typename Prec<TS>::TA;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -538,7 +551,7 @@ __device__ void phase_B_tile(const FactorArgs &a, int K, bool Lside, int sa, int
     }
     __syncthreads();
     // load A: L side rows i of A restricted to columns B_K; U side columns j restricted to rows B_K
-    for (int r = warp; r < cnt; r += NW) {
+    for (int r = warp; r < (part > 0 ? 0 : cnt); r += NW) {
         const int idx = g[r];
         double sq = 0.0;
         bool found = false;
@@ -607,8 +620,10 @@ __device__ void phase_B_tile(const FactorArgs &a, int K, bool Lside, int sa, int
     }
     long long flops = 0;
     ProdStage<TA> st;
-    if (pcnt > 0) prefetch_producer<TS>(a, Lside, 0, sa, cnt, s0, b, sxs, sxe, pbJ, pny, poff, pxv, pyv, pyp, st);
-    for (int t = 0; t < pcnt; ++t) {
+    const int tbeg = part >= 0 ? pcnt * part / nparts : 0;
+    const int tend = part >= 0 ? pcnt * (part + 1) / nparts : pcnt;
+    if (tbeg < tend) prefetch_producer<TS>(a, Lside, tbeg, sa, cnt, s0, b, sxs, sxe, pbJ, pny, poff, pxv, pyv, pyp, st);
+    for (int t = tbeg; t < tend; ++t) {
         const int nx = st.nx, ny = st.ny, bJ = st.bJ;
         if (nx > 0) {
             if (nx > TRMAX || ny > b) {
@@ -641,7 +656,7 @@ __device__ void phase_B_tile(const FactorArgs &a, int K, bool Lside, int sa, int
         }
         __syncthreads();
         // the next producer's panels load while this one is multiplied
-        if (t + 1 < pcnt) prefetch_producer<TS>(a, Lside, t + 1, sa, cnt, s0, b, sxs, sxe, pbJ, pny, poff, pxv, pyv, pyp, st);
+        if (t + 1 < tend) prefetch_producer<TS>(a, Lside, t + 1, sa, cnt, s0, b, sxs, sxe, pbJ, pny, poff, pxv, pyv, pyp, st);
         if (nx > 0) {
             for (int e = tid; e < nx * ny; e += NT) {
                 const int x = e / ny, y = e - x * ny;
@@ -663,7 +678,8 @@ __device__ void phase_B_tile(const FactorArgs &a, int K, bool Lside, int sa, int
         }
         __syncthreads();
     }
-    TA *out = (TA *)(Lside ? a.TL : a.TU) + (int64_t)sa * b;
+    TA *out = part >= 0 ? (TA *)a.TLP + (int64_t)part * BILU_MAX_BLOCK * BILU_MAX_BLOCK + (int64_t)sa * b
+                        : (TA *)(Lside ? a.TL : a.TU) + (int64_t)sa * b;
     for (int e = tid; e < cnt * b; e += NT) out[e] = T[e];
     // per-thread counts of the products computed, summed over the CTA
     {
@@ -770,9 +786,15 @@ __device__ void phase_C(const FactorArgs &a, int K, char *smem) {
     int32_t *sp = phys + 2 * BILU_MAX_BLOCK;    // 2: pivot row per step parity
     int32_t *sh = sp + 2;                       // [0] bad column, [2] perturbation count
     unsigned long long *smax = (unsigned long long *)(sh + 4);
-    for (int e = tid; e < b * b; e += NT) {
-        const int r = e / b, c = e - r * b;
-        P[r * PS + c] = (double)ldv((const TA *)a.TL + (int64_t)r * b + c);
+    {
+        const int np = pivot_parts(a.G > 1 ? a.G - 1 : 1, (b + TRP - 1) / TRP);
+        const TA *tp = (const TA *)a.TLP;
+        for (int e = tid; e < b * b; e += NT) {
+            const int r = e / b, c = e - r * b;
+            TA v = ldv(tp + (int64_t)r * b + c);
+            for (int q = 1; q < np; ++q) v += ldv(tp + (int64_t)q * BILU_MAX_BLOCK * BILU_MAX_BLOCK + (int64_t)r * b + c);
+            P[r * PS + c] = (double)v;
+        }
     }
     if (tid == 0) sh[2] = 0;
     __syncthreads();
@@ -1193,7 +1215,6 @@ __device__ void factor_chain(const FactorArgs &a, char *smem) {
             tprev = t;
         }
     };
-    constexpr int TRP = 2;  // rows per pivot-row tile
     for (int K = 0; K < a.nb; ++K) {
         const int b = a.bstart[K + 1] - a.bstart[K];
         if (cr == 0) phase_A(a, K, true, smem);
@@ -1208,20 +1229,21 @@ __device__ void factor_chain(const FactorArgs &a, char *smem) {
         const int npt = (b + TRP - 1) / TRP;
         {
             const int W = a.G > 1 ? a.G - 1 : 1;  // CTAs taking tiles (CTA 0 factors the pivot block)
+            const int np = pivot_parts(W, npt);    // producer slices per pivot-row tile
             int TR = (nrest + W - 1) / W;
             TR = max(4, min(TRMAX, TR));
             const int nLt = (nrestL + TR - 1) / TR, nUt = (mU + TR - 1) / TR;
-            const int ntiles = npt + (a.skip_bound ? 0 : nLt + nUt);
+            const int ntiles = npt * np + (a.skip_bound ? 0 : nLt + nUt);
             if (a.G == 1 || cr > 0) {
                 const int wid = a.G > 1 ? cr - 1 : 0;
                 for (int it = wid; it < ntiles; it += W) {
-                    if (it < npt) {
-                        const int sa = it * TRP;
-                        phase_B_tile<TS>(a, K, true, sa, min(TRP, b - sa), smem, false);
+                    if (it < npt * np) {
+                        const int sa = (it / np) * TRP;
+                        phase_B_tile<TS>(a, K, true, sa, min(TRP, b - sa), smem, false, false, it % np, np);
                         __syncthreads();
                         if (threadIdx.x == 0) red_add_release(a.pivdone, 1u);
                     } else {
-                        const int r = it - npt;
+                        const int r = it - npt * np;
                         const bool Ls = r < nLt;
                         const int sa = Ls ? b + r * TR : (r - nLt) * TR;
                         const int cnt = Ls ? min(TR, mL - sa) : min(TR, mU - sa);
@@ -1237,7 +1259,7 @@ __device__ void factor_chain(const FactorArgs &a, char *smem) {
                     int go = 1;
                     if (a.G > 1) {
                         long long itn = 0;
-                        while (ld_acquire_u32(a.pivdone) < (uint32_t)npt) {
+                        while (ld_acquire_u32(a.pivdone) < (uint32_t)(npt * pivot_parts(a.G - 1, npt))) {
                             if (++itn > a.spin_limit) {
                                 if (atomicCAS(a.status, 0, DEV_TIMEOUT) == 0) a.info[INFO_TIMEOUT_SITE] = 7;
                                 go = 0;
@@ -1381,7 +1403,7 @@ void factor_free(bilu_ctx *c) {
     dev_free(c->d_Dinv); dev_free(c->d_Pblk);
     dev_free(c->d_prodL); dev_free(c->d_prodLcnt); dev_free(c->d_prodU); dev_free(c->d_prodUcnt);
     dev_free(c->d_lastL); dev_free(c->d_lastU);
-    dev_free(c->d_TL); dev_free(c->d_TU); dev_free(c->d_rowsL); dev_free(c->d_rowsU);
+    dev_free(c->d_TL); dev_free(c->d_TU); dev_free(c->d_TLP); dev_free(c->d_rowsL); dev_free(c->d_rowsU);
     dev_free(c->d_keepL); dev_free(c->d_keepU); dev_free(c->d_bmL); dev_free(c->d_bmU);
     dev_free(c->d_LU); dev_free(c->d_perm); dev_free(c->d_kstate); dev_free(c->d_status);
     dev_free(c->d_info); dev_free(c->d_bar);
@@ -1454,6 +1476,7 @@ bilu_status factor_alloc(bilu_ctx *c) {
         (e = dev_alloc(&c->d_lastL, nb)) != cudaSuccess || (e = dev_alloc(&c->d_lastU, nb)) != cudaSuccess ||
         (e = dev_alloc(&c->d_TL, c->capT * bmax)) != cudaSuccess ||
         (e = dev_alloc(&c->d_TU, c->capT * bmax)) != cudaSuccess ||
+        (e = dev_alloc(&c->d_TLP, (int64_t)PPART * BILU_MAX_BLOCK * BILU_MAX_BLOCK)) != cudaSuccess ||
         (e = dev_alloc(&c->d_rowsL, c->capT)) != cudaSuccess || (e = dev_alloc(&c->d_rowsU, c->capT)) != cudaSuccess ||
         (e = dev_alloc(&c->d_keepL, c->capT)) != cudaSuccess || (e = dev_alloc(&c->d_keepU, c->capT)) != cudaSuccess ||
         (e = dev_alloc(&c->d_bmL, n / 32 + 2)) != cudaSuccess || (e = dev_alloc(&c->d_bmU, n / 32 + 2)) != cudaSuccess ||
@@ -1546,7 +1569,7 @@ FactorArgs make_args(bilu_ctx *c, double droptol, int G) {
     a.prodcap = c->prodcap;
     a.prodL = c->d_prodL; a.prodLcnt = c->d_prodLcnt; a.prodU = c->d_prodU; a.prodUcnt = c->d_prodUcnt;
     a.lastL = c->d_lastL; a.lastU = c->d_lastU;
-    a.TL = c->d_TL; a.TU = c->d_TU; a.rowsL = c->d_rowsL; a.rowsU = c->d_rowsU;
+    a.TL = c->d_TL; a.TU = c->d_TU; a.TLP = c->d_TLP; a.rowsL = c->d_rowsL; a.rowsU = c->d_rowsU;
     a.keepL = c->d_keepL; a.keepU = c->d_keepU; a.bmL = c->d_bmL; a.bmU = c->d_bmU;
     a.wbL = c->d_wbL; a.wbU = c->d_wbU; a.xslotL = c->d_xslotL; a.xslotU = c->d_xslotU;
     a.capXS = c->capXS; a.pinfoL = c->d_pinfoL; a.pinfoU = c->d_pinfoU; a.capT = c->capT;
