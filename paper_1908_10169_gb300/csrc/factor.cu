@@ -925,10 +925,13 @@ __device__ void phase_C2(const FactorArgs &a, int K, char *smem) {
     if (warp >= per) return;
     double *D = a.Dinv + a.Dptr[K];
     for (int c = crank(a) * per + warp; c < b; c += a.G * per) {
-        // lane owns rows lane and lane + 32
+        // lane owns rows lane and lane + 32; the right-hand side e has its one at position
+        // kq (prm[kq] == c), so the forward solve starts there (the entries above stay 0)
         double y0 = (lane < b && prm[lane] == c) ? 1.0 : 0.0;
         double y1 = (lane + 32 < b && prm[lane + 32] == c) ? 1.0 : 0.0;
-        for (int k = 0; k < b; ++k) {  // forward, unit lower
+        const unsigned m0 = __ballot_sync(FULL_MASK, y0 != 0.0), m1 = __ballot_sync(FULL_MASK, y1 != 0.0);
+        const int kq = m0 ? __ffs(m0) - 1 : (m1 ? __ffs(m1) + 31 : 0);
+        for (int k = kq; k < b; ++k) {  // forward, unit lower
             const double yk = __shfl_sync(FULL_MASK, k < 32 ? y0 : y1, k & 31);
             if (lane > k && lane < b) y0 -= M[lane * PS + k] * yk;
             if (lane + 32 > k && lane + 32 < b) y1 -= M[(lane + 32) * PS + k] * yk;
