@@ -39,6 +39,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--workload", choices=["cd3d", "elasticity", "laplace27x4"], default="cd3d",
+                    help="cd3d: 3D upwind convection-diffusion (the benchmark); elasticity: Q1 3-dof/node "
+                         "(mixed-precision configuration, --side 48 --block 63); laplace27x4: Q1 27-point, "
+                         "4 dof/node (learned-skip evaluation, --side 64)")
     ap.add_argument("--side", type=int, default=64)
     ap.add_argument("--block", type=int, default=64)
     ap.add_argument("--precision", choices=["fp64", "fp32", "bf16"], default="fp64")
@@ -60,13 +64,20 @@ def dist_env():
     return rank, world, local
 
 
-def workload(side, block):
+def workload(args):
+    """The matrix of a run: the 3D upwind convection-diffusion benchmark matrix (default), the Q1
+    elasticity matrix of the mixed-precision configuration, or the 27-point 4-dof/node matrix
+    the learned skip is evaluated on."""
     from paper_1908_10169_gb300 import workloads as W
-    return W.cd3d(side=side, seed=1, block=block)
+    if args.workload == "elasticity":
+        return W.elasticity3d(side=args.side, seed=2, block=args.block)
+    if args.workload == "laplace27x4":
+        return W.laplace27_4dof(side=args.side, seed=3, block=args.block)
+    return W.cd3d(side=args.side, seed=1, block=args.block)
 
 
 def config(args, w, extra=None):
-    c = {"workload": f"cd3d_7pt_upwind_{args.side}^3", "n": w.A.n, "nnz": w.A.nnz, "droptol": w.droptol,
+    c = {"workload": w.name, "n": w.A.n, "nnz": w.A.nnz, "droptol": w.droptol,
          "blocking": f"fixed {args.block}", "gmres": f"GMRES({w.restart}) rtol {w.gmres_tol}, x0 = 0, b = A*1",
          "updates": getattr(args, "precision", "fp64"), "skip": getattr(args, "skip", "none"),
          "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{args.gpus}"}
@@ -187,9 +198,9 @@ def run_reference(args):
         return 0
     import oracle as O
     oracle_cores, model = cpu_desc()
-    w = workload(args.side, args.block)
+    w = workload(args)
     bs = O.partition_fixed(w.A.n, args.block)
-    small = workload(16, 16)
+    small = workload(argparse.Namespace(**{**vars(args), "side": 16, "block": 16}))
     for _ in range(args.warmup):  # warm-up on a small case of the same kind
         oracle_step(small, O.partition_fixed(small.A.n, 16))
     times, iters = [], 0
@@ -221,7 +232,7 @@ def run_gpu(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w = workload(args.side, args.block)
+    w = workload(args)
     stream = torch.cuda.Stream(device=dev)
     ctx = B.bilu_create(local, stream)
     params = B.bilu_params_default(blocking=B.BILU_BLOCKING_FIXED, fixed_block=args.block, max_block=64,
