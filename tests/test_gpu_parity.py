@@ -75,6 +75,19 @@ def test_factor_parity_cd3d(ctx, side, blk):
     compare_factors(o, g)
 
 
+@pytest.mark.parametrize("kind,side,blk", [("elasticity", 6, 63), ("elasticity", 8, 24), ("laplace27x4", 6, 64),
+                                           ("laplace27x4", 7, 32)])
+def test_factor_parity_vector_stencils(ctx, kind, side, blk):
+    """The mixed-precision and learned-skip configurations' matrices (3 and 4 coupled unknowns
+    per node, 27-point couplings) at small sizes: FP64 factor against the oracle."""
+    if kind == "elasticity":
+        w = W.elasticity3d(side=side, seed=2, block=blk)
+    else:
+        w = W.laplace27_4dof(side=side, seed=3, block=blk)
+    g = gpu_factor(ctx, w.A, w.droptol, _fixed(blk))
+    compare_factors(_oracle(w.A, g.bstart, w.droptol), g)
+
+
 def test_factor_is_deterministic(ctx):
     A = W.convdiff_upwind((16, 16, 16), seed=5)
     g1 = gpu_factor(ctx, A, 1e-2, _fixed(32))
