@@ -1065,7 +1065,9 @@ __device__ void phase_E(const FactorArgs &a, int K, char *smem) {
     const int nLc = mL - b;
     const int tL = (nLc + 31) >> 5, tU = (mU + 31) >> 5;
     const int cr = crank(a);
-    const bool has_work = cr == 0 || cr < max(tL, tU);
+    // tiles of 32 candidates, L side then U side in one sequence: CTA cr takes tiles cr,
+    // cr + G, ... of it, so the two sides' tiles go to different CTAs
+    const bool has_work = cr == 0 || cr < tL + tU;
     if (!has_work) return;
     int32_t *cnt = (int32_t *)smem;  // NT tile offsets of the current chunk
     int32_t *ws = cnt + NT;          // scan scratch (40)
@@ -1109,7 +1111,9 @@ __device__ void phase_E(const FactorArgs &a, int K, char *smem) {
     for (int side = 0; side < 2; ++side) {
         const bool isL = side == 0;
         const int ntile = isL ? tL : tU;
-        if (cr >= ntile) continue;  // uniform in the CTA
+        const int gofs = isL ? 0 : tL;                           // sequence index of the side's first tile
+        const int tfirst = ((cr - gofs) % a.G + a.G) % a.G;      // this CTA's first tile of the side
+        if (tfirst >= ntile) continue;  // uniform in the CTA
         const int sfirst = isL ? b : 0, send = isL ? mL : mU;
         const int32_t *kp = isL ? a.keepL : a.keepU;
         const int32_t *rows = isL ? a.rowsL : a.rowsU;
@@ -1137,7 +1141,8 @@ __device__ void phase_E(const FactorArgs &a, int K, char *smem) {
             const int ex = block_excl_scan(my, ws, &tot);
             if (tid < cn) cnt[tid] = carry + ex;
             __syncthreads();
-            for (int T = c0 + cr + warp * a.G; T < c0 + cn; T += a.G * NW) {
+            const int t0c = c0 + (((tfirst - c0) % a.G) + a.G) % a.G;  // first of this CTA's tiles >= c0
+            for (int T = t0c + warp * a.G; T < c0 + cn; T += a.G * NW) {
                 const int sb = sfirst + T * 32, se = min(send, sb + 32);
                 const bool kept = sb + lane < se && ldcg(kp + sb + lane) == 1;
                 const unsigned m = __ballot_sync(FULL_MASK, kept);
