@@ -979,7 +979,9 @@ __device__ void phase_D(const FactorArgs &a, int K, char *smem) {
     const int s0 = a.bstart[K], s1 = a.bstart[K + 1], b = s1 - s0;
     const int mL = ldcg(a.kst + 0), mU = ldcg(a.kst + 1);
     const int nLc = mL - b, total = nLc + mU;
-    if (crank(a) * NW >= total) return;
+    // candidates round-robin over the CTAs first, then over their warps: the FP64 products
+    // spread over every SM's FP64 pipe
+    if (crank(a) >= total) return;
     TA *Ds = (TA *)smem;
     const double *D = a.Dinv + a.Dptr[K];
     for (int e = tid; e < b * b; e += NT) {
@@ -987,7 +989,7 @@ __device__ void phase_D(const FactorArgs &a, int K, char *smem) {
         Ds[r * PS + c] = (TA)ldcg(D + e);
     }
     __syncthreads();
-    for (int item = crank(a) * NW + warp; item < total; item += a.G * NW) {
+    for (int item = crank(a) + a.G * warp; item < total; item += a.G * NW) {
         if (item < nLc) {
             const int slot = b + item;
             if ((a.skip_bound || a.learned) && ldcg(a.keepL + slot) < 0) continue;  // skipped: dropped
