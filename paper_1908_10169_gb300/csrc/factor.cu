@@ -1144,6 +1144,43 @@ __device__ void phase_E(const FactorArgs &a, int K, char *smem) {
             if (tid < cn) cnt[tid] = carry + ex;
             __syncthreads();
             const int t0c = c0 + (((tfirst - c0) % a.G) + a.G) % a.G;  // first of this CTA's tiles >= c0
+            if (t0c < c0 + cn && t0c + a.G >= c0 + cn) {
+                // one tile of this CTA in the chunk: warp 0 compacts its indices, every warp
+                // copies the kept rows, then warp 0 appends to the producer lists
+                const int T = t0c;
+                const int sb = sfirst + T * 32, se = min(send, sb + 32);
+                const int64_t base = cnt[T - c0];
+                bool kept = false;
+                int idx = 0;
+                if (warp == 0) {
+                    kept = sb + lane < se && ldcg(kp + sb + lane) == 1;
+                    const unsigned m = __ballot_sync(FULL_MASK, kept);
+                    if (kept) {
+                        const int rank = __popc(m & ((1u << lane) - 1u));
+                        const int slot = sb + lane;
+                        wsl[rank] = slot;
+                        idx = ldcg(rows + slot);
+                        idxpool[base + rank] = idx;
+                        nrmpool[base + rank] = ldcg(nrmslot + slot);
+                    }
+                    if (lane == 0) ws[39] = __popc(m);
+                }
+                __syncthreads();
+                const int tot_e = ws[39] * b;
+                const int32_t *wsl0 = sl;  // warp 0's slot list
+                for (int e = tid; e < tot_e; e += NT) {
+                    const int r = e / b, cc = e - r * b;
+                    pool[(base + r) * b + cc] = store_of<TS>((double)ldv(Tb + (int64_t)wsl0[r] * b + cc));
+                }
+                if (kept) {
+                    const int tb = a.blkof[idx];
+                    if (atomicExch(last + tb, K) != K) {
+                        const int pos = atomicAdd(pc + tb, 1);
+                        if (pos < a.prodcap) pl[(int64_t)tb * a.prodcap + pos] = K;
+                        else set_status(a.status, DEV_PROD_OVERFLOW, a.info, K);
+                    }
+                }
+            } else
             for (int T = t0c + warp * a.G; T < c0 + cn; T += a.G * NW) {
                 const int sb = sfirst + T * 32, se = min(send, sb + 32);
                 const bool kept = sb + lane < se && ldcg(kp + sb + lane) == 1;
