@@ -852,12 +852,16 @@ __device__ void phase_C(const FactorArgs &a, int K, char *smem) {
                 if (m > 0)
                     lu_column_step(M, ph, phys + (cur ^ 1) * BILU_MAX_BLOCK, b, j + 1, true, M[p * PS + j + 1], thresh,
                                    srp + ((j + 1) & 1), sp + ((j + 1) & 1), sh);
-            } else if (m > 1 && (warp & 3) != 0) {
-                // trailing update of columns j+2.. with the multipliers of column j, by the 12
-                // warps off warp 0's scheduler partition (warps 4, 8, 12 would delay its chain)
-                const int rank = warp - 1 - (warp >> 2);
+            } else if (m > 1 && (m > 48 || (warp & 3) != 0)) {
+                // trailing update of columns j+2.. with the multipliers of column j: while it
+                // is large (more than 48 rows below the pivot) it bounds the step and takes all
+                // 15 warps; then only the 12 warps off warp 0's scheduler partition (warps 4, 8,
+                // 12 would delay warp 0's column chain, which then bounds the step)
+                const bool all = m > 48;
+                const int rank = all ? warp - 1 : warp - 1 - (warp >> 2);
+                const int nw = all ? NW - 1 : 12;
                 const int w = m - 1, tot = m * w;
-                for (int e = rank * 32 + lane; e < tot; e += 12 * 32) {
+                for (int e = rank * 32 + lane; e < tot; e += nw * 32) {
                     const int r = e / w, c = j + 2 + (e - r * w);
                     const int i = ph[j + 1 + r];
                     M[i * PS + c] = fma(-M[i * PS + j], M[p * PS + c], M[i * PS + c]);
