@@ -65,6 +65,31 @@ def dist_env():
     return rank, world, local
 
 
+def shard_systems(sizes, world):
+    """Independent systems of a batch over `world` ranks: largest first onto the rank with the
+    least work so far (work estimate: the given sizes, e.g. nnz), ties to the lower rank.
+    Deterministic; returns one ascending index list per rank."""
+    order = sorted(range(len(sizes)), key=lambda i: (-sizes[i], i))
+    load = [0] * world
+    parts = [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda q: (load[q], q))
+        parts[r].append(i)
+        load[r] += sizes[i]
+    return [sorted(p) for p in parts]
+
+
+def max_over_ranks(value, device):
+    """The largest of every rank's value (the job's time is its slowest rank's)."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def workload(args):
     """The matrix of a run: the 3D upwind convection-diffusion benchmark matrix (default), the Q1
     elasticity matrix of the mixed-precision configuration, or the 27-point 4-dof/node matrix
@@ -446,12 +471,17 @@ def run_batch(args):
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if world > 1:  # the systems are independent: each rank takes a share, no data-path collective
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
     t_start = time.time()
 
     def progress(msg):
         print(f"[batch {time.time() - t_start:7.1f} s] {msg}", file=sys.stderr, flush=True)
 
-    ws = W.cd_batch(count=args.batch, seed0=100)
+    ws_all = W.cd_batch(count=args.batch, seed0=100)
+    mine = shard_systems([w.A.nnz for w in ws_all], world)[rank]
+    ws = [ws_all[i] for i in mine]
     prec = {"fp64": B.BILU_PREC_FP64, "fp32": B.BILU_PREC_FP32, "bf16": B.BILU_PREC_BF16}[args.precision]
     stream = torch.cuda.Stream(device=dev)
     skip = {"none": B.BILU_SKIP_NONE, "bound": B.BILU_SKIP_BOUND, "learned": B.BILU_SKIP_LEARNED}[args.skip]
@@ -489,17 +519,24 @@ def run_batch(args):
         progress(f"warm-up step {k} done, GMRES iterations max {max(i.iters for i in infos)}")
     l0 = sum(B.bilu_stats(c).kernel_launches for c in ctxs)
     times = []
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
     with ClockSampler(local) as clk:
         for _ in range(args.steps):
             flush.fill_(1)
             torch.cuda.synchronize()
+            barrier()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             infos = step()
             e1.record(stream)
             torch.cuda.synchronize()
-            times.append(e0.elapsed_time(e1))
+            barrier()
+            times.append(max_over_ranks(e0.elapsed_time(e1), dev))
             progress(f"timed step: {times[-1]:.1f} ms")
     launches = (sum(B.bilu_stats(c).kernel_launches for c in ctxs) - l0) / args.steps
     batch_factor_ms, batch_gmres_ms = B.bilu_stats(ctxs[0]).t_factor_ms, infos[0].t_solve_ms
@@ -528,20 +565,36 @@ def run_batch(args):
     B.bilu_destroy(one)
     for c in ctxs:
         B.bilu_destroy(c)
-    line = {"metric": f"batched BILU factor+GMRES seconds for {len(ws)} systems to rel. residual 1e-8",
-            "value": ms / 1e3, "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup),
-            "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp64": "f64", "fp32": "f32+f64", "bf16": "bf16+f32+f64"}[args.precision], "data": "synthetic",
-            "config": {"workload": f"cd_batch_{len(ws)}", "sum_n": int(sum(w.A.n for w in ws)),
-                       "n_range": [int(min(w.A.n for w in ws)), int(max(w.A.n for w in ws))],
-                       "updates": args.precision, "gmres_iters_batched": iters_b, "gmres_iters_plain_fp64": iters_s,
-                       "max_iter_ratio": max(a / max(1, b2) for a, b2 in zip(iters_b, iters_s)),
-                       "plain_fp64_one_by_one_s": t_seq / 1e3, "speedup_vs_plain_one_by_one": t_seq / ms,
-                       "l2": "flushed (512 MB write) before every timed step", "skip": args.skip,
-                       "batch_factor_ms": batch_factor_ms, "batch_gmres_ms": batch_gmres_ms,
-                       **({"learned_skip": learned} if learned is not None else {})},
-            "gpu_launches": launches, "clocks": clk.summary()}
-    print(json.dumps(line), flush=True)
+    # job totals: one by one the whole batch runs serially (the ranks' shares add up)
+    ratio = max_over_ranks(max(a / max(1, b2) for a, b2 in zip(iters_b, iters_s)), dev)
+    t_seq_all = t_seq
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_seq, launches], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+        t_seq_all, launches = float(tt[0].item()), float(tt[1].item())
+    if rank == 0:
+        line = {"metric": f"batched BILU factor+GMRES seconds for {len(ws_all)} systems to rel. residual 1e-8",
+                "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup),
+                "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+                "dtype": {"fp64": "f64", "fp32": "f32+f64", "bf16": "bf16+f32+f64"}[args.precision],
+                "data": "synthetic",
+                "config": {"workload": f"cd_batch_{len(ws_all)}", "sum_n": int(sum(w.A.n for w in ws_all)),
+                           "n_range": [int(min(w.A.n for w in ws_all)), int(max(w.A.n for w in ws_all))],
+                           "parallelism": f"systems sharded over {world} GPU(s) by nnz, no collective",
+                           "systems_on_rank0": len(ws), "updates": args.precision,
+                           "gmres_iters_batched_rank0": iters_b, "gmres_iters_plain_fp64_rank0": iters_s,
+                           "max_iter_ratio": ratio,
+                           "plain_fp64_one_by_one_s": t_seq_all / 1e3,
+                           "speedup_vs_plain_one_by_one": t_seq_all / ms,
+                           "l2": "flushed (512 MB write) before every timed step", "skip": args.skip,
+                           "batch_factor_ms_rank0": batch_factor_ms, "batch_gmres_ms_rank0": batch_gmres_ms,
+                           **({"learned_skip": learned} if learned is not None else {})},
+                "gpu_launches": launches, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
     return 0
 
 
