@@ -54,7 +54,7 @@ def test_factor_parity_cd2d(ctx, blk):
     w = W.cd2d_32()
     g = gpu_factor(ctx, w.A, 1e-2, _fixed(blk))
     o = _oracle(w.A, g.bstart, 1e-2)
-    rep = compare_factors(o, g)
+    rep = compare_factors(o, g, A=w.A, tau=1e-2)
     assert rep.blocks == len(g.bstart) - 1
 
 
@@ -64,7 +64,7 @@ def test_factor_parity_random(ctx, seed, maxb, tau):
     p = B.bilu_params_default(blocking=B.BILU_BLOCKING_ILU1T, max_block=maxb, tau_analyze=1e-2)
     g = gpu_factor(ctx, A, tau, p)
     o = _oracle(A, g.bstart, tau)
-    compare_factors(o, g)
+    compare_factors(o, g, A=A, tau=tau)
 
 
 @pytest.mark.parametrize("side,blk", [(12, 12), (16, 16), (16, 64), (20, 40)])
@@ -72,7 +72,7 @@ def test_factor_parity_cd3d(ctx, side, blk):
     A = W.convdiff_upwind((side, side, side), seed=1)
     g = gpu_factor(ctx, A, 1e-2, _fixed(blk))
     o = _oracle(A, g.bstart, 1e-2)
-    compare_factors(o, g)
+    compare_factors(o, g, A=A, tau=1e-2)
 
 
 @pytest.mark.parametrize("kind,side,blk", [("elasticity", 6, 63), ("elasticity", 8, 24), ("laplace27x4", 6, 64),
@@ -85,7 +85,7 @@ def test_factor_parity_vector_stencils(ctx, kind, side, blk):
     else:
         w = W.laplace27_4dof(side=side, seed=3, block=blk)
     g = gpu_factor(ctx, w.A, w.droptol, _fixed(blk))
-    compare_factors(_oracle(w.A, g.bstart, w.droptol), g)
+    compare_factors(_oracle(w.A, g.bstart, w.droptol), g, A=w.A, tau=w.droptol)
 
 
 def test_factor_is_deterministic(ctx):
@@ -175,7 +175,7 @@ def test_bounded_wait_timeout_leaves_context_usable(ctx):
         B.bilu_debug_set(ctx, B.BILU_DEBUG_EXTRA_CTA, 0)
         B.bilu_debug_set(ctx, B.BILU_DEBUG_SPIN_LIMIT, 0)
     g = gpu_factor(ctx, A, 1e-2, _fixed(8))
-    compare_factors(O.bilu_factor(A, g.bstart, 1e-2), g)
+    compare_factors(O.bilu_factor(A, g.bstart, 1e-2), g, A=A, tau=1e-2)
 
 
 def test_argument_and_state_errors(ctx):
@@ -251,7 +251,7 @@ def test_norm_bound_skip_gives_identical_factor(ctx, side, blk):
         assert np.array_equal(getattr(g0, f), getattr(g1, f)), f
     assert g1.stats.skipped_rows + g1.stats.skipped_cols > 0
     assert g1.stats.flop_upd_l + g1.stats.flop_upd_u < g0.stats.flop_upd_l + g0.stats.flop_upd_u
-    compare_factors(_oracle(A, g1.bstart, 1e-2), g1)
+    compare_factors(_oracle(A, g1.bstart, 1e-2), g1, A=A, tau=1e-2)
 
 
 def _rel_err_common(Fo, g):
