@@ -13,6 +13,13 @@ time through the same API from pinned host buffers (analyze + factor + solve + c
 the roofline of the dominant kernel, and the FP64 CPU oracle on the host.
 
     python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Other lines (not the default): --precision fp32|bf16 (mixed-precision updates), --skip
+bound|learned (norm-bound or learned candidate skip; learned trains its classifier first, on
+200 generated 3D problems, untimed), --workload elasticity|laplace27x4 (the mixed-precision and
+learned-skip configurations' matrices), --batch N (N uneven 2D / 3D systems in one launch and
+one graph per GMRES cycle, sharded over the ranks under torchrun). Under torchrun the single-
+matrix line runs one replica per rank; the reference arm runs on rank 0 only.
 """
 from __future__ import annotations
 
