@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include <cuda_bf16.h>
 
@@ -1772,6 +1773,7 @@ struct BatchTune {
     int nsm, nmat, bmax, precision, G, tuned;
 };
 std::vector<BatchTune> g_batch_tune;  // group sizes chosen by the autotuner
+std::mutex g_batch_tune_mu;           // guards g_batch_tune (calls on different contexts may overlap)
 
 }  // namespace
 
@@ -1865,21 +1867,31 @@ bilu_status factor_batch_run(bilu_ctx *const *ctxs, int count, double droptol, d
     }
     if (cands.empty()) cands.push_back(std::max(1, nsm / 2));
     int G = 0;
-    BatchTune *entry = nullptr;
-    for (auto &t : g_batch_tune)
-        if (t.nsm == nsm && t.nmat == count && t.bmax == bmax && t.precision == prec) entry = &t;
+    auto same = [&](const BatchTune &t) {
+        return t.nsm == nsm && t.nmat == count && t.bmax == bmax && t.precision == prec;
+    };
+    bool have = false, tuned = false;
+    int cachedG = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_batch_tune_mu);
+        for (const auto &t : g_batch_tune)
+            if (same(t)) { have = true; tuned = t.tuned != 0; cachedG = t.G; }
+    }
     std::vector<int> todo(order);
     float best_ms = 0.f;
     if (g_debug_batch_group > 0) {
         G = (int)std::min<long long>(g_debug_batch_group, nsm);
-    } else if (!entry) {
+    } else if (!have) {
         int g = 1;
         while (4 * g < count && 2 * g <= nsm / 2) g *= 2;
         G = std::max(1, nsm / g);
-        g_batch_tune.push_back({nsm, count, bmax, prec, G, 0});
-    } else if (!entry->tuned) {
+        std::lock_guard<std::mutex> lk(g_batch_tune_mu);
+        bool dup = false;
+        for (const auto &t : g_batch_tune) dup = dup || same(t);
+        if (!dup) g_batch_tune.push_back({nsm, count, bmax, prec, G, 0});
+    } else if (!tuned) {
         float best = 1e30f;
-        int bestG = entry->G;
+        int bestG = cachedG;
         bool ok = true;
         for (int Gc : cands) {
             float ms = 0.f;
@@ -1895,9 +1907,13 @@ bilu_status factor_batch_run(bilu_ctx *const *ctxs, int count, double droptol, d
             else break;  // past the minimum
         }
         G = bestG;
-        if (ok) { entry->G = bestG; entry->tuned = 1; }
+        if (ok) {
+            std::lock_guard<std::mutex> lk(g_batch_tune_mu);
+            for (auto &t : g_batch_tune)
+                if (same(t)) { t.G = bestG; t.tuned = 1; }
+        }
     } else {
-        G = entry->G;
+        G = cachedG;
     }
     bilu_status result = BILU_OK;
     for (int attempt = 0; attempt < 12 && !todo.empty(); ++attempt) {
