@@ -38,7 +38,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "BILU factor+GMRES seconds to rel. residual 1e-8"
 UNIT = "s"
-FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12  # 152 SMs x 4 FP64 flop/clk/SM x 2070 MHz (see DESIGN)
+FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12  # nominal: 152 SMs x 4 FP64 flop/clk/SM x 2070 MHz max SM clock
 
 
 def parse():
