@@ -49,3 +49,22 @@ def test_block_check_detects_a_changed_value():
     E["Lval"][lo + 3] += 1e-8 * np.abs(E["Lval"][lo:lo + b]).max()  # relative change 1e-8 of the row
     with pytest.raises(AssertionError):
         BC.compare_block(w.A, E, K, w.droptol)
+
+
+def test_block_check_rejects_a_flip_far_from_tau():
+    """A kept row of L removed from the factor (its norm far above tau) is a drop decision
+    that differs for a reason other than rounding: the checker raises."""
+    w = W.cd3d(side=8, seed=3, block=16)
+    bs = np.arange(0, w.A.n + 1, 16)
+    F = O.bilu_factor(w.A, bs, w.droptol)
+    E = _export(F)
+    K, b = 5, 16
+    p = int(F.Lptr[K])
+    lo = p * b
+    assert np.linalg.norm(F.Lval[lo:lo + b]) > 10 * w.droptol
+    E["Lrow"] = np.delete(F.Lrow, p)
+    E["Lval"] = np.delete(F.Lval, np.arange(lo, lo + b))
+    E["Lptr"] = F.Lptr.copy()
+    E["Lptr"][K + 1:] -= 1
+    with pytest.raises(AssertionError, match="drop decision"):
+        BC.compare_block(w.A, E, K, w.droptol)

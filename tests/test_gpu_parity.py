@@ -161,6 +161,15 @@ def test_singular_block_status(ctx):
     g2 = gpu_factor(ctx, A2, 0.0, B.bilu_params_default(fixed_block=2, max_block=2))
     o2 = O.bilu_factor(A2, np.array([0, 2], np.int32), 0.0)
     compare_factors(o2, g2)
+    # a zero row in the pivot block; a breakdown whose diagonal entry is within a factor of two
+    # of the column's largest (perturbed at the diagonal) or not (perturbed at the largest)
+    for Ad3, bs3 in ((np.array([[2.0, 1.0, 0.5], [0.0, 0.0, 3.0], [1.0, 0.5, 4.0]]), [0, 2, 3]),
+                     (np.array([[1.0, 2.0], [0.75, 1.5]]), [0, 2]),
+                     (np.array([[1.0, 2.0], [0.25, 0.5]]), [0, 2])):
+        A3 = W.from_dense(Ad3)
+        g3 = gpu_factor(ctx, A3, 0.0, B.bilu_params_default(blocking=B.BILU_BLOCKING_FIXED, fixed_block=2, max_block=2))
+        assert g3.status == B.BILU_PERTURBED
+        compare_factors(O.bilu_factor(A3, np.array(bs3, np.int32), 0.0), g3)
 
 
 def test_bounded_wait_timeout_leaves_context_usable(ctx):

@@ -271,6 +271,20 @@ def test_gmres_preconditioned_solution():
     assert r.hist[-1] <= 1e-8
 
 
+def test_gmres_is_scale_invariant():
+    """GMRES is invariant under b -> 2^-30 b (stopping test relative to ||b||, Sec. 4 setup):
+    the same number of steps and x scaled by the same power of two."""
+    A = W.convdiff_upwind((12, 12, 12), seed=1)
+    b = W.rhs_ones(A)
+    F = O.bilu_factor(A, O.partition_fixed(A.n, 12), 1e-2)
+    s = 2.0 ** -30
+    for M in (F, None):
+        r = O.gmres(A, M, b, tol=1e-8)
+        rs = O.gmres(A, M, b * s, tol=1e-8)
+        assert rs.iters == r.iters and rs.status == 0
+        assert np.max(np.abs(rs.x / s - r.x)) <= 1e-12 * np.max(np.abs(r.x))
+
+
 def test_gmres_zero_rhs():
     A = W.convdiff_upwind((4, 4, 4), seed=1)
     r = O.gmres(A, None, np.zeros(A.n))
@@ -295,6 +309,18 @@ def test_zero_column_in_diagonal_block_is_perturbed():
         O.bilu_factor(A, bs, 0.0, perturb=False)
 
 
+def test_zero_row_in_diagonal_block_is_perturbed():
+    """Row 1 of the 2x2 diagonal block [[2,1],[0,0]] is zero (row 1 of A has its only entry
+    outside the block): its diagonal entry becomes sign(0) tau alpha = 1e-2 * alpha, alpha =
+    max|a_ij| = 4 (Sec. 3.6, rows like columns)."""
+    Ad = np.array([[2.0, 1.0, 0.5], [0.0, 0.0, 3.0], [1.0, 0.5, 4.0]])
+    F = O.bilu_factor(W.from_dense(Ad), np.array([0, 2, 3], np.int32), 0.0, perturb=True)
+    assert F.status == 2 and F.counters["nperturb"] == 1
+    Pexp = np.array([[2.0, 1.0], [0.0, 4e-2]])
+    assert np.allclose(F.P_block(0), Pexp, rtol=1e-15, atol=0)
+    assert np.allclose(F.D_block(0), np.linalg.inv(Pexp), rtol=1e-12)
+
+
 def test_singular_block_perturbed_at_diagonal():
     """[[1,1],[1,1]] breaks at pivot 2; column 1's largest entry is a_01 = 1 but the diagonal
     wins (2|d_11| >= |d_01|): d_11 <- d_11 (1 + rho) + tau alpha."""
@@ -305,6 +331,23 @@ def test_singular_block_perturbed_at_diagonal():
     Pexp = np.array([[1.0, 1.0], [1.0, 1.0 * 1.1 + 1e-2 * 1.0]])
     assert np.allclose(F.P_block(0), Pexp, rtol=1e-15)
     assert np.allclose(F.D_block(0), np.linalg.inv(Pexp), rtol=1e-12)
+
+
+@pytest.mark.parametrize("d11,expect", [
+    # 2|d_11| = 3 >= |d_01| = 2: the diagonal entry is perturbed, 1.5 (1 + 0.1) + 0.01 * 2
+    (1.5, [[1.0, 2.0], [0.75, 1.67]]),
+    # 2|d_11| = 1 < |d_01| = 2: the largest entry of the column is perturbed, 2 (1 + 0.1) + 0.01 * 2
+    (0.5, [[1.0, 2.22], [0.25, 0.5]])])
+def test_breakdown_perturbs_diagonal_only_within_factor_two(d11, expect):
+    """Singular [[1, 2], [d_10, d_11]] with d_10 = d_11 / 2 breaks at pivot 2 (first pivot row 0,
+    l_10 = d_10, u_11 = d_11 - 2 d_10 = 0).  Column 1's largest entry is d_01 = 2; the diagonal
+    entry is taken instead when 2|d_11| >= |d_01| (Sec. 3.6); alpha = max|a_ij| = 2."""
+    Ad = np.array([[1.0, 2.0], [d11 / 2, d11]])
+    F = O.bilu_factor(W.from_dense(Ad), np.array([0, 2], np.int32), 0.0, perturb=True,
+                      pert_tau=1e-2, pert_rho=1e-1)
+    assert F.status == 2 and F.counters["nperturb"] == 1
+    assert np.allclose(F.P_block(0), np.array(expect), rtol=1e-15, atol=0)
+    assert np.allclose(F.D_block(0), np.linalg.inv(np.array(expect)), rtol=1e-12)
 
 
 def test_no_perturbation_on_regular_workloads():

@@ -1,0 +1,176 @@
+"""Mutation check of the oracle's pins.
+
+Each case plants one plausible mistake in a copy of the oracle, on the CPU: a wrong sign, a
+transposed operand, a dropped term, an index off by one, a changed threshold, norm or
+tie-break. It then runs the pin tests (the oracle against the paper and the mathematics)
+against that copy, and at least one pin must fail. The unmodified copy must pass them all,
+which shows that the harness itself works. The product library is not involved: the copy
+holds only the oracle, the pin tests and the seeded input generators.
+"""
+import concurrent.futures
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+PIN_TESTS = ["test_oracle.py", "test_partition_oracle.py", "test_block_check_oracle.py", "test_skip_oracle.py"]
+ORACLE_FILES = ["__init__.py", "bilu_oracle.c", "bilu_oracle.h", "block_check.py", "skip_oracle.py"]
+
+C, BCK, SKP = "bilu_oracle.c", "block_check.py", "skip_oracle.py"
+
+# (name, file, fragment, replacement, which occurrence of the fragment: 1 = first)
+MUTANTS = [
+    # Crout block factorization (Algorithm 1 with blocks, Sec. 2.2)
+    ("L-update sign", C, "TL.buf[(size_t)sl * b + (F->Ucol.a[q] - s0)] -= sum;",
+     "TL.buf[(size_t)sl * b + (F->Ucol.a[q] - s0)] += sum;", 1),
+    ("U-update sign", C, "TU.buf[(size_t)sl * b + (F->Lrow.a[p] - s0)] -= sum;",
+     "TU.buf[(size_t)sl * b + (F->Lrow.a[p] - s0)] += sum;", 1),
+    ("pivot rows miss L-side updates", C, "int64_t ps = lower_bound_i32(F->Lrow.a, F->Lptr[J], F->Lptr[J + 1], s0);",
+     "int64_t ps = lower_bound_i32(F->Lrow.a, F->Lptr[J], F->Lptr[J + 1], s1);", 1),
+    ("block row of A loses its first column", C, "if (j < s1) continue;", "if (j <= s1) continue;", 1),
+    ("only the previous block produces updates", C, "if (t != last) { vi_push(&prodU[t], K); last = t; }",
+     "if (t != last && t == K + 1) { vi_push(&prodU[t], K); last = t; }", 1),
+    ("L scaling by D transposed", C, "s += trow[k] * D[k * b + c];", "s += trow[k] * D[c * b + k];", 1),
+    ("U scaling by D transposed", C, "s += D[r * b + k] * tcol[k];", "s += D[k * b + r] * tcol[k];", 1),
+    ("L kept at the threshold", C, "if (sqrt(nrm2) > droptol) {", "if (sqrt(nrm2) >= droptol) {", 1),
+    ("U kept at the threshold", C, "if (sqrt(nrm2) > droptol) {", "if (sqrt(nrm2) >= droptol) {", 2),
+    ("L max-norm", C, "nrm2 += s * s;", "nrm2 = fmax(nrm2, s * s);", 1),
+    ("U max-norm", C, "nrm2 += s * s;", "nrm2 = fmax(nrm2, s * s);", 2),
+    ("U-side updates skip the first column right of the block", C,
+     "int64_t qs = lower_bound_i32(F->Ucol.a, F->Uptr[J], F->Uptr[J + 1], s1);",
+     "int64_t qs = lower_bound_i32(F->Ucol.a, F->Uptr[J], F->Uptr[J + 1], s1 + 1);", 1),
+    ("pivot tie takes the last row", C, "if (fabs(a[i * b + j]) > amax)", "if (fabs(a[i * b + j]) >= amax)", 1),
+    ("row swap not recorded", C, "int32_t t = perm[j]; perm[j] = perm[p]; perm[p] = t;", "", 1),
+    ("LU multipliers not divided by the pivot", C, "for (int i = j + 1; i < b; ++i) a[i * b + j] /= a[j * b + j];",
+     "for (int i = j + 1; i < b; ++i) a[i * b + j] /= 1.0;", 1),
+    ("inverse multiplies by the pivot", C, "y[i] /= lu[i * b + i];", "y[i] *= lu[i * b + i];", 1),
+    # perturbation (Sec. 3.6)
+    ("sign(0) = -1", C, "return x >= 0.0 ? 1.0 : -1.0;", "return x > 0.0 ? 1.0 : -1.0;", 1),
+    ("rho ignored", C, "return d * (1.0 + prho) + sgn_plus(d) * ptau * alpha;",
+     "return d + sgn_plus(d) * ptau * alpha;", 1),
+    ("zero rows not perturbed", C, "if (zero) { P[i * b + i] = perturbed(P[i * b + i], ptau, prho, alpha); ++count; }",
+     "", 1),
+    ("diagonal preference lost", C, "if (2.0 * fabs(P[bad * b + bad]) >= fabs(P[k * b + bad])) k = bad;",
+     "if (fabs(P[bad * b + bad]) >= fabs(P[k * b + bad])) k = bad;", 1),
+    # preconditioner application (Sec. 2.2)
+    ("forward sweep sign", C, "y[F->Lrow.a[p]] -= s;", "y[F->Lrow.a[p]] += s;", 1),
+    ("backward sweep sign", C, "t[i] -= ucol[i] * zj;", "t[i] += ucol[i] * zj;", 1),
+    ("apply D transposed", C, "s += D[i * b + k] * t[k];", "s += D[k * b + i] * t[k];", 1),
+    # GMRES (Sec. 4)
+    ("Givens rotation sign", C, "H[(i + 1) * m + j] = -sn[i] * a + cs[i] * c2;",
+     "H[(i + 1) * m + j] = sn[i] * a + cs[i] * c2;", 1),
+    ("Gram-Schmidt against the newest vector only", C, "for (int i = 0; i <= j; ++i) {",
+     "for (int i = j; i <= j; ++i) {", 1),
+    ("least squares without the diagonal of H", C, "y[i] = s / H[i * m + i];", "y[i] = s;", 1),
+    ("Givens update of g sign", C, "g[j + 1] = -sn[j] * g[j];", "g[j + 1] = sn[j] * g[j];", 1),
+    ("correction not preconditioned", C, "for (int64_t e = 0; e < n; ++e) x[e] += zt[e];",
+     "for (int64_t e = 0; e < n; ++e) x[e] += w[e];", 1),
+    ("stopping test not relative to ||b||", C, "if (fabs(g[j + 1]) <= tol * bnorm || hn == 0.0) break;",
+     "if (fabs(g[j + 1]) <= tol || hn == 0.0) break;", 1),
+    # ILU(1,tau) blocking (Sec. 3.4)
+    ("growth rule loses its second clause", C,
+     "int accept = (3 * f2 <= 4 * scal2) || (f2 <= scal2 + 4 * (l + 1));", "int accept = (3 * f2 <= 4 * scal2);", 1),
+    ("scalar count without the diagonal", C, "int64_t scal2 = scal + I.n + J.n + 1;",
+     "int64_t scal2 = scal + I.n + J.n;", 1),
+    ("fill rows ignored", C, "if (fabs(c->val[f] * ajk) >= tau * fabs(ajj * akk) && stamp[i] != stampval) {",
+     "if (0 && stamp[i] != stampval) {", 1),
+    ("strict threshold on original entries", C,
+     "if (i > k && fabs(c->val[e]) >= tau * fabs(akk) && stamp[i] != stampval) {",
+     "if (i > k && fabs(c->val[e]) > tau * fabs(akk) && stamp[i] != stampval) {", 1),
+    ("new rows all counted", C, "r2 += (inR[I.a[t]] != blk); /* all > cand */", "r2 += 1;", 1),
+    ("rows inside the block counted", C, "r2 += (R.a[t] > cand);", "r2 += (R.a[t] >= cand);", 1),
+    # single block step checker
+    ("checker: L-side update sign", BCK, "t[uc[qs:qe] - s0] -= upd[a]", "t[uc[qs:qe] - s0] += upd[a]", 1),
+    ("checker: U-side update sign", BCK, "t[lr[ps2:pe2] - s0] -= upd[:, a]", "t[lr[ps2:pe2] - s0] += upd[:, a]", 1),
+    ("checker: pivot rows miss updates", BCK, "ps = np.searchsorted(lr, s0)", "ps = np.searchsorted(lr, s1)", 1),
+    ("checker: L scaling by D transposed", BCK, ".reshape(-1, b) @ D if", ".reshape(-1, b) @ D.T if", 1),
+    ("checker: U scaling by D transposed", BCK, "uh = (D @ Uc.T).T", "uh = (D.T @ Uc.T).T", 1),
+    ("checker: D is the transposed inverse", BCK, "D = sla.lu_solve(sla.lu_factor(P), np.eye(b))",
+     "D = np.linalg.inv(P).T", 1),
+    ("checker: any flip accepted", BCK, "assert abs(nrm[k] - tau) <= flip_rtol * tau",
+     "assert abs(nrm[k] - tau) <= 1e30 * tau", 1),
+    # learned-skip features and classifier
+    ("features: sum of products is the last one", SKP, "S += v", "S = v", 1),
+    ("features: max is a sum", SKP, "M = max(M, v)", "M = M + v", 1),
+    ("features: d from block K", SKP, "d = Dfro[K - 1] if K > 0", "d = Dfro[K] if K > 0", 1),
+    ("features: 1-norm of A's part", SKP, "apart[i] += float(cval[e]) ** 2", "apart[i] += abs(float(cval[e]))", 1),
+    ("features: position from s_{K-1}", SKP, "max(0, i - s1)", "max(0, i - s0)", 1),
+    ("features: producer width not averaged", SKP, "(SB / C / 64.0) if C else 0.0", "(SB / 64.0) if C else 0.0", 1),
+    ("features: Y norm is a max", SKP, "yf = float(np.sqrt(sum(Ynorms[k] ** 2 for k in ys_in)))",
+     "yf = float(max(Ynorms[k] for k in ys_in))", 1),
+    ("features: first row right of the block never a candidate", SKP, "cand.update(i for i in Xset if i >= s1)",
+     "cand.update(i for i in Xset if i > s1)", 1),
+    ("features: labels inverted", SKP, "ys.append(0.0 if i in kept else 1.0)", "ys.append(1.0 if i in kept else 0.0)", 1),
+    ("classifier: no second ReLU", SKP, "h2 = np.maximum(a2, 0.0)", "h2 = a2", 1),
+    ("classifier: normalisation multiplies", SKP, "/ p[\"std\"]", "* p[\"std\"]", 1),
+    ("classifier: W2 transposed", SKP, "a2 = h1 @ p[\"W2\"].T + p[\"b2\"]", "a2 = h1 @ p[\"W2\"] + p[\"b2\"]", 1),
+    ("classifier: b1 dropped", SKP, "a1 = xs @ p[\"W1\"].T + p[\"b1\"]", "a1 = xs @ p[\"W1\"].T", 1),
+    ("classifier: gradient sign", SKP, "dz = (1.0 / (1.0 + np.exp(-z)) - y) / n", "dz = (y - 1.0 / (1.0 + np.exp(-z))) / n", 1),
+    ("classifier: W2 gradient transposed", SKP, "g[\"W2\"] = da2.T @ h1", "g[\"W2\"] = h1.T @ da2", 1),
+]
+
+
+def _plant(text: str, old: str, new: str, nth: int) -> str:
+    pos = -1
+    for _ in range(nth):
+        pos = text.find(old, pos + 1)
+        if pos < 0:
+            raise AssertionError(f"fragment not found (occurrence {nth}): {old!r}")
+    return text[:pos] + new + text[pos + len(old):]
+
+
+def _tree(dst: str, mutant) -> None:
+    os.makedirs(os.path.join(dst, "oracle"))
+    os.makedirs(os.path.join(dst, "tests"))
+    os.makedirs(os.path.join(dst, "paper_1908_10169_gb300"))
+    for f in ORACLE_FILES:
+        shutil.copy(os.path.join(ROOT, "oracle", f), os.path.join(dst, "oracle", f))
+    for f in PIN_TESTS + ["conftest.py"]:
+        shutil.copy(os.path.join(ROOT, "tests", f), os.path.join(dst, "tests", f))
+    # the seeded input generators only (no arithmetic of the method, no library binding)
+    shutil.copy(os.path.join(ROOT, "paper_1908_10169_gb300", "workloads.py"),
+                os.path.join(dst, "paper_1908_10169_gb300", "workloads.py"))
+    open(os.path.join(dst, "paper_1908_10169_gb300", "__init__.py"), "w").close()
+    shutil.copy(os.path.join(ROOT, "pytest.ini"), os.path.join(dst, "pytest.ini"))
+    if mutant is not None:
+        _, fname, old, new, nth = mutant
+        p = os.path.join(dst, "oracle", fname)
+        text = open(p).read()
+        open(p, "w").write(_plant(text, old, new, nth))
+
+
+def _run(dst: str):
+    env = {k: v for k, v in os.environ.items() if k != "PYTHONPATH"}
+    env.update(OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1", PYTHONDONTWRITEBYTECODE="1")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-m", "not gpu", "tests"], cwd=dst, env=env,
+                       capture_output=True, text=True, timeout=600)
+    return r.returncode, (r.stdout + r.stderr)[-1500:]
+
+
+def test_fragments_are_present():
+    """Every planted mistake still finds the code it changes (the check fails loudly when the
+    oracle is edited under it)."""
+    for name, fname, old, new, nth in MUTANTS:
+        text = open(os.path.join(ROOT, "oracle", fname)).read()
+        _plant(text, old, new, nth)
+
+
+def test_every_planted_mistake_fails_a_pin(tmp_path):
+    cases = [("unmodified", None)] + [(m[0], m) for m in MUTANTS]
+    dirs = {}
+    for i, (name, m) in enumerate(cases):
+        d = str(tmp_path / f"m{i:02d}")
+        _tree(d, m)
+        dirs[name] = d
+    workers = max(2, min(8, (os.cpu_count() or 2)))
+    with concurrent.futures.ThreadPoolExecutor(workers) as ex:
+        res = dict(zip(dirs, ex.map(_run, dirs.values())))
+    rc0, out0 = res.pop("unmodified")
+    assert rc0 == 0, f"the unmodified oracle copy fails its pins:\n{out0}"
+    survived = [n for n, (rc, _) in res.items() if rc == 0]
+    crashed = {n: (rc, out) for n, (rc, out) in res.items() if rc not in (0, 1)}
+    assert not survived, f"planted mistakes that no pin catches: {survived}"
+    assert not crashed, f"mutants that ended without a failing pin: {crashed}"

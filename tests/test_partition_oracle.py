@@ -48,6 +48,19 @@ def test_four_thirds_branch():
     assert list(O.partition_ilu1t(W.from_dense(Ad.T.copy()), 1e-3, 64)) == list(bs)
 
 
+def test_threshold_is_inclusive():
+    """Sec. 3.4 keeps an entry with |a_ik| >= tau |a_kk|: the case above with diagonal 64,
+    entries 1 and tau = 1/64 (tau |a_kk| = 1 exactly) gives the same blocks; a tau one ulp
+    larger drops the entries and leaves the diagonal's blocks of five."""
+    n = 50
+    Ad = 64.0 * np.eye(n)
+    Ad[10:40, 0] = 1.0
+    Ad[14:44, 1] = 1.0
+    A = W.from_dense(Ad)
+    assert list(O.partition_ilu1t(A, 1.0 / 64, 64)) == [0, 2, 7, 12, 17, 22, 27, 32, 37, 42, 47, 50]
+    assert list(O.partition_ilu1t(A, np.nextafter(1.0 / 64, 1.0), 64)) == list(range(0, 51, 5))
+
+
 def test_fill_from_original_entries():
     """a_01 = 1 and column 0 has rows 10..17: column 1 gets the fill rows 10..17 because
     |a_i0 a_01| >= tau |a_00 a_11|.  With them: r = 8, f = 20 <= s + 8 = 19 + 8, accepted;
