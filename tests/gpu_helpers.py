@@ -22,6 +22,29 @@ class GpuFactor:
     stats: object
     status: int
 
+    # block accessors with the oracle Factor's names (small problems)
+    def _b(self, K):
+        return int(self.bstart[K + 1] - self.bstart[K])
+
+    def L_block(self, K):
+        vp = _vptr(self.Lptr, self.bstart)
+        return self.Lrow[self.Lptr[K]:self.Lptr[K + 1]], self.Lval[vp[K]:vp[K + 1]].reshape(-1, self._b(K))
+
+    def U_block(self, K):
+        vp = _vptr(self.Uptr, self.bstart)
+        return self.Ucol[self.Uptr[K]:self.Uptr[K + 1]], self.Uval[vp[K]:vp[K + 1]].reshape(-1, self._b(K))
+
+    def _dblk(self, arr, K):
+        d0 = int(np.sum(np.diff(self.bstart[:K + 1]).astype(np.int64) ** 2))
+        b = self._b(K)
+        return arr[d0:d0 + b * b].reshape(b, b)
+
+    def D_block(self, K):
+        return self._dblk(self.Dinv, K)
+
+    def P_block(self, K):
+        return self._dblk(self.Pblk, K)
+
 
 def gpu_factor(ctx, A, droptol, params=None, export=True) -> GpuFactor:
     p = params if params is not None else B.bilu_params_default()

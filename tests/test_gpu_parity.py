@@ -10,6 +10,7 @@ import pytest
 import oracle as O
 import paper_1908_10169_gb300 as B
 from paper_1908_10169_gb300 import workloads as W
+from tests import test_golden as TG
 from tests.gpu_helpers import compare_factors, gpu_factor
 
 pytestmark = pytest.mark.gpu
@@ -170,6 +171,17 @@ def test_singular_block_status(ctx):
         g3 = gpu_factor(ctx, A3, 0.0, B.bilu_params_default(blocking=B.BILU_BLOCKING_FIXED, fixed_block=2, max_block=2))
         assert g3.status == B.BILU_PERTURBED
         compare_factors(O.bilu_factor(A3, np.array(bs3, np.int32), 0.0), g3)
+
+
+@pytest.mark.parametrize("name", TG.factor_fixtures())
+def test_gpu_matches_worked_example(ctx, name):
+    """The hand-derived worked examples of tests/golden, factored by the library."""
+    g = TG.load(name)
+    A = W.from_dense(TG.frac(g["A"]))
+    b = int(np.diff(g["bstart"]).max())
+    G = gpu_factor(ctx, A, TG.frac(g["tau"]), _fixed(b))
+    assert G.status == B.BILU_OK and list(G.bstart) == g["bstart"]
+    TG.check_factor(g, G, rtol=1e-14)
 
 
 def test_bounded_wait_timeout_leaves_context_usable(ctx):

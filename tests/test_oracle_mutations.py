@@ -16,7 +16,8 @@ import sys
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-PIN_TESTS = ["test_oracle.py", "test_partition_oracle.py", "test_block_check_oracle.py", "test_skip_oracle.py"]
+PIN_TESTS = ["test_oracle.py", "test_partition_oracle.py", "test_block_check_oracle.py", "test_skip_oracle.py",
+             "test_golden.py"]
 ORACLE_FILES = ["__init__.py", "bilu_oracle.c", "bilu_oracle.h", "block_check.py", "skip_oracle.py"]
 
 C, BCK, SKP = "bilu_oracle.c", "block_check.py", "skip_oracle.py"
@@ -130,6 +131,7 @@ def _tree(dst: str, mutant) -> None:
         shutil.copy(os.path.join(ROOT, "oracle", f), os.path.join(dst, "oracle", f))
     for f in PIN_TESTS + ["conftest.py"]:
         shutil.copy(os.path.join(ROOT, "tests", f), os.path.join(dst, "tests", f))
+    shutil.copytree(os.path.join(ROOT, "tests", "golden"), os.path.join(dst, "tests", "golden"))
     # the seeded input generators only (no arithmetic of the method, no library binding)
     shutil.copy(os.path.join(ROOT, "paper_1908_10169_gb300", "workloads.py"),
                 os.path.join(dst, "paper_1908_10169_gb300", "workloads.py"))
