@@ -238,6 +238,32 @@ def test_empty_matrix(ctx):
         B.bilu_destroy(c)
 
 
+@pytest.mark.parametrize("case", ["diagonal", "drop_all", "n1"])
+def test_degenerate_factors(ctx, case):
+    """Degenerate cases of the method: a diagonal matrix (no candidate anywhere, ragged
+    blocks), tau so large that every candidate is dropped (the preconditioner is block
+    Jacobi), and n = 1.  Factor and GMRES(30) against the oracle."""
+    if case == "diagonal":
+        A = W.from_dense(np.diag(np.random.default_rng(3).uniform(1.0, 5.0, 100)))
+        tau, blk = 1e-2, 7
+    elif case == "drop_all":
+        A = W.convdiff_upwind((8, 8, 8), seed=2)
+        tau, blk = 1e300, 8
+    else:
+        A = W.from_dense(np.array([[3.0]]))
+        tau, blk = 1e-2, 1
+    g = gpu_factor(ctx, A, tau, _fixed(blk))
+    o = _oracle(A, g.bstart, tau)
+    assert g.Lrow.size == 0 and g.Ucol.size == 0 and o.Lrow.size == 0 and o.Ucol.size == 0
+    compare_factors(o, g)
+    b = W.rhs_ones(A)
+    ro = O.gmres(A, o, b, tol=1e-8, restart=30)
+    x = np.zeros(A.n)
+    info = B.gmres_solve(ctx, b, x, 1e-8, 30, 10000)
+    assert info.status == B.BILU_OK and info.iters == ro.iters, (info.iters, ro.iters)
+    assert np.abs(x - ro.x).max() <= 1e-6 * np.abs(ro.x).max()
+
+
 def test_algorithmic_flop_counters_match_oracle(ctx):
     """The factor kernel counts its algorithmic work on the device; the integer counts
     equal the oracle's (same candidate sets, same update shapes)."""
