@@ -170,7 +170,9 @@ bilu_status gmres_solve(bilu_ctx *ctx, const double *b, double *x, double tol, i
  * The grid is split into groups of CTAs; each group takes the next matrix from a device
  * work queue (largest first) and runs the block recurrence of Algorithm 1 (Sec. 2.2) on
  * it.  The group size is tuned by timing candidates on the second call for a given (matrix
- * count, largest block, precision) and cached; the first call uses a size from the count.  Each context ends as after bilu_factor on it;
+ * count, largest block, precision) and cached process-wide (the cache is locked, so
+ * batches on disjoint contexts may be factored from different host threads); the first
+ * call uses a size from the count.  Each context ends as after bilu_factor on it;
  * statuses as bilu_factor (the worst one is returned, details in bilu_last_error of ctxs[0]).
  * Allocates and frees small device buffers per call.  Synchronizes the device.
  */
