@@ -205,8 +205,53 @@ bilu_status bilu_get_partition(bilu_ctx *ctx, int32_t *bstart);
 bilu_status bilu_export(bilu_ctx *ctx, int64_t *Lptr, int32_t *Lrow, double *Lval, int64_t *Uptr,
                         int32_t *Ucol, double *Uval, double *Dinv, double *Pblk);
 
-/* Human-readable description of the last error on this context ("" if none). */
+/* Human-readable description of the last error on this context ("" if none).  With
+ * ctx == NULL: the last error of this host thread's context-free calls
+ * (bilu_cosine_blocking, bilu_permute_csr). */
 const char *bilu_last_error(const bilu_ctx *ctx);
+
+/*
+ * Cosine-based blocking (Sec. 3.2), host only: no context, no device, no allocation visible
+ * to the caller.  Rows i and j of A (n x n CSR as in bilu_analyze; the values are not read)
+ * are grouped when their 0/1 patterns c_i, c_j satisfy |c_i n c_j|^2 >= tau |c_i| |c_j|
+ * (the paper uses tau = 0.8), checked over the pairs j > i that share a column and are not
+ * yet in a block.  Rows are visited in increasing order; a row not yet in a block leads a new
+ * block and takes its passing partners in increasing order, up to max_block (1..64) rows.
+ * An index whose row or column holds more than mu + 2 sigma entries (mu = nnz / n, sigma
+ * the standard deviation of the row, resp. column, counts; decided in exact integer
+ * arithmetic) takes no part and forms a block of its own.
+ * Outputs (caller-owned host arrays): perm[n], the original index at every new position
+ * (the symmetric permutation Q with A~ = Q^T A Q, A~[k][l] = A[perm[k]][perm[l]]; the blocks
+ * in the order of their leaders, each as leader then members ascending); bstart[n + 1], of
+ * which the first *nblocks + 1 entries are the block starts of A~; *nblocks.
+ * Errors: BILU_ERR_ARG (malformed pattern, tau < 0 or not finite, max_block out of range,
+ * null output), message in bilu_last_error(NULL).
+ */
+bilu_status bilu_cosine_blocking(int64_t n, const int64_t *rowptr, const int32_t *colind, double tau,
+                                 int32_t max_block, int32_t *perm, int32_t *bstart, int32_t *nblocks);
+
+/*
+ * Symmetric permutation A~ = Q^T A Q of a CSR matrix on the host (the reordering step of
+ * Sec. 3.2): row k of A~ is row perm[k] of A, every column index j renamed to the position of
+ * j in perm, each row sorted.  out_rowptr[n + 1], out_colind[nnz], out_val[nnz] are caller-
+ * owned host arrays of A's sizes.  A right-hand side b becomes b[perm[k]] at position k and
+ * a solution x~ of A~ maps back by x[perm[k]] = x~[k].
+ * Errors: BILU_ERR_ARG (malformed CSR, perm not a permutation of 0..n-1, null array), message
+ * in bilu_last_error(NULL).
+ */
+bilu_status bilu_permute_csr(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val,
+                             const int32_t *perm, int64_t *out_rowptr, int32_t *out_colind, double *out_val);
+
+/*
+ * bilu_analyze with the block partition given by the caller (for instance the one from
+ * bilu_cosine_blocking on the permuted matrix): bstart[nblocks + 1] with
+ * 0 = bstart[0] < ... < bstart[nblocks] = n and every block of 1..p->max_block indices
+ * (host array, copied).  p->blocking and p->fixed_block are not used.  Errors as
+ * bilu_analyze, BILU_ERR_ARG for an invalid partition.
+ */
+bilu_status bilu_analyze_partition(bilu_ctx *ctx, int64_t n, const int64_t *rowptr, const int32_t *colind,
+                                   const double *val, int32_t on_device, const bilu_params *p, int32_t nblocks,
+                                   const int32_t *bstart);
 
 /*
  * Test hooks for the failure paths (not for production use).  Settings are global to the

@@ -30,7 +30,8 @@ EXPORTED = ["bilu_params_default", "bilu_create", "bilu_analyze", "bilu_factor",
             "gmres_solve", "bilu_stats", "bilu_get_partition", "bilu_export", "bilu_last_error",
             "bilu_debug_set", "bilu_apply_noalloc", "bilu_factor_batch", "gmres_solve_batch",
             "bilu_record_samples", "bilu_get_samples", "bilu_mlp_train", "bilu_mlp_forward", "bilu_mlp_grad",
-            "bilu_set_skip_model", "bilu_destroy"]
+            "bilu_set_skip_model", "bilu_cosine_blocking", "bilu_permute_csr", "bilu_analyze_partition",
+            "bilu_destroy"]
 
 # learned skip classifier (layout of the model array: mean[F] std[F] W1[64][F] b1[64] W2[64][64]
 # b2[64] w3[64] b3)
@@ -105,6 +106,9 @@ def lib():
             "bilu_mlp_forward": ([P, P, P, i64, P], i32),
             "bilu_mlp_grad": ([P, P, P, P, i64, P], i32),
             "bilu_set_skip_model": ([P, P, f64], i32),
+            "bilu_cosine_blocking": ([i64, P, P, f64, i32, P, P, ct.POINTER(i32)], i32),
+            "bilu_permute_csr": ([i64, P, P, P, P, P, P, P], i32),
+            "bilu_analyze_partition": ([P, i64, P, P, P, i32, ct.POINTER(bilu_params), i32, P], i32),
             "bilu_destroy": ([P], None),
         }
         for name, (args, res) in sig.items():
@@ -130,7 +134,7 @@ def _check(ctx, st: int, allow=(BILU_OK,)):
     if st in allow or st > 0 and BILU_PERTURBED in allow:
         return st
     if st < 0 or st not in allow:
-        msg = lib().bilu_last_error(ctx).decode() if ctx else ""
+        msg = lib().bilu_last_error(ctx).decode()  # ctx None: this thread's context-free calls
         raise BiluError(st, msg)
     return st
 
@@ -169,6 +173,46 @@ def bilu_analyze(ctx, n: int, rowptr, colind, val, params: bilu_params | None = 
     p = params if params is not None else bilu_params_default()
     st = lib().bilu_analyze(ctx, n, _ptr(rowptr), _ptr(colind), _ptr(val), on_dev, ct.byref(p))
     return _check(ctx, st)
+
+
+def bilu_analyze_partition(ctx, n: int, rowptr, colind, val, bstart, params: bilu_params | None = None):
+    """bilu_analyze with the caller's block partition bstart (int32[nblocks + 1], host)."""
+    import numpy as np
+    on_dev = int(bool(getattr(val, "is_cuda", False)))
+    p = params if params is not None else bilu_params_default()
+    bs = np.ascontiguousarray(bstart, dtype=np.int32)
+    st = lib().bilu_analyze_partition(ctx, n, _ptr(rowptr), _ptr(colind), _ptr(val), on_dev, ct.byref(p),
+                                      len(bs) - 1, _ptr(bs))
+    return _check(ctx, st)
+
+
+def bilu_cosine_blocking(n: int, rowptr, colind, tau: float = 0.8, max_block: int = BILU_MAX_BLOCK):
+    """Sec. 3.2 cosine blocking on the host: returns (perm int32[n], bstart int32[nblocks + 1])."""
+    import numpy as np
+    rp = np.ascontiguousarray(rowptr, dtype=np.int64)
+    ci = np.ascontiguousarray(colind, dtype=np.int32)
+    perm = np.zeros(max(n, 1), np.int32)
+    bs = np.zeros(n + 1, np.int32)
+    nb = ct.c_int32(0)
+    st = lib().bilu_cosine_blocking(n, _ptr(rp), _ptr(ci), tau, max_block, _ptr(perm), _ptr(bs), ct.byref(nb))
+    _check(None, st)
+    return perm[:n].copy(), bs[:nb.value + 1].copy()
+
+
+def bilu_permute_csr(n: int, rowptr, colind, val, perm):
+    """Q^T A Q on the host: returns (rowptr int64[n+1], colind int32[nnz], val float64[nnz])."""
+    import numpy as np
+    rp = np.ascontiguousarray(rowptr, dtype=np.int64)
+    ci = np.ascontiguousarray(colind, dtype=np.int32)
+    va = np.ascontiguousarray(val, dtype=np.float64)
+    pm = np.ascontiguousarray(perm, dtype=np.int32)
+    nnz = int(rp[n]) if n > 0 else 0
+    orp = np.zeros(n + 1, np.int64)
+    oci = np.zeros(max(nnz, 1), np.int32)
+    ova = np.zeros(max(nnz, 1), np.float64)
+    st = lib().bilu_permute_csr(n, _ptr(rp), _ptr(ci), _ptr(va), _ptr(pm), _ptr(orp), _ptr(oci), _ptr(ova))
+    _check(None, st)
+    return orp, oci[:nnz].copy(), ova[:nnz].copy()
 
 
 def bilu_factor(ctx, droptol: float) -> int:

@@ -7,6 +7,8 @@
 #include <cmath>
 #include <cstring>
 #include <numeric>
+#include <string>
+#include <utility>
 
 #include "bilu_internal.h"
 
@@ -132,7 +134,147 @@ std::vector<int32_t> partition_ilu1t(const HostCSR &A, const std::vector<int32_t
     return bstart;
 }
 
+// Pattern checks shared by the host-only helpers: rowptr monotone from 0, column indices in
+// range and strictly increasing within each row.  Returns an empty string when valid.
+std::string check_pattern(int64_t n, const int64_t *rowptr, const int32_t *colind) {
+    if (n < 0 || n >= (int64_t)INT32_MAX) return "n out of range";
+    if (n > 0 && (!rowptr || !colind)) return "null CSR array";
+    if (n == 0) return "";
+    if (rowptr[0] != 0) return "rowptr[0] != 0";
+    for (int64_t i = 0; i < n; ++i)
+        if (rowptr[i + 1] < rowptr[i]) return "rowptr not monotone";
+    if (rowptr[n] >= (int64_t)INT32_MAX) return "nnz >= 2^31 not supported";
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+            if (colind[e] < 0 || colind[e] >= n) return "column index out of range";
+            if (e > rowptr[i] && colind[e] <= colind[e - 1])
+                return "column indices not strictly increasing within a row";
+        }
+    return "";
+}
+
+// count > mu + 2 sigma for each count (mu = nnz / n, sigma the population standard deviation
+// of the counts), decided exactly: n count > nnz and (n count - nnz)^2 > 4 (n S - nnz^2),
+// S = sum of squared counts.
+std::vector<char> above_two_sigma(const std::vector<int64_t> &cnt, int64_t nnz) {
+    const __int128 n = (__int128)cnt.size();
+    __int128 S = 0;
+    for (int64_t v : cnt) S += (__int128)v * v;
+    const __int128 var4 = 4 * (n * S - (__int128)nnz * nnz);
+    std::vector<char> out(cnt.size(), 0);
+    for (size_t i = 0; i < cnt.size(); ++i) {
+        const __int128 d = n * cnt[i] - nnz;
+        out[i] = d > 0 && d * d > var4;
+    }
+    return out;
+}
+
 }  // namespace
+
+// Sec. 3.2: rows i, j of A with 0/1 patterns c_i, c_j are grouped when
+// |c_i n c_j|^2 >= tau |c_i| |c_j|, over the pairs j > i that share a column (the upper part of
+// the pattern of A A^T) and are not yet in a block.  Rows are visited in increasing order; an
+// unplaced row leads a block and takes its passing partners in increasing order up to
+// max_block.  A row or column with more than mu + 2 sigma entries takes no part: its index is
+// a block of its own.  perm lists the blocks in the order of their leaders (leader first,
+// members ascending); bstart holds the block starts of Q^T A Q.
+bilu_status cosine_blocking_host(int64_t n, const int64_t *rowptr, const int32_t *colind, double tau,
+                                 int32_t max_block, int32_t *perm, int32_t *bstart, int32_t *nblocks,
+                                 std::string *err) {
+    auto fail = [&](const char *m) { if (err) *err = m; return BILU_ERR_ARG; };
+    const std::string bad = check_pattern(n, rowptr, colind);
+    if (!bad.empty()) return fail(bad.c_str());
+    if (!(tau >= 0.0) || !std::isfinite(tau)) return fail("tau must be finite and >= 0");
+    if (max_block < 1 || max_block > BILU_MAX_BLOCK) return fail("max_block must be in 1..64");
+    if (!bstart || !nblocks || (n > 0 && !perm)) return fail("null output array");
+    const int64_t nnz = n > 0 ? rowptr[n] : 0;
+    // columns of the pattern (rows ascending) and the row / column counts
+    std::vector<int64_t> rcnt(n), ccnt(n, 0);
+    std::vector<int64_t> cptr(n + 1, 0);
+    for (int64_t i = 0; i < n; ++i) rcnt[i] = rowptr[i + 1] - rowptr[i];
+    for (int64_t e = 0; e < nnz; ++e) ccnt[colind[e]]++;
+    for (int64_t j = 0; j < n; ++j) cptr[j + 1] = cptr[j] + ccnt[j];
+    std::vector<int32_t> crow(nnz);
+    {
+        std::vector<int64_t> next(cptr.begin(), cptr.end() - 1);
+        for (int64_t i = 0; i < n; ++i)
+            for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) crow[next[colind[e]]++] = (int32_t)i;
+    }
+    const std::vector<char> xr = above_two_sigma(rcnt, nnz), xc = above_two_sigma(ccnt, nnz);
+    std::vector<char> placed(n, 0);
+    std::vector<int32_t> seen(n, -1), partners;
+    int64_t pos = 0;
+    int32_t nb = 0;
+    bstart[0] = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (placed[i]) continue;
+        placed[i] = 1;
+        perm[pos++] = (int32_t)i;
+        int64_t size = 1;
+        if (!xr[i] && !xc[i]) {
+            partners.clear();
+            for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+                const int32_t k = colind[e];
+                for (int64_t f = cptr[k]; f < cptr[k + 1]; ++f) {
+                    const int32_t j = crow[f];
+                    if (j > i && seen[j] != (int32_t)i) {
+                        seen[j] = (int32_t)i;
+                        partners.push_back(j);
+                    }
+                }
+            }
+            std::sort(partners.begin(), partners.end());
+            const double ni = (double)rcnt[i];
+            for (int32_t j : partners) {
+                if (size >= max_block) break;
+                if (placed[j] || xr[j] || xc[j]) continue;
+                // |c_i n c_j| by merging the two sorted rows
+                int64_t a = rowptr[i], b = rowptr[j], cnt = 0;
+                while (a < rowptr[i + 1] && b < rowptr[j + 1]) {
+                    if (colind[a] < colind[b]) ++a;
+                    else if (colind[b] < colind[a]) ++b;
+                    else { ++cnt; ++a; ++b; }
+                }
+                if ((double)cnt * (double)cnt >= (tau * ni) * (double)rcnt[j]) {
+                    placed[j] = 1;
+                    perm[pos++] = j;
+                    ++size;
+                }
+            }
+        }
+        bstart[++nb] = (int32_t)pos;
+    }
+    *nblocks = nb;
+    return BILU_OK;
+}
+
+// A~ = Q^T A Q: row k of A~ is row perm[k] of A with every column j renamed iperm[j] and the
+// row re-sorted.
+bilu_status permute_csr_host(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val,
+                             const int32_t *perm, int64_t *out_rowptr, int32_t *out_colind, double *out_val,
+                             std::string *err) {
+    auto fail = [&](const char *m) { if (err) *err = m; return BILU_ERR_ARG; };
+    const std::string bad = check_pattern(n, rowptr, colind);
+    if (!bad.empty()) return fail(bad.c_str());
+    if (!out_rowptr || (n > 0 && (!perm || !val || !out_colind || !out_val))) return fail("null array");
+    std::vector<int32_t> iperm(n, -1);
+    for (int64_t k = 0; k < n; ++k) {
+        if (perm[k] < 0 || perm[k] >= n || iperm[perm[k]] >= 0) return fail("perm is not a permutation");
+        iperm[perm[k]] = (int32_t)k;
+    }
+    out_rowptr[0] = 0;
+    std::vector<std::pair<int32_t, double>> row;
+    for (int64_t k = 0; k < n; ++k) {
+        const int32_t i = perm[k];
+        row.clear();
+        for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) row.emplace_back(iperm[colind[e]], val[e]);
+        std::sort(row.begin(), row.end(), [](const auto &x, const auto &y) { return x.first < y.first; });
+        int64_t o = out_rowptr[k];
+        for (const auto &rv : row) { out_colind[o] = rv.first; out_val[o] = rv.second; ++o; }
+        out_rowptr[k + 1] = o;
+    }
+    return BILU_OK;
+}
 
 void matrix_free(bilu_ctx *c) {
     dev_free(c->d_rowptr);
@@ -147,15 +289,26 @@ void matrix_free(bilu_ctx *c) {
 }
 
 bilu_status analyze_run(bilu_ctx *c, int64_t n, const int64_t *rowptr, const int32_t *colind,
-                        const double *val, int on_device, const bilu_params *p) {
+                        const double *val, int on_device, const bilu_params *p,
+                        const int32_t *given_bstart, int32_t given_nb) {
     if (!p) return set_err(c, BILU_ERR_ARG, "params is NULL");
     if (n < 0 || n >= (int64_t)INT32_MAX) return set_err(c, BILU_ERR_ARG, "n out of range");
     if (p->max_block < 1 || p->max_block > BILU_MAX_BLOCK)
         return set_err(c, BILU_ERR_ARG, "max_block must be in 1..64");
-    if (p->blocking == BILU_BLOCKING_FIXED && (p->fixed_block < 1 || p->fixed_block > p->max_block))
+    const bool given = given_nb >= 0;
+    if (!given && p->blocking == BILU_BLOCKING_FIXED && (p->fixed_block < 1 || p->fixed_block > p->max_block))
         return set_err(c, BILU_ERR_ARG, "fixed_block must be in 1..max_block");
-    if (p->blocking != BILU_BLOCKING_FIXED && p->blocking != BILU_BLOCKING_ILU1T)
+    if (!given && p->blocking != BILU_BLOCKING_FIXED && p->blocking != BILU_BLOCKING_ILU1T)
         return set_err(c, BILU_ERR_ARG, "unknown blocking");
+    if (given) {  // a caller's partition: 0 = s_0 < s_1 < ... < s_nb = n, blocks <= max_block
+        if (!given_bstart) return set_err(c, BILU_ERR_ARG, "null partition");
+        if (given_bstart[0] != 0 || given_bstart[given_nb] != n || (n > 0 && given_nb == 0))
+            return set_err(c, BILU_ERR_ARG, "partition must run from 0 to n");
+        for (int32_t K = 0; K < given_nb; ++K) {
+            const int64_t b = (int64_t)given_bstart[K + 1] - given_bstart[K];
+            if (b < 1 || b > p->max_block) return set_err(c, BILU_ERR_ARG, "partition block size not in 1..max_block");
+        }
+    }
     if (!(p->tau_analyze >= 0.0) || !(p->pert_tau >= 0.0) || !(p->pert_rho >= 0.0))
         return set_err(c, BILU_ERR_ARG, "negative or NaN tolerance");
     if (p->precision != BILU_PREC_FP64 && p->precision != BILU_PREC_FP32 && p->precision != BILU_PREC_BF16)
@@ -207,7 +360,9 @@ bilu_status analyze_run(bilu_ctx *c, int64_t n, const int64_t *rowptr, const int
     build_csc(A, colptr, rowind, cval);
 
     std::vector<int32_t> bstart;
-    if (p->blocking == BILU_BLOCKING_FIXED) {
+    if (given) {
+        bstart.assign(given_bstart, given_bstart + given_nb + 1);
+    } else if (p->blocking == BILU_BLOCKING_FIXED) {
         for (int64_t s = 0; s < n; s += p->fixed_block) bstart.push_back((int32_t)s);
         bstart.push_back((int32_t)n);
     } else {

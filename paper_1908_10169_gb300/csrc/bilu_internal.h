@@ -178,6 +178,15 @@ bilu_status gmres_batch_run(bilu_ctx *const *ctxs, int count, const double *cons
                             int m, int maxit, gmres_info *info);
 bilu_status factor_batch_run(bilu_ctx *const *ctxs, int count, double droptol, double *ms_out);
 bilu_status analyze_run(bilu_ctx *c, int64_t n, const int64_t *rowptr, const int32_t *colind,
-                        const double *val, int on_device, const bilu_params *p);
+                        const double *val, int on_device, const bilu_params *p,
+                        const int32_t *given_bstart = nullptr, int32_t given_nb = -1);
+// host-only analysis helpers (no context, no device): Sec. 3.2 cosine blocking and the
+// symmetric permutation of a CSR matrix; the message goes to *err
+bilu_status cosine_blocking_host(int64_t n, const int64_t *rowptr, const int32_t *colind, double tau,
+                                 int32_t max_block, int32_t *perm, int32_t *bstart, int32_t *nblocks,
+                                 std::string *err);
+bilu_status permute_csr_host(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val,
+                             const int32_t *perm, int64_t *out_rowptr, int32_t *out_colind, double *out_val,
+                             std::string *err);
 void matrix_free(bilu_ctx *c);
 void mlp_free(bilu_ctx *c);

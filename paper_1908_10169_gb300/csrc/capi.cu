@@ -2,6 +2,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "bilu_internal.h"
@@ -93,7 +94,23 @@ void bilu_destroy(bilu_ctx *c) {
     delete c;
 }
 
-const char *bilu_last_error(const bilu_ctx *c) { return c ? c->err.c_str() : "null context"; }
+namespace {
+thread_local std::string g_host_err;  // last error of this thread's context-free calls
+}
+
+const char *bilu_last_error(const bilu_ctx *c) { return c ? c->err.c_str() : g_host_err.c_str(); }
+
+bilu_status bilu_cosine_blocking(int64_t n, const int64_t *rowptr, const int32_t *colind, double tau,
+                                 int32_t max_block, int32_t *perm, int32_t *bstart, int32_t *nblocks) {
+    g_host_err.clear();
+    return cosine_blocking_host(n, rowptr, colind, tau, max_block, perm, bstart, nblocks, &g_host_err);
+}
+
+bilu_status bilu_permute_csr(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val,
+                             const int32_t *perm, int64_t *out_rowptr, int32_t *out_colind, double *out_val) {
+    g_host_err.clear();
+    return permute_csr_host(n, rowptr, colind, val, perm, out_rowptr, out_colind, out_val, &g_host_err);
+}
 
 bilu_status bilu_analyze(bilu_ctx *c, int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val,
                          int32_t on_device, const bilu_params *p) {
@@ -101,6 +118,16 @@ bilu_status bilu_analyze(bilu_ctx *c, int64_t n, const int64_t *rowptr, const in
     c->err.clear();
     BILU_CUDA(c, cudaSetDevice(c->device));
     return analyze_run(c, n, rowptr, colind, val, on_device, p);
+}
+
+bilu_status bilu_analyze_partition(bilu_ctx *c, int64_t n, const int64_t *rowptr, const int32_t *colind,
+                                   const double *val, int32_t on_device, const bilu_params *p, int32_t nblocks,
+                                   const int32_t *bstart) {
+    if (!c) return BILU_ERR_ARG;
+    c->err.clear();
+    if (nblocks < 0) return set_err(c, BILU_ERR_ARG, "nblocks < 0");
+    BILU_CUDA(c, cudaSetDevice(c->device));
+    return analyze_run(c, n, rowptr, colind, val, on_device, p, bstart, nblocks);
 }
 
 bilu_status bilu_factor(bilu_ctx *c, double droptol) {

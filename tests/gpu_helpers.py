@@ -46,9 +46,14 @@ class GpuFactor:
         return self._dblk(self.Pblk, K)
 
 
-def gpu_factor(ctx, A, droptol, params=None, export=True) -> GpuFactor:
+def gpu_factor(ctx, A, droptol, params=None, export=True, bstart=None) -> GpuFactor:
+    """Analyse (with the partition bstart when given), factor and export through the C ABI."""
     p = params if params is not None else B.bilu_params_default()
-    B.bilu_analyze(ctx, A.n, A.rowptr.astype(np.int64), A.colind.astype(np.int32), A.val.astype(np.float64), p)
+    if bstart is not None:
+        B.bilu_analyze_partition(ctx, A.n, A.rowptr.astype(np.int64), A.colind.astype(np.int32),
+                                 A.val.astype(np.float64), bstart, p)
+    else:
+        B.bilu_analyze(ctx, A.n, A.rowptr.astype(np.int64), A.colind.astype(np.int32), A.val.astype(np.float64), p)
     st = B.bilu_factor(ctx, droptol)
     s = B.bilu_stats(ctx)
     bs = np.zeros(s.nblocks + 1, np.int32)

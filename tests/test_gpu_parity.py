@@ -184,6 +184,37 @@ def test_gpu_matches_worked_example(ctx, name):
     TG.check_factor(g, G, rtol=1e-14)
 
 
+def test_cosine_blocking_end_to_end(ctx):
+    """Sec. 3.2 then Sec. 2.2 / Sec. 4: a Q1 elasticity matrix (3 unknowns per node) in a
+    random ordering; the library's cosine blocking finds the node blocks, the permuted matrix
+    is factored with that partition (bilu_analyze_partition), and factor and GMRES(30) match
+    the oracle on the same matrix and partition."""
+    w = W.elasticity3d(side=5, seed=2, block=63)
+    scramble = np.random.default_rng(11).permutation(w.A.n).astype(np.int32)
+    A1 = W.CSR(w.A.n, *B.bilu_permute_csr(w.A.n, w.A.rowptr, w.A.colind, w.A.val, scramble))
+    perm, bs = B.bilu_cosine_blocking(A1.n, A1.rowptr, A1.colind, 0.8, 64)
+    assert np.diff(bs).max() == 3 and (np.diff(bs) == 3).sum() >= 50
+    A2 = W.CSR(A1.n, *B.bilu_permute_csr(A1.n, A1.rowptr, A1.colind, A1.val, perm))
+    g = gpu_factor(ctx, A2, w.droptol, bstart=bs)
+    assert np.array_equal(g.bstart, bs)
+    o = _oracle(A2, bs, w.droptol)
+    compare_factors(o, g, A=A2, tau=w.droptol)
+    b = W.rhs_ones(A2)
+    ro = O.gmres(A2, o, b, tol=1e-8, restart=30)
+    x = np.zeros(A2.n)
+    info = B.gmres_solve(ctx, b, x, 1e-8, 30, 10000)
+    assert info.status == B.BILU_OK and info.iters == ro.iters, (info.iters, ro.iters)
+    assert np.abs(x - ro.x).max() <= 1e-6 * np.abs(ro.x).max()
+
+
+def test_analyze_partition_rejects_invalid_partitions(ctx):
+    A = W.convdiff_upwind((4, 4, 4), seed=1)
+    for bs in ([0, 10, 10, 64], [0, 70], [1, 64], [0, 32]):
+        with pytest.raises(B.BiluError) as e:
+            B.bilu_analyze_partition(ctx, A.n, A.rowptr, A.colind, A.val, np.array(bs, np.int32))
+        assert e.value.status == B.BILU_ERR_ARG
+
+
 def test_bounded_wait_timeout_leaves_context_usable(ctx):
     A = W.convdiff_upwind((8, 8, 8), seed=1)
     B.bilu_debug_set(ctx, B.BILU_DEBUG_SPIN_LIMIT, 20000)

@@ -17,10 +17,11 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PIN_TESTS = ["test_oracle.py", "test_partition_oracle.py", "test_block_check_oracle.py", "test_skip_oracle.py",
-             "test_golden.py"]
-ORACLE_FILES = ["__init__.py", "bilu_oracle.c", "bilu_oracle.h", "block_check.py", "skip_oracle.py"]
+             "test_golden.py", "test_cosine_oracle.py"]
+ORACLE_FILES = ["__init__.py", "bilu_oracle.c", "bilu_oracle.h", "block_check.py", "skip_oracle.py",
+                "cosine_oracle.py"]
 
-C, BCK, SKP = "bilu_oracle.c", "block_check.py", "skip_oracle.py"
+C, BCK, SKP, COS = "bilu_oracle.c", "block_check.py", "skip_oracle.py", "cosine_oracle.py"
 
 # (name, file, fragment, replacement, which occurrence of the fragment: 1 = first)
 MUTANTS = [
@@ -93,6 +94,17 @@ MUTANTS = [
      "D = np.linalg.inv(P).T", 1),
     ("checker: any flip accepted", BCK, "assert abs(nrm[k] - tau) <= flip_rtol * tau",
      "assert abs(nrm[k] - tau) <= 1e30 * tau", 1),
+    # cosine blocking (Sec. 3.2)
+    ("cosine: strict test", COS, "float(cnt) ** 2 >= (tau", "float(cnt) ** 2 > (tau", 1),
+    ("cosine: excluded partners join", COS, "if placed[j] or skip[j]:", "if placed[j]:", 1),
+    ("cosine: block one larger than max_block", COS, "if len(block) >= max_block:", "if len(block) > max_block:", 1),
+    ("cosine: exclusion by rows only", COS, "return np.array([a or b for a, b in zip(r, c)], dtype=bool)",
+     "return np.array([a for a, b in zip(r, c)], dtype=bool)", 1),
+    ("cosine: three sigma", COS, "var4 = 4 * (n * S - nnz * nnz)", "var4 = 9 * (n * S - nnz * nnz)", 1),
+    ("cosine: members in decreasing order", COS, "partners = sorted({j for k in rows[i] for j in cols[k] if j > i})",
+     "partners = sorted({j for k in rows[i] for j in cols[k] if j > i}, reverse=True)", 1),
+    ("cosine: test against the column count", COS, "(tau * len(rows[i])) * len(rows[j])",
+     "(tau * len(rows[i])) * len(cols[j])", 1),
     # learned-skip features and classifier
     ("features: sum of products is the last one", SKP, "S += v", "S = v", 1),
     ("features: max is a sum", SKP, "M = max(M, v)", "M = M + v", 1),
