@@ -130,6 +130,63 @@ def _ptr(a):
     return a.ctypes.data_as(ct.c_void_p)
 
 
+def _size_of(a, dtype: str, name: str) -> int:
+    """Element count of a numpy array or torch tensor of exactly `dtype` (e.g. "float64"),
+    C-contiguous; raises TypeError / ValueError otherwise (no silent conversion: the C side
+    reads the memory as that type)."""
+    if hasattr(a, "data_ptr"):
+        got = str(a.dtype).replace("torch.", "")
+        if got != dtype:
+            raise TypeError(f"{name}: tensor of {got}, expected {dtype}")
+        if not a.is_contiguous():
+            raise ValueError(f"{name}: tensor must be contiguous")
+        return int(a.numel())
+    if not hasattr(a, "dtype") or not hasattr(a, "flags"):
+        raise TypeError(f"{name}: expected a numpy array or a torch tensor, got {type(a).__name__}")
+    if str(a.dtype) != dtype:
+        raise TypeError(f"{name}: array of {a.dtype}, expected {dtype}")
+    if not a.flags.c_contiguous:
+        raise ValueError(f"{name}: array must be C-contiguous")
+    return int(a.size)
+
+
+def _buf(a, dtype: str, count: int | None, name: str, allow_none: bool = False):
+    """Pointer of `a` after checking its type and that it holds at least `count` elements
+    (count None: not known here).  None passes as NULL where the C call accepts NULL."""
+    if a is None:
+        if allow_none or count == 0:
+            return None
+        raise ValueError(f"{name} is None")
+    size = _size_of(a, dtype, name)
+    if count is not None and size < count:
+        raise ValueError(f"{name}: {size} elements, the call needs {count}")
+    return _ptr(a)
+
+
+def _item(a, i: int) -> int:
+    """a[i] of a numpy array or a (host or device) torch tensor as a Python int."""
+    v = a[i]
+    return int(v.item()) if hasattr(v, "item") else int(v)
+
+
+# the size n of each context's last analysis through this binding (vector length checks)
+_CTX_N: dict = {}
+
+
+def _ctx_key(ctx):
+    return ctx.value if hasattr(ctx, "value") else ctx
+
+
+def _csr(n: int, rowptr, colind, val):
+    if n < 0:
+        raise ValueError("n < 0")
+    prp = _buf(rowptr, "int64", n + 1, "rowptr")
+    nnz = _item(rowptr, n)
+    if nnz < 0:
+        raise ValueError("rowptr[n] < 0")
+    return prp, _buf(colind, "int32", nnz, "colind"), _buf(val, "float64", nnz, "val")
+
+
 def _check(ctx, st: int, allow=(BILU_OK,)):
     if st in allow or st > 0 and BILU_PERTURBED in allow:
         return st
@@ -160,6 +217,7 @@ def bilu_create(device: int = 0, stream=None):
 
 
 def bilu_destroy(ctx):
+    _CTX_N.pop(_ctx_key(ctx), None)
     lib().bilu_destroy(ctx)
 
 
@@ -170,27 +228,40 @@ def bilu_last_error(ctx) -> str:
 def bilu_analyze(ctx, n: int, rowptr, colind, val, params: bilu_params | None = None):
     """rowptr int64[n+1], colind int32[nnz], val float64[nnz]; numpy / CPU tensors or CUDA tensors."""
     on_dev = int(bool(getattr(val, "is_cuda", False)))
+    prp, pci, pva = _csr(n, rowptr, colind, val)
     p = params if params is not None else bilu_params_default()
-    st = lib().bilu_analyze(ctx, n, _ptr(rowptr), _ptr(colind), _ptr(val), on_dev, ct.byref(p))
-    return _check(ctx, st)
+    st = lib().bilu_analyze(ctx, n, prp, pci, pva, on_dev, ct.byref(p))
+    _check(ctx, st)
+    _CTX_N[_ctx_key(ctx)] = n
+    return st
 
 
 def bilu_analyze_partition(ctx, n: int, rowptr, colind, val, bstart, params: bilu_params | None = None):
     """bilu_analyze with the caller's block partition bstart (int32[nblocks + 1], host)."""
     import numpy as np
     on_dev = int(bool(getattr(val, "is_cuda", False)))
+    prp, pci, pva = _csr(n, rowptr, colind, val)
     p = params if params is not None else bilu_params_default()
     bs = np.ascontiguousarray(bstart, dtype=np.int32)
-    st = lib().bilu_analyze_partition(ctx, n, _ptr(rowptr), _ptr(colind), _ptr(val), on_dev, ct.byref(p),
-                                      len(bs) - 1, _ptr(bs))
-    return _check(ctx, st)
+    if bs.size < 1:
+        raise ValueError("bstart needs at least one entry")
+    st = lib().bilu_analyze_partition(ctx, n, prp, pci, pva, on_dev, ct.byref(p), len(bs) - 1, _ptr(bs))
+    _check(ctx, st)
+    _CTX_N[_ctx_key(ctx)] = n
+    return st
 
 
 def bilu_cosine_blocking(n: int, rowptr, colind, tau: float = 0.8, max_block: int = BILU_MAX_BLOCK):
     """Sec. 3.2 cosine blocking on the host: returns (perm int32[n], bstart int32[nblocks + 1])."""
     import numpy as np
+    if n < 0:
+        raise ValueError("n < 0")
     rp = np.ascontiguousarray(rowptr, dtype=np.int64)
+    if rp.size < n + 1:
+        raise ValueError("rowptr needs n + 1 entries")
     ci = np.ascontiguousarray(colind, dtype=np.int32)
+    if ci.size < (int(rp[n]) if n > 0 else 0):
+        raise ValueError("colind shorter than rowptr[n]")
     perm = np.zeros(max(n, 1), np.int32)
     bs = np.zeros(n + 1, np.int32)
     nb = ct.c_int32(0)
@@ -202,11 +273,17 @@ def bilu_cosine_blocking(n: int, rowptr, colind, tau: float = 0.8, max_block: in
 def bilu_permute_csr(n: int, rowptr, colind, val, perm):
     """Q^T A Q on the host: returns (rowptr int64[n+1], colind int32[nnz], val float64[nnz])."""
     import numpy as np
+    if n < 0:
+        raise ValueError("n < 0")
     rp = np.ascontiguousarray(rowptr, dtype=np.int64)
     ci = np.ascontiguousarray(colind, dtype=np.int32)
     va = np.ascontiguousarray(val, dtype=np.float64)
     pm = np.ascontiguousarray(perm, dtype=np.int32)
+    if rp.size < n + 1 or pm.size < n:
+        raise ValueError("rowptr needs n + 1 entries and perm n")
     nnz = int(rp[n]) if n > 0 else 0
+    if ci.size < nnz or va.size < nnz:
+        raise ValueError("colind / val shorter than rowptr[n]")
     orp = np.zeros(n + 1, np.int64)
     oci = np.zeros(max(nnz, 1), np.int32)
     ova = np.zeros(max(nnz, 1), np.float64)
@@ -220,20 +297,24 @@ def bilu_factor(ctx, droptol: float) -> int:
     return _check(ctx, st, (BILU_OK, BILU_PERTURBED))
 
 
+def _vec(ctx, v, name):
+    return _buf(v, "float64", _CTX_N.get(_ctx_key(ctx)), name)
+
+
 def bilu_apply(ctx, r, z) -> int:
-    st = lib().bilu_apply(ctx, _ptr(r), _ptr(z))
+    st = lib().bilu_apply(ctx, _vec(ctx, r, "r"), _vec(ctx, z, "z"))
     return _check(ctx, st)
 
 
 def bilu_apply_noalloc(ctx, r, z) -> int:
     """bilu_apply for callers that cannot allocate: device vectors only, fixed scratch."""
-    st = lib().bilu_apply_noalloc(ctx, _ptr(r), _ptr(z))
+    st = lib().bilu_apply_noalloc(ctx, _vec(ctx, r, "r"), _vec(ctx, z, "z"))
     return _check(ctx, st)
 
 
 def gmres_solve(ctx, b, x, tol: float = 1e-8, restart: int = 30, maxit: int = 10000) -> gmres_info:
     info = gmres_info()
-    st = lib().gmres_solve(ctx, _ptr(b), _ptr(x), tol, restart, maxit, ct.byref(info))
+    st = lib().gmres_solve(ctx, _vec(ctx, b, "b"), _vec(ctx, x, "x"), tol, restart, maxit, ct.byref(info))
     _check(ctx, st, (BILU_OK, BILU_NOT_CONVERGED))
     info.status = st
     return info
@@ -250,8 +331,10 @@ def gmres_solve_batch(ctxs, bs, xs, tol: float = 1e-8, restart: int = 30, maxit:
     """GMRES on every system of a batch; returns the gmres_info of each system."""
     n = len(ctxs)
     arr = (ct.c_void_p * n)(*[c.value if hasattr(c, "value") else c for c in ctxs])
-    pb = (ct.c_void_p * n)(*[_ptr(v).value for v in bs])
-    px = (ct.c_void_p * n)(*[_ptr(v).value for v in xs])
+    if len(bs) != n or len(xs) != n:
+        raise ValueError("one b and one x per context")
+    pb = (ct.c_void_p * n)(*[_vec(c, v, "b").value for c, v in zip(ctxs, bs)])
+    px = (ct.c_void_p * n)(*[_vec(c, v, "x").value for c, v in zip(ctxs, xs)])
     infos = (gmres_info * n)()
     st = lib().gmres_solve_batch(arr, n, pb, px, tol, restart, maxit, infos)
     _check(ctxs[0], st, (BILU_OK, BILU_NOT_CONVERGED))
@@ -265,12 +348,19 @@ def bilu_stats(ctx) -> bilu_stats_t:
 
 
 def bilu_get_partition(ctx, out):
-    return _check(ctx, lib().bilu_get_partition(ctx, _ptr(out)))
+    s = bilu_stats(ctx)
+    return _check(ctx, lib().bilu_get_partition(ctx, _buf(out, "int32", s.nblocks + 1, "bstart")))
 
 
 def bilu_export(ctx, Lptr=None, Lrow=None, Lval=None, Uptr=None, Ucol=None, Uval=None, Dinv=None, Pblk=None):
-    return _check(ctx, lib().bilu_export(ctx, _ptr(Lptr), _ptr(Lrow), _ptr(Lval), _ptr(Uptr), _ptr(Ucol),
-                                         _ptr(Uval), _ptr(Dinv), _ptr(Pblk)))
+    """Copies the factor into host arrays sized from bilu_stats (any may be None)."""
+    s = bilu_stats(ctx)
+    nb1 = s.nblocks + 1
+    args = [_buf(Lptr, "int64", nb1, "Lptr", True), _buf(Lrow, "int32", s.kept_rows, "Lrow", True),
+            _buf(Lval, "float64", s.nnz_l, "Lval", True), _buf(Uptr, "int64", nb1, "Uptr", True),
+            _buf(Ucol, "int32", s.kept_cols, "Ucol", True), _buf(Uval, "float64", s.nnz_u, "Uval", True),
+            _buf(Dinv, "float64", s.nnz_d, "Dinv", True), _buf(Pblk, "float64", s.nnz_d, "Pblk", True)]
+    return _check(ctx, lib().bilu_export(ctx, *args))
 
 
 def bilu_debug_set(ctx, what: int, value: int):
@@ -288,7 +378,10 @@ def bilu_get_samples(ctx, x=None, y=None, tags=None, cap: int = 0) -> int:
     """Copies up to cap samples into x (cap x F float32), y (cap float32), tags (cap int64 or
     None); returns the number of samples held."""
     cnt = ct.c_int64()
-    _check(ctx, lib().bilu_get_samples(ctx, _ptr(x), _ptr(y), _ptr(tags), cap, ct.byref(cnt)))
+    px = _buf(x, "float32", cap * BILU_MLP_FEATURES, "x")
+    py = _buf(y, "float32", cap, "y")
+    pt = _buf(tags, "int64", cap, "tags", allow_none=True)
+    _check(ctx, lib().bilu_get_samples(ctx, px, py, pt, cap, ct.byref(cnt)))
     return cnt.value
 
 
@@ -296,23 +389,30 @@ def bilu_mlp_train(ctx, x, y, epochs: int = 4, batch: int = 4096, lr: float = 2e
     """Trains the classifier on n samples (x n x F float32, y n float32); returns (model, loss)."""
     import numpy as np
     n = int(y.shape[0])
+    px, py = _buf(x, "float32", n * BILU_MLP_FEATURES, "x"), _buf(y, "float32", n, "y")
     cfg = bilu_mlp_train_cfg(epochs, batch, lr, seed)
     model = np.zeros(BILU_MLP_PARAMS, np.float32)
     loss = ct.c_double()
-    _check(ctx, lib().bilu_mlp_train(ctx, _ptr(x), _ptr(y), n, ct.byref(cfg), _ptr(model), ct.byref(loss)))
+    _check(ctx, lib().bilu_mlp_train(ctx, px, py, n, ct.byref(cfg), _ptr(model), ct.byref(loss)))
     return model, loss.value
 
 
 def bilu_mlp_forward(ctx, model, x, logits):
-    return _check(ctx, lib().bilu_mlp_forward(ctx, _ptr(model), _ptr(x), int(logits.shape[0]), _ptr(logits)))
+    n = int(logits.shape[0])
+    return _check(ctx, lib().bilu_mlp_forward(ctx, _buf(model, "float32", BILU_MLP_PARAMS, "model"),
+                                              _buf(x, "float32", n * BILU_MLP_FEATURES, "x"), n,
+                                              _buf(logits, "float32", n, "logits")))
 
 
 def bilu_mlp_grad(ctx, model, x, y):
     import numpy as np
+    n = int(y.shape[0])
     g = np.zeros(BILU_MLP_PARAMS, np.float32)
-    _check(ctx, lib().bilu_mlp_grad(ctx, _ptr(model), _ptr(x), _ptr(y), int(y.shape[0]), _ptr(g)))
+    _check(ctx, lib().bilu_mlp_grad(ctx, _buf(model, "float32", BILU_MLP_PARAMS, "model"),
+                                    _buf(x, "float32", n * BILU_MLP_FEATURES, "x"), _buf(y, "float32", n, "y"),
+                                    n, _ptr(g)))
     return g
 
 
 def bilu_set_skip_model(ctx, model, logit_hi: float):
-    return _check(ctx, lib().bilu_set_skip_model(ctx, _ptr(model), logit_hi))
+    return _check(ctx, lib().bilu_set_skip_model(ctx, _buf(model, "float32", BILU_MLP_PARAMS, "model"), logit_hi))
