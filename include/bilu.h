@@ -207,7 +207,7 @@ bilu_status bilu_export(bilu_ctx *ctx, int64_t *Lptr, int32_t *Lrow, double *Lva
 
 /* Human-readable description of the last error on this context ("" if none).  With
  * ctx == NULL: the last error of this host thread's context-free calls
- * (bilu_cosine_blocking, bilu_permute_csr). */
+ * (bilu_cosine_blocking, bilu_partition_ilu1t, bilu_permute_csr). */
 const char *bilu_last_error(const bilu_ctx *ctx);
 
 /*
@@ -231,6 +231,21 @@ bilu_status bilu_cosine_blocking(int64_t n, const int64_t *rowptr, const int32_t
                                  int32_t max_block, int32_t *perm, int32_t *bstart, int32_t *nblocks);
 
 /*
+ * The simplified ILU(1,tau) block-pattern guess of Sec. 3.4 on the host (the partition that
+ * bilu_analyze builds with BILU_BLOCKING_ILU1T), no context or device.  A as in bilu_analyze
+ * (host arrays, values read); tau >= 0 the analysis threshold; max_block 1..64.  With
+ * gstart == NULL columns join a block one at a time; otherwise gstart[ngroups + 1]
+ * (0 = gstart[0] < ... < gstart[ngroups] = n, groups of 1..max_block) are the units of growth,
+ * for instance the cosine blocks of Sec. 3.2: a group joins (or starts) a block as a whole, by
+ * the same rule with its columns' pattern unions and scalar counts.  bstart[n + 1] (caller-
+ * owned) receives the block starts, *nblocks their number.  Errors: BILU_ERR_ARG, message in
+ * bilu_last_error(NULL).
+ */
+bilu_status bilu_partition_ilu1t(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val,
+                                 double tau, int32_t max_block, int32_t ngroups, const int32_t *gstart,
+                                 int32_t *bstart, int32_t *nblocks);
+
+/*
  * Symmetric permutation A~ = Q^T A Q of a CSR matrix on the host (the reordering step of
  * Sec. 3.2): row k of A~ is row perm[k] of A, every column index j renamed to the position of
  * j in perm, each row sorted.  out_rowptr[n + 1], out_colind[nnz], out_val[nnz] are caller-
@@ -246,8 +261,10 @@ bilu_status bilu_permute_csr(int64_t n, const int64_t *rowptr, const int32_t *co
  * bilu_analyze with the block partition given by the caller (for instance the one from
  * bilu_cosine_blocking on the permuted matrix): bstart[nblocks + 1] with
  * 0 = bstart[0] < ... < bstart[nblocks] = n and every block of 1..p->max_block indices
- * (host array, copied).  p->blocking and p->fixed_block are not used.  Errors as
- * bilu_analyze, BILU_ERR_ARG for an invalid partition.
+ * (host array, copied).  With p->blocking == BILU_BLOCKING_ILU1T the given blocks are groups
+ * that the Sec. 3.4 growth rule merges (as bilu_partition_ilu1t with gstart = bstart, threshold
+ * p->tau_analyze); otherwise they are used as they are (p->fixed_block is not used).  Errors
+ * as bilu_analyze, BILU_ERR_ARG for an invalid partition.
  */
 bilu_status bilu_analyze_partition(bilu_ctx *ctx, int64_t n, const int64_t *rowptr, const int32_t *colind,
                                    const double *val, int32_t on_device, const bilu_params *p, int32_t nblocks,

@@ -47,6 +47,8 @@ def lib():
         L.orc_partition_fixed.restype = i32
         L.orc_partition_ilu1t.argtypes = [i64, P, P, P, f64, i32, P]
         L.orc_partition_ilu1t.restype = i32
+        L.orc_partition_ilu1t_groups.argtypes = [i64, P, P, P, f64, i32, i32, P, P]
+        L.orc_partition_ilu1t_groups.restype = i32
         L.orc_bilu_factor.argtypes = [i64, P, P, P, i32, P, f64, i32, f64, f64, ct.POINTER(P)]
         L.orc_bilu_factor.restype = i32
         L.orc_factor_sizes.argtypes = [P, P]
@@ -85,6 +87,18 @@ def partition_ilu1t(A, tau: float, max_block: int) -> np.ndarray:
     nb = lib().orc_partition_ilu1t(A.n, _p(rp), _p(ci), _p(va), tau, max_block, _p(out))
     if nb < 0:
         raise ValueError("orc_partition_ilu1t failed")
+    return out[: nb + 1].copy()
+
+
+def partition_ilu1t_groups(A, tau: float, max_block: int, gstart) -> np.ndarray:
+    """Sec. 3.4 growth rule with whole groups of columns (e.g. cosine blocks) as the unit."""
+    rp, ci, va = _csr_args(A)
+    gs = np.ascontiguousarray(gstart, dtype=np.int32)
+    out = np.zeros(A.n + 1, dtype=np.int32)
+    nb = lib().orc_partition_ilu1t_groups(A.n, _p(rp), _p(ci), _p(va), tau, max_block, len(gs) - 1, _p(gs),
+                                          _p(out))
+    if nb < 0:
+        raise ValueError("orc_partition_ilu1t_groups failed")
     return out[: nb + 1].copy()
 
 

@@ -153,52 +153,103 @@ static void ilu1t_sets(int64_t k, const int64_t *rowptr, const int32_t *colind, 
     }
 }
 
-int32_t orc_partition_ilu1t(int64_t n, const int64_t *rowptr, const int32_t *colind,
-                            const double *val, double tau, int32_t max_block, int32_t *bstart) {
-    if (n < 0 || max_block < 1 || tau < 0) return ORC_ERR_ARG;
+/*
+ * The union of the sets of the columns of one group [g0, g1) (deduplicated with the stamp
+ * value gsv) and its scalar count: the sum over its columns of |I~_k| + |J~_k| + 1.
+ */
+static int64_t ilu1t_group_sets(int64_t g0, int64_t g1, const int64_t *rowptr, const int32_t *colind,
+                                const double *val, const csc_t *c, double tau, int32_t *stamp,
+                                int32_t *colstamp, int32_t *inI, int32_t *inJ, int32_t gsv,
+                                vec_i32 *I, vec_i32 *J, vec_i32 *GI, vec_i32 *GJ) {
+    int64_t scal = 0;
+    GI->n = 0;
+    GJ->n = 0;
+    for (int64_t k = g0; k < g1; ++k) {
+        ilu1t_sets(k, rowptr, colind, val, c, tau, stamp, ++*colstamp, I, J);
+        scal += I->n + J->n + 1;
+        for (int64_t t = 0; t < I->n; ++t)
+            if (inI[I->a[t]] != gsv) { inI[I->a[t]] = gsv; vi_push(GI, I->a[t]); }
+        for (int64_t t = 0; t < J->n; ++t)
+            if (inJ[J->a[t]] != gsv) { inJ[J->a[t]] = gsv; vi_push(GJ, J->a[t]); }
+    }
+    return scal;
+}
+
+/*
+ * Sec. 3.4 growth rule over whole groups of columns (a group is never split): a block
+ * [s, s+l) with r rows at or after its end in L and s' columns at or after its end in U
+ * stores f = (r + s' + l) l entries; its scalar count is the sum over its columns of
+ * |I~_k| + |J~_k| + 1.  The next group [e, e+g) joins while f_{l+g} <= (4/3) s_{l+g} or
+ * f_{l+g} <= s_{l+g} + 4 (l+g), and l+g <= max_block.  With groups of one column this is the
+ * column-by-column rule of orc_partition_ilu1t.
+ */
+int32_t orc_partition_ilu1t_groups(int64_t n, const int64_t *rowptr, const int32_t *colind,
+                                   const double *val, double tau, int32_t max_block, int32_t ngroups,
+                                   const int32_t *gstart, int32_t *bstart) {
+    if (n < 0 || max_block < 1 || tau < 0 || ngroups < 0) return ORC_ERR_ARG;
+    if (gstart[0] != 0 || gstart[ngroups] != n || (n > 0 && ngroups == 0)) return ORC_ERR_ARG;
+    for (int32_t g = 0; g < ngroups; ++g)
+        if (gstart[g + 1] - gstart[g] < 1 || gstart[g + 1] - gstart[g] > max_block) return ORC_ERR_ARG;
     csc_t c = csr_to_csc(n, rowptr, colind, val);
-    /* set-building stamps (per column) and block-membership stamps (per block) */
     int32_t *stamp = xcalloc((size_t)n + 1, sizeof(int32_t));
     int32_t *inR = xcalloc((size_t)n + 1, sizeof(int32_t));
     int32_t *inC = xcalloc((size_t)n + 1, sizeof(int32_t));
-    vec_i32 I = {0}, J = {0}, R = {0}, C = {0};
-    int32_t nb = 0;
-    int32_t colstamp = 0;
-    int64_t k = 0;
-    while (k < n) {
-        int64_t start = k;
+    int32_t *inI = xcalloc((size_t)n + 1, sizeof(int32_t));
+    int32_t *inJ = xcalloc((size_t)n + 1, sizeof(int32_t));
+    vec_i32 I = {0}, J = {0}, GI = {0}, GJ = {0}, R = {0}, C = {0};
+    int32_t nb = 0, colstamp = 0, gsv = 0;
+    int32_t g = 0;
+    while (g < ngroups) {
+        int64_t start = gstart[g];
         int32_t blk = nb + 1; /* membership stamp of this block */
-        ilu1t_sets(start, rowptr, colind, val, &c, tau, stamp, ++colstamp, &I, &J);
+        int64_t scal = ilu1t_group_sets(start, gstart[g + 1], rowptr, colind, val, &c, tau, stamp, &colstamp,
+                                        inI, inJ, ++gsv, &I, &J, &GI, &GJ);
         R.n = 0; C.n = 0;
-        for (int64_t t = 0; t < I.n; ++t) { inR[I.a[t]] = blk; vi_push(&R, I.a[t]); }
-        for (int64_t t = 0; t < J.n; ++t) { inC[J.a[t]] = blk; vi_push(&C, J.a[t]); }
-        int64_t scal = I.n + J.n + 1; /* scalar entries s_l */
-        int64_t l = 1;
-        while (l < max_block && start + l < n) {
-            int64_t cand = start + l;
-            ilu1t_sets(cand, rowptr, colind, val, &c, tau, stamp, ++colstamp, &I, &J);
+        for (int64_t t = 0; t < GI.n; ++t) { inR[GI.a[t]] = blk; vi_push(&R, GI.a[t]); }
+        for (int64_t t = 0; t < GJ.n; ++t) { inC[GJ.a[t]] = blk; vi_push(&C, GJ.a[t]); }
+        int64_t l = gstart[g + 1] - start;
+        ++g;
+        while (g < ngroups) {
+            int64_t gs = gstart[g + 1] - gstart[g];
+            if (l + gs > max_block) break;
+            int64_t end = gstart[g + 1];
+            int64_t gscal = ilu1t_group_sets(gstart[g], end, rowptr, colind, val, &c, tau, stamp, &colstamp,
+                                             inI, inJ, ++gsv, &I, &J, &GI, &GJ);
             int64_t r2 = 0, s2 = 0;
-            for (int64_t t = 0; t < R.n; ++t) r2 += (R.a[t] > cand);
-            for (int64_t t = 0; t < I.n; ++t) r2 += (inR[I.a[t]] != blk); /* all > cand */
-            for (int64_t t = 0; t < C.n; ++t) s2 += (C.a[t] > cand);
-            for (int64_t t = 0; t < J.n; ++t) s2 += (inC[J.a[t]] != blk);
-            int64_t f2 = (r2 + s2 + l + 1) * (l + 1);
-            int64_t scal2 = scal + I.n + J.n + 1;
-            int accept = (3 * f2 <= 4 * scal2) || (f2 <= scal2 + 4 * (l + 1));
+            for (int64_t t = 0; t < R.n; ++t) r2 += (R.a[t] >= end);
+            for (int64_t t = 0; t < GI.n; ++t) r2 += (inR[GI.a[t]] != blk && GI.a[t] >= end);
+            for (int64_t t = 0; t < C.n; ++t) s2 += (C.a[t] >= end);
+            for (int64_t t = 0; t < GJ.n; ++t) s2 += (inC[GJ.a[t]] != blk && GJ.a[t] >= end);
+            int64_t l2 = l + gs;
+            int64_t f2 = (r2 + s2 + l2) * l2;
+            int64_t scal2 = scal + gscal;
+            int accept = (3 * f2 <= 4 * scal2) || (f2 <= scal2 + 4 * l2);
             if (!accept) break;
-            for (int64_t t = 0; t < I.n; ++t)
-                if (inR[I.a[t]] != blk) { inR[I.a[t]] = blk; vi_push(&R, I.a[t]); }
-            for (int64_t t = 0; t < J.n; ++t)
-                if (inC[J.a[t]] != blk) { inC[J.a[t]] = blk; vi_push(&C, J.a[t]); }
+            for (int64_t t = 0; t < GI.n; ++t)
+                if (inR[GI.a[t]] != blk) { inR[GI.a[t]] = blk; vi_push(&R, GI.a[t]); }
+            for (int64_t t = 0; t < GJ.n; ++t)
+                if (inC[GJ.a[t]] != blk) { inC[GJ.a[t]] = blk; vi_push(&C, GJ.a[t]); }
             scal = scal2;
-            ++l;
+            l = l2;
+            ++g;
         }
         bstart[nb++] = (int32_t)start;
-        k = start + l;
     }
     bstart[nb] = (int32_t)n;
-    free(stamp); free(inR); free(inC); free(I.a); free(J.a); free(R.a); free(C.a);
+    free(stamp); free(inR); free(inC); free(inI); free(inJ);
+    free(I.a); free(J.a); free(GI.a); free(GJ.a); free(R.a); free(C.a);
     csc_free(&c);
+    return nb;
+}
+
+/* Column-by-column growth: every column its own group. */
+int32_t orc_partition_ilu1t(int64_t n, const int64_t *rowptr, const int32_t *colind,
+                            const double *val, double tau, int32_t max_block, int32_t *bstart) {
+    if (n < 0 || max_block < 1 || tau < 0) return ORC_ERR_ARG;
+    int32_t *unit = xmalloc(((size_t)n + 1) * sizeof(int32_t));
+    for (int64_t k = 0; k <= n; ++k) unit[k] = (int32_t)k;
+    int32_t nb = orc_partition_ilu1t_groups(n, rowptr, colind, val, tau, max_block, (int32_t)n, unit, bstart);
+    free(unit);
     return nb;
 }
 

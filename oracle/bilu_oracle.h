@@ -79,6 +79,14 @@ int32_t orc_partition_ilu1t(int64_t n, const int64_t *rowptr, const int32_t *col
                             const double *val, double tau, int32_t max_block,
                             int32_t *bstart);
 
+/* The same growth rule over whole groups of columns gstart[ngroups+1] (0 = gstart[0] < ...
+ * < gstart[ngroups] = n, groups of 1..max_block columns, for instance cosine blocks): a group
+ * joins or starts a block as a whole.  bstart holds n+1 entries; returns the number of
+ * blocks (< 0 on error). */
+int32_t orc_partition_ilu1t_groups(int64_t n, const int64_t *rowptr, const int32_t *colind,
+                                   const double *val, double tau, int32_t max_block, int32_t ngroups,
+                                   const int32_t *gstart, int32_t *bstart);
+
 /* Numeric Crout BILU.  A is CSR with sorted column indices.  On success (status >= 0)
  * *out receives the factor, to be freed with orc_factor_free. */
 int32_t orc_bilu_factor(int64_t n, const int64_t *rowptr, const int32_t *colind,

@@ -30,7 +30,8 @@ EXPORTED = ["bilu_params_default", "bilu_create", "bilu_analyze", "bilu_factor",
             "gmres_solve", "bilu_stats", "bilu_get_partition", "bilu_export", "bilu_last_error",
             "bilu_debug_set", "bilu_apply_noalloc", "bilu_factor_batch", "gmres_solve_batch",
             "bilu_record_samples", "bilu_get_samples", "bilu_mlp_train", "bilu_mlp_forward", "bilu_mlp_grad",
-            "bilu_set_skip_model", "bilu_cosine_blocking", "bilu_permute_csr", "bilu_analyze_partition",
+            "bilu_set_skip_model", "bilu_cosine_blocking", "bilu_partition_ilu1t", "bilu_permute_csr",
+            "bilu_analyze_partition",
             "bilu_destroy"]
 
 # learned skip classifier (layout of the model array: mean[F] std[F] W1[64][F] b1[64] W2[64][64]
@@ -108,6 +109,7 @@ def lib():
             "bilu_set_skip_model": ([P, P, f64], i32),
             "bilu_cosine_blocking": ([i64, P, P, f64, i32, P, P, ct.POINTER(i32)], i32),
             "bilu_permute_csr": ([i64, P, P, P, P, P, P, P], i32),
+            "bilu_partition_ilu1t": ([i64, P, P, P, f64, i32, i32, P, P, ct.POINTER(i32)], i32),
             "bilu_analyze_partition": ([P, i64, P, P, P, i32, ct.POINTER(bilu_params), i32, P], i32),
             "bilu_destroy": ([P], None),
         }
@@ -268,6 +270,31 @@ def bilu_cosine_blocking(n: int, rowptr, colind, tau: float = 0.8, max_block: in
     st = lib().bilu_cosine_blocking(n, _ptr(rp), _ptr(ci), tau, max_block, _ptr(perm), _ptr(bs), ct.byref(nb))
     _check(None, st)
     return perm[:n].copy(), bs[:nb.value + 1].copy()
+
+
+def bilu_partition_ilu1t(n: int, rowptr, colind, val, tau: float = 1e-2, max_block: int = BILU_MAX_BLOCK,
+                         groups=None):
+    """Sec. 3.4 partition on the host, column by column or over the given group starts."""
+    import numpy as np
+    if n < 0:
+        raise ValueError("n < 0")
+    rp = np.ascontiguousarray(rowptr, dtype=np.int64)
+    if rp.size < n + 1:
+        raise ValueError("rowptr needs n + 1 entries")
+    nnz = int(rp[n]) if n > 0 else 0
+    ci = np.ascontiguousarray(colind, dtype=np.int32)
+    va = np.ascontiguousarray(val, dtype=np.float64)
+    if ci.size < nnz or va.size < nnz:
+        raise ValueError("colind / val shorter than rowptr[n]")
+    gs = None if groups is None else np.ascontiguousarray(groups, dtype=np.int32)
+    if gs is not None and gs.size < 1:
+        raise ValueError("groups needs at least one entry")
+    bs = np.zeros(n + 1, np.int32)
+    nb = ct.c_int32(0)
+    st = lib().bilu_partition_ilu1t(n, _ptr(rp), _ptr(ci), _ptr(va), tau, max_block,
+                                    -1 if gs is None else len(gs) - 1, _ptr(gs), _ptr(bs), ct.byref(nb))
+    _check(None, st)
+    return bs[:nb.value + 1].copy()
 
 
 def bilu_permute_csr(n: int, rowptr, colind, val, perm):

@@ -93,13 +93,15 @@ std::vector<int32_t> sorted_union(const std::vector<int32_t> &a, const std::vect
     return out;
 }
 
-// Sec. 3.4 growth rule: a block [k, k+l) with r rows below and s columns to the right
-// stores f = (r + s + l) l entries; the scalar count grows by |I~| + |J~| + 1 for every
-// added column.  Column k+l joins while f_{l+1} <= 4/3 s_{l+1} or f_{l+1} <= s_{l+1} + 4(l+1)
-// and the size stays <= max_block.  Indices inside the block are not counted in r, s.
+// Sec. 3.4 growth rule over whole groups of columns (groups of one column: the rule column by
+// column): a block [k, k+l) with r rows at or after its end in L and s columns at or after its
+// end in U stores f = (r + s + l) l entries; its scalar count is the sum over its columns of
+// |I~| + |J~| + 1.  The next group [e, e+g) joins while f_{l+g} <= 4/3 s_{l+g} or
+// f_{l+g} <= s_{l+g} + 4(l+g), and l+g <= max_block.  Indices inside the block are not counted
+// in r, s.  `groups` holds the group starts and n at the end.
 std::vector<int32_t> partition_ilu1t(const HostCSR &A, const std::vector<int32_t> &colptr,
                                      const std::vector<int32_t> &rowind, const std::vector<double> &cval,
-                                     double tau, int max_block) {
+                                     double tau, int max_block, const std::vector<int32_t> &groups) {
     const int64_t n = A.n;
     std::vector<double> diag(n);
     for (int64_t i = 0; i < n; ++i) diag[i] = diag_of(A.rowptr.data(), A.colind.data(), A.val.data(), i);
@@ -108,30 +110,53 @@ std::vector<int32_t> partition_ilu1t(const HostCSR &A, const std::vector<int32_t
     auto rowpat = [&](int64_t k) {
         return ilu1t_pattern(k, A.rowptr.data(), A.colind.data(), A.val.data(), diag, tau);
     };
-    std::vector<int32_t> bstart;
-    int64_t k = 0;
-    while (k < n) {
-        const int64_t start = k;
-        std::vector<int32_t> R = colpat(start), C = rowpat(start);
-        int64_t scalar = (int64_t)R.size() + (int64_t)C.size() + 1;
-        int64_t l = 1;
-        while (l < max_block && start + l < n) {
-            const int64_t cand = start + l;
-            std::vector<int32_t> I = colpat(cand), J = rowpat(cand);
-            const int64_t r2 = union_count_above(R, I, cand), s2 = union_count_above(C, J, cand);
-            const int64_t f2 = (r2 + s2 + l + 1) * (l + 1);
-            const int64_t scalar2 = scalar + (int64_t)I.size() + (int64_t)J.size() + 1;
-            if (!(3 * f2 <= 4 * scalar2 || f2 <= scalar2 + 4 * (l + 1))) break;
-            R = sorted_union(R, I);
-            C = sorted_union(C, J);
+    // union of the patterns of the columns [g0, g1) and their scalar count
+    auto group_sets = [&](int64_t g0, int64_t g1, std::vector<int32_t> &GI, std::vector<int32_t> &GJ) {
+        int64_t scal = 0;
+        GI.clear();
+        GJ.clear();
+        for (int64_t k = g0; k < g1; ++k) {
+            const std::vector<int32_t> I = colpat(k), J = rowpat(k);
+            scal += (int64_t)I.size() + (int64_t)J.size() + 1;
+            GI = sorted_union(GI, I);
+            GJ = sorted_union(GJ, J);
+        }
+        return scal;
+    };
+    std::vector<int32_t> bstart, R, C, GI, GJ;
+    const size_t ng = groups.size() - 1;
+    size_t g = 0;
+    while (g < ng) {
+        const int64_t start = groups[g];
+        int64_t scalar = group_sets(start, groups[g + 1], R, C);
+        int64_t l = groups[g + 1] - start;
+        ++g;
+        while (g < ng) {
+            const int64_t gs = groups[g + 1] - groups[g];
+            if (l + gs > max_block) break;
+            const int64_t end = groups[g + 1];
+            const int64_t gscal = group_sets(groups[g], end, GI, GJ);
+            const int64_t r2 = union_count_above(R, GI, end - 1), s2 = union_count_above(C, GJ, end - 1);
+            const int64_t l2 = l + gs;
+            const int64_t f2 = (r2 + s2 + l2) * l2;
+            const int64_t scalar2 = scalar + gscal;
+            if (!(3 * f2 <= 4 * scalar2 || f2 <= scalar2 + 4 * l2)) break;
+            R = sorted_union(R, GI);
+            C = sorted_union(C, GJ);
             scalar = scalar2;
-            ++l;
+            l = l2;
+            ++g;
         }
         bstart.push_back((int32_t)start);
-        k = start + l;
     }
     bstart.push_back((int32_t)n);
     return bstart;
+}
+
+std::vector<int32_t> unit_groups(int64_t n) {
+    std::vector<int32_t> g(n + 1);
+    for (int64_t k = 0; k <= n; ++k) g[k] = (int32_t)k;
+    return g;
 }
 
 // Pattern checks shared by the host-only helpers: rowptr monotone from 0, column indices in
@@ -248,6 +273,47 @@ bilu_status cosine_blocking_host(int64_t n, const int64_t *rowptr, const int32_t
     return BILU_OK;
 }
 
+// The Sec. 3.4 partition on the host: column by column (gstart NULL) or over the given groups.
+bilu_status partition_ilu1t_host(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val,
+                                 double tau, int32_t max_block, int32_t ngroups, const int32_t *gstart,
+                                 int32_t *bstart, int32_t *nblocks, std::string *err) {
+    auto fail = [&](const char *m) { if (err) *err = m; return BILU_ERR_ARG; };
+    const std::string bad = check_pattern(n, rowptr, colind);
+    if (!bad.empty()) return fail(bad.c_str());
+    if (n > 0 && !val) return fail("null CSR array");
+    if (!(tau >= 0.0) || !std::isfinite(tau)) return fail("tau must be finite and >= 0");
+    if (max_block < 1 || max_block > BILU_MAX_BLOCK) return fail("max_block must be in 1..64");
+    if (!bstart || !nblocks) return fail("null output array");
+    HostCSR A;
+    A.n = n;
+    A.rowptr.assign(rowptr, rowptr + n + 1);
+    if (n == 0) A.rowptr.assign(1, 0);
+    const int64_t nnz = A.rowptr[n];
+    A.colind.assign(colind, colind + nnz);
+    A.val.assign(val, val + nnz);
+    for (double v : A.val)
+        if (!std::isfinite(v)) return fail("non-finite matrix value");
+    std::vector<int32_t> groups;
+    if (gstart) {
+        if (ngroups < 0 || gstart[0] != 0 || gstart[ngroups] != n || (n > 0 && ngroups == 0))
+            return fail("groups must run from 0 to n");
+        for (int32_t g = 0; g < ngroups; ++g)
+            if (gstart[g + 1] - gstart[g] < 1 || gstart[g + 1] - gstart[g] > max_block)
+                return fail("group size not in 1..max_block");
+        groups.assign(gstart, gstart + ngroups + 1);
+    } else {
+        groups = unit_groups(n);
+    }
+    std::vector<int32_t> colptr, rowind;
+    std::vector<double> cval;
+    build_csc(A, colptr, rowind, cval);
+    const std::vector<int32_t> bs = n > 0 ? partition_ilu1t(A, colptr, rowind, cval, tau, max_block, groups)
+                                          : std::vector<int32_t>(1, 0);
+    std::copy(bs.begin(), bs.end(), bstart);
+    *nblocks = (int32_t)bs.size() - 1;
+    return BILU_OK;
+}
+
 // A~ = Q^T A Q: row k of A~ is row perm[k] of A with every column j renamed iperm[j] and the
 // row re-sorted.
 bilu_status permute_csr_host(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val,
@@ -360,13 +426,17 @@ bilu_status analyze_run(bilu_ctx *c, int64_t n, const int64_t *rowptr, const int
     build_csc(A, colptr, rowind, cval);
 
     std::vector<int32_t> bstart;
-    if (given) {
+    if (given && p->blocking == BILU_BLOCKING_ILU1T && n > 0) {
+        // the given blocks are groups that the Sec. 3.4 growth rule merges
+        const std::vector<int32_t> groups(given_bstart, given_bstart + given_nb + 1);
+        bstart = partition_ilu1t(A, colptr, rowind, cval, p->tau_analyze, p->max_block, groups);
+    } else if (given) {
         bstart.assign(given_bstart, given_bstart + given_nb + 1);
     } else if (p->blocking == BILU_BLOCKING_FIXED) {
         for (int64_t s = 0; s < n; s += p->fixed_block) bstart.push_back((int32_t)s);
         bstart.push_back((int32_t)n);
     } else {
-        bstart = partition_ilu1t(A, colptr, rowind, cval, p->tau_analyze, p->max_block);
+        bstart = partition_ilu1t(A, colptr, rowind, cval, p->tau_analyze, p->max_block, unit_groups(n));
     }
     if (n == 0) bstart.assign(1, 0);
 

@@ -106,6 +106,14 @@ bilu_status bilu_cosine_blocking(int64_t n, const int64_t *rowptr, const int32_t
     return cosine_blocking_host(n, rowptr, colind, tau, max_block, perm, bstart, nblocks, &g_host_err);
 }
 
+bilu_status bilu_partition_ilu1t(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val,
+                                 double tau, int32_t max_block, int32_t ngroups, const int32_t *gstart,
+                                 int32_t *bstart, int32_t *nblocks) {
+    g_host_err.clear();
+    return partition_ilu1t_host(n, rowptr, colind, val, tau, max_block, ngroups, gstart, bstart, nblocks,
+                                &g_host_err);
+}
+
 bilu_status bilu_permute_csr(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val,
                              const int32_t *perm, int64_t *out_rowptr, int32_t *out_colind, double *out_val) {
     g_host_err.clear();

@@ -207,6 +207,28 @@ def test_cosine_blocking_end_to_end(ctx):
     assert np.abs(x - ro.x).max() <= 1e-6 * np.abs(ro.x).max()
 
 
+def test_cosine_blocks_merged_by_ilu1t_end_to_end(ctx):
+    """Sec. 3.2 then Sec. 3.4: the cosine blocks of a scrambled elasticity matrix, merged whole
+    by the ILU(1,tau) growth rule inside bilu_analyze_partition (BILU_BLOCKING_ILU1T); the
+    partition equals the oracle's, and factor and GMRES(30) match the oracle on it."""
+    w = W.elasticity3d(side=5, seed=2, block=63)
+    scramble = np.random.default_rng(11).permutation(w.A.n).astype(np.int32)
+    A1 = W.CSR(w.A.n, *B.bilu_permute_csr(w.A.n, w.A.rowptr, w.A.colind, w.A.val, scramble))
+    perm, groups = B.bilu_cosine_blocking(A1.n, A1.rowptr, A1.colind, 0.8, 64)
+    A2 = W.CSR(A1.n, *B.bilu_permute_csr(A1.n, A1.rowptr, A1.colind, A1.val, perm))
+    p = B.bilu_params_default(blocking=B.BILU_BLOCKING_ILU1T, max_block=63, tau_analyze=1e-2)
+    g = gpu_factor(ctx, A2, w.droptol, p, bstart=groups)
+    want = O.partition_ilu1t_groups(A2, 1e-2, 63, groups)
+    assert np.array_equal(g.bstart, want) and len(want) < len(groups)
+    o = _oracle(A2, want, w.droptol)
+    compare_factors(o, g, A=A2, tau=w.droptol)
+    b = W.rhs_ones(A2)
+    ro = O.gmres(A2, o, b, tol=1e-8, restart=30)
+    x = np.zeros(A2.n)
+    info = B.gmres_solve(ctx, b, x, 1e-8, 30, 10000)
+    assert info.status == B.BILU_OK and info.iters == ro.iters, (info.iters, ro.iters)
+
+
 def test_analyze_partition_rejects_invalid_partitions(ctx):
     A = W.convdiff_upwind((4, 4, 4), seed=1)
     for bs in ([0, 10, 10, 64], [0, 70], [1, 64], [0, 32]):

@@ -74,16 +74,18 @@ MUTANTS = [
      "if (fabs(g[j + 1]) <= tol || hn == 0.0) break;", 1),
     # ILU(1,tau) blocking (Sec. 3.4)
     ("growth rule loses its second clause", C,
-     "int accept = (3 * f2 <= 4 * scal2) || (f2 <= scal2 + 4 * (l + 1));", "int accept = (3 * f2 <= 4 * scal2);", 1),
-    ("scalar count without the diagonal", C, "int64_t scal2 = scal + I.n + J.n + 1;",
-     "int64_t scal2 = scal + I.n + J.n;", 1),
+     "int accept = (3 * f2 <= 4 * scal2) || (f2 <= scal2 + 4 * l2);", "int accept = (3 * f2 <= 4 * scal2);", 1),
+    ("scalar count without the diagonal", C, "scal += I->n + J->n + 1;", "scal += I->n + J->n;", 1),
+    ("group joins beyond max_block", C, "if (l + gs > max_block) break;", "if (l + gs > max_block + 1) break;", 1),
     ("fill rows ignored", C, "if (fabs(c->val[f] * ajk) >= tau * fabs(ajj * akk) && stamp[i] != stampval) {",
      "if (0 && stamp[i] != stampval) {", 1),
     ("strict threshold on original entries", C,
      "if (i > k && fabs(c->val[e]) >= tau * fabs(akk) && stamp[i] != stampval) {",
      "if (i > k && fabs(c->val[e]) > tau * fabs(akk) && stamp[i] != stampval) {", 1),
-    ("new rows all counted", C, "r2 += (inR[I.a[t]] != blk); /* all > cand */", "r2 += 1;", 1),
-    ("rows inside the block counted", C, "r2 += (R.a[t] > cand);", "r2 += (R.a[t] >= cand);", 1),
+    ("new rows all counted", C, "r2 += (inR[GI.a[t]] != blk && GI.a[t] >= end);", "r2 += 1;", 1),
+    ("rows inside the block counted", C, "r2 += (R.a[t] >= end);", "r2 += (R.a[t] >= end - 1);", 1),
+    ("rows of the candidate group counted", C, "r2 += (inR[GI.a[t]] != blk && GI.a[t] >= end);",
+     "r2 += (inR[GI.a[t]] != blk);", 1),
     # single block step checker
     ("checker: L-side update sign", BCK, "t[uc[qs:qe] - s0] -= upd[a]", "t[uc[qs:qe] - s0] += upd[a]", 1),
     ("checker: U-side update sign", BCK, "t[lr[ps2:pe2] - s0] -= upd[:, a]", "t[lr[ps2:pe2] - s0] += upd[:, a]", 1),

@@ -88,3 +88,55 @@ def test_partition_covers_and_respects_cap_on_stencil():
     assert np.all(np.diff(bs) >= 1) and np.all(np.diff(bs) <= 8)
     fx = O.partition_fixed(A.n, 100)
     assert list(fx[:3]) == [0, 100, 200] and fx[-1] == A.n
+
+
+# ----------------------------------------------------------------- growth over groups of columns
+
+def test_groups_of_one_are_the_column_rule():
+    A = W.convdiff_upwind((8, 8, 8), seed=2)
+    for tau, mb in ((1e-2, 64), (1e-3, 16), (0.0, 7)):
+        assert list(O.partition_ilu1t_groups(A, tau, mb, np.arange(A.n + 1))) == list(O.partition_ilu1t(A, tau, mb))
+
+
+def test_diagonal_groups_of_two_and_three():
+    """Diagonal, groups of 2 (every column adds 1 to the scalar count, r = s' = 0): the block
+    [0, 2) starts with s = 2; adding [2, 4): l = 4, f = 16, s = 4: 48 > 16 but 16 <= 4 + 4*4,
+    accepted; adding [4, 6): l = 6, f = 36, s = 6: 36 > 6 + 24, rejected.  Blocks of 4.
+    Groups of 3: a second group gives l = 6, f = 36 > 6 + 24: blocks of 3 (the column rule
+    makes blocks of 5)."""
+    A = W.from_dense(np.eye(12) * 3.0)
+    assert list(O.partition_ilu1t_groups(A, 1e-2, 64, np.arange(0, 13, 2))) == [0, 4, 8, 12]
+    assert list(O.partition_ilu1t_groups(A, 1e-2, 64, np.arange(0, 13, 3))) == [0, 3, 6, 9, 12]
+    # max_block caps whole groups: groups of 2 under max_block 3 never merge
+    assert list(O.partition_ilu1t_groups(A, 1e-2, 3, np.arange(0, 13, 2))) == list(range(0, 13, 2))
+
+
+def test_group_counts_exclude_the_candidate_group():
+    """Tridiagonal (diag 4, off -1, tau 0.1), groups of 2.  Column k has I~ = J~ = {k+1}, so a
+    group [e, e+2) inside the matrix contributes the scalar count 2 (1 + 1 + 1) = 6 and one row and one
+    column at or after its end.  First block [0, 2): R = {1, 2}, C = {1, 2}, s = 6.  Adding
+    [2, 4): rows at or after 4: {4} (from column 3), columns {4}: r = s' = 1, l = 4,
+    f = (1 + 1 + 4) 4 = 24, s = 12: 72 > 48, 24 <= 12 + 16, accepted.  Adding [4, 6): r = s' = 1,
+    l = 6, f = 48, s = 18: 144 > 72, 48 > 18 + 24, rejected.  Blocks of 4; the last group
+    [10, 12) adds s = 3 + 1 (column 11 has no neighbour after it) and nothing at or after 12:
+    f = 16 <= 10 + 16, so [8, 12) is one block."""
+    n = 12
+    Ad = 4 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)
+    assert list(O.partition_ilu1t_groups(W.from_dense(Ad), 0.1, 64, np.arange(0, 13, 2))) == [0, 4, 8, 12]
+
+
+def test_rows_inside_the_candidate_group_do_not_count():
+    """Diagonal 4 plus a_43 = -1, tau = 0.1, groups [0, 3) and [3, 5).  Column 3 has
+    I~ = {4}, every other set is empty.  Block [0, 3): s = 3.  Adding [3, 5): the row 4 lies
+    inside the candidate group, so r = s' = 0, l = 5, f = 25, s = 3 + 2 + 1 = 6: 75 > 24 but
+    25 <= 6 + 20, accepted: one block (counting row 4 would give f = 30 > 26)."""
+    d = 4 * np.eye(5)
+    d[4, 3] = -1.0
+    assert list(O.partition_ilu1t_groups(W.from_dense(d), 0.1, 64, [0, 3, 5])) == [0, 5]
+
+
+def test_blocks_are_unions_of_groups():
+    w = W.elasticity3d(side=4, seed=2, block=63)
+    groups = np.arange(0, w.A.n + 1, 3)
+    bs = O.partition_ilu1t_groups(w.A, 1e-2, 64, groups)
+    assert set(bs) <= set(groups) and np.diff(bs).max() <= 63 and bs[-1] == w.A.n
