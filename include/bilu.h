@@ -207,7 +207,8 @@ bilu_status bilu_export(bilu_ctx *ctx, int64_t *Lptr, int32_t *Lrow, double *Lva
 
 /* Human-readable description of the last error on this context ("" if none).  With
  * ctx == NULL: the last error of this host thread's context-free calls
- * (bilu_cosine_blocking, bilu_partition_ilu1t, bilu_permute_csr). */
+ * (bilu_cosine_blocking, bilu_partition_ilu1t, bilu_mwm, bilu_scale_permute_csr,
+ * bilu_permute_csr). */
 const char *bilu_last_error(const bilu_ctx *ctx);
 
 /*
@@ -244,6 +245,34 @@ bilu_status bilu_cosine_blocking(int64_t n, const int64_t *rowptr, const int32_t
 bilu_status bilu_partition_ilu1t(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val,
                                  double tau, int32_t max_block, int32_t ngroups, const int32_t *gstart,
                                  int32_t *bstart, int32_t *nblocks);
+
+/*
+ * Maximum weight matching with scaling (Sec. 3.1), host only: no context or device.  With
+ * costs c_ij = log a_j - log|a_ij| on the stored nonzeros of A (a_j = max_k |a_kj|), finds a
+ * perfect matching sigma (row i -> column sigma[i]) of least total cost, i.e. of largest
+ * product of |a_{i sigma(i)}| (a maximum product transversal), by shortest augmenting paths,
+ * and dual variables u, v (u_i + v_j <= c_ij, equal on the matching).  Outputs (caller-owned
+ * host arrays of n entries): sigma; dl[i] = e^{u_i}; dr[j] = e^{v_j} / a_j.  Then
+ * A^ = D_l A D_r Pi (column sigma[i] moved to position i, see bilu_scale_permute_csr) has
+ * |a^_ij| <= 1 and |a^_ii| = 1.  To solve A x = b: solve A^ y = D_l b, then
+ * x[sigma[l]] = dr[sigma[l]] y[l].
+ * Errors: BILU_ERR_ARG (malformed CSR, non-finite value, null array), BILU_ERR_SINGULAR (no
+ * perfect matching on the nonzeros: A is structurally singular); message in
+ * bilu_last_error(NULL).
+ */
+bilu_status bilu_mwm(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val, int32_t *sigma,
+                     double *dl, double *dr);
+
+/*
+ * B[k][l] = dl[r_k] * A[r_k][c_l] * dr[c_l] on the host, with r_k = rowperm[k] and
+ * c_l = colperm[l] (a NULL permutation is the identity, a NULL scaling is 1): rowperm = NULL,
+ * colperm = sigma and the scalings of bilu_mwm give A^ = D_l A D_r Pi; rowperm = colperm = Q
+ * and no scaling give Q^T A Q.  Output arrays as in bilu_permute_csr (rows sorted).
+ * Errors: BILU_ERR_ARG (malformed CSR, a permutation that is not one, null array).
+ */
+bilu_status bilu_scale_permute_csr(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val,
+                                   const int32_t *rowperm, const int32_t *colperm, const double *dl,
+                                   const double *dr, int64_t *out_rowptr, int32_t *out_colind, double *out_val);
 
 /*
  * Symmetric permutation A~ = Q^T A Q of a CSR matrix on the host (the reordering step of

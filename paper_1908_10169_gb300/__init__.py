@@ -30,7 +30,8 @@ EXPORTED = ["bilu_params_default", "bilu_create", "bilu_analyze", "bilu_factor",
             "gmres_solve", "bilu_stats", "bilu_get_partition", "bilu_export", "bilu_last_error",
             "bilu_debug_set", "bilu_apply_noalloc", "bilu_factor_batch", "gmres_solve_batch",
             "bilu_record_samples", "bilu_get_samples", "bilu_mlp_train", "bilu_mlp_forward", "bilu_mlp_grad",
-            "bilu_set_skip_model", "bilu_cosine_blocking", "bilu_partition_ilu1t", "bilu_permute_csr",
+            "bilu_set_skip_model", "bilu_cosine_blocking", "bilu_partition_ilu1t", "bilu_mwm", "bilu_scale_permute_csr",
+            "bilu_permute_csr",
             "bilu_analyze_partition",
             "bilu_destroy"]
 
@@ -110,6 +111,8 @@ def lib():
             "bilu_cosine_blocking": ([i64, P, P, f64, i32, P, P, ct.POINTER(i32)], i32),
             "bilu_permute_csr": ([i64, P, P, P, P, P, P, P], i32),
             "bilu_partition_ilu1t": ([i64, P, P, P, f64, i32, i32, P, P, ct.POINTER(i32)], i32),
+            "bilu_mwm": ([i64, P, P, P, P, P, P], i32),
+            "bilu_scale_permute_csr": ([i64, P, P, P, P, P, P, P, P, P, P], i32),
             "bilu_analyze_partition": ([P, i64, P, P, P, i32, ct.POINTER(bilu_params), i32, P], i32),
             "bilu_destroy": ([P], None),
         }
@@ -295,6 +298,55 @@ def bilu_partition_ilu1t(n: int, rowptr, colind, val, tau: float = 1e-2, max_blo
                                     -1 if gs is None else len(gs) - 1, _ptr(gs), _ptr(bs), ct.byref(nb))
     _check(None, st)
     return bs[:nb.value + 1].copy()
+
+
+def _host_csr(n: int, rowptr, colind, val):
+    """Host CSR arrays of the C types, checked against n and rowptr[n] (context-free calls)."""
+    import numpy as np
+    if n < 0:
+        raise ValueError("n < 0")
+    rp = np.ascontiguousarray(rowptr, dtype=np.int64)
+    if rp.size < n + 1:
+        raise ValueError("rowptr needs n + 1 entries")
+    nnz = int(rp[n]) if n > 0 else 0
+    ci = np.ascontiguousarray(colind, dtype=np.int32)
+    va = np.ascontiguousarray(val, dtype=np.float64)
+    if ci.size < nnz or va.size < nnz:
+        raise ValueError("colind / val shorter than rowptr[n]")
+    return rp, ci, va, nnz
+
+
+def bilu_mwm(n: int, rowptr, colind, val):
+    """Sec. 3.1 maximum weight matching with scaling on the host: (sigma, dl, dr)."""
+    import numpy as np
+    rp, ci, va, _ = _host_csr(n, rowptr, colind, val)
+    sigma = np.zeros(max(n, 1), np.int32)
+    dl = np.zeros(max(n, 1))
+    dr = np.zeros(max(n, 1))
+    _check(None, lib().bilu_mwm(n, _ptr(rp), _ptr(ci), _ptr(va), _ptr(sigma), _ptr(dl), _ptr(dr)))
+    return sigma[:n].copy(), dl[:n].copy(), dr[:n].copy()
+
+
+def bilu_scale_permute_csr(n: int, rowptr, colind, val, rowperm=None, colperm=None, dl=None, dr=None):
+    """B[k, l] = dl[r_k] A[r_k, c_l] dr[c_l] on the host: returns (rowptr, colind, val)."""
+    import numpy as np
+    rp, ci, va, nnz = _host_csr(n, rowptr, colind, val)
+
+    def opt(a, dt):
+        if a is None:
+            return None
+        a = np.ascontiguousarray(a, dtype=dt)
+        if a.size < n:
+            raise ValueError("permutations and scalings need n entries")
+        return a
+    rpm, cpm = opt(rowperm, np.int32), opt(colperm, np.int32)
+    sl, sr = opt(dl, np.float64), opt(dr, np.float64)
+    orp = np.zeros(n + 1, np.int64)
+    oci = np.zeros(max(nnz, 1), np.int32)
+    ova = np.zeros(max(nnz, 1), np.float64)
+    _check(None, lib().bilu_scale_permute_csr(n, _ptr(rp), _ptr(ci), _ptr(va), _ptr(rpm), _ptr(cpm), _ptr(sl),
+                                              _ptr(sr), _ptr(orp), _ptr(oci), _ptr(ova)))
+    return orp, oci[:nnz].copy(), ova[:nnz].copy()
 
 
 def bilu_permute_csr(n: int, rowptr, colind, val, perm):

@@ -7,6 +7,8 @@
 #include <cmath>
 #include <cstring>
 #include <numeric>
+#include <queue>
+#include <limits>
 #include <string>
 #include <utility>
 
@@ -311,6 +313,125 @@ bilu_status partition_ilu1t_host(int64_t n, const int64_t *rowptr, const int32_t
                                           : std::vector<int32_t>(1, 0);
     std::copy(bs.begin(), bs.end(), bstart);
     *nblocks = (int32_t)bs.size() - 1;
+    return BILU_OK;
+}
+
+// Sec. 3.1: maximum product transversal and scaling.  Costs c_ij = log a_j - log|a_ij| on the
+// stored nonzeros (a_j the largest |a_kj| of column j); a minimum-cost perfect matching sigma by
+// one shortest augmenting path per row (Dijkstra on the reduced costs c_ij - u_i - v_j >= 0,
+// columns taken by distance, then index); the duals give d_l = e^u, d_r = e^v / a_j, so that
+// D_l A D_r has |entries| <= 1 and |entry| = 1 on the matching.
+bilu_status mwm_host(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val,
+                     int32_t *sigma, double *dl, double *dr, std::string *err) {
+    auto fail = [&](bilu_status st, const char *m) { if (err) *err = m; return st; };
+    const std::string bad = check_pattern(n, rowptr, colind);
+    if (!bad.empty()) return fail(BILU_ERR_ARG, bad.c_str());
+    if (n > 0 && (!val || !sigma || !dl || !dr)) return fail(BILU_ERR_ARG, "null array");
+    const int64_t nnz = n > 0 ? rowptr[n] : 0;
+    std::vector<double> amax(n, 0.0), c(nnz, 0.0);
+    for (int64_t e = 0; e < nnz; ++e) {
+        if (!std::isfinite(val[e])) return fail(BILU_ERR_ARG, "non-finite matrix value");
+        amax[colind[e]] = std::max(amax[colind[e]], std::fabs(val[e]));
+    }
+    for (int64_t e = 0; e < nnz; ++e)
+        if (val[e] != 0.0) c[e] = std::log(amax[colind[e]]) - std::log(std::fabs(val[e]));
+    const double inf = std::numeric_limits<double>::infinity();
+    std::vector<double> u(n, 0.0), v(n, 0.0), dist(n, inf);
+    std::vector<int32_t> row_of(n, -1), col_of(n, -1), prev(n, -1), touched, finished;
+    std::vector<char> done(n, 0);
+    using Item = std::pair<double, int32_t>;
+    std::priority_queue<Item, std::vector<Item>, std::greater<Item>> heap;
+    for (int64_t s = 0; s < n; ++s) {
+        auto relax = [&](int32_t i, double base) {
+            for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+                const int32_t k = colind[e];
+                if (val[e] == 0.0 || done[k]) continue;
+                const double d = base + c[e] - u[i] - v[k];
+                if (d < dist[k]) {
+                    if (dist[k] == inf) touched.push_back(k);
+                    dist[k] = d;
+                    prev[k] = i;
+                    heap.push({d, k});
+                }
+            }
+        };
+        relax((int32_t)s, 0.0);
+        int32_t free = -1;
+        while (!heap.empty()) {
+            const auto [d, j] = heap.top();
+            heap.pop();
+            if (done[j] || d > dist[j]) continue;
+            done[j] = 1;
+            finished.push_back(j);
+            if (row_of[j] < 0) { free = j; break; }
+            relax(row_of[j], dist[j]);
+        }
+        if (free < 0) return fail(BILU_ERR_SINGULAR, "structurally singular: no perfect matching on the nonzeros");
+        const double D = dist[free];
+        u[s] += D;
+        for (int32_t j : finished)
+            if (j != free) {
+                u[row_of[j]] += D - dist[j];
+                v[j] -= D - dist[j];
+            }
+        for (int32_t j = free;;) {  // augment along the path
+            const int32_t i = prev[j], nxt = col_of[i];
+            row_of[j] = i;
+            col_of[i] = j;
+            if (i == s) break;
+            j = nxt;
+        }
+        for (int32_t k : touched) { dist[k] = inf; done[k] = 0; prev[k] = -1; }
+        touched.clear();
+        finished.clear();
+        heap = decltype(heap)();
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        sigma[i] = col_of[i];
+        dl[i] = std::exp(u[i]);
+        dr[i] = std::exp(v[i]) / (amax[i] > 0.0 ? amax[i] : 1.0);
+    }
+    return BILU_OK;
+}
+
+// B[k][l] = dl[r_k] A[r_k][c_l] dr[c_l] with r_k = rowperm[k], c_l = colperm[l] (identity or
+// unit scaling where a pointer is NULL); each row of B sorted by column.
+bilu_status scale_permute_csr_host(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val,
+                                   const int32_t *rowperm, const int32_t *colperm, const double *dl,
+                                   const double *dr, int64_t *out_rowptr, int32_t *out_colind, double *out_val,
+                                   std::string *err) {
+    auto fail = [&](const char *m) { if (err) *err = m; return BILU_ERR_ARG; };
+    const std::string bad = check_pattern(n, rowptr, colind);
+    if (!bad.empty()) return fail(bad.c_str());
+    if (!out_rowptr || (n > 0 && (!val || !out_colind || !out_val))) return fail("null array");
+    auto inverse = [&](const int32_t *p, std::vector<int32_t> &inv) {
+        inv.assign(n, -1);
+        for (int64_t k = 0; k < n; ++k) {
+            if (p[k] < 0 || p[k] >= n || inv[p[k]] >= 0) return false;
+            inv[p[k]] = (int32_t)k;
+        }
+        return true;
+    };
+    std::vector<int32_t> icol, irow;
+    if (rowperm && !inverse(rowperm, irow)) return fail("rowperm is not a permutation");
+    if (colperm && !inverse(colperm, icol)) return fail("colperm is not a permutation");
+    out_rowptr[0] = 0;
+    std::vector<std::pair<int32_t, double>> row;
+    for (int64_t k = 0; k < n; ++k) {
+        const int32_t i = rowperm ? rowperm[k] : (int32_t)k;
+        row.clear();
+        for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+            const int32_t j = colind[e];
+            double a = val[e];
+            if (dl) a *= dl[i];
+            if (dr) a *= dr[j];
+            row.emplace_back(colperm ? icol[j] : j, a);
+        }
+        std::sort(row.begin(), row.end(), [](const auto &x, const auto &y) { return x.first < y.first; });
+        int64_t o = out_rowptr[k];
+        for (const auto &rv : row) { out_colind[o] = rv.first; out_val[o] = rv.second; ++o; }
+        out_rowptr[k + 1] = o;
+    }
     return BILU_OK;
 }
 

@@ -188,6 +188,12 @@ bilu_status cosine_blocking_host(int64_t n, const int64_t *rowptr, const int32_t
 bilu_status partition_ilu1t_host(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val,
                                  double tau, int32_t max_block, int32_t ngroups, const int32_t *gstart,
                                  int32_t *bstart, int32_t *nblocks, std::string *err);
+bilu_status mwm_host(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val,
+                     int32_t *sigma, double *dl, double *dr, std::string *err);
+bilu_status scale_permute_csr_host(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val,
+                                   const int32_t *rowperm, const int32_t *colperm, const double *dl,
+                                   const double *dr, int64_t *out_rowptr, int32_t *out_colind, double *out_val,
+                                   std::string *err);
 bilu_status permute_csr_host(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val,
                              const int32_t *perm, int64_t *out_rowptr, int32_t *out_colind, double *out_val,
                              std::string *err);

@@ -114,6 +114,20 @@ bilu_status bilu_partition_ilu1t(int64_t n, const int64_t *rowptr, const int32_t
                                 &g_host_err);
 }
 
+bilu_status bilu_mwm(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val, int32_t *sigma,
+                     double *dl, double *dr) {
+    g_host_err.clear();
+    return mwm_host(n, rowptr, colind, val, sigma, dl, dr, &g_host_err);
+}
+
+bilu_status bilu_scale_permute_csr(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val,
+                                   const int32_t *rowperm, const int32_t *colperm, const double *dl,
+                                   const double *dr, int64_t *out_rowptr, int32_t *out_colind, double *out_val) {
+    g_host_err.clear();
+    return scale_permute_csr_host(n, rowptr, colind, val, rowperm, colperm, dl, dr, out_rowptr, out_colind,
+                                  out_val, &g_host_err);
+}
+
 bilu_status bilu_permute_csr(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val,
                              const int32_t *perm, int64_t *out_rowptr, int32_t *out_colind, double *out_val) {
     g_host_err.clear();

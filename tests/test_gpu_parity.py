@@ -229,6 +229,30 @@ def test_cosine_blocks_merged_by_ilu1t_end_to_end(ctx):
     assert info.status == B.BILU_OK and info.iters == ro.iters, (info.iters, ro.iters)
 
 
+def test_matching_and_scaling_end_to_end(ctx):
+    """Sec. 3.1 then Sec. 2.2 / Sec. 4: a convection-diffusion matrix with its rows in a random
+    order (zeros on the diagonal; the oracle's factor of it fails as singular) is matched and
+    scaled on the host, A^ = D_l A D_r Pi; the library factors A^ and solves A^ y = D_l b like
+    the oracle, and x = D_r Pi y solves A x = b."""
+    A0 = W.convdiff_upwind((8, 8, 8), seed=2)
+    rows = np.random.default_rng(5).permutation(A0.n).astype(np.int32)
+    A = W.CSR(A0.n, *B.bilu_scale_permute_csr(A0.n, A0.rowptr, A0.colind, A0.val, rowperm=rows))
+    sigma, dl, dr = B.bilu_mwm(A.n, A.rowptr, A.colind, A.val)
+    Ah = W.CSR(A.n, *B.bilu_scale_permute_csr(A.n, A.rowptr, A.colind, A.val, None, sigma, dl, dr))
+    g = gpu_factor(ctx, Ah, 1e-2, _fixed(8))
+    assert g.status == B.BILU_OK
+    o = _oracle(Ah, g.bstart, 1e-2)
+    compare_factors(o, g, A=Ah, tau=1e-2)
+    b = np.random.default_rng(1).standard_normal(A.n)
+    ro = O.gmres(Ah, o, dl * b, tol=1e-8, restart=30)
+    y = np.zeros(A.n)
+    info = B.gmres_solve(ctx, dl * b, y, 1e-8, 30, 10000)
+    assert info.status == B.BILU_OK and info.iters == ro.iters, (info.iters, ro.iters)
+    x = np.zeros(A.n)
+    x[sigma] = dr[sigma] * y
+    assert np.linalg.norm(O.spmv(A, x) - b) <= 1e-7 * np.linalg.norm(b)
+
+
 def test_analyze_partition_rejects_invalid_partitions(ctx):
     A = W.convdiff_upwind((4, 4, 4), seed=1)
     for bs in ([0, 10, 10, 64], [0, 70], [1, 64], [0, 32]):

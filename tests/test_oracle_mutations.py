@@ -17,11 +17,11 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PIN_TESTS = ["test_oracle.py", "test_partition_oracle.py", "test_block_check_oracle.py", "test_skip_oracle.py",
-             "test_golden.py", "test_cosine_oracle.py"]
+             "test_golden.py", "test_cosine_oracle.py", "test_mwm_oracle.py"]
 ORACLE_FILES = ["__init__.py", "bilu_oracle.c", "bilu_oracle.h", "block_check.py", "skip_oracle.py",
-                "cosine_oracle.py"]
+                "cosine_oracle.py", "mwm_oracle.py"]
 
-C, BCK, SKP, COS = "bilu_oracle.c", "block_check.py", "skip_oracle.py", "cosine_oracle.py"
+C, BCK, SKP, COS, MWM = "bilu_oracle.c", "block_check.py", "skip_oracle.py", "cosine_oracle.py", "mwm_oracle.py"
 
 # (name, file, fragment, replacement, which occurrence of the fragment: 1 = first)
 MUTANTS = [
@@ -107,6 +107,20 @@ MUTANTS = [
      "partners = sorted({j for k in rows[i] for j in cols[k] if j > i}, reverse=True)", 1),
     ("cosine: test against the column count", COS, "(tau * len(rows[i])) * len(rows[j])",
      "(tau * len(rows[i])) * len(cols[j])", 1),
+    # maximum weight matching with scaling (Sec. 3.1)
+    ("matching: cost from the row maximum", MWM, "amax[j] = max(amax[j], abs(float(A.val[e])))",
+     "amax[i] = max(amax[i], abs(float(A.val[e])))", 1),
+    ("matching: cost sign", MWM, "C[i, j] = math.log(amax[j]) - math.log(a)", "C[i, j] = math.log(a) - math.log(amax[j])", 1),
+    ("matching: greedy (no potentials on the path)", MWM, "d = dist[j] + C[i, k] - u[i] - v[k]",
+     "d = C[i, k] - u[i] - v[k]", 1),
+    ("matching: row potential not raised", MWM, "u[row_of[j]] += D - dist[j]", "u[row_of[j]] += 0.0", 1),
+    ("matching: column potential sign", MWM, "v[j] -= D - dist[j]", "v[j] += D - dist[j]", 1),
+    ("matching: start row potential", MWM, "u[s] += D", "u[s] += 0.0", 1),
+    ("matching: left scaling inverted", MWM, "dl = np.array([math.exp(x) for x in u])",
+     "dl = np.array([math.exp(-x) for x in u])", 1),
+    ("matching: right scaling not normalised", MWM,
+     "dr = np.array([math.exp(v[j]) / (amax[j] if amax[j] > 0 else 1.0) for j in range(A.n)])",
+     "dr = np.array([math.exp(v[j]) for j in range(A.n)])", 1),
     # learned-skip features and classifier
     ("features: sum of products is the last one", SKP, "S += v", "S = v", 1),
     ("features: max is a sum", SKP, "M = max(M, v)", "M = M + v", 1),
