@@ -208,7 +208,7 @@ bilu_status bilu_export(bilu_ctx *ctx, int64_t *Lptr, int32_t *Lrow, double *Lva
 /* Human-readable description of the last error on this context ("" if none).  With
  * ctx == NULL: the last error of this host thread's context-free calls
  * (bilu_cosine_blocking, bilu_partition_ilu1t, bilu_mwm, bilu_scale_permute_csr,
- * bilu_permute_csr). */
+ * bilu_nd_order, bilu_block_etree, bilu_permute_csr). */
 const char *bilu_last_error(const bilu_ctx *ctx);
 
 /*
@@ -273,6 +273,34 @@ bilu_status bilu_mwm(int64_t n, const int64_t *rowptr, const int32_t *colind, co
 bilu_status bilu_scale_permute_csr(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val,
                                    const int32_t *rowperm, const int32_t *colperm, const double *dl,
                                    const double *dr, int64_t *out_rowptr, int32_t *out_colind, double *out_val);
+
+/*
+ * Block nested dissection (Sec. 3.3), host only: the blocks bstart[nblocks + 1] of A (pattern
+ * only) are compressed to the companion graph (K ~ L when A couples B_K and B_L, either
+ * direction), which is reordered by George's level-structure dissection (in place of the
+ * paper's METIS): a connected set of more than `leaf` (>= 1) blocks is split by the middle
+ * level of a breadth-first level structure from a pseudo-peripheral block, ordered as first
+ * part, second part, separator; sets with fewer than 3 levels stay in increasing order.  The
+ * block order is expanded to the unknowns with every block kept whole.  Outputs (caller-
+ * owned): perm[n] (original index at each new position; A' = P^T A P, see bilu_permute_csr),
+ * bstart_out[nblocks + 1] (the blocks of A'), block_order[nblocks] (the original block at each
+ * new block position).  Errors: BILU_ERR_ARG, message in bilu_last_error(NULL).
+ */
+bilu_status bilu_nd_order(int64_t n, const int64_t *rowptr, const int32_t *colind, int32_t nblocks,
+                          const int32_t *bstart, int32_t leaf, int32_t *perm, int32_t *bstart_out,
+                          int32_t *block_order);
+
+/*
+ * Block elimination tree, host only: parent[K] (-1 for a root) for the blocks bstart of A in
+ * their given order, from the symmetrised companion graph with the fill of block elimination
+ * (each block's later neighbours become a clique; its parent is the first of them).  Every
+ * block J whose factor entries update block K (a kept row of L_J or column of U-breve_J
+ * inside B_K, Algorithm 1 with blocks, Sec. 2.2) is a descendant of K, so K depends only on
+ * its subtree; *height is the number of blocks on the longest leaf-to-root path (the critical
+ * path of a factorization that runs independent subtrees side by side).
+ */
+bilu_status bilu_block_etree(int64_t n, const int64_t *rowptr, const int32_t *colind, int32_t nblocks,
+                             const int32_t *bstart, int32_t *parent, int32_t *height);
 
 /*
  * Symmetric permutation A~ = Q^T A Q of a CSR matrix on the host (the reordering step of

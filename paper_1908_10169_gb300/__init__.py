@@ -31,6 +31,7 @@ EXPORTED = ["bilu_params_default", "bilu_create", "bilu_analyze", "bilu_factor",
             "bilu_debug_set", "bilu_apply_noalloc", "bilu_factor_batch", "gmres_solve_batch",
             "bilu_record_samples", "bilu_get_samples", "bilu_mlp_train", "bilu_mlp_forward", "bilu_mlp_grad",
             "bilu_set_skip_model", "bilu_cosine_blocking", "bilu_partition_ilu1t", "bilu_mwm", "bilu_scale_permute_csr",
+            "bilu_nd_order", "bilu_block_etree",
             "bilu_permute_csr",
             "bilu_analyze_partition",
             "bilu_destroy"]
@@ -112,6 +113,8 @@ def lib():
             "bilu_permute_csr": ([i64, P, P, P, P, P, P, P], i32),
             "bilu_partition_ilu1t": ([i64, P, P, P, f64, i32, i32, P, P, ct.POINTER(i32)], i32),
             "bilu_mwm": ([i64, P, P, P, P, P, P], i32),
+            "bilu_nd_order": ([i64, P, P, i32, P, i32, P, P, P], i32),
+            "bilu_block_etree": ([i64, P, P, i32, P, P, ct.POINTER(i32)], i32),
             "bilu_scale_permute_csr": ([i64, P, P, P, P, P, P, P, P, P, P], i32),
             "bilu_analyze_partition": ([P, i64, P, P, P, i32, ct.POINTER(bilu_params), i32, P], i32),
             "bilu_destroy": ([P], None),
@@ -347,6 +350,46 @@ def bilu_scale_permute_csr(n: int, rowptr, colind, val, rowperm=None, colperm=No
     _check(None, lib().bilu_scale_permute_csr(n, _ptr(rp), _ptr(ci), _ptr(va), _ptr(rpm), _ptr(cpm), _ptr(sl),
                                               _ptr(sr), _ptr(orp), _ptr(oci), _ptr(ova)))
     return orp, oci[:nnz].copy(), ova[:nnz].copy()
+
+
+def _host_pattern(n: int, rowptr, colind, bstart):
+    """Host pattern arrays (rowptr, colind) and a partition of the C types, length-checked."""
+    import numpy as np
+    if n < 0:
+        raise ValueError("n < 0")
+    rp = np.ascontiguousarray(rowptr, dtype=np.int64)
+    if rp.size < n + 1:
+        raise ValueError("rowptr needs n + 1 entries")
+    ci = np.ascontiguousarray(colind, dtype=np.int32)
+    if ci.size < (int(rp[n]) if n > 0 else 0):
+        raise ValueError("colind shorter than rowptr[n]")
+    bs = np.ascontiguousarray(bstart, dtype=np.int32)
+    if bs.size < 1:
+        raise ValueError("bstart needs at least one entry")
+    return rp, ci, bs
+
+
+def bilu_nd_order(n: int, rowptr, colind, bstart, leaf: int = 1):
+    """Sec. 3.3 block nested dissection on the host: (perm, bstart_out, block_order)."""
+    import numpy as np
+    rp, ci, bs = _host_pattern(n, rowptr, colind, bstart)
+    nb = len(bs) - 1
+    perm = np.zeros(max(n, 1), np.int32)
+    bso = np.zeros(nb + 1, np.int32)
+    order = np.zeros(max(nb, 1), np.int32)
+    _check(None, lib().bilu_nd_order(n, _ptr(rp), _ptr(ci), nb, _ptr(bs), leaf, _ptr(perm), _ptr(bso), _ptr(order)))
+    return perm[:n].copy(), bso, order[:nb].copy()
+
+
+def bilu_block_etree(n: int, rowptr, colind, bstart):
+    """Block elimination tree on the host: (parent, height)."""
+    import numpy as np
+    rp, ci, bs = _host_pattern(n, rowptr, colind, bstart)
+    nb = len(bs) - 1
+    parent = np.zeros(max(nb, 1), np.int32)
+    h = ct.c_int32(0)
+    _check(None, lib().bilu_block_etree(n, _ptr(rp), _ptr(ci), nb, _ptr(bs), _ptr(parent), ct.byref(h)))
+    return parent[:nb].copy(), h.value
 
 
 def bilu_permute_csr(n: int, rowptr, colind, val, perm):

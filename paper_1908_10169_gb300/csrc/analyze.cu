@@ -435,6 +435,194 @@ bilu_status scale_permute_csr_host(int64_t n, const int64_t *rowptr, const int32
     return BILU_OK;
 }
 
+namespace {
+
+// Symmetrised companion graph of a block partition: K ~ L when A couples B_K and B_L in either
+// direction (sorted, unique adjacency lists).
+std::vector<std::vector<int32_t>> block_graph(int64_t n, const int64_t *rowptr, const int32_t *colind,
+                                              int32_t nb, const int32_t *bstart) {
+    std::vector<int32_t> blk(n);
+    for (int32_t K = 0; K < nb; ++K)
+        for (int32_t i = bstart[K]; i < bstart[K + 1]; ++i) blk[i] = K;
+    std::vector<std::vector<int32_t>> adj(nb);
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+            const int32_t K = blk[i], L = blk[colind[e]];
+            if (K != L) {
+                adj[K].push_back(L);
+                adj[L].push_back(K);
+            }
+        }
+    for (auto &a : adj) {
+        std::sort(a.begin(), a.end());
+        a.erase(std::unique(a.begin(), a.end()), a.end());
+    }
+    return adj;
+}
+
+// George's level-structure nested dissection of the block graph (Sec. 3.3 with a dissection
+// written here in place of METIS).  A connected set of more than `leaf` nodes is split by the
+// breadth-first level structure from a pseudo-peripheral node (from the set's smallest node,
+// move to a least-degree node of the last level, ties by index, while the level count grows):
+// the middle level (L / 2 of L levels) is the separator, the levels before and after it the
+// two parts; order = first part, second part, separator (ascending).  Fewer than 3 levels, or
+// at most `leaf` nodes: ascending order.  A disconnected set: its components by smallest node.
+struct Dissection {
+    const std::vector<std::vector<int32_t>> &adj;
+    int leaf;
+    std::vector<int32_t> mark, seen, out;
+    int32_t marks = 0, seens = 0;
+
+    Dissection(const std::vector<std::vector<int32_t>> &a, int lf)
+        : adj(a), leaf(lf), mark(a.size(), 0), seen(a.size(), 0) {}
+
+    std::vector<std::vector<int32_t>> levels(int32_t sid, int32_t root) {
+        ++seens;
+        seen[root] = seens;
+        std::vector<std::vector<int32_t>> L{{root}};
+        for (;;) {
+            std::vector<int32_t> nxt;
+            for (int32_t v : L.back())
+                for (int32_t w : adj[v])
+                    if (mark[w] == sid && seen[w] != seens) {
+                        seen[w] = seens;
+                        nxt.push_back(w);
+                    }
+            if (nxt.empty()) return L;
+            std::sort(nxt.begin(), nxt.end());
+            L.push_back(std::move(nxt));
+        }
+    }
+
+    int degree(int32_t v, int32_t sid) const {
+        int d = 0;
+        for (int32_t w : adj[v]) d += mark[w] == sid;
+        return d;
+    }
+
+    void dissect(std::vector<int32_t> nodes) {
+        const int32_t sid = ++marks;
+        for (int32_t v : nodes) mark[v] = sid;
+        std::sort(nodes.begin(), nodes.end());
+        // components, by smallest node
+        std::vector<std::vector<int32_t>> comps;
+        ++seens;
+        const int32_t cs = seens;
+        for (int32_t v : nodes) {
+            if (seen[v] == cs) continue;
+            std::vector<int32_t> comp{v};
+            seen[v] = cs;
+            for (size_t q = 0; q < comp.size(); ++q)
+                for (int32_t w : adj[comp[q]])
+                    if (mark[w] == sid && seen[w] != cs) {
+                        seen[w] = cs;
+                        comp.push_back(w);
+                    }
+            comps.push_back(std::move(comp));
+        }
+        for (auto &comp : comps) {
+            std::sort(comp.begin(), comp.end());
+            if ((int)comp.size() <= leaf) {
+                out.insert(out.end(), comp.begin(), comp.end());
+                continue;
+            }
+            const int32_t cid = ++marks;
+            for (int32_t v : comp) mark[v] = cid;
+            int32_t root = comp[0];
+            auto L = levels(cid, root);
+            for (;;) {
+                int32_t cand = -1, cdeg = 0;
+                for (int32_t v : L.back()) {
+                    const int d = degree(v, cid);
+                    if (cand < 0 || d < cdeg || (d == cdeg && v < cand)) { cand = v; cdeg = d; }
+                }
+                auto L2 = levels(cid, cand);
+                if (L2.size() <= L.size()) break;
+                root = cand;
+                L = std::move(L2);
+            }
+            if (L.size() < 3) {
+                out.insert(out.end(), comp.begin(), comp.end());
+                continue;
+            }
+            const size_t m = L.size() / 2;
+            std::vector<int32_t> first, second;
+            for (size_t k = 0; k < m; ++k) first.insert(first.end(), L[k].begin(), L[k].end());
+            for (size_t k = m + 1; k < L.size(); ++k) second.insert(second.end(), L[k].begin(), L[k].end());
+            const std::vector<int32_t> sep = L[m];
+            dissect(std::move(first));
+            dissect(std::move(second));
+            out.insert(out.end(), sep.begin(), sep.end());
+        }
+    }
+};
+
+std::string check_partition(int64_t n, int32_t nb, const int32_t *bstart) {
+    if (nb < 0 || !bstart) return "invalid partition";
+    if (bstart[0] != 0 || bstart[nb] != n || (n > 0 && nb == 0)) return "partition must run from 0 to n";
+    for (int32_t K = 0; K < nb; ++K)
+        if (bstart[K + 1] <= bstart[K]) return "partition not strictly increasing";
+    return "";
+}
+
+}  // namespace
+
+bilu_status nd_order_host(int64_t n, const int64_t *rowptr, const int32_t *colind, int32_t nb,
+                          const int32_t *bstart, int32_t leaf, int32_t *perm, int32_t *bstart_out,
+                          int32_t *order_out, std::string *err) {
+    auto fail = [&](const std::string &m) { if (err) *err = m; return BILU_ERR_ARG; };
+    std::string bad = check_pattern(n, rowptr, colind);
+    if (bad.empty()) bad = check_partition(n, nb, bstart);
+    if (!bad.empty()) return fail(bad);
+    if (leaf < 1) return fail("leaf must be >= 1");
+    if (!bstart_out || (n > 0 && (!perm || !order_out))) return fail("null output array");
+    const auto adj = block_graph(n, rowptr, colind, nb, bstart);
+    Dissection d(adj, leaf);
+    std::vector<int32_t> all(nb);
+    std::iota(all.begin(), all.end(), 0);
+    d.dissect(all);
+    int64_t pos = 0;
+    bstart_out[0] = 0;
+    for (int32_t k = 0; k < nb; ++k) {
+        const int32_t K = d.out[k];
+        order_out[k] = K;
+        for (int32_t i = bstart[K]; i < bstart[K + 1]; ++i) perm[pos++] = i;
+        bstart_out[k + 1] = (int32_t)pos;
+    }
+    return BILU_OK;
+}
+
+// Elimination tree of the symmetrised block graph: eliminating the blocks in order, each one's
+// later neighbours become a clique, so they are handed to its first later neighbour, its parent.
+bilu_status block_etree_host(int64_t n, const int64_t *rowptr, const int32_t *colind, int32_t nb,
+                             const int32_t *bstart, int32_t *parent, int32_t *height, std::string *err) {
+    auto fail = [&](const std::string &m) { if (err) *err = m; return BILU_ERR_ARG; };
+    std::string bad = check_pattern(n, rowptr, colind);
+    if (bad.empty()) bad = check_partition(n, nb, bstart);
+    if (!bad.empty()) return fail(bad);
+    if (!height || (nb > 0 && !parent)) return fail("null output array");
+    const auto adj = block_graph(n, rowptr, colind, nb, bstart);
+    std::vector<std::vector<int32_t>> later(nb);
+    for (int32_t K = 0; K < nb; ++K)
+        for (int32_t w : adj[K])
+            if (w > K) later[K].push_back(w);
+    std::vector<int32_t> h(nb, 1);
+    for (int32_t K = 0; K < nb; ++K) {
+        parent[K] = -1;
+        if (later[K].empty()) continue;
+        const int32_t p = later[K][0];
+        parent[K] = p;
+        std::vector<int32_t> merged;
+        std::set_union(later[p].begin(), later[p].end(), later[K].begin() + 1, later[K].end(),
+                       std::back_inserter(merged));
+        later[p] = std::move(merged);
+        std::vector<int32_t>().swap(later[K]);
+        h[p] = std::max(h[p], h[K] + 1);
+    }
+    *height = nb > 0 ? *std::max_element(h.begin(), h.end()) : 0;
+    return BILU_OK;
+}
+
 // A~ = Q^T A Q: row k of A~ is row perm[k] of A with every column j renamed iperm[j] and the
 // row re-sorted.
 bilu_status permute_csr_host(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val,

@@ -194,6 +194,11 @@ bilu_status scale_permute_csr_host(int64_t n, const int64_t *rowptr, const int32
                                    const int32_t *rowperm, const int32_t *colperm, const double *dl,
                                    const double *dr, int64_t *out_rowptr, int32_t *out_colind, double *out_val,
                                    std::string *err);
+bilu_status nd_order_host(int64_t n, const int64_t *rowptr, const int32_t *colind, int32_t nb,
+                          const int32_t *bstart, int32_t leaf, int32_t *perm, int32_t *bstart_out,
+                          int32_t *order_out, std::string *err);
+bilu_status block_etree_host(int64_t n, const int64_t *rowptr, const int32_t *colind, int32_t nb,
+                             const int32_t *bstart, int32_t *parent, int32_t *height, std::string *err);
 bilu_status permute_csr_host(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val,
                              const int32_t *perm, int64_t *out_rowptr, int32_t *out_colind, double *out_val,
                              std::string *err);

@@ -128,6 +128,19 @@ bilu_status bilu_scale_permute_csr(int64_t n, const int64_t *rowptr, const int32
                                   out_val, &g_host_err);
 }
 
+bilu_status bilu_nd_order(int64_t n, const int64_t *rowptr, const int32_t *colind, int32_t nblocks,
+                          const int32_t *bstart, int32_t leaf, int32_t *perm, int32_t *bstart_out,
+                          int32_t *block_order) {
+    g_host_err.clear();
+    return nd_order_host(n, rowptr, colind, nblocks, bstart, leaf, perm, bstart_out, block_order, &g_host_err);
+}
+
+bilu_status bilu_block_etree(int64_t n, const int64_t *rowptr, const int32_t *colind, int32_t nblocks,
+                             const int32_t *bstart, int32_t *parent, int32_t *height) {
+    g_host_err.clear();
+    return block_etree_host(n, rowptr, colind, nblocks, bstart, parent, height, &g_host_err);
+}
+
 bilu_status bilu_permute_csr(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val,
                              const int32_t *perm, int64_t *out_rowptr, int32_t *out_colind, double *out_val) {
     g_host_err.clear();

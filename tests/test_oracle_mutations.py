@@ -17,11 +17,12 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PIN_TESTS = ["test_oracle.py", "test_partition_oracle.py", "test_block_check_oracle.py", "test_skip_oracle.py",
-             "test_golden.py", "test_cosine_oracle.py", "test_mwm_oracle.py"]
+             "test_golden.py", "test_cosine_oracle.py", "test_mwm_oracle.py", "test_nd_oracle.py"]
 ORACLE_FILES = ["__init__.py", "bilu_oracle.c", "bilu_oracle.h", "block_check.py", "skip_oracle.py",
-                "cosine_oracle.py", "mwm_oracle.py"]
+                "cosine_oracle.py", "mwm_oracle.py", "nd_oracle.py"]
 
-C, BCK, SKP, COS, MWM = "bilu_oracle.c", "block_check.py", "skip_oracle.py", "cosine_oracle.py", "mwm_oracle.py"
+C, BCK, SKP, COS, MWM, ND = ("bilu_oracle.c", "block_check.py", "skip_oracle.py", "cosine_oracle.py", "mwm_oracle.py",
+                             "nd_oracle.py")
 
 # (name, file, fragment, replacement, which occurrence of the fragment: 1 = first)
 MUTANTS = [
@@ -121,6 +122,14 @@ MUTANTS = [
     ("matching: right scaling not normalised", MWM,
      "dr = np.array([math.exp(v[j]) / (amax[j] if amax[j] > 0 else 1.0) for j in range(A.n)])",
      "dr = np.array([math.exp(v[j]) for j in range(A.n)])", 1),
+    # block nested dissection and elimination tree (Sec. 3.3)
+    ("nd: separator is the first level", ND, "m = len(levels) // 2", "m = 1", 1),
+    ("nd: separator ordered first", ND, "order += dissect(adj, first, leaf) + dissect(adj, second, leaf) + sorted(levels[m])",
+     "order += sorted(levels[m]) + dissect(adj, first, leaf) + dissect(adj, second, leaf)", 1),
+    ("nd: graph not symmetrised", ND, "                adj[L].add(K)\n", "", 1),
+    ("nd: root not pseudo-peripheral", ND, "        if len(lv) <= len(levels):", "        if True:", 1),
+    ("etree: no fill", ND, "            later[p] |= later[K] - {p}", "            pass", 1),
+    ("etree: parent is the last later neighbour", ND, "            p = min(later[K])", "            p = max(later[K])", 1),
     # learned-skip features and classifier
     ("features: sum of products is the last one", SKP, "S += v", "S = v", 1),
     ("features: max is a sum", SKP, "M = max(M, v)", "M = M + v", 1),
