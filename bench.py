@@ -18,12 +18,16 @@ Other lines (not the default): --precision fp32|bf16 (mixed-precision updates), 
 bound|learned (norm-bound or learned candidate skip; learned trains its classifier first, on
 200 generated 3D problems, untimed), --workload elasticity|laplace27x4 (the mixed-precision and
 learned-skip configurations' matrices), --batch N (N uneven 2D / 3D systems in one launch and
-one graph per GMRES cycle, sharded over the ranks under torchrun). Under torchrun the single-
-matrix line runs one replica per rank; the reference arm runs on rank 0 only.
+one graph per GMRES cycle, sharded over the ranks under torchrun), --mwm / --blocking
+cosine|cosine+ilu1t|ilu1t / --order nd (the host analysis of Sec. 3.1-3.4 before the factorization,
+outside the timed region and inside the end-to-end time; --workload cd3d_rows_scrambled is the
+benchmark matrix with its equations in random order, which needs --mwm). Under torchrun the
+single-matrix line runs one replica per rank; the reference arm runs on rank 0 only.
 """
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import platform
@@ -47,7 +51,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
-    ap.add_argument("--workload", choices=["cd3d", "elasticity", "laplace27x4"], default="cd3d",
+    ap.add_argument("--workload", choices=["cd3d", "elasticity", "laplace27x4", "cd3d_rows_scrambled"], default="cd3d",
                     help="cd3d: 3D upwind convection-diffusion (the benchmark); elasticity: Q1 3-dof/node "
                          "(mixed-precision configuration, --side 48 --block 63); laplace27x4: Q1 27-point, "
                          "4 dof/node (learned-skip evaluation, --side 64)")
@@ -58,6 +62,13 @@ def parse():
     ap.add_argument("--train-count", type=int, default=200,
                     help="learned skip: training problems (3D 7-point, sides 32..48, Peclet 1..1000)")
     ap.add_argument("--train-rate", type=float, default=0.05, help="learned skip: share of candidates recorded")
+    ap.add_argument("--mwm", action="store_true",
+                    help="maximum weight matching + scaling (Sec. 3.1) before the factorization (host)")
+    ap.add_argument("--blocking", choices=["fixed", "ilu1t", "cosine", "cosine+ilu1t"], default="fixed",
+                    help="fixed blocks of --block (default); the ILU(1,tau) guess (Sec. 3.4); cosine blocks "
+                         "(Sec. 3.2), as they are or merged by the ILU(1,tau) rule")
+    ap.add_argument("--order", choices=["natural", "nd"], default="natural",
+                    help="nd: block nested dissection of the blocks (Sec. 3.3) before the factorization (host)")
     ap.add_argument("--batch", type=int, default=0,
                     help="factor + solve this many uneven 2D/3D matrices in one batched launch instead")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -106,14 +117,90 @@ def workload(args):
         return W.elasticity3d(side=args.side, seed=2, block=args.block)
     if args.workload == "laplace27x4":
         return W.laplace27_4dof(side=args.side, seed=3, block=args.block)
+    if args.workload == "cd3d_rows_scrambled":
+        return W.rows_scrambled(W.cd3d(side=args.side, seed=1, block=args.block), seed=5)
     return W.cd3d(side=args.side, seed=1, block=args.block)
 
 
+class Prepared:
+    """The system the factorization sees after the host analysis of Sec. 3.1-3.4, and the map
+    of its solution back to the original unknowns."""
+
+    def __init__(self, A, b, bstart, steps, maps):
+        self.A, self.b, self.bstart, self.steps, self._maps = A, b, bstart, steps, maps
+
+    def to_original(self, y):
+        """x of A x = b from the solution y of the prepared system."""
+        import numpy as np
+        x = np.asarray(y, dtype=np.float64)
+        for f in reversed(self._maps):
+            x = f(x)
+        return x
+
+
+def preprocess(args, w):
+    """Runs the library's host analysis calls the options ask for, in the paper's order:
+    matching + scaling (A^ = D_l A D_r Pi, Sec. 3.1), cosine blocking (Q^T A Q, Sec. 3.2), block
+    nested dissection (P^T A P, Sec. 3.3).  With no option it returns the workload unchanged
+    (bstart None: fixed blocks of --block)."""
+    import numpy as np
+
+    import paper_1908_10169_gb300 as B
+    from paper_1908_10169_gb300 import workloads as W
+    A, b, bstart, steps, maps = w.A, w.b, None, [], []
+    if getattr(args, "mwm", False):
+        sigma, dl, dr = B.bilu_mwm(A.n, A.rowptr, A.colind, A.val)
+        A = W.CSR(A.n, *B.bilu_scale_permute_csr(A.n, A.rowptr, A.colind, A.val, None, sigma, dl, dr))
+        b = dl * b
+
+        def unmatch(y, sigma=sigma, dr=dr):
+            x = np.empty_like(y)
+            x[sigma] = dr[sigma] * y
+            return x
+        maps.append(unmatch)
+        steps.append("mwm")
+
+    def sym_permute(perm):
+        nonlocal A, b
+        A = W.CSR(A.n, *B.bilu_permute_csr(A.n, A.rowptr, A.colind, A.val, perm))
+        b = b[perm]
+
+        def unpermute(y, perm=perm):
+            x = np.empty_like(y)
+            x[perm] = y
+            return x
+        maps.append(unpermute)
+
+    blocking = getattr(args, "blocking", "fixed")
+    if blocking.startswith("cosine"):
+        perm, groups = B.bilu_cosine_blocking(A.n, A.rowptr, A.colind, 0.8, 64)
+        sym_permute(perm)
+        bstart = groups
+        if blocking == "cosine+ilu1t":
+            bstart = B.bilu_partition_ilu1t(A.n, A.rowptr, A.colind, A.val, 1e-2, 64, groups)
+        steps.append(blocking)
+    elif blocking == "ilu1t":
+        bstart = B.bilu_partition_ilu1t(A.n, A.rowptr, A.colind, A.val, 1e-2, 64)
+        steps.append("ilu1t")
+    if getattr(args, "order", "natural") == "nd":
+        if bstart is None:
+            bstart = np.append(np.arange(0, A.n, args.block), A.n).astype(np.int32)
+        perm, bstart, _ = B.bilu_nd_order(A.n, A.rowptr, A.colind, bstart)
+        sym_permute(perm)
+        steps.append("nd")
+    return Prepared(A, b, bstart, steps, maps)
+
+
 def config(args, w, extra=None):
+    blocking = getattr(args, "blocking", "fixed")
     c = {"workload": w.name, "n": w.A.n, "nnz": w.A.nnz, "droptol": w.droptol,
-         "blocking": f"fixed {args.block}", "gmres": f"GMRES({w.restart}) rtol {w.gmres_tol}, x0 = 0, b = A*1",
+         "blocking": f"fixed {args.block}" if blocking == "fixed" else blocking, "gmres": f"GMRES({w.restart}) rtol {w.gmres_tol}, x0 = 0, b = A*1",
          "updates": getattr(args, "precision", "fp64"), "skip": getattr(args, "skip", "none"),
          "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{args.gpus}"}
+    pre = [k for k, on in (("mwm", getattr(args, "mwm", False)),
+                           ("nd", getattr(args, "order", "natural") == "nd")) if on]
+    if pre or blocking != "fixed":
+        c["host_analysis"] = pre + ([blocking] if blocking != "fixed" else [])
     if extra:
         c.update(extra)
     return c
@@ -232,10 +319,17 @@ def run_reference(args):
     import oracle as O
     oracle_cores, model = cpu_desc()
     w = workload(args)
-    bs = O.partition_fixed(w.A.n, args.block)
-    small = workload(argparse.Namespace(**{**vars(args), "side": 16, "block": 16}))
+    # the options' host analysis prepares the input (library calls, not timed); the oracle's
+    # factor + GMRES on the prepared system is what is timed
+    prep = preprocess(args, w)
+    bs = prep.bstart if prep.bstart is not None else O.partition_fixed(w.A.n, args.block)
+    w = dataclasses.replace(w, A=prep.A, b=prep.b)
+    sargs = argparse.Namespace(**{**vars(args), "side": 16, "block": 16})
+    small = workload(sargs)
+    sprep = preprocess(sargs, small)
+    small = dataclasses.replace(small, A=sprep.A, b=sprep.b)
     for _ in range(args.warmup):  # warm-up on a small case of the same kind
-        oracle_step(small, O.partition_fixed(small.A.n, 16))
+        oracle_step(small, sprep.bstart if sprep.bstart is not None else O.partition_fixed(small.A.n, 16))
     times, iters = [], 0
     for _ in range(args.steps):
         t, tf, tg, iters = oracle_step(w, bs)
@@ -285,13 +379,17 @@ def run_gpu(args):
                    "train_loss": sm.train_loss, "logit_hi": sm.logit_hi, "train_skip_rate": sm.skip_rate,
                    "train_false_drop_rate": sm.false_drop_rate, "record_s": t1 - t0, "train_s": time.time() - t1}
         B.bilu_set_skip_model(ctx, sm.model, sm.logit_hi)
-    rp = torch.from_numpy(w.A.rowptr.astype(np.int64)).to(dev)
-    ci = torch.from_numpy(w.A.colind.astype(np.int32)).to(dev)
-    va = torch.from_numpy(w.A.val).to(dev)
-    b = torch.from_numpy(w.b).to(dev)
+    prep = preprocess(args, w)  # host analysis of Sec. 3.1-3.3 when asked for (outside the timed region)
+    rp = torch.from_numpy(prep.A.rowptr.astype(np.int64)).to(dev)
+    ci = torch.from_numpy(prep.A.colind.astype(np.int32)).to(dev)
+    va = torch.from_numpy(prep.A.val).to(dev)
+    b = torch.from_numpy(np.ascontiguousarray(prep.b)).to(dev)
     x = torch.zeros_like(b)
     torch.cuda.synchronize()
-    B.bilu_analyze(ctx, w.A.n, rp, ci, va, params)
+    if prep.bstart is None:
+        B.bilu_analyze(ctx, w.A.n, rp, ci, va, params)
+    else:
+        B.bilu_analyze_partition(ctx, w.A.n, rp, ci, va, prep.bstart, params)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
     def barrier():
@@ -404,10 +502,22 @@ def run_gpu(args):
         for k in range(min(args.steps, 3) + 1):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            B.bilu_analyze(ctx2, n, h_rp, h_ci, h_va, params)
-            B.bilu_factor(ctx2, w.droptol)
-            h_x.zero_()
-            B.gmres_solve(ctx2, h_b, h_x, w.gmres_tol, w.restart, 10000)
+            if prep.steps:  # the host analysis is part of the end-to-end path
+                p2 = preprocess(args, w)
+                hb = torch.from_numpy(np.ascontiguousarray(p2.b))
+                if p2.bstart is None:
+                    B.bilu_analyze(ctx2, n, p2.A.rowptr, p2.A.colind, p2.A.val, params)
+                else:
+                    B.bilu_analyze_partition(ctx2, n, p2.A.rowptr, p2.A.colind, p2.A.val, p2.bstart, params)
+                B.bilu_factor(ctx2, w.droptol)
+                h_x.zero_()
+                B.gmres_solve(ctx2, hb, h_x, w.gmres_tol, w.restart, 10000)
+                p2.to_original(h_x.numpy())
+            else:
+                B.bilu_analyze(ctx2, n, h_rp, h_ci, h_va, params)
+                B.bilu_factor(ctx2, w.droptol)
+                h_x.zero_()
+                B.gmres_solve(ctx2, h_b, h_x, w.gmres_tol, w.restart, 10000)
             torch.cuda.synchronize()
             if k > 0:
                 et.append(time.perf_counter() - t0)
@@ -419,7 +529,8 @@ def run_gpu(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle as O
         cores, model = cpu_desc()
-        t, tfo, tgo, it_o = oracle_step(w, O.partition_fixed(n, args.block))
+        wp = dataclasses.replace(w, A=prep.A, b=prep.b)
+        t, tfo, tgo, it_o = oracle_step(wp, prep.bstart if prep.bstart is not None else O.partition_fixed(n, args.block))
         cpu = {"value": t, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"one full step (oracle factor {tfo:.1f} s + GMRES {tgo:.1f} s, {it_o} iters) on the "
                          f"same matrix; host {model}, {cores} cores visible, 1 used",
@@ -429,7 +540,10 @@ def run_gpu(args):
                         "kept": st.kept_rows + st.kept_cols, "flops_factor": st.flops_factor})
         ctx3 = B.bilu_create(local, stream)
         params.skip = B.BILU_SKIP_NONE
-        B.bilu_analyze(ctx3, w.A.n, rp, ci, va, params)
+        if prep.bstart is None:
+            B.bilu_analyze(ctx3, w.A.n, rp, ci, va, params)
+        else:
+            B.bilu_analyze_partition(ctx3, w.A.n, rp, ci, va, prep.bstart, params)
         for _ in range(2):
             B.bilu_factor(ctx3, w.droptol)
         s3 = B.bilu_stats(ctx3)

@@ -191,6 +191,19 @@ def cd3d(side: int = 64, seed: int = 1, block: int = 64) -> Workload:
     return Workload(f"cd3d_7pt_{side}^3", A, rhs_ones(A), 1e-2, 64, "fixed", block)
 
 
+def rows_scrambled(w: Workload, seed: int = 5) -> Workload:
+    """The same system with its equations (rows of A and entries of b) in a seeded random order:
+    a nonsymmetric matrix with zeros on its diagonal, the kind that needs the matching of
+    Sec. 3.1 before an incomplete factorization.  The solution x is unchanged."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    order = rng.permutation(w.A.n)
+    counts = np.diff(w.A.rowptr)[order]
+    rowptr = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    take = np.concatenate([np.arange(w.A.rowptr[i], w.A.rowptr[i + 1]) for i in order]) if w.A.n else np.zeros(0, int)
+    A = CSR(w.A.n, rowptr, w.A.colind[take].astype(np.int32), w.A.val[take].astype(np.float64))
+    return dataclasses.replace(w, name=w.name + "_rows_scrambled", A=A, b=w.b[order].copy())
+
+
 def cd_batch(count: int = 64, seed0: int = 100, n_lo: float = 1e4, n_hi: float = 2e5, block: int = 64):
     """Batch of uneven convection-diffusion matrices.  Matrix k has seed seed0 + k: even seeds
     give 2D 5-point, odd seeds 3D 7-point upwind problems; the target size is log-uniform in

@@ -37,3 +37,58 @@ def test_argument_defaults():
         sys.argv = old
     assert a.gpus == 1 and a.impl == "gpu" and a.warmup >= 3 and 1 <= a.steps <= 10
     assert a.side == 64 and a.block == 64 and a.workload == "cd3d" and a.precision == "fp64"
+
+
+def _args(**kw):
+    import argparse
+    base = dict(side=8, block=8, workload="cd3d", mwm=False, blocking="fixed", order="natural")
+    base.update(kw)
+    return argparse.Namespace(**base)
+
+
+import pytest  # noqa: E402
+
+
+@pytest.mark.parametrize("kw", [
+    {},
+    {"order": "nd"},
+    {"blocking": "cosine"},
+    {"blocking": "cosine+ilu1t", "workload": "elasticity", "side": 3, "block": 9},
+    {"blocking": "ilu1t", "order": "nd"},
+    {"workload": "cd3d_rows_scrambled", "mwm": True},
+    {"workload": "cd3d_rows_scrambled", "mwm": True, "order": "nd"},
+])
+def test_preprocessed_system_maps_back(kw):
+    """The prepared system (matching, cosine blocking, ILU(1,tau), nested dissection as
+    asked), solved exactly and mapped back, solves the original A x = b; its partition is
+    valid and the default leaves the workload untouched."""
+    import numpy as np
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    sys.path.insert(0, ROOT)
+    import bench
+    args = _args(**kw)
+    w = bench.workload(args)
+    prep = bench.preprocess(args, w)
+    if not kw:
+        assert prep.A is w.A and prep.bstart is None and not prep.steps
+    Ap = sp.csr_matrix((prep.A.val, prep.A.colind, prep.A.rowptr), shape=(w.A.n, w.A.n)).tocsc()
+    y = spla.spsolve(Ap, prep.b)
+    x = prep.to_original(y)
+    A0 = sp.csr_matrix((w.A.val, w.A.colind, w.A.rowptr), shape=(w.A.n, w.A.n))
+    assert np.linalg.norm(A0 @ x - w.b) <= 1e-9 * np.linalg.norm(w.b)
+    if prep.bstart is not None:
+        bs = np.asarray(prep.bstart)
+        assert bs[0] == 0 and bs[-1] == w.A.n and np.all(np.diff(bs) >= 1) and np.diff(bs).max() <= 64
+    if kw.get("mwm"):
+        assert np.allclose(np.abs(Ap.diagonal()), 1.0, atol=1e-12)
+
+
+def test_reference_arm_with_host_analysis():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--workload", "cd3d_rows_scrambled", "--mwm", "--order", "nd", "--side", "8",
+                          "--block", "8", "--steps", "1", "--warmup", "1"], capture_output=True, text=True,
+                         timeout=300, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    d = json.loads([l for l in out.stdout.splitlines() if l.startswith("{")][0])
+    assert d["config"]["host_analysis"] == ["mwm", "nd"] and d["config"]["gmres_iters"] > 0
