@@ -47,6 +47,17 @@ def test_library_cosine_blocking_matches_oracle(name, tau, max_block):
     assert np.all(np.diff(b) >= 1) and np.all(np.diff(b) <= max_block)
 
 
+def test_larger_matrices_match_oracle():
+    """Scrambled Q1 elasticity on a 7^3 grid (1,029 unknowns, rows of up to 81 entries) and the
+    4-unknown 27-point operator on 5^3 nodes."""
+    el = W.elasticity3d(side=7, seed=2, block=63).A
+    l27 = W.laplace27_4dof(side=5, seed=3, block=64).A
+    for A in (permuted(el, np.random.default_rng(8).permutation(el.n).astype(np.int32)), l27):
+        p, b = B.bilu_cosine_blocking(A.n, A.rowptr, A.colind, 0.8, 64)
+        po, bo = C.cosine_blocking(A, 0.8, 64)
+        assert np.array_equal(p, po) and np.array_equal(b, bo)
+
+
 def test_empty_matrix():
     p, b = B.bilu_cosine_blocking(0, np.zeros(1, np.int64), np.zeros(0, np.int32))
     assert p.size == 0 and list(b) == [0]

@@ -62,6 +62,19 @@ def test_block_etree_matches_oracle(name):
         assert height == h.max()
 
 
+def test_larger_grids_match_oracle():
+    """Line blocks of 16^3 and 12 x 20 x 24 convection-diffusion grids (256 and 240 blocks)."""
+    for A, b in ((W.convdiff_upwind((16, 16, 16), seed=1), 16), (W.convdiff_upwind((12, 20, 24), seed=2), 12)):
+        bs = _bs(A, b)
+        got = B.bilu_nd_order(A.n, A.rowptr, A.colind, bs)
+        want = N.nd_order(A, bs)
+        for g, w in zip(got, want):
+            assert np.array_equal(g, w)
+        Ap = permuted(A, got[0])
+        parent, height = B.bilu_block_etree(Ap.n, Ap.rowptr, Ap.colind, got[1])
+        assert np.array_equal(parent, N.block_etree(Ap, got[1]))
+
+
 def test_nd_and_etree_errors():
     A = pattern_matrix([{0, 1}, {0, 1, 2}, {1, 2}])
     with pytest.raises(B.BiluError, match="partition"):
