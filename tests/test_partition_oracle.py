@@ -140,3 +140,14 @@ def test_blocks_are_unions_of_groups():
     groups = np.arange(0, w.A.n + 1, 3)
     bs = O.partition_ilu1t_groups(w.A, 1e-2, 64, groups)
     assert set(bs) <= set(groups) and np.diff(bs).max() <= 63 and bs[-1] == w.A.n
+
+
+def test_group_arguments_are_checked():
+    A = W.from_dense(np.eye(6) * 3.0)
+    for groups in ([0, 3, 5], [1, 6], [0, 3, 3, 6], [0, 6]):
+        mb = 4 if groups == [0, 6] else 64
+        try:
+            O.partition_ilu1t_groups(A, 1e-2, mb, groups)
+        except ValueError:
+            continue
+        raise AssertionError(f"groups {groups} accepted")
