@@ -114,11 +114,12 @@ typedef struct {
 } bilu_stats_t;
 
 /* Fills *p with the defaults: FIXED blocking of 32 (max 64), tau_analyze 1e-2,
- * perturbation on with tau 1e-2 and rho 1e-1 (Sec. 3.6), FP64, no skipping. */
+ * perturbation on with tau 1e-2 and rho 1e-1 (Sec. 3.6), FP64, no skipping.
+ * Errors: BILU_ERR_ARG (p NULL). */
 bilu_status bilu_params_default(bilu_params *p);
 
-/* Creates a context on CUDA device `device`, issuing work on `cuda_stream` (a
- * cudaStream_t).  NULL makes the context create and own a private non-blocking stream
+/* Creates a context (the library's runtime state; no counterpart in the paper) on CUDA
+ * device `device`, issuing work on `cuda_stream` (a cudaStream_t).  NULL makes the context create and own a private non-blocking stream
  * (the solver captures CUDA graphs, which the legacy default stream does not allow).
  * Errors: BILU_ERR_ARG (no such device), BILU_ERR_CUDA (device lacks cooperative launch). */
 bilu_status bilu_create(bilu_ctx **ctx, int device, void *cuda_stream);
@@ -158,7 +159,10 @@ bilu_status bilu_apply(bilu_ctx *ctx, const double *r, double *z);
  * Restarted GMRES(restart), right preconditioned with M (Sec. 4 uses GMRES(30)):
  * solves A x = b; x holds x0 on entry and the solution on exit.  Stops when the Givens
  * residual estimate is <= tol ||b|| and the true residual ||b - A x|| <= tol ||b||, or
- * after maxit inner steps (BILU_NOT_CONVERGED).  info may be NULL.
+ * after maxit inner steps (BILU_NOT_CONVERGED).  info may be NULL.  b and x hold n doubles,
+ * device or host memory.  Errors: BILU_ERR_STATE (no factor), BILU_ERR_ARG (null vector,
+ * restart outside 1..1000, maxit < 0, tol < 0 or NaN), BILU_ERR_OOM, BILU_ERR_CUDA,
+ * BILU_ERR_TIMEOUT (a device-side wait gave up).
  */
 bilu_status gmres_solve(bilu_ctx *ctx, const double *b, double *x, double tol, int32_t restart,
                         int32_t maxit, gmres_info *info);
@@ -188,10 +192,13 @@ bilu_status bilu_factor_batch(bilu_ctx *const *ctxs, int32_t count, double dropt
 bilu_status gmres_solve_batch(bilu_ctx *const *ctxs, int32_t count, const double *const *b, double *const *x,
                               double tol, int32_t restart, int32_t maxit, gmres_info *info);
 
-/* Statistics of the last analysis / factorization (fill, block sizes, work). */
+/* Statistics of the last analysis / factorization (fill, block sizes, the algorithmic work
+ * of Algorithm 1 with blocks, Sec. 2.2, as counted on the device) into *out (caller-owned).
+ * Errors: BILU_ERR_ARG (NULL), BILU_ERR_STATE (no analysis). */
 bilu_status bilu_stats(bilu_ctx *ctx, bilu_stats_t *out);
 
-/* Copies the partition to host memory: bstart[nblocks + 1] (nblocks from bilu_stats). */
+/* Copies the block partition (Sec. 3.4 or fixed) to host memory: bstart[nblocks + 1]
+ * (caller-owned; nblocks from bilu_stats).  Errors: BILU_ERR_ARG (NULL), BILU_ERR_STATE. */
 bilu_status bilu_get_partition(bilu_ctx *ctx, int32_t *bstart);
 
 /*
@@ -200,7 +207,10 @@ bilu_status bilu_get_partition(bilu_ctx *ctx, int32_t *bstart);
  *   Lval[nnz_l] per block kept_rows_K x b_K row-major (rows of unit L);
  *   Uptr[nb+1]; Ucol[kept_cols]; Uval[nnz_u] per block kept_cols_K x b_K, entry (q,t) =
  *   U-breve(s_K + t, Ucol[q]); Dinv[nnz_d] per block b_K x b_K row-major (D_K = P_K^{-1});
- *   Pblk[nnz_d] the updated pivot blocks P_K.  Any pointer may be NULL.
+ *   Pblk[nnz_d] the updated pivot blocks P_K.  Any pointer may be NULL.  All host arrays,
+ *   caller-owned, sized from bilu_stats; the factor is A ~ L D^{-1} U of Sec. 2.2 with
+ *   L D^{-1} U = L U-breve.  Reduced-precision factors are widened to FP64.
+ * Errors: BILU_ERR_ARG (NULL context), BILU_ERR_STATE (no factor), BILU_ERR_CUDA.
  */
 bilu_status bilu_export(bilu_ctx *ctx, int64_t *Lptr, int32_t *Lrow, double *Lval, int64_t *Uptr,
                         int32_t *Ucol, double *Uval, double *Dinv, double *Pblk);
@@ -267,7 +277,8 @@ bilu_status bilu_mwm(int64_t n, const int64_t *rowptr, const int32_t *colind, co
  * B[k][l] = dl[r_k] * A[r_k][c_l] * dr[c_l] on the host, with r_k = rowperm[k] and
  * c_l = colperm[l] (a NULL permutation is the identity, a NULL scaling is 1): rowperm = NULL,
  * colperm = sigma and the scalings of bilu_mwm give A^ = D_l A D_r Pi; rowperm = colperm = Q
- * and no scaling give Q^T A Q.  Output arrays as in bilu_permute_csr (rows sorted).
+ * and no scaling give Q^T A Q (the reorderings of Sec. 3.1-3.3).  Output arrays as in
+ * bilu_permute_csr (rows sorted).
  * Errors: BILU_ERR_ARG (malformed CSR, a permutation that is not one, null array).
  */
 bilu_status bilu_scale_permute_csr(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val,
@@ -293,7 +304,9 @@ bilu_status bilu_nd_order(int64_t n, const int64_t *rowptr, const int32_t *colin
 /*
  * Block elimination tree, host only: parent[K] (-1 for a root) for the blocks bstart of A in
  * their given order, from the symmetrised companion graph with the fill of block elimination
- * (each block's later neighbours become a clique; its parent is the first of them).  Every
+ * (each block's later neighbours become a clique; its parent is the first of them).
+ * Outputs caller-owned (parent[nblocks], *height).  Errors: BILU_ERR_ARG (malformed pattern or
+ * partition, NULL output), message in bilu_last_error(NULL).  Every
  * block J whose factor entries update block K (a kept row of L_J or column of U-breve_J
  * inside B_K, Algorithm 1 with blocks, Sec. 2.2) is a descendant of K, so K depends only on
  * its subtree; *height is the number of blocks on the longest leaf-to-root path (the critical
@@ -357,7 +370,8 @@ enum {
 bilu_status bilu_debug_set(bilu_ctx *ctx, int32_t what, int64_t value);
 
 /*
- * bilu_apply without any device allocation.  The paper has no counterpart: this entry point
+ * bilu_apply (Sec. 2.2: block forward / backward substitution) without any device
+ * allocation.  The paper has no counterpart for the no-allocation constraint: this entry point
  * serves callers that cannot allocate device memory when they apply the preconditioner --
  * code running while a CUDA graph is being captured, programs whose device memory belongs
  * to a fixed pool or to another framework's allocator, real-time loops that must not enter
@@ -425,7 +439,9 @@ typedef struct {
  * cap or NULL; host or device memory) and the number held in *count.  A tag identifies the
  * candidate: K * 2^33 + side * 2^32 + its global row (side 0) or column (side 1) index.
  * Sample order is not deterministic; a factorization that re-runs with grown storage keeps
- * only the samples of its final run.
+ * only the samples of its final run.  (The paper computes every candidate; the learned skip
+ * predicts its drop rule, Sec. 2.2.)  Errors: BILU_ERR_ARG (capacity < 0, rate outside
+ * [0, 1]; count NULL, cap < 0, or x / y NULL with cap > 0), BILU_ERR_OOM, BILU_ERR_CUDA.
  */
 bilu_status bilu_record_samples(bilu_ctx *ctx, int64_t capacity, double rate, uint64_t seed);
 bilu_status bilu_get_samples(bilu_ctx *ctx, float *x, float *y, int64_t *tags, int64_t cap, int64_t *count);
@@ -437,23 +453,31 @@ bilu_status bilu_get_samples(bilu_ctx *ctx, float *x, float *y, int64_t *tags, i
  * weights whose FP16 roundings are used in the forward and backward passes.  Deterministic
  * for a given seed.  Writes the model (host, BILU_MLP_PARAMS) and, if final_loss is not NULL,
  * the mean cross-entropy over all n samples at the end.  Runs on ctx's device and stream
- * (ctx needs no matrix); synchronizes.
+ * (ctx needs no matrix); synchronizes.  Errors: BILU_ERR_ARG (NULL array, n < 1, a
+ * configuration out of range), BILU_ERR_OOM, BILU_ERR_CUDA.
  */
 bilu_status bilu_mlp_train(bilu_ctx *ctx, const float *x, const float *y, int64_t n, const bilu_mlp_train_cfg *cfg,
                            float *model, double *final_loss);
 
-/* Logits of n samples (x host or device; logits host or device, n entries). */
+/* Logits of n samples (x host or device; logits host or device, n entries).
+ * Errors: BILU_ERR_ARG (NULL array, n < 0, a model with non-finite entries or std <= 0),
+ * BILU_ERR_OOM, BILU_ERR_CUDA. */
 bilu_status bilu_mlp_forward(bilu_ctx *ctx, const float *model, const float *x, int64_t n, float *logits);
 
 /* Gradient of the mean cross-entropy over n samples with respect to the model entries
- * (host, BILU_MLP_PARAMS; zero for mean and std), at the FP16-rounded weights. */
+ * (host, BILU_MLP_PARAMS; zero for mean and std), at the FP16-rounded weights.
+ * Errors: BILU_ERR_ARG (NULL array, n outside 1..65536, an invalid model), BILU_ERR_OOM,
+ * BILU_ERR_CUDA. */
 bilu_status bilu_mlp_grad(bilu_ctx *ctx, const float *model, const float *x, const float *y, int64_t n, float *grad);
 
 /* Installs the model used by BILU_SKIP_LEARNED factorizations of ctx: a candidate is skipped
- * when its logit is >= logit_hi (the pivot rows of a block are never skipped). */
+ * when its logit is >= logit_hi (the pivot rows of a block are never skipped).  The model
+ * (host, BILU_MLP_PARAMS) is copied.  Errors: BILU_ERR_ARG (NULL model, non-finite logit_hi,
+ * an invalid model), BILU_ERR_OOM, BILU_ERR_CUDA. */
 bilu_status bilu_set_skip_model(bilu_ctx *ctx, const float *model, double logit_hi);
 
-/* Releases the context and all device memory it owns.  NULL is ignored. */
+/* Releases the context and all device memory it owns (synchronizing its stream first).
+ * NULL is ignored; no status. */
 void bilu_destroy(bilu_ctx *ctx);
 
 #ifdef __cplusplus
