@@ -205,6 +205,7 @@ def _check(ctx, st: int, allow=(BILU_OK,)):
 
 
 def bilu_params_default(**overrides) -> bilu_params:
+    """The library defaults (bilu_params_default), with the given fields overridden."""
     p = bilu_params()
     lib().bilu_params_default(ct.byref(p))
     for k, v in overrides.items():
@@ -225,11 +226,13 @@ def bilu_create(device: int = 0, stream=None):
 
 
 def bilu_destroy(ctx):
+    """Releases the context and its device memory."""
     _CTX_N.pop(_ctx_key(ctx), None)
     lib().bilu_destroy(ctx)
 
 
 def bilu_last_error(ctx) -> str:
+    """The last error message of ctx (None: this thread's context-free calls)."""
     return lib().bilu_last_error(ctx).decode()
 
 
@@ -415,6 +418,7 @@ def bilu_permute_csr(n: int, rowptr, colind, val, perm):
 
 
 def bilu_factor(ctx, droptol: float) -> int:
+    """Numeric block Crout ILU (Algorithm 1 with blocks, Sec. 2.2); returns BILU_OK or BILU_PERTURBED."""
     st = lib().bilu_factor(ctx, droptol)
     return _check(ctx, st, (BILU_OK, BILU_PERTURBED))
 
@@ -424,6 +428,7 @@ def _vec(ctx, v, name):
 
 
 def bilu_apply(ctx, r, z) -> int:
+    """z = M^{-1} r (float64, n entries each, host or device; r and z distinct)."""
     st = lib().bilu_apply(ctx, _vec(ctx, r, "r"), _vec(ctx, z, "z"))
     return _check(ctx, st)
 
@@ -435,6 +440,7 @@ def bilu_apply_noalloc(ctx, r, z) -> int:
 
 
 def gmres_solve(ctx, b, x, tol: float = 1e-8, restart: int = 30, maxit: int = 10000) -> gmres_info:
+    """Right-preconditioned GMRES(restart) (Sec. 4); x holds x0 on entry.  The info carries the status."""
     info = gmres_info()
     st = lib().gmres_solve(ctx, _vec(ctx, b, "b"), _vec(ctx, x, "x"), tol, restart, maxit, ct.byref(info))
     _check(ctx, st, (BILU_OK, BILU_NOT_CONVERGED))
@@ -464,12 +470,14 @@ def gmres_solve_batch(ctxs, bs, xs, tol: float = 1e-8, restart: int = 30, maxit:
 
 
 def bilu_stats(ctx) -> bilu_stats_t:
+    """Statistics of the last analysis / factorization."""
     s = bilu_stats_t()
     _check(ctx, lib().bilu_stats(ctx, ct.byref(s)))
     return s
 
 
 def bilu_get_partition(ctx, out):
+    """Copies the block starts into out (int32, nblocks + 1)."""
     s = bilu_stats(ctx)
     return _check(ctx, lib().bilu_get_partition(ctx, _buf(out, "int32", s.nblocks + 1, "bstart")))
 
@@ -486,6 +494,7 @@ def bilu_export(ctx, Lptr=None, Lrow=None, Lval=None, Uptr=None, Ucol=None, Uval
 
 
 def bilu_debug_set(ctx, what: int, value: int):
+    """Test hooks of the failure paths (BILU_DEBUG_*); not for production use."""
     return _check(ctx, lib().bilu_debug_set(ctx, what, value))
 
 
@@ -520,6 +529,7 @@ def bilu_mlp_train(ctx, x, y, epochs: int = 4, batch: int = 4096, lr: float = 2e
 
 
 def bilu_mlp_forward(ctx, model, x, logits):
+    """Logits of the samples x (n x 12 float32) into logits (n float32)."""
     n = int(logits.shape[0])
     return _check(ctx, lib().bilu_mlp_forward(ctx, _buf(model, "float32", BILU_MLP_PARAMS, "model"),
                                               _buf(x, "float32", n * BILU_MLP_FEATURES, "x"), n,
@@ -527,6 +537,7 @@ def bilu_mlp_forward(ctx, model, x, logits):
 
 
 def bilu_mlp_grad(ctx, model, x, y):
+    """Gradient of the mean cross-entropy with respect to the model (float32, BILU_MLP_PARAMS)."""
     import numpy as np
     n = int(y.shape[0])
     g = np.zeros(BILU_MLP_PARAMS, np.float32)
@@ -537,4 +548,5 @@ def bilu_mlp_grad(ctx, model, x, y):
 
 
 def bilu_set_skip_model(ctx, model, logit_hi: float):
+    """Installs the classifier for BILU_SKIP_LEARNED: candidates with logit >= logit_hi are skipped."""
     return _check(ctx, lib().bilu_set_skip_model(ctx, _buf(model, "float32", BILU_MLP_PARAMS, "model"), logit_hi))
