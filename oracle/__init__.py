@@ -7,6 +7,12 @@ product never imports it.
 
 Paper: Bollhoefer, Schenk, Verbosio, "High Performance Block Incomplete LU
 Factorization", arXiv:1908.10169 (Algorithm 1, Sec. 2.2, Sec. 3.4, Sec. 3.6, Sec. 4).
+
+The other modules of this package are plain Python / numpy references of the remaining
+parts: ``mwm_oracle`` (matching + scaling, Sec. 3.1), ``cosine_oracle`` (cosine blocking,
+Sec. 3.2), ``nd_oracle`` (block nested dissection and elimination tree, Sec. 3.3),
+``block_check`` (one block step of Sec. 2.2 from a given factor) and ``skip_oracle`` (the
+learned skip's features and classifier).
 """
 from __future__ import annotations
 
