@@ -1,0 +1,61 @@
+// Random-input stress of the library's host analysis (Sec. 3.1-3.4 helpers), built with the
+// address and undefined-behaviour sanitizers by tests/test_host_analysis_sanitizers.py.  Only host
+// code runs; the stubs stand for the device-side symbols analyze.cu refers to but never reaches here.
+#include <cstdio>
+#include <random>
+#include <string>
+#include <vector>
+#include "bilu_internal.h"
+
+// stubs for symbols analyze.cu references but this driver never calls
+void factor_free(bilu_ctx *) {}
+void apply_free(bilu_ctx *) {}
+void gmres_free(bilu_ctx *) {}
+bilu_status set_err(bilu_ctx *, bilu_status st, const std::string &) { return st; }
+bilu_status cuda_err(bilu_ctx *, cudaError_t, const char *) { return BILU_ERR_CUDA; }
+
+int main() {
+    std::mt19937_64 rng(1);
+    long checked = 0;
+    for (int trial = 0; trial < 3000; ++trial) {
+        const int n = (int)(rng() % 40);
+        const double dens = std::vector<double>{0.0, 0.05, 0.2, 0.6, 1.0}[rng() % 5];
+        std::vector<int64_t> rp(n + 1, 0);
+        std::vector<int32_t> ci;
+        std::vector<double> va;
+        std::uniform_real_distribution<double> U(-2, 2), Pr(0, 1);
+        const bool diag = rng() % 2;
+        for (int i = 0; i < n; ++i) {
+            for (int j = 0; j < n; ++j)
+                if ((diag && i == j) || Pr(rng) < dens) { ci.push_back(j); va.push_back(i == j ? 4.0 : U(rng)); }
+            rp[i + 1] = (int64_t)ci.size();
+        }
+        std::string err;
+        const int mb = 1 + (int)(rng() % 64);
+        std::vector<int32_t> perm(n + 1), bs(n + 2), order(n + 1), parent(n + 1), sigma(n + 1);
+        std::vector<double> dl(n + 1), dr(n + 1);
+        int32_t nb = 0, h = 0;
+        cosine_blocking_host(n, rp.data(), ci.data(), Pr(rng), mb, perm.data(), bs.data(), &nb, &err);
+        partition_ilu1t_host(n, rp.data(), ci.data(), va.data(), Pr(rng) * 0.3, mb, nb, bs.data(), order.data(), &h,
+                             &err);
+        partition_ilu1t_host(n, rp.data(), ci.data(), va.data(), 1e-2, mb, -1, nullptr, order.data(), &h, &err);
+        std::vector<int64_t> orp(n + 1);
+        std::vector<int32_t> oci(ci.size() + 1);
+        std::vector<double> ova(va.size() + 1);
+        permute_csr_host(n, rp.data(), ci.data(), va.data(), perm.data(), orp.data(), oci.data(), ova.data(), &err);
+        // partition for the dissection: blocks of random width
+        std::vector<int32_t> part{0};
+        while (part.back() < n) part.push_back(std::min(n, part.back() + 1 + (int)(rng() % 4)));
+        const int32_t np = (int32_t)part.size() - 1;
+        std::vector<int32_t> pbs(np + 1), pord(np + 1);
+        nd_order_host(n, rp.data(), ci.data(), np, part.data(), 1 + (int)(rng() % 3), perm.data(), pbs.data(),
+                      pord.data(), &err);
+        block_etree_host(n, rp.data(), ci.data(), np, part.data(), parent.data(), &h, &err);
+        mwm_host(n, rp.data(), ci.data(), va.data(), sigma.data(), dl.data(), dr.data(), &err);
+        scale_permute_csr_host(n, rp.data(), ci.data(), va.data(), perm.data(), perm.data(), dl.data(), dr.data(),
+                               orp.data(), oci.data(), ova.data(), &err);
+        ++checked;
+    }
+    std::printf("ok %ld trials\n", checked);
+    return 0;
+}
