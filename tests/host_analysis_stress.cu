@@ -2,6 +2,7 @@
 // address and undefined-behaviour sanitizers by tests/test_host_analysis_sanitizers.py.  Only host
 // code runs; the stubs stand for the device-side symbols analyze.cu refers to but never reaches here.
 #include <cstdio>
+#include <limits>
 #include <random>
 #include <string>
 #include <vector>
@@ -54,6 +55,33 @@ int main() {
         mwm_host(n, rp.data(), ci.data(), va.data(), sigma.data(), dl.data(), dr.data(), &err);
         scale_permute_csr_host(n, rp.data(), ci.data(), va.data(), perm.data(), perm.data(), dl.data(), dr.data(),
                                orp.data(), oci.data(), ova.data(), &err);
+        // analysis: validation, CSC copy and partition run on the host; the device upload that
+        // follows fails where there is no GPU (or succeeds where there is one)
+        {
+            bilu_ctx ctx;
+            bilu_params p{};
+            p.blocking = (int32_t)(rng() % 2);
+            p.max_block = mb;
+            p.fixed_block = 1 + (int32_t)(rng() % mb);
+            p.tau_analyze = 1e-2;
+            p.perturb = 1;
+            p.pert_tau = 1e-2;
+            p.pert_rho = 1e-1;
+            std::vector<int32_t> ci2(ci);
+            std::vector<double> va2(va);
+            const int corrupt = (int)(rng() % 6);
+            if (corrupt == 1 && ci2.size() > 1) std::swap(ci2[0], ci2[1]);
+            if (corrupt == 2 && !va2.empty()) va2[0] = std::numeric_limits<double>::quiet_NaN();
+            if (corrupt == 3 && !ci2.empty()) ci2.back() = n + 3;
+            if (corrupt == 4) {  // a caller's partition, merged or not
+                std::vector<int32_t> g{0};
+                while (g.back() < n) g.push_back(std::min(n, g.back() + 1 + (int)(rng() % mb)));
+                analyze_run(&ctx, n, rp.data(), ci2.data(), va2.data(), 0, &p, g.data(), (int32_t)g.size() - 1);
+            } else {
+                analyze_run(&ctx, n, rp.data(), ci2.data(), va2.data(), 0, &p);
+            }
+            matrix_free(&ctx);
+        }
         ++checked;
     }
     std::printf("ok %ld trials\n", checked);

@@ -1,4 +1,4 @@
-"""The library's host analysis (cosine blocking, ILU(1,tau) partition, permutation, nested
+"""The library's host analysis (analysis validation and partitioning, cosine blocking, ILU(1,tau), permutation, nested
 dissection, elimination tree, matching, scale-and-permute) built with the address and
 undefined-behaviour sanitizers and run on 3,000 random patterns (empty and full rows,
 structurally singular matrices, random block and group sizes): no invalid access, no undefined
