@@ -1,6 +1,7 @@
-"""The library's host analysis (analysis validation and partitioning, cosine blocking, ILU(1,tau), permutation, nested
-dissection, elimination tree, matching, scale-and-permute) built with the address and
-undefined-behaviour sanitizers and run on 3,000 random patterns (empty and full rows,
+"""The library's host analysis (the analysis entry's validation and partitioning, cosine
+blocking, ILU(1,tau), permutation, nested dissection, elimination tree, matching,
+scale-and-permute) built with the address and undefined-behaviour sanitizers and run on 3,000
+random patterns (empty and full rows, corrupted inputs,
 structurally singular matrices, random block and group sizes): no invalid access, no undefined
 behaviour, no leak.  Host code only; skipped where nvcc or g++ is missing."""
 import os
