@@ -92,3 +92,40 @@ def test_reference_arm_with_host_analysis():
     assert out.returncode == 0, out.stderr[-2000:]
     d = json.loads([l for l in out.stdout.splitlines() if l.startswith("{")][0])
     assert d["config"]["host_analysis"] == ["mwm", "nd"] and d["config"]["gmres_iters"] > 0
+
+
+def test_clock_summary_parses_samples_and_reasons(tmp_path):
+    """nvidia-smi rows (index, sm MHz, max MHz, power, active mask, hw_slowdown,
+    hw_thermal_slowdown, sw_thermal_slowdown, sw_power_cap): median and maximum clocks, the
+    reasons seen Active in any sample; rows that do not parse are skipped."""
+    sys.path.insert(0, ROOT)
+    import bench
+    c = bench.ClockSampler(0)
+    c.path = str(tmp_path / "clocks.csv")
+    with open(c.path, "w") as f:
+        f.write("0, 1965, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active\n")
+        f.write("0, 1980, 2070, 1300.0, 0x4, Not Active, Not Active, Not Active, Active\n")
+        f.write("0, 2010, 2070, 1100.0, 0x0, Not Active, Not Active, Not Active, Not Active\n")
+        f.write("garbage line\n")
+    s = c.summary()
+    assert s["sm_mhz"] == 1980 and s["sm_max_mhz"] == 2070 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap"]
+    c.path = str(tmp_path / "missing.csv")
+    assert c.summary()["sm_mhz"] is None
+
+
+def test_traffic_figures_only_while_sources_match(tmp_path, monkeypatch):
+    """The committed ncu traffic per stored value is used only while the kernel sources hash
+    to what was captured; after a change the figure is dropped (the bench reports null)."""
+    import hashlib
+    sys.path.insert(0, ROOT)
+    import bench
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "k.cu").write_text("kernel v1")
+    sha = hashlib.sha256(b"kernel v1").hexdigest()[:16]
+    (tmp_path / "profiles" / "ncu_traffic.json").write_text(json.dumps(
+        {"note": "x", "my_kernel": {"bytes_per_factor_value": 8.5, "source_sha": sha, "sources": ["k.cu"]}}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.load_traffic() == {"my_kernel": 8.5}
+    (tmp_path / "k.cu").write_text("kernel v2")
+    assert bench.load_traffic() == {}
