@@ -1,7 +1,12 @@
-// Analysis: validation and copy of A, its CSC copy, block partition (host side).
+// Analysis (host side): validation and copy of A, its CSC copy, the block partition, and the
+// preprocessing of Sec. 3.
 //
 // Sec. 2.1: the Crout ILU needs A by rows and by columns, so a CSC copy is built once.
-// Sec. 3.4: the block partition is either fixed-size or the simplified ILU(1,tau) guess.
+// Sec. 3.4: the block partition is fixed-size, the simplified ILU(1,tau) guess (column by
+//           column or over given groups), or the caller's.
+// Sec. 3.1: maximum weight matching with scaling (mwm_host) and the scale-and-permute step.
+// Sec. 3.2: cosine-based blocking (cosine_blocking_host) and symmetric permutation.
+// Sec. 3.3: block nested dissection (nd_order_host) and the block elimination tree.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
