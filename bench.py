@@ -22,7 +22,8 @@ one graph per GMRES cycle, sharded over the ranks under torchrun), --mwm / --blo
 cosine|cosine+ilu1t|ilu1t / --order nd (the host analysis of Sec. 3.1-3.4 before the factorization,
 outside the timed region and inside the end-to-end time; --workload cd3d_rows_scrambled is the
 benchmark matrix with its equations in random order, which needs --mwm). Under torchrun the
-single-matrix line runs one replica per rank; the reference arm runs on rank 0 only.
+single-matrix line runs one replica per rank; the reference arm runs on rank 0 only (with
+--batch it times the oracle on every 16th system and scales by the batch's unknowns).
 """
 from __future__ import annotations
 
@@ -312,10 +313,50 @@ def cpu_desc():
     return cores, model
 
 
+def run_reference_batch(args):
+    """Reference arm of the batched line: the oracle (factor + GMRES) on a fixed sample of the
+    batch's systems (every 16th, at least 2), scaled to the whole batch by its total number of
+    unknowns (the oracle's time per system grows about linearly with n on these stencils)."""
+    import oracle as O
+    from paper_1908_10169_gb300 import workloads as W
+    oracle_cores, model = cpu_desc()
+    ws = W.cd_batch(count=args.batch, seed0=100)
+    sample = list(range(0, len(ws), 16))
+    if len(sample) < 2 and len(ws) > 1:
+        sample.append(len(ws) - 1)
+    small = W.cd3d(side=12, seed=1, block=12)
+    for _ in range(args.warmup):
+        oracle_step(small, O.partition_fixed(small.A.n, 12))
+    n_all = sum(w.A.n for w in ws)
+    n_sample = sum(ws[i].A.n for i in sample)
+    times = []
+    for _ in range(args.steps):
+        t = 0.0
+        for i in sample:
+            w = ws[i]
+            t += oracle_step(w, O.partition_fixed(w.A.n, w.fixed_block))[0]
+        times.append(t * n_all / n_sample)
+    v = sum(times) / len(times)
+    line = {"impl": "reference", "metric": f"batched BILU factor+GMRES seconds for {len(ws)} systems to rel. residual 1e-8",
+            "value": v, "unit": "s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"cd_batch_{len(ws)}", "sum_n": int(n_all), "sample_systems": sample},
+            "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
+                             "sample": f"oracle factor + GMRES on systems {sample} ({n_sample} of {n_all} unknowns), "
+                                       f"scaled by unknowns to the whole batch; host {model}, {oracle_cores} cores "
+                                       f"visible, 1 used"},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
+    if getattr(args, "batch", 0):
+        return run_reference_batch(args)
     import oracle as O
     oracle_cores, model = cpu_desc()
     w = workload(args)

@@ -129,3 +129,14 @@ def test_traffic_figures_only_while_sources_match(tmp_path, monkeypatch):
     assert bench.load_traffic() == {"my_kernel": 8.5}
     (tmp_path / "k.cu").write_text("kernel v2")
     assert bench.load_traffic() == {}
+
+
+def test_reference_arm_batch_line():
+    """--impl reference --batch N: the oracle on a sample of the batch, scaled to all systems,
+    with the batched line's metric."""
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--batch", "3",
+                          "--steps", "1", "--warmup", "1"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    d = json.loads([l for l in out.stdout.splitlines() if l.startswith("{")][0])
+    assert d["impl"] == "reference" and d["metric"].startswith("batched") and d["value"] > 0
+    assert d["config"]["workload"] == "cd_batch_3" and d["config"]["sample_systems"] == [0, 2]
