@@ -379,7 +379,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config(args, w, {"gmres_iters": iters}),
+            "config": config(args, w, {"gmres_iters": iters, "updates": "fp64 (the oracle)", "skip": "none (the oracle)"}),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"full step (oracle factor + GMRES) on the same matrix; host {model}, "
                                        f"{oracle_cores} cores visible, 1 used"},
