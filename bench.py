@@ -43,6 +43,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "BILU factor+GMRES seconds to rel. residual 1e-8"
 UNIT = "s"
+REF_BUDGET_S = 150.0  # the reference arm's timed steps: full oracle steps while they fit in this
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12  # nominal: 152 SMs x 4 FP64 flop/clk/SM x 2070 MHz max SM clock
 
 
@@ -70,6 +71,10 @@ def parse():
                          "(Sec. 3.2), as they are or merged by the ILU(1,tau) rule")
     ap.add_argument("--order", choices=["natural", "nd"], default="natural",
                     help="nd: block nested dissection of the blocks (Sec. 3.3) before the factorization (host)")
+    ap.add_argument("--schedule", choices=["chain", "tree"], default="chain",
+                    help="tree: CTA groups factor independent subtrees of the block elimination tree "
+                         "(pays off with --order nd), the trunk on the whole GPU")
+    ap.add_argument("--group-ctas", type=int, default=0, help="tree schedule: CTAs per group (0: library default)")
     ap.add_argument("--batch", type=int, default=0,
                     help="factor + solve this many uneven 2D/3D matrices in one batched launch instead")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -197,6 +202,7 @@ def config(args, w, extra=None):
     c = {"workload": w.name, "n": w.A.n, "nnz": w.A.nnz, "droptol": w.droptol,
          "blocking": f"fixed {args.block}" if blocking == "fixed" else blocking, "gmres": f"GMRES({w.restart}) rtol {w.gmres_tol}, x0 = 0, b = A*1",
          "updates": getattr(args, "precision", "fp64"), "skip": getattr(args, "skip", "none"),
+         "order": getattr(args, "order", "natural"), "schedule": getattr(args, "schedule", "chain"),
          "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{args.gpus}"}
     pre = [k for k, on in (("mwm", getattr(args, "mwm", False)),
                            ("nd", getattr(args, "order", "natural") == "nd")) if on]
@@ -313,39 +319,52 @@ def cpu_desc():
     return cores, model
 
 
+def batch_sample(count):
+    """The batch systems the reference arm times: every 16th system of each kind (even index:
+    2D 5-point, odd index: 3D 7-point), so that both kinds are in the sample."""
+    evens, odds = list(range(0, count, 2)), list(range(1, count, 2))
+    return {"2d": evens[::16], "3d": odds[::16]}
+
+
 def run_reference_batch(args):
     """Reference arm of the batched line: the oracle (factor + GMRES) on a fixed sample of the
-    batch's systems (every 16th, at least 2), scaled to the whole batch by its total number of
-    unknowns (the oracle's time per system grows about linearly with n on these stencils)."""
+    batch's systems (every 16th system of each kind), each kind's time scaled to all systems of
+    that kind by their number of unknowns (the oracle's time per system grows about linearly
+    with n on these stencils, at a different rate for 2D and 3D)."""
     import oracle as O
     from paper_1908_10169_gb300 import workloads as W
     oracle_cores, model = cpu_desc()
     ws = W.cd_batch(count=args.batch, seed0=100)
-    sample = list(range(0, len(ws), 16))
-    if len(sample) < 2 and len(ws) > 1:
-        sample.append(len(ws) - 1)
+    kinds = batch_sample(len(ws))
+    sample = sorted(i for v in kinds.values() for i in v)
     small = W.cd3d(side=12, seed=1, block=12)
     for _ in range(args.warmup):
         oracle_step(small, O.partition_fixed(small.A.n, 12))
     n_all = sum(w.A.n for w in ws)
     n_sample = sum(ws[i].A.n for i in sample)
+    scale = {}
+    for k, idx in kinds.items():
+        members = range(0, len(ws), 2) if k == "2d" else range(1, len(ws), 2)
+        scale[k] = sum(ws[i].A.n for i in members) / max(1, sum(ws[i].A.n for i in idx))
     times = []
     for _ in range(args.steps):
         t = 0.0
-        for i in sample:
-            w = ws[i]
-            t += oracle_step(w, O.partition_fixed(w.A.n, w.fixed_block))[0]
-        times.append(t * n_all / n_sample)
+        for k, idx in kinds.items():
+            for i in idx:
+                w = ws[i]
+                t += oracle_step(w, O.partition_fixed(w.A.n, w.fixed_block))[0] * scale[k]
+        times.append(t)
     v = sum(times) / len(times)
     line = {"impl": "reference", "metric": f"batched BILU factor+GMRES seconds for {len(ws)} systems to rel. residual 1e-8",
             "value": v, "unit": "s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"cd_batch_{len(ws)}", "sum_n": int(n_all), "sample_systems": sample},
+            "config": {"workload": f"cd_batch_{len(ws)}", "sum_n": int(n_all), "sample_systems": sample,
+                       "sample_by_kind": kinds},
             "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
-                             "sample": f"oracle factor + GMRES on systems {sample} ({n_sample} of {n_all} unknowns), "
-                                       f"scaled by unknowns to the whole batch; host {model}, {oracle_cores} cores "
-                                       f"visible, 1 used"},
+                             "sample": f"oracle factor + GMRES on systems {sample} ({n_sample} of {n_all} unknowns; "
+                                       f"2D {kinds['2d']}, 3D {kinds['3d']}), each kind scaled by its unknowns to "
+                                       f"all systems of that kind; host {model}, {oracle_cores} cores visible, 1 used"},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -371,18 +390,40 @@ def run_reference(args):
     small = dataclasses.replace(small, A=sprep.A, b=sprep.b)
     for _ in range(args.warmup):  # warm-up on a small case of the same kind
         oracle_step(small, sprep.bstart if sprep.bstart is not None else O.partition_fixed(small.A.n, 16))
-    times, iters = [], 0
-    for _ in range(args.steps):
-        t, tf, tg, iters = oracle_step(w, bs)
-        times.append(t)
+    # one full step on the workload itself (the last warm-up step); when K of them would take
+    # longer than REF_BUDGET_S, every timed step is a bounded sample instead: the oracle's full
+    # step on the same kind of problem with 3/4 of the side, scaled by the ratio of the two
+    # measured once here
+    t_full, _, _, iters = oracle_step(w, bs)
+    sample_note = "full step (oracle factor + GMRES, FP64 arithmetic, every candidate computed) on the same matrix"
+    times = []
+    if t_full * args.steps <= REF_BUDGET_S:
+        times.append(t_full)
+        for _ in range(args.steps - 1):
+            t, tf, tg, iters = oracle_step(w, bs)
+            times.append(t)
+        times = times[:args.steps]
+    else:
+        side_s = max(8, (3 * args.side) // 4)
+        sa = argparse.Namespace(**{**vars(args), "side": side_s})
+        ws_ = workload(sa)
+        sp_ = preprocess(sa, ws_)
+        ws_ = dataclasses.replace(ws_, A=sp_.A, b=sp_.b)
+        bs_ = sp_.bstart if sp_.bstart is not None else O.partition_fixed(ws_.A.n, args.block)
+        t_cal = oracle_step(ws_, bs_)[0]
+        for _ in range(args.steps):
+            times.append(oracle_step(ws_, bs_)[0] * t_full / t_cal)
+        sample_note = (f"each timed step: the oracle's full step (factor + GMRES, FP64) on the {side_s}^3 problem of "
+                       f"the same kind and host analysis, scaled by t({args.side}^3) / t({side_s}^3) = "
+                       f"{t_full:.2f} s / {t_cal:.2f} s, both measured once before the timed steps (a full step on "
+                       f"the workload takes {t_full:.1f} s, {args.steps} of them would exceed {REF_BUDGET_S:.0f} s)")
     v = sum(times) / len(times)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config(args, w, {"gmres_iters": iters, "updates": "fp64 (the oracle)", "skip": "none (the oracle)"}),
+            "config": config(args, w, {"gmres_iters": iters}),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"full step (oracle factor + GMRES) on the same matrix; host {model}, "
-                                       f"{oracle_cores} cores visible, 1 used"},
+                             "sample": f"{sample_note}; host {model}, {oracle_cores} cores visible, 1 used"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -407,7 +448,9 @@ def run_gpu(args):
                                    precision={"fp64": B.BILU_PREC_FP64, "fp32": B.BILU_PREC_FP32,
                                               "bf16": B.BILU_PREC_BF16}[args.precision],
                                    skip={"none": B.BILU_SKIP_NONE, "bound": B.BILU_SKIP_BOUND,
-                                         "learned": B.BILU_SKIP_LEARNED}[args.skip])
+                                         "learned": B.BILU_SKIP_LEARNED}[args.skip],
+                                   schedule={"chain": B.BILU_SCHED_CHAIN, "tree": B.BILU_SCHED_TREE}[args.schedule],
+                                   group_ctas=args.group_ctas)
     learned = None
     if args.skip == "learned":  # train the classifier first (not timed)
         from paper_1908_10169_gb300 import learned_skip as LS
@@ -606,6 +649,12 @@ def run_gpu(args):
                                            "solve_ms": statistics.median(ts), "apply_ms": t_apply,
                                            "fill_nnz(L+U+D)/nnz(A)": (st.nnz_l + st.nnz_u + st.nnz_d) / w.A.nnz,
                                            "nblocks": st.nblocks,
+                                           **({"tree": {"height": st.tree_height, "trunk_blocks": st.tree_trunk,
+                                                        "group_ctas": st.group_ctas,
+                                                        "groups": (torch.cuda.get_device_properties(dev).multi_processor_count
+                                                                   // max(1, st.group_ctas)),
+                                                        "idle_ms_summed": round(st.idle_ms, 3)}}
+                                              if args.schedule == "tree" else {}),
                                            "factor_phase_ms": dict(zip(["candidates", "pivot_rows+lu", "inverse",
                                                                         "bound_skip_updates", "scale_drop", "compact",
                                                                         "cta0_lu_work", "cta0_pivot_tile_wait"],

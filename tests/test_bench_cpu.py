@@ -139,4 +139,17 @@ def test_reference_arm_batch_line():
     assert out.returncode == 0, out.stderr[-2000:]
     d = json.loads([l for l in out.stdout.splitlines() if l.startswith("{")][0])
     assert d["impl"] == "reference" and d["metric"].startswith("batched") and d["value"] > 0
-    assert d["config"]["workload"] == "cd_batch_3" and d["config"]["sample_systems"] == [0, 2]
+    assert d["config"]["workload"] == "cd_batch_3" and d["config"]["sample_systems"] == [0, 1]
+
+
+def test_batch_sample_covers_both_kinds():
+    """The batch alternates 2D (even index) and 3D (odd index) systems; the reference arm's
+    sample holds both kinds, every 16th of each."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1908_10169_gb300 import workloads as W
+    s = bench.batch_sample(64)
+    assert s == {"2d": [0, 32], "3d": [1, 33]}
+    ws = W.cd_batch(count=4, seed0=100)
+    assert "cd2d" in ws[0].name and "cd3d" in ws[1].name
+    assert bench.batch_sample(3) == {"2d": [0], "3d": [1]}
