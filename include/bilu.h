@@ -49,6 +49,7 @@ typedef enum {
 enum { BILU_BLOCKING_FIXED = 0, BILU_BLOCKING_ILU1T = 1 };
 enum { BILU_PREC_FP64 = 0, BILU_PREC_FP32 = 1, BILU_PREC_BF16 = 2 };
 enum { BILU_SKIP_NONE = 0, BILU_SKIP_BOUND = 1, BILU_SKIP_LEARNED = 2 };
+enum { BILU_SCHED_CHAIN = 0, BILU_SCHED_TREE = 1 };
 
 /* Maximum diagonal block size supported by the kernels. */
 #define BILU_MAX_BLOCK 64
@@ -71,6 +72,18 @@ typedef struct {
                             ||D_K||_2 <= ||D_K||_F); columns likewise.  Same factor as without.
                             BILU_SKIP_LEARNED: a classifier decides before the updates (see
                             bilu_set_skip_model); needs a model.                                */
+    int32_t schedule;    /* BILU_SCHED_CHAIN: the blocks are factored one after another by the
+                            whole GPU.  BILU_SCHED_TREE: the block elimination tree of the
+                            partition (see bilu_block_etree) is built by bilu_analyze, and groups
+                            of group_ctas CTAs factor independent subtrees side by side, each
+                            block after all of its children (every block that updates K lies in
+                            K's subtree, Sec. 3.3); the chain of single-child blocks at the top
+                            of the tree (the trunk) is then factored by the whole GPU.  Same
+                            factor, bit for bit, as BILU_SCHED_CHAIN on the same ordering.  It
+                            pays off on an ordering with independent subtrees (nested
+                            dissection, bilu_nd_order); in natural order the tree is a chain.
+                            Not with BILU_SKIP_LEARNED or sample recording (BILU_ERR_ARG).      */
+    int32_t group_ctas;  /* CTAs per group of BILU_SCHED_TREE, 1..number of SMs (0: 8)         */
 } bilu_params;
 
 typedef struct {
@@ -104,17 +117,24 @@ typedef struct {
     int64_t kernel_launches;  /* kernels of this library launched on the context so far
                                  (each node of a launched CUDA graph counts once)       */
     double phase_ms[8];       /* factorization time by phase, each up to the end of its
-                                 grid barrier: candidate sets; pivot-row updates + pivot
+                                 grid barrier (tree schedule: summed over the groups): candidate sets; pivot-row updates + pivot
                                  LU (other updates overlap); inverse; bound-tested
                                  updates (norm-bound skip only); scaling + dropping;
                                  compaction.  Then CTA 0's time inside the pivot LU and
                                  waiting for the pivot-row updates                      */
     int64_t skipped_rows;     /* candidate rows / columns skipped (norm bound proved them */
     int64_t skipped_cols;     /* dropped, or the classifier predicted it): not computed  */
+    int32_t schedule;         /* BILU_SCHED_* of the analysis                            */
+    int32_t tree_height;      /* BILU_SCHED_TREE: blocks on the longest leaf-to-root path */
+    int32_t tree_trunk;       /*   blocks of the trunk (factored by the whole GPU)        */
+    int32_t group_ctas;       /*   CTAs per group                                         */
+    double idle_ms;           /*   time the groups waited for a ready block, summed over
+                                   the groups (0 for the chain schedule)                 */
 } bilu_stats_t;
 
 /* Fills *p with the defaults: FIXED blocking of 32 (max 64), tau_analyze 1e-2,
- * perturbation on with tau 1e-2 and rho 1e-1 (Sec. 3.6), FP64, no skipping.
+ * perturbation on with tau 1e-2 and rho 1e-1 (Sec. 3.6), FP64, no skipping, the chain
+ * schedule (group_ctas 0).
  * Errors: BILU_ERR_ARG (p NULL). */
 bilu_status bilu_params_default(bilu_params *p);
 
@@ -358,6 +378,10 @@ bilu_status bilu_analyze_partition(bilu_ctx *ctx, int64_t n, const int64_t *rowp
  *       again with grown storage several times (the result does not change).
  *   BILU_DEBUG_POISON (value 0/1): every factorization first fills the factor's value
  *       arrays and work arrays with NaN, so that a value the kernels fail to write shows.
+ *   BILU_DEBUG_NO_TRUNK (value 0/1): the tree schedule factors every block in its CTA
+ *       groups, the trunk included (same factor), instead of the trunk on the whole grid.
+ *   BILU_DEBUG_TRACE (value 0/1): the tree schedule prints one line per factorization run
+ *       (status, storage sizes) to stderr.
  */
 enum {
     BILU_DEBUG_EXTRA_CTA = 1,
@@ -365,30 +389,33 @@ enum {
     BILU_DEBUG_SELFTEST_RECIP = 3,
     BILU_DEBUG_BATCH_GROUP = 4,
     BILU_DEBUG_SMALL_POOLS = 5,
-    BILU_DEBUG_POISON = 6
+    BILU_DEBUG_POISON = 6,
+    BILU_DEBUG_NO_TRUNK = 7,
+    BILU_DEBUG_TRACE = 8
 };
 bilu_status bilu_debug_set(bilu_ctx *ctx, int32_t what, int64_t value);
 
 /*
- * bilu_apply (Sec. 2.2: block forward / backward substitution) without any device
- * allocation.  The paper has no counterpart for the no-allocation constraint: this entry point
- * serves callers that cannot allocate device memory when they apply the preconditioner --
- * code running while a CUDA graph is being captured, programs whose device memory belongs
- * to a fixed pool or to another framework's allocator, real-time loops that must not enter
- * the allocator.  bilu_apply itself allocates nothing per call, but it relies on buffers
- * created with the factor and stages host vectors through buffers allocated on first use.
+ * bilu_apply's result without any device allocation.  The paper has no counterpart: the
+ * method does not deal with memory allocation.  This entry point serves callers that cannot
+ * allocate device memory at the moment they apply the preconditioner: programs whose device
+ * memory belongs to a fixed pool or to another framework's allocator, and real-time loops
+ * that must not enter the allocator.  bilu_apply itself allocates nothing per call, but it
+ * relies on buffers created with the factor and stages host vectors through buffers
+ * allocated on first use.
  *
- * The result of bilu_apply (z = M^{-1} r, the same operations; the backward sweep's sums
- * are grouped differently, so results agree to rounding), for device pointers only
- * (host pointers: BILU_ERR_ARG).  Its scratch (per-block completion flags and sweep state)
- * is one fixed array of 512 KB in device memory that every GPU loading the library holds
- * until the process exits; it serves factors of at most 65536 diagonal blocks (more:
- * BILU_ERR_ARG).  The first call on a device looks up that array's device address (a CUDA
- * runtime query, no allocation): make the first call on each device before any stream
- * capture.  All calls on a device share the array and each call clears the part it uses:
- * calls whose work overlaps on the GPU (other streams, other contexts) race and must be
- * ordered by the caller.  Stream-ordered on the context's stream; does not synchronize, so
- * a device-side wait that gives up is not reported.  Calls no cudaMalloc / cudaFree.
+ * z = M^{-1} r as bilu_apply computes it (the same operations; the backward sweep's sums are
+ * grouped differently, so results agree to rounding), FP64 factors and device pointers only
+ * (host pointers, reduced-precision factors: BILU_ERR_ARG).  Its scratch (per-block
+ * completion flags and sweep state) is one fixed array of 512 KB in device memory that every
+ * GPU loading the library holds until the process exits; it serves factors of at most 65536
+ * diagonal blocks (more: BILU_ERR_ARG).  The first call on a device looks up that array's
+ * device address (a CUDA runtime query, no allocation): make the first call on each device
+ * before any stream capture.  All calls on a device share the array and each call clears
+ * the part it uses: calls whose work overlaps on the GPU (other streams, other contexts)
+ * race and must be ordered by the caller.  Stream-ordered on the context's stream; does not
+ * synchronize.  A device-side wait that gives up (bounded; never expected) fills z with NaN.
+ * Calls no cudaMalloc / cudaFree.
  */
 bilu_status bilu_apply_noalloc(bilu_ctx *ctx, const double *r, double *z);
 

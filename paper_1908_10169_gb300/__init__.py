@@ -21,8 +21,9 @@ BILU_ERR_ARG, BILU_ERR_OOM, BILU_ERR_CUDA, BILU_ERR_SINGULAR, BILU_ERR_TIMEOUT, 
 BILU_BLOCKING_FIXED, BILU_BLOCKING_ILU1T = 0, 1
 BILU_PREC_FP64, BILU_PREC_FP32, BILU_PREC_BF16 = 0, 1, 2
 BILU_SKIP_NONE, BILU_SKIP_BOUND, BILU_SKIP_LEARNED = 0, 1, 2
+BILU_SCHED_CHAIN, BILU_SCHED_TREE = 0, 1
 (BILU_DEBUG_EXTRA_CTA, BILU_DEBUG_SPIN_LIMIT, BILU_DEBUG_SELFTEST_RECIP, BILU_DEBUG_BATCH_GROUP,
- BILU_DEBUG_SMALL_POOLS, BILU_DEBUG_POISON) = 1, 2, 3, 4, 5, 6
+ BILU_DEBUG_SMALL_POOLS, BILU_DEBUG_POISON, BILU_DEBUG_NO_TRUNK, BILU_DEBUG_TRACE) = 1, 2, 3, 4, 5, 6, 7, 8
 BILU_MAX_BLOCK = 64
 
 # every extern "C" symbol that include/bilu.h declares
@@ -46,7 +47,8 @@ BILU_MLP_PARAMS = 2 * 12 + 64 * 12 + 64 + 64 * 64 + 64 + 64 + 1
 class bilu_params(ct.Structure):
     _fields_ = [("blocking", ct.c_int32), ("max_block", ct.c_int32), ("fixed_block", ct.c_int32),
                 ("tau_analyze", ct.c_double), ("perturb", ct.c_int32), ("pert_tau", ct.c_double),
-                ("pert_rho", ct.c_double), ("precision", ct.c_int32), ("skip", ct.c_int32)]
+                ("pert_rho", ct.c_double), ("precision", ct.c_int32), ("skip", ct.c_int32),
+                ("schedule", ct.c_int32), ("group_ctas", ct.c_int32)]
 
 
 class gmres_info(ct.Structure):
@@ -64,7 +66,9 @@ class bilu_stats_t(ct.Structure):
                 ("t_analyze_ms", ct.c_double),
                 ("t_factor_ms", ct.c_double), ("pool_retries", ct.c_int32),
                 ("kernel_launches", ct.c_int64), ("phase_ms", ct.c_double * 8),
-                ("skipped_rows", ct.c_int64), ("skipped_cols", ct.c_int64)]
+                ("skipped_rows", ct.c_int64), ("skipped_cols", ct.c_int64), ("schedule", ct.c_int32),
+                ("tree_height", ct.c_int32), ("tree_trunk", ct.c_int32), ("group_ctas", ct.c_int32),
+                ("idle_ms", ct.c_double)]
 
 
 class bilu_mlp_train_cfg(ct.Structure):

@@ -657,6 +657,11 @@ bilu_status permute_csr_host(int64_t n, const int64_t *rowptr, const int32_t *co
 }
 
 void matrix_free(bilu_ctx *c) {
+    dev_free(c->d_parent);
+    dev_free(c->d_tree0);
+    dev_free(c->d_tree);
+    c->h_parent.clear();
+    c->tree_split = c->tree_height = c->tree_nleaves = 0;
     dev_free(c->d_rowptr);
     dev_free(c->d_colind);
     dev_free(c->d_val);
@@ -666,6 +671,81 @@ void matrix_free(bilu_ctx *c) {
     dev_free(c->d_bstart);
     dev_free(c->d_blkof);
     dev_free(c->d_Dptr);
+}
+
+// The tree schedule's static data (Sec. 3.3: each block depends only on its subtree): the
+// block elimination tree of the partition and the trunk (the longest run of blocks at the end
+// in which every block's only child is the block before it, down to the first block with
+// another child count: factored by the whole grid).  The device copy of the initial queue
+// state is built by tree_init (below) for the trunk the factorization uses.
+bilu_status tree_setup(bilu_ctx *c, const HostCSR &A) {
+    const int32_t nb = c->nb;
+    std::vector<int32_t> parent(std::max(nb, 1), -1);
+    int32_t height = 0;
+    std::string err;
+    if (nb > 0) {
+        const bilu_status st = block_etree_host(A.n, A.rowptr.data(), A.colind.data(), nb, c->h_bstart.data(),
+                                                parent.data(), &height, &err);
+        if (st != BILU_OK) return set_err(c, st, "block elimination tree: " + err);
+    }
+    std::vector<int32_t> nchild(std::max(nb, 1), 0);
+    for (int32_t K = 0; K < nb; ++K)
+        if (parent[K] >= 0) nchild[parent[K]]++;
+    int32_t split = nb;
+    if (nb > 0 && parent[nb - 1] < 0) {
+        split = nb - 1;
+        while (split > 0 && nchild[split] == 1 && parent[split - 1] == split) --split;
+    }
+    c->h_parent.assign(parent.begin(), parent.begin() + nb);
+    c->tree_split = split;
+    c->tree_height = height;
+    c->tree_init_split = -1;
+    cudaError_t e;
+    if ((e = dev_alloc(&c->d_parent, std::max(nb, 1))) != cudaSuccess ||
+        (e = cudaMemcpyAsync(c->d_parent, parent.data(), std::max(nb, 1) * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+        return e == cudaErrorMemoryAllocation ? set_err(c, BILU_ERR_OOM, "device allocation failed in analyze")
+                                              : cuda_err(c, e, "tree upload");
+    return BILU_OK;
+}
+
+// Initial queue state of a tree factorization whose trunk starts at block `split` (d_tree0;
+// copied to d_tree before every run).  Int32 words: [0, 8) four 64-bit pool cursors, [8, 12)
+// the whole-grid barrier, [12, 14) queue head and tail, [14, 14 + nsm) the group slots, then
+// pending[nb] (children of every block below the trunk not finished yet) and queue[nb] (the
+// leaves below the trunk first, those farthest from the trunk first; -1 elsewhere).
+bilu_status tree_init(bilu_ctx *c, int32_t split) {
+    if (c->tree_init_split == split && c->d_tree0 && c->d_tree) return BILU_OK;
+    const int32_t nb = c->nb;
+    const std::vector<int32_t> &parent = c->h_parent;
+    std::vector<int32_t> nchild(std::max(nb, 1), 0), depth(std::max(nb, 1), 0);
+    for (int32_t K = 0; K < split; ++K)
+        if (parent[K] >= 0 && parent[K] < split) nchild[parent[K]]++;
+    for (int32_t K = split - 1; K >= 0; --K)
+        depth[K] = (parent[K] >= 0 && parent[K] < split) ? depth[parent[K]] + 1 : 0;
+    std::vector<int32_t> leaves;
+    for (int32_t K = 0; K < split; ++K)
+        if (nchild[K] == 0) leaves.push_back(K);
+    std::stable_sort(leaves.begin(), leaves.end(), [&](int32_t x, int32_t y) { return depth[x] > depth[y]; });
+    const int64_t words = 14 + (int64_t)c->nsm + 2 * (int64_t)std::max(nb, 1);
+    std::vector<int32_t> t0(words, 0);
+    t0[13] = (int32_t)leaves.size();
+    int32_t *pending = t0.data() + 14 + c->nsm, *queue = pending + std::max(nb, 1);
+    for (int32_t K = 0; K < std::max(nb, 1); ++K) queue[K] = -1;
+    for (int32_t K = 0; K < split; ++K) pending[K] = nchild[K];
+    for (size_t i = 0; i < leaves.size(); ++i) queue[i] = leaves[i];
+    dev_free(c->d_tree0);
+    dev_free(c->d_tree);
+    c->tree_init_split = -1;
+    cudaError_t e;
+    if ((e = dev_alloc(&c->d_tree0, words)) != cudaSuccess || (e = dev_alloc(&c->d_tree, words)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(c->d_tree0, t0.data(), words * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+        return e == cudaErrorMemoryAllocation ? set_err(c, BILU_ERR_OOM, "device allocation failed in factor")
+                                              : cuda_err(c, e, "tree queue upload");
+    c->tree_init_split = split;
+    c->tree_nleaves = (int32_t)leaves.size();
+    return BILU_OK;
 }
 
 bilu_status analyze_run(bilu_ctx *c, int64_t n, const int64_t *rowptr, const int32_t *colind,
@@ -696,6 +776,10 @@ bilu_status analyze_run(bilu_ctx *c, int64_t n, const int64_t *rowptr, const int
     if (p->skip != BILU_SKIP_NONE && p->skip != BILU_SKIP_BOUND && p->skip != BILU_SKIP_LEARNED)
         return set_err(c, BILU_ERR_ARG, "unknown skip mode");
     if (n > 0 && (!rowptr || !colind || !val)) return set_err(c, BILU_ERR_ARG, "null CSR array");
+    if (p->schedule != BILU_SCHED_CHAIN && p->schedule != BILU_SCHED_TREE)
+        return set_err(c, BILU_ERR_ARG, "unknown schedule");
+    if (p->group_ctas < 0 || p->group_ctas > c->nsm)
+        return set_err(c, BILU_ERR_ARG, "group_ctas must be in 0..number of SMs");
 
     const auto t_start = std::chrono::steady_clock::now();
 
@@ -796,6 +880,13 @@ bilu_status analyze_run(bilu_ctx *c, int64_t n, const int64_t *rowptr, const int
         matrix_free(c);
         return e == cudaErrorMemoryAllocation ? set_err(c, BILU_ERR_OOM, "device allocation failed in analyze")
                                               : cuda_err(c, e, "analyze upload");
+    }
+    if (p->schedule == BILU_SCHED_TREE) {
+        bilu_status st = tree_setup(c, A);
+        if (st != BILU_OK) {
+            matrix_free(c);
+            return st;
+        }
     }
     BILU_CUDA(c, cudaStreamSynchronize(c->stream));
     c->t_analyze_ms =

@@ -36,6 +36,7 @@ enum {
     INFO_B_WORK_NS = 17,     // time CTA 0 waits for the pivot-row tiles
     INFO_SKIP_ROWS = 18,     // candidate rows skipped (norm bound or classifier)
     INFO_SKIP_COLS = 19,     // candidate columns skipped
+    INFO_IDLE_NS = 20,       // tree schedule: time the groups wait for a ready block (summed)
     INFO_COUNT = 24
 };
 
@@ -96,6 +97,27 @@ struct bilu_ctx {
     int32_t *d_status = nullptr;
     int64_t *d_info = nullptr;
     uint32_t *d_bar = nullptr;     // grid barrier counter + generation
+
+    // tree schedule (BILU_SCHED_TREE): block elimination tree, the ready queue, the scratch of
+    // the CTA groups after group 0 (group 0 uses the scratch above) and the chunked pools
+    // ("arena") that the groups fill before the closing copy into the block-ordered pools
+    std::vector<int32_t> h_parent;  // parent block (-1: root)
+    int32_t tree_split = 0;         // blocks [tree_split, nb) form the trunk
+    int32_t tree_height = 0;
+    int32_t *d_parent = nullptr;
+    int32_t tree_nleaves = 0;
+    int32_t tree_init_split = -1;   // the trunk start d_tree0 was built for
+    char *d_grp_big = nullptr;      // per-group scratch of every group
+    char *d_grp_reset = nullptr;    // per-group state cleared before every run
+    size_t grp_big_bytes = 0, grp_reset_bytes = 0;  // per group
+    int32_t grp_n = 0;              // groups the scratch was carved for
+    int64_t grp_key[3] = {0, 0, 0}; // capT, prodcap, capXS it was carved for
+    int32_t *d_tree0 = nullptr, *d_tree = nullptr;  // initial / live: pending, queue, control words
+    int64_t capA[4] = {0, 0, 0, 0}; // arena capacities (rows L, values L, columns U, values U)
+    int32_t *d_aLrow = nullptr, *d_aUcol = nullptr;
+    double *d_aLval = nullptr, *d_aUval = nullptr, *d_aLnrm = nullptr, *d_aUnrm = nullptr;
+    int64_t *d_aptr = nullptr;      // 6 x nb: L begin, L end, L value begin, U begin, U end, U value begin
+    double idle_ms = 0.0;           // last tree factorization: time its groups waited for ready blocks
 
     // apply
     int32_t *d_flagF = nullptr, *d_flagB = nullptr;
@@ -194,6 +216,7 @@ bilu_status scale_permute_csr_host(int64_t n, const int64_t *rowptr, const int32
                                    const int32_t *rowperm, const int32_t *colperm, const double *dl,
                                    const double *dr, int64_t *out_rowptr, int32_t *out_colind, double *out_val,
                                    std::string *err);
+bilu_status tree_init(bilu_ctx *c, int32_t split);
 bilu_status nd_order_host(int64_t n, const int64_t *rowptr, const int32_t *colind, int32_t nb,
                           const int32_t *bstart, int32_t leaf, int32_t *perm, int32_t *bstart_out,
                           int32_t *order_out, std::string *err);

@@ -12,6 +12,8 @@ extern long long g_debug_spin_limit;
 extern long long g_debug_batch_group;
 extern int g_debug_small_pools;
 extern int g_debug_poison;
+extern int g_debug_no_trunk;
+extern int g_debug_trace;
 int recip_selftest(int n);
 
 bilu_status set_err(bilu_ctx *c, bilu_status st, const std::string &msg) {
@@ -296,6 +298,12 @@ bilu_status bilu_stats(bilu_ctx *c, bilu_stats_t *o) {
     o->nnz_d = c->h_Dptr.empty() ? 0 : c->h_Dptr.back();
     o->t_analyze_ms = c->t_analyze_ms;
     o->kernel_launches = c->launches;
+    o->schedule = c->p.schedule;
+    if (c->p.schedule == BILU_SCHED_TREE) {
+        o->tree_height = c->tree_height;
+        o->tree_trunk = c->nb - c->tree_split;
+        o->group_ctas = std::max(1, std::min(c->nsm, c->p.group_ctas > 0 ? c->p.group_ctas : 8));
+    }
     if (c->state >= 2) {
         o->nnz_l = c->nnz_l;
         o->nnz_u = c->nnz_u;
@@ -314,6 +322,7 @@ bilu_status bilu_stats(bilu_ctx *c, bilu_stats_t *o) {
         for (int k = 0; k < 8; ++k) o->phase_ms[k] = c->phase_ms[k];
         o->skipped_rows = c->skipped_rows;
         o->skipped_cols = c->skipped_cols;
+        o->idle_ms = c->p.schedule == BILU_SCHED_TREE ? c->idle_ms : 0.0;
     }
     return BILU_OK;
 }
@@ -383,6 +392,8 @@ bilu_status bilu_debug_set(bilu_ctx *c, int32_t what, int64_t value) {
         case BILU_DEBUG_BATCH_GROUP: g_debug_batch_group = value > 0 ? value : 0; return BILU_OK;
         case BILU_DEBUG_SMALL_POOLS: g_debug_small_pools = value ? 1 : 0; return BILU_OK;
         case BILU_DEBUG_POISON: g_debug_poison = value ? 1 : 0; return BILU_OK;
+        case BILU_DEBUG_NO_TRUNK: g_debug_no_trunk = value ? 1 : 0; return BILU_OK;
+        case BILU_DEBUG_TRACE: g_debug_trace = value ? 1 : 0; return BILU_OK;
         case BILU_DEBUG_SELFTEST_RECIP: {
             cudaSetDevice(c->device);
             const int bad = recip_selftest((int)value);

@@ -127,7 +127,8 @@ __device__ __forceinline__ void st_relaxed_u32(uint32_t *p, uint32_t v) {
 }
 
 __device__ __forceinline__ bool grid_barrier(uint32_t *bar, uint32_t G, int32_t *status,
-                                             long long spin_limit, int64_t *info, int site) {
+                                             long long spin_limit, int64_t *info, int site,
+                                             volatile int32_t *heartbeat = nullptr) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -150,6 +151,7 @@ __device__ __forceinline__ bool grid_barrier(uint32_t *bar, uint32_t G, int32_t 
                     ok = 0;
                     break;
                 }
+                if (heartbeat && (it & 1023) == 0) *heartbeat = (int32_t)(it >> 10);  // test hook
                 if (it > 64) __nanosleep(32);
             }
             // the snapshot cannot be overwritten before this CTA arrives at the next barrier

@@ -17,7 +17,9 @@
 //      producer-list appends for the later blocks they hit (the role of L_head/L_list
 //      and U_head/U_list of Sec. 2.1).
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <mutex>
 
@@ -98,6 +100,10 @@ struct FactorArgs {
     int64_t *info;
     uint32_t *bar;
     int32_t debug_extra_cta;     // test hook: the barrier waits for one CTA that never comes
+    volatile int32_t *trace;     // test hook (tree schedule): per CTA [mode, block, last barrier
+                                 // site, CTA-0 wait site, wait heartbeat], mapped host memory, or null
+    int64_t *timeline;           // test hook (tree schedule): per block 8 words: group, then the
+                                 // clock at its start and after phases A, B+C, C2, (Bs,) D, E
     int32_t skip_bound;          // 1: skip candidates that the norm bound proves dropped
     double *Lnrm, *Unrm;         // per kept row of L: ||l_i||; per kept column of U-breve: ||u_j||
     double *dcolsq;              // squared column norms of D_K (b entries)
@@ -118,6 +124,15 @@ struct FactorArgs {
     float *rec_x, *rec_y;
     long long *rec_tag;
     unsigned long long *rec_count;
+    // end of block K's kept rows of L / columns of U-breve (chain schedule: Lptr + 1, Uptr + 1)
+    int64_t *Lend, *Uend;
+    // tree schedule: blocks of different subtrees finish in any order, so the pools are filled
+    // from per-group chunks (arena) and the producer lists are sorted before use
+    int32_t arena, sortprod;
+    int64_t *gcur;               // this group's chunk cursors: [cur, end] for L rows, L values,
+                                 // U columns, U values, then the current block's four bases
+    unsigned long long *acur;    // global cursors of the four pools
+    int64_t chunkR, chunkV;      // chunk sizes (rows / columns, values)
 };
 
 // (always PPART: the factor must not depend on the launch configuration, so that a batched
@@ -159,12 +174,38 @@ __device__ void phase_A(const FactorArgs &a, int K, bool Lside, char *smem) {
     int32_t *xposs = off + PMAX + 1;             // PMAX
     int32_t *ws = xposs + PMAX;                  // 40
     int32_t *lohi = ws + 40;                     // 2
+    int32_t *slist = lohi + 2;                   // PMAX: the producer list
+    int32_t *stmp = slist + PMAX;                // PMAX: sort buffer
 
-    const int32_t *plist = (Lside ? a.prodL : a.prodU) + (int64_t)K * a.prodcap;
+    int32_t *plist = (Lside ? a.prodL : a.prodU) + (int64_t)K * a.prodcap;
     int pcnt = ldcg((Lside ? a.prodLcnt : a.prodUcnt) + K);
+    // until the sets are complete the step's counts say "pivot rows only, no producers", so
+    // that the later phases of a step that ends early (an overflow) stay within their buffers
+    if (tid == 0) {
+        a.kst[Lside ? 0 : 1] = Lside ? b : 0;
+        a.kst[Lside ? 2 : 3] = 0;
+    }
     if (pcnt > a.prodcap || pcnt > PMAX) {
         if (tid == 0) set_status(a.status, DEV_PROD_OVERFLOW, a.info, K);
         pcnt = 0;
+    }
+    for (int t = tid; t < pcnt; t += NT) slist[t] = ldcg(plist + t);
+    __syncthreads();
+    if (a.sortprod && pcnt > 1) {
+        // blocks of different subtrees append to the list in any order: a rank sort (the
+        // entries are distinct) restores increasing J, written back for the later readers
+        for (int t = tid; t < pcnt; t += NT) {
+            const int v = slist[t];
+            int r = 0;
+            for (int u = 0; u < pcnt; ++u) r += slist[u] < v;
+            stmp[r] = v;
+        }
+        __syncthreads();
+        for (int t = tid; t < pcnt; t += NT) {
+            slist[t] = stmp[t];
+            plist[t] = stmp[t];
+        }
+        __syncthreads();
     }
     int64_t *pinfo = Lside ? a.pinfoL : a.pinfoU;
     uint32_t *bm = Lside ? a.bmL : a.bmU;
@@ -175,10 +216,10 @@ __device__ void phase_A(const FactorArgs &a, int K, bool Lside, char *smem) {
 
     // producer ranges: warp per producer
     for (int t = warp; t < pcnt; t += NW) {
-        const int J = ldcg(plist + t);
+        const int J = slist[t];
         const int bJ = a.bstart[J + 1] - a.bstart[J];
-        const int l0 = (int)ldcg(a.Lptr + J), l1 = (int)ldcg(a.Lptr + J + 1);
-        const int u0 = (int)ldcg(a.Uptr + J), u1 = (int)ldcg(a.Uptr + J + 1);
+        const int l0 = (int)ldcg(a.Lptr + J), l1 = (int)ldcg(a.Lend + J);
+        const int u0 = (int)ldcg(a.Uptr + J), u1 = (int)ldcg(a.Uend + J);
         const int64_t lv = ldcg(a.Lvptr + J), uv = ldcg(a.Uvptr + J);
         int xbeg, xend, ybeg, yend;
         int64_t xval, yval;
@@ -1079,8 +1120,10 @@ __device__ void phase_E(const FactorArgs &a, int K, char *smem) {
     int32_t *cnt = (int32_t *)smem;  // NT tile offsets of the current chunk
     int32_t *ws = cnt + NT;          // scan scratch (40)
     int32_t *sl = ws + 40;           // NW x 32: slot of the r-th kept entry of a warp's tile
-    const int64_t Lbase = ldcg(a.Lptr + K), LVbase = ldcg(a.Lvptr + K);
-    const int64_t Ubase = ldcg(a.Uptr + K), UVbase = ldcg(a.Uvptr + K);
+    // pool positions of this block: after the previous block (chain schedule) or the bases
+    // reserved for it in its group's chunks (tree schedule)
+    const int64_t Lbase = ldcg(a.arena ? a.gcur + 8 : a.Lptr + K), LVbase = ldcg(a.arena ? a.gcur + 9 : a.Lvptr + K);
+    const int64_t Ubase = ldcg(a.arena ? a.gcur + 10 : a.Uptr + K), UVbase = ldcg(a.arena ? a.gcur + 11 : a.Uvptr + K);
     int keptL, keptU, skipped = 0;
     {
         int lk = 0, uk = 0, sk = 0;
@@ -1105,10 +1148,24 @@ __device__ void phase_E(const FactorArgs &a, int K, char *smem) {
         return;
     }
     if (cr == 0 && tid == 0) {
-        a.Lptr[K + 1] = Lbase + keptL;
-        a.Lvptr[K + 1] = LVbase + (int64_t)keptL * b;
-        a.Uptr[K + 1] = Ubase + keptU;
-        a.Uvptr[K + 1] = UVbase + (int64_t)keptU * b;
+        if (a.arena) {
+            a.Lptr[K] = Lbase;
+            a.Lend[K] = Lbase + keptL;
+            a.Lvptr[K] = LVbase;
+            a.Uptr[K] = Ubase;
+            a.Uend[K] = Ubase + keptU;
+            a.Uvptr[K] = UVbase;
+            // the group's cursors move past what the block kept (read again only by this thread)
+            a.gcur[0] = Lbase + keptL;
+            a.gcur[2] = LVbase + (int64_t)keptL * b;
+            a.gcur[4] = Ubase + keptU;
+            a.gcur[6] = UVbase + (int64_t)keptU * b;
+        } else {
+            a.Lptr[K + 1] = Lbase + keptL;
+            a.Lvptr[K + 1] = LVbase + (int64_t)keptL * b;
+            a.Uptr[K + 1] = Ubase + keptU;
+            a.Uvptr[K + 1] = UVbase + (int64_t)keptU * b;
+        }
         atomicAdd((unsigned long long *)(a.info + INFO_CAND_ROWS), (unsigned long long)nLc);
         atomicAdd((unsigned long long *)(a.info + INFO_CAND_COLS), (unsigned long long)mU);
         atomicAdd((unsigned long long *)(a.info + INFO_FLOP_SCALE), 2ULL * b * b * (unsigned long long)(nLc + mU - skipped));
@@ -1179,7 +1236,7 @@ __device__ void phase_E(const FactorArgs &a, int K, char *smem) {
                 }
                 if (kept) {
                     const int tb = a.blkof[idx];
-                    if (atomicExch(last + tb, K) != K) {
+                    if (atomicExch(last + tb, K + 1) != K + 1) {
                         const int pos = atomicAdd(pc + tb, 1);
                         if (pos < a.prodcap) pl[(int64_t)tb * a.prodcap + pos] = K;
                         else set_status(a.status, DEV_PROD_OVERFLOW, a.info, K);
@@ -1200,7 +1257,7 @@ __device__ void phase_E(const FactorArgs &a, int K, char *smem) {
                     idxpool[base + rank] = idx;
                     nrmpool[base + rank] = ldcg(nrmslot + slot);
                     const int tb = a.blkof[idx];
-                    if (atomicExch(last + tb, K) != K) {
+                    if (atomicExch(last + tb, K + 1) != K + 1) {
                         const int pos = atomicAdd(pc + tb, 1);
                         if (pos < a.prodcap) pl[(int64_t)tb * a.prodcap + pos] = K;
                         else set_status(a.status, DEV_PROD_OVERFLOW, a.info, K);
@@ -1244,7 +1301,52 @@ __device__ __forceinline__ void red_add_release(uint32_t *p, uint32_t v) {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// One block step (per block K, five or six grid-barrier phases):
+__device__ __forceinline__ void trace_at(const FactorArgs &a, int slot, int v) {
+    if (a.trace && threadIdx.x == 0) {
+        a.trace[8 * blockIdx.x + slot] = v;
+        __threadfence_system();
+    }
+}
+__device__ __forceinline__ volatile int32_t *trace_hb(const FactorArgs &a) {
+    return a.trace ? a.trace + 8 * blockIdx.x + 4 : nullptr;
+}
+
+// Pool space for block K in the tree schedule (CTA 0, thread 0 of the group, after the
+// candidate sets are known): the block keeps at most its candidates, so each of the four
+// pools must have that much left in the group's current chunk, or the group takes a new chunk
+// from the pool's global cursor.  The bases are published to the group's CTAs by the next
+// barriers (phase E reads them); a pool that is full reports DEV_POOL_OVERFLOW (the host grows
+// the pools and runs the factorization again) and leaves bases at the capacity, so that phase E
+// writes nothing.
+__device__ void arena_reserve(const FactorArgs &a, int K, int64_t nLc, int64_t mU, int b) {
+    const int64_t need[4] = {nLc, nLc * b, mU, mU * b};
+    const int64_t chunk[4] = {a.chunkR, a.chunkV, a.chunkR, a.chunkV};
+    const int64_t cap[4] = {a.capLrow, a.capLval, a.capUcol, a.capUval};
+    for (int q = 0; q < 4; ++q) {
+        int64_t cur = a.gcur[2 * q], end = a.gcur[2 * q + 1];
+        if (cur + need[q] > end) {
+            const int64_t sz = max(chunk[q], need[q]);
+            cur = (int64_t)atomicAdd(a.acur + q, (unsigned long long)sz);
+            end = cur + sz;
+            if (end > cap[q]) {
+                set_status(a.status, DEV_POOL_OVERFLOW, a.info, K);
+                cur = end = cap[q];
+            }
+            a.gcur[2 * q] = cur;
+            a.gcur[2 * q + 1] = end;
+        }
+        a.gcur[8 + q] = cur;
+    }
+}
+
+// CTA 0's phase clock (ns, summed over the blocks it leads): A, B1+C, C2, Bs, D, E; time
+// inside the pivot LU; waiting for the pivot-row tiles
+struct StepTimers {
+    uint64_t acc[6];
+    uint64_t tprev, tlu, twait, tidle;
+};
+
+// One block step (per block K, five or six barrier phases among the a.G CTAs of the group):
 //   A           candidate sets and update plans (CTA 0: L side, CTA 1: U side)
 //   B1 + C      pivot-row tiles (two rows each, every producer hits them) on CTAs 1.., then
 //               the pivot LU on CTA 0 as soon as those tiles are done, while the remaining
@@ -1253,116 +1355,144 @@ __device__ __forceinline__ void red_add_release(uint32_t *p, uint32_t v) {
 //   Bs          (norm-bound skip only) the remaining update tiles, bound-tested
 //   D           scaling, norms, drop decisions
 //   E           compaction and producer lists
+// Returns false when a barrier reports an error (every CTA of the group returns at the same one).
 template <class TS>
-__device__ void factor_chain(const FactorArgs &a, char *smem) {
+__device__ bool block_step(const FactorArgs &a, int K, char *smem, StepTimers &tm) {
     const uint32_t G = a.G + a.debug_extra_cta;
     const int cr = crank(a);
-    // CTA 0 times (ns, summed over the blocks): A, B1+C, C2, Bs, D, E; LU work; pivot-tile wait
-    uint64_t tacc[6] = {0, 0, 0, 0, 0, 0};
-    uint64_t tprev = gtimer(), tlu = 0, twait = 0;
     auto lap = [&](int ph) {
         if (cr == 0 && threadIdx.x == 0) {
             const uint64_t t = gtimer();
-            tacc[ph] += t - tprev;
-            tprev = t;
+            tm.acc[ph] += t - tm.tprev;
+            tm.tprev = t;
+            if (a.timeline) a.timeline[8 * (int64_t)K + 2 + ph] = (int64_t)t;
         }
     };
-    for (int K = 0; K < a.nb; ++K) {
-        const int b = a.bstart[K + 1] - a.bstart[K];
-        if (cr == 0) phase_A(a, K, true, smem);
-        if (cr == (1 % a.G)) {
-            __syncthreads();
-            phase_A(a, K, false, smem);
-        }
-        if (!grid_barrier(a.bar, G, a.status, a.spin_limit, a.info, 1)) return;
-        lap(0);
-        const int mL = ldcg(a.kst + 0), mU = ldcg(a.kst + 1);
-        const int nrestL = mL - b, nrest = nrestL + mU;
-        const int npt = (b + TRP - 1) / TRP;
-        {
-            const int W = a.G > 1 ? a.G - 1 : 1;  // CTAs taking tiles (CTA 0 factors the pivot block)
-            const int np = pivot_parts(W, npt);    // producer slices per pivot-row tile
-            int TR = (nrest + W - 1) / W;
-            TR = max(4, min(TRMAX, TR));
-            const int nLt = (nrestL + TR - 1) / TR, nUt = (mU + TR - 1) / TR;
-            const int ntiles = npt * np + (a.skip_bound ? 0 : nLt + nUt);
-            if (a.G == 1 || cr > 0) {
-                const int wid = a.G > 1 ? cr - 1 : 0;
-                for (int it = wid; it < ntiles; it += W) {
-                    if (it < npt * np) {
-                        const int sa = (it / np) * TRP;
-                        phase_B_tile<TS>(a, K, true, sa, min(TRP, b - sa), smem, false, false, it % np, np);
-                        __syncthreads();
-                        if (threadIdx.x == 0) red_add_release(a.pivdone, 1u);
-                    } else {
-                        const int r = it - npt * np;
-                        const bool Ls = r < nLt;
-                        const int sa = Ls ? b + r * TR : (r - nLt) * TR;
-                        const int cnt = Ls ? min(TR, mL - sa) : min(TR, mU - sa);
-                        phase_B_tile<TS>(a, K, Ls, sa, cnt, smem, false, a.learned || a.record);
-                        __syncthreads();
-                    }
+    if (a.timeline && cr == 0 && threadIdx.x == 0) {
+        a.timeline[8 * (int64_t)K] = (int64_t)(blockIdx.x / a.G) + (a.G == (int)gridDim.x ? 1000 : 0);
+        a.timeline[8 * (int64_t)K + 1] = (int64_t)gtimer();
+    }
+    const int b = a.bstart[K + 1] - a.bstart[K];
+    if (cr == 0) phase_A(a, K, true, smem);
+    if (cr == (1 % a.G)) {
+        __syncthreads();
+        phase_A(a, K, false, smem);
+    }
+    trace_at(a, 2, 1);
+    if (!grid_barrier(a.bar, G, a.status, a.spin_limit, a.info, 1, trace_hb(a))) return false;
+    lap(0);
+    // candidate counts of this step (kept within the candidate buffers: phase A reports an
+    // overflow and writes safe counts instead of overrunning them)
+    const int capT = (int)min(a.capT, (int64_t)INT32_MAX);
+    const int mL = max(b, min((int)ldcg(a.kst + 0), capT)), mU = max(0, min((int)ldcg(a.kst + 1), capT));
+    const int nrestL = mL - b, nrest = nrestL + mU;
+    const int npt = (b + TRP - 1) / TRP;
+    if (a.arena && cr == 0 && threadIdx.x == 0) arena_reserve(a, K, nrestL, mU, b);
+    {
+        const int W = a.G > 1 ? a.G - 1 : 1;  // CTAs taking tiles (CTA 0 factors the pivot block)
+        const int np = pivot_parts(W, npt);    // producer slices per pivot-row tile
+        int TR = (nrest + W - 1) / W;
+        TR = max(4, min(TRMAX, TR));
+        const int nLt = (nrestL + TR - 1) / TR, nUt = (mU + TR - 1) / TR;
+        const int ntiles = npt * np + (a.skip_bound ? 0 : nLt + nUt);
+        if (a.G == 1 || cr > 0) {
+            const int wid = a.G > 1 ? cr - 1 : 0;
+            for (int it = wid; it < ntiles; it += W) {
+                if (it < npt * np) {
+                    const int sa = (it / np) * TRP;
+                    phase_B_tile<TS>(a, K, true, sa, min(TRP, b - sa), smem, false, false, it % np, np);
+                    __syncthreads();
+                    if (threadIdx.x == 0) red_add_release(a.pivdone, 1u);
+                } else {
+                    const int r = it - npt * np;
+                    const bool Ls = r < nLt;
+                    const int sa = Ls ? b + r * TR : (r - nLt) * TR;
+                    const int cnt = Ls ? min(TR, mL - sa) : min(TR, mU - sa);
+                    phase_B_tile<TS>(a, K, Ls, sa, cnt, smem, false, a.learned || a.record);
+                    __syncthreads();
                 }
             }
-            if (cr == 0) {
-                __shared__ int s_go;
-                const uint64_t tw = gtimer();
-                if (threadIdx.x == 0) {
-                    int go = 1;
-                    if (a.G > 1) {
-                        long long itn = 0;
-                        while (ld_acquire_u32(a.pivdone) < (uint32_t)(npt * pivot_parts(a.G - 1, npt))) {
-                            if (++itn > a.spin_limit) {
-                                if (atomicCAS(a.status, 0, DEV_TIMEOUT) == 0) a.info[INFO_TIMEOUT_SITE] = 7;
-                                go = 0;
-                                break;
-                            }
-                            if (itn > 64) __nanosleep(32);
+        }
+        if (cr == 0) {
+            __shared__ int s_go;
+            const uint64_t tw = gtimer();
+            trace_at(a, 3, 7);
+            if (threadIdx.x == 0) {
+                int go = 1;
+                if (a.G > 1) {
+                    long long itn = 0;
+                    while (ld_acquire_u32(a.pivdone) < (uint32_t)(npt * pivot_parts(a.G - 1, npt))) {
+                        if (a.trace && (itn & 1023) == 0) a.trace[8 * blockIdx.x + 6] = (int32_t)(itn >> 10);
+                        if (++itn > a.spin_limit) {
+                            if (atomicCAS(a.status, 0, DEV_TIMEOUT) == 0) a.info[INFO_TIMEOUT_SITE] = 7;
+                            go = 0;
+                            break;
                         }
-                        atomicExch(a.pivdone, 0u);
+                        if (itn > 64) __nanosleep(32);
                     }
-                    s_go = go;
-                    twait += gtimer() - tw;
+                    atomicExch(a.pivdone, 0u);
                 }
-                __syncthreads();
-                if (s_go) {
-                    const uint64_t t0 = gtimer();
-                    phase_C<TS>(a, K, smem);
-                    if (threadIdx.x == 0) tlu += gtimer() - t0;
-                }
+                s_go = go;
+                tm.twait += gtimer() - tw;
+            }
+            trace_at(a, 3, 0);
+            __syncthreads();
+            if (s_go) {
+                const uint64_t t0 = gtimer();
+                phase_C<TS>(a, K, smem);
+                if (threadIdx.x == 0) tm.tlu += gtimer() - t0;
             }
         }
-        if (!grid_barrier(a.bar, G, a.status, a.spin_limit, a.info, 2)) return;
-        lap(1);
-        phase_C2(a, K, smem);
-        if (!grid_barrier(a.bar, G, a.status, a.spin_limit, a.info, 3)) return;
-        lap(2);
-        if (a.skip_bound) {
-            int TR = (nrest + a.G - 1) / a.G;
-            TR = max(4, min(TRMAX, TR));
-            const int nLt = (nrestL + TR - 1) / TR, nUt = (mU + TR - 1) / TR;
-            for (int it = cr; it < nLt + nUt; it += a.G) {
-                const bool Ls = it < nLt;
-                const int sa = Ls ? b + it * TR : (it - nLt) * TR;
-                const int cnt = Ls ? min(TR, mL - sa) : min(TR, mU - sa);
-                phase_B_tile<TS>(a, K, Ls, sa, cnt, smem, true);
-                __syncthreads();
-            }
-            if (!grid_barrier(a.bar, G, a.status, a.spin_limit, a.info, 4)) return;
+    }
+    trace_at(a, 2, 2);
+    if (!grid_barrier(a.bar, G, a.status, a.spin_limit, a.info, 2, trace_hb(a))) return false;
+    lap(1);
+    phase_C2(a, K, smem);
+    trace_at(a, 2, 3);
+    if (!grid_barrier(a.bar, G, a.status, a.spin_limit, a.info, 3, trace_hb(a))) return false;
+    lap(2);
+    if (a.skip_bound) {
+        int TR = (nrest + a.G - 1) / a.G;
+        TR = max(4, min(TRMAX, TR));
+        const int nLt = (nrestL + TR - 1) / TR, nUt = (mU + TR - 1) / TR;
+        for (int it = cr; it < nLt + nUt; it += a.G) {
+            const bool Ls = it < nLt;
+            const int sa = Ls ? b + it * TR : (it - nLt) * TR;
+            const int cnt = Ls ? min(TR, mL - sa) : min(TR, mU - sa);
+            phase_B_tile<TS>(a, K, Ls, sa, cnt, smem, true);
+            __syncthreads();
         }
-        lap(3);
-        phase_D<TS>(a, K, smem);
-        if (!grid_barrier(a.bar, G, a.status, a.spin_limit, a.info, 5)) return;
-        lap(4);
-        phase_E<TS>(a, K, smem);
-        if (!grid_barrier(a.bar, G, a.status, a.spin_limit, a.info, 6)) return;
-        lap(5);
+        trace_at(a, 2, 4);
+    if (!grid_barrier(a.bar, G, a.status, a.spin_limit, a.info, 4, trace_hb(a))) return false;
     }
-    if (cr == 0 && threadIdx.x == 0) {
-        for (int p = 0; p < 6; ++p) a.info[INFO_PHASE_NS + p] = (int64_t)tacc[p];
-        a.info[INFO_C2_WORK_NS] = (int64_t)tlu;
-        a.info[INFO_B_WORK_NS] = (int64_t)twait;
-    }
+    lap(3);
+    phase_D<TS>(a, K, smem);
+    trace_at(a, 2, 5);
+    if (!grid_barrier(a.bar, G, a.status, a.spin_limit, a.info, 5, trace_hb(a))) return false;
+    lap(4);
+    phase_E<TS>(a, K, smem);
+    trace_at(a, 2, 6);
+    if (!grid_barrier(a.bar, G, a.status, a.spin_limit, a.info, 6, trace_hb(a))) return false;
+    lap(5);
+    return true;
+}
+
+// CTA 0's clocks into the info array (added: the tree schedule sums over its groups)
+__device__ void store_timers(const FactorArgs &a, const StepTimers &tm) {
+    for (int p = 0; p < 6; ++p) atomicAdd((unsigned long long *)(a.info + INFO_PHASE_NS + p), (unsigned long long)tm.acc[p]);
+    atomicAdd((unsigned long long *)(a.info + INFO_C2_WORK_NS), (unsigned long long)tm.tlu);
+    atomicAdd((unsigned long long *)(a.info + INFO_B_WORK_NS), (unsigned long long)tm.twait);
+    atomicAdd((unsigned long long *)(a.info + INFO_IDLE_NS), (unsigned long long)tm.tidle);
+}
+
+// The blocks K = 0..nb-1 one after another, each by the whole group.
+template <class TS>
+__device__ void factor_chain(const FactorArgs &a, char *smem) {
+    StepTimers tm{};
+    tm.tprev = gtimer();
+    for (int K = 0; K < a.nb; ++K)
+        if (!block_step<TS>(a, K, smem, tm)) return;
+    if (crank(a) == 0 && threadIdx.x == 0) store_timers(a, tm);
 }
 
 template <class TS>
@@ -1420,6 +1550,225 @@ __global__ void __launch_bounds__(NT, 1) bilu_factor_batch_kernel(const FactorAr
     }
 }
 
+// ---------------------------------------------------------------- tree schedule
+// Every block J that updates block K is a descendant of K in the block elimination tree
+// (Sec. 3.3 reorders so that this tree has independent subtrees), so K can be factored as soon
+// as its children are.  The grid is cut into groups of G CTAs; CTA 0 of a group takes the next
+// entry of a queue of ready blocks (the leaves first, then every block whose last child has
+// finished, in the order they become ready), the group runs block_step on it, and CTA 0
+// counts the block off at its parent.  The chain of single-child blocks at the top of the tree
+// (the trunk) runs afterwards on the whole grid.  Each block sees the same inputs and
+// producer order (sorted) as in the chain schedule, so the factor is the same bit for bit.
+struct TreeArgs {
+    int32_t nb, split, ngroups, G, extra;
+    const int32_t *parent;
+    int32_t *pending;            // children of each block not finished yet
+    int32_t *queue;              // ready blocks, -1 until filled
+    int32_t *tctl;               // [0] queue head, [1] queue tail, [2 + g] block of group g
+    uint32_t *fullbar;           // whole-grid barrier
+};
+
+__device__ __forceinline__ int32_t atom_add_acqrel_s32(int32_t *p, int32_t v) {
+    int32_t old;
+    asm volatile("atom.add.acq_rel.gpu.global.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+template <class TS>
+__global__ void __launch_bounds__(NT, 1) bilu_factor_tree_kernel(const FactorArgs *gargs, TreeArgs t) {
+    extern __shared__ __align__(16) char smem[];
+    __shared__ FactorArgs s_a;
+    __shared__ int s_K;
+    const int grp = blockIdx.x / t.G;
+    StepTimers tm{};
+    tm.tprev = gtimer();
+    // mode 0: a CTA of group grp takes ready blocks; 1: the groups are done, the grid meets;
+    // 2: the trunk on the whole grid (one block_step call site for all of them)
+    int mode = grp < t.ngroups ? 0 : 1;
+    if (mode == 0 && threadIdx.x == 0) s_a = gargs[grp];
+    __syncthreads();
+    int Kt = t.split;
+    while (true) {
+        int K = -1;
+        trace_at(s_a, 0, mode);
+        if (mode == 0) {
+            trace_at(s_a, 3, 8);
+            if (crank(s_a) == 0 && threadIdx.x == 0) {
+                // the next ready block; slots past the last block end the group's work.  The
+                // block reaches the group's CTAs (this thread included) only through the slot
+                // word after the barrier, so that a failed barrier leaves every thread at -1.
+                const uint64_t t0 = gtimer();
+                int Kp = -1;
+                const int slot = atomicAdd(t.tctl, 1);
+                if (slot < t.split) {
+                    long long it = 0;
+                    while ((Kp = ld_acquire_s32(t.queue + slot)) < 0) {
+                        if (++it > s_a.spin_limit) {
+                            if (atomicCAS(s_a.status, 0, DEV_TIMEOUT) == 0) s_a.info[INFO_TIMEOUT_SITE] = 9;
+                            break;
+                        }
+                        if ((it & 63) == 0 && ld_acquire_s32(s_a.status) != DEV_OK) break;  // another group failed
+                        if (s_a.trace && (it & 1023) == 0) s_a.trace[8 * blockIdx.x + 5] = (int32_t)(it >> 10);
+                        if (it > 64) __nanosleep(64);
+                    }
+                }
+                st_release_s32(t.tctl + 2 + grp, Kp);
+                tm.tidle += gtimer() - t0;
+            }
+            trace_at(s_a, 3, 0);
+            trace_at(s_a, 2, 8);
+            if (grid_barrier(s_a.bar, s_a.G + s_a.debug_extra_cta, s_a.status, s_a.spin_limit, s_a.info, 8, trace_hb(s_a))) {
+                if (threadIdx.x == 0) {
+                    s_K = ld_acquire_s32(t.tctl + 2 + grp);
+                    tm.tprev = gtimer();
+                }
+                __syncthreads();
+                K = s_K;
+                __syncthreads();
+            }
+            if (K < 0 || K >= t.split) mode = 1;
+        }
+        if (mode == 1) {
+            if (grp < t.ngroups && crank(s_a) == 0 && threadIdx.x == 0) store_timers(s_a, tm);
+            const FactorArgs &a0 = gargs[0];
+            trace_at(s_a, 0, 1);
+            trace_at(s_a, 2, 10);
+            if (!grid_barrier(t.fullbar, gridDim.x + t.extra, a0.status, a0.spin_limit, a0.info, 10, trace_hb(s_a))) {
+                trace_at(s_a, 0, 9);
+                return;
+            }
+            if (t.split >= t.nb) {
+                trace_at(s_a, 0, 9);
+                return;
+            }
+            if (threadIdx.x == 0) {
+                s_a = a0;
+                s_a.G = gridDim.x;
+                s_a.bar = t.fullbar;
+            }
+            __syncthreads();
+            tm = StepTimers{};
+            tm.tprev = gtimer();
+            mode = 2;
+        }
+        if (mode == 2) {
+            if (Kt >= t.nb) {
+                if (blockIdx.x == 0 && threadIdx.x == 0) store_timers(s_a, tm);
+                trace_at(s_a, 0, 9);
+                return;
+            }
+            K = Kt++;
+        }
+        trace_at(s_a, 1, K);
+        const bool ok = block_step<TS>(s_a, K, smem, tm);
+        if (mode == 2) {
+            if (!ok) {
+                trace_at(s_a, 0, 9);
+                return;
+            }
+            continue;
+        }
+        if (!ok) {  // every CTA of the group leaves at the same barrier; the grid meets
+            mode = 1;
+            continue;
+        }
+        if (crank(s_a) == 0 && threadIdx.x == 0) {
+            // the block is complete (the barrier at the end of its step): count it off at its
+            // parent, which is queued when this was its last unfinished child
+            const int p = t.parent[K];
+            if (p >= 0 && p < t.split && atom_add_acqrel_s32(t.pending + p, -1) == 1) {
+                const int pos = atomicAdd(t.tctl + 1, 1);
+                st_release_s32(t.queue + pos, p);
+            }
+        }
+    }
+}
+
+// Closing copy of the tree schedule, part 1 (one CTA): block-ordered offsets of the kept rows
+// and columns and of their values, the exclusive prefix sums of the blocks' counts.
+__device__ __forceinline__ long long block_excl_scan_ll(long long v, long long *ws, long long *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    long long inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long u = __shfl_up_sync(FULL_MASK, inc, o);
+        if (lane >= o) inc += u;
+    }
+    if (lane == 31) ws[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const long long x = lane < nw ? ws[lane] : 0;
+        long long xi = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long u = __shfl_up_sync(FULL_MASK, xi, o);
+            if (lane >= o) xi += u;
+        }
+        if (lane < nw) ws[lane] = xi - x;
+        if (lane == nw - 1) ws[32] = xi;
+    }
+    __syncthreads();
+    const long long res = inc - v + ws[warp];
+    *total = ws[32];
+    __syncthreads();
+    return res;
+}
+
+__global__ void __launch_bounds__(1024) tree_offsets_kernel(int nb, const int32_t *bstart, const int64_t *aptr,
+                                                            int64_t *Lptr, int64_t *Lvptr, int64_t *Uptr,
+                                                            int64_t *Uvptr, int64_t cap0, int64_t cap1, int64_t cap2,
+                                                            int64_t cap3, int32_t *status) {
+    __shared__ long long ws[33];
+    if (*status != DEV_OK) return;
+    long long carry[4] = {0, 0, 0, 0};
+    int64_t *out[4] = {Lptr, Lvptr, Uptr, Uvptr};
+    for (int c0 = 0; c0 < nb; c0 += blockDim.x) {
+        const int K = c0 + threadIdx.x;
+        long long v[4] = {0, 0, 0, 0};
+        if (K < nb) {
+            const long long bK = bstart[K + 1] - bstart[K];
+            v[0] = aptr[(int64_t)nb + K] - aptr[K];
+            v[1] = v[0] * bK;
+            v[2] = aptr[4 * (int64_t)nb + K] - aptr[3 * (int64_t)nb + K];
+            v[3] = v[2] * bK;
+        }
+        for (int q = 0; q < 4; ++q) {
+            long long tot;
+            const long long ex = block_excl_scan_ll(v[q], ws, &tot);
+            if (K < nb) out[q][K] = carry[q] + ex;
+            carry[q] += tot;
+        }
+    }
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < 4; ++q) out[q][nb] = carry[q];
+        // the block-ordered pools must hold every kept entry (else grow them and run again)
+        if (carry[0] > cap0 || carry[1] > cap1 || carry[2] > cap2 || carry[3] > cap3) *status = DEV_POOL_OVERFLOW;
+    }
+}
+
+// Part 2: every block's kept row indices and values (and column indices and values) from its
+// chunk positions to the block-ordered pools that the apply sweeps and bilu_export read.
+template <class TS>
+__global__ void __launch_bounds__(256) tree_copy_kernel(int nb, const int32_t *bstart, const int64_t *aptr,
+                                                        const int64_t *Lptr, const int64_t *Lvptr, const int64_t *Uptr,
+                                                        const int64_t *Uvptr, const int32_t *aLrow, const int32_t *aUcol,
+                                                        const TS *aLval, const TS *aUval, int32_t *Lrow, int32_t *Ucol,
+                                                        TS *Lval, TS *Uval, const int32_t *status) {
+    if (*status != DEV_OK) return;
+    for (int K = blockIdx.x; K < nb; K += gridDim.x) {
+        const int64_t bK = bstart[K + 1] - bstart[K];
+        const int64_t cL = aptr[(int64_t)nb + K] - aptr[K], cU = aptr[4 * (int64_t)nb + K] - aptr[3 * (int64_t)nb + K];
+        const int32_t *sLr = aLrow + aptr[K], *sUc = aUcol + aptr[3 * (int64_t)nb + K];
+        const TS *sLv = aLval + aptr[2 * (int64_t)nb + K], *sUv = aUval + aptr[5 * (int64_t)nb + K];
+        int32_t *dLr = Lrow + Lptr[K], *dUc = Ucol + Uptr[K];
+        TS *dLv = Lval + Lvptr[K], *dUv = Uval + Uvptr[K];
+        for (int64_t e = threadIdx.x; e < cL; e += blockDim.x) dLr[e] = sLr[e];
+        for (int64_t e = threadIdx.x; e < cU; e += blockDim.x) dUc[e] = sUc[e];
+        for (int64_t e = threadIdx.x; e < cL * bK; e += blockDim.x) dLv[e] = sLv[e];
+        for (int64_t e = threadIdx.x; e < cU * bK; e += blockDim.x) dUv[e] = sUv[e];
+    }
+}
+
 // Self-test of recip_nr against the IEEE quotient 1.0 / p on n values spread over many
 // binades (test hook).  out[0] = number of results more than one ulp away.
 __global__ void recip_selftest_kernel(int n, unsigned long long seed, int *out) {
@@ -1464,6 +1813,12 @@ void factor_free(bilu_ctx *c) {
     dev_free(c->d_Lnrm); dev_free(c->d_Unrm); dev_free(c->d_nrmL); dev_free(c->d_nrmU);
     dev_free(c->d_dcolsq); dev_free(c->d_pivdone);
     c->capLrow = c->capLval = c->capUcol = c->capUval = 0;
+    dev_free(c->d_grp_big); dev_free(c->d_grp_reset);
+    c->grp_n = 0;
+    c->grp_big_bytes = c->grp_reset_bytes = 0;
+    dev_free(c->d_aLrow); dev_free(c->d_aUcol); dev_free(c->d_aLval); dev_free(c->d_aUval);
+    dev_free(c->d_aLnrm); dev_free(c->d_aUnrm); dev_free(c->d_aptr);
+    for (auto &v : c->capA) v = 0;
 }
 
 namespace {
@@ -1503,6 +1858,8 @@ long long g_debug_spin_limit = 0;   // polls before a bounded wait gives up (0: 
 long long g_debug_batch_group = 0;  // batch group size (0: tuned)
 int g_debug_small_pools = 0;        // factorizations start from minimal pools and producer lists
 int g_debug_poison = 0;             // factor storage is filled with NaN before every run
+int g_debug_no_trunk = 0;           // the tree schedule leaves no trunk to the whole grid
+int g_debug_trace = 0;              // the tree schedule prints one line per run to stderr
 
 bilu_status factor_alloc(bilu_ctx *c) {
     factor_free(c);
@@ -1572,8 +1929,8 @@ cudaError_t prepare_run(bilu_ctx *c, cudaStream_t st) {
     if ((e = cudaMemsetAsync(c->d_Uvptr, 0, (nb + 1) * sizeof(int64_t), st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(c->d_prodLcnt, 0, nb * sizeof(int32_t), st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(c->d_prodUcnt, 0, nb * sizeof(int32_t), st)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(c->d_lastL, 0xff, nb * sizeof(int32_t), st)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(c->d_lastU, 0xff, nb * sizeof(int32_t), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(c->d_lastL, 0, nb * sizeof(int32_t), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(c->d_lastU, 0, nb * sizeof(int32_t), st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(c->d_bmL, 0, (n / 32 + 2) * sizeof(uint32_t), st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(c->d_bmU, 0, (n / 32 + 2) * sizeof(uint32_t), st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(c->d_status, 0, 4 * sizeof(int32_t), st)) != cudaSuccess) return e;
@@ -1583,12 +1940,13 @@ cudaError_t prepare_run(bilu_ctx *c, cudaStream_t st) {
         const int64_t nd = std::max<int64_t>(c->h_Dptr.back(), 1);
         const size_t vs = c->p.precision == BILU_PREC_FP64 ? 8 : c->p.precision == BILU_PREC_FP32 ? 4 : 2;
         const size_t as = c->p.precision == BILU_PREC_FP64 ? 8 : 4;
+        const size_t tb = (size_t)c->capT * (size_t)std::max(c->bmax, 1) * as;
         struct { void *p; size_t bytes; } fill[] = {
-            {c->d_Dinv, nd * 8}, {c->d_Pblk, nd * 8}, {c->d_Lval, c->capLval * vs}, {c->d_Uval, c->capUval * vs},
-            {c->d_Lnrm, c->capLrow * 8},
-            {c->d_Unrm, c->capUcol * 8}, {c->d_TL, c->capT * (int64_t)std::max(c->bmax, 1) * as},
-            {c->d_TU, c->capT * (int64_t)std::max(c->bmax, 1) * as}, {c->d_LU, (BILU_MAX_BLOCK * BILU_MAX_BLOCK + BILU_MAX_BLOCK) * 8},
-            {c->d_dcolsq, BILU_MAX_BLOCK * 8}, {c->d_nrmL, c->capT * 8}, {c->d_nrmU, c->capT * 8}};
+            {c->d_Dinv, (size_t)nd * 8}, {c->d_Pblk, (size_t)nd * 8}, {c->d_Lval, (size_t)c->capLval * vs},
+            {c->d_Uval, (size_t)c->capUval * vs}, {c->d_Lnrm, (size_t)c->capLrow * 8},
+            {c->d_Unrm, (size_t)c->capUcol * 8}, {c->d_TL, tb}, {c->d_TU, tb},
+            {c->d_LU, (size_t)(BILU_MAX_BLOCK * BILU_MAX_BLOCK + BILU_MAX_BLOCK) * 8},
+            {c->d_dcolsq, (size_t)BILU_MAX_BLOCK * 8}, {c->d_nrmL, (size_t)c->capT * 8}, {c->d_nrmU, (size_t)c->capT * 8}};
         for (auto &f : fill)
             if ((e = cudaMemsetAsync(f.p, 0xff, f.bytes, st)) != cudaSuccess) return e;
     }
@@ -1628,6 +1986,8 @@ FactorArgs make_args(bilu_ctx *c, double droptol, int G) {
     a.LU = c->d_LU; a.perm = c->d_perm; a.kst = c->d_kstate; a.status = c->d_status; a.info = c->d_info;
     a.bar = c->d_bar;
     a.debug_extra_cta = g_debug_extra_cta;
+    a.trace = nullptr;
+    a.timeline = nullptr;
     // recording takes exact samples: no skipping while it is on
     const bool rec = c->rec_cap > 0;
     a.skip_bound = c->p.skip == BILU_SKIP_BOUND && !rec ? 1 : 0;
@@ -1647,6 +2007,10 @@ FactorArgs make_args(bilu_ctx *c, double droptol, int G) {
     a.rec_count = c->d_rec_count;
     a.Lnrm = c->d_Lnrm; a.Unrm = c->d_Unrm; a.nrmL = c->d_nrmL; a.nrmU = c->d_nrmU;
     a.dcolsq = c->d_dcolsq; a.pivdone = c->d_pivdone;
+    a.Lend = c->d_Lptr + 1;  // chain schedule: block K ends where block K + 1 starts
+    a.Uend = c->d_Uptr + 1;
+    a.arena = 0;
+    a.sortprod = 0;
     return a;
 }
 
@@ -1715,11 +2079,323 @@ static cudaError_t record_begin(bilu_ctx *c) {
     return e;
 }
 
+// ---------------------------------------------------------------- tree schedule, host side
+
+namespace {
+
+// One group's scratch, carved from the groups' two allocations (base == nullptr: sizes only).
+// `big` holds the candidate buffers and plans, `reset` what must be zero before every run
+// (bitmaps, barrier, pivot-tile count, producer de-duplication, chunk cursors).
+struct GroupPtrs {
+    double *TL, *TU, *TLP, *LU, *nrmL, *nrmU, *dcolsq;
+    int32_t *rowsL, *rowsU, *keepL, *keepU, *wbL, *wbU, *xslotL, *xslotU, *perm, *kst;
+    int64_t *pinfoL, *pinfoU;
+    uint32_t *bmL, *bmU, *bar, *pivdone;
+    int32_t *lastL, *lastU;
+    int64_t *gcur;
+};
+
+template <class T>
+void take(char *base, size_t &off, T *&p, int64_t count) {
+    off = (off + 255) & ~(size_t)255;
+    p = base ? (T *)(base + off) : nullptr;
+    off += (size_t)std::max<int64_t>(count, 1) * sizeof(T);
+}
+
+size_t carve_big(const bilu_ctx *c, char *base, GroupPtrs &g) {
+    size_t off = 0;
+    const int64_t bmax = std::max(c->bmax, 1), n = std::max<int64_t>(c->n, 1);
+    take(base, off, g.TL, c->capT * bmax);
+    take(base, off, g.TU, c->capT * bmax);
+    take(base, off, g.TLP, (int64_t)PPART * BILU_MAX_BLOCK * BILU_MAX_BLOCK);
+    take(base, off, g.LU, BILU_MAX_BLOCK * BILU_MAX_BLOCK + BILU_MAX_BLOCK);
+    take(base, off, g.nrmL, c->capT);
+    take(base, off, g.nrmU, c->capT);
+    take(base, off, g.dcolsq, BILU_MAX_BLOCK);
+    take(base, off, g.rowsL, c->capT);
+    take(base, off, g.rowsU, c->capT);
+    take(base, off, g.keepL, c->capT);
+    take(base, off, g.keepU, c->capT);
+    take(base, off, g.wbL, n / 32 + 2);
+    take(base, off, g.wbU, n / 32 + 2);
+    take(base, off, g.xslotL, c->capXS);
+    take(base, off, g.xslotU, c->capXS);
+    take(base, off, g.perm, BILU_MAX_BLOCK);
+    take(base, off, g.kst, 16);
+    take(base, off, g.pinfoL, (int64_t)PIS * c->prodcap);
+    take(base, off, g.pinfoU, (int64_t)PIS * c->prodcap);
+    return (off + 255) & ~(size_t)255;
+}
+
+size_t carve_reset(const bilu_ctx *c, char *base, GroupPtrs &g) {
+    size_t off = 0;
+    const int64_t n = std::max<int64_t>(c->n, 1), nb = std::max<int64_t>(c->nb, 1);
+    take(base, off, g.gcur, 16);
+    take(base, off, g.bar, 4);
+    take(base, off, g.pivdone, 4);
+    take(base, off, g.bmL, n / 32 + 2);
+    take(base, off, g.bmU, n / 32 + 2);
+    take(base, off, g.lastL, nb);
+    take(base, off, g.lastU, nb);
+    return (off + 255) & ~(size_t)255;
+}
+
+cudaError_t alloc_groups(bilu_ctx *c, int ng) {
+    if (c->grp_n == ng && c->grp_key[0] == c->capT && c->grp_key[1] == c->prodcap && c->grp_key[2] == c->capXS)
+        return cudaSuccess;
+    dev_free(c->d_grp_big);
+    dev_free(c->d_grp_reset);
+    c->grp_n = 0;
+    GroupPtrs g{};
+    c->grp_big_bytes = carve_big(c, nullptr, g);
+    c->grp_reset_bytes = carve_reset(c, nullptr, g);
+    cudaError_t e;
+    if ((e = dev_alloc(&c->d_grp_big, (int64_t)(c->grp_big_bytes * ng))) != cudaSuccess) return e;
+    if ((e = dev_alloc(&c->d_grp_reset, (int64_t)(c->grp_reset_bytes * ng))) != cudaSuccess) return e;
+    c->grp_n = ng;
+    c->grp_key[0] = c->capT;
+    c->grp_key[1] = c->prodcap;
+    c->grp_key[2] = c->capXS;
+    return cudaSuccess;
+}
+
+// The chunked pools of the tree schedule, as large as the block-ordered pools or larger.
+cudaError_t alloc_arena(bilu_ctx *c, const int64_t cap[4]) {
+    dev_free(c->d_aLrow); dev_free(c->d_aUcol); dev_free(c->d_aLval); dev_free(c->d_aUval);
+    dev_free(c->d_aLnrm); dev_free(c->d_aUnrm);
+    for (auto &v : c->capA) v = 0;
+    cudaError_t e;
+    if ((e = dev_alloc(&c->d_aLrow, cap[0])) != cudaSuccess || (e = dev_alloc(&c->d_aLnrm, cap[0])) != cudaSuccess ||
+        (e = dev_alloc(&c->d_aLval, cap[1])) != cudaSuccess || (e = dev_alloc(&c->d_aUcol, cap[2])) != cudaSuccess ||
+        (e = dev_alloc(&c->d_aUnrm, cap[2])) != cudaSuccess || (e = dev_alloc(&c->d_aUval, cap[3])) != cudaSuccess)
+        return e;
+    for (int q = 0; q < 4; ++q) c->capA[q] = cap[q];
+    return cudaSuccess;
+}
+
+const void *tree_kernel_for(int precision) {
+    return precision == BILU_PREC_FP32   ? (const void *)bilu_factor_tree_kernel<float>
+           : precision == BILU_PREC_BF16 ? (const void *)bilu_factor_tree_kernel<__nv_bfloat16>
+                                         : (const void *)bilu_factor_tree_kernel<double>;
+}
+
+template <class TS>
+cudaError_t launch_tree_copy(bilu_ctx *c, int grid) {
+    tree_copy_kernel<TS><<<grid, 256, 0, c->stream>>>(
+        c->nb, c->d_bstart, c->d_aptr, c->d_Lptr, c->d_Lvptr, c->d_Uptr, c->d_Uvptr, c->d_aLrow, c->d_aUcol,
+        (const TS *)c->d_aLval, (const TS *)c->d_aUval, c->d_Lrow, c->d_Ucol, (TS *)c->d_Lval, (TS *)c->d_Uval,
+        c->d_status);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// Tree schedule: groups of G CTAs factor independent subtrees of the block elimination tree,
+// the whole grid the trunk; then the kept rows and columns are copied from the groups' chunks
+// into the block-ordered pools.
+static bilu_status factor_tree_run(bilu_ctx *c, double droptol) {
+    if (c->p.skip == BILU_SKIP_LEARNED || c->rec_cap > 0)
+        return set_err(c, BILU_ERR_ARG, "the tree schedule does not run the learned skip or sample recording");
+    const void *kfn = tree_kernel_for(c->p.precision);
+    BILU_CUDA(c, cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    int per_sm = 0;
+    BILU_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, NT, SMEM_BYTES));
+    if (per_sm < 1) return set_err(c, BILU_ERR_CUDA, "tree factor kernel cannot be resident");
+    const int grid = c->nsm;
+    const int G = std::max(1, std::min(grid, c->p.group_ctas > 0 ? c->p.group_ctas : 8));
+    const int ng = grid / G;
+    const int32_t nb = c->nb;
+    const int32_t split = g_debug_no_trunk ? nb : c->tree_split;
+    {
+        const bilu_status st = tree_init(c, split);
+        if (st != BILU_OK) return st;
+    }
+    cudaEvent_t e0, e1;
+    BILU_CUDA(c, cudaEventCreate(&e0));
+    BILU_CUDA(c, cudaEventCreate(&e1));
+    bilu_status result = BILU_OK;
+    bool finished = false;
+    for (int attempt = 0; attempt < 16; ++attempt) {
+        const int64_t need[4] = {c->capLrow, c->capLval, c->capUcol, c->capUval};
+        if (c->capA[0] < need[0] || c->capA[1] < need[1] || c->capA[2] < need[2] || c->capA[3] < need[3] ||
+            c->d_aptr == nullptr) {
+            const int64_t cap[4] = {std::max(need[0], c->capA[0]), std::max(need[1], c->capA[1]),
+                                    std::max(need[2], c->capA[2]), std::max(need[3], c->capA[3])};
+            if (alloc_arena(c, cap) != cudaSuccess) { result = set_err(c, BILU_ERR_OOM, "tree factor: arena allocation failed"); break; }
+            if (!c->d_aptr && dev_alloc(&c->d_aptr, 6 * (int64_t)std::max(nb, 1)) != cudaSuccess) {
+                result = set_err(c, BILU_ERR_OOM, "tree factor: allocation failed");
+                break;
+            }
+        }
+        if (alloc_groups(c, ng) != cudaSuccess) { result = set_err(c, BILU_ERR_OOM, "tree factor: group scratch allocation failed"); break; }
+        BILU_CUDA(c, prepare_run(c, c->stream));
+        BILU_CUDA(c, cudaMemsetAsync(c->d_grp_reset, 0, c->grp_reset_bytes * ng, c->stream));
+        const int64_t words = 14 + (int64_t)c->nsm + 2 * (int64_t)std::max(nb, 1);
+        BILU_CUDA(c, cudaMemcpyAsync(c->d_tree, c->d_tree0, words * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream));
+        std::vector<FactorArgs> h(ng);
+        for (int g = 0; g < ng; ++g) {
+            GroupPtrs gp{};
+            carve_big(c, c->d_grp_big + (size_t)g * c->grp_big_bytes, gp);
+            carve_reset(c, c->d_grp_reset + (size_t)g * c->grp_reset_bytes, gp);
+            FactorArgs a = make_args(c, droptol, G);
+            a.TL = gp.TL; a.TU = gp.TU; a.TLP = gp.TLP; a.LU = gp.LU; a.nrmL = gp.nrmL; a.nrmU = gp.nrmU;
+            a.dcolsq = gp.dcolsq; a.rowsL = gp.rowsL; a.rowsU = gp.rowsU; a.keepL = gp.keepL; a.keepU = gp.keepU;
+            a.wbL = gp.wbL; a.wbU = gp.wbU; a.xslotL = gp.xslotL; a.xslotU = gp.xslotU; a.perm = gp.perm;
+            a.kst = gp.kst; a.pinfoL = gp.pinfoL; a.pinfoU = gp.pinfoU; a.bmL = gp.bmL; a.bmU = gp.bmU;
+            a.bar = gp.bar; a.pivdone = gp.pivdone; a.lastL = gp.lastL; a.lastU = gp.lastU; a.gcur = gp.gcur;
+            // the pools are the arena; block K's rows are [Lptr[K], Lend[K]) there
+            a.Lrow = c->d_aLrow; a.Ucol = c->d_aUcol; a.Lval = c->d_aLval; a.Uval = c->d_aUval;
+            a.Lnrm = c->d_aLnrm; a.Unrm = c->d_aUnrm;
+            a.Lptr = c->d_aptr; a.Lend = c->d_aptr + nb; a.Lvptr = c->d_aptr + 2 * (int64_t)nb;
+            a.Uptr = c->d_aptr + 3 * (int64_t)nb; a.Uend = c->d_aptr + 4 * (int64_t)nb;
+            a.Uvptr = c->d_aptr + 5 * (int64_t)nb;
+            a.capLrow = c->capA[0]; a.capLval = c->capA[1]; a.capUcol = c->capA[2]; a.capUval = c->capA[3];
+            a.arena = 1;
+            a.sortprod = 1;
+            a.acur = (unsigned long long *)c->d_tree;
+            a.chunkR = std::max<int64_t>(1024, c->capA[0] / (16 * (int64_t)ng));
+            a.chunkV = std::max<int64_t>(1024 * (int64_t)std::max(c->bmax, 1), c->capA[1] / (16 * (int64_t)ng));
+            h[g] = a;
+        }
+        int32_t *h_trace = nullptr, *d_trace = nullptr;  // test hook: per-CTA progress, readable while running
+        if (g_debug_trace && cudaHostAlloc((void **)&h_trace, 8 * sizeof(int32_t) * grid, cudaHostAllocMapped) == cudaSuccess) {
+            for (int i = 0; i < 8 * grid; ++i) h_trace[i] = -1;
+            if (cudaHostGetDevicePointer((void **)&d_trace, h_trace, 0) != cudaSuccess) d_trace = nullptr;
+            for (auto &a : h) a.trace = d_trace;
+        }
+        int64_t *d_tl = nullptr;
+        if (g_debug_trace && dev_alloc(&d_tl, 8 * (int64_t)std::max(nb, 1)) == cudaSuccess) {
+            cudaMemsetAsync(d_tl, 0, 8 * sizeof(int64_t) * std::max(nb, 1), c->stream);
+            for (auto &a : h) a.timeline = d_tl;
+        }
+        FactorArgs *d_args = nullptr;
+        if (dev_alloc(&d_args, ng) != cudaSuccess) { result = set_err(c, BILU_ERR_OOM, "tree factor: allocation failed"); break; }
+        cudaError_t e = cudaMemcpyAsync(d_args, h.data(), ng * sizeof(FactorArgs), cudaMemcpyHostToDevice, c->stream);
+        TreeArgs t{};
+        t.nb = nb; t.split = split; t.ngroups = ng; t.G = G; t.extra = g_debug_extra_cta;
+        t.parent = c->d_parent;
+        t.fullbar = (uint32_t *)(c->d_tree + 8);
+        t.tctl = c->d_tree + 12;
+        t.pending = c->d_tree + 14 + c->nsm;
+        t.queue = t.pending + std::max(nb, 1);
+        void *args[] = {&d_args, &t};
+        if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+        if (e == cudaSuccess && nb > 0) {
+            e = cudaLaunchCooperativeKernel(kfn, dim3(grid), dim3(NT), args, SMEM_BYTES, c->stream);
+            if (e == cudaSuccess) {
+                tree_offsets_kernel<<<1, 1024, 0, c->stream>>>(nb, c->d_bstart, c->d_aptr, c->d_Lptr, c->d_Lvptr,
+                                                              c->d_Uptr, c->d_Uvptr, c->capLrow, c->capLval,
+                                                              c->capUcol, c->capUval, c->d_status);
+                e = cudaGetLastError();
+            }
+            const int cg = std::max(1, std::min<int>(nb, 4 * c->nsm));
+            if (e == cudaSuccess)
+                e = c->p.precision == BILU_PREC_FP32   ? launch_tree_copy<float>(c, cg)
+                    : c->p.precision == BILU_PREC_BF16 ? launch_tree_copy<__nv_bfloat16>(c, cg)
+                                                       : launch_tree_copy<double>(c, cg);
+            c->launches += 3;
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+        if (e == cudaSuccess && h_trace) {  // test hook: report where the CTAs are if the run takes long
+            const auto t0 = std::chrono::steady_clock::now();
+            int shots = 0;
+            while (cudaStreamQuery(c->stream) == cudaErrorNotReady && shots < 3) {
+                if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(5 + 5 * shots)) {
+                    for (int b0 = 0; b0 < grid; ++b0)
+                        if (h_trace[8 * b0] != 9)
+                            fprintf(stderr, "t+%ds cta %d: mode %d block %d barrier %d wait %d barrier-polls/1024 %d "
+                                    "pop-polls/1024 %d tile-wait-polls/1024 %d\n", 5 + 5 * shots, b0, h_trace[8 * b0],
+                                    h_trace[8 * b0 + 1], h_trace[8 * b0 + 2], h_trace[8 * b0 + 3], h_trace[8 * b0 + 4],
+                                    h_trace[8 * b0 + 5], h_trace[8 * b0 + 6]);
+                    fflush(stderr);
+                    ++shots;
+                }
+            }
+        }
+        int32_t status = 0;
+        int64_t info[INFO_COUNT];
+        unsigned long long used[4] = {0, 0, 0, 0};
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&status, c->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(info, c->d_info, sizeof(info), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(used, c->d_tree, sizeof(used), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (h_trace) cudaFreeHost(h_trace);
+        if (d_tl) {  // test hook: the per-block timeline, one line per block
+            std::vector<int64_t> tl(8 * (size_t)std::max(nb, 1));
+            if (cudaMemcpy(tl.data(), d_tl, tl.size() * sizeof(int64_t), cudaMemcpyDeviceToHost) == cudaSuccess && e == cudaSuccess)
+                for (int32_t K = 0; K < nb; ++K)
+                    fprintf(stderr, "tl %d %lld %lld %lld %lld %lld %lld %lld %lld\n", K, (long long)tl[8 * K],
+                            (long long)tl[8 * K + 1], (long long)tl[8 * K + 2], (long long)tl[8 * K + 3],
+                            (long long)tl[8 * K + 4], (long long)tl[8 * K + 5], (long long)tl[8 * K + 6],
+                            (long long)tl[8 * K + 7]);
+            dev_free(d_tl);
+        }
+        dev_free(d_args);
+        if (e != cudaSuccess) { result = cuda_err(c, e, "tree factor launch"); break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        c->t_factor_ms = ms;
+        if (g_debug_trace)
+            fprintf(stderr, "bilu tree factor: attempt %d status %d (block %lld, site %lld) %.3f ms; pools %lld %lld "
+                    "%lld %lld, arena used %llu %llu %llu %llu of %lld %lld %lld %lld; prodcap %d capXS %lld\n",
+                    attempt, status, (long long)info[INFO_FAIL_BLOCK], (long long)info[INFO_TIMEOUT_SITE], ms,
+                    (long long)c->capLrow, (long long)c->capLval, (long long)c->capUcol, (long long)c->capUval,
+                    used[0], used[1], used[2], used[3], (long long)c->capA[0], (long long)c->capA[1],
+                    (long long)c->capA[2], (long long)c->capA[3], c->prodcap, (long long)c->capXS);
+        if (status == DEV_POOL_OVERFLOW) {
+            // the arena grows at once to what the failed run's chunks asked for (a cursor counts
+            // every chunk handed out), the block-ordered pools to the kept totals the closing copy
+            // found (when it ran), both at least doubled
+            int64_t tot[4] = {0, 0, 0, 0};
+            if (nb > 0) {
+                BILU_CUDA(c, cudaMemcpy(&tot[0], c->d_Lptr + nb, sizeof(int64_t), cudaMemcpyDeviceToHost));
+                BILU_CUDA(c, cudaMemcpy(&tot[1], c->d_Lvptr + nb, sizeof(int64_t), cudaMemcpyDeviceToHost));
+                BILU_CUDA(c, cudaMemcpy(&tot[2], c->d_Uptr + nb, sizeof(int64_t), cudaMemcpyDeviceToHost));
+                BILU_CUDA(c, cudaMemcpy(&tot[3], c->d_Uvptr + nb, sizeof(int64_t), cudaMemcpyDeviceToHost));
+            }
+            int64_t *pc[4] = {&c->capLrow, &c->capLval, &c->capUcol, &c->capUval};
+            int64_t cap[4];
+            for (int q = 0; q < 4; ++q) {
+                cap[q] = std::max(2 * c->capA[q], (int64_t)used[q] + (int64_t)used[q] / 4);
+                const bool grow = (int64_t)used[q] > c->capA[q] || tot[q] > *pc[q];
+                if (grow) *pc[q] = std::max(2 * *pc[q], tot[q] + tot[q] / 4);
+            }
+            if (alloc_pools(c) != cudaSuccess || alloc_arena(c, cap) != cudaSuccess) {
+                result = set_err(c, BILU_ERR_OOM, "tree factor: growing the pools failed");
+                break;
+            }
+            c->pool_retries++;
+            continue;
+        }
+        bilu_status err = BILU_OK;
+        const int r = finish_run(c, status, info, &err);
+        if (r == 1) continue;
+        result = err;
+        finished = r == 0;
+        if (finished) {
+            c->idle_ms = info[INFO_IDLE_NS] * 1e-6;
+            // chunks left partly unused: keep a quarter of the arena free for the next run
+            bool grow = false;
+            for (int q = 0; q < 4; ++q) grow = grow || (int64_t)used[q] * 4 > c->capA[q] * 3;
+            if (grow) {
+                const int64_t cap[4] = {2 * c->capA[0], 2 * c->capA[1], 2 * c->capA[2], 2 * c->capA[3]};
+                if (alloc_arena(c, cap) != cudaSuccess) result = set_err(c, BILU_ERR_OOM, "tree factor: arena growth failed");
+            }
+        }
+        break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!finished && result >= 0) return set_err(c, BILU_ERR_OOM, "tree factor: too many pool re-runs");
+    return result;
+}
+
 bilu_status factor_run(bilu_ctx *c, double droptol) {
     if (c->d_Lptr == nullptr) {
         bilu_status st = factor_alloc(c);
         if (st != BILU_OK) return st;
     }
+    if (c->p.schedule == BILU_SCHED_TREE) return factor_tree_run(c, droptol);
     BILU_CUDA(c, record_begin(c));
     // kernel instance by the precision of the updates and the stored factor values
     const void *kfn = factor_kernel_for(c->p.precision);

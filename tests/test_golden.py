@@ -51,6 +51,8 @@ def check_factor(g, F, rtol=1e-15):
 def test_fixtures_are_present():
     assert set(os.listdir(GOLDEN)) >= {"block_crout_4x4.json", "scalar_crout_3x3_fill.json", "perturbation_2x2.json"}
     for name in os.listdir(GOLDEN):
+        if not name.endswith(".json"):  # computed/: oracle runs written by a script, not by hand
+            continue
         g = load(name)
         assert g["citation"] and g["derivation"]
 
