@@ -153,6 +153,10 @@ def block_step(A, F: dict, K: int, tau: float, blocks=None, magnitudes: bool = F
 U_FP32 = 2.0 ** -24
 U_BF16 = 2.0 ** -8
 U_FP64 = 2.0 ** -53
+# Gradual underflow adds an absolute error of at most half the smallest subnormal to a rounded
+# result: FP32 2^-150 (subnormals down to 2^-149), BF16 2^-134 (8-bit significand, the FP32
+# exponent range: subnormals down to 2^-133), FP64 2^-1075.
+ETA = {U_FP32: 2.0 ** -150, U_BF16: 2.0 ** -134, U_FP64: 2.0 ** -1075}
 
 
 def gamma(n: int, u: float) -> float:
@@ -174,6 +178,13 @@ class StepBounds:
 
 
 def step_bounds(R: BlockResult, u_acc: float, u_scale: float, u_store: float) -> StepBounds:
+    """(see below)"""
+    return _step_bounds(R, u_acc, u_scale, u_store, ETA.get(u_acc, 0.0), ETA.get(u_scale, 0.0),
+                        ETA.get(u_store, 0.0))
+
+
+def _step_bounds(R: BlockResult, u_acc: float, u_scale: float, u_store: float, eta_acc: float, eta_scale: float,
+                 eta_store: float) -> StepBounds:
     """First-order componentwise bounds of the error of one block step computed with reduced
     precision, against the same step in exact arithmetic on the same inputs (A and the earlier
     blocks' stored values), for a step that (a) accumulates every entry of T_L / T_U -- A's
@@ -188,28 +199,34 @@ def step_bounds(R: BlockResult, u_acc: float, u_scale: float, u_store: float) ->
               the LU factors P = Pi L^ U^ is within gamma_3b |L^||U^|)
       |dl_i| <= |dT_i| |D| + |T_i| |dD| + (u_scale + gamma_b(u_scale)) |T_i| |D|
       stored: + u_store |l_i|;  U-breve_j: gamma_m S_j + u_store |T_U[:,j]|
-      | ||l_i|| - ||l_i^exact|| | <= || bound of dl_i ||_2 (the triangle inequality)."""
+      | ||l_i|| - ||l_i^exact|| | <= || bound of dl_i ||_2 (the triangle inequality),
+    each with the absolute underflow terms of its format (ETA): m eta_acc per accumulated entry,
+    eta_scale (sum_k |T_ik| + b) per scaled entry (D_K rounded, b products and sums), eta_store
+    per stored value."""
     b = R.P.shape[0]
-    gm = gamma(R.nterms + 4, u_acc)
+    m = R.nterms + 4
+    gm = gamma(m, u_acc)
     gb = gamma(b, u_scale) + u_scale
     aD = np.abs(R.D)
-    dP = gm * R.SP
+    dP = gm * R.SP + m * eta_acc
     Pm, Lf, Uf = sla.lu(R.P)
     dD = aD @ (dP + 2.0 * gamma(4 * b, U_FP64) * (Pm @ (np.abs(Lf) @ np.abs(Uf)))) @ aD
     if len(R.lcand):
         aT = np.abs(R.TL)
-        dl = (gm * R.SL) @ aD + aT @ dD + gb * (aT @ aD)
+        dl = (gm * R.SL + m * eta_acc) @ aD + aT @ dD + gb * (aT @ aD)
+        dl += eta_scale * (aT.sum(axis=1, keepdims=True) + b)
     else:
         dl = np.zeros((0, b))
     if len(R.ucand):
         aU = np.abs(R.TU)
-        dU = gm * R.SU
-        du = aD @ dU.T + dD @ aU.T + gb * (aD @ aU.T)
-        du = du.T
+        dU = gm * R.SU + m * eta_acc
+        du = (aD @ dU.T + dD @ aU.T + gb * (aD @ aU.T)).T
+        du += eta_scale * (aU.sum(axis=1, keepdims=True) + b)
     else:
         dU = du = np.zeros((0, b))
     Lc = R.TL @ R.D if len(R.lcand) else np.zeros((0, b))
-    return StepBounds(L=dl, Lstore=dl + u_store * np.abs(Lc), U=dU + u_store * np.abs(R.TU) if len(R.ucand) else dU,
+    return StepBounds(L=dl, Lstore=dl + u_store * np.abs(Lc) + eta_store,
+                      U=dU + u_store * np.abs(R.TU) + eta_store if len(R.ucand) else dU,
                       P=dP, D=dD, lnorm=np.sqrt(np.sum(dl * dl, axis=1)), unorm=np.sqrt(np.sum(du * du, axis=1)))
 
 
