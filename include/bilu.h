@@ -83,7 +83,8 @@ typedef struct {
                             pays off on an ordering with independent subtrees (nested
                             dissection, bilu_nd_order); in natural order the tree is a chain.
                             Not with BILU_SKIP_LEARNED or sample recording (BILU_ERR_ARG).      */
-    int32_t group_ctas;  /* CTAs per group of BILU_SCHED_TREE, 1..number of SMs (0: 8)         */
+    int32_t group_ctas;  /* CTAs per group of BILU_SCHED_TREE, 1..number of SMs (0: an eighth of
+                            the SMs, 8 groups)                                                  */
 } bilu_params;
 
 typedef struct {
@@ -110,7 +111,7 @@ typedef struct {
     int64_t flop_upd_l;       /* 2 m n b_J summed over the L-side block updates        */
     int64_t flop_upd_u;       /* 2 m n b_J summed over the U-side block updates        */
     int64_t flop_scale;       /* 2 b_K^2 per candidate row and column (D_K products),
-                                 skipped candidates excluded                            */
+                                 skipped and bound-dropped candidates excluded          */
     int64_t flop_norm;        /* 2 b_K per candidate row and column (drop norms), ditto */
     double t_analyze_ms, t_factor_ms;
     int32_t pool_retries;     /* factor re-runs after growing the L/U pools             */
@@ -130,6 +131,10 @@ typedef struct {
     int32_t group_ctas;       /*   CTAs per group                                         */
     double idle_ms;           /*   time the groups waited for a ready block, summed over
                                    the groups (0 for the chain schedule)                 */
+    int64_t bound_drops;      /* candidates dropped unscaled: the upper bound
+                                 sum_k |T_ik| ||D_K(k,:)|| of the norm (columns: with the
+                                 column norms of D_K) was already <= tau, so the product
+                                 would have dropped them too; the factor is unchanged    */
 } bilu_stats_t;
 
 /* Fills *p with the defaults: FIXED blocking of 32 (max 64), tau_analyze 1e-2,

@@ -68,7 +68,7 @@ class bilu_stats_t(ct.Structure):
                 ("kernel_launches", ct.c_int64), ("phase_ms", ct.c_double * 8),
                 ("skipped_rows", ct.c_int64), ("skipped_cols", ct.c_int64), ("schedule", ct.c_int32),
                 ("tree_height", ct.c_int32), ("tree_trunk", ct.c_int32), ("group_ctas", ct.c_int32),
-                ("idle_ms", ct.c_double)]
+                ("idle_ms", ct.c_double), ("bound_drops", ct.c_int64)]
 
 
 class bilu_mlp_train_cfg(ct.Structure):

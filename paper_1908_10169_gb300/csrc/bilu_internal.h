@@ -37,6 +37,7 @@ enum {
     INFO_SKIP_ROWS = 18,     // candidate rows skipped (norm bound or classifier)
     INFO_SKIP_COLS = 19,     // candidate columns skipped
     INFO_IDLE_NS = 20,       // tree schedule: time the groups wait for a ready block (summed)
+    INFO_BOUND_DROPS = 21,   // candidates dropped by the norm bound of phase D, unscaled
     INFO_COUNT = 24
 };
 
@@ -155,7 +156,7 @@ struct bilu_ctx {
 
     // results of the last factorization
     int64_t kept_rows = 0, kept_cols = 0, nnz_l = 0, nnz_u = 0, cand_rows = 0, cand_cols = 0;
-    int64_t nperturb = 0, skipped_rows = 0, skipped_cols = 0;
+    int64_t nperturb = 0, skipped_rows = 0, skipped_cols = 0, bound_drops = 0;
     int32_t pool_retries = 0;
     int64_t launches = 0;          // kernels of this library launched on the context (graph nodes included)
     int64_t gm_graph_kernels = 0;  // kernel nodes of the captured GMRES cycle
@@ -217,6 +218,7 @@ bilu_status scale_permute_csr_host(int64_t n, const int64_t *rowptr, const int32
                                    const double *dr, int64_t *out_rowptr, int32_t *out_colind, double *out_val,
                                    std::string *err);
 bilu_status tree_init(bilu_ctx *c, int32_t split);
+int tree_group_ctas(const bilu_ctx *c);
 bilu_status nd_order_host(int64_t n, const int64_t *rowptr, const int32_t *colind, int32_t nb,
                           const int32_t *bstart, int32_t leaf, int32_t *perm, int32_t *bstart_out,
                           int32_t *order_out, std::string *err);

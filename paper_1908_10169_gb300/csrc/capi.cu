@@ -302,7 +302,7 @@ bilu_status bilu_stats(bilu_ctx *c, bilu_stats_t *o) {
     if (c->p.schedule == BILU_SCHED_TREE) {
         o->tree_height = c->tree_height;
         o->tree_trunk = c->nb - c->tree_split;
-        o->group_ctas = std::max(1, std::min(c->nsm, c->p.group_ctas > 0 ? c->p.group_ctas : 8));
+        o->group_ctas = tree_group_ctas(c);
     }
     if (c->state >= 2) {
         o->nnz_l = c->nnz_l;
@@ -323,6 +323,7 @@ bilu_status bilu_stats(bilu_ctx *c, bilu_stats_t *o) {
         o->skipped_rows = c->skipped_rows;
         o->skipped_cols = c->skipped_cols;
         o->idle_ms = c->p.schedule == BILU_SCHED_TREE ? c->idle_ms : 0.0;
+        o->bound_drops = c->bound_drops;
     }
     return BILU_OK;
 }

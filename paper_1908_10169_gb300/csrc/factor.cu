@@ -664,8 +664,22 @@ __device__ void phase_B_tile(const FactorArgs &a, int K, bool Lside, int sa, int
     ProdStage<TA> st;
     const int tbeg = part >= 0 ? pcnt * part / nparts : 0;
     const int tend = part >= 0 ? pcnt * (part + 1) / nparts : pcnt;
-    if (tbeg < tend) prefetch_producer<TS>(a, Lside, tbeg, sa, cnt, s0, b, sxs, sxe, pbJ, pny, poff, pxv, pyv, pyp, st);
-    for (int t = tbeg; t < tend; ++t) {
+    // the producers with entries in this tile, in increasing order (the others add nothing to
+    // it, so leaving them out keeps the sums and their order)
+    int32_t *tl = pxc;             // free after the searches above
+    int32_t *ws = (int32_t *)pn;   // scan scratch (pn is free after the feature pass)
+    int ntl = 0;
+    for (int c0 = tbeg; c0 < tend; c0 += NT) {
+        const int t = c0 + tid;
+        const int hit = (t < tend && sxe[t] > sxs[t] && pny[t] > 0) ? 1 : 0;
+        int tot;
+        const int ex = block_excl_scan(hit, ws, &tot);
+        if (hit) tl[ntl + ex] = t;
+        ntl += tot;
+    }
+    __syncthreads();
+    if (ntl > 0) prefetch_producer<TS>(a, Lside, tl[0], sa, cnt, s0, b, sxs, sxe, pbJ, pny, poff, pxv, pyv, pyp, st);
+    for (int i = 0; i < ntl; ++i) {
         const int nx = st.nx, ny = st.ny, bJ = st.bJ;
         if (nx > 0) {
             if (nx > TRMAX || ny > b) {
@@ -698,7 +712,7 @@ __device__ void phase_B_tile(const FactorArgs &a, int K, bool Lside, int sa, int
         }
         __syncthreads();
         // the next producer's panels load while this one is multiplied
-        if (t + 1 < tend) prefetch_producer<TS>(a, Lside, t + 1, sa, cnt, s0, b, sxs, sxe, pbJ, pny, poff, pxv, pyv, pyp, st);
+        if (i + 1 < ntl) prefetch_producer<TS>(a, Lside, tl[i + 1], sa, cnt, s0, b, sxs, sxe, pbJ, pny, poff, pxv, pyv, pyp, st);
         if (nx > 0) {
             for (int e = tid; e < nx * ny; e += NT) {
                 const int x = e / ny, y = e - x * ny;
@@ -1018,6 +1032,16 @@ __device__ __forceinline__ void record_sample(const FactorArgs &a, int K, int si
 }
 
 // Normalised rows l_i = T_L[i,:] D_K and columns u^_j = D_K T_U[:,j]; keep iff ||.||_2 > tau.
+// A candidate is first tested against an upper bound of its norm, ||T_i D_K|| <= sum_k |T_ik|
+// ||D_K(k,:)|| (||D_K T_j|| <= sum_k ||D_K(:,k)|| |T_kj| for a column; triangle inequality): b
+// flops instead of the b^2 of the product.  When the bound, widened by the rounding of the
+// product (gamma_b of the arithmetic, covered by the margin), is <= tau, the computed norm
+// would be <= tau as well: the candidate is dropped unscaled (keep flag -2), with the decision
+// the product would have given.
+template <class TA> struct BoundMargin;
+template <> struct BoundMargin<double> { static constexpr double v = 1e-10; };
+template <> struct BoundMargin<float> { static constexpr double v = 1e-4; };
+
 template <class TS>
 __device__ void phase_D(const FactorArgs &a, int K, char *smem) {
     using TA = typename Prec<TS>::TA;
@@ -1029,12 +1053,30 @@ __device__ void phase_D(const FactorArgs &a, int K, char *smem) {
     // spread over every SM's FP64 pipe
     if (crank(a) >= total) return;
     TA *Ds = (TA *)smem;
+    double *rn = (double *)(Ds + BILU_MAX_BLOCK * PS);  // row norms of D_K (as used, in TA)
+    double *cn = rn + BILU_MAX_BLOCK;                   // column norms
     const double *D = a.Dinv + a.Dptr[K];
     for (int e = tid; e < b * b; e += NT) {
         const int r = e / b, c = e - r * b;
         Ds[r * PS + c] = (TA)ldcg(D + e);
     }
     __syncthreads();
+    for (int k = warp; k < b; k += NW) {
+        double sr = 0.0, sc = 0.0;
+        for (int c = lane; c < b; c += 32) {
+            const double vr = (double)Ds[k * PS + c], vc = (double)Ds[c * PS + k];
+            sr = fma(vr, vr, sr);
+            sc = fma(vc, vc, sc);
+        }
+        sr = warp_sum(sr);
+        sc = warp_sum(sc);
+        if (lane == 0) {
+            rn[k] = sqrt(sr);
+            cn[k] = sqrt(sc);
+        }
+    }
+    __syncthreads();
+    const double tau_b = a.tau / (1.0 + BoundMargin<TA>::v);
     for (int item = crank(a) + a.G * warp; item < total; item += a.G * NW) {
         if (item < nLc) {
             const int slot = b + item;
@@ -1042,6 +1084,13 @@ __device__ void phase_D(const FactorArgs &a, int K, char *smem) {
             TA *t = (TA *)a.TL + (int64_t)slot * b;
             const TA t0 = lane < b ? ldv(t + lane) : TA(0);
             const TA t1 = lane + 32 < b ? ldv(t + lane + 32) : TA(0);
+            const double bnd = warp_sum((lane < b ? fabs((double)t0) * rn[lane] : 0.0) +
+                                        (lane + 32 < b ? fabs((double)t1) * rn[lane + 32] : 0.0));
+            if (bnd <= tau_b) {
+                if (lane == 0) a.keepL[slot] = -2;
+                if (a.record) record_sample(a, K, 0, slot, ldcg(a.rowsL + slot), false);
+                continue;
+            }
             TA l0 = 0, l1 = 0, l0b = 0, l1b = 0;
             int k = 0;
             for (; k + 1 < b; k += 2) {
@@ -1072,6 +1121,13 @@ __device__ void phase_D(const FactorArgs &a, int K, char *smem) {
             const TA *t = (const TA *)a.TU + (int64_t)slot * b;
             const TA t0 = lane < b ? ldv(t + lane) : TA(0);
             const TA t1 = lane + 32 < b ? ldv(t + lane + 32) : TA(0);
+            const double bnd = warp_sum((lane < b ? fabs((double)t0) * cn[lane] : 0.0) +
+                                        (lane + 32 < b ? fabs((double)t1) * cn[lane + 32] : 0.0));
+            if (bnd <= tau_b) {
+                if (lane == 0) a.keepU[slot] = -2;
+                if (a.record) record_sample(a, K, 1, slot, ldcg(a.rowsU + slot), false);
+                continue;
+            }
             TA u0 = 0, u1 = 0, u0b = 0, u1b = 0;
             int k = 0;
             for (; k + 1 < b; k += 2) {
@@ -1124,22 +1180,27 @@ __device__ void phase_E(const FactorArgs &a, int K, char *smem) {
     // reserved for it in its group's chunks (tree schedule)
     const int64_t Lbase = ldcg(a.arena ? a.gcur + 8 : a.Lptr + K), LVbase = ldcg(a.arena ? a.gcur + 9 : a.Lvptr + K);
     const int64_t Ubase = ldcg(a.arena ? a.gcur + 10 : a.Uptr + K), UVbase = ldcg(a.arena ? a.gcur + 11 : a.Uvptr + K);
-    int keptL, keptU, skipped = 0;
+    int keptL, keptU, skipped = 0, bounded = 0;
     {
-        int lk = 0, uk = 0, sk = 0;
+        // keep flags: 1 kept, 0 dropped by its norm, -1 skipped before its updates (norm bound,
+        // classifier: neither scaled nor normed), -2 dropped by the bound of phase D (not scaled)
+        int lk = 0, uk = 0, sk = 0, bk = 0;
         for (int s = tid; s < nLc; s += NT) {
             const int k = ldcg(a.keepL + b + s);
             lk += k == 1;
-            sk += k < 0;
+            sk += k == -1;
+            bk += k == -2;
         }
         for (int s = tid; s < mU; s += NT) {
             const int k = ldcg(a.keepU + s);
             uk += k == 1;
-            sk += k < 0;
+            sk += k == -1;
+            bk += k == -2;
         }
         block_excl_scan(lk, ws, &keptL);
         block_excl_scan(uk, ws, &keptU);
-        if (a.skip_bound || a.learned) block_excl_scan(sk, ws, &skipped);  // skipped: neither scaled nor normed
+        block_excl_scan(sk, ws, &skipped);
+        block_excl_scan(bk, ws, &bounded);
     }
     const bool overflow = Lbase + keptL > a.capLrow || LVbase + (int64_t)keptL * b > a.capLval ||
                           Ubase + keptU > a.capUcol || UVbase + (int64_t)keptU * b > a.capUval;
@@ -1168,8 +1229,9 @@ __device__ void phase_E(const FactorArgs &a, int K, char *smem) {
         }
         atomicAdd((unsigned long long *)(a.info + INFO_CAND_ROWS), (unsigned long long)nLc);
         atomicAdd((unsigned long long *)(a.info + INFO_CAND_COLS), (unsigned long long)mU);
-        atomicAdd((unsigned long long *)(a.info + INFO_FLOP_SCALE), 2ULL * b * b * (unsigned long long)(nLc + mU - skipped));
+        atomicAdd((unsigned long long *)(a.info + INFO_FLOP_SCALE), 2ULL * b * b * (unsigned long long)(nLc + mU - skipped - bounded));
         atomicAdd((unsigned long long *)(a.info + INFO_FLOP_NORM), 2ULL * b * (unsigned long long)(nLc + mU - skipped));
+        if (bounded) atomicAdd((unsigned long long *)(a.info + INFO_BOUND_DROPS), (unsigned long long)bounded);
     }
     int32_t *wsl = sl + warp * 32;
     for (int side = 0; side < 2; ++side) {
@@ -2055,6 +2117,7 @@ int finish_run(bilu_ctx *c, int32_t status, const int64_t *info, bilu_status *er
     for (int p = 0; p < 6; ++p) c->phase_ms[p] = info[INFO_PHASE_NS + p] * 1e-6;
     c->phase_ms[6] = info[INFO_C2_WORK_NS] * 1e-6;
     c->phase_ms[7] = info[INFO_B_WORK_NS] * 1e-6;
+    c->bound_drops = info[INFO_BOUND_DROPS];
     c->skipped_rows = info[INFO_SKIP_ROWS];
     c->skipped_cols = info[INFO_SKIP_COLS];
     double f_lu = 0.0;  // getrf (2/3 b^3) and inverse (4/3 b^3) per diagonal block
@@ -2190,6 +2253,12 @@ cudaError_t launch_tree_copy(bilu_ctx *c, int grid) {
 
 }  // namespace
 
+// CTAs per group of the tree schedule: the caller's, else an eighth of the SMs (8 groups; on
+// the 64^3 benchmark groups of 19 CTAs beat 4, 8, 38 and 76).
+int tree_group_ctas(const bilu_ctx *c) {
+    return std::max(1, std::min(c->nsm, c->p.group_ctas > 0 ? c->p.group_ctas : std::max(1, c->nsm / 8)));
+}
+
 // Tree schedule: groups of G CTAs factor independent subtrees of the block elimination tree,
 // the whole grid the trunk; then the kept rows and columns are copied from the groups' chunks
 // into the block-ordered pools.
@@ -2202,7 +2271,7 @@ static bilu_status factor_tree_run(bilu_ctx *c, double droptol) {
     BILU_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, NT, SMEM_BYTES));
     if (per_sm < 1) return set_err(c, BILU_ERR_CUDA, "tree factor kernel cannot be resident");
     const int grid = c->nsm;
-    const int G = std::max(1, std::min(grid, c->p.group_ctas > 0 ? c->p.group_ctas : 8));
+    const int G = tree_group_ctas(c);
     const int ng = grid / G;
     const int32_t nb = c->nb;
     const int32_t split = g_debug_no_trunk ? nb : c->tree_split;

@@ -343,16 +343,18 @@ def test_degenerate_factors(ctx, case):
 
 def test_algorithmic_flop_counters_match_oracle(ctx):
     """The factor kernel counts its algorithmic work on the device; the integer counts
-    equal the oracle's (same candidate sets, same update shapes)."""
+    equal the oracle's (same candidate sets, same update shapes).  Candidates that the norm
+    bound of the scaling phase drops are not scaled: their 2 b^2 flops are the difference."""
     A = W.convdiff_upwind((16, 16, 16), seed=1)
     g = gpu_factor(ctx, A, 1e-2, _fixed(32), export=False)
     o = _oracle(A, g.bstart, 1e-2)
     c, s = o.counters, g.stats
     assert s.flop_upd_l == c["flop_upd_L"] and s.flop_upd_u == c["flop_upd_U"]
-    assert s.flop_scale == c["flop_scale"] and s.flop_norm == c["flop_norm"]
+    assert s.bound_drops > 0
+    assert s.flop_scale + 2 * 32 * 32 * s.bound_drops == c["flop_scale"] and s.flop_norm == c["flop_norm"]
     assert s.cand_rows == c["cand_rows"] and s.cand_cols == c["cand_cols"]
     total = sum(c[k] for k in ("flop_upd_L", "flop_upd_U", "flop_getrf", "flop_inv", "flop_scale", "flop_norm"))
-    assert abs(s.flops_factor - total) <= 1e-9 * total
+    assert abs(s.flops_factor + 2 * 32 * 32 * s.bound_drops - total) <= 1e-9 * total
 
 
 def test_newton_reciprocal_within_one_ulp_of_ieee(ctx):
@@ -376,52 +378,6 @@ def test_norm_bound_skip_gives_identical_factor(ctx, side, blk):
     assert g1.stats.skipped_rows + g1.stats.skipped_cols > 0
     assert g1.stats.flop_upd_l + g1.stats.flop_upd_u < g0.stats.flop_upd_l + g0.stats.flop_upd_u
     compare_factors(_oracle(A, g1.bstart, 1e-2), g1, A=A, tau=1e-2)
-
-
-def _rel_err_common(Fo, g):
-    """Max relative error of L / U-breve values over the blocks whose kept sets agree with the
-    oracle, and the number of blocks whose kept sets differ."""
-    from tests.gpu_helpers import _vptr
-    oLv, oUv, gLv, gUv = Fo.Lvptr(), Fo.Uvptr(), _vptr(g.Lptr, g.bstart), _vptr(g.Uptr, g.bstart)
-    err, differ = 0.0, 0
-    for K in range(len(Fo.bstart) - 1):
-        ro, rg = Fo.Lrow[Fo.Lptr[K]:Fo.Lptr[K + 1]], g.Lrow[g.Lptr[K]:g.Lptr[K + 1]]
-        co, cg = Fo.Ucol[Fo.Uptr[K]:Fo.Uptr[K + 1]], g.Ucol[g.Uptr[K]:g.Uptr[K + 1]]
-        if not (np.array_equal(ro, rg) and np.array_equal(co, cg)):
-            differ += 1
-            continue
-        for a, bb in ((Fo.Lval[oLv[K]:oLv[K + 1]], g.Lval[gLv[K]:gLv[K + 1]]),
-                      (Fo.Uval[oUv[K]:oUv[K + 1]], g.Uval[gUv[K]:gUv[K + 1]])):
-            if a.size:
-                err = max(err, float(np.abs(a - bb).max() / np.abs(a).max()))
-    return err, differ
-
-
-@pytest.mark.parametrize("prec,bound,max_differ", [(B.BILU_PREC_FP32, 1e-5, 0.05), (B.BILU_PREC_BF16, 1e-1, 1.0)])
-def test_mixed_precision_factor_and_gmres(ctx, prec, bound, max_differ):
-    """Updates and scaling in FP32 (or BF16 storage with FP32 accumulation); pivot LU, inverse,
-    drop norms and GMRES in FP64.  GMRES(30) reaches 1e-8 within 10 % of the FP64 iterations;
-    the factor's error against the FP64 oracle is bounded by the storage precision (BF16 rounds
-    at 2^-9 relative, and the rounding of earlier blocks enters later ones through the updates,
-    so the bound is 10 %).  With BF16 the rounding moves many rows across the drop threshold,
-    so the kept sets of later blocks differ from the oracle's; only FP32 bounds that count."""
-    import torch
-    A = W.convdiff_upwind((20, 20, 20), seed=1)
-    b = W.rhs_ones(A)
-    g64 = gpu_factor(ctx, A, 1e-2, _fixed(20), export=False)
-    bt = torch.from_numpy(b).cuda()
-    x64 = torch.zeros_like(bt)
-    it64 = B.gmres_solve(ctx, bt, x64, 1e-8, 30, 10000).iters
-    p = _fixed(20)
-    p.precision = prec
-    g = gpu_factor(ctx, A, 1e-2, p)
-    xm = torch.zeros_like(bt)
-    info = B.gmres_solve(ctx, bt, xm, 1e-8, 30, 10000)
-    assert info.status == B.BILU_OK and info.relres_true <= 1e-8
-    assert info.iters <= 1.1 * it64 + 1, (info.iters, it64)
-    err, differ = _rel_err_common(_oracle(A, g.bstart, 1e-2), g)
-    assert err <= bound, err
-    assert differ <= max_differ * (len(g.bstart) - 1), differ
 
 
 def test_batched_factor_and_gmres_match_one_by_one(ctx):

@@ -51,7 +51,7 @@ def same_factor(g1, g2):
         a, b = getattr(g1, k), getattr(g2, k)
         assert a.shape == b.shape and np.array_equal(a.view(np.uint8), b.view(np.uint8)), k
     for k in ("kept_rows", "kept_cols", "cand_rows", "cand_cols", "flop_upd_l", "flop_upd_u", "flop_scale",
-              "flop_norm", "nperturb", "skipped_rows", "skipped_cols"):
+              "flop_norm", "nperturb", "skipped_rows", "skipped_cols", "bound_drops"):
         assert getattr(g1.stats, k) == getattr(g2.stats, k), k
 
 
