@@ -3,11 +3,12 @@
 // bilu_apply relies on device buffers the context allocated when the factor was computed
 // (completion flags, sweep tickets, the forward-sweep plan) and, for host vectors, on
 // staging buffers allocated on first use.  Some callers cannot allocate at the moment they
-// apply the preconditioner: code running while a CUDA graph is being captured, programs
-// whose device memory is owned by a fixed pool or another framework's allocator, and
-// real-time loops that must not enter the allocator.  bilu_apply_noalloc serves them: it
-// allocates nothing.  Its only scratch is the fixed array below; the forward plan is
-// recomputed inside the kernel by searching the kept row lists.
+// apply the preconditioner: programs whose device memory is owned by a fixed pool or by
+// another framework's allocator, and real-time loops that must not enter the allocator.
+// bilu_apply_noalloc serves them: it allocates nothing.  Its only scratch is the fixed array
+// below; the forward plan is recomputed inside the kernel by searching the kept row lists.
+// A bounded wait that gives up ends the sweeps early; a last small kernel then fills z with
+// NaN, so that a timeout cannot pass for a result.
 //
 // The scratch is one file-scope __device__ array, so every GPU that loads the library holds
 // it until the process exits, and all calls on a device share it: calls that overlap on
@@ -15,6 +16,9 @@
 #include <mutex>
 
 #include "dev_common.cuh"
+
+extern int g_debug_extra_cta;         // test hooks (bilu_debug_set)
+extern long long g_debug_spin_limit;
 
 namespace {
 
@@ -47,12 +51,14 @@ struct NaArgs {
     const double *r;
     double *z;
     NoAllocScratch *sc;
+    long long spin;       // polls before a wait gives up
+    int32_t debug_wait;   // test hook: block 0 of the forward sweep waits for a flag nothing sets
 };
 
-__device__ __forceinline__ bool na_wait(const int32_t *flag, int32_t *status) {
+__device__ __forceinline__ bool na_wait(const int32_t *flag, int32_t *status, long long spin) {
     long long it = 0;
     while (ld_acquire_s32(flag) < 1) {
-        if (++it > NA_SPIN) {
+        if (++it > spin) {
             atomicCAS(status, 0, DEV_TIMEOUT);
             return false;
         }
@@ -77,6 +83,10 @@ __global__ void __launch_bounds__(NT) na_forward_kernel(NaArgs a) {
         const int K = s_K;
         __syncthreads();
         if (K >= a.nb) return;
+        if (a.debug_wait && K == 0) {  // flagF[nb] is cleared by the call and never set
+            const int ok = tid == 0 ? (na_wait(a.sc->flagF + a.nb, st + 3, a.spin) ? 1 : 0) : 1;
+            if (!__syncthreads_and(ok)) return;
+        }
         const int s0 = a.bstart[K], s1 = a.bstart[K + 1], b = s1 - s0;
         if (tid < b) acc[tid] = a.r[s0 + tid];
         const int pc = a.prodUcnt[K];
@@ -86,7 +96,7 @@ __global__ void __launch_bounds__(NT) na_forward_kernel(NaArgs a) {
             if (tid < cn) {
                 const int J = a.prodU[(int64_t)K * a.prodcap + c0 + tid];
                 sJ[tid] = J;
-                ok = na_wait(a.sc->flagF + J, st + 3) ? 1 : 0;
+                ok = na_wait(a.sc->flagF + J, st + 3, a.spin) ? 1 : 0;
             }
             if (!__syncthreads_and(ok)) return;
             for (int t = warp; t < cn; t += NW) {
@@ -165,7 +175,7 @@ __global__ void __launch_bounds__(NT) na_backward_kernel(NaArgs a) {
                 if (lane == 0) prev = last;
                 const bool first = q < q1 && blk != prev;
                 int okl = 1;
-                if (first) okl = na_wait(a.sc->flagB + blk, st + 3) ? 1 : 0;
+                if (first) okl = na_wait(a.sc->flagB + blk, st + 3, a.spin) ? 1 : 0;
                 ok = ok && __all_sync(FULL_MASK, okl);
                 last = __shfl_sync(FULL_MASK, blk, 31);
                 if (!ok) break;
@@ -203,6 +213,14 @@ __global__ void __launch_bounds__(NT) na_backward_kernel(NaArgs a) {
             st_release_s32(a.sc->flagB + K, 1);
         }
     }
+}
+
+// After the sweeps: when a wait gave up, z is incomplete; every entry becomes NaN.
+__global__ void __launch_bounds__(256) na_finish_kernel(NaArgs a, int64_t n) {
+    if (ldcg(a.sc->st + 3) == DEV_OK) return;
+    const double nan = __longlong_as_double(0x7ff8000000000000LL);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        a.z[i] = nan;
 }
 
 bool na_is_device_ptr(const void *p) {
@@ -246,7 +264,8 @@ extern "C" bilu_status bilu_apply_noalloc(bilu_ctx *c, const double *r, double *
     }
     // the array keeps the previous call's contents: clear the flags this factor uses and the
     // sweep state
-    BILU_CUDA(c, cudaMemsetAsync(sc->flagF, 0, (size_t)c->nb * sizeof(int32_t), c->stream));
+    const bool debug_wait = g_debug_extra_cta && c->nb < NA_MAX_BLOCKS;
+    BILU_CUDA(c, cudaMemsetAsync(sc->flagF, 0, (size_t)(c->nb + (debug_wait ? 1 : 0)) * sizeof(int32_t), c->stream));
     BILU_CUDA(c, cudaMemsetAsync(sc->flagB, 0, (size_t)c->nb * sizeof(int32_t), c->stream));
     BILU_CUDA(c, cudaMemsetAsync(sc->st, 0, sizeof(sc->st), c->stream));
     NaArgs a{};
@@ -260,10 +279,13 @@ extern "C" bilu_status bilu_apply_noalloc(bilu_ctx *c, const double *r, double *
     a.r = r;
     a.z = z;
     a.sc = sc;
+    a.spin = g_debug_spin_limit > 0 ? g_debug_spin_limit : NA_SPIN;
+    a.debug_wait = debug_wait ? 1 : 0;
     const int G = c->nsm * 2;
     na_forward_kernel<<<G, NT, 0, c->stream>>>(a);
     na_backward_kernel<<<G, NT, 0, c->stream>>>(a);
-    c->launches += 2;
+    na_finish_kernel<<<c->nsm, 256, 0, c->stream>>>(a, c->n);
+    c->launches += 3;
     BILU_CUDA(c, cudaGetLastError());
     return BILU_OK;
 }
