@@ -161,8 +161,13 @@ def test_learned_skip_needs_a_model(ctx):
 
 
 def test_learned_skip_gain_on_held_out_problem(ctx):
-    """Trained on small 3D problems (seeds 1000..), applied to a held-out one: candidates are
-    skipped, the update flops drop, and GMRES(30) still converges in about as many steps."""
+    """Trained on small 3D problems (seeds 1000..), applied to a held-out one, against the
+    exact norm-bound skip (BILU_SKIP_BOUND, the method without the classifier that skips only
+    what it can prove dropped) and against no skip: the classifier skips candidates before
+    their updates, so its update flops are below both; GMRES(30) stays within 10 % of the
+    iterations of the exact factor.  (Without a skip, the scaling phase already drops, unscaled,
+    every candidate whose norm bound is below tau: the total flops of the three differ mainly in
+    the updates.)"""
     import torch
     train = list(W.cd3d_skip_train(count=12, seed0=1000, side_lo=14, side_hi=20, block=64))
     x, y = LS.record(train, rate=0.5, cap_per_problem=200000)
@@ -171,7 +176,7 @@ def test_learned_skip_gain_on_held_out_problem(ctx):
     w = W.cd3d(side=24, seed=77, block=64)
     bt = torch.from_numpy(w.b).cuda()
     res = {}
-    for mode in (B.BILU_SKIP_NONE, B.BILU_SKIP_LEARNED):
+    for mode in (B.BILU_SKIP_NONE, B.BILU_SKIP_BOUND, B.BILU_SKIP_LEARNED):
         c = B.bilu_create(0)
         try:
             if mode == B.BILU_SKIP_LEARNED:
@@ -184,10 +189,15 @@ def test_learned_skip_gain_on_held_out_problem(ctx):
         finally:
             B.bilu_destroy(c)
     s0, i0 = res[B.BILU_SKIP_NONE]
+    sb, ib = res[B.BILU_SKIP_BOUND]
     s1, i1 = res[B.BILU_SKIP_LEARNED]
-    assert s1.skipped_rows + s1.skipped_cols > 0
-    # the skipped candidates are neither updated nor scaled: fewer algorithmic flops
-    assert s1.flop_upd_l + s1.flop_upd_u < s0.flop_upd_l + s0.flop_upd_u
-    assert s1.flops_factor < 0.85 * s0.flops_factor, (s1.flops_factor, s0.flops_factor)
+    upd = {k: v[0].flop_upd_l + v[0].flop_upd_u for k, v in res.items()}
+    print(f"update flops: none {upd[B.BILU_SKIP_NONE]}, bound {upd[B.BILU_SKIP_BOUND]}, learned "
+          f"{upd[B.BILU_SKIP_LEARNED]}; total flops {s0.flops_factor:.4g} / {sb.flops_factor:.4g} / "
+          f"{s1.flops_factor:.4g}; skipped bound {sb.skipped_rows + sb.skipped_cols}, learned "
+          f"{s1.skipped_rows + s1.skipped_cols}; GMRES {i0.iters} / {ib.iters} / {i1.iters}")
+    assert s1.skipped_rows + s1.skipped_cols > sb.skipped_rows + sb.skipped_cols > 0
+    assert upd[B.BILU_SKIP_LEARNED] < upd[B.BILU_SKIP_BOUND] < upd[B.BILU_SKIP_NONE]
+    assert ib.iters == i0.iters  # the exact skip gives the same factor
     assert i1.relres_true <= 1e-8
-    assert i1.iters <= 1.25 * i0.iters + 2, (i1.iters, i0.iters)
+    assert i1.iters <= 1.1 * i0.iters + 1, (i1.iters, i0.iters)
