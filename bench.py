@@ -294,6 +294,30 @@ def load_traffic():
     return out
 
 
+def fp64_gemm_tflops(dev, n=4096, reps=5):
+    """Measured FP64 rate of this GPU: cuBLAS DGEMM (torch.matmul, n^3 float64, 2 n^3 flops),
+    the best of `reps` timed with CUDA events after a warm-up; context for the derived FP64 peak
+    that the factor's roofline uses."""
+    import torch
+    try:
+        a = torch.randn(n, n, dtype=torch.float64, device=dev)
+        b = torch.randn(n, n, dtype=torch.float64, device=dev)
+        torch.matmul(a, b)
+        best = None
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        del a, b
+        return 2.0 * n ** 3 / (best * 1e-3) / 1e12
+    except Exception:
+        return None
+
+
 def oracle_step(w, bstart):
     """One full step of the FP64 CPU oracle (single thread): factor + GMRES(30)."""
     import oracle as O
@@ -556,6 +580,7 @@ def run_gpu(args):
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
+    fp64_meas = fp64_gemm_tflops(dev)
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
     applies_per_step = iters + restarts  # one per Arnoldi step, one per cycle for x
@@ -563,11 +588,13 @@ def run_gpu(args):
     share_apply = applies_per_step * t_apply / ms
     traffic = load_traffic()
     nvals = st.nnz_l + st.nnz_u + st.nnz_d
-    roof_factor = {"kernel": "bilu_factor_tree_kernel" if args.schedule == "tree" else "bilu_factor_kernel",
-                   "bound": "alu", "achieved": factor_tf,
+    kname = "bilu_factor_tree_kernel" if args.schedule == "tree" else "bilu_factor_kernel"
+    roof_factor = {"kernel": kname, "bound": "alu", "achieved": factor_tf,
                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": factor_tf / FP64_PEAK_TFLOPS,
                    "peak_source": "derived FP64 DFMA peak (152 SMs x 4 flop/clk x 2070 MHz)",
-                   "traffic": (traffic["bilu_factor_kernel"] * nvals) if "bilu_factor_kernel" in traffic else None,
+                   "peak_measured_fp64_gemm": fp64_meas,
+                   "frac_of_measured_fp64_gemm": factor_tf / fp64_meas if fp64_meas else None,
+                   "traffic": (traffic[kname] * nvals) if kname in traffic else None,
                    "traffic_source": "ncu dram bytes per stored factor value on 48^3 (profiles/), scaled",
                    "flops_per_launch": st.flops_factor, "ms_per_launch": t_factor, "share_of_step": share_factor}
     roof_apply = {"kernel": "apply_forward_kernel+apply_backward_kernel", "bound": "hbm", "achieved": apply_gbs,
