@@ -713,7 +713,40 @@ __device__ void phase_B_tile(const FactorArgs &a, int K, bool Lside, int sa, int
         __syncthreads();
         // the next producer's panels load while this one is multiplied
         if (i + 1 < ntl) prefetch_producer<TS>(a, Lside, tl[i + 1], sa, cnt, s0, b, sxs, sxe, pbJ, pny, poff, pxv, pyv, pyp, st);
-        if (nx > 0) {
+        if (nx > 0 && part >= 0) {
+            // pivot-row tile: at most TRP x 64 outputs for the CTA's 512 threads, so 4 adjacent
+            // lanes share an output and split its contraction (lane q takes k = q, q + 4, ...);
+            // their partial sums are combined by a fixed butterfly (same order for every launch)
+            constexpr int KS = 4;
+            const int q = tid & (KS - 1);
+            for (int base = 0; base < nx * ny; base += NT / KS) {
+                const int e = base + tid / KS;
+                bool on = e < nx * ny;
+                int x = 0, y = 0;
+                if (on) {
+                    x = e / ny;
+                    y = e - x * ny;
+                    on = !(useact && !act[xl[x]]);
+                }
+                TA s0a = 0, s1a = 0;
+                if (on) {
+                    const TA *xr = Xs + x * PS, *yr = Ys + y * PS;
+                    int k = q;
+                    for (; k + KS < bJ; k += 2 * KS) {
+                        s0a = fma(xr[k], yr[k], s0a);
+                        s1a = fma(xr[k + KS], yr[k + KS], s1a);
+                    }
+                    if (k < bJ) s0a = fma(xr[k], yr[k], s0a);
+                }
+                TA sum = s0a + s1a;
+                sum += __shfl_xor_sync(FULL_MASK, sum, 1);
+                sum += __shfl_xor_sync(FULL_MASK, sum, 2);
+                if (on && q == 0) {
+                    flops += 2LL * bJ;
+                    T[xl[x] * b + yc[y]] -= sum;
+                }
+            }
+        } else if (nx > 0) {
             for (int e = tid; e < nx * ny; e += NT) {
                 const int x = e / ny, y = e - x * ny;
                 if (useact && !act[xl[x]]) continue;
