@@ -23,6 +23,7 @@ struct ApplyArgs {
     const int64_t *Lptr, *Lvptr, *Uptr, *Uvptr, *Dptr;
     const int32_t *Lrow, *Ucol;
     const void *Lval, *Uval;  // factor values, storage type TS of the kernel instance
+    const void *Uhval;        // D_K U-breve_K, the layout of Uval (the backward sweep's columns)
     const double *Dinv;
     const int32_t *prodU, *prodUcnt;
     int32_t prodcap;
@@ -33,6 +34,15 @@ struct ApplyArgs {
     int32_t *st;           // [0] epoch, [1] forward ticket, [2] backward ticket, [3] status
     const int32_t *skip;   // optional: nonzero -> return immediately
 };
+
+// The factor values a block will read, fetched into L2 while it waits for its dependencies
+// (warp-cooperative, one 128-byte line per lane and step).
+__device__ __forceinline__ void warp_prefetch_l2(const void *p, int64_t bytes) {
+    const int lane = threadIdx.x & 31;
+    const uintptr_t beg = (uintptr_t)p & ~(uintptr_t)127, end = (uintptr_t)p + (uintptr_t)bytes;
+    for (uintptr_t q = beg + (uintptr_t)lane * 128; q < end; q += 32 * 128)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(q));
+}
 
 __device__ __forceinline__ bool wait_flag(const int32_t *flag, int epoch, int32_t *status) {
     long long it = 0;
@@ -68,7 +78,7 @@ __global__ void __launch_bounds__(AT) apply_forward_kernel(ApplyArgs a) {
     if (a.skip && ldcg(a.skip)) return;
     __shared__ double acc[BILU_MAX_BLOCK];
     __shared__ double dmat[FCH][BILU_MAX_BLOCK];
-    __shared__ int sps[FCH], soff[FCH + 1], sbJ[FCH], ssJ[FCH], sJ[FCH], sst[FCH];
+    __shared__ int sps[FCH], soff[FCH + 1], sbJ[FCH], ssJ[FCH], sJ[FCH], sst[FCH], scnt[FCH];
     __shared__ int srl[FCH], sro[FCH + 1];  // producers computed this round and their row offsets
     __shared__ int64_t sLv[FCH];
     __shared__ int s_K, s_ok, s_work, s_more, s_fold, s_nrd;
@@ -90,6 +100,7 @@ __global__ void __launch_bounds__(AT) apply_forward_kernel(ApplyArgs a) {
                 const int2 rg = a.planF[(int64_t)K * a.prodcap + c0 + tid];
                 sps[tid] = rg.x;
                 soff[tid + 1] = rg.y - rg.x;
+                scnt[tid] = rg.y - rg.x;
                 const int sj = a.bstart[J];
                 ssJ[tid] = sj;
                 sbJ[tid] = a.bstart[J + 1] - sj;
@@ -104,6 +115,9 @@ __global__ void __launch_bounds__(AT) apply_forward_kernel(ApplyArgs a) {
                 soff[0] = 0;
                 for (int t = 0; t < cn; ++t) soff[t + 1] += soff[t];
             }
+            // the chunk's L rows into L2 before the waits (warps 1.., one producer each)
+            for (int t = warp - 1; warp > 0 && t < cn; t += AW - 1)
+                warp_prefetch_l2((const TS *)a.Lval + sLv[t], (int64_t)scnt[t] * sbJ[t] * (int64_t)sizeof(TS));
             __syncthreads();
             while (true) {
                 if (warp == 0) {
@@ -207,17 +221,19 @@ __global__ void __launch_bounds__(AT) apply_forward_kernel(ApplyArgs a) {
     }
 }
 
-// Backward sweep, block K: the kept columns of U-breve_K in blocks after K+1 (complete early)
-// are multiplied while block K+1 -- the newest dependency -- may still be running; its own
-// columns (the leading range, the columns are sorted) follow once it is done.  Both partial
-// sums are formed in a fixed order, so the result does not depend on timing.
+// Backward sweep, block K: z_K = D_K y_K - (D_K U-breve_K) z(C_K).  D_K y_K is formed first,
+// before any wait (y_K is final after the forward sweep), so only the columns of the normalised
+// U (stored by the factor) lie on the sweep's critical path.  The kept columns in blocks after
+// K+1 (complete early) are multiplied while block K+1 -- the newest dependency -- may still be
+// running; its own columns (the leading range, the columns are sorted) follow once it is done.
+// The partial sums are formed in a fixed order, so the result does not depend on timing.
 template <class TS>
 __device__ __forceinline__ double backward_columns(const ApplyArgs &a, int K, int b, int64_t q0, int64_t qa,
                                                    int64_t qb, int g, int rr) {
     constexpr int NG = AT / BILU_MAX_BLOCK;  // column groups
     double s = 0.0;
     if (rr < b) {
-        const TS *Uv = (const TS *)a.Uval + a.Uvptr[K];
+        const TS *Uv = (const TS *)a.Uhval + a.Uvptr[K];
         int64_t q = qa + g;
         // four independent columns per iteration keep several loads in flight
         double s1 = 0.0, s2 = 0.0, s3 = 0.0;
@@ -264,7 +280,7 @@ __global__ void __launch_bounds__(AT) apply_backward_kernel(ApplyArgs a) {
     if (a.skip && ldcg(a.skip)) return;
     constexpr int NG = AT / BILU_MAX_BLOCK;  // column groups
     __shared__ double part[NG][BILU_MAX_BLOCK];
-    __shared__ double tv[BILU_MAX_BLOCK];
+    __shared__ double tv[BILU_MAX_BLOCK], yv[BILU_MAX_BLOCK];
     __shared__ int32_t rq[RMAX + 1], rblk[RMAX];
     __shared__ int s_K, s_ok, s_nr, s_take;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -278,7 +294,32 @@ __global__ void __launch_bounds__(AT) apply_backward_kernel(ApplyArgs a) {
         const int s0 = a.bstart[K], b = a.bstart[K + 1] - s0;
         const int64_t q0 = a.Uptr[K], q1 = a.Uptr[K + 1];
         const int g = tid / BILU_MAX_BLOCK, rr = tid % BILU_MAX_BLOCK;
-        if (tid < b) tv[tid] = ldcg(a.z + s0 + tid);
+        if (tid < b) yv[tid] = ldcg(a.z + s0 + tid);
+        // the normalised U columns into L2 before the waits
+        if (warp == 1) warp_prefetch_l2((const TS *)a.Uhval + a.Uvptr[K], (q1 - q0) * b * (int64_t)sizeof(TS));
+        __syncthreads();
+        {
+            // tv = D_K y_K: warp per row, four rows in flight
+            const double *D = a.Dinv + a.Dptr[K];
+            const double y0 = lane < b ? yv[lane] : 0.0, y1 = lane + 32 < b ? yv[lane + 32] : 0.0;
+            for (int r0 = warp * 4; r0 < b; r0 += AW * 4) {
+                double v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int r = r0 + u;
+                    v[u] = 0.0;
+                    if (r < b) {
+                        if (lane < b) v[u] = D[(int64_t)r * b + lane] * y0;
+                        if (lane + 32 < b) v[u] = fma(D[(int64_t)r * b + lane + 32], y1, v[u]);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const double w = warp_sum(v[u]);
+                    if (lane == 0 && r0 + u < b) tv[r0 + u] = w;
+                }
+            }
+        }
         // runs of kept columns by block (the columns are sorted): run i = [rq[i], rq[i+1])
         if (warp == 0) {
             int nr = 0, last = -1;
@@ -360,26 +401,7 @@ __global__ void __launch_bounds__(AT) apply_backward_kernel(ApplyArgs a) {
                 ri -= take;
             }
         }
-        // z_K = D_K t: warp per row
-        const double *D = a.Dinv + a.Dptr[K];
-        const double t0 = lane < b ? tv[lane] : 0.0, t1 = lane + 32 < b ? tv[lane + 32] : 0.0;
-        for (int r0 = warp * 4; r0 < b; r0 += AW * 4) {
-            double v[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int r = r0 + u;
-                v[u] = 0.0;
-                if (r < b) {
-                    if (lane < b) v[u] = D[(int64_t)r * b + lane] * t0;
-                    if (lane + 32 < b) v[u] = fma(D[(int64_t)r * b + lane + 32], t1, v[u]);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const double w = warp_sum(v[u]);
-                if (lane == 0 && r0 + u < b) a.z[s0 + r0 + u] = w;
-            }
-        }
+        if (tid < b) a.z[s0 + tid] = tv[tid];
         __syncthreads();
         if (tid == 0) {
             __threadfence();
@@ -447,6 +469,7 @@ bilu_status apply_launch(bilu_ctx *c, const double *d_r, double *d_z, const int3
     a.blkof = c->d_blkof;
     a.Lptr = c->d_Lptr; a.Lvptr = c->d_Lvptr; a.Uptr = c->d_Uptr; a.Uvptr = c->d_Uvptr; a.Dptr = c->d_Dptr;
     a.Lrow = c->d_Lrow; a.Ucol = c->d_Ucol; a.Lval = c->d_Lval; a.Uval = c->d_Uval; a.Dinv = c->d_Dinv;
+    a.Uhval = c->d_Uhval;
     a.prodU = c->d_prodU; a.prodUcnt = c->d_prodUcnt; a.prodcap = c->prodcap;
     a.planF = c->d_planF;
     a.r = d_r;

@@ -71,6 +71,7 @@ struct bilu_ctx {
     int64_t *d_Lptr = nullptr, *d_Lvptr = nullptr, *d_Uptr = nullptr, *d_Uvptr = nullptr;
     int32_t *d_Lrow = nullptr, *d_Ucol = nullptr;
     double *d_Lval = nullptr, *d_Uval = nullptr;
+    double *d_Uhval = nullptr;     // D_K U-breve_K, the layout of d_Uval (read by the backward sweep)
     double *d_Dinv = nullptr, *d_Pblk = nullptr;
     double *d_Lnrm = nullptr, *d_Unrm = nullptr;  // norms of the kept rows of L / columns of U-breve
 
@@ -81,7 +82,7 @@ struct bilu_ctx {
 
     // factor scratch
     int64_t capT = 0;
-    double *d_TL = nullptr, *d_TU = nullptr;
+    double *d_TL = nullptr, *d_TU = nullptr, *d_TUh = nullptr;
     double *d_TLP = nullptr;       // partial accumulators of the pivot rows (4 x 64 x 64)
     int32_t *d_rowsL = nullptr, *d_rowsU = nullptr;
     int32_t *d_keepL = nullptr, *d_keepU = nullptr;
@@ -116,7 +117,7 @@ struct bilu_ctx {
     int32_t *d_tree0 = nullptr, *d_tree = nullptr;  // initial / live: pending, queue, control words
     int64_t capA[4] = {0, 0, 0, 0}; // arena capacities (rows L, values L, columns U, values U)
     int32_t *d_aLrow = nullptr, *d_aUcol = nullptr;
-    double *d_aLval = nullptr, *d_aUval = nullptr, *d_aLnrm = nullptr, *d_aUnrm = nullptr;
+    double *d_aLval = nullptr, *d_aUval = nullptr, *d_aUhval = nullptr, *d_aLnrm = nullptr, *d_aUnrm = nullptr;
     int64_t *d_aptr = nullptr;      // 6 x nb: L begin, L end, L value begin, U begin, U end, U value begin
     double idle_ms = 0.0;           // last tree factorization: time its groups waited for ready blocks
 

@@ -80,11 +80,13 @@ struct FactorArgs {
     int64_t *Lptr, *Lvptr, *Uptr, *Uvptr;
     int32_t *Lrow, *Ucol;
     void *Lval, *Uval;           // factor values, storage type TS of the kernel instance
+    void *Uhval;                 // D_K U-breve_K (the normalised columns), layout of Uval, for the sweeps
     double *Dinv, *Pblk;
     int64_t capLrow, capLval, capUcol, capUval;
     int32_t prodcap;
     int32_t *prodL, *prodLcnt, *prodU, *prodUcnt, *lastL, *lastU;
     void *TL, *TU;               // candidate accumulators, type TA of the kernel instance
+    void *TUh;                   // per candidate column: u^_j = D_K T_U[:,j] (type TA)
     void *TLP;                   // pivot rows: PPART partial accumulators of b x b (type TA)
     int32_t *rowsL, *rowsU, *keepL, *keepU;
     uint32_t *bmL, *bmU;
@@ -1176,6 +1178,9 @@ __device__ void phase_D(const FactorArgs &a, int K, char *smem) {
             }
             u0 += u0b;
             u1 += u1b;
+            TA *th = (TA *)a.TUh + (int64_t)slot * b;  // the normalised column, for the sweeps
+            if (lane < b) th[lane] = u0;
+            if (lane + 32 < b) th[lane + 32] = u1;
             const double nrm2 = warp_sum((double)u0 * (double)u0 + (double)u1 * (double)u1);
             const double tn2 = warp_sum((double)t0 * (double)t0 + (double)t1 * (double)t1);
             if (lane == 0) {
@@ -1278,6 +1283,8 @@ __device__ void phase_E(const FactorArgs &a, int K, char *smem) {
         const int32_t *rows = isL ? a.rowsL : a.rowsU;
         const TA *Tb = (const TA *)(isL ? a.TL : a.TU);
         TS *pool = (TS *)(isL ? a.Lval : a.Uval) + (isL ? LVbase : UVbase);
+        const TA *Th = (const TA *)a.TUh;                        // U side: the normalised columns
+        TS *hpool = (TS *)a.Uhval + UVbase;
         int32_t *idxpool = isL ? a.Lrow + Lbase : a.Ucol + Ubase;
         double *nrmpool = isL ? a.Lnrm + Lbase : a.Unrm + Ubase;
         const double *nrmslot = isL ? a.nrmL : a.nrmU;
@@ -1328,6 +1335,7 @@ __device__ void phase_E(const FactorArgs &a, int K, char *smem) {
                 for (int e = tid; e < tot_e; e += NT) {
                     const int r = e / b, cc = e - r * b;
                     pool[(base + r) * b + cc] = store_of<TS>((double)ldv(Tb + (int64_t)wsl0[r] * b + cc));
+                    if (!isL) hpool[(base + r) * b + cc] = store_of<TS>((double)ldv(Th + (int64_t)wsl0[r] * b + cc));
                 }
                 if (kept) {
                     const int tb = a.blkof[idx];
@@ -1376,6 +1384,16 @@ __device__ void phase_E(const FactorArgs &a, int K, char *smem) {
                     for (int u = 0; u < 4; ++u) {
                         const int e = e0 + u * 32;
                         if (e < tot_e) pool[(base + e / b) * b + (e % b)] = store_of<TS>((double)v[u]);
+                    }
+                    if (!isL) {
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int e = e0 + u * 32;
+                            if (e < tot_e) {
+                                const int r = e / b, cc = e - r * b;
+                                hpool[(base + r) * b + cc] = store_of<TS>((double)ldv(Th + (int64_t)wsl[r] * b + cc));
+                            }
+                        }
                     }
                 }
                 __syncwarp();
@@ -1847,8 +1865,9 @@ template <class TS>
 __global__ void __launch_bounds__(256) tree_copy_kernel(int nb, const int32_t *bstart, const int64_t *aptr,
                                                         const int64_t *Lptr, const int64_t *Lvptr, const int64_t *Uptr,
                                                         const int64_t *Uvptr, const int32_t *aLrow, const int32_t *aUcol,
-                                                        const TS *aLval, const TS *aUval, int32_t *Lrow, int32_t *Ucol,
-                                                        TS *Lval, TS *Uval, const int32_t *status) {
+                                                        const TS *aLval, const TS *aUval, const TS *aUhval, int32_t *Lrow,
+                                                        int32_t *Ucol, TS *Lval, TS *Uval, TS *Uhval,
+                                                        const int32_t *status) {
     if (*status != DEV_OK) return;
     for (int K = blockIdx.x; K < nb; K += gridDim.x) {
         const int64_t bK = bstart[K + 1] - bstart[K];
@@ -1856,11 +1875,15 @@ __global__ void __launch_bounds__(256) tree_copy_kernel(int nb, const int32_t *b
         const int32_t *sLr = aLrow + aptr[K], *sUc = aUcol + aptr[3 * (int64_t)nb + K];
         const TS *sLv = aLval + aptr[2 * (int64_t)nb + K], *sUv = aUval + aptr[5 * (int64_t)nb + K];
         int32_t *dLr = Lrow + Lptr[K], *dUc = Ucol + Uptr[K];
-        TS *dLv = Lval + Lvptr[K], *dUv = Uval + Uvptr[K];
+        TS *dLv = Lval + Lvptr[K], *dUv = Uval + Uvptr[K], *dUh = Uhval + Uvptr[K];
+        const TS *sUh = aUhval + aptr[5 * (int64_t)nb + K];
         for (int64_t e = threadIdx.x; e < cL; e += blockDim.x) dLr[e] = sLr[e];
         for (int64_t e = threadIdx.x; e < cU; e += blockDim.x) dUc[e] = sUc[e];
         for (int64_t e = threadIdx.x; e < cL * bK; e += blockDim.x) dLv[e] = sLv[e];
-        for (int64_t e = threadIdx.x; e < cU * bK; e += blockDim.x) dUv[e] = sUv[e];
+        for (int64_t e = threadIdx.x; e < cU * bK; e += blockDim.x) {
+            dUv[e] = sUv[e];
+            dUh[e] = sUh[e];
+        }
     }
 }
 
@@ -1895,11 +1918,11 @@ int recip_selftest(int n) {
 
 void factor_free(bilu_ctx *c) {
     dev_free(c->d_Lptr); dev_free(c->d_Lvptr); dev_free(c->d_Uptr); dev_free(c->d_Uvptr);
-    dev_free(c->d_Lrow); dev_free(c->d_Ucol); dev_free(c->d_Lval); dev_free(c->d_Uval);
+    dev_free(c->d_Lrow); dev_free(c->d_Ucol); dev_free(c->d_Lval); dev_free(c->d_Uval); dev_free(c->d_Uhval);
     dev_free(c->d_Dinv); dev_free(c->d_Pblk);
     dev_free(c->d_prodL); dev_free(c->d_prodLcnt); dev_free(c->d_prodU); dev_free(c->d_prodUcnt);
     dev_free(c->d_lastL); dev_free(c->d_lastU);
-    dev_free(c->d_TL); dev_free(c->d_TU); dev_free(c->d_TLP); dev_free(c->d_rowsL); dev_free(c->d_rowsU);
+    dev_free(c->d_TL); dev_free(c->d_TU); dev_free(c->d_TUh); dev_free(c->d_TLP); dev_free(c->d_rowsL); dev_free(c->d_rowsU);
     dev_free(c->d_keepL); dev_free(c->d_keepU); dev_free(c->d_bmL); dev_free(c->d_bmU);
     dev_free(c->d_LU); dev_free(c->d_perm); dev_free(c->d_kstate); dev_free(c->d_status);
     dev_free(c->d_info); dev_free(c->d_bar);
@@ -1911,7 +1934,7 @@ void factor_free(bilu_ctx *c) {
     dev_free(c->d_grp_big); dev_free(c->d_grp_reset);
     c->grp_n = 0;
     c->grp_big_bytes = c->grp_reset_bytes = 0;
-    dev_free(c->d_aLrow); dev_free(c->d_aUcol); dev_free(c->d_aLval); dev_free(c->d_aUval);
+    dev_free(c->d_aLrow); dev_free(c->d_aUcol); dev_free(c->d_aLval); dev_free(c->d_aUval); dev_free(c->d_aUhval);
     dev_free(c->d_aLnrm); dev_free(c->d_aUnrm); dev_free(c->d_aptr);
     for (auto &v : c->capA) v = 0;
 }
@@ -1920,7 +1943,7 @@ namespace {
 
 cudaError_t alloc_pools(bilu_ctx *c) {
     cudaError_t e;
-    dev_free(c->d_Lrow); dev_free(c->d_Ucol); dev_free(c->d_Lval); dev_free(c->d_Uval);
+    dev_free(c->d_Lrow); dev_free(c->d_Ucol); dev_free(c->d_Lval); dev_free(c->d_Uval); dev_free(c->d_Uhval);
     dev_free(c->d_Lnrm); dev_free(c->d_Unrm);
     if ((e = dev_alloc(&c->d_Lnrm, c->capLrow)) != cudaSuccess) return e;
     if ((e = dev_alloc(&c->d_Unrm, c->capUcol)) != cudaSuccess) return e;
@@ -1928,6 +1951,7 @@ cudaError_t alloc_pools(bilu_ctx *c) {
     if ((e = dev_alloc(&c->d_Ucol, c->capUcol)) != cudaSuccess) return e;
     if ((e = dev_alloc(&c->d_Lval, c->capLval)) != cudaSuccess) return e;
     if ((e = dev_alloc(&c->d_Uval, c->capUval)) != cudaSuccess) return e;
+    if ((e = dev_alloc(&c->d_Uhval, c->capUval)) != cudaSuccess) return e;
     return cudaSuccess;
 }
 
@@ -1980,6 +2004,7 @@ bilu_status factor_alloc(bilu_ctx *c) {
         (e = dev_alloc(&c->d_lastL, nb)) != cudaSuccess || (e = dev_alloc(&c->d_lastU, nb)) != cudaSuccess ||
         (e = dev_alloc(&c->d_TL, c->capT * bmax)) != cudaSuccess ||
         (e = dev_alloc(&c->d_TU, c->capT * bmax)) != cudaSuccess ||
+        (e = dev_alloc(&c->d_TUh, c->capT * bmax)) != cudaSuccess ||
         (e = dev_alloc(&c->d_TLP, (int64_t)PPART * BILU_MAX_BLOCK * BILU_MAX_BLOCK)) != cudaSuccess ||
         (e = dev_alloc(&c->d_rowsL, c->capT)) != cudaSuccess || (e = dev_alloc(&c->d_rowsU, c->capT)) != cudaSuccess ||
         (e = dev_alloc(&c->d_keepL, c->capT)) != cudaSuccess || (e = dev_alloc(&c->d_keepU, c->capT)) != cudaSuccess ||
@@ -2038,7 +2063,8 @@ cudaError_t prepare_run(bilu_ctx *c, cudaStream_t st) {
         const size_t tb = (size_t)c->capT * (size_t)std::max(c->bmax, 1) * as;
         struct { void *p; size_t bytes; } fill[] = {
             {c->d_Dinv, (size_t)nd * 8}, {c->d_Pblk, (size_t)nd * 8}, {c->d_Lval, (size_t)c->capLval * vs},
-            {c->d_Uval, (size_t)c->capUval * vs}, {c->d_Lnrm, (size_t)c->capLrow * 8},
+            {c->d_Uval, (size_t)c->capUval * vs}, {c->d_Uhval, (size_t)c->capUval * vs},
+            {c->d_Lnrm, (size_t)c->capLrow * 8},
             {c->d_Unrm, (size_t)c->capUcol * 8}, {c->d_TL, tb}, {c->d_TU, tb},
             {c->d_LU, (size_t)(BILU_MAX_BLOCK * BILU_MAX_BLOCK + BILU_MAX_BLOCK) * 8},
             {c->d_dcolsq, (size_t)BILU_MAX_BLOCK * 8}, {c->d_nrmL, (size_t)c->capT * 8}, {c->d_nrmU, (size_t)c->capT * 8}};
@@ -2068,13 +2094,13 @@ FactorArgs make_args(bilu_ctx *c, double droptol, int G) {
     a.rowptr = c->d_rowptr; a.colind = c->d_colind; a.colptr = c->d_colptr; a.rowind = c->d_rowind;
     a.bstart = c->d_bstart; a.blkof = c->d_blkof; a.val = c->d_val; a.cval = c->d_cval; a.Dptr = c->d_Dptr;
     a.Lptr = c->d_Lptr; a.Lvptr = c->d_Lvptr; a.Uptr = c->d_Uptr; a.Uvptr = c->d_Uvptr;
-    a.Lrow = c->d_Lrow; a.Ucol = c->d_Ucol; a.Lval = c->d_Lval; a.Uval = c->d_Uval;
+    a.Lrow = c->d_Lrow; a.Ucol = c->d_Ucol; a.Lval = c->d_Lval; a.Uval = c->d_Uval; a.Uhval = c->d_Uhval;
     a.Dinv = c->d_Dinv; a.Pblk = c->d_Pblk;
     a.capLrow = c->capLrow; a.capLval = c->capLval; a.capUcol = c->capUcol; a.capUval = c->capUval;
     a.prodcap = c->prodcap;
     a.prodL = c->d_prodL; a.prodLcnt = c->d_prodLcnt; a.prodU = c->d_prodU; a.prodUcnt = c->d_prodUcnt;
     a.lastL = c->d_lastL; a.lastU = c->d_lastU;
-    a.TL = c->d_TL; a.TU = c->d_TU; a.TLP = c->d_TLP; a.rowsL = c->d_rowsL; a.rowsU = c->d_rowsU;
+    a.TL = c->d_TL; a.TU = c->d_TU; a.TUh = c->d_TUh; a.TLP = c->d_TLP; a.rowsL = c->d_rowsL; a.rowsU = c->d_rowsU;
     a.keepL = c->d_keepL; a.keepU = c->d_keepU; a.bmL = c->d_bmL; a.bmU = c->d_bmU;
     a.wbL = c->d_wbL; a.wbU = c->d_wbU; a.xslotL = c->d_xslotL; a.xslotU = c->d_xslotU;
     a.capXS = c->capXS; a.pinfoL = c->d_pinfoL; a.pinfoU = c->d_pinfoU; a.capT = c->capT;
@@ -2183,7 +2209,7 @@ namespace {
 // `big` holds the candidate buffers and plans, `reset` what must be zero before every run
 // (bitmaps, barrier, pivot-tile count, producer de-duplication, chunk cursors).
 struct GroupPtrs {
-    double *TL, *TU, *TLP, *LU, *nrmL, *nrmU, *dcolsq;
+    double *TL, *TU, *TUh, *TLP, *LU, *nrmL, *nrmU, *dcolsq;
     int32_t *rowsL, *rowsU, *keepL, *keepU, *wbL, *wbU, *xslotL, *xslotU, *perm, *kst;
     int64_t *pinfoL, *pinfoU;
     uint32_t *bmL, *bmU, *bar, *pivdone;
@@ -2203,6 +2229,7 @@ size_t carve_big(const bilu_ctx *c, char *base, GroupPtrs &g) {
     const int64_t bmax = std::max(c->bmax, 1), n = std::max<int64_t>(c->n, 1);
     take(base, off, g.TL, c->capT * bmax);
     take(base, off, g.TU, c->capT * bmax);
+    take(base, off, g.TUh, c->capT * bmax);
     take(base, off, g.TLP, (int64_t)PPART * BILU_MAX_BLOCK * BILU_MAX_BLOCK);
     take(base, off, g.LU, BILU_MAX_BLOCK * BILU_MAX_BLOCK + BILU_MAX_BLOCK);
     take(base, off, g.nrmL, c->capT);
@@ -2257,13 +2284,14 @@ cudaError_t alloc_groups(bilu_ctx *c, int ng) {
 
 // The chunked pools of the tree schedule, as large as the block-ordered pools or larger.
 cudaError_t alloc_arena(bilu_ctx *c, const int64_t cap[4]) {
-    dev_free(c->d_aLrow); dev_free(c->d_aUcol); dev_free(c->d_aLval); dev_free(c->d_aUval);
+    dev_free(c->d_aLrow); dev_free(c->d_aUcol); dev_free(c->d_aLval); dev_free(c->d_aUval); dev_free(c->d_aUhval);
     dev_free(c->d_aLnrm); dev_free(c->d_aUnrm);
     for (auto &v : c->capA) v = 0;
     cudaError_t e;
     if ((e = dev_alloc(&c->d_aLrow, cap[0])) != cudaSuccess || (e = dev_alloc(&c->d_aLnrm, cap[0])) != cudaSuccess ||
         (e = dev_alloc(&c->d_aLval, cap[1])) != cudaSuccess || (e = dev_alloc(&c->d_aUcol, cap[2])) != cudaSuccess ||
-        (e = dev_alloc(&c->d_aUnrm, cap[2])) != cudaSuccess || (e = dev_alloc(&c->d_aUval, cap[3])) != cudaSuccess)
+        (e = dev_alloc(&c->d_aUnrm, cap[2])) != cudaSuccess || (e = dev_alloc(&c->d_aUval, cap[3])) != cudaSuccess ||
+        (e = dev_alloc(&c->d_aUhval, cap[3])) != cudaSuccess)
         return e;
     for (int q = 0; q < 4; ++q) c->capA[q] = cap[q];
     return cudaSuccess;
@@ -2279,7 +2307,8 @@ template <class TS>
 cudaError_t launch_tree_copy(bilu_ctx *c, int grid) {
     tree_copy_kernel<TS><<<grid, 256, 0, c->stream>>>(
         c->nb, c->d_bstart, c->d_aptr, c->d_Lptr, c->d_Lvptr, c->d_Uptr, c->d_Uvptr, c->d_aLrow, c->d_aUcol,
-        (const TS *)c->d_aLval, (const TS *)c->d_aUval, c->d_Lrow, c->d_Ucol, (TS *)c->d_Lval, (TS *)c->d_Uval,
+        (const TS *)c->d_aLval, (const TS *)c->d_aUval, (const TS *)c->d_aUhval, c->d_Lrow, c->d_Ucol,
+        (TS *)c->d_Lval, (TS *)c->d_Uval, (TS *)c->d_Uhval,
         c->d_status);
     return cudaGetLastError();
 }
@@ -2340,13 +2369,13 @@ static bilu_status factor_tree_run(bilu_ctx *c, double droptol) {
             carve_big(c, c->d_grp_big + (size_t)g * c->grp_big_bytes, gp);
             carve_reset(c, c->d_grp_reset + (size_t)g * c->grp_reset_bytes, gp);
             FactorArgs a = make_args(c, droptol, G);
-            a.TL = gp.TL; a.TU = gp.TU; a.TLP = gp.TLP; a.LU = gp.LU; a.nrmL = gp.nrmL; a.nrmU = gp.nrmU;
+            a.TL = gp.TL; a.TU = gp.TU; a.TUh = gp.TUh; a.TLP = gp.TLP; a.LU = gp.LU; a.nrmL = gp.nrmL; a.nrmU = gp.nrmU;
             a.dcolsq = gp.dcolsq; a.rowsL = gp.rowsL; a.rowsU = gp.rowsU; a.keepL = gp.keepL; a.keepU = gp.keepU;
             a.wbL = gp.wbL; a.wbU = gp.wbU; a.xslotL = gp.xslotL; a.xslotU = gp.xslotU; a.perm = gp.perm;
             a.kst = gp.kst; a.pinfoL = gp.pinfoL; a.pinfoU = gp.pinfoU; a.bmL = gp.bmL; a.bmU = gp.bmU;
             a.bar = gp.bar; a.pivdone = gp.pivdone; a.lastL = gp.lastL; a.lastU = gp.lastU; a.gcur = gp.gcur;
             // the pools are the arena; block K's rows are [Lptr[K], Lend[K]) there
-            a.Lrow = c->d_aLrow; a.Ucol = c->d_aUcol; a.Lval = c->d_aLval; a.Uval = c->d_aUval;
+            a.Lrow = c->d_aLrow; a.Ucol = c->d_aUcol; a.Lval = c->d_aLval; a.Uval = c->d_aUval; a.Uhval = c->d_aUhval;
             a.Lnrm = c->d_aLnrm; a.Unrm = c->d_aUnrm;
             a.Lptr = c->d_aptr; a.Lend = c->d_aptr + nb; a.Lvptr = c->d_aptr + 2 * (int64_t)nb;
             a.Uptr = c->d_aptr + 3 * (int64_t)nb; a.Uend = c->d_aptr + 4 * (int64_t)nb;
