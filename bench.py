@@ -80,6 +80,9 @@ def parse():
     ap.add_argument("--group-ctas", type=int, default=0, help="tree schedule: CTAs per group (0: library default)")
     ap.add_argument("--batch", type=int, default=0,
                     help="factor + solve this many uneven 2D/3D matrices in one batched launch instead")
+    ap.add_argument("--compare-fp64", action="store_true",
+                    help="also time plain FP64 factor + GMRES (no skip) on the same matrix, order and schedule, "
+                         "and report the variant's speedup over it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -358,6 +361,7 @@ def run_reference_batch(args):
     batch's systems (every 16th system of each kind), each kind's time scaled to all systems of
     that kind by their number of unknowns (the oracle's time per system grows about linearly
     with n on these stencils, at a different rate for 2D and 3D)."""
+    import numpy as np
     import oracle as O
     from paper_1908_10169_gb300 import workloads as W
     oracle_cores, model = cpu_desc()
@@ -379,7 +383,11 @@ def run_reference_batch(args):
         for k, idx in kinds.items():
             for i in idx:
                 w = ws[i]
-                t += oracle_step(w, O.partition_fixed(w.A.n, w.fixed_block))[0] * scale[k]
+                if args.order == "nd":  # the same host analysis as the GPU arm (not timed)
+                    pw = preprocess(argparse.Namespace(block=w.fixed_block, order="nd", mwm=False, blocking="fixed"), w)
+                    t += oracle_step(dataclasses.replace(w, A=pw.A, b=np.ascontiguousarray(pw.b)), pw.bstart)[0] * scale[k]
+                else:
+                    t += oracle_step(w, O.partition_fixed(w.A.n, w.fixed_block))[0] * scale[k]
         times.append(t)
     v = sum(times) / len(times)
     line = {"impl": "reference", "metric": f"batched BILU factor+GMRES seconds for {len(ws)} systems to rel. residual 1e-8",
@@ -387,7 +395,7 @@ def run_reference_batch(args):
             "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"cd_batch_{len(ws)}", "sum_n": int(n_all), "sample_systems": sample,
-                       "sample_by_kind": kinds},
+                       "sample_by_kind": kinds, "order": args.order},
             "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
                              "sample": f"oracle factor + GMRES on systems {sample} ({n_sample} of {n_all} unknowns; "
                                        f"2D {kinds['2d']}, 3D {kinds['3d']}), each kind scaled by its unknowns to "
@@ -653,6 +661,37 @@ def run_gpu(args):
                "sample": f"one full step (oracle factor {tfo:.1f} s + GMRES {tgo:.1f} s, {it_o} iters) on the "
                          f"same matrix; host {model}, {cores} cores visible, 1 used",
                "gmres_iters": it_o}
+    plain = None
+    if args.compare_fp64:  # plain FP64 (no skip) on the same matrix, order and schedule, same timing
+        ctx4 = B.bilu_create(local, stream)
+        p4 = B.bilu_params_default(blocking=B.BILU_BLOCKING_FIXED, fixed_block=args.block, max_block=64,
+                                   schedule=params.schedule, group_ctas=args.group_ctas)
+        if prep.bstart is None:
+            B.bilu_analyze(ctx4, w.A.n, rp, ci, va, p4)
+        else:
+            B.bilu_analyze_partition(ctx4, w.A.n, rp, ci, va, prep.bstart, p4)
+        pt = []
+        for k in range(args.warmup + args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(1)
+            torch.cuda.synchronize()
+            q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            q0.record(stream)
+            B.bilu_factor(ctx4, w.droptol)
+            with torch.cuda.stream(stream):
+                x.zero_()
+            i4 = B.gmres_solve(ctx4, b, x, w.gmres_tol, w.restart, 10000)
+            q1.record(stream)
+            q1.synchronize()
+            if k >= args.warmup:
+                pt.append(q0.elapsed_time(q1))
+        s4 = B.bilu_stats(ctx4)
+        pms = sum(pt) / len(pt)
+        plain = {"ms_per_step": pms, "factor_ms": s4.t_factor_ms, "solve_ms": i4.t_solve_ms, "gmres_iters": i4.iters,
+                 "schedule": "tree" if p4.schedule == B.BILU_SCHED_TREE else "chain",
+                 "speedup_of_this_line": pms / ms, "factor_speedup": s4.t_factor_ms / t_factor,
+                 "iters_ratio": iters / max(1, i4.iters)}
+        B.bilu_destroy(ctx4)
     if learned is not None:  # the method without the skip on the same matrix, for the gain
         learned.update({"skipped": st.skipped_rows + st.skipped_cols, "candidates": st.cand_rows + st.cand_cols,
                         "kept": st.kept_rows + st.kept_cols, "flops_factor": st.flops_factor})
@@ -693,7 +732,8 @@ def run_gpu(args):
                                                                         "bound_skip_updates", "scale_drop", "compact",
                                                                         "cta0_lu_work", "cta0_pivot_tile_wait"],
                                                                        [round(v, 3) for v in st.phase_ms])),
-                                           **({"learned_skip": learned} if learned is not None else {})}),
+                                           **({"learned_skip": learned} if learned is not None else {}),
+                                           **({"plain_fp64": plain} if plain is not None else {})}),
                 "roofline": dominant, "roofline_other": other,
                 "gpu_launches": launches, "clocks": clk.summary(), "e2e": e2e, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
@@ -738,16 +778,31 @@ def run_batch(args):
         learned = {"train_problems": args.train_count, "samples": sm.samples, "logit_hi": sm.logit_hi,
                    "train_skip_rate": sm.skip_rate}
         progress(f"classifier trained on {sm.samples} samples")
-    ctxs, bs, xs = [], [], []
+    # each system as the factor sees it: with --order nd its blocks reordered by nested dissection
+    # (host analysis, not timed), else as generated
+    prepared = []
     for w in ws:
+        if args.order == "nd":
+            pw = preprocess(argparse.Namespace(block=w.fixed_block, order="nd", mwm=False, blocking="fixed"), w)
+            prepared.append((pw.A, np.ascontiguousarray(pw.b), pw.bstart))
+        else:
+            prepared.append((w.A, w.b, None))
+
+    def analyze(c, A, bst, params):
+        t = [torch.from_numpy(v).to(dev) for v in (A.rowptr, A.colind, A.val)]
+        if bst is None:
+            B.bilu_analyze(c, A.n, *t, params)
+        else:
+            B.bilu_analyze_partition(c, A.n, *t, bst, params)
+
+    ctxs, bs, xs = [], [], []
+    for w, (Aw, bw, bst) in zip(ws, prepared):
         c = B.bilu_create(local, stream if not ctxs else None)
-        B.bilu_analyze(c, w.A.n, torch.from_numpy(w.A.rowptr).to(dev), torch.from_numpy(w.A.colind).to(dev),
-                       torch.from_numpy(w.A.val).to(dev),
-                       B.bilu_params_default(fixed_block=w.fixed_block, max_block=64, precision=prec, skip=skip))
+        analyze(c, Aw, bst, B.bilu_params_default(fixed_block=w.fixed_block, max_block=64, precision=prec, skip=skip))
         if learned is not None:
             B.bilu_set_skip_model(c, sm.model, sm.logit_hi)
         ctxs.append(c)
-        bs.append(torch.from_numpy(w.b).to(dev))
+        bs.append(torch.from_numpy(bw).to(dev))
         xs.append(torch.zeros(w.A.n, dtype=torch.float64, device=dev))
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
     progress(f"{len(ws)} systems analysed")
@@ -793,9 +848,10 @@ def run_batch(args):
     # the same systems one by one, plain FP64
     t_seq, iters_s = 0.0, []
     one = B.bilu_create(local, stream)
-    for w, bvec in zip(ws, bs):
-        B.bilu_analyze(one, w.A.n, torch.from_numpy(w.A.rowptr).to(dev), torch.from_numpy(w.A.colind).to(dev),
-                       torch.from_numpy(w.A.val).to(dev), B.bilu_params_default(fixed_block=w.fixed_block, max_block=64))
+    for w, bvec, (Aw, bw, bst) in zip(ws, bs, prepared):
+        # one by one: plain FP64 on the same ordering, with the single-matrix schedule of that ordering
+        analyze(one, Aw, bst, B.bilu_params_default(fixed_block=w.fixed_block, max_block=64,
+                                                    schedule=B.BILU_SCHED_TREE if bst is not None else B.BILU_SCHED_CHAIN))
         x = torch.zeros_like(bvec)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -827,6 +883,7 @@ def run_batch(args):
                 "config": {"workload": f"cd_batch_{len(ws_all)}", "sum_n": int(sum(w.A.n for w in ws_all)),
                            "n_range": [int(min(w.A.n for w in ws_all)), int(max(w.A.n for w in ws_all))],
                            "parallelism": f"systems sharded over {world} GPU(s) by nnz, no collective",
+                           "order": args.order,
                            "systems_on_rank0": len(ws), "updates": args.precision,
                            "gmres_iters_batched_rank0": iters_b, "gmres_iters_plain_fp64_rank0": iters_s,
                            "max_iter_ratio": ratio,

@@ -387,6 +387,9 @@ bilu_status bilu_analyze_partition(bilu_ctx *ctx, int64_t n, const int64_t *rowp
  *       groups, the trunk included (same factor), instead of the trunk on the whole grid.
  *   BILU_DEBUG_TRACE (value 0/1): the tree schedule prints one line per factorization run
  *       (status, storage sizes) to stderr.
+ *   BILU_DEBUG_BATCH_TRCAP (value >= 0): bilu_factor_batch's update tiles hold at most this
+ *       many candidate rows (values below 4 count as 4, above 16 as 16) instead of the tuned
+ *       cap; 0 restores tuning.  The factor does not change.
  */
 enum {
     BILU_DEBUG_EXTRA_CTA = 1,
@@ -396,7 +399,8 @@ enum {
     BILU_DEBUG_SMALL_POOLS = 5,
     BILU_DEBUG_POISON = 6,
     BILU_DEBUG_NO_TRUNK = 7,
-    BILU_DEBUG_TRACE = 8
+    BILU_DEBUG_TRACE = 8,
+    BILU_DEBUG_BATCH_TRCAP = 9
 };
 bilu_status bilu_debug_set(bilu_ctx *ctx, int32_t what, int64_t value);
 

@@ -106,6 +106,7 @@ struct FactorArgs {
                                  // site, CTA-0 wait site, wait heartbeat], mapped host memory, or null
     int64_t *timeline;           // test hook (tree schedule): per block 8 words: group, then the
                                  // clock at its start and after phases A, B+C, C2, (Bs,) D, E
+    int32_t trcap;               // most candidate rows per accumulation tile (4..TRMAX)
     int32_t skip_bound;          // 1: skip candidates that the norm bound proves dropped
     double *Lnrm, *Unrm;         // per kept row of L: ||l_i||; per kept column of U-breve: ||u_j||
     double *dcolsq;              // squared column norms of D_K (b entries)
@@ -1505,7 +1506,7 @@ __device__ bool block_step(const FactorArgs &a, int K, char *smem, StepTimers &t
         const int W = a.G > 1 ? a.G - 1 : 1;  // CTAs taking tiles (CTA 0 factors the pivot block)
         const int np = pivot_parts(W, npt);    // producer slices per pivot-row tile
         int TR = (nrest + W - 1) / W;
-        TR = max(4, min(TRMAX, TR));
+        TR = max(4, min(a.trcap, TR));
         const int nLt = (nrestL + TR - 1) / TR, nUt = (mU + TR - 1) / TR;
         const int ntiles = npt * np + (a.skip_bound ? 0 : nLt + nUt);
         if (a.G == 1 || cr > 0) {
@@ -1566,7 +1567,7 @@ __device__ bool block_step(const FactorArgs &a, int K, char *smem, StepTimers &t
     lap(2);
     if (a.skip_bound) {
         int TR = (nrest + a.G - 1) / a.G;
-        TR = max(4, min(TRMAX, TR));
+        TR = max(4, min(a.trcap, TR));
         const int nLt = (nrestL + TR - 1) / TR, nUt = (mU + TR - 1) / TR;
         for (int it = cr; it < nLt + nUt; it += a.G) {
             const bool Ls = it < nLt;
@@ -1975,6 +1976,7 @@ cudaError_t alloc_prod(bilu_ctx *c) {
 int g_debug_extra_cta = 0;          // the barrier waits for a CTA that never arrives
 long long g_debug_spin_limit = 0;   // polls before a bounded wait gives up (0: default)
 long long g_debug_batch_group = 0;  // batch group size (0: tuned)
+long long g_debug_batch_trcap = 0;  // batch tile row cap (0: tuned)
 int g_debug_small_pools = 0;        // factorizations start from minimal pools and producer lists
 int g_debug_poison = 0;             // factor storage is filled with NaN before every run
 int g_debug_no_trunk = 0;           // the tree schedule leaves no trunk to the whole grid
@@ -2109,6 +2111,7 @@ FactorArgs make_args(bilu_ctx *c, double droptol, int G) {
     a.debug_extra_cta = g_debug_extra_cta;
     a.trace = nullptr;
     a.timeline = nullptr;
+    a.trcap = TRMAX;
     // recording takes exact samples: no skipping while it is on
     const bool rec = c->rec_cap > 0;
     a.skip_bound = c->p.skip == BILU_SKIP_BOUND && !rec ? 1 : 0;
@@ -2577,16 +2580,17 @@ bilu_status factor_run(bilu_ctx *c, double droptol) {
 namespace {
 
 struct BatchTune {
-    int nsm, nmat, bmax, precision, G, tuned;
+    int nsm, nmat, bmax, precision, G, trcap, tuned;
 };
-std::vector<BatchTune> g_batch_tune;  // group sizes chosen by the autotuner
+std::vector<BatchTune> g_batch_tune;  // group sizes and tile row caps chosen by the autotuner
 std::mutex g_batch_tune_mu;           // guards g_batch_tune (calls on different contexts may overlap)
 
 }  // namespace
 
 // Factors every context's matrix in one cooperative launch: groups of G CTAs take matrices
-// from a queue, largest first.  G is chosen by timing candidate group sizes on the second
-// call for a given (matrix count, largest block, precision) and cached.
+// from a queue, largest first.  G, and then the most candidate rows per update tile, are
+// chosen by timing candidates on the second call for a given (matrix count, largest block,
+// precision) and cached.
 bilu_status factor_batch_run(bilu_ctx *const *ctxs, int count, double droptol, double *ms_out) {
     bilu_ctx *c0 = ctxs[0];
     const int prec = c0->p.precision;
@@ -2631,13 +2635,14 @@ bilu_status factor_batch_run(bilu_ctx *const *ctxs, int count, double droptol, d
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     // one launch over the matrices in `todo`; returns the kernel time
-    auto launch = [&](const std::vector<int> &todo, int G, float *ms) -> cudaError_t {
+    auto launch = [&](const std::vector<int> &todo, int G, int trcap, float *ms) -> cudaError_t {
         cudaError_t e;
         std::vector<FactorArgs> h(todo.size());
         for (size_t k = 0; k < todo.size(); ++k) {
             bilu_ctx *c = ctxs[todo[k]];
             if ((e = prepare_run(c, c0->stream)) != cudaSuccess) return e;
             h[k] = make_args(c, droptol, G);
+            h[k].trcap = std::max(4, std::min(TRMAX, trcap));
         }
         if ((e = cudaMemcpyAsync(d_args, h.data(), h.size() * sizeof(FactorArgs), cudaMemcpyHostToDevice, c0->stream)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(d_queue, 0, 4 * sizeof(int), c0->stream)) != cudaSuccess) return e;
@@ -2678,11 +2683,11 @@ bilu_status factor_batch_run(bilu_ctx *const *ctxs, int count, double droptol, d
         return t.nsm == nsm && t.nmat == count && t.bmax == bmax && t.precision == prec;
     };
     bool have = false, tuned = false;
-    int cachedG = 0;
+    int cachedG = 0, cachedCap = TRMAX, cap = TRMAX;
     {
         std::lock_guard<std::mutex> lk(g_batch_tune_mu);
         for (const auto &t : g_batch_tune)
-            if (same(t)) { have = true; tuned = t.tuned != 0; cachedG = t.G; }
+            if (same(t)) { have = true; tuned = t.tuned != 0; cachedG = t.G; cachedCap = t.trcap; }
     }
     std::vector<int> todo(order);
     float best_ms = 0.f;
@@ -2695,37 +2700,54 @@ bilu_status factor_batch_run(bilu_ctx *const *ctxs, int count, double droptol, d
         std::lock_guard<std::mutex> lk(g_batch_tune_mu);
         bool dup = false;
         for (const auto &t : g_batch_tune) dup = dup || same(t);
-        if (!dup) g_batch_tune.push_back({nsm, count, bmax, prec, G, 0});
+        if (!dup) g_batch_tune.push_back({nsm, count, bmax, prec, G, TRMAX, 0});
     } else if (!tuned) {
         float best = 1e30f;
-        int bestG = cachedG;
+        int bestG = cachedG, bestCap = TRMAX;
         bool ok = true;
-        for (int Gc : cands) {
-            float ms = 0.f;
-            cudaError_t e = launch(todo, Gc, &ms);
-            if (e != cudaSuccess) { release(); cudaEventDestroy(e0); cudaEventDestroy(e1); return cuda_err(c0, e, "batch factor launch"); }
+        // one timed launch; false when it must stop tuning (a pool grew, or a launch error in *err)
+        auto trial = [&](int Gc, int capc, float *ms, cudaError_t *err) -> bool {
+            *err = launch(todo, Gc, capc, ms);
+            if (*err != cudaSuccess) return false;
             for (int i : todo) {
                 int32_t st = 0;
                 cudaMemcpy(&st, ctxs[i]->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost);
                 ok = ok && st == DEV_OK;
             }
-            if (!ok) break;  // pools still growing: tune on a later call
+            return ok;  // pools still growing: tune on a later call
+        };
+        cudaError_t e = cudaSuccess;
+        for (int Gc : cands) {
+            float ms = 0.f;
+            if (!trial(Gc, TRMAX, &ms, &e)) break;
             if (ms < best) { best = ms; bestG = Gc; }
             else break;  // past the minimum
         }
+        // then smaller update tiles at that group size: more tiles per block for the group's
+        // CTAs when the matrices are small
+        for (int capc = TRMAX / 2; ok && e == cudaSuccess && capc >= 4; capc /= 2) {
+            float ms = 0.f;
+            if (!trial(bestG, capc, &ms, &e)) break;
+            if (ms < best) { best = ms; bestCap = capc; }
+            else break;
+        }
+        if (e != cudaSuccess) { release(); cudaEventDestroy(e0); cudaEventDestroy(e1); return cuda_err(c0, e, "batch factor launch"); }
         G = bestG;
+        cap = bestCap;
         if (ok) {
             std::lock_guard<std::mutex> lk(g_batch_tune_mu);
             for (auto &t : g_batch_tune)
-                if (same(t)) { t.G = bestG; t.tuned = 1; }
+                if (same(t)) { t.G = bestG; t.trcap = bestCap; t.tuned = 1; }
         }
     } else {
         G = cachedG;
+        cap = cachedCap;
     }
+    if (g_debug_batch_trcap > 0) cap = (int)std::min<long long>(g_debug_batch_trcap, TRMAX);
     bilu_status result = BILU_OK;
     for (int attempt = 0; attempt < 12 && !todo.empty(); ++attempt) {
         float ms = 0.f;
-        cudaError_t e = launch(todo, G, &ms);
+        cudaError_t e = launch(todo, G, cap, &ms);
         if (e != cudaSuccess) { release(); cudaEventDestroy(e0); cudaEventDestroy(e1); return cuda_err(c0, e, "batch factor launch"); }
         best_ms += ms;
         std::vector<int> again;

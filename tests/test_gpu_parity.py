@@ -455,15 +455,17 @@ def test_batched_factor_and_gmres_match_one_by_one(ctx):
             B.bilu_destroy(c)
 
 
-@pytest.mark.parametrize("G", [1, 2, 5])
-def test_batched_small_groups_large_blocks(ctx, G):
+@pytest.mark.parametrize("G,cap", [(1, 0), (2, 0), (5, 0), (5, 4), (2, 8)])
+def test_batched_small_groups_large_blocks(ctx, G, cap):
     """Groups with fewer CTAs than half a block's columns (the inverse D_K = P_K^{-1} then
-    takes several columns per CTA and several rounds): same factors as one by one, with every
-    value array filled with NaN before each run."""
+    takes several columns per CTA and several rounds), and update tiles capped at fewer
+    candidate rows (cap; 0: the tuned cap): same factors as one by one, with every value
+    array filled with NaN before each run."""
     ws = W.cd_batch(count=3, seed0=200, n_lo=1500, n_hi=4000, block=48)
     ctxs = [B.bilu_create(0) for _ in ws]
     B.bilu_debug_set(ctxs[0], B.BILU_DEBUG_POISON, 1)
     B.bilu_debug_set(ctxs[0], B.BILU_DEBUG_BATCH_GROUP, G)
+    B.bilu_debug_set(ctxs[0], B.BILU_DEBUG_BATCH_TRCAP, cap)
     try:
         for c, w in zip(ctxs, ws):
             B.bilu_analyze(c, w.A.n, w.A.rowptr, w.A.colind, w.A.val,
@@ -482,6 +484,7 @@ def test_batched_small_groups_large_blocks(ctx, G):
                 assert np.array_equal(v, getattr(g1, k)), (w.name, k)
     finally:
         B.bilu_debug_set(ctxs[0], B.BILU_DEBUG_BATCH_GROUP, 0)
+        B.bilu_debug_set(ctxs[0], B.BILU_DEBUG_BATCH_TRCAP, 0)
         B.bilu_debug_set(ctxs[0], B.BILU_DEBUG_POISON, 0)
         for c in ctxs:
             B.bilu_destroy(c)
