@@ -711,6 +711,24 @@ def run_gpu(args):
                         "exact_kept": s3.kept_rows + s3.kept_cols, "exact_gmres_iters": i3.iters,
                         "exact_solve_ms": i3.t_solve_ms})
         B.bilu_destroy(ctx3)
+        # the exact skip (the norm bound: the same factor as no skip) on the same schedule
+        ctx5 = B.bilu_create(local, stream)
+        params.skip = B.BILU_SKIP_BOUND
+        if prep.bstart is None:
+            B.bilu_analyze(ctx5, w.A.n, rp, ci, va, params)
+        else:
+            B.bilu_analyze_partition(ctx5, w.A.n, rp, ci, va, prep.bstart, params)
+        for _ in range(2):
+            B.bilu_factor(ctx5, w.droptol)
+        s5 = B.bilu_stats(ctx5)
+        with torch.cuda.stream(stream):
+            x.zero_()
+        i5 = B.gmres_solve(ctx5, b, x, w.gmres_tol, w.restart, 10000)
+        learned.update({"bound_factor_ms": s5.t_factor_ms, "bound_flops_factor": s5.flops_factor,
+                        "bound_kept": s5.kept_rows + s5.kept_cols, "bound_gmres_iters": i5.iters,
+                        "bound_solve_ms": i5.t_solve_ms, "bound_skipped": s5.skipped_rows + s5.skipped_cols})
+        B.bilu_destroy(ctx5)
+        params.skip = B.BILU_SKIP_LEARNED
     B.bilu_destroy(ctx)
     if rank == 0:
         line = {"metric": METRIC, "value": ms / 1e3 / world, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -33,7 +33,8 @@ C_NAMES = ["flop_upd_L", "flop_upd_U", "flop_getrf", "flop_inv", "flop_scale", "
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (plain C11, -O2, no vectorisation flags beyond -O2)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    hdr = os.path.join(_HERE, "bilu_oracle.h")
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(os.path.getmtime(_SRC), os.path.getmtime(hdr)):
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
@@ -57,6 +58,11 @@ def lib():
         L.orc_partition_ilu1t_groups.restype = i32
         L.orc_bilu_factor.argtypes = [i64, P, P, P, i32, P, f64, i32, f64, f64, ct.POINTER(P)]
         L.orc_bilu_factor.restype = i32
+        L.orc_bilu_factor_agg.argtypes = [i64, P, P, P, i32, P, f64, i32, f64, f64, i32, ct.POINTER(P)]
+        L.orc_bilu_factor_agg.restype = i32
+        L.orc_agg_rule.argtypes = [i64] * 10
+        L.orc_agg_rule.restype = i32
+        L.orc_factor_bstart.argtypes = [P, P]
         L.orc_factor_sizes.argtypes = [P, P]
         L.orc_factor_export.argtypes = [P] * 11
         L.orc_factor_counters.argtypes = [P, P]
@@ -125,6 +131,7 @@ class Factor:
     counters: dict
     status: int
     handle: object = None
+    merges: int = 0  # progressive aggregation: blocks merged into their successor (void blocks)
 
     @property
     def nb(self) -> int:
@@ -148,13 +155,13 @@ class Factor:
     def L_block(self, K):
         b = self.bsize(K)
         rows = self.Lrow[self.Lptr[K]:self.Lptr[K + 1]]
-        v = self.Lval[self.Lvptr()[K]:self.Lvptr()[K + 1]].reshape(-1, b)
+        v = self.Lval[self.Lvptr()[K]:self.Lvptr()[K + 1]].reshape(len(rows), b)
         return rows, v
 
     def U_block(self, K):
         b = self.bsize(K)
         cols = self.Ucol[self.Uptr[K]:self.Uptr[K + 1]]
-        v = self.Uval[self.Uvptr()[K]:self.Uvptr()[K + 1]].reshape(-1, b)
+        v = self.Uval[self.Uvptr()[K]:self.Uvptr()[K + 1]].reshape(len(cols), b)
         return cols, v
 
     def D_block(self, K):
@@ -212,19 +219,24 @@ class Factor:
 
 
 def bilu_factor(A, bstart: np.ndarray, droptol: float, perturb: bool = True,
-                pert_tau: float = 1e-2, pert_rho: float = 1e-1, keep_handle: bool = True) -> Factor:
-    """Crout BILU (Sec. 2.2).  Raises on argument errors and singular blocks."""
+                pert_tau: float = 1e-2, pert_rho: float = 1e-1, keep_handle: bool = True,
+                agg_max: int = 0) -> Factor:
+    """Crout BILU (Sec. 2.2), with progressive aggregation of blocks up to agg_max columns
+    when agg_max > 0 (Sec. 3.5; the factor's bstart then has void blocks).  Raises on
+    argument errors and singular blocks."""
     L = lib()
     rp, ci, va = _csr_args(A)
     bs = np.ascontiguousarray(bstart, dtype=np.int32)
     h = ct.c_void_p()
-    st = L.orc_bilu_factor(A.n, _p(rp), _p(ci), _p(va), len(bs) - 1, _p(bs), droptol,
-                           int(perturb), pert_tau, pert_rho, ct.byref(h))
+    st = L.orc_bilu_factor_agg(A.n, _p(rp), _p(ci), _p(va), len(bs) - 1, _p(bs), droptol,
+                               int(perturb), pert_tau, pert_rho, int(agg_max), ct.byref(h))
     if st < 0:
         raise RuntimeError(f"oracle factor failed with status {st}")
     sizes = np.zeros(8, dtype=np.int64)
     L.orc_factor_sizes(h, _p(sizes))
     nb = len(bs) - 1
+    bs = np.zeros(nb + 1, np.int32)
+    L.orc_factor_bstart(h, _p(bs))
     Lptr = np.zeros(nb + 1, np.int64)
     Uptr = np.zeros(nb + 1, np.int64)
     Lrow = np.zeros(sizes[0], np.int32)
@@ -241,10 +253,15 @@ def bilu_factor(A, bstart: np.ndarray, droptol: float, perturb: bool = True,
     L.orc_factor_counters(h, _p(c))
     counters = {k: float(c[i]) for i, k in enumerate(C_NAMES)}
     F = Factor(bs.copy(), Lptr, Lrow, Lval, Uptr, Ucol, Uval, Dinv, Pblk, LUblk, piv, counters, st,
-               h if keep_handle else None)
+               h if keep_handle else None, int(sizes[7]))
     if not keep_handle:
         L.orc_factor_free(h)
     return F
+
+
+def agg_rule(p, q, r, s, rp, sp, t, tp, u, v) -> bool:
+    """The Sec. 3.5 merge test on the counts it names (see bilu_oracle.c)."""
+    return bool(lib().orc_agg_rule(p, q, r, s, rp, sp, t, tp, u, v))
 
 
 def bilu_apply(F: Factor, r: np.ndarray) -> np.ndarray:

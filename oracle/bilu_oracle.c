@@ -263,7 +263,9 @@ struct orc_factor {
     vec_i32 Lrow, Ucol;
     vec_f64 Lval, Uval;
     double *Dinv, *Pblk, *LUblk;
+    int64_t dcap;   /* entries allocated in Dinv, Pblk, LUblk */
     int32_t *piv;
+    int64_t merges; /* progressive aggregation: blocks merged into their successor (Sec. 3.5) */
     double counters[ORC_C_COUNT];
 };
 
@@ -394,6 +396,228 @@ static void spa_reset(spa_t *s, int b) {
     if (b != s->b) { s->b = b; s->buf = xrealloc(s->buf, (size_t)(s->cap ? s->cap : 1) * (size_t)b * sizeof(double)); }
 }
 
+/* ------------------------------------------------------------ progressive aggregation */
+
+/*
+ * Sec. 3.5 merge test.  Block k-1 has p columns, block k has q; L_{k,k-1}, L_{k+1,k-1},
+ * L_{k+1,k} have r, s, t stored rows and U_{k-1,k}, U_{k-1,k+1}, U_{k,k+1} have rp, sp, tp
+ * stored columns; u (v) counts the rows (columns) of the merged block column of L (row of
+ * U) beyond block k.  Before merging mu = p (p + r + s + rp + sp) + q (q + t + tp) values
+ * are stored, after it nu = (p + q)(p + q + u + v) (the diagonal block dense).  Merge iff
+ * nu <= 1.2 mu or nu <= mu + 2 (p + q); 1.2 mu is compared exactly as 5 nu <= 6 mu.
+ */
+int32_t orc_agg_rule(int64_t p, int64_t q, int64_t r, int64_t s, int64_t rp, int64_t sp, int64_t t,
+                     int64_t tp, int64_t u, int64_t v) {
+    const int64_t mu = p * (p + r + s + rp + sp) + q * (q + t + tp);
+    const int64_t nu = (p + q) * (p + q + u + v);
+    return (5 * nu <= 6 * mu) || (nu <= mu + 2 * (p + q));
+}
+
+/* sorted union of two sorted index lists (no duplicates inside either); out may be NULL */
+static int64_t sorted_union(const int32_t *a, int64_t na, const int32_t *b, int64_t nb, int32_t *out) {
+    int64_t i = 0, j = 0, m = 0;
+    while (i < na || j < nb) {
+        int32_t x;
+        if (j == nb || (i < na && a[i] < b[j])) x = a[i++];
+        else if (i == na || b[j] < a[i]) x = b[j++];
+        else { x = a[i]; ++i; ++j; }
+        if (out) out[m] = x;
+        ++m;
+    }
+    return m;
+}
+
+/* position of x in the sorted list a[0..n), or -1 */
+static int64_t find_i32(const int32_t *a, int64_t n, int32_t x) {
+    int64_t k = lower_bound_i32(a, 0, n, x);
+    return (k < n && a[k] == x) ? k : -1;
+}
+
+/* the last two producers appended to a later block's list are k-1 and / or k: after the
+ * merge only k remains (block k-1 is void) */
+static void fix_producers(vec_i32 *list, int32_t k) {
+    if (list->n >= 2 && list->a[list->n - 1] == k && list->a[list->n - 2] == k - 1) {
+        list->a[list->n - 2] = k;
+        list->n -= 1;
+    } else if (list->n >= 1 && list->a[list->n - 1] == k - 1) {
+        list->a[list->n - 1] = k;
+    }
+}
+
+/*
+ * After block k is finished: test the merge of the (possibly already merged) block k-1
+ * with k, Sec. 3.5, and on success rewrite both as one block k of p + q columns and make
+ * k-1 void (size 0).  With L21 = L_{k,k-1} (q x p, zero rows where nothing is stored) and
+ * U12 = U-breve_{k-1,k} (p x q), the product of the factors is unchanged when
+ *   L-hat_{i,:}   = [ L_{i,k-1} - L_{i,k} L21 ,  L_{i,k} ]         for rows i beyond B_k,
+ *   U-hat_{:,j}   = [ U_{k-1,j} ; L21 U_{k-1,j} + U_{k,j} ]         for columns j beyond B_k,
+ *   P-hat         = [ P_{k-1}  U12 ; L21 P_{k-1}  L21 U12 + P_k ],
+ *   D-hat = P-hat^{-1} = [ D_{k-1} + (D_{k-1} U12) D_k L21   -(D_{k-1} U12) D_k ;
+ *                          -D_k L21                           D_k ],
+ * the rows (columns) of the merged block being the union of both blocks' (the common
+ * pattern the paper asks for), absent entries taken as zero.
+ */
+static void aggregate_step(orc_factor *F, int32_t k, int32_t agg_max, vec_i32 *prodL, vec_i32 *prodU,
+                           int32_t *blk_of) {
+    const int32_t a0 = F->bstart[k - 1], s0 = F->bstart[k], s1 = F->bstart[k + 1];
+    const int64_t p = s0 - a0, q = s1 - s0, w = p + q;
+    if (p == 0 || q == 0 || w > agg_max) return;
+    const int64_t L0 = F->Lptr[k - 1], L1 = F->Lptr[k], L2 = F->Lptr[k + 1];
+    const int64_t U0 = F->Uptr[k - 1], U1 = F->Uptr[k], U2 = F->Uptr[k + 1];
+    /* rows of L_{:,k-1} are all >= s0: those inside B_k come first */
+    const int64_t Lm = lower_bound_i32(F->Lrow.a, L0, L1, s1), Um = lower_bound_i32(F->Ucol.a, U0, U1, s1);
+    const int64_t r = Lm - L0, s = L1 - Lm, t = L2 - L1;
+    const int64_t rp = Um - U0, sp = U1 - Um, tp = U2 - U1;
+    const int64_t u = sorted_union(F->Lrow.a + Lm, s, F->Lrow.a + L1, t, NULL);
+    const int64_t v = sorted_union(F->Ucol.a + Um, sp, F->Ucol.a + U1, tp, NULL);
+    if (!orc_agg_rule(p, q, r, s, rp, sp, t, tp, u, v)) return;
+
+    const double *Lv0 = F->Lval.a + F->Lvptr[k - 1], *Lv1 = F->Lval.a + F->Lvptr[k];
+    const double *Uv0 = F->Uval.a + F->Uvptr[k - 1], *Uv1 = F->Uval.a + F->Uvptr[k];
+    const double *P1 = F->Pblk + F->Dptr[k - 1], *P2 = F->Pblk + F->Dptr[k];
+    const double *D1 = F->Dinv + F->Dptr[k - 1], *D2 = F->Dinv + F->Dptr[k];
+
+    double *L21 = xcalloc((size_t)(q * p + 1), sizeof(double));
+    double *U12 = xcalloc((size_t)(p * q + 1), sizeof(double));
+    for (int64_t e = L0; e < Lm; ++e)
+        for (int64_t c = 0; c < p; ++c) L21[(F->Lrow.a[e] - s0) * p + c] = Lv0[(e - L0) * p + c];
+    for (int64_t e = U0; e < Um; ++e)
+        for (int64_t c = 0; c < p; ++c) U12[c * q + (F->Ucol.a[e] - s0)] = Uv0[(e - U0) * p + c];
+
+    /* merged diagonal block and its inverse */
+    double *Ph = xcalloc((size_t)(w * w), sizeof(double));
+    double *Dh = xcalloc((size_t)(w * w), sizeof(double));
+    double *DU = xcalloc((size_t)(p * q + 1), sizeof(double)); /* D_{k-1} U12 */
+    double *DL = xcalloc((size_t)(q * p + 1), sizeof(double)); /* D_k L21 */
+    for (int64_t i = 0; i < p; ++i)
+        for (int64_t j = 0; j < p; ++j) Ph[i * w + j] = P1[i * p + j];
+    for (int64_t i = 0; i < p; ++i)
+        for (int64_t j = 0; j < q; ++j) Ph[i * w + p + j] = U12[i * q + j];
+    for (int64_t i = 0; i < q; ++i) {
+        for (int64_t j = 0; j < p; ++j) {
+            double acc = 0.0;
+            for (int64_t m = 0; m < p; ++m) acc += L21[i * p + m] * P1[m * p + j];
+            Ph[(p + i) * w + j] = acc;
+        }
+        for (int64_t j = 0; j < q; ++j) {
+            double acc = P2[i * q + j];
+            for (int64_t m = 0; m < p; ++m) acc += L21[i * p + m] * U12[m * q + j];
+            Ph[(p + i) * w + p + j] = acc;
+        }
+    }
+    for (int64_t i = 0; i < p; ++i)
+        for (int64_t j = 0; j < q; ++j) {
+            double acc = 0.0;
+            for (int64_t m = 0; m < p; ++m) acc += D1[i * p + m] * U12[m * q + j];
+            DU[i * q + j] = acc;
+        }
+    for (int64_t i = 0; i < q; ++i)
+        for (int64_t j = 0; j < p; ++j) {
+            double acc = 0.0;
+            for (int64_t m = 0; m < q; ++m) acc += D2[i * q + m] * L21[m * p + j];
+            DL[i * p + j] = acc;
+        }
+    for (int64_t i = 0; i < p; ++i) {
+        for (int64_t j = 0; j < p; ++j) {
+            double acc = D1[i * p + j];
+            for (int64_t m = 0; m < q; ++m) acc += DU[i * q + m] * DL[m * p + j];
+            Dh[i * w + j] = acc;
+        }
+        for (int64_t j = 0; j < q; ++j) {
+            double acc = 0.0;
+            for (int64_t m = 0; m < q; ++m) acc += DU[i * q + m] * D2[m * q + j];
+            Dh[i * w + p + j] = -acc;
+        }
+    }
+    for (int64_t i = 0; i < q; ++i) {
+        for (int64_t j = 0; j < p; ++j) Dh[(p + i) * w + j] = -DL[i * p + j];
+        for (int64_t j = 0; j < q; ++j) Dh[(p + i) * w + p + j] = D2[i * q + j];
+    }
+
+    /* merged rows of L and columns of U-breve */
+    int32_t *Rn = xmalloc((size_t)(u + 1) * sizeof(int32_t));
+    int32_t *Cn = xmalloc((size_t)(v + 1) * sizeof(int32_t));
+    sorted_union(F->Lrow.a + Lm, s, F->Lrow.a + L1, t, Rn);
+    sorted_union(F->Ucol.a + Um, sp, F->Ucol.a + U1, tp, Cn);
+    double *Lh = xcalloc((size_t)(u * w + 1), sizeof(double));
+    double *Uh = xcalloc((size_t)(v * w + 1), sizeof(double));
+    for (int64_t e = 0; e < u; ++e) {
+        const int64_t ia = find_i32(F->Lrow.a + Lm, s, Rn[e]), ib = find_i32(F->Lrow.a + L1, t, Rn[e]);
+        const double *la = ia >= 0 ? Lv0 + (r + ia) * p : NULL, *lb = ib >= 0 ? Lv1 + ib * q : NULL;
+        double *out = Lh + e * w;
+        for (int64_t j = 0; j < p; ++j) {
+            double acc = la ? la[j] : 0.0;
+            if (lb)
+                for (int64_t m = 0; m < q; ++m) acc -= lb[m] * L21[m * p + j];
+            out[j] = acc;
+        }
+        for (int64_t m = 0; m < q; ++m) out[p + m] = lb ? lb[m] : 0.0;
+    }
+    for (int64_t e = 0; e < v; ++e) {
+        const int64_t ia = find_i32(F->Ucol.a + Um, sp, Cn[e]), ib = find_i32(F->Ucol.a + U1, tp, Cn[e]);
+        const double *ua = ia >= 0 ? Uv0 + (rp + ia) * p : NULL, *ub = ib >= 0 ? Uv1 + ib * q : NULL;
+        double *out = Uh + e * w;
+        for (int64_t j = 0; j < p; ++j) out[j] = ua ? ua[j] : 0.0;
+        for (int64_t i = 0; i < q; ++i) {
+            double acc = ub ? ub[i] : 0.0;
+            if (ua)
+                for (int64_t m = 0; m < p; ++m) acc += L21[i * p + m] * ua[m];
+            out[p + i] = acc;
+        }
+    }
+
+    /* producer lists of later blocks: k-1 becomes k (read before the rows are rewritten) */
+    int32_t last = -1;
+    for (int64_t e = 0; e < u; ++e) {
+        int32_t tb = blk_of[Rn[e]];
+        if (tb != last) { fix_producers(&prodU[tb], k); last = tb; }
+    }
+    last = -1;
+    for (int64_t e = 0; e < v; ++e) {
+        int32_t tb = blk_of[Cn[e]];
+        if (tb != last) { fix_producers(&prodL[tb], k); last = tb; }
+    }
+
+    /* rewrite the storage: block k-1 void, block k = the merged block */
+    F->Lrow.n = L0;
+    F->Lval.n = F->Lvptr[k - 1];
+    for (int64_t e = 0; e < u; ++e) vi_push(&F->Lrow, Rn[e]);
+    vd_reserve(&F->Lval, u * w);
+    memcpy(F->Lval.a + F->Lval.n, Lh, (size_t)(u * w) * sizeof(double));
+    F->Lval.n += u * w;
+    F->Ucol.n = U0;
+    F->Uval.n = F->Uvptr[k - 1];
+    for (int64_t e = 0; e < v; ++e) vi_push(&F->Ucol, Cn[e]);
+    vd_reserve(&F->Uval, v * w);
+    memcpy(F->Uval.a + F->Uval.n, Uh, (size_t)(v * w) * sizeof(double));
+    F->Uval.n += v * w;
+    F->Lptr[k] = L0; F->Lvptr[k] = F->Lvptr[k - 1];
+    F->Uptr[k] = U0; F->Uvptr[k] = F->Uvptr[k - 1];
+    F->Lptr[k + 1] = F->Lrow.n; F->Lvptr[k + 1] = F->Lval.n;
+    F->Uptr[k + 1] = F->Ucol.n; F->Uvptr[k + 1] = F->Uval.n;
+
+    const int64_t d0 = F->Dptr[k - 1];
+    if (d0 + w * w > F->dcap) {
+        F->dcap = 2 * (d0 + w * w);
+        F->Dinv = xrealloc(F->Dinv, (size_t)F->dcap * sizeof(double));
+        F->Pblk = xrealloc(F->Pblk, (size_t)F->dcap * sizeof(double));
+        F->LUblk = xrealloc(F->LUblk, (size_t)F->dcap * sizeof(double));
+    }
+    memcpy(F->Dinv + d0, Dh, (size_t)(w * w) * sizeof(double));
+    memcpy(F->Pblk + d0, Ph, (size_t)(w * w) * sizeof(double));
+    /* the getrf factors of P-hat, for export only (D-hat comes from the identity above) */
+    memcpy(F->LUblk + d0, Ph, (size_t)(w * w) * sizeof(double));
+    getrf_plain(F->LUblk + d0, (int)w, F->piv + a0, 0.0);
+    F->Dptr[k] = d0;
+    F->Dptr[k + 1] = d0 + w * w;
+    F->bstart[k] = a0;
+    for (int32_t i = a0; i < s0; ++i) blk_of[i] = k;
+    F->merges += 1;
+
+    free(L21); free(U12); free(Ph); free(Dh); free(DU); free(DL);
+    free(Rn); free(Cn); free(Lh); free(Uh);
+}
+
 /*
  * Crout-type BILU (Algorithm 1 with blocks, Sec. 2.2).  For K = 0..nb-1 with block
  * B_K = [s0, s1), b = s1 - s0:
@@ -412,7 +636,14 @@ static void spa_reset(spa_t *s, int b) {
 int32_t orc_bilu_factor(int64_t n, const int64_t *rowptr, const int32_t *colind,
                         const double *val, int32_t nb, const int32_t *bstart, double droptol,
                         int32_t perturb, double pert_tau, double pert_rho, orc_factor **out) {
-    if (n < 0 || nb < 0 || droptol < 0 || !out) return ORC_ERR_ARG;
+    return orc_bilu_factor_agg(n, rowptr, colind, val, nb, bstart, droptol, perturb, pert_tau, pert_rho, 0, out);
+}
+
+int32_t orc_bilu_factor_agg(int64_t n, const int64_t *rowptr, const int32_t *colind,
+                            const double *val, int32_t nb, const int32_t *bstart, double droptol,
+                            int32_t perturb, double pert_tau, double pert_rho, int32_t agg_max,
+                            orc_factor **out) {
+    if (n < 0 || nb < 0 || droptol < 0 || agg_max < 0 || !out) return ORC_ERR_ARG;
     if (bstart[0] != 0 || bstart[nb] != n) return ORC_ERR_ARG;
     for (int32_t K = 0; K < nb; ++K)
         if (bstart[K + 1] <= bstart[K]) return ORC_ERR_ARG;
@@ -426,13 +657,15 @@ int32_t orc_bilu_factor(int64_t n, const int64_t *rowptr, const int32_t *colind,
     F->Uptr = xcalloc((size_t)nb + 1, sizeof(int64_t));
     F->Uvptr = xcalloc((size_t)nb + 1, sizeof(int64_t));
     F->Dptr = xcalloc((size_t)nb + 1, sizeof(int64_t));
+    /* D blocks are laid out in block order as the blocks are factored (a merge rewrites
+     * the last two); the initial capacity is that of the unmerged partition */
     for (int32_t K = 0; K < nb; ++K) {
         int64_t b = bstart[K + 1] - bstart[K];
-        F->Dptr[K + 1] = F->Dptr[K] + b * b;
+        F->dcap += b * b;
     }
-    F->Dinv = xcalloc((size_t)F->Dptr[nb], sizeof(double));
-    F->Pblk = xcalloc((size_t)F->Dptr[nb], sizeof(double));
-    F->LUblk = xcalloc((size_t)F->Dptr[nb], sizeof(double));
+    F->Dinv = xcalloc((size_t)F->dcap + 1, sizeof(double));
+    F->Pblk = xcalloc((size_t)F->dcap + 1, sizeof(double));
+    F->LUblk = xcalloc((size_t)F->dcap + 1, sizeof(double));
     F->piv = xcalloc((size_t)n, sizeof(int32_t));
 
     csc_t csc = csr_to_csc(n, rowptr, colind, val);
@@ -485,7 +718,7 @@ int32_t orc_bilu_factor(int64_t n, const int64_t *rowptr, const int32_t *colind,
         /* step 2a: L side, J with kept U columns in B_K */
         for (int64_t t = 0; t < prodL[K].n; ++t) {
             int32_t J = prodL[K].a[t];
-            int bJ = bstart[J + 1] - bstart[J];
+            int bJ = F->bstart[J + 1] - F->bstart[J]; /* a merged producer spans its void predecessor */
             int64_t qs = lower_bound_i32(F->Ucol.a, F->Uptr[J], F->Uptr[J + 1], s0);
             int64_t qe = lower_bound_i32(F->Ucol.a, qs, F->Uptr[J + 1], s1);
             int64_t ps = lower_bound_i32(F->Lrow.a, F->Lptr[J], F->Lptr[J + 1], s0);
@@ -508,7 +741,7 @@ int32_t orc_bilu_factor(int64_t n, const int64_t *rowptr, const int32_t *colind,
         /* step 2b: U side, J with kept L rows in B_K */
         for (int64_t t = 0; t < prodU[K].n; ++t) {
             int32_t J = prodU[K].a[t];
-            int bJ = bstart[J + 1] - bstart[J];
+            int bJ = F->bstart[J + 1] - F->bstart[J];
             int64_t ps = lower_bound_i32(F->Lrow.a, F->Lptr[J], F->Lptr[J + 1], s0);
             int64_t pe = lower_bound_i32(F->Lrow.a, ps, F->Lptr[J + 1], s1);
             int64_t qs = lower_bound_i32(F->Ucol.a, F->Uptr[J], F->Uptr[J + 1], s1);
@@ -530,6 +763,13 @@ int32_t orc_bilu_factor(int64_t n, const int64_t *rowptr, const int32_t *colind,
         }
 
         /* step 3: pivot block */
+        F->Dptr[K + 1] = F->Dptr[K] + (int64_t)b * b;
+        if (F->Dptr[K + 1] > F->dcap) { /* merges made the D blocks larger than the partition's */
+            F->dcap = 2 * F->Dptr[K + 1];
+            F->Dinv = xrealloc(F->Dinv, (size_t)F->dcap * sizeof(double));
+            F->Pblk = xrealloc(F->Pblk, (size_t)F->dcap * sizeof(double));
+            F->LUblk = xrealloc(F->LUblk, (size_t)F->dcap * sizeof(double));
+        }
         P = xrealloc(P, (size_t)b * b * sizeof(double));
         for (int r = 0; r < b; ++r)
             for (int c = 0; c < b; ++c) P[r * b + c] = TL.buf[(size_t)r * b + c]; /* slots 0..b-1 = rows s0.. */
@@ -608,6 +848,9 @@ int32_t orc_bilu_factor(int64_t n, const int64_t *rowptr, const int32_t *colind,
             int32_t t = blk_of[F->Ucol.a[q]];
             if (t != last) { vi_push(&prodL[t], K); last = t; }
         }
+
+        /* Sec. 3.5: merge the finished blocks K-1 and K when the memory grows mildly */
+        if (agg_max > 0 && K > 0) aggregate_step(F, K, agg_max, prodL, prodU, blk_of);
     }
 
     if (status >= 0 && F->counters[ORC_C_NPERTURB] > 0) status = ORC_PERTURBED;
@@ -622,8 +865,13 @@ int32_t orc_bilu_factor(int64_t n, const int64_t *rowptr, const int32_t *colind,
     return status;
 }
 
+void orc_factor_bstart(const orc_factor *F, int32_t *bstart) {
+    memcpy(bstart, F->bstart, (size_t)(F->nb + 1) * sizeof(int32_t));
+}
+
 void orc_factor_sizes(const orc_factor *F, int64_t sizes[8]) {
     memset(sizes, 0, 8 * sizeof(int64_t));
+    sizes[7] = F->merges;
     sizes[0] = F->Lrow.n;
     sizes[1] = F->Ucol.n;
     sizes[2] = F->Lval.n;

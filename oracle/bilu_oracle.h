@@ -17,6 +17,7 @@
  *     blocks factored (LU with pivoting inside the block only) and inverted
  *     (Sec. 2.2, end).
  *   - Perturbation of singular diagonal blocks (Sec. 3.6).
+ *   - Progressive aggregation of consecutive blocks during the factorization (Sec. 3.5).
  *   - Simplified ILU(1,tau) block-pattern guess (Sec. 3.4).
  *   - Restarted GMRES(30) (Sec. 4, Example setup).
  *
@@ -93,8 +94,26 @@ int32_t orc_bilu_factor(int64_t n, const int64_t *rowptr, const int32_t *colind,
                         const double *val, int32_t nb, const int32_t *bstart, double droptol,
                         int32_t perturb, double pert_tau, double pert_rho, orc_factor **out);
 
+/* The same with progressive aggregation (Sec. 3.5) when agg_max > 0: after block K is
+ * finished it is merged with block K-1 when the merge test holds and the merged block has at
+ * most agg_max columns; block K-1 then becomes void (size 0) and block K holds both.  The
+ * factor's block boundaries are then those of orc_factor_bstart.  agg_max = 0: no merging
+ * (orc_bilu_factor). */
+int32_t orc_bilu_factor_agg(int64_t n, const int64_t *rowptr, const int32_t *colind,
+                            const double *val, int32_t nb, const int32_t *bstart, double droptol,
+                            int32_t perturb, double pert_tau, double pert_rho, int32_t agg_max,
+                            orc_factor **out);
+
+/* Sec. 3.5 merge test for the counts it names (see bilu_oracle.c); 1 = merge. */
+int32_t orc_agg_rule(int64_t p, int64_t q, int64_t r, int64_t s, int64_t rp, int64_t sp, int64_t t,
+                     int64_t tp, int64_t u, int64_t v);
+
+/* The factor's block boundaries (nb + 1 entries): the partition given, with merged blocks
+ * (void blocks have bstart[K] == bstart[K+1]). */
+void orc_factor_bstart(const orc_factor *F, int32_t *bstart);
+
 /* sizes[0] = kept L rows, [1] = kept U cols, [2] = L values, [3] = U values,
- * [4] = sum b_K^2, [5] = number of blocks, [6] = perturbations */
+ * [4] = sum b_K^2, [5] = number of blocks, [6] = perturbations, [7] = merges */
 void orc_factor_sizes(const orc_factor *F, int64_t sizes[8]);
 
 /* Exports the factor in the layout shared by the tests:

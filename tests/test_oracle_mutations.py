@@ -17,7 +17,8 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PIN_TESTS = ["test_oracle.py", "test_partition_oracle.py", "test_block_check_oracle.py", "test_skip_oracle.py",
-             "test_golden.py", "test_cosine_oracle.py", "test_mwm_oracle.py", "test_nd_oracle.py"]
+             "test_golden.py", "test_cosine_oracle.py", "test_mwm_oracle.py", "test_nd_oracle.py",
+             "test_aggregation_oracle.py"]
 ORACLE_FILES = ["__init__.py", "bilu_oracle.c", "bilu_oracle.h", "block_check.py", "skip_oracle.py",
                 "cosine_oracle.py", "mwm_oracle.py", "nd_oracle.py"]
 
@@ -50,6 +51,25 @@ MUTANTS = [
     ("LU multipliers not divided by the pivot", C, "for (int i = j + 1; i < b; ++i) a[i * b + j] /= a[j * b + j];",
      "for (int i = j + 1; i < b; ++i) a[i * b + j] /= 1.0;", 1),
     ("inverse multiplies by the pivot", C, "y[i] /= lu[i * b + i];", "y[i] *= lu[i * b + i];", 1),
+    # progressive aggregation (Sec. 3.5)
+    ("merge test 1.3 mu", C, "return (5 * nu <= 6 * mu) || (nu <= mu + 2 * (p + q));",
+     "return (10 * nu <= 13 * mu) || (nu <= mu + 2 * (p + q));", 1),
+    ("merge test without the two-entry allowance", C, "return (5 * nu <= 6 * mu) || (nu <= mu + 2 * (p + q));",
+     "return (5 * nu <= 6 * mu);", 1),
+    ("mu misses the U rows of block k-1", C, "const int64_t mu = p * (p + r + s + rp + sp) + q * (q + t + tp);",
+     "const int64_t mu = p * (p + r + s) + q * (q + t + tp);", 1),
+    ("merged L rows keep L_{i,k-1} unchanged", C, "for (int64_t m = 0; m < q; ++m) acc -= lb[m] * L21[m * p + j];", "",
+     1),
+    ("merged U columns add L21 U with the wrong sign", C, "for (int64_t m = 0; m < p; ++m) acc += L21[i * p + m] * ua[m];",
+     "for (int64_t m = 0; m < p; ++m) acc -= L21[i * p + m] * ua[m];", 1),
+    ("merged inverse without the coupling term", C, "for (int64_t m = 0; m < q; ++m) acc += DU[i * q + m] * DL[m * p + j];",
+     "", 1),
+    ("merged pivot block with L21 and U12 swapped", C, "for (int64_t j = 0; j < q; ++j) Ph[i * w + p + j] = U12[i * q + j];",
+     "for (int64_t j = 0; j < q; ++j) Ph[i * w + p + j] = L21[j * p + i];", 1),
+    ("producer lists keep the void block", C, "if (tb != last) { fix_producers(&prodU[tb], k); last = tb; }", "", 1),
+    ("merged producer read with its unmerged width", C,
+     "int bJ = F->bstart[J + 1] - F->bstart[J]; /* a merged producer spans its void predecessor */",
+     "int bJ = bstart[J + 1] - bstart[J];", 1),
     # perturbation (Sec. 3.6)
     ("sign(0) = -1", C, "return x >= 0.0 ? 1.0 : -1.0;", "return x > 0.0 ? 1.0 : -1.0;", 1),
     ("rho ignored", C, "return d * (1.0 + prho) + sgn_plus(d) * ptau * alpha;",
