@@ -78,6 +78,8 @@ def parse():
                     help="tree (default): CTA groups factor independent subtrees of the block elimination tree "
                          "(pays off with --order nd), the trunk on the whole GPU; chain: one block after another")
     ap.add_argument("--group-ctas", type=int, default=0, help="tree schedule: CTAs per group (0: library default)")
+    ap.add_argument("--aggregate", type=int, default=0,
+                    help="progressive aggregation (Sec. 3.5): merge consecutive blocks up to this size (0: off)")
     ap.add_argument("--batch", type=int, default=0,
                     help="factor + solve this many uneven 2D/3D matrices in one batched launch instead")
     ap.add_argument("--compare-fp64", action="store_true",
@@ -210,6 +212,8 @@ def config(args, w, extra=None):
          "updates": getattr(args, "precision", "fp64"), "skip": getattr(args, "skip", "none"),
          "order": getattr(args, "order", "natural"), "schedule": getattr(args, "schedule", "chain"),
          "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{args.gpus}"}
+    if getattr(args, "aggregate", 0):
+        c["aggregate_max"] = args.aggregate
     pre = [k for k, on in (("mwm", getattr(args, "mwm", False)),
                            ("nd", getattr(args, "order", "natural") == "nd")) if on]
     if pre or blocking != "fixed":
@@ -488,7 +492,7 @@ def run_gpu(args):
                                    skip={"none": B.BILU_SKIP_NONE, "bound": B.BILU_SKIP_BOUND,
                                          "learned": B.BILU_SKIP_LEARNED}[args.skip],
                                    schedule={"chain": B.BILU_SCHED_CHAIN, "tree": B.BILU_SCHED_TREE}[args.schedule],
-                                   group_ctas=args.group_ctas)
+                                   group_ctas=args.group_ctas, aggregate_max=args.aggregate)
     learned = None
     if args.skip == "learned":  # train the classifier first (not timed)
         from paper_1908_10169_gb300 import learned_skip as LS
@@ -740,6 +744,12 @@ def run_gpu(args):
                                            "solve_ms": statistics.median(ts), "apply_ms": t_apply,
                                            "fill_nnz(L+U+D)/nnz(A)": (st.nnz_l + st.nnz_u + st.nnz_d) / w.A.nnz,
                                            "nblocks": st.nblocks, "bound_drops": st.bound_drops,
+                                           "block_size": {"avg": st.avg_bsize, "max": st.max_bsize},
+                                           **({"aggregation": {"merges": st.agg_merges,
+                                                               "blocks_after": st.nblocks - st.agg_merges,
+                                                               "max_block_after": st.agg_max_bsize,
+                                                               "ms": st.t_aggregate_ms}}
+                                              if args.aggregate else {}),
                                            **({"tree": {"height": st.tree_height, "trunk_blocks": st.tree_trunk,
                                                         "group_ctas": st.group_ctas,
                                                         "groups": (torch.cuda.get_device_properties(dev).multi_processor_count

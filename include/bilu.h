@@ -85,6 +85,19 @@ typedef struct {
                             Not with BILU_SKIP_LEARNED or sample recording (BILU_ERR_ARG).      */
     int32_t group_ctas;  /* CTAs per group of BILU_SCHED_TREE, 1..number of SMs (0: an eighth of
                             the SMs, 8 groups)                                                  */
+    int32_t aggregate_max; /* progressive aggregation (Sec. 3.5), 0 (off) or 2..BILU_MAX_BLOCK:
+                            consecutive finished blocks k-1, k are merged into one block of at
+                            most this many columns whenever the merge test of Sec. 3.5 holds
+                            (nu <= 1.2 mu or nu <= mu + 2 (p + q), mu / nu the stored values
+                            before / after); block k-1 becomes void (size 0) and block k holds
+                            both.  The merged block stores the union of the rows (columns) and
+                            L-hat = L_{:,G} L_GG^{-1}, U-hat = L_GG U-breve_{G,:}, P-hat = L_GG T_GG,
+                            D-hat = P-hat^{-1} for the merged group G (L_GG its unit lower part,
+                            T_GG its upper part with the pivot blocks): the product of the factors
+                            is unchanged, so the preconditioner is the same operator.  Applied
+                            after the factorization, in block order, to the finished factor
+                            (every schedule); the sweeps, the solves and bilu_export then use
+                            the merged blocks (bilu_get_factor_partition).                    */
 } bilu_params;
 
 typedef struct {
@@ -135,6 +148,10 @@ typedef struct {
                                  sum_k |T_ik| ||D_K(k,:)|| of the norm (columns: with the
                                  column norms of D_K) was already <= tau, so the product
                                  would have dropped them too; the factor is unchanged    */
+    int32_t agg_merges;       /* progressive aggregation: blocks merged into their
+                                 successor (void blocks of the factor); 0 when off       */
+    int32_t agg_max_bsize;    /* largest block of the factor after the merges            */
+    double t_aggregate_ms;    /* host + device time of the merges (part of bilu_factor)  */
 } bilu_stats_t;
 
 /* Fills *p with the defaults: FIXED blocking of 32 (max 64), tau_analyze 1e-2,
@@ -226,6 +243,13 @@ bilu_status bilu_stats(bilu_ctx *ctx, bilu_stats_t *out);
  * (caller-owned; nblocks from bilu_stats).  Errors: BILU_ERR_ARG (NULL), BILU_ERR_STATE. */
 bilu_status bilu_get_partition(bilu_ctx *ctx, int32_t *bstart);
 
+/* Copies the block boundaries of the factor (nblocks + 1 entries, caller-owned host memory):
+ * the analysis partition, or after progressive aggregation (aggregate_max) the merged one,
+ * void blocks having bstart[K] == bstart[K+1] (Sec. 3.5).  The export's per-block arrays
+ * (Lptr, Uptr, the value layouts) follow these boundaries.
+ * Errors: BILU_ERR_ARG (NULL), BILU_ERR_STATE (no factor), BILU_ERR_CUDA. */
+bilu_status bilu_get_factor_partition(bilu_ctx *ctx, int32_t *bstart);
+
 /*
  * Copies the factor to host memory in the layout:
  *   Lptr[nb+1] kept-row offsets; Lrow[kept_rows] global rows (sorted per block);
@@ -234,7 +258,8 @@ bilu_status bilu_get_partition(bilu_ctx *ctx, int32_t *bstart);
  *   U-breve(s_K + t, Ucol[q]); Dinv[nnz_d] per block b_K x b_K row-major (D_K = P_K^{-1});
  *   Pblk[nnz_d] the updated pivot blocks P_K.  Any pointer may be NULL.  All host arrays,
  *   caller-owned, sized from bilu_stats; the factor is A ~ L D^{-1} U of Sec. 2.2 with
- *   L D^{-1} U = L U-breve.  Reduced-precision factors are widened to FP64.
+ *   L D^{-1} U = L U-breve.  Reduced-precision factors are widened to FP64.  With
+ *   progressive aggregation the blocks are those of bilu_get_factor_partition.
  * Errors: BILU_ERR_ARG (NULL context), BILU_ERR_STATE (no factor), BILU_ERR_CUDA.
  */
 bilu_status bilu_export(bilu_ctx *ctx, int64_t *Lptr, int32_t *Lrow, double *Lval, int64_t *Uptr,

@@ -29,7 +29,8 @@ BILU_MAX_BLOCK = 64
 
 # every extern "C" symbol that include/bilu.h declares
 EXPORTED = ["bilu_params_default", "bilu_create", "bilu_analyze", "bilu_factor", "bilu_apply",
-            "gmres_solve", "bilu_stats", "bilu_get_partition", "bilu_export", "bilu_last_error",
+            "gmres_solve", "bilu_stats", "bilu_get_partition", "bilu_get_factor_partition", "bilu_export",
+            "bilu_last_error",
             "bilu_debug_set", "bilu_apply_noalloc", "bilu_factor_batch", "gmres_solve_batch",
             "bilu_record_samples", "bilu_get_samples", "bilu_mlp_train", "bilu_mlp_forward", "bilu_mlp_grad",
             "bilu_set_skip_model", "bilu_cosine_blocking", "bilu_partition_ilu1t", "bilu_mwm", "bilu_scale_permute_csr",
@@ -49,7 +50,7 @@ class bilu_params(ct.Structure):
     _fields_ = [("blocking", ct.c_int32), ("max_block", ct.c_int32), ("fixed_block", ct.c_int32),
                 ("tau_analyze", ct.c_double), ("perturb", ct.c_int32), ("pert_tau", ct.c_double),
                 ("pert_rho", ct.c_double), ("precision", ct.c_int32), ("skip", ct.c_int32),
-                ("schedule", ct.c_int32), ("group_ctas", ct.c_int32)]
+                ("schedule", ct.c_int32), ("group_ctas", ct.c_int32), ("aggregate_max", ct.c_int32)]
 
 
 class gmres_info(ct.Structure):
@@ -69,7 +70,8 @@ class bilu_stats_t(ct.Structure):
                 ("kernel_launches", ct.c_int64), ("phase_ms", ct.c_double * 8),
                 ("skipped_rows", ct.c_int64), ("skipped_cols", ct.c_int64), ("schedule", ct.c_int32),
                 ("tree_height", ct.c_int32), ("tree_trunk", ct.c_int32), ("group_ctas", ct.c_int32),
-                ("idle_ms", ct.c_double), ("bound_drops", ct.c_int64)]
+                ("idle_ms", ct.c_double), ("bound_drops", ct.c_int64), ("agg_merges", ct.c_int32),
+                ("agg_max_bsize", ct.c_int32), ("t_aggregate_ms", ct.c_double)]
 
 
 class bilu_mlp_train_cfg(ct.Structure):
@@ -102,6 +104,7 @@ def lib():
             "gmres_solve": ([P, P, P, f64, i32, i32, ct.POINTER(gmres_info)], i32),
             "bilu_stats": ([P, ct.POINTER(bilu_stats_t)], i32),
             "bilu_get_partition": ([P, P], i32),
+            "bilu_get_factor_partition": ([P, P], i32),
             "bilu_export": ([P] * 9, i32),
             "bilu_last_error": ([P], ct.c_char_p),
             "bilu_debug_set": ([P, i32, i64], i32),
@@ -485,6 +488,13 @@ def bilu_get_partition(ctx, out):
     """Copies the block starts into out (int32, nblocks + 1)."""
     s = bilu_stats(ctx)
     return _check(ctx, lib().bilu_get_partition(ctx, _buf(out, "int32", s.nblocks + 1, "bstart")))
+
+
+def bilu_get_factor_partition(ctx, out):
+    """Copies the factor's block starts (after any merges; void blocks repeat a start) into out
+    (int32, nblocks + 1)."""
+    s = bilu_stats(ctx)
+    return _check(ctx, lib().bilu_get_factor_partition(ctx, _buf(out, "int32", s.nblocks + 1, "bstart")))
 
 
 def bilu_export(ctx, Lptr=None, Lrow=None, Lval=None, Uptr=None, Ucol=None, Uval=None, Dinv=None, Pblk=None):

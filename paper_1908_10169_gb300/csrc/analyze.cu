@@ -780,6 +780,8 @@ bilu_status analyze_run(bilu_ctx *c, int64_t n, const int64_t *rowptr, const int
         return set_err(c, BILU_ERR_ARG, "unknown schedule");
     if (p->group_ctas < 0 || p->group_ctas > c->nsm)
         return set_err(c, BILU_ERR_ARG, "group_ctas must be in 0..number of SMs");
+    if (p->aggregate_max != 0 && (p->aggregate_max < 2 || p->aggregate_max > BILU_MAX_BLOCK))
+        return set_err(c, BILU_ERR_ARG, "aggregate_max must be 0 or in 2..BILU_MAX_BLOCK");
 
     const auto t_start = std::chrono::steady_clock::now();
 

@@ -443,19 +443,20 @@ bilu_status apply_alloc(bilu_ctx *c) {
     apply_free(c);
     const int64_t nb = std::max<int64_t>(c->nb, 1);
     if (dev_alloc(&c->d_flagF, nb) != cudaSuccess || dev_alloc(&c->d_flagB, nb) != cudaSuccess ||
-        dev_alloc(&c->d_planF, nb * (int64_t)c->prodcap) != cudaSuccess || dev_alloc(&c->d_apst, 8) != cudaSuccess) {
+        dev_alloc(&c->d_planF, nb * (int64_t)factor_view(c).prodcap) != cudaSuccess || dev_alloc(&c->d_apst, 8) != cudaSuccess) {
         apply_free(c);
         return set_err(c, BILU_ERR_OOM, "apply allocation failed");
     }
     BILU_CUDA(c, cudaMemsetAsync(c->d_flagF, 0, nb * sizeof(int32_t), c->stream));
     BILU_CUDA(c, cudaMemsetAsync(c->d_flagB, 0, nb * sizeof(int32_t), c->stream));
     BILU_CUDA(c, cudaMemsetAsync(c->d_apst, 0, 8 * sizeof(int32_t), c->stream));
-    const int64_t warps = nb * c->prodcap;
+    const FactorView v = factor_view(c);
+    const int64_t warps = nb * v.prodcap;
     const int threads = 256;
     const int64_t blocks = std::min<int64_t>((warps * 32 + threads - 1) / threads, 65535);
     if (c->nb > 0) {
-        apply_plan_kernel<<<(unsigned)blocks, threads, 0, c->stream>>>(c->nb, c->prodcap, c->d_bstart, c->d_Lptr, c->d_Lrow,
-                                                                     c->d_prodU, c->d_prodUcnt, c->d_planF);
+        apply_plan_kernel<<<(unsigned)blocks, threads, 0, c->stream>>>(c->nb, v.prodcap, v.bstart, v.Lptr, v.Lrow,
+                                                                     v.prodU, v.prodUcnt, c->d_planF);
         c->launches += 1;
     }
     BILU_CUDA(c, cudaGetLastError());
@@ -463,14 +464,15 @@ bilu_status apply_alloc(bilu_ctx *c) {
 }
 
 bilu_status apply_launch(bilu_ctx *c, const double *d_r, double *d_z, const int32_t *skip) {
+    const FactorView v = factor_view(c);  // the merged blocks after progressive aggregation
     ApplyArgs a{};
     a.nb = c->nb;
-    a.bstart = c->d_bstart;
-    a.blkof = c->d_blkof;
-    a.Lptr = c->d_Lptr; a.Lvptr = c->d_Lvptr; a.Uptr = c->d_Uptr; a.Uvptr = c->d_Uvptr; a.Dptr = c->d_Dptr;
-    a.Lrow = c->d_Lrow; a.Ucol = c->d_Ucol; a.Lval = c->d_Lval; a.Uval = c->d_Uval; a.Dinv = c->d_Dinv;
-    a.Uhval = c->d_Uhval;
-    a.prodU = c->d_prodU; a.prodUcnt = c->d_prodUcnt; a.prodcap = c->prodcap;
+    a.bstart = v.bstart;
+    a.blkof = v.blkof;
+    a.Lptr = v.Lptr; a.Lvptr = v.Lvptr; a.Uptr = v.Uptr; a.Uvptr = v.Uvptr; a.Dptr = v.Dptr;
+    a.Lrow = v.Lrow; a.Ucol = v.Ucol; a.Lval = v.Lval; a.Uval = v.Uval; a.Dinv = v.Dinv;
+    a.Uhval = v.Uhval;
+    a.prodU = v.prodU; a.prodUcnt = v.prodUcnt; a.prodcap = v.prodcap;
     a.planF = c->d_planF;
     a.r = d_r;
     a.z = d_z;

@@ -269,13 +269,15 @@ extern "C" bilu_status bilu_apply_noalloc(bilu_ctx *c, const double *r, double *
     BILU_CUDA(c, cudaMemsetAsync(sc->flagB, 0, (size_t)c->nb * sizeof(int32_t), c->stream));
     BILU_CUDA(c, cudaMemsetAsync(sc->st, 0, sizeof(sc->st), c->stream));
     NaArgs a{};
+    const FactorView v = factor_view(c);  // the merged blocks after progressive aggregation
     a.nb = c->nb;
-    a.prodcap = c->prodcap;
-    a.bstart = c->d_bstart;
-    a.blkof = c->d_blkof;
-    a.Lptr = c->d_Lptr; a.Lvptr = c->d_Lvptr; a.Uptr = c->d_Uptr; a.Uvptr = c->d_Uvptr; a.Dptr = c->d_Dptr;
-    a.Lrow = c->d_Lrow; a.Ucol = c->d_Ucol; a.Lval = c->d_Lval; a.Uval = c->d_Uval; a.Dinv = c->d_Dinv;
-    a.prodU = c->d_prodU; a.prodUcnt = c->d_prodUcnt;
+    a.prodcap = v.prodcap;
+    a.bstart = v.bstart;
+    a.blkof = v.blkof;
+    a.Lptr = v.Lptr; a.Lvptr = v.Lvptr; a.Uptr = v.Uptr; a.Uvptr = v.Uvptr; a.Dptr = v.Dptr;
+    a.Lrow = v.Lrow; a.Ucol = v.Ucol; a.Lval = (const double *)v.Lval; a.Uval = (const double *)v.Uval;
+    a.Dinv = v.Dinv;
+    a.prodU = v.prodU; a.prodUcnt = v.prodUcnt;
     a.r = r;
     a.z = z;
     a.sc = sc;

@@ -121,6 +121,19 @@ struct bilu_ctx {
     int64_t *d_aptr = nullptr;      // 6 x nb: L begin, L end, L value begin, U begin, U end, U value begin
     double idle_ms = 0.0;           // last tree factorization: time its groups waited for ready blocks
 
+    // progressive aggregation (Sec. 3.5): the merged copy of the last factor, which the sweeps,
+    // the solves and the export read when agg_merges > 0 (see factor_view)
+    int32_t agg_merges = 0, agg_bmax = 0, agg_prodcap = 0;
+    int64_t agg_rows = 0, agg_cols = 0, agg_nnz_l = 0, agg_nnz_u = 0, agg_nnz_d = 0;
+    double t_aggregate_ms = 0.0;
+    std::vector<int32_t> h_ag_bstart;
+    int64_t ag_cap[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};  // allocated sizes of the buffers below
+    int32_t *d_ag_bstart = nullptr, *d_ag_blkof = nullptr, *d_ag_Lrow = nullptr, *d_ag_Ucol = nullptr;
+    int32_t *d_ag_prodU = nullptr, *d_ag_prodUcnt = nullptr, *d_ag_grp = nullptr;
+    int64_t *d_ag_ptr = nullptr;   // 5 x (nb + 1): Lptr, Lvptr, Uptr, Uvptr, Dptr
+    void *d_ag_Lval = nullptr, *d_ag_Uval = nullptr, *d_ag_Uhval = nullptr;
+    double *d_ag_Dinv = nullptr, *d_ag_Pblk = nullptr;
+
     // apply
     int32_t *d_flagF = nullptr, *d_flagB = nullptr;
     int2 *d_planF = nullptr;       // per (block, forward producer): L rows inside the block
@@ -166,6 +179,20 @@ struct bilu_ctx {
     double phase_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 };
 
+// The factor as the sweeps, the solves and the export read it: the factorization's own arrays,
+// or, after progressive aggregation merged blocks, the merged copy.  Value arrays hold the
+// storage type of the precision (FP64, FP32 or BF16).
+struct FactorView {
+    int32_t nb = 0, prodcap = 0;
+    const int32_t *bstart = nullptr, *blkof = nullptr, *Lrow = nullptr, *Ucol = nullptr;
+    const int32_t *prodU = nullptr, *prodUcnt = nullptr;
+    const int64_t *Lptr = nullptr, *Lvptr = nullptr, *Uptr = nullptr, *Uvptr = nullptr, *Dptr = nullptr;
+    const void *Lval = nullptr, *Uval = nullptr, *Uhval = nullptr;
+    const double *Dinv = nullptr, *Pblk = nullptr;
+    int64_t kept_rows = 0, kept_cols = 0, nnz_l = 0, nnz_u = 0, nnz_d = 0;
+};
+FactorView factor_view(const bilu_ctx *c);
+
 // helpers shared by the translation units of the library
 bilu_status set_err(bilu_ctx *c, bilu_status st, const std::string &msg);
 bilu_status cuda_err(bilu_ctx *c, cudaError_t e, const char *where);
@@ -198,6 +225,8 @@ void apply_free(bilu_ctx *c);
 bilu_status gmres_run(bilu_ctx *c, const double *d_b, double *d_x, double tol, int restart,
                       int maxit, gmres_info *info);
 void gmres_free(bilu_ctx *c);
+bilu_status aggregate_run(bilu_ctx *c);
+void aggregate_free(bilu_ctx *c);
 bilu_status gmres_batch_run(bilu_ctx *const *ctxs, int count, const double *const *b, double *const *x, double tol,
                             int m, int maxit, gmres_info *info);
 bilu_status factor_batch_run(bilu_ctx *const *ctxs, int count, double droptol, double *ms_out);

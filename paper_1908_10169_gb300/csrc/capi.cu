@@ -180,6 +180,8 @@ bilu_status bilu_factor(bilu_ctx *c, double droptol) {
     gmres_free(c);  // captured graphs refer to the previous factor
     bilu_status st = factor_run(c, droptol);
     if (st < 0) return st;
+    bilu_status sg = aggregate_run(c);
+    if (sg < 0) return sg;
     bilu_status sa = apply_alloc(c);
     if (sa != BILU_OK) return sa;
     BILU_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -255,6 +257,8 @@ bilu_status bilu_factor_batch(bilu_ctx *const *ctxs, int32_t count, double dropt
     bilu_status st = factor_batch_run(ctxs, count, droptol, &ms);
     if (st < 0) return st;
     for (int32_t i = 0; i < count; ++i) {
+        bilu_status sg = aggregate_run(ctxs[i]);
+        if (sg < 0) return sg;
         bilu_status sa = apply_alloc(ctxs[i]);
         if (sa != BILU_OK) return sa;
     }
@@ -298,6 +302,7 @@ bilu_status bilu_stats(bilu_ctx *c, bilu_stats_t *o) {
     o->std_bsize = c->nb ? std::sqrt(std::max(0.0, s2 / c->nb - o->avg_bsize * o->avg_bsize)) : 0.0;
     o->nnz_d = c->h_Dptr.empty() ? 0 : c->h_Dptr.back();
     o->t_analyze_ms = c->t_analyze_ms;
+    o->agg_max_bsize = c->bmax;
     o->kernel_launches = c->launches;
     o->schedule = c->p.schedule;
     if (c->p.schedule == BILU_SCHED_TREE) {
@@ -306,10 +311,16 @@ bilu_status bilu_stats(bilu_ctx *c, bilu_stats_t *o) {
         o->group_ctas = tree_group_ctas(c);
     }
     if (c->state >= 2) {
-        o->nnz_l = c->nnz_l;
-        o->nnz_u = c->nnz_u;
-        o->kept_rows = c->kept_rows;
-        o->kept_cols = c->kept_cols;
+        // sizes of the factor as exported (after any merges)
+        const FactorView v = factor_view(c);
+        o->nnz_l = v.nnz_l;
+        o->nnz_u = v.nnz_u;
+        o->nnz_d = v.nnz_d;
+        o->kept_rows = v.kept_rows;
+        o->kept_cols = v.kept_cols;
+        o->agg_merges = c->agg_merges;
+        o->agg_max_bsize = c->agg_merges > 0 ? c->agg_bmax : c->bmax;
+        o->t_aggregate_ms = c->t_aggregate_ms;
         o->cand_rows = c->cand_rows;
         o->cand_cols = c->cand_cols;
         o->nperturb = c->nperturb;
@@ -329,6 +340,14 @@ bilu_status bilu_stats(bilu_ctx *c, bilu_stats_t *o) {
     return BILU_OK;
 }
 
+bilu_status bilu_get_factor_partition(bilu_ctx *c, int32_t *bstart) {
+    if (!c || !bstart) return BILU_ERR_ARG;
+    if (c->state < 2) return set_err(c, BILU_ERR_STATE, "no factor");
+    const std::vector<int32_t> &b = c->agg_merges > 0 ? c->h_ag_bstart : c->h_bstart;
+    std::memcpy(bstart, b.data(), b.size() * sizeof(int32_t));
+    return BILU_OK;
+}
+
 bilu_status bilu_get_partition(bilu_ctx *c, int32_t *bstart) {
     if (!c || !bstart) return BILU_ERR_ARG;
     if (c->state < 1) return set_err(c, BILU_ERR_STATE, "no analysis");
@@ -341,18 +360,19 @@ bilu_status bilu_export(bilu_ctx *c, int64_t *Lptr, int32_t *Lrow, double *Lval,
     if (!c) return BILU_ERR_ARG;
     if (c->state < 2) return set_err(c, BILU_ERR_STATE, "no factor");
     BILU_CUDA(c, cudaSetDevice(c->device));
-    const int64_t nb1 = c->nb + 1, nd = c->h_Dptr.back();
+    const FactorView v = factor_view(c);  // after any merges
+    const int64_t nb1 = c->nb + 1, nd = v.nnz_d;
     auto cp = [&](void *dst, const void *src, int64_t bytes) -> cudaError_t {
         if (!dst || bytes <= 0) return cudaSuccess;
         return cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost);
     };
-    BILU_CUDA(c, cp(Lptr, c->d_Lptr, nb1 * sizeof(int64_t)));
-    BILU_CUDA(c, cp(Uptr, c->d_Uptr, nb1 * sizeof(int64_t)));
-    BILU_CUDA(c, cp(Lrow, c->d_Lrow, c->kept_rows * sizeof(int32_t)));
-    BILU_CUDA(c, cp(Ucol, c->d_Ucol, c->kept_cols * sizeof(int32_t)));
+    BILU_CUDA(c, cp(Lptr, v.Lptr, nb1 * sizeof(int64_t)));
+    BILU_CUDA(c, cp(Uptr, v.Uptr, nb1 * sizeof(int64_t)));
+    BILU_CUDA(c, cp(Lrow, v.Lrow, v.kept_rows * sizeof(int32_t)));
+    BILU_CUDA(c, cp(Ucol, v.Ucol, v.kept_cols * sizeof(int32_t)));
     if (c->p.precision == BILU_PREC_FP64) {
-        BILU_CUDA(c, cp(Lval, c->d_Lval, c->nnz_l * sizeof(double)));
-        BILU_CUDA(c, cp(Uval, c->d_Uval, c->nnz_u * sizeof(double)));
+        BILU_CUDA(c, cp(Lval, v.Lval, v.nnz_l * sizeof(double)));
+        BILU_CUDA(c, cp(Uval, v.Uval, v.nnz_u * sizeof(double)));
     } else {
         // reduced-precision storage: widen to FP64 on the host
         const bool f32 = c->p.precision == BILU_PREC_FP32;
@@ -378,11 +398,11 @@ bilu_status bilu_export(bilu_ctx *c, int64_t *Lptr, int32_t *Lrow, double *Lval,
             }
             return cudaSuccess;
         };
-        BILU_CUDA(c, widen(Lval, c->d_Lval, c->nnz_l));
-        BILU_CUDA(c, widen(Uval, c->d_Uval, c->nnz_u));
+        BILU_CUDA(c, widen(Lval, v.Lval, v.nnz_l));
+        BILU_CUDA(c, widen(Uval, v.Uval, v.nnz_u));
     }
-    BILU_CUDA(c, cp(Dinv, c->d_Dinv, nd * sizeof(double)));
-    BILU_CUDA(c, cp(Pblk, c->d_Pblk, nd * sizeof(double)));
+    BILU_CUDA(c, cp(Dinv, v.Dinv, nd * sizeof(double)));
+    BILU_CUDA(c, cp(Pblk, v.Pblk, nd * sizeof(double)));
     return BILU_OK;
 }
 

@@ -1918,6 +1918,7 @@ int recip_selftest(int n) {
 // ---------------------------------------------------------------- host side
 
 void factor_free(bilu_ctx *c) {
+    aggregate_free(c);
     dev_free(c->d_Lptr); dev_free(c->d_Lvptr); dev_free(c->d_Uptr); dev_free(c->d_Uvptr);
     dev_free(c->d_Lrow); dev_free(c->d_Ucol); dev_free(c->d_Lval); dev_free(c->d_Uval); dev_free(c->d_Uhval);
     dev_free(c->d_Dinv); dev_free(c->d_Pblk);

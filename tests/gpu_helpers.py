@@ -28,11 +28,13 @@ class GpuFactor:
 
     def L_block(self, K):
         vp = _vptr(self.Lptr, self.bstart)
-        return self.Lrow[self.Lptr[K]:self.Lptr[K + 1]], self.Lval[vp[K]:vp[K + 1]].reshape(-1, self._b(K))
+        rows = self.Lrow[self.Lptr[K]:self.Lptr[K + 1]]
+        return rows, self.Lval[vp[K]:vp[K + 1]].reshape(len(rows), self._b(K))
 
     def U_block(self, K):
         vp = _vptr(self.Uptr, self.bstart)
-        return self.Ucol[self.Uptr[K]:self.Uptr[K + 1]], self.Uval[vp[K]:vp[K + 1]].reshape(-1, self._b(K))
+        cols = self.Ucol[self.Uptr[K]:self.Uptr[K + 1]]
+        return cols, self.Uval[vp[K]:vp[K + 1]].reshape(len(cols), self._b(K))
 
     def _dblk(self, arr, K):
         d0 = int(np.sum(np.diff(self.bstart[:K + 1]).astype(np.int64) ** 2))
@@ -57,7 +59,7 @@ def gpu_factor(ctx, A, droptol, params=None, export=True, bstart=None) -> GpuFac
     st = B.bilu_factor(ctx, droptol)
     s = B.bilu_stats(ctx)
     bs = np.zeros(s.nblocks + 1, np.int32)
-    B.bilu_get_partition(ctx, bs)
+    B.bilu_get_factor_partition(ctx, bs)  # the analysis partition, or the merged one
     if not export:
         return GpuFactor(bs, *([None] * 8), s, st)
     nb = s.nblocks
