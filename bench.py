@@ -78,6 +78,8 @@ def parse():
                     help="tree (default): CTA groups factor independent subtrees of the block elimination tree "
                          "(pays off with --order nd), the trunk on the whole GPU; chain: one block after another")
     ap.add_argument("--group-ctas", type=int, default=0, help="tree schedule: CTAs per group (0: library default)")
+    ap.add_argument("--no-tensor", action="store_true",
+                    help="bf16: compute the update tiles on the FP32 units instead of the tensor cores")
     ap.add_argument("--aggregate", type=int, default=0,
                     help="progressive aggregation (Sec. 3.5): merge consecutive blocks up to this size (0: off)")
     ap.add_argument("--batch", type=int, default=0,
@@ -214,6 +216,9 @@ def config(args, w, extra=None):
          "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{args.gpus}"}
     if getattr(args, "aggregate", 0):
         c["aggregate_max"] = args.aggregate
+    if getattr(args, "precision", "fp64") == "bf16":
+        c["update_tiles"] = "FP32 units" if getattr(args, "no_tensor", False) else "tensor cores (tcgen05, BF16 x BF16 -> FP32)"
+
     pre = [k for k, on in (("mwm", getattr(args, "mwm", False)),
                            ("nd", getattr(args, "order", "natural") == "nd")) if on]
     if pre or blocking != "fixed":
@@ -486,6 +491,8 @@ def run_gpu(args):
     w = workload(args)
     stream = torch.cuda.Stream(device=dev)
     ctx = B.bilu_create(local, stream)
+    if args.no_tensor:
+        B.bilu_debug_set(ctx, B.BILU_DEBUG_NO_TENSOR, 1)
     params = B.bilu_params_default(blocking=B.BILU_BLOCKING_FIXED, fixed_block=args.block, max_block=64,
                                    precision={"fp64": B.BILU_PREC_FP64, "fp32": B.BILU_PREC_FP32,
                                               "bf16": B.BILU_PREC_BF16}[args.precision],
@@ -616,6 +623,16 @@ def run_gpu(args):
                   "traffic_note": "forward + backward sweep",
                   "bytes_per_launch": apply_bytes, "ms_per_launch": t_apply, "share_of_step": share_apply}
     dominant, other = (roof_factor, roof_apply) if share_factor >= share_apply else (roof_apply, roof_factor)
+    if args.precision == "bf16" and not args.no_tensor and args.skip == "none":
+        # the Schur updates of the candidate tiles run on the tensor cores: their algorithmic
+        # flops (the pivot-row tiles, on the FP32 units, are a small part) over the factor time,
+        # against the measured dense BF16 rate (a lower bound of the pipe's use while it runs)
+        upd = st.flop_upd_l + st.flop_upd_u
+        pk = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1700.0))
+        ach = upd / (t_factor * 1e-3) / 1e12
+        other = dict(other, tensor_updates={"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                                            "frac": ach / pk, "peak_source": "measured bf16 (sustained)",
+                                            "flops_per_launch": upd, "ms_per_launch": t_factor})
 
     # end to end through the public API from pinned host buffers
     e2e = None

@@ -64,7 +64,11 @@ typedef struct {
     int32_t perturb;     /* 1: perturb singular diagonal blocks (Sec. 3.6); 0: report singular */
     double pert_tau;     /* absolute perturbation tolerance tau (paper: 1e-2)                  */
     double pert_rho;     /* relative perturbation tolerance rho (paper: 1e-1)                  */
-    int32_t precision;   /* BILU_PREC_*: arithmetic of the Schur updates and panel scaling     */
+    int32_t precision;   /* BILU_PREC_*: arithmetic of the Schur updates and panel scaling.
+                            BILU_PREC_BF16: BF16 storage of L and U-breve; the Schur updates of
+                            the candidate rows run on the tensor cores (tcgen05 MMA, BF16
+                            operands, FP32 accumulation in tensor memory) unless a skip mode or
+                            sample recording is on                                              */
     int32_t skip;        /* BILU_SKIP_*: candidate-row skipping in the factorization.
                             BILU_SKIP_BOUND: after D_K is known, a candidate row i is skipped
                             when (||A(i,B_K)|| + sum_J ||L_J(i,:)|| ||U_J(:,B_K)||_F) ||D_K||_F
@@ -415,6 +419,9 @@ bilu_status bilu_analyze_partition(bilu_ctx *ctx, int64_t n, const int64_t *rowp
  *   BILU_DEBUG_BATCH_TRCAP (value >= 0): bilu_factor_batch's update tiles hold at most this
  *       many candidate rows (values below 4 count as 4, above 16 as 16) instead of the tuned
  *       cap; 0 restores tuning.  The factor does not change.
+ *   BILU_DEBUG_NO_TENSOR (value 0/1): BF16 factorizations compute their update tiles on the
+ *       FP32 units instead of the tensor cores (for comparison; the results agree within the
+ *       FP32 accumulation rounding).
  */
 enum {
     BILU_DEBUG_EXTRA_CTA = 1,
@@ -425,7 +432,8 @@ enum {
     BILU_DEBUG_POISON = 6,
     BILU_DEBUG_NO_TRUNK = 7,
     BILU_DEBUG_TRACE = 8,
-    BILU_DEBUG_BATCH_TRCAP = 9
+    BILU_DEBUG_BATCH_TRCAP = 9,
+    BILU_DEBUG_NO_TENSOR = 10
 };
 bilu_status bilu_debug_set(bilu_ctx *ctx, int32_t what, int64_t value);
 

@@ -24,7 +24,7 @@ BILU_SKIP_NONE, BILU_SKIP_BOUND, BILU_SKIP_LEARNED = 0, 1, 2
 BILU_SCHED_CHAIN, BILU_SCHED_TREE = 0, 1
 (BILU_DEBUG_EXTRA_CTA, BILU_DEBUG_SPIN_LIMIT, BILU_DEBUG_SELFTEST_RECIP, BILU_DEBUG_BATCH_GROUP,
  BILU_DEBUG_SMALL_POOLS, BILU_DEBUG_POISON, BILU_DEBUG_NO_TRUNK, BILU_DEBUG_TRACE,
- BILU_DEBUG_BATCH_TRCAP) = 1, 2, 3, 4, 5, 6, 7, 8, 9
+ BILU_DEBUG_BATCH_TRCAP, BILU_DEBUG_NO_TENSOR) = 1, 2, 3, 4, 5, 6, 7, 8, 9, 10
 BILU_MAX_BLOCK = 64
 
 # every extern "C" symbol that include/bilu.h declares

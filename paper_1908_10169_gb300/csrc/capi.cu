@@ -11,6 +11,7 @@ extern int g_debug_extra_cta;
 extern long long g_debug_spin_limit;
 extern long long g_debug_batch_group;
 extern long long g_debug_batch_trcap;
+extern int g_debug_tc_off;
 extern int g_debug_small_pools;
 extern int g_debug_poison;
 extern int g_debug_no_trunk;
@@ -412,6 +413,7 @@ bilu_status bilu_debug_set(bilu_ctx *c, int32_t what, int64_t value) {
         case BILU_DEBUG_EXTRA_CTA: g_debug_extra_cta = value ? 1 : 0; return BILU_OK;
         case BILU_DEBUG_SPIN_LIMIT: g_debug_spin_limit = value; return BILU_OK;
         case BILU_DEBUG_BATCH_GROUP: g_debug_batch_group = value > 0 ? value : 0; return BILU_OK;
+        case BILU_DEBUG_NO_TENSOR: g_debug_tc_off = value ? 1 : 0; return BILU_OK;
         case BILU_DEBUG_BATCH_TRCAP: g_debug_batch_trcap = value > 0 ? std::max<int64_t>(4, value) : 0; return BILU_OK;
         case BILU_DEBUG_SMALL_POOLS: g_debug_small_pools = value ? 1 : 0; return BILU_OK;
         case BILU_DEBUG_POISON: g_debug_poison = value ? 1 : 0; return BILU_OK;

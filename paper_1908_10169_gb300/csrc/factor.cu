@@ -107,6 +107,7 @@ struct FactorArgs {
     int64_t *timeline;           // test hook (tree schedule): per block 8 words: group, then the
                                  // clock at its start and after phases A, B+C, C2, (Bs,) D, E
     int32_t trcap;               // most candidate rows per accumulation tile (4..TRMAX)
+    int32_t tc;                  // 1: BF16 update tiles on the tensor cores (tcgen05, TMEM)
     int32_t skip_bound;          // 1: skip candidates that the norm bound proves dropped
     double *Lnrm, *Unrm;         // per kept row of L: ||l_i||; per kept column of U-breve: ||u_j||
     double *dcolsq;              // squared column norms of D_K (b entries)
@@ -518,6 +519,272 @@ __device__ __noinline__ void tile_features(const FactorArgs &a, int K, bool Lsid
         __syncthreads();
     }
     }
+
+// ---------------------------------------------------------------- tensor-core update tiles
+// BF16 storage: the Schur updates of a tile, T[r, c] = A_part[r, c] - sum_J X_J[r, :] Y_J[c, :]
+// (L side: X_J the tile's rows of L_J, Y_J the columns of U-breve_J inside B_K; U side: X_J
+// the tile's columns of U-breve_J, Y_J the rows of L_J inside B_K), run on the 5th-generation
+// tensor cores: per producer J (increasing J) the tile's X rows are placed at their tile slots
+// in a zero 128 x 64 BF16 operand and the Y rows at their B_K columns in a zero 64 x 64 one,
+// both in the no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core matrix), and
+// ceil(b_J / 16) MMAs of 128 x 64 x 16 accumulate X_J Y_J^T in FP32 in tensor memory (TMEM,
+// 128 lanes = tile rows, 64 columns).  The products of BF16 values are exact in FP32; the
+// accumulation is FP32.  One thread issues the MMAs; their completion arrives on an mbarrier
+// that the CTA waits on (bounded) before the operands are overwritten.
+constexpr int TC_ROWS = 128;             // tile rows (MMA M)
+constexpr int TC_COLS = BILU_MAX_BLOCK;  // B_K columns (MMA N) and TMEM columns allocated
+constexpr uint32_t TC_IDESC = (1u << 4)                    // accumulator FP32
+                            | (1u << 7) | (1u << 10)       // A and B BF16, both K-major
+                            | ((uint32_t)(TC_COLS >> 3) << 17) | ((uint32_t)(TC_ROWS >> 4) << 24);
+constexpr int TC_PF = (TC_ROWS * BILU_MAX_BLOCK + BILU_MAX_BLOCK * BILU_MAX_BLOCK + NT - 1) / NT;
+
+__shared__ uint32_t s_tc_tmem;   // TMEM address of the CTA's accumulator
+__shared__ __align__(8) uint64_t s_tc_bar;
+__shared__ uint32_t s_tc_phase;  // parity of the mbarrier phase the next commit completes
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: no swizzle, K-major; lbo = byte step between core matrices
+// along K, sbo = along M (N)
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+// element offset of (row, k) in the core-matrix layout of a rows x 64 K-major BF16 operand
+__device__ __forceinline__ int tc_off(int row, int k) {
+    return ((row >> 3) * (BILU_MAX_BLOCK / 8) + (k >> 3)) * 64 + (row & 7) * 8 + (k & 7);
+}
+
+template <class TS> __device__ __forceinline__ bool tc_on(const FactorArgs &a) { return false; }
+template <> __device__ __forceinline__ bool tc_on<__nv_bfloat16>(const FactorArgs &a) { return a.tc != 0; }
+
+// TMEM for the CTA's accumulator and the MMA mbarrier, at kernel start (all threads call)
+template <class TS>
+__device__ void tc_begin(bool on) {
+    if (!on) return;
+    if (threadIdx.x < 32)
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n\t"
+                     "tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;"
+                     ::"r"(smem_addr(&s_tc_tmem)), "r"((uint32_t)TC_COLS) : "memory");
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_tc_bar)) : "memory");
+        s_tc_phase = 0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// releases the TMEM at kernel end (all threads call, after their last tile)
+template <class TS>
+__device__ void tc_end(bool on) {
+    if (!on) return;
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x < 32)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_tc_tmem), "r"((uint32_t)TC_COLS)
+                     : "memory");
+}
+
+// waits (thread 0, bounded) for the MMAs of the last commit; the CTA then goes on together.
+// False on timeout (status set).
+__device__ __forceinline__ bool tc_wait(const FactorArgs &a, int K) {
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        const uint32_t par = s_tc_phase;
+        uint32_t done = 0;
+        for (long long it = 0; !done; ++it) {
+            asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                         "selp.u32 %0, 1, 0, p;\n\t}"
+                         : "=r"(done) : "r"(smem_addr(&s_tc_bar)), "r"(par) : "memory");
+            if (!done && it > a.spin_limit) break;
+        }
+        if (done) {
+            s_tc_phase = par ^ 1u;
+        } else if (atomicCAS(a.status, 0, DEV_TIMEOUT) == 0) {
+            a.info[INFO_TIMEOUT_SITE] = 9;
+            a.info[INFO_FAIL_BLOCK] = K;
+        }
+        s_ok = done ? 1 : 0;
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    return s_ok != 0;
+}
+
+__device__ void phase_B_tile_tc(const FactorArgs &a, int K, bool Lside, int sa, int cnt, char *smem) {
+    using TS = __nv_bfloat16;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int s0 = a.bstart[K], s1 = a.bstart[K + 1], b = s1 - s0;
+    // shared memory: the tile's A part, the two operands, the producer metadata
+    float *Ain = (float *)smem;                              // TC_ROWS x 64
+    TS *sA = (TS *)(Ain + TC_ROWS * BILU_MAX_BLOCK);         // TC_ROWS x 64, core-matrix layout
+    TS *sB = sA + TC_ROWS * BILU_MAX_BLOCK;                  // 64 x 64, core-matrix layout
+    int64_t *pxv = (int64_t *)(sB + BILU_MAX_BLOCK * BILU_MAX_BLOCK);
+    int64_t *pyv = pxv + PMAX;
+    int32_t *sxs = (int32_t *)(pyv + PMAX), *sxe = sxs + PMAX, *pbJ = sxe + PMAX, *pny = pbJ + PMAX;
+    int32_t *poff = pny + PMAX, *pyp = poff + PMAX, *pxc = pyp + PMAX;
+    int32_t *g = pxc + PMAX;                                 // TC_ROWS
+    int32_t *ws = g + TC_ROWS;                               // 33 (scan scratch)
+    if (cnt > TC_ROWS) {
+        if (tid == 0) set_status(a.status, DEV_INTERNAL, a.info, K);
+        return;
+    }
+    const int32_t *rows = Lside ? a.rowsL : a.rowsU;
+    const int pcnt = ldcg(a.kst + (Lside ? 2 : 3));
+    const int64_t *pinfo = Lside ? a.pinfoL : a.pinfoU;
+    for (int r = tid; r < cnt; r += NT) g[r] = ldcg(rows + sa + r);
+    for (int e = tid; e < TC_ROWS * BILU_MAX_BLOCK; e += NT) Ain[e] = 0.f;
+    for (int t = tid; t < pcnt; t += NT) {
+        const int64_t *pi = pinfo + PIS * t;
+        pbJ[t] = (int)ldcg(pi + PI_BJ);
+        pny[t] = (int)ldcg(pi + PI_YCNT);
+        poff[t] = (int)ldcg(pi + PI_OFF);
+        pyp[t] = (int)ldcg(pi + PI_YPOS);
+        pxc[t] = (int)ldcg(pi + PI_XCNT);
+        pxv[t] = ldcg(pi + PI_XVAL);
+        pyv[t] = ldcg(pi + PI_YVAL);
+    }
+    __syncthreads();
+    // A restricted to B_K: rows i (L side) or columns j (U side) of the tile
+    for (int r = warp; r < cnt; r += NW) {
+        const int idx = g[r];
+        if (Lside) {
+            for (int e = a.rowptr[idx] + lane; e < a.rowptr[idx + 1]; e += 32) {
+                const int c = a.colind[e];
+                if (c >= s0 && c < s1) Ain[r * BILU_MAX_BLOCK + (c - s0)] = (float)a.val[e];
+            }
+        } else {
+            for (int e = a.colptr[idx] + lane; e < a.colptr[idx + 1]; e += 32) {
+                const int rr = a.rowind[e];
+                if (rr >= s0 && rr < s1) Ain[r * BILU_MAX_BLOCK + (rr - s0)] = (float)a.cval[e];
+            }
+        }
+    }
+    const int32_t *xslot = Lside ? a.xslotL : a.xslotU;
+    for (int t = warp; t < pcnt; t += NW) {
+        const int xs = warp_lower_bound(xslot + poff[t], 0, pxc[t], sa);
+        const int xe = warp_lower_bound(xslot + poff[t], xs, pxc[t], sa + cnt);
+        if (lane == 0) { sxs[t] = xs; sxe[t] = xe; }
+    }
+    __syncthreads();
+    // the producers with entries in this tile, increasing
+    int32_t *tl = pxc;
+    int ntl = 0;
+    for (int c0 = 0; c0 < pcnt; c0 += NT) {
+        const int t = c0 + tid;
+        const int hit = (t < pcnt && sxe[t] > sxs[t] && pny[t] > 0) ? 1 : 0;
+        int tot;
+        const int ex = block_excl_scan(hit, ws, &tot);
+        if (hit) tl[ntl + ex] = t;
+        ntl += tot;
+    }
+    __syncthreads();
+    const TS *Xpool = (const TS *)(Lside ? a.Lval : a.Uval);
+    const TS *Ypool = (const TS *)(Lside ? a.Uval : a.Lval);
+    const int32_t *Yidx = Lside ? a.Ucol : a.Lrow;
+    long long flops = 0;
+    bool ok = true;
+    for (int i = 0; i < ntl && ok; ++i) {
+        const int t = tl[i];
+        const int nx = sxe[t] - sxs[t], ny = pny[t], bJ = pbJ[t];
+        if (nx > cnt || ny > b || bJ > BILU_MAX_BLOCK) {
+            if (tid == 0) set_status(a.status, DEV_INTERNAL, a.info, K);
+            ok = false;
+            break;
+        }
+        flops += 2LL * nx * ny * bJ;
+        // this producer's values into registers (they load while the previous MMAs run)
+        const int nxv = nx * bJ, tot = nxv + ny * bJ;
+        const int64_t xval = pxv[t] + (int64_t)sxs[t] * bJ, yval = pyv[t];
+        TS v[TC_PF];
+#pragma unroll
+        for (int k = 0; k < TC_PF; ++k) {
+            const int e = tid + k * NT;
+            v[k] = e < nxv ? Xpool[xval + e] : (e < tot ? Ypool[yval + (e - nxv)] : __float2bfloat16(0.f));
+        }
+        int xr = -1, yr = -1;
+        if (tid < nx) xr = ldcg(xslot + poff[t] + sxs[t] + tid) - sa;
+        if (tid >= TC_ROWS && tid - TC_ROWS < ny) yr = ldcg(Yidx + pyp[t] + (tid - TC_ROWS)) - s0;
+        if (i > 0 && !tc_wait(a, K)) { ok = false; break; }
+        // zero both operands (K padding and absent rows stay zero), then place the values
+        {
+            uint4 *z = (uint4 *)sA;
+            const int nz = (TC_ROWS + BILU_MAX_BLOCK) * BILU_MAX_BLOCK * (int)sizeof(TS) / 16;
+            for (int e = tid; e < nz; e += NT) z[e] = make_uint4(0, 0, 0, 0);
+        }
+        __shared__ int32_t s_xrow[TC_ROWS], s_ycol[BILU_MAX_BLOCK];  // tile slot / B_K column
+        if (tid < nx) s_xrow[tid] = (xr >= 0 && xr < cnt) ? xr : -1;
+        if (tid >= TC_ROWS && tid - TC_ROWS < ny) s_ycol[tid - TC_ROWS] = (yr >= 0 && yr < b) ? yr : -1;
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < TC_PF; ++k) {
+            const int e = tid + k * NT;
+            if (e < nxv) {
+                const int x = e / bJ, kk = e - x * bJ, r = s_xrow[x];
+                if (r >= 0) sA[tc_off(r, kk)] = v[k];
+            } else if (e < tot) {
+                const int ee = e - nxv, y = ee / bJ, kk = ee - y * bJ, c = s_ycol[y];
+                if (c >= 0) sB[tc_off(c, kk)] = v[k];
+            }
+        }
+        if (tid < nx && !(xr >= 0 && xr < cnt)) set_status(a.status, DEV_INTERNAL, a.info, K);
+        if (tid >= TC_ROWS && tid - TC_ROWS < ny && !(yr >= 0 && yr < b)) set_status(a.status, DEV_INTERNAL, a.info, K);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = smem_addr(sA), b0 = smem_addr(sB);
+            const int ks = (bJ + 15) >> 4;
+            for (int s = 0; s < ks; ++s) {
+                const uint64_t da = tc_desc(a0 + s * 256, 128, (BILU_MAX_BLOCK / 8) * 128);
+                const uint64_t db = tc_desc(b0 + s * 256, 128, (BILU_MAX_BLOCK / 8) * 128);
+                const uint32_t accum = (i > 0 || s > 0) ? 1u : 0u;
+                asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                             ::"r"(s_tc_tmem), "l"(da), "l"(db), "r"(TC_IDESC), "r"(accum) : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         ::"r"(smem_addr(&s_tc_bar)) : "memory");
+        }
+    }
+    if (ok && ntl > 0 && !tc_wait(a, K)) ok = false;
+    if (ok) {
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (tile rows), columns 16 (w / 4) ..
+        float *out = (float *)(Lside ? a.TL : a.TU) + (int64_t)sa * b;
+        const int r = (warp & 3) * 32 + lane, c0 = (warp >> 2) * 16;
+        uint32_t d[16];
+        if (ntl > 0) {
+            const uint32_t taddr = s_tc_tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0;
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                         : "=r"(d[0]), "=r"(d[1]), "=r"(d[2]), "=r"(d[3]), "=r"(d[4]), "=r"(d[5]), "=r"(d[6]),
+                           "=r"(d[7]), "=r"(d[8]), "=r"(d[9]), "=r"(d[10]), "=r"(d[11]), "=r"(d[12]), "=r"(d[13]),
+                           "=r"(d[14]), "=r"(d[15])
+                         : "r"(taddr) : "memory");
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) d[j] = 0u;
+        }
+        if (r < cnt) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int c = c0 + j;
+                if (c < b) out[(int64_t)r * b + c] = Ain[r * BILU_MAX_BLOCK + c] - __uint_as_float(d[j]);
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    }
+    __syncthreads();
+    // the products computed (the algorithmic count, as the FFMA tiles count it)
+    {
+        long long f = tid == 0 ? flops : 0;
+        if (tid == 0 && f) atomicAdd((unsigned long long *)(a.info + (Lside ? INFO_FLOP_UPD_L : INFO_FLOP_UPD_U)),
+                                     (unsigned long long)f);
+    }
+}
 
 template <class TS>
 __device__ void phase_B_tile(const FactorArgs &a, int K, bool Lside, int sa, int cnt, char *smem, bool bound,
@@ -1505,8 +1772,9 @@ __device__ bool block_step(const FactorArgs &a, int K, char *smem, StepTimers &t
     {
         const int W = a.G > 1 ? a.G - 1 : 1;  // CTAs taking tiles (CTA 0 factors the pivot block)
         const int np = pivot_parts(W, npt);    // producer slices per pivot-row tile
+        const bool tc = tc_on<TS>(a);          // update tiles on the tensor cores (up to 128 rows)
         int TR = (nrest + W - 1) / W;
-        TR = max(4, min(a.trcap, TR));
+        TR = max(4, min(tc ? TC_ROWS : a.trcap, TR));
         const int nLt = (nrestL + TR - 1) / TR, nUt = (mU + TR - 1) / TR;
         const int ntiles = npt * np + (a.skip_bound ? 0 : nLt + nUt);
         if (a.G == 1 || cr > 0) {
@@ -1522,7 +1790,8 @@ __device__ bool block_step(const FactorArgs &a, int K, char *smem, StepTimers &t
                     const bool Ls = r < nLt;
                     const int sa = Ls ? b + r * TR : (r - nLt) * TR;
                     const int cnt = Ls ? min(TR, mL - sa) : min(TR, mU - sa);
-                    phase_B_tile<TS>(a, K, Ls, sa, cnt, smem, false, a.learned || a.record);
+                    if (tc) phase_B_tile_tc(a, K, Ls, sa, cnt, smem);
+                    else phase_B_tile<TS>(a, K, Ls, sa, cnt, smem, false, a.learned || a.record);
                     __syncthreads();
                 }
             }
@@ -1612,14 +1881,17 @@ __device__ void factor_chain(const FactorArgs &a, char *smem) {
 template <class TS>
 __global__ void __launch_bounds__(NT, 1) bilu_factor_kernel(FactorArgs a) {
     extern __shared__ __align__(16) char smem[];
+    const bool tc = tc_on<TS>(a);
+    tc_begin<TS>(tc);
     factor_chain<TS>(a, smem);
+    tc_end<TS>(tc);
 }
 
 // Batch of independent matrices in one launch: the grid is cut into groups of G CTAs, each
 // group takes the next matrix from a work queue (sorted largest first by the host), runs its
 // block chain with the group's own barrier, and repeats until the queue is empty.
 template <class TS>
-__global__ void __launch_bounds__(NT, 1) bilu_factor_batch_kernel(const FactorArgs *all, int nmat, int *queue,
+__device__ void factor_batch_body(const FactorArgs *all, int nmat, int *queue,
                                                                   uint32_t *gbar, uint32_t *gpiv, int32_t *gslot,
                                                                   int32_t *gstat, int64_t *ginfo, int G,
                                                                   long long spin) {
@@ -1664,6 +1936,17 @@ __global__ void __launch_bounds__(NT, 1) bilu_factor_batch_kernel(const FactorAr
     }
 }
 
+template <class TS>
+__global__ void __launch_bounds__(NT, 1) bilu_factor_batch_kernel(const FactorArgs *all, int nmat, int *queue,
+                                                                  uint32_t *gbar, uint32_t *gpiv, int32_t *gslot,
+                                                                  int32_t *gstat, int64_t *ginfo, int G,
+                                                                  long long spin) {
+    const bool tc = tc_on<TS>(all[0]);
+    tc_begin<TS>(tc);
+    factor_batch_body<TS>(all, nmat, queue, gbar, gpiv, gslot, gstat, ginfo, G, spin);
+    tc_end<TS>(tc);
+}
+
 // ---------------------------------------------------------------- tree schedule
 // Every block J that updates block K is a descendant of K in the block elimination tree
 // (Sec. 3.3 reorders so that this tree has independent subtrees), so K can be factored as soon
@@ -1689,7 +1972,7 @@ __device__ __forceinline__ int32_t atom_add_acqrel_s32(int32_t *p, int32_t v) {
 }
 
 template <class TS>
-__global__ void __launch_bounds__(NT, 1) bilu_factor_tree_kernel(const FactorArgs *gargs, TreeArgs t) {
+__device__ void factor_tree_body(const FactorArgs *gargs, TreeArgs t) {
     extern __shared__ __align__(16) char smem[];
     __shared__ FactorArgs s_a;
     __shared__ int s_K;
@@ -1796,6 +2079,14 @@ __global__ void __launch_bounds__(NT, 1) bilu_factor_tree_kernel(const FactorArg
             }
         }
     }
+}
+
+template <class TS>
+__global__ void __launch_bounds__(NT, 1) bilu_factor_tree_kernel(const FactorArgs *gargs, TreeArgs t) {
+    const bool tc = tc_on<TS>(gargs[0]);
+    tc_begin<TS>(tc);
+    factor_tree_body<TS>(gargs, t);
+    tc_end<TS>(tc);
 }
 
 // Closing copy of the tree schedule, part 1 (one CTA): block-ordered offsets of the kept rows
@@ -1978,6 +2269,7 @@ int g_debug_extra_cta = 0;          // the barrier waits for a CTA that never ar
 long long g_debug_spin_limit = 0;   // polls before a bounded wait gives up (0: default)
 long long g_debug_batch_group = 0;  // batch group size (0: tuned)
 long long g_debug_batch_trcap = 0;  // batch tile row cap (0: tuned)
+int g_debug_tc_off = 0;             // BF16 update tiles on the FP32 units instead of the tensor cores
 int g_debug_small_pools = 0;        // factorizations start from minimal pools and producer lists
 int g_debug_poison = 0;             // factor storage is filled with NaN before every run
 int g_debug_no_trunk = 0;           // the tree schedule leaves no trunk to the whole grid
@@ -2122,6 +2414,9 @@ FactorArgs make_args(bilu_ctx *c, double droptol, int G) {
     a.mlp_w = (const __half *)c->d_mlp_w;
     a.record = rec ? 1 : 0;
     a.rec_thresh = c->rec_thresh;
+    // the plain BF16 updates run on the tensor cores (the skip modes and recording keep their
+    // per-row tiles on the FP32 units)
+    a.tc = c->p.precision == BILU_PREC_BF16 && !a.skip_bound && !a.learned && !rec && !g_debug_tc_off ? 1 : 0;
     a.rec_seed = c->rec_seed;
     a.rec_cap = c->rec_cap;
     a.featL = c->d_featL;

@@ -1,0 +1,89 @@
+"""The BF16 update tiles on the tensor cores (tcgen05 MMA, BF16 operands, FP32 accumulation
+in tensor memory) against the same factorization with the update tiles on the FP32 units.
+
+Both sum the same exact BF16 products in FP32, in different orders, so the stored BF16 values
+differ by at most a few units in their last place, and a drop decision may flip only for a
+candidate whose norm lies within that rounding of tau.  The step parity of the BF16 factor
+against the FP64 oracle (tests/test_gpu_mixed.py) runs on the tensor path as well."""
+import numpy as np
+import pytest
+
+import paper_1908_10169_gb300 as B
+from paper_1908_10169_gb300 import workloads as W
+from tests.gpu_helpers import _vptr, gpu_factor
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = B.bilu_create(0)
+    yield c
+    B.bilu_destroy(c)
+
+
+def _factor(ctx, w, tensor, sched=B.BILU_SCHED_CHAIN, bs=None):
+    B.bilu_debug_set(ctx, B.BILU_DEBUG_NO_TENSOR, 0 if tensor else 1)
+    try:
+        p = B.bilu_params_default(fixed_block=w.fixed_block, max_block=64, precision=B.BILU_PREC_BF16, schedule=sched)
+        return gpu_factor(ctx, w.A, w.droptol, p, bstart=bs)
+    finally:
+        B.bilu_debug_set(ctx, B.BILU_DEBUG_NO_TENSOR, 0)
+
+
+def _iters(ctx, w):
+    import torch
+    b = torch.from_numpy(w.b).cuda()
+    x = torch.zeros_like(b)
+    info = B.gmres_solve(ctx, b, x, 1e-8, 30, 10000)
+    assert info.relres_true <= 1e-8
+    return info.iters
+
+
+@pytest.mark.parametrize("case", ["cd3d16", "elasticity6"])
+def test_tensor_tiles_agree_with_fp32_unit_tiles(ctx, case):
+    w = W.cd3d(side=16, seed=1, block=32) if case == "cd3d16" else W.elasticity3d(side=6, seed=2, block=24)
+    gt = _factor(ctx, w, True)
+    it_t = _iters(ctx, w)
+    gf = _factor(ctx, w, False)
+    it_f = _iters(ctx, w)
+    # the same algorithmic work
+    assert gt.stats.flop_upd_l == gf.stats.flop_upd_l and gt.stats.flop_upd_u == gf.stats.flop_upd_u
+    nb = len(gt.bstart) - 1
+    differ, worst = 0, 0.0
+    for K in range(nb):
+        b = int(gt.bstart[K + 1] - gt.bstart[K])
+        same = (np.array_equal(gt.Lrow[gt.Lptr[K]:gt.Lptr[K + 1]], gf.Lrow[gf.Lptr[K]:gf.Lptr[K + 1]]) and
+                np.array_equal(gt.Ucol[gt.Uptr[K]:gt.Uptr[K + 1]], gf.Ucol[gf.Uptr[K]:gf.Uptr[K + 1]]))
+        if not same:
+            differ += 1
+            break  # the later blocks follow different patterns
+        for (pa, pb, va, vb, vp) in ((gt.Lptr, gf.Lptr, gt.Lval, gf.Lval, _vptr(gt.Lptr, gt.bstart)),
+                                     (gt.Uptr, gf.Uptr, gt.Uval, gf.Uval, _vptr(gt.Uptr, gt.bstart))):
+            a, c = va[vp[K]:vp[K + 1]], vb[vp[K]:vp[K + 1]]
+            if a.size:
+                a2, c2 = a.reshape(-1, b), c.reshape(-1, b)
+                worst = max(worst, float((np.abs(a2 - c2).max(axis=1) / np.abs(c2).max(axis=1)).max()))
+    print(f"{case}: kept sets of all {nb} blocks equal: {differ == 0}; worst row difference {worst:.2e}; "
+          f"GMRES {it_t} (tensor) / {it_f} (FP32 units)")
+    # BF16 stores 8 significant bits: rows agree to a few units of 2^-8 relative to the row
+    assert worst <= 4 * 2.0 ** -8
+    assert abs(it_t - it_f) <= max(1, it_f // 10)
+
+
+def test_tensor_tiles_same_factor_on_every_schedule(ctx):
+    """The tile a row falls in does not change its MMA sums (the contraction of one output runs
+    over its own k only), so the chain and tree schedules give the same BF16 factor bit for bit."""
+    w = W.cd3d(side=16, seed=1, block=32)
+    n = w.A.n
+    perm, bnd, _ = B.bilu_nd_order(n, w.A.rowptr, w.A.colind, np.append(np.arange(0, n, 32), n).astype(np.int32))
+    A2 = W.CSR(n, *B.bilu_permute_csr(n, w.A.rowptr, w.A.colind, w.A.val, perm))
+    import dataclasses
+    w2 = dataclasses.replace(w, A=A2)
+    gc = _factor(ctx, w2, True, B.BILU_SCHED_CHAIN, bnd)
+    gt = _factor(ctx, w2, True, B.BILU_SCHED_TREE, bnd)
+    for k in ("Lptr", "Lrow", "Lval", "Uptr", "Ucol", "Uval", "Dinv", "Pblk"):
+        assert np.array_equal(getattr(gc, k), getattr(gt, k)), k
