@@ -613,7 +613,11 @@ __device__ __forceinline__ bool tc_wait(const FactorArgs &a, int K) {
     return s_ok != 0;
 }
 
-__device__ void phase_B_tile_tc(const FactorArgs &a, int K, bool Lside, int sa, int cnt, char *smem) {
+// part >= 0: the pivot rows [0, b) of the L side over one of nparts slices of the producer list
+// (A's values only in part 0), written to the part's pivot accumulator, which the LU sums in
+// part order -- as the FP32-unit pivot-row tiles do, with all rows in one tile.
+__device__ void phase_B_tile_tc(const FactorArgs &a, int K, bool Lside, int sa, int cnt, char *smem, int part = -1,
+                                int nparts = 1) {
     using TS = __nv_bfloat16;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int s0 = a.bstart[K], s1 = a.bstart[K + 1], b = s1 - s0;
@@ -648,7 +652,7 @@ __device__ void phase_B_tile_tc(const FactorArgs &a, int K, bool Lside, int sa, 
     }
     __syncthreads();
     // A restricted to B_K: rows i (L side) or columns j (U side) of the tile
-    for (int r = warp; r < cnt; r += NW) {
+    for (int r = warp; r < (part > 0 ? 0 : cnt); r += NW) {
         const int idx = g[r];
         if (Lside) {
             for (int e = a.rowptr[idx] + lane; e < a.rowptr[idx + 1]; e += 32) {
@@ -669,12 +673,14 @@ __device__ void phase_B_tile_tc(const FactorArgs &a, int K, bool Lside, int sa, 
         if (lane == 0) { sxs[t] = xs; sxe[t] = xe; }
     }
     __syncthreads();
-    // the producers with entries in this tile, increasing
+    // the producers with entries in this tile (of the part's slice), increasing
     int32_t *tl = pxc;
     int ntl = 0;
-    for (int c0 = 0; c0 < pcnt; c0 += NT) {
+    const int tbeg = part >= 0 ? pcnt * part / nparts : 0;
+    const int tend = part >= 0 ? pcnt * (part + 1) / nparts : pcnt;
+    for (int c0 = tbeg; c0 < tend; c0 += NT) {
         const int t = c0 + tid;
-        const int hit = (t < pcnt && sxe[t] > sxs[t] && pny[t] > 0) ? 1 : 0;
+        const int hit = (t < tend && sxe[t] > sxs[t] && pny[t] > 0) ? 1 : 0;
         int tot;
         const int ex = block_excl_scan(hit, ws, &tot);
         if (hit) tl[ntl + ex] = t;
@@ -753,7 +759,8 @@ __device__ void phase_B_tile_tc(const FactorArgs &a, int K, bool Lside, int sa, 
     if (ok && ntl > 0 && !tc_wait(a, K)) ok = false;
     if (ok) {
         // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (tile rows), columns 16 (w / 4) ..
-        float *out = (float *)(Lside ? a.TL : a.TU) + (int64_t)sa * b;
+        float *out = part >= 0 ? (float *)a.TLP + (int64_t)part * BILU_MAX_BLOCK * BILU_MAX_BLOCK + (int64_t)sa * b
+                               : (float *)(Lside ? a.TL : a.TU) + (int64_t)sa * b;
         const int r = (warp & 3) * 32 + lane, c0 = (warp >> 2) * 16;
         uint32_t d[16];
         if (ntl > 0) {
@@ -1776,17 +1783,23 @@ __device__ bool block_step(const FactorArgs &a, int K, char *smem, StepTimers &t
         int TR = (nrest + W - 1) / W;
         TR = max(4, min(tc ? TC_ROWS : a.trcap, TR));
         const int nLt = (nrestL + TR - 1) / TR, nUt = (mU + TR - 1) / TR;
-        const int ntiles = npt * np + (a.skip_bound ? 0 : nLt + nUt);
+        // pivot-row tiles: TRP rows per producer slice, or on the tensor cores all b rows per slice
+        const int npiv = tc ? np : npt * np;
+        const int ntiles = npiv + (a.skip_bound ? 0 : nLt + nUt);
         if (a.G == 1 || cr > 0) {
             const int wid = a.G > 1 ? cr - 1 : 0;
             for (int it = wid; it < ntiles; it += W) {
-                if (it < npt * np) {
-                    const int sa = (it / np) * TRP;
-                    phase_B_tile<TS>(a, K, true, sa, min(TRP, b - sa), smem, false, false, it % np, np);
+                if (it < npiv) {
+                    if (tc) {
+                        phase_B_tile_tc(a, K, true, 0, b, smem, it, np);
+                    } else {
+                        const int sa = (it / np) * TRP;
+                        phase_B_tile<TS>(a, K, true, sa, min(TRP, b - sa), smem, false, false, it % np, np);
+                    }
                     __syncthreads();
                     if (threadIdx.x == 0) red_add_release(a.pivdone, 1u);
                 } else {
-                    const int r = it - npt * np;
+                    const int r = it - npiv;
                     const bool Ls = r < nLt;
                     const int sa = Ls ? b + r * TR : (r - nLt) * TR;
                     const int cnt = Ls ? min(TR, mL - sa) : min(TR, mU - sa);
@@ -1804,7 +1817,8 @@ __device__ bool block_step(const FactorArgs &a, int K, char *smem, StepTimers &t
                 int go = 1;
                 if (a.G > 1) {
                     long long itn = 0;
-                    while (ld_acquire_u32(a.pivdone) < (uint32_t)(npt * pivot_parts(a.G - 1, npt))) {
+                    while (ld_acquire_u32(a.pivdone) < (uint32_t)(tc_on<TS>(a) ? pivot_parts(a.G - 1, npt)
+                                                                               : npt * pivot_parts(a.G - 1, npt))) {
                         if (a.trace && (itn & 1023) == 0) a.trace[8 * blockIdx.x + 6] = (int32_t)(itn >> 10);
                         if (++itn > a.spin_limit) {
                             if (atomicCAS(a.status, 0, DEV_TIMEOUT) == 0) a.info[INFO_TIMEOUT_SITE] = 7;
