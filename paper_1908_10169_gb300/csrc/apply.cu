@@ -35,6 +35,22 @@ struct ApplyArgs {
     const int32_t *skip;   // optional: nonzero -> return immediately
 };
 
+// Arithmetic of the sweeps: FP64 for an FP64 factor; FP32 for the reduced-precision factors,
+// whose stored values carry 8 (BF16) or 24 (FP32) significant bits, so FP32 products and sums
+// (relative error ~2^-24 per operation) add nothing that the factor's own rounding does not
+// already dominate.  The vectors r, y, z stay FP64 in memory; GMRES is FP64 throughout.
+template <class TS> struct SweepT { using T = float; };
+template <> struct SweepT<double> { using T = double; };
+__device__ __forceinline__ float cval(float v) { return v; }
+__device__ __forceinline__ float cval(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ double cval(double v) { return v; }
+__device__ __forceinline__ float warp_sum_t(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_sum_t(double v) { return warp_sum(v); }
+
 // The factor values a block will read, fetched into L2 while it waits for its dependencies
 // (warp-cooperative, one 128-byte line per lane and step).
 __device__ __forceinline__ void warp_prefetch_l2(const void *p, int64_t bytes) {
@@ -75,9 +91,10 @@ constexpr int FCH = 32;  // producers per chunk
 
 template <class TS>
 __global__ void __launch_bounds__(AT) apply_forward_kernel(ApplyArgs a) {
+    using TC = typename SweepT<TS>::T;
     if (a.skip && ldcg(a.skip)) return;
-    __shared__ double acc[BILU_MAX_BLOCK];
-    __shared__ double dmat[FCH][BILU_MAX_BLOCK];
+    __shared__ TC acc[BILU_MAX_BLOCK];
+    __shared__ TC dmat[FCH][BILU_MAX_BLOCK];
     __shared__ int sps[FCH], soff[FCH + 1], sbJ[FCH], ssJ[FCH], sJ[FCH], sst[FCH], scnt[FCH];
     __shared__ int srl[FCH], sro[FCH + 1];  // producers computed this round and their row offsets
     __shared__ int64_t sLv[FCH];
@@ -91,7 +108,7 @@ __global__ void __launch_bounds__(AT) apply_forward_kernel(ApplyArgs a) {
         __syncthreads();
         if (K >= a.nb) return;
         const int s0 = a.bstart[K], b = a.bstart[K + 1] - s0;
-        if (tid < b) acc[tid] = a.r[s0 + tid];
+        if (tid < b) acc[tid] = (TC)a.r[s0 + tid];
         const int pc = ldcg(a.prodUcnt + K);
         for (int c0 = 0; c0 < pc; c0 += FCH) {
             const int cn = min(FCH, pc - c0);
@@ -109,7 +126,7 @@ __global__ void __launch_bounds__(AT) apply_forward_kernel(ApplyArgs a) {
                 sst[tid] = 0;  // 0 running, 1 to compute this round, 2 computed
             }
             if (tid == 0) s_fold = 0;
-            for (int e = tid; e < cn * BILU_MAX_BLOCK; e += AT) (&dmat[0][0])[e] = 0.0;
+            for (int e = tid; e < cn * BILU_MAX_BLOCK; e += AT) (&dmat[0][0])[e] = TC(0);
             __syncthreads();
             if (tid == 0) {
                 soff[0] = 0;
@@ -163,7 +180,7 @@ __global__ void __launch_bounds__(AT) apply_forward_kernel(ApplyArgs a) {
                 if (!s_ok) return;
                 // fold the leading run of computed producers into acc, in producer order
                 if (tid < b) {
-                    double v = acc[tid];
+                    TC v = acc[tid];
                     int t = s_fold;
                     while (t < cn && sst[t] == 2) v -= dmat[t++][tid];
                     acc[tid] = v;
@@ -173,12 +190,12 @@ __global__ void __launch_bounds__(AT) apply_forward_kernel(ApplyArgs a) {
                 // loads in flight together; row -> producer by binary search over the offsets
                 const int nrd = s_nrd, nrr = sro[nrd];
                 for (int it0 = warp * 4; it0 < nrr; it0 += AW * 4) {
-                    double v[4];
+                    TC v[4];
                     int tt[4], pp[4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         const int it = it0 + u;
-                        v[u] = 0.0;
+                        v[u] = TC(0);
                         tt[u] = -1;
                         if (it < nrr) {
                             int lo = 0, hi = nrd - 1;  // largest k with sro[k] <= it
@@ -190,15 +207,15 @@ __global__ void __launch_bounds__(AT) apply_forward_kernel(ApplyArgs a) {
                             const int bJ = sbJ[t];
                             const TS *row = (const TS *)a.Lval + sLv[t] + (int64_t)ir * bJ;
                             const double *yJ = a.z + ssJ[t];
-                            if (lane < bJ) v[u] = dval(row[lane]) * ldcg(yJ + lane);
-                            if (lane + 32 < bJ) v[u] = fma(dval(row[lane + 32]), ldcg(yJ + lane + 32), v[u]);
+                            if (lane < bJ) v[u] = cval(row[lane]) * (TC)ldcg(yJ + lane);
+                            if (lane + 32 < bJ) v[u] = fma(cval(row[lane + 32]), (TC)ldcg(yJ + lane + 32), v[u]);
                             tt[u] = t;
                             pp[u] = sps[t] + ir;
                         }
                     }
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        const double w = warp_sum(v[u]);
+                        const TC w = warp_sum_t(v[u]);
                         if (lane == 0 && tt[u] >= 0) dmat[tt[u]][a.Lrow[pp[u]] - s0] = w;
                     }
                 }
@@ -212,7 +229,7 @@ __global__ void __launch_bounds__(AT) apply_forward_kernel(ApplyArgs a) {
             }
             __syncthreads();
         }
-        if (tid < b) a.z[s0 + tid] = acc[tid];
+        if (tid < b) a.z[s0 + tid] = (double)acc[tid];
         __syncthreads();
         if (tid == 0) {
             __threadfence();
@@ -228,26 +245,27 @@ __global__ void __launch_bounds__(AT) apply_forward_kernel(ApplyArgs a) {
 // running; its own columns (the leading range, the columns are sorted) follow once it is done.
 // The partial sums are formed in a fixed order, so the result does not depend on timing.
 template <class TS>
-__device__ __forceinline__ double backward_columns(const ApplyArgs &a, int K, int b, int64_t q0, int64_t qa,
-                                                   int64_t qb, int g, int rr) {
+__device__ __forceinline__ typename SweepT<TS>::T backward_columns(const ApplyArgs &a, int K, int b, int64_t q0,
+                                                                    int64_t qa, int64_t qb, int g, int rr) {
+    using TC = typename SweepT<TS>::T;
     constexpr int NG = AT / BILU_MAX_BLOCK;  // column groups
-    double s = 0.0;
+    TC s = TC(0);
     if (rr < b) {
         const TS *Uv = (const TS *)a.Uhval + a.Uvptr[K];
         int64_t q = qa + g;
         // four independent columns per iteration keep several loads in flight
-        double s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        TC s1 = TC(0), s2 = TC(0), s3 = TC(0);
         for (; q + 3 * NG < qb; q += 4 * NG) {
-            const double u0 = dval(Uv[(q - q0) * b + rr]), u1 = dval(Uv[(q + NG - q0) * b + rr]);
-            const double u2 = dval(Uv[(q + 2 * NG - q0) * b + rr]), u3 = dval(Uv[(q + 3 * NG - q0) * b + rr]);
-            const double z0 = ldcg(a.z + a.Ucol[q]), z1 = ldcg(a.z + a.Ucol[q + NG]);
-            const double z2 = ldcg(a.z + a.Ucol[q + 2 * NG]), z3 = ldcg(a.z + a.Ucol[q + 3 * NG]);
+            const TC u0 = cval(Uv[(q - q0) * b + rr]), u1 = cval(Uv[(q + NG - q0) * b + rr]);
+            const TC u2 = cval(Uv[(q + 2 * NG - q0) * b + rr]), u3 = cval(Uv[(q + 3 * NG - q0) * b + rr]);
+            const TC z0 = (TC)ldcg(a.z + a.Ucol[q]), z1 = (TC)ldcg(a.z + a.Ucol[q + NG]);
+            const TC z2 = (TC)ldcg(a.z + a.Ucol[q + 2 * NG]), z3 = (TC)ldcg(a.z + a.Ucol[q + 3 * NG]);
             s = fma(u0, z0, s);
             s1 = fma(u1, z1, s1);
             s2 = fma(u2, z2, s2);
             s3 = fma(u3, z3, s3);
         }
-        for (; q < qb; q += NG) s = fma(dval(Uv[(q - q0) * b + rr]), ldcg(a.z + a.Ucol[q]), s);
+        for (; q < qb; q += NG) s = fma(cval(Uv[(q - q0) * b + rr]), (TC)ldcg(a.z + a.Ucol[q]), s);
         s = (s + s1) + (s2 + s3);
     }
     return s;
@@ -277,10 +295,11 @@ constexpr int RMAX = 512;  // column runs (distinct later blocks) per block held
 
 template <class TS>
 __global__ void __launch_bounds__(AT) apply_backward_kernel(ApplyArgs a) {
+    using TC = typename SweepT<TS>::T;
     if (a.skip && ldcg(a.skip)) return;
     constexpr int NG = AT / BILU_MAX_BLOCK;  // column groups
-    __shared__ double part[NG][BILU_MAX_BLOCK];
-    __shared__ double tv[BILU_MAX_BLOCK], yv[BILU_MAX_BLOCK];
+    __shared__ TC part[NG][BILU_MAX_BLOCK];
+    __shared__ TC tv[BILU_MAX_BLOCK], yv[BILU_MAX_BLOCK];
     __shared__ int32_t rq[RMAX + 1], rblk[RMAX];
     __shared__ int s_K, s_ok, s_nr, s_take;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -294,28 +313,28 @@ __global__ void __launch_bounds__(AT) apply_backward_kernel(ApplyArgs a) {
         const int s0 = a.bstart[K], b = a.bstart[K + 1] - s0;
         const int64_t q0 = a.Uptr[K], q1 = a.Uptr[K + 1];
         const int g = tid / BILU_MAX_BLOCK, rr = tid % BILU_MAX_BLOCK;
-        if (tid < b) yv[tid] = ldcg(a.z + s0 + tid);
+        if (tid < b) yv[tid] = (TC)ldcg(a.z + s0 + tid);
         // the normalised U columns into L2 before the waits
         if (warp == 1) warp_prefetch_l2((const TS *)a.Uhval + a.Uvptr[K], (q1 - q0) * b * (int64_t)sizeof(TS));
         __syncthreads();
         {
             // tv = D_K y_K: warp per row, four rows in flight
             const double *D = a.Dinv + a.Dptr[K];
-            const double y0 = lane < b ? yv[lane] : 0.0, y1 = lane + 32 < b ? yv[lane + 32] : 0.0;
+            const TC y0 = lane < b ? yv[lane] : TC(0), y1 = lane + 32 < b ? yv[lane + 32] : TC(0);
             for (int r0 = warp * 4; r0 < b; r0 += AW * 4) {
-                double v[4];
+                TC v[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int r = r0 + u;
-                    v[u] = 0.0;
+                    v[u] = TC(0);
                     if (r < b) {
-                        if (lane < b) v[u] = D[(int64_t)r * b + lane] * y0;
-                        if (lane + 32 < b) v[u] = fma(D[(int64_t)r * b + lane + 32], y1, v[u]);
+                        if (lane < b) v[u] = (TC)D[(int64_t)r * b + lane] * y0;
+                        if (lane + 32 < b) v[u] = fma((TC)D[(int64_t)r * b + lane + 32], y1, v[u]);
                     }
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const double w = warp_sum(v[u]);
+                    const TC w = warp_sum_t(v[u]);
                     if (lane == 0 && r0 + u < b) tv[r0 + u] = w;
                 }
             }
@@ -356,7 +375,7 @@ __global__ void __launch_bounds__(AT) apply_backward_kernel(ApplyArgs a) {
             part[g][rr] = backward_columns<TS>(a, K, b, q0, q0, q1, g, rr);
             __syncthreads();
             if (tid < b) {
-                double t = tv[tid];
+                TC t = tv[tid];
                 for (int gg = 0; gg < NG; ++gg) t -= part[gg][tid];
                 tv[tid] = t;
             }
@@ -392,7 +411,7 @@ __global__ void __launch_bounds__(AT) apply_backward_kernel(ApplyArgs a) {
                     part[g][rr] = backward_columns<TS>(a, K, b, q0, q0 + rq[r], q0 + rq[r + 1], g, rr);
                     __syncthreads();
                     if (tid < b) {
-                        double t = tv[tid];
+                        TC t = tv[tid];
                         for (int gg = 0; gg < NG; ++gg) t -= part[gg][tid];
                         tv[tid] = t;
                     }
@@ -401,7 +420,7 @@ __global__ void __launch_bounds__(AT) apply_backward_kernel(ApplyArgs a) {
                 ri -= take;
             }
         }
-        if (tid < b) a.z[s0 + tid] = tv[tid];
+        if (tid < b) a.z[s0 + tid] = (double)tv[tid];
         __syncthreads();
         if (tid == 0) {
             __threadfence();

@@ -118,11 +118,12 @@ def test_aggregation_after_the_tree_schedule(ctx):
     compare_factors(Fo, gc, rtol=1e-10)
 
 
-@pytest.mark.parametrize("prec,tol", [(B.BILU_PREC_FP32, 1e-5), (B.BILU_PREC_BF16, 3e-2)])
+@pytest.mark.parametrize("prec,tol", [(B.BILU_PREC_FP32, 1e-4), (B.BILU_PREC_BF16, 3e-2)])
 def test_aggregation_with_reduced_precision_storage(ctx, prec, tol):
     """FP32 / BF16 storage: the merged values are formed in FP64 from the stored ones and
     rounded once, so the merged preconditioner agrees with the unmerged one of the same
-    precision to the storage rounding, and GMRES needs at most one more step."""
+    precision to the storage rounding (and to the sweeps' FP32 arithmetic), and GMRES needs at
+    most one more step."""
     import torch
     w, bs = _case("elasticity 6^3 node blocks")
     c2 = B.bilu_create(0)

@@ -87,3 +87,35 @@ def test_tensor_tiles_same_factor_on_every_schedule(ctx):
     gt = _factor(ctx, w2, True, B.BILU_SCHED_TREE, bnd)
     for k in ("Lptr", "Lrow", "Lval", "Uptr", "Ucol", "Uval", "Dinv", "Pblk"):
         assert np.array_equal(getattr(gc, k), getattr(gt, k)), k
+
+
+@pytest.mark.parametrize("prec,tol", [(B.BILU_PREC_FP32, 1e-5), (B.BILU_PREC_BF16, 2e-2)])
+def test_reduced_precision_sweeps_against_a_dense_solve(ctx, prec, tol):
+    """The sweeps of a reduced-precision factor run in FP32 arithmetic: z = M^{-1} r agrees with
+    a dense FP64 solve with M = L U-breve assembled from the exported (widened) factor.  The
+    backward sweep multiplies by D_K U-breve_K as the factor stored it, rounded to the storage
+    format, so the two agree to that rounding (FP32: 2^-24, BF16: 2^-8) amplified by M's
+    conditioning, plus FP32 arithmetic."""
+    import torch
+    w = W.cd3d(side=12, seed=2, block=24)
+    g = gpu_factor(ctx, w.A, w.droptol, B.bilu_params_default(fixed_block=24, max_block=64, precision=prec))
+    n = w.A.n
+    Ld, Ud = np.eye(n), np.zeros((n, n))
+    for K in range(len(g.bstart) - 1):
+        s0, s1 = int(g.bstart[K]), int(g.bstart[K + 1])
+        rows, Lv = g.L_block(K)
+        Ld[rows, s0:s1] = Lv
+        cols, Uv = g.U_block(K)
+        Ud[s0:s1, s0:s1] = g.P_block(K)
+        Ud[s0:s1, cols] = Uv.T
+    M = Ld @ Ud
+    r = np.random.default_rng(9).standard_normal(n)
+    zref = np.linalg.solve(M, r)
+    rt = torch.from_numpy(r).cuda()
+    z = torch.empty_like(rt)
+    B.bilu_apply(ctx, rt, z)
+    torch.cuda.synchronize()
+    zg = z.cpu().numpy()
+    err = np.abs(zg - zref).max() / np.abs(zref).max()
+    print(f"precision {prec}: sweeps against the dense FP64 solve {err:.2e}")
+    assert err <= tol
