@@ -54,6 +54,29 @@ def test_cd3d64_sampled_blocks_and_solution(ctx):
     assert _residual(w.A, w.b, x.cpu().numpy()) <= 1e-8
 
 
+def test_laplace27x4_64_sampled_blocks_and_solution(ctx):
+    """The learned skip's evaluation matrix at full size, plain FP64 (the method without the
+    skip): Q1 27-point operator on 64^3 nodes with 4 coupled unknowns per node, n = 1,048,576,
+    blocks of 64, natural order.  Sampled blocks against the oracle's single-step checker, and
+    the GMRES solution's true residual."""
+    import torch
+    w = W.laplace27_4dof(side=64, seed=3, block=64)
+    g = gpu_factor(ctx, w.A, w.droptol, B.bilu_params_default(fixed_block=64, max_block=64))
+    E = _exp(g)
+    blocks = BC._blocks(E)
+    nb = len(g.bstart) - 1
+    flips = 0
+    for K in (0, 1, 2, 255, 256, nb // 2, nb - 2, nb - 1):
+        f, err = BC.compare_block(w.A, E, K, w.droptol, rtol=1e-10, blocks=blocks)
+        flips += f
+    assert flips == 0
+    bt = torch.from_numpy(w.b).cuda()
+    x = torch.zeros_like(bt)
+    info = B.gmres_solve(ctx, bt, x, 1e-8, 30, 10000)
+    assert _residual(w.A, w.b, x.cpu().numpy()) <= 1e-8
+    print(f"laplace27x4 64^3: {nb} blocks, GMRES {info.iters} iterations")
+
+
 @pytest.mark.parametrize("prec,u_store", [(B.BILU_PREC_FP32, BC.U_FP32), (B.BILU_PREC_BF16, BC.U_BF16)])
 def test_cd3d64_mixed_precision_sampled_blocks(ctx, prec, u_store):
     """FP32 updates (or BF16 storage) at full size: every sampled block equals the FP64 step
