@@ -63,7 +63,7 @@ static_assert(NW == 16, "the pivot LU's trailing update maps 12 of the 16 warps"
 constexpr int TRMAX = 16;        // max candidate slots per accumulation tile
 constexpr int PS = BILU_MAX_BLOCK + 1;  // padded row stride (doubles) of staged panels
 constexpr int PMAX = 1024;       // max producers per block handled by the kernel
-constexpr int SMEM_BYTES = 128 * 1024;
+constexpr int SMEM_BYTES = 160 * 1024;  // dynamic shared memory of the factor kernels (one CTA per SM)
 constexpr int TRP = 2;           // rows per pivot-row tile
 // Producer slices per pivot-row tile: the pivot rows' updates are on the critical path (the LU
 // waits for them), so each tile's producer list is split into PPART slices computed side by
@@ -530,13 +530,15 @@ __device__ __noinline__ void tile_features(const FactorArgs &a, int K, bool Lsid
 // ceil(b_J / 16) MMAs of 128 x 64 x 16 accumulate X_J Y_J^T in FP32 in tensor memory (TMEM,
 // 128 lanes = tile rows, 64 columns).  The products of BF16 values are exact in FP32; the
 // accumulation is FP32.  One thread issues the MMAs; their completion arrives on an mbarrier
-// that the CTA waits on (bounded) before the operands are overwritten.
+// that the CTA waits on (bounded) before the operands are overwritten.  The producers' panel
+// ranges (contiguous per producer) and their slot / column indices are copied into shared
+// memory by cp.async one producer ahead, so their loads overlap the placement and the MMAs of
+// the producer before.
 constexpr int TC_ROWS = 128;             // tile rows (MMA M)
 constexpr int TC_COLS = BILU_MAX_BLOCK;  // B_K columns (MMA N) and TMEM columns allocated
 constexpr uint32_t TC_IDESC = (1u << 4)                    // accumulator FP32
                             | (1u << 7) | (1u << 10)       // A and B BF16, both K-major
                             | ((uint32_t)(TC_COLS >> 3) << 17) | ((uint32_t)(TC_ROWS >> 4) << 24);
-constexpr int TC_PF = (TC_ROWS * BILU_MAX_BLOCK + BILU_MAX_BLOCK * BILU_MAX_BLOCK + NT - 1) / NT;
 
 __shared__ uint32_t s_tc_tmem;   // TMEM address of the CTA's accumulator
 __shared__ __align__(8) uint64_t s_tc_bar;
@@ -554,6 +556,15 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32
 // element offset of (row, k) in the core-matrix layout of a rows x 64 K-major BF16 operand
 __device__ __forceinline__ int tc_off(int row, int k) {
     return ((row >> 3) * (BILU_MAX_BLOCK / 8) + (k >> 3)) * 64 + (row & 7) * 8 + (k & 7);
+}
+
+// 4-byte asynchronous copy global -> shared (both 4-byte aligned), and its group fences
+__device__ __forceinline__ void cp_async4(void *sdst, const void *gsrc) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(sdst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 template <class TS> __device__ __forceinline__ bool tc_on(const FactorArgs &a) { return false; }
@@ -690,8 +701,32 @@ __device__ void phase_B_tile_tc(const FactorArgs &a, int K, bool Lside, int sa, 
     const TS *Xpool = (const TS *)(Lside ? a.Lval : a.Uval);
     const TS *Ypool = (const TS *)(Lside ? a.Uval : a.Lval);
     const int32_t *Yidx = Lside ? a.Ucol : a.Lrow;
+    // raw panel ranges of two producers in flight (cp.async, 4-byte words): the next producer's
+    // X rows, Y rows and their slot / column indices load while the current one is placed and
+    // multiplied
+    constexpr int RAWX = TC_ROWS * BILU_MAX_BLOCK / 2 + 2, RAWY = BILU_MAX_BLOCK * BILU_MAX_BLOCK / 2 + 2;
+    uint32_t *raw = (uint32_t *)(ws + 40);                 // 2 stages: X words, Y words, X slots, Y columns
+    const int stage_words = RAWX + RAWY + TC_ROWS + BILU_MAX_BLOCK;
+    auto prefetch = [&](int i) {
+        const int t = tl[i];
+        const int nx = sxe[t] - sxs[t], ny = pny[t], bJ = pbJ[t];
+        uint32_t *st = raw + (i & 1) * stage_words;
+        const int64_t xval = pxv[t] + (int64_t)sxs[t] * bJ, yval = pyv[t];
+        const int64_t xw0 = xval >> 1, yw0 = yval >> 1;
+        const int nxw = (int)(((xval + (int64_t)nx * bJ + 1) >> 1) - xw0);
+        const int nyw = (int)(((yval + (int64_t)ny * bJ + 1) >> 1) - yw0);
+        if (nx <= cnt && ny <= BILU_MAX_BLOCK && bJ <= BILU_MAX_BLOCK && nxw <= RAWX && nyw <= RAWY) {
+            const uint32_t *gx = (const uint32_t *)Xpool + xw0, *gy = (const uint32_t *)Ypool + yw0;
+            for (int e = tid; e < nxw; e += NT) cp_async4(st + e, gx + e);
+            for (int e = tid; e < nyw; e += NT) cp_async4(st + RAWX + e, gy + e);
+            for (int e = tid; e < nx; e += NT) cp_async4(st + RAWX + RAWY + e, xslot + poff[t] + sxs[t] + e);
+            for (int e = tid; e < ny; e += NT) cp_async4(st + RAWX + RAWY + TC_ROWS + e, Yidx + pyp[t] + e);
+        }
+        cp_async_commit();
+    };
     long long flops = 0;
     bool ok = true;
+    if (ntl > 0) prefetch(0);
     for (int i = 0; i < ntl && ok; ++i) {
         const int t = tl[i];
         const int nx = sxe[t] - sxs[t], ny = pny[t], bJ = pbJ[t];
@@ -701,18 +736,13 @@ __device__ void phase_B_tile_tc(const FactorArgs &a, int K, bool Lside, int sa, 
             break;
         }
         flops += 2LL * nx * ny * bJ;
-        // this producer's values into registers (they load while the previous MMAs run)
-        const int nxv = nx * bJ, tot = nxv + ny * bJ;
-        const int64_t xval = pxv[t] + (int64_t)sxs[t] * bJ, yval = pyv[t];
-        TS v[TC_PF];
-#pragma unroll
-        for (int k = 0; k < TC_PF; ++k) {
-            const int e = tid + k * NT;
-            v[k] = e < nxv ? Xpool[xval + e] : (e < tot ? Ypool[yval + (e - nxv)] : __float2bfloat16(0.f));
+        if (i + 1 < ntl) {
+            prefetch(i + 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
-        int xr = -1, yr = -1;
-        if (tid < nx) xr = ldcg(xslot + poff[t] + sxs[t] + tid) - sa;
-        if (tid >= TC_ROWS && tid - TC_ROWS < ny) yr = ldcg(Yidx + pyp[t] + (tid - TC_ROWS)) - s0;
+        __syncthreads();  // producer i's words are in shared memory for every thread
         if (i > 0 && !tc_wait(a, K)) { ok = false; break; }
         // zero both operands (K padding and absent rows stay zero), then place the values
         {
@@ -720,23 +750,23 @@ __device__ void phase_B_tile_tc(const FactorArgs &a, int K, bool Lside, int sa, 
             const int nz = (TC_ROWS + BILU_MAX_BLOCK) * BILU_MAX_BLOCK * (int)sizeof(TS) / 16;
             for (int e = tid; e < nz; e += NT) z[e] = make_uint4(0, 0, 0, 0);
         }
-        __shared__ int32_t s_xrow[TC_ROWS], s_ycol[BILU_MAX_BLOCK];  // tile slot / B_K column
-        if (tid < nx) s_xrow[tid] = (xr >= 0 && xr < cnt) ? xr : -1;
-        if (tid >= TC_ROWS && tid - TC_ROWS < ny) s_ycol[tid - TC_ROWS] = (yr >= 0 && yr < b) ? yr : -1;
         __syncthreads();
-#pragma unroll
-        for (int k = 0; k < TC_PF; ++k) {
-            const int e = tid + k * NT;
+        const uint32_t *st = raw + (i & 1) * stage_words;
+        const TS *rx = (const TS *)st + ((pxv[t] + (int64_t)sxs[t] * bJ) & 1);
+        const TS *ry = (const TS *)(st + RAWX) + (pyv[t] & 1);
+        const int32_t *rxs = (const int32_t *)(st + RAWX + RAWY), *ryc = rxs + TC_ROWS;
+        const int nxv = nx * bJ, tot = nxv + ny * bJ;
+        for (int e = tid; e < tot; e += NT) {
             if (e < nxv) {
-                const int x = e / bJ, kk = e - x * bJ, r = s_xrow[x];
-                if (r >= 0) sA[tc_off(r, kk)] = v[k];
-            } else if (e < tot) {
-                const int ee = e - nxv, y = ee / bJ, kk = ee - y * bJ, c = s_ycol[y];
-                if (c >= 0) sB[tc_off(c, kk)] = v[k];
+                const int x = e / bJ, kk = e - x * bJ, r = rxs[x] - sa;
+                if (r >= 0 && r < cnt) sA[tc_off(r, kk)] = rx[e];
+                else set_status(a.status, DEV_INTERNAL, a.info, K);
+            } else {
+                const int ee = e - nxv, y = ee / bJ, kk = ee - y * bJ, c = ryc[y] - s0;
+                if (c >= 0 && c < b) sB[tc_off(c, kk)] = ry[ee];
+                else set_status(a.status, DEV_INTERNAL, a.info, K);
             }
         }
-        if (tid < nx && !(xr >= 0 && xr < cnt)) set_status(a.status, DEV_INTERNAL, a.info, K);
-        if (tid >= TC_ROWS && tid - TC_ROWS < ny && !(yr >= 0 && yr < b)) set_status(a.status, DEV_INTERNAL, a.info, K);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
@@ -756,6 +786,7 @@ __device__ void phase_B_tile_tc(const FactorArgs &a, int K, bool Lside, int sa, 
                          ::"r"(smem_addr(&s_tc_bar)) : "memory");
         }
     }
+    cp_async_wait<0>();  // nothing left in flight when the tile ends early
     if (ok && ntl > 0 && !tc_wait(a, K)) ok = false;
     if (ok) {
         // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (tile rows), columns 16 (w / 4) ..
