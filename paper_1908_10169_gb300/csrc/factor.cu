@@ -756,13 +756,16 @@ __device__ void phase_B_tile_tc(const FactorArgs &a, int K, bool Lside, int sa, 
         const TS *ry = (const TS *)(st + RAWX) + (pyv[t] & 1);
         const int32_t *rxs = (const int32_t *)(st + RAWX + RAWY), *ryc = rxs + TC_ROWS;
         const int nxv = nx * bJ, tot = nxv + ny * bJ;
+        // row of element e: floor((e + 1/2) / bJ) in FP32 is exact here (e < 2^14, bJ <= 64: the
+        // quotient stays at least 1/128 from an integer, far above the FP32 rounding)
+        const float rb = 1.0f / (float)bJ;
         for (int e = tid; e < tot; e += NT) {
             if (e < nxv) {
-                const int x = e / bJ, kk = e - x * bJ, r = rxs[x] - sa;
+                const int x = (int)(((float)e + 0.5f) * rb), kk = e - x * bJ, r = rxs[x] - sa;
                 if (r >= 0 && r < cnt) sA[tc_off(r, kk)] = rx[e];
                 else set_status(a.status, DEV_INTERNAL, a.info, K);
             } else {
-                const int ee = e - nxv, y = ee / bJ, kk = ee - y * bJ, c = ryc[y] - s0;
+                const int ee = e - nxv, y = (int)(((float)ee + 0.5f) * rb), kk = ee - y * bJ, c = ryc[y] - s0;
                 if (c >= 0 && c < b) sB[tc_off(c, kk)] = ry[ee];
                 else set_status(a.status, DEV_INTERNAL, a.info, K);
             }
