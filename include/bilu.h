@@ -190,6 +190,10 @@ bilu_status bilu_analyze(bilu_ctx *ctx, int64_t n, const int64_t *rowptr, const 
  * and a scalar row / column is dropped when its Euclidean norm is <= droptol.
  * Returns BILU_OK, BILU_PERTURBED, BILU_ERR_SINGULAR (perturb == 0), BILU_ERR_TIMEOUT,
  * BILU_ERR_OOM, BILU_ERR_CUDA, BILU_ERR_STATE (no analysis), BILU_ERR_ARG (droptol < 0).
+ * BILU_ERR_OOM also reports a block updated by more than 1024 earlier blocks (the kernels'
+ * per-block producer list lives in shared memory): a partition whose blocks do not follow the
+ * matrix's structure (for instance fixed blocks after a matching that scrambled the order)
+ * needs a blocking or reordering first (Sec. 3.2-3.4).
  */
 bilu_status bilu_factor(bilu_ctx *ctx, double droptol);
 
