@@ -119,3 +119,29 @@ def test_reduced_precision_sweeps_against_a_dense_solve(ctx, prec, tol):
     err = np.abs(zg - zref).max() / np.abs(zref).max()
     print(f"precision {prec}: sweeps against the dense FP64 solve {err:.2e}")
     assert err <= tol
+
+
+def test_tensor_tiles_in_the_batched_launch(ctx):
+    """The batched launch (groups of CTAs over a queue of matrices) runs the BF16 tiles on the
+    tensor cores too: each matrix's factor equals its one-by-one BF16 factor bit for bit (a
+    row's MMA sums do not depend on the tile or the group it falls in)."""
+    ws = W.cd_batch(count=3, seed0=300, n_lo=1500, n_hi=4000, block=32)
+    ctxs = [B.bilu_create(0) for _ in ws]
+    try:
+        p = lambda w: B.bilu_params_default(fixed_block=w.fixed_block, max_block=64, precision=B.BILU_PREC_BF16)
+        for c, w in zip(ctxs, ws):
+            B.bilu_analyze(c, w.A.n, w.A.rowptr, w.A.colind, w.A.val, p(w))
+        B.bilu_factor_batch(ctxs, 1e-2)
+        for c, w in zip(ctxs, ws):
+            g1 = gpu_factor(ctx, w.A, 1e-2, p(w))
+            s = B.bilu_stats(c)
+            arrs = dict(Lptr=np.zeros(s.nblocks + 1, np.int64), Lrow=np.zeros(s.kept_rows, np.int32),
+                        Lval=np.zeros(s.nnz_l), Uptr=np.zeros(s.nblocks + 1, np.int64),
+                        Ucol=np.zeros(s.kept_cols, np.int32), Uval=np.zeros(s.nnz_u),
+                        Dinv=np.zeros(s.nnz_d), Pblk=np.zeros(s.nnz_d))
+            B.bilu_export(c, **arrs)
+            for k, v in arrs.items():
+                assert np.array_equal(v, getattr(g1, k)), (w.name, k)
+    finally:
+        for c in ctxs:
+            B.bilu_destroy(c)
