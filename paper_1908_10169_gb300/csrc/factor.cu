@@ -2030,7 +2030,9 @@ __device__ void factor_tree_body(const FactorArgs *gargs, TreeArgs t) {
     // mode 0: a CTA of group grp takes ready blocks; 1: the groups are done, the grid meets;
     // 2: the trunk on the whole grid (one block_step call site for all of them)
     int mode = grp < t.ngroups ? 0 : 1;
-    if (mode == 0 && threadIdx.x == 0) s_a = gargs[grp];
+    // the CTAs past the last whole group (when G does not divide the grid) join only the trunk;
+    // they hold group 0's arguments until then, so that every field they read is defined
+    if (threadIdx.x == 0) s_a = gargs[mode == 0 ? grp : 0];
     __syncthreads();
     int Kt = t.split;
     while (true) {

@@ -57,7 +57,11 @@ def same_factor(g1, g2):
 
 @pytest.mark.parametrize("side,blk,G,trunk", [(12, 12, 4, True), (16, 16, 1, False), (16, 16, 8, True),
                                               (20, 20, 2, False), (16, 8, 19, True), (24, 24, 8, False),
-                                              (24, 24, 38, True)])
+                                              (24, 24, 38, True),
+                                              # group sizes that do not divide the grid: the CTAs
+                                              # past the last group join only the trunk
+                                              (16, 16, 12, True), (20, 20, 5, True), (24, 24, 24, False),
+                                              (16, 16, 100, True)])
 def test_tree_equals_chain_bitwise(ctx, side, blk, G, trunk):
     A, b, bs = nd_workload(W.cd3d(side=side, seed=1, block=blk), blk)
     gc = gpu_factor(ctx, A, 1e-2, params(B.BILU_SCHED_CHAIN), bstart=bs)
