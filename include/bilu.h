@@ -87,8 +87,10 @@ typedef struct {
                             pays off on an ordering with independent subtrees (nested
                             dissection, bilu_nd_order); in natural order the tree is a chain.
                             Not with BILU_SKIP_LEARNED or sample recording (BILU_ERR_ARG).      */
-    int32_t group_ctas;  /* CTAs per group of BILU_SCHED_TREE, 1..number of SMs (0: an eighth of
-                            the SMs, 8 groups)                                                  */
+    int32_t group_ctas;  /* CTAs per group of BILU_SCHED_TREE, 1..number of SMs (0: by A's
+                            coupling: 8 groups when its rows hold >= 32 entries on average, else
+                            15 groups, 19 with BF16 storage; a size that does not divide the SM
+                            count leaves the remaining CTAs to the trunk)                       */
     int32_t aggregate_max; /* progressive aggregation (Sec. 3.5), 0 (off) or 2..BILU_MAX_BLOCK:
                             consecutive finished blocks k-1, k are merged into one block of at
                             most this many columns whenever the merge test of Sec. 3.5 holds
@@ -160,7 +162,7 @@ typedef struct {
 
 /* Fills *p with the defaults: FIXED blocking of 32 (max 64), tau_analyze 1e-2,
  * perturbation on with tau 1e-2 and rho 1e-1 (Sec. 3.6), FP64, no skipping, the chain
- * schedule (group_ctas 0).
+ * schedule (group_ctas 0: chosen by the library), no aggregation.
  * Errors: BILU_ERR_ARG (p NULL). */
 bilu_status bilu_params_default(bilu_params *p);
 

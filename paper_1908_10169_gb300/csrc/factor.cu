@@ -2667,7 +2667,16 @@ cudaError_t launch_tree_copy(bilu_ctx *c, int grid) {
 // CTAs per group of the tree schedule: the caller's, else an eighth of the SMs (8 groups; on
 // the 64^3 benchmark groups of 19 CTAs beat 4, 8, 38 and 76).
 int tree_group_ctas(const bilu_ctx *c) {
-    return std::max(1, std::min(c->nsm, c->p.group_ctas > 0 ? c->p.group_ctas : std::max(1, c->nsm / 8)));
+    if (c->p.group_ctas > 0) return std::max(1, std::min(c->nsm, c->p.group_ctas));
+    // Default: a block's parallel work (its candidates' updates and scaling) grows with the
+    // coupling of A's rows, its pivot LU does not.  Densely coupled rows (>= 32 entries, e.g.
+    // the 27-point elasticity operator) keep 8 groups of an eighth of the SMs; sparse stencils
+    // run more groups of fewer CTAs: 15, or 19 with BF16 storage, whose update tiles on the
+    // tensor cores are cheap (measured group-size sweeps on 64^3 convection-diffusion and 48^3
+    // elasticity).
+    const double per_row = c->n > 0 ? (double)c->nnz / (double)c->n : 0.0;
+    const int groups = per_row >= 32.0 ? 8 : (c->p.precision == BILU_PREC_BF16 ? 19 : 15);
+    return std::max(1, c->nsm / groups);
 }
 
 // Tree schedule: groups of G CTAs factor independent subtrees of the block elimination tree,
