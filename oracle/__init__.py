@@ -72,6 +72,10 @@ def lib():
         L.orc_gmres.argtypes = [i64, P, P, P, P, P, P, f64, i32, i32, ct.POINTER(i32),
                                 ct.POINTER(f64), P]
         L.orc_gmres.restype = i32
+        L.orc_bildl_factor.argtypes = [i64, P, P, P, i32, P, f64, i32, f64, f64, ct.POINTER(P)]
+        L.orc_bildl_factor.restype = i32
+        L.orc_sqmr.argtypes = [i64, P, P, P, P, P, P, f64, i32, ct.POINTER(i32), ct.POINTER(f64), P]
+        L.orc_sqmr.restype = i32
         _lib = L
     return _lib
 
@@ -224,12 +228,30 @@ def bilu_factor(A, bstart: np.ndarray, droptol: float, perturb: bool = True,
     """Crout BILU (Sec. 2.2), with progressive aggregation of blocks up to agg_max columns
     when agg_max > 0 (Sec. 3.5; the factor's bstart then has void blocks).  Raises on
     argument errors and singular blocks."""
+    return _factor(A, bstart, droptol, perturb, pert_tau, pert_rho, keep_handle, agg_max, False)
+
+
+def bildl_factor(A, bstart: np.ndarray, droptol: float, perturb: bool = True,
+                 pert_tau: float = 1e-2, pert_rho: float = 1e-1, keep_handle: bool = True) -> Factor:
+    """BILDL, the incomplete block L D L^T of a symmetric A (Sec. 4.2), in the BILU layout:
+    column i of U-breve is the unnormalised row of L's row i.  Raises ValueError when A is
+    not symmetric."""
+    return _factor(A, bstart, droptol, perturb, pert_tau, pert_rho, keep_handle, 0, True)
+
+
+def _factor(A, bstart, droptol, perturb, pert_tau, pert_rho, keep_handle, agg_max, sym) -> Factor:
     L = lib()
     rp, ci, va = _csr_args(A)
     bs = np.ascontiguousarray(bstart, dtype=np.int32)
     h = ct.c_void_p()
-    st = L.orc_bilu_factor_agg(A.n, _p(rp), _p(ci), _p(va), len(bs) - 1, _p(bs), droptol,
-                               int(perturb), pert_tau, pert_rho, int(agg_max), ct.byref(h))
+    if sym:
+        st = L.orc_bildl_factor(A.n, _p(rp), _p(ci), _p(va), len(bs) - 1, _p(bs), droptol,
+                                int(perturb), pert_tau, pert_rho, ct.byref(h))
+        if st == -1:
+            raise ValueError("BILDL needs a symmetric matrix and a valid partition")
+    else:
+        st = L.orc_bilu_factor_agg(A.n, _p(rp), _p(ci), _p(va), len(bs) - 1, _p(bs), droptol,
+                                   int(perturb), pert_tau, pert_rho, int(agg_max), ct.byref(h))
     if st < 0:
         raise RuntimeError(f"oracle factor failed with status {st}")
     sizes = np.zeros(8, dtype=np.int64)
@@ -302,3 +324,27 @@ def gmres(A, F: Factor | None, b: np.ndarray, tol: float = 1e-8, restart: int = 
     st = lib().orc_gmres(A.n, _p(rp), _p(ci), _p(va), None if F is None else F.handle, _p(b),
                          _p(x), tol, restart, maxit, ct.byref(it), ct.byref(rr), _p(hist))
     return GmresResult(x, it.value, rr.value, st, hist[: it.value + 1].copy())
+
+
+@dataclasses.dataclass
+class SqmrResult:
+    x: np.ndarray
+    iters: int
+    berr: float
+    status: int
+    hist: np.ndarray
+
+
+def sqmr(A, F: Factor | None, b: np.ndarray, tol: float = 1e-6, maxit: int = 10000,
+         x0: np.ndarray | None = None) -> SqmrResult:
+    """Simplified QMR with the symmetric preconditioner F (None: none), stopped on the
+    normwise backward error (Sec. 4.2).  status: 0 converged, 1 maxit, 3 breakdown."""
+    rp, ci, va = _csr_args(A)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros(A.n) if x0 is None else np.array(x0, dtype=np.float64)
+    it = ct.c_int32()
+    be = ct.c_double()
+    hist = np.zeros(maxit + 1)
+    st = lib().orc_sqmr(A.n, _p(rp), _p(ci), _p(va), None if F is None else F.handle, _p(b),
+                        _p(x), tol, maxit, ct.byref(it), ct.byref(be), _p(hist))
+    return SqmrResult(x, it.value, be.value, st, hist[: it.value + 1].copy())

@@ -323,10 +323,11 @@ static double perturbed(double d, double ptau, double prho, double alpha) {
  * perturbed).  Sec. 3.6: an all-zero column j is perturbed at its largest entry, the
  * diagonal entry taking precedence when 2|d_jj| >= |d_kj|; rows likewise.  A pivot
  * breakdown during the LU perturbs the breaking column the same way and restarts.
+ * With sym (BILDL) the breaking column is perturbed at its diagonal entry.
  * Returns the number of perturbations, or -1 when singular and perturbation is off
  * (or did not cure the block).
  */
-static int factor_pivot_block(double *P, int b, int perturb, double ptau, double prho, double alpha,
+static int factor_pivot_block(double *P, int b, int perturb, double ptau, double prho, double alpha, int sym,
                               double *lu, int32_t *perm, double *dinv) {
     int count = 0;
     if (perturb) {
@@ -355,6 +356,7 @@ static int factor_pivot_block(double *P, int b, int perturb, double ptau, double
         for (int i = 1; i < b; ++i)
             if (fabs(P[i * b + bad]) > fabs(P[k * b + bad])) k = i;
         if (2.0 * fabs(P[bad * b + bad]) >= fabs(P[k * b + bad])) k = bad;
+        if (sym) k = bad; /* symmetric variant: the diagonal entry, so that P stays symmetric (reading R22) */
         P[k * b + bad] = perturbed(P[k * b + bad], ptau, prho, alpha);
         ++count;
     }
@@ -633,16 +635,49 @@ static void aggregate_step(orc_factor *F, int32_t k, int32_t agg_max, vec_i32 *p
  *  5. u^_j = D_K T_U[B_K, j] for candidate cols j >= s1; keep iff ||u^_j||_2 > tau; store
  *     the column T_U[B_K, j] unnormalised (readings R1-R3).
  */
+static int32_t crout_factor(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val,
+                            int32_t nb, const int32_t *bstart, double droptol, int32_t perturb,
+                            double pert_tau, double pert_rho, int32_t agg_max, int sym, orc_factor **out);
+
 int32_t orc_bilu_factor(int64_t n, const int64_t *rowptr, const int32_t *colind,
                         const double *val, int32_t nb, const int32_t *bstart, double droptol,
                         int32_t perturb, double pert_tau, double pert_rho, orc_factor **out) {
-    return orc_bilu_factor_agg(n, rowptr, colind, val, nb, bstart, droptol, perturb, pert_tau, pert_rho, 0, out);
+    return crout_factor(n, rowptr, colind, val, nb, bstart, droptol, perturb, pert_tau, pert_rho, 0, 0, out);
 }
 
 int32_t orc_bilu_factor_agg(int64_t n, const int64_t *rowptr, const int32_t *colind,
                             const double *val, int32_t nb, const int32_t *bstart, double droptol,
                             int32_t perturb, double pert_tau, double pert_rho, int32_t agg_max,
                             orc_factor **out) {
+    return crout_factor(n, rowptr, colind, val, nb, bstart, droptol, perturb, pert_tau, pert_rho, agg_max, 0, out);
+}
+
+/*
+ * BILDL, the symmetric variant (incomplete block L D L^T of a symmetric A, Sec. 4.2): the
+ * same Crout loop on the lower triangle only.  For symmetric A the row block T_U[B_K, :]
+ * of step 1-2 is the transpose of the column block T_L[:, B_K], so step 2b and step 5 are
+ * not computed; instead
+ *  3'. the pivot block is the lower triangle of T_L[B_K, B_K] mirrored (symmetric by
+ *      construction), factored as in step 3 with perturbations on the diagonal only, and
+ *      D_K = (X + X^T) / 2 for the computed inverse X (symmetric to the last bit);
+ *  4'. a kept row l_i = t_i D_K is stored in L and its unnormalised t_i, as column i, in
+ *      U-breve (D_K t_i^T = l_i^T, so the column's drop test is the row's).
+ * The preconditioner L U-breve = L P L^T is then symmetric (readings R22, R23).
+ */
+int32_t orc_bildl_factor(int64_t n, const int64_t *rowptr, const int32_t *colind,
+                         const double *val, int32_t nb, const int32_t *bstart, double droptol,
+                         int32_t perturb, double pert_tau, double pert_rho, orc_factor **out) {
+    if (n < 0 || !rowptr) return ORC_ERR_ARG;
+    for (int64_t i = 0; i < n; ++i) /* A must equal A^T, entry by entry */
+        for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e)
+            if (colind[e] < 0 || colind[e] >= n || entry(rowptr, colind, val, colind[e], (int32_t)i) != val[e])
+                return ORC_ERR_ARG;
+    return crout_factor(n, rowptr, colind, val, nb, bstart, droptol, perturb, pert_tau, pert_rho, 0, 1, out);
+}
+
+static int32_t crout_factor(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val,
+                            int32_t nb, const int32_t *bstart, double droptol, int32_t perturb,
+                            double pert_tau, double pert_rho, int32_t agg_max, int sym, orc_factor **out) {
     if (n < 0 || nb < 0 || droptol < 0 || agg_max < 0 || !out) return ORC_ERR_ARG;
     if (bstart[0] != 0 || bstart[nb] != n) return ORC_ERR_ARG;
     for (int32_t K = 0; K < nb; ++K)
@@ -707,7 +742,7 @@ int32_t orc_bilu_factor_agg(int64_t n, const int64_t *rowptr, const int32_t *col
                 int32_t sl = spa_slot(&TL, i);
                 TL.buf[(size_t)sl * b + (c - s0)] = csc.val[e];
             }
-        for (int32_t r = s0; r < s1; ++r)
+        for (int32_t r = s0; r < s1 && !sym; ++r)
             for (int64_t e = rowptr[r]; e < rowptr[r + 1]; ++e) {
                 int32_t j = colind[e];
                 if (j < s1) continue;
@@ -738,8 +773,8 @@ int32_t orc_bilu_factor_agg(int64_t n, const int64_t *rowptr, const int32_t *col
                 }
             }
         }
-        /* step 2b: U side, J with kept L rows in B_K */
-        for (int64_t t = 0; t < prodU[K].n; ++t) {
+        /* step 2b: U side, J with kept L rows in B_K (BILDL: the transpose of step 2a) */
+        for (int64_t t = 0; t < prodU[K].n && !sym; ++t) {
             int32_t J = prodU[K].a[t];
             int bJ = F->bstart[J + 1] - F->bstart[J];
             int64_t ps = lower_bound_i32(F->Lrow.a, F->Lptr[J], F->Lptr[J + 1], s0);
@@ -773,9 +808,19 @@ int32_t orc_bilu_factor_agg(int64_t n, const int64_t *rowptr, const int32_t *col
         P = xrealloc(P, (size_t)b * b * sizeof(double));
         for (int r = 0; r < b; ++r)
             for (int c = 0; c < b; ++c) P[r * b + c] = TL.buf[(size_t)r * b + c]; /* slots 0..b-1 = rows s0.. */
+        if (sym) /* BILDL: the lower triangle defines the symmetric pivot block */
+            for (int r = 0; r < b; ++r)
+                for (int c = r + 1; c < b; ++c) P[r * b + c] = P[c * b + r];
         double *D = F->Dinv + F->Dptr[K];
-        int np = factor_pivot_block(P, b, perturb, pert_tau, pert_rho, alpha,
+        int np = factor_pivot_block(P, b, perturb, pert_tau, pert_rho, alpha, sym,
                                     F->LUblk + F->Dptr[K], F->piv + s0, D);
+        if (np >= 0 && sym)
+            for (int r = 0; r < b; ++r)
+                for (int c = r + 1; c < b; ++c) {
+                    double v = (D[r * b + c] + D[c * b + r]) * 0.5;
+                    D[r * b + c] = v;
+                    D[c * b + r] = v;
+                }
         memcpy(F->Pblk + F->Dptr[K], P, (size_t)b * b * sizeof(double));
         if (np < 0) { status = ORC_ERR_SINGULAR; break; }
         if (np > 0) { F->counters[ORC_C_NPERTURB] += np; }
@@ -807,10 +852,16 @@ int32_t orc_bilu_factor_agg(int64_t n, const int64_t *rowptr, const int32_t *col
                 vd_reserve(&F->Lval, b);
                 memcpy(F->Lval.a + F->Lval.n, ell, (size_t)b * sizeof(double));
                 F->Lval.n += b;
+                if (sym) { /* BILDL: column i of U-breve is t_i^T */
+                    vi_push(&F->Ucol, TL.idx[order[t]]);
+                    vd_reserve(&F->Uval, b);
+                    memcpy(F->Uval.a + F->Uval.n, trow, (size_t)b * sizeof(double));
+                    F->Uval.n += b;
+                }
             }
         }
-        /* step 5: U columns, in increasing column order */
-        int64_t ncc = TU.nslot;
+        /* step 5: U columns, in increasing column order (BILDL: taken in step 4) */
+        int64_t ncc = sym ? 0 : TU.nslot;
         for (int64_t t = 0; t < ncc; ++t) order[t] = (int32_t)t;
         g_sort_keys = TU.idx;
         qsort(order, (size_t)ncc, sizeof(int32_t), cmp_slot);
@@ -1062,5 +1113,88 @@ int32_t orc_gmres(int64_t n, const int64_t *rowptr, const int32_t *colind, const
     status = (rel <= tol) ? ORC_OK : ORC_NOT_CONVERGED;
 done:
     free(V); free(H); free(cs); free(sn); free(g); free(y); free(w); free(zt); free(r);
+    return status;
+}
+
+/* ------------------------------------------------------------ SQMR */
+
+/* Normwise backward error of x (Rigal and Gaches, with the data A and b perturbed):
+ * ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf)  (reading R24). */
+static double backward_error(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val,
+                             double anorm, const double *b, const double *x, double *work) {
+    orc_spmv(n, rowptr, colind, val, x, work);
+    double rmax = 0.0, xmax = 0.0, bmax = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        rmax = fmax(rmax, fabs(b[i] - work[i]));
+        xmax = fmax(xmax, fabs(x[i]));
+        bmax = fmax(bmax, fabs(b[i]));
+    }
+    double den = anorm * xmax + bmax;
+    return den > 0.0 ? rmax / den : 0.0;
+}
+
+/*
+ * Simplified QMR (Freund and Nachtigal; Freund and Jarre) for a symmetric, possibly
+ * indefinite A with a symmetric preconditioner M (the solver paired with BILDL, Sec. 4.2).
+ * No look-ahead.  With the BCG residual r, direction q, rho = r^T M^{-1} r:
+ *   sigma = q^T A q,  alpha = rho / sigma,  r <- r - alpha A q,
+ *   theta' = ||r|| / tau,  c = 1 / sqrt(1 + theta'^2),  tau <- tau theta' c,
+ *   d <- c^2 theta^2 d + c^2 alpha q,  x <- x + d,
+ *   u = M^{-1} r,  rho' = r^T u,  q <- u + (rho' / rho) q,
+ * starting from r = b - A x0, tau = ||r||, q = M^{-1} r, theta = 0, d = 0.  Stops when the
+ * backward error of x (backward_error above) is <= tol, after maxit steps, or when sigma or
+ * rho vanishes (a breakdown).  iters counts steps (one product with A and one with M^{-1}
+ * each); hist[k] is the backward error after step k (hist[0]: of x0).
+ */
+int32_t orc_sqmr(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val,
+                 const orc_factor *M, const double *b, double *x, double tol, int32_t maxit,
+                 int32_t *iters, double *berr, double *hist) {
+    double *r = xmalloc((size_t)n * sizeof(double) + 8), *t = xmalloc((size_t)n * sizeof(double) + 8);
+    double *q = xmalloc((size_t)n * sizeof(double) + 8), *d = xcalloc((size_t)n + 1, sizeof(double));
+    double *u = xmalloc((size_t)n * sizeof(double) + 8), *w = xmalloc((size_t)n * sizeof(double) + 8);
+    int32_t its = 0, status = ORC_NOT_CONVERGED;
+    double anorm = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) s += fabs(val[e]);
+        anorm = fmax(anorm, s);
+    }
+    double eta = backward_error(n, rowptr, colind, val, anorm, b, x, w);
+    if (hist) hist[0] = eta;
+    if (eta <= tol) { status = ORC_OK; goto done; }
+    orc_spmv(n, rowptr, colind, val, x, t);
+    for (int64_t i = 0; i < n; ++i) r[i] = b[i] - t[i];
+    double tau = sqrt(dot(n, r, r)), theta = 0.0;
+    precond(M, n, r, q);
+    double rho = dot(n, r, q);
+    while (its < maxit) {
+        orc_spmv(n, rowptr, colind, val, q, t);
+        double sigma = dot(n, q, t);
+        if (sigma == 0.0) { status = ORC_BREAKDOWN; break; }
+        double alpha = rho / sigma;
+        for (int64_t i = 0; i < n; ++i) r[i] -= alpha * t[i];
+        double theta1 = sqrt(dot(n, r, r)) / tau;
+        double c = 1.0 / sqrt(1.0 + theta1 * theta1);
+        tau = tau * theta1 * c;
+        for (int64_t i = 0; i < n; ++i) {
+            d[i] = c * c * theta * theta * d[i] + c * c * alpha * q[i];
+            x[i] += d[i];
+        }
+        ++its;
+        eta = backward_error(n, rowptr, colind, val, anorm, b, x, w);
+        if (hist) hist[its] = eta;
+        if (eta <= tol) { status = ORC_OK; break; }
+        if (rho == 0.0) { status = ORC_BREAKDOWN; break; }
+        precond(M, n, r, u);
+        double rho1 = dot(n, r, u);
+        double beta = rho1 / rho;
+        for (int64_t i = 0; i < n; ++i) q[i] = u[i] + beta * q[i];
+        rho = rho1;
+        theta = theta1;
+    }
+done:
+    *iters = its;
+    *berr = eta;
+    free(r); free(t); free(q); free(d); free(u); free(w);
     return status;
 }

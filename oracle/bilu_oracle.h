@@ -20,6 +20,7 @@
  *   - Progressive aggregation of consecutive blocks during the factorization (Sec. 3.5).
  *   - Simplified ILU(1,tau) block-pattern guess (Sec. 3.4).
  *   - Restarted GMRES(30) (Sec. 4, Example setup).
+ *   - The symmetric variant BILDL and simplified QMR with a backward-error stop (Sec. 4.2).
  *
  * Readings where the paper is silent or garbled (all listed in the design notes):
  *   R1 drop norm = Euclidean norm of one scalar row (1 x b_K) of the normalised
@@ -34,6 +35,11 @@
  *   R8 GMRES: right preconditioning, modified Gram-Schmidt, Givens rotations,
  *      stop when the Givens residual <= tol * ||b|| and the true residual agrees.
  *   R9 ILU(1,tau) blocking bookkeeping: see orc_partition_ilu1t.
+ *   R22 BILDL pivot block: the mirrored lower triangle, LU with pivoting as in step 3,
+ *      perturbations on the diagonal, D_K = (X + X^T) / 2 for the computed inverse X;
+ *   R23 BILDL storage: l_i in L, the unnormalised t_i as column i of U-breve;
+ *   R24 SQMR: no look-ahead, normwise backward error in the infinity norm, checked after
+ *      every step, x0 = 0.
  */
 #ifndef BILU_ORACLE_H
 #define BILU_ORACLE_H
@@ -50,6 +56,7 @@ typedef struct orc_factor orc_factor;
 #define ORC_OK 0
 #define ORC_NOT_CONVERGED 1
 #define ORC_PERTURBED 2
+#define ORC_BREAKDOWN 3 /* SQMR: sigma or rho vanished */
 #define ORC_ERR_ARG (-1)
 #define ORC_ERR_SINGULAR (-4)
 
@@ -147,6 +154,22 @@ void orc_spmv(int64_t n, const int64_t *rowptr, const int32_t *colind, const dou
 int32_t orc_gmres(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val,
                   const orc_factor *M, const double *b, double *x, double tol, int32_t restart,
                   int32_t maxit, int32_t *iters, double *relres_true, double *hist);
+
+/* BILDL (Sec. 4.2): incomplete block L D L^T of a symmetric A (A must equal A^T entry by
+ * entry, column indices sorted in each row; else ORC_ERR_ARG).  The factor has the BILU
+ * layout: U-breve's column i holds the unnormalised row t_i of L, so orc_bilu_apply applies
+ * M^{-1} = (L P L^T)^{-1}. */
+int32_t orc_bildl_factor(int64_t n, const int64_t *rowptr, const int32_t *colind,
+                         const double *val, int32_t nb, const int32_t *bstart, double droptol,
+                         int32_t perturb, double pert_tau, double pert_rho, orc_factor **out);
+
+/* Simplified QMR with the symmetric preconditioner M (NULL: none), stopped on the normwise
+ * backward error ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf) <= tol (Sec. 4.2).
+ * Returns ORC_OK, ORC_NOT_CONVERGED (maxit) or ORC_BREAKDOWN; hist (maxit + 1 entries, or
+ * NULL) receives the backward error after every step. */
+int32_t orc_sqmr(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val,
+                 const orc_factor *M, const double *b, double *x, double tol, int32_t maxit,
+                 int32_t *iters, double *berr, double *hist);
 
 #ifdef __cplusplus
 }

@@ -341,6 +341,23 @@ def elasticity3d(side: int = 48, seed: int = 2, block: int = 63) -> Workload:
     return Workload(f"elasticity_q1_{side}^3x3", A, rhs_ones(A), 1e-2, 63, "fixed", block)
 
 
+def elasticity3d_shifted(side: int = 48, seed: int = 2, block: int = 63, shift: float = 0.3) -> Workload:
+    """Symmetric indefinite operator: the Q1 elasticity matrix K of elasticity3d (same seed),
+    made exactly symmetric as (K + K^T) / 2, minus shift times its diagonal, so that the
+    eigenvalues of diag(K)^{-1/2} K diag(K)^{-1/2} below the shift turn negative.  It stands in
+    for the symmetric indefinite af_shell matrices of the paper's BILDL experiments (sheet
+    metal forming; not available here).  Right-hand side A * ones; drop tolerance 1e-2."""
+    import scipy.sparse as sp
+    K = elasticity3d(side, seed, block).A
+    Ks = sp.csr_matrix((K.val, K.colind, K.rowptr), shape=(K.n, K.n))
+    S = (Ks + Ks.T).tocsr() * 0.5
+    S = (S - shift * sp.diags(S.diagonal())).tocsr()
+    S.sum_duplicates()
+    S.sort_indices()
+    A = CSR(S.shape[0], S.indptr.astype(np.int64), S.indices.astype(np.int32), S.data.astype(np.float64))
+    return Workload(f"elasticity_q1_shifted_{side}^3x3", A, rhs_ones(A), 1e-2, 63, "fixed", block, gmres_tol=1e-6)
+
+
 def laplace27_4dof(side: int = 64, seed: int = 3, block: int = 64) -> Workload:
     """Q1 27-point scalar diffusion operator (kappa log-uniform in [1e-3, 1e3] per element,
     seed) on side^3 interior nodes, coupled across 4 unknowns per node by the Kronecker product

@@ -18,7 +18,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PIN_TESTS = ["test_oracle.py", "test_partition_oracle.py", "test_block_check_oracle.py", "test_skip_oracle.py",
              "test_golden.py", "test_cosine_oracle.py", "test_mwm_oracle.py", "test_nd_oracle.py",
-             "test_aggregation_oracle.py"]
+             "test_aggregation_oracle.py", "test_bildl_oracle.py", "test_sqmr_oracle.py"]
 ORACLE_FILES = ["__init__.py", "bilu_oracle.c", "bilu_oracle.h", "block_check.py", "skip_oracle.py",
                 "cosine_oracle.py", "mwm_oracle.py", "nd_oracle.py"]
 
@@ -70,6 +70,26 @@ MUTANTS = [
     ("merged producer read with its unmerged width", C,
      "int bJ = F->bstart[J + 1] - F->bstart[J]; /* a merged producer spans its void predecessor */",
      "int bJ = bstart[J + 1] - bstart[J];", 1),
+    # BILDL, the symmetric variant (Sec. 4.2)
+    ("bildl: pivot block mirrored from the upper triangle", C,
+     "for (int c = r + 1; c < b; ++c) P[r * b + c] = P[c * b + r];",
+     "for (int c = r + 1; c < b; ++c) P[c * b + r] = P[r * b + c];", 1),
+    ("bildl: D_K symmetrised on one side only", C, "                    D[c * b + r] = v;\n", "", 1),
+    ("bildl: U-breve column holds the normalised row", C,
+     "memcpy(F->Uval.a + F->Uval.n, trow, (size_t)b * sizeof(double));",
+     "memcpy(F->Uval.a + F->Uval.n, ell, (size_t)b * sizeof(double));", 1),
+    ("bildl: breakdown perturbed off the diagonal", C, "if (sym) k = bad;", "", 1),
+    # simplified QMR (Sec. 4.2)
+    ("sqmr: alpha inverted", C, "double alpha = rho / sigma;", "double alpha = sigma / rho;", 1),
+    ("sqmr: theta from the previous residual", C, "double theta1 = sqrt(dot(n, r, r)) / tau;",
+     "double theta1 = sqrt(dot(n, t, t)) / tau;", 1),
+    ("sqmr: d without the c^2 theta^2 term", C, "d[i] = c * c * theta * theta * d[i] + c * c * alpha * q[i];",
+     "d[i] = c * c * alpha * q[i];", 1),
+    ("sqmr: tau not damped by c", C, "tau = tau * theta1 * c;", "tau = tau * theta1;", 1),
+    ("sqmr: beta inverted", C, "double beta = rho1 / rho;", "double beta = rho / rho1;", 1),
+    ("sqmr: direction without the preconditioner", C, "for (int64_t i = 0; i < n; ++i) q[i] = u[i] + beta * q[i];",
+     "for (int64_t i = 0; i < n; ++i) q[i] = r[i] + beta * q[i];", 1),
+    ("sqmr: backward error without ||b||", C, "double den = anorm * xmax + bmax;", "double den = anorm * xmax;", 1),
     # perturbation (Sec. 3.6)
     ("sign(0) = -1", C, "return x >= 0.0 ? 1.0 : -1.0;", "return x > 0.0 ? 1.0 : -1.0;", 1),
     ("rho ignored", C, "return d * (1.0 + prho) + sgn_plus(d) * ptau * alpha;",
