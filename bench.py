@@ -45,6 +45,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "BILU factor+GMRES seconds to rel. residual 1e-8"
 UNIT = "s"
+METRIC_SYM = "BILDL factor+SQMR seconds to backward error 1e-6"
+SQMR_TOL = 1e-6  # the paper's stop for SQMR (normwise backward error)
 REF_BUDGET_S = 150.0  # the reference arm's timed steps: full oracle steps while they fit in this
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12  # nominal: 152 SMs x 4 FP64 flop/clk/SM x 2070 MHz max SM clock
 
@@ -55,7 +57,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
-    ap.add_argument("--workload", choices=["cd3d", "elasticity", "laplace27x4", "cd3d_rows_scrambled"], default="cd3d",
+    ap.add_argument("--workload", choices=["cd3d", "elasticity", "laplace27x4", "cd3d_rows_scrambled",
+                                           "elasticity_shifted"], default="cd3d",
                     help="cd3d: 3D upwind convection-diffusion (the benchmark); elasticity: Q1 3-dof/node "
                          "(mixed-precision configuration, --side 48 --block 63); laplace27x4: Q1 27-point, "
                          "4 dof/node (learned-skip evaluation, --side 64)")
@@ -84,6 +87,10 @@ def parse():
                     help="progressive aggregation (Sec. 3.5): merge consecutive blocks up to this size (0: off)")
     ap.add_argument("--batch", type=int, default=0,
                     help="factor + solve this many uneven 2D/3D matrices in one batched launch instead")
+    ap.add_argument("--symmetric", action="store_true",
+                    help="BILDL (incomplete block L D L^T, Sec. 4.2) solved by SQMR to the backward error "
+                         "1e-6 instead of BILU + GMRES(30); needs a symmetric workload (elasticity_shifted)")
+    ap.add_argument("--droptol", type=float, default=None, help="drop tolerance (default: the workload's)")
     ap.add_argument("--compare-fp64", action="store_true",
                     help="also time plain FP64 factor + GMRES (no skip) on the same matrix, order and schedule, "
                          "and report the variant's speedup over it")
@@ -130,12 +137,18 @@ def workload(args):
     the learned skip is evaluated on."""
     from paper_1908_10169_gb300 import workloads as W
     if args.workload == "elasticity":
-        return W.elasticity3d(side=args.side, seed=2, block=args.block)
-    if args.workload == "laplace27x4":
-        return W.laplace27_4dof(side=args.side, seed=3, block=args.block)
+        w = W.elasticity3d(side=args.side, seed=2, block=args.block)
+    elif args.workload == "laplace27x4":
+        w = W.laplace27_4dof(side=args.side, seed=3, block=args.block)
     if args.workload == "cd3d_rows_scrambled":
-        return W.rows_scrambled(W.cd3d(side=args.side, seed=1, block=args.block), seed=5)
-    return W.cd3d(side=args.side, seed=1, block=args.block)
+        w = W.rows_scrambled(W.cd3d(side=args.side, seed=1, block=args.block), seed=5)
+    elif args.workload == "elasticity_shifted":
+        w = W.elasticity3d_shifted(side=args.side, seed=2, block=args.block)
+    else:
+        w = W.cd3d(side=args.side, seed=1, block=args.block)
+    if getattr(args, "droptol", None) is not None:
+        w = dataclasses.replace(w, droptol=args.droptol)
+    return w
 
 
 class Prepared:
@@ -216,6 +229,9 @@ def config(args, w, extra=None):
          "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{args.gpus}"}
     if getattr(args, "aggregate", 0):
         c["aggregate_max"] = args.aggregate
+    if getattr(args, "symmetric", False):
+        c["factorization"] = "BILDL (incomplete block L D L^T, symmetric variant)"
+        c["gmres"] = f"none: SQMR to the normwise backward error {SQMR_TOL}, x0 = 0, b = A*1"
     if getattr(args, "precision", "fp64") == "bf16":
         c["update_tiles"] = "FP32 units" if getattr(args, "no_tensor", False) else "tensor cores (tcgen05, BF16 x BF16 -> FP32)"
 
@@ -330,13 +346,17 @@ def fp64_gemm_tflops(dev, n=4096, reps=5):
         return None
 
 
-def oracle_step(w, bstart):
-    """One full step of the FP64 CPU oracle (single thread): factor + GMRES(30)."""
+def oracle_step(w, bstart, symmetric=False):
+    """One full step of the FP64 CPU oracle (single thread): factor + GMRES(30), or with
+    symmetric BILDL + SQMR to the backward error SQMR_TOL."""
     import oracle as O
     t0 = time.perf_counter()
-    F = O.bilu_factor(w.A, bstart, w.droptol)
+    F = O.bildl_factor(w.A, bstart, w.droptol) if symmetric else O.bilu_factor(w.A, bstart, w.droptol)
     t1 = time.perf_counter()
-    r = O.gmres(w.A, F, w.b, tol=w.gmres_tol, restart=w.restart)
+    if symmetric:
+        r = O.sqmr(w.A, F, w.b, tol=SQMR_TOL, maxit=10000)
+    else:
+        r = O.gmres(w.A, F, w.b, tol=w.gmres_tol, restart=w.restart)
     t2 = time.perf_counter()
     F.free()
     return t2 - t0, t1 - t0, t2 - t1, r.iters
@@ -433,18 +453,20 @@ def run_reference(args):
     sprep = preprocess(sargs, small)
     small = dataclasses.replace(small, A=sprep.A, b=sprep.b)
     for _ in range(args.warmup):  # warm-up on a small case of the same kind
-        oracle_step(small, sprep.bstart if sprep.bstart is not None else O.partition_fixed(small.A.n, 16))
+        oracle_step(small, sprep.bstart if sprep.bstart is not None else O.partition_fixed(small.A.n, 16),
+                    args.symmetric)
     # one full step on the workload itself (the last warm-up step); when K of them would take
     # longer than REF_BUDGET_S, every timed step is a bounded sample instead: the oracle's full
     # step on the same kind of problem with 3/4 of the side, scaled by the ratio of the two
     # measured once here
-    t_full, _, _, iters = oracle_step(w, bs)
-    sample_note = "full step (oracle factor + GMRES, FP64 arithmetic, every candidate computed) on the same matrix"
+    t_full, _, _, iters = oracle_step(w, bs, args.symmetric)
+    sample_note = ("full step (oracle factor + " + ("SQMR" if args.symmetric else "GMRES") +
+                   ", FP64 arithmetic, every candidate computed) on the same matrix")
     times = []
     if t_full * args.steps <= REF_BUDGET_S:
         times.append(t_full)
         for _ in range(args.steps - 1):
-            t, tf, tg, iters = oracle_step(w, bs)
+            t, tf, tg, iters = oracle_step(w, bs, args.symmetric)
             times.append(t)
         times = times[:args.steps]
     else:
@@ -454,15 +476,15 @@ def run_reference(args):
         sp_ = preprocess(sa, ws_)
         ws_ = dataclasses.replace(ws_, A=sp_.A, b=sp_.b)
         bs_ = sp_.bstart if sp_.bstart is not None else O.partition_fixed(ws_.A.n, args.block)
-        t_cal = oracle_step(ws_, bs_)[0]
+        t_cal = oracle_step(ws_, bs_, args.symmetric)[0]
         for _ in range(args.steps):
-            times.append(oracle_step(ws_, bs_)[0] * t_full / t_cal)
+            times.append(oracle_step(ws_, bs_, args.symmetric)[0] * t_full / t_cal)
         sample_note = (f"each timed step: the oracle's full step (factor + GMRES, FP64) on the {side_s}^3 problem of "
                        f"the same kind and host analysis, scaled by t({args.side}^3) / t({side_s}^3) = "
                        f"{t_full:.2f} s / {t_cal:.2f} s, both measured once before the timed steps (a full step on "
                        f"the workload takes {t_full:.1f} s, {args.steps} of them would exceed {REF_BUDGET_S:.0f} s)")
     v = sum(times) / len(times)
-    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+    line = {"impl": "reference", "metric": METRIC_SYM if args.symmetric else METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config(args, w, {"gmres_iters": iters}),
@@ -499,7 +521,8 @@ def run_gpu(args):
                                    skip={"none": B.BILU_SKIP_NONE, "bound": B.BILU_SKIP_BOUND,
                                          "learned": B.BILU_SKIP_LEARNED}[args.skip],
                                    schedule={"chain": B.BILU_SCHED_CHAIN, "tree": B.BILU_SCHED_TREE}[args.schedule],
-                                   group_ctas=args.group_ctas, aggregate_max=args.aggregate)
+                                   group_ctas=args.group_ctas, aggregate_max=args.aggregate,
+                                   symmetric=1 if args.symmetric else 0)
     learned = None
     if args.skip == "learned":  # train the classifier first (not timed)
         from paper_1908_10169_gb300 import learned_skip as LS
@@ -530,11 +553,16 @@ def run_gpu(args):
             import torch.distributed as dist
             dist.barrier()
 
+    def solve(c_, b_, x_):
+        if args.symmetric:
+            return B.sqmr_solve(c_, b_, x_, SQMR_TOL, 10000)
+        return B.gmres_solve(c_, b_, x_, w.gmres_tol, w.restart, 10000)
+
     def step():
         B.bilu_factor(ctx, w.droptol)
         with torch.cuda.stream(stream):
             x.zero_()
-        return B.gmres_solve(ctx, b, x, w.gmres_tol, w.restart, 10000)
+        return solve(ctx, b, x)
 
     for _ in range(args.warmup):
         step()
@@ -561,7 +589,7 @@ def run_gpu(args):
             st = B.bilu_stats(ctx)
             tf.append(st.t_factor_ms)
             ts.append(info.t_solve_ms)
-            infos.append((info.iters, info.restarts, info.relres_true))
+            infos.append((info.iters, getattr(info, "restarts", 0), info.relres_true))
     st = B.bilu_stats(ctx)
     launches = (st.kernel_launches - launches0) / args.steps
     ms = sum(times) / len(times)
@@ -602,7 +630,8 @@ def run_gpu(args):
     fp64_meas = fp64_gemm_tflops(dev)
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    applies_per_step = iters + restarts  # one per Arnoldi step, one per cycle for x
+    # GMRES: one per Arnoldi step, one per cycle for x; SQMR: one per step and one at the start
+    applies_per_step = iters + (1 if args.symmetric else restarts)
     share_factor = t_factor / ms
     share_apply = applies_per_step * t_apply / ms
     traffic = load_traffic()
@@ -658,13 +687,13 @@ def run_gpu(args):
                     B.bilu_analyze_partition(ctx2, n, p2.A.rowptr, p2.A.colind, p2.A.val, p2.bstart, params)
                 B.bilu_factor(ctx2, w.droptol)
                 h_x.zero_()
-                B.gmres_solve(ctx2, hb, h_x, w.gmres_tol, w.restart, 10000)
+                solve(ctx2, hb, h_x)
                 p2.to_original(h_x.numpy())
             else:
                 B.bilu_analyze(ctx2, n, h_rp, h_ci, h_va, params)
                 B.bilu_factor(ctx2, w.droptol)
                 h_x.zero_()
-                B.gmres_solve(ctx2, h_b, h_x, w.gmres_tol, w.restart, 10000)
+                solve(ctx2, h_b, h_x)
             torch.cuda.synchronize()
             if k > 0:
                 et.append(time.perf_counter() - t0)
@@ -677,9 +706,11 @@ def run_gpu(args):
         import oracle as O
         cores, model = cpu_desc()
         wp = dataclasses.replace(w, A=prep.A, b=prep.b)
-        t, tfo, tgo, it_o = oracle_step(wp, prep.bstart if prep.bstart is not None else O.partition_fixed(n, args.block))
+        t, tfo, tgo, it_o = oracle_step(wp, prep.bstart if prep.bstart is not None else O.partition_fixed(n, args.block),
+                                        args.symmetric)
         cpu = {"value": t, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"one full step (oracle factor {tfo:.1f} s + GMRES {tgo:.1f} s, {it_o} iters) on the "
+               "sample": f"one full step (oracle factor {tfo:.1f} s + {'SQMR' if args.symmetric else 'GMRES'} "
+                         f"{tgo:.1f} s, {it_o} iters) on the "
                          f"same matrix; host {model}, {cores} cores visible, 1 used",
                "gmres_iters": it_o}
     plain = None
@@ -710,6 +741,7 @@ def run_gpu(args):
         pms = sum(pt) / len(pt)
         plain = {"ms_per_step": pms, "factor_ms": s4.t_factor_ms, "solve_ms": i4.t_solve_ms, "gmres_iters": i4.iters,
                  "schedule": "tree" if p4.schedule == B.BILU_SCHED_TREE else "chain",
+                 "method": "BILU + GMRES(30), rel. residual %g" % w.gmres_tol,
                  "speedup_of_this_line": pms / ms, "factor_speedup": s4.t_factor_ms / t_factor,
                  "iters_ratio": iters / max(1, i4.iters)}
         B.bilu_destroy(ctx4)
@@ -752,7 +784,7 @@ def run_gpu(args):
         params.skip = B.BILU_SKIP_LEARNED
     B.bilu_destroy(ctx)
     if rank == 0:
-        line = {"metric": METRIC, "value": ms / 1e3 / world, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        line = {"metric": METRIC_SYM if args.symmetric else METRIC, "value": ms / 1e3 / world, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
                 "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32+f64", "bf16": "bf16+f32+f64"}[args.precision],
                 "data": "synthetic",
@@ -947,6 +979,8 @@ def run_batch(args):
 
 def main():
     args = parse()
+    if args.symmetric and args.workload != "elasticity_shifted":
+        raise SystemExit("--symmetric needs a symmetric workload: --workload elasticity_shifted")
     if args.impl == "reference":
         return run_reference(args)
     if args.batch:

@@ -104,7 +104,25 @@ typedef struct {
                             after the factorization, in block order, to the finished factor
                             (every schedule); the sweeps, the solves and bilu_export then use
                             the merged blocks (bilu_get_factor_partition).                    */
+    int32_t symmetric;   /* 1: BILDL, the symmetric variant (Sec. 4.2): A must equal A^T entry
+                            by entry (BILU_ERR_ARG otherwise).  The factor is an incomplete block
+                            L D L^T: only the block columns of L are computed (the row blocks of
+                            U-breve are their transposes, half the update and scaling work), the
+                            pivot block is the lower triangle of P_K mirrored, perturbed on its
+                            diagonal only (Sec. 3.6), and D_K = (X + X^T) / 2 for the computed
+                            inverse X, so that M = L P L^T and the sweeps apply a symmetric
+                            M^{-1}.  Same storage as BILU (U-breve's column i holds L's
+                            unnormalised row i).  Not with a skip mode, sample recording or
+                            aggregation (BILU_ERR_ARG).  0: BILU.                                */
 } bilu_params;
+
+typedef struct {
+    int32_t iters;          /* SQMR steps taken (one product with A, one with M^{-1})    */
+    int32_t breakdown;      /* 1: sigma = q^T A q or rho = r^T M^{-1} r vanished          */
+    double backward_error;  /* ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf) at exit */
+    double relres_true;     /* ||b - A x||_2 / ||b||_2 at exit                            */
+    double t_solve_ms;      /* device time of the solve                                   */
+} sqmr_info;
 
 typedef struct {
     int32_t iters;       /* inner Arnoldi steps taken                                  */
@@ -162,7 +180,7 @@ typedef struct {
 
 /* Fills *p with the defaults: FIXED blocking of 32 (max 64), tau_analyze 1e-2,
  * perturbation on with tau 1e-2 and rho 1e-1 (Sec. 3.6), FP64, no skipping, the chain
- * schedule (group_ctas 0: chosen by the library), no aggregation.
+ * schedule (group_ctas 0: chosen by the library), no aggregation, BILU (symmetric 0).
  * Errors: BILU_ERR_ARG (p NULL). */
 bilu_status bilu_params_default(bilu_params *p);
 
@@ -218,6 +236,24 @@ bilu_status bilu_apply(bilu_ctx *ctx, const double *r, double *z);
  */
 bilu_status gmres_solve(bilu_ctx *ctx, const double *b, double *x, double tol, int32_t restart,
                         int32_t maxit, gmres_info *info);
+
+/*
+ * Simplified QMR (Freund and Nachtigal), the solver the paper pairs with BILDL (Sec. 4.2),
+ * preconditioned with the context's factor (symmetric when it was made with
+ * params.symmetric = 1; A must then be symmetric as well).  No look-ahead.  With the BCG
+ * residual r, direction q and rho = r^T M^{-1} r, one step takes sigma = q^T A q,
+ * alpha = rho / sigma, r -= alpha A q, theta' = ||r|| / tau, c = (1 + theta'^2)^{-1/2},
+ * tau = tau theta' c, d = c^2 theta^2 d + c^2 alpha q, x += d, u = M^{-1} r,
+ * rho' = r^T u, q = u + (rho' / rho) q.  Stops when the normwise backward error of x,
+ * ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf), is <= tol (the paper uses 1e-6),
+ * checked after every step; after maxit steps (BILU_NOT_CONVERGED); or at a breakdown
+ * (sigma or rho zero: BILU_NOT_CONVERGED with info->breakdown = 1).  x holds x0 on entry
+ * and the last iterate on exit; b and x hold n doubles, device or host memory; info may be
+ * NULL.  The steps run as CUDA graphs of 8 steps each; a step after convergence returns at
+ * once.  Errors: BILU_ERR_STATE (no factor), BILU_ERR_ARG (null vector, maxit < 0, tol < 0
+ * or NaN), BILU_ERR_OOM, BILU_ERR_CUDA, BILU_ERR_TIMEOUT (a sweep's bounded wait gave up).
+ */
+bilu_status sqmr_solve(bilu_ctx *ctx, const double *b, double *x, double tol, int32_t maxit, sqmr_info *info);
 
 /*
  * Batched factorization of many independent matrices in one persistent launch.  Every

@@ -29,7 +29,7 @@ BILU_MAX_BLOCK = 64
 
 # every extern "C" symbol that include/bilu.h declares
 EXPORTED = ["bilu_params_default", "bilu_create", "bilu_analyze", "bilu_factor", "bilu_apply",
-            "gmres_solve", "bilu_stats", "bilu_get_partition", "bilu_get_factor_partition", "bilu_export",
+            "gmres_solve", "sqmr_solve", "bilu_stats", "bilu_get_partition", "bilu_get_factor_partition", "bilu_export",
             "bilu_last_error",
             "bilu_debug_set", "bilu_apply_noalloc", "bilu_factor_batch", "gmres_solve_batch",
             "bilu_record_samples", "bilu_get_samples", "bilu_mlp_train", "bilu_mlp_forward", "bilu_mlp_grad",
@@ -50,7 +50,13 @@ class bilu_params(ct.Structure):
     _fields_ = [("blocking", ct.c_int32), ("max_block", ct.c_int32), ("fixed_block", ct.c_int32),
                 ("tau_analyze", ct.c_double), ("perturb", ct.c_int32), ("pert_tau", ct.c_double),
                 ("pert_rho", ct.c_double), ("precision", ct.c_int32), ("skip", ct.c_int32),
-                ("schedule", ct.c_int32), ("group_ctas", ct.c_int32), ("aggregate_max", ct.c_int32)]
+                ("schedule", ct.c_int32), ("group_ctas", ct.c_int32), ("aggregate_max", ct.c_int32),
+                ("symmetric", ct.c_int32)]
+
+
+class sqmr_info(ct.Structure):
+    _fields_ = [("iters", ct.c_int32), ("breakdown", ct.c_int32), ("backward_error", ct.c_double),
+                ("relres_true", ct.c_double), ("t_solve_ms", ct.c_double)]
 
 
 class gmres_info(ct.Structure):
@@ -102,6 +108,7 @@ def lib():
             "bilu_factor": ([P, f64], i32),
             "bilu_apply": ([P, P, P], i32),
             "gmres_solve": ([P, P, P, f64, i32, i32, ct.POINTER(gmres_info)], i32),
+            "sqmr_solve": ([P, P, P, f64, i32, ct.POINTER(sqmr_info)], i32),
             "bilu_stats": ([P, ct.POINTER(bilu_stats_t)], i32),
             "bilu_get_partition": ([P, P], i32),
             "bilu_get_factor_partition": ([P, P], i32),
@@ -451,6 +458,17 @@ def gmres_solve(ctx, b, x, tol: float = 1e-8, restart: int = 30, maxit: int = 10
     """Right-preconditioned GMRES(restart) (Sec. 4); x holds x0 on entry.  The info carries the status."""
     info = gmres_info()
     st = lib().gmres_solve(ctx, _vec(ctx, b, "b"), _vec(ctx, x, "x"), tol, restart, maxit, ct.byref(info))
+    _check(ctx, st, (BILU_OK, BILU_NOT_CONVERGED))
+    info.status = st
+    return info
+
+
+def sqmr_solve(ctx, b, x, tol: float = 1e-6, maxit: int = 10000) -> sqmr_info:
+    """Simplified QMR preconditioned with the context's factor (Sec. 4.2; the symmetric variant
+    BILDL gives a symmetric preconditioner), stopped on the normwise backward error; x holds
+    x0 on entry.  The info carries the status."""
+    info = sqmr_info()
+    st = lib().sqmr_solve(ctx, _vec(ctx, b, "b"), _vec(ctx, x, "x"), tol, maxit, ct.byref(info))
     _check(ctx, st, (BILU_OK, BILU_NOT_CONVERGED))
     info.status = st
     return info

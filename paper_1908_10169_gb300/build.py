@@ -15,7 +15,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbilu.so")
-SOURCES = ["capi.cu", "analyze.cu", "factor.cu", "apply.cu", "gmres.cu", "apply_noalloc.cu", "mlp.cu", "aggregate.cu"]
+SOURCES = ["capi.cu", "analyze.cu", "factor.cu", "apply.cu", "gmres.cu", "apply_noalloc.cu", "mlp.cu", "aggregate.cu",
+           "sqmr.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include")]

@@ -782,6 +782,9 @@ bilu_status analyze_run(bilu_ctx *c, int64_t n, const int64_t *rowptr, const int
         return set_err(c, BILU_ERR_ARG, "group_ctas must be in 0..number of SMs");
     if (p->aggregate_max != 0 && (p->aggregate_max < 2 || p->aggregate_max > BILU_MAX_BLOCK))
         return set_err(c, BILU_ERR_ARG, "aggregate_max must be 0 or in 2..BILU_MAX_BLOCK");
+    if (p->symmetric != 0 && p->symmetric != 1) return set_err(c, BILU_ERR_ARG, "symmetric must be 0 or 1");
+    if (p->symmetric && (p->skip != BILU_SKIP_NONE || p->aggregate_max != 0))
+        return set_err(c, BILU_ERR_ARG, "the symmetric variant takes no skip mode and no aggregation");
 
     const auto t_start = std::chrono::steady_clock::now();
 
@@ -824,6 +827,15 @@ bilu_status analyze_run(bilu_ctx *c, int64_t n, const int64_t *rowptr, const int
     std::vector<int32_t> colptr, rowind;
     std::vector<double> cval;
     build_csc(A, colptr, rowind, cval);
+    if (p->symmetric) {
+        // with strictly increasing columns in every row, A = A^T exactly when its column
+        // storage equals its row storage
+        for (int64_t i = 0; i <= n; ++i)
+            if ((int64_t)colptr[i] != A.rowptr[i]) return set_err(c, BILU_ERR_ARG, "symmetric variant: A is not symmetric");
+        for (int64_t e = 0; e < nnz; ++e)
+            if (rowind[e] != A.colind[e] || cval[e] != A.val[e])
+                return set_err(c, BILU_ERR_ARG, "symmetric variant: A is not symmetric");
+    }
 
     std::vector<int32_t> bstart;
     if (given && p->blocking == BILU_BLOCKING_ILU1T && n > 0) {
@@ -844,6 +856,7 @@ bilu_status analyze_run(bilu_ctx *c, int64_t n, const int64_t *rowptr, const int
     factor_free(c);
     apply_free(c);
     gmres_free(c);
+    sqmr_free(c);
     matrix_free(c);
     c->state = 0;
     c->p = *p;

@@ -116,6 +116,11 @@ struct bilu_ctx {
     int64_t grp_key[3] = {0, 0, 0}; // capT, prodcap, capXS it was carved for
     int32_t *d_tree0 = nullptr, *d_tree = nullptr;  // initial / live: pending, queue, control words
     int64_t capA[4] = {0, 0, 0, 0}; // arena capacities (rows L, values L, columns U, values U)
+    // capacities a factorization ended with, kept across re-analysis: a matrix of the same
+    // size, nonzero count, partition and mode starts from them instead of re-running to grow
+    int64_t hint_key[5] = {-1, -1, -1, -1, -1};
+    int64_t hint_cap[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int32_t hint_prodcap = 0;
     int32_t *d_aLrow = nullptr, *d_aUcol = nullptr;
     double *d_aLval = nullptr, *d_aUval = nullptr, *d_aUhval = nullptr, *d_aLnrm = nullptr, *d_aUnrm = nullptr;
     int64_t *d_aptr = nullptr;      // 6 x nb: L begin, L end, L value begin, U begin, U end, U value begin
@@ -153,6 +158,15 @@ struct bilu_ctx {
     int gm_graph_restart = 0;
     const double *gm_graph_b = nullptr;
     double *gm_graph_x = nullptr;
+
+    // sqmr workspace: r, t, q, d, u, residual, b, x; partials; scalar / integer state
+    int64_t sq_n = -1;
+    double *d_sq = nullptr, *d_sqpart = nullptr, *d_sqs = nullptr;
+    int32_t *d_sqi = nullptr;
+    double *h_sqs = nullptr;
+    int32_t *h_sqi = nullptr;
+    cudaGraphExec_t sq_graph = nullptr;
+    int64_t sq_graph_kernels = 0;
 
     // learned skip: classifier (FP32 normalisation, FP16 weights) and sample recording
     float *d_mlp_norm = nullptr;
@@ -217,6 +231,7 @@ void dev_free(T *&p) {
 // Library-internal entry points implemented in the .cu files.
 bilu_status factor_run(bilu_ctx *c, double droptol);
 bilu_status factor_alloc(bilu_ctx *c);
+void factor_remember_pools(bilu_ctx *c);
 void factor_free(bilu_ctx *c);
 bilu_status apply_run(bilu_ctx *c, const double *d_r, double *d_z);
 bilu_status apply_launch(bilu_ctx *c, const double *d_r, double *d_z, const int32_t *skip);
@@ -225,6 +240,10 @@ void apply_free(bilu_ctx *c);
 bilu_status gmres_run(bilu_ctx *c, const double *d_b, double *d_x, double tol, int restart,
                       int maxit, gmres_info *info);
 void gmres_free(bilu_ctx *c);
+void gmres_drop_graph(bilu_ctx *c);
+void sqmr_drop_graph(bilu_ctx *c);
+bilu_status sqmr_run(bilu_ctx *c, const double *b, double *x, double tol, int maxit, sqmr_info *info);
+void sqmr_free(bilu_ctx *c);
 bilu_status aggregate_run(bilu_ctx *c);
 void aggregate_free(bilu_ctx *c);
 bilu_status gmres_batch_run(bilu_ctx *const *ctxs, int count, const double *const *b, double *const *x, double tol,

@@ -90,6 +90,7 @@ void bilu_destroy(bilu_ctx *c) {
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     gmres_free(c);
+    sqmr_free(c);
     apply_free(c);
     factor_free(c);
     matrix_free(c);
@@ -178,9 +179,13 @@ bilu_status bilu_factor(bilu_ctx *c, double droptol) {
         return set_err(c, BILU_ERR_STATE, "BILU_SKIP_LEARNED needs a model (bilu_set_skip_model)");
     BILU_CUDA(c, cudaSetDevice(c->device));
     c->state = 1;
-    gmres_free(c);  // captured graphs refer to the previous factor
+    gmres_drop_graph(c);  // captured graphs refer to the previous factor
+    sqmr_drop_graph(c);
+    if (c->p.symmetric && c->rec_cap > 0)
+        return set_err(c, BILU_ERR_ARG, "the symmetric variant records no samples");
     bilu_status st = factor_run(c, droptol);
     if (st < 0) return st;
+    factor_remember_pools(c);
     bilu_status sg = aggregate_run(c);
     if (sg < 0) return sg;
     bilu_status sa = apply_alloc(c);
@@ -230,6 +235,17 @@ bilu_status gmres_solve(bilu_ctx *c, const double *b, double *x, double tol, int
     return gmres_run(c, b, x, tol, restart, maxit, info);
 }
 
+bilu_status sqmr_solve(bilu_ctx *c, const double *b, double *x, double tol, int32_t maxit, sqmr_info *info) {
+    if (!c) return BILU_ERR_ARG;
+    c->err.clear();
+    if (c->state < 2) return set_err(c, BILU_ERR_STATE, "sqmr_solve before bilu_factor");
+    if (c->n > 0 && (!b || !x)) return set_err(c, BILU_ERR_ARG, "null vector");
+    if (info) std::memset(info, 0, sizeof(*info));
+    if (c->n == 0) return BILU_OK;
+    BILU_CUDA(c, cudaSetDevice(c->device));
+    return sqmr_run(c, b, x, tol, maxit, info);
+}
+
 bilu_status bilu_factor_batch(bilu_ctx *const *ctxs, int32_t count, double droptol) {
     if (!ctxs || count < 1) return BILU_ERR_ARG;
     bilu_ctx *c0 = ctxs[0];
@@ -252,7 +268,8 @@ bilu_status bilu_factor_batch(bilu_ctx *const *ctxs, int32_t count, double dropt
     BILU_CUDA(c0, cudaSetDevice(c0->device));
     for (int32_t i = 0; i < count; ++i) {
         ctxs[i]->state = 1;
-        gmres_free(ctxs[i]);
+        gmres_drop_graph(ctxs[i]);
+        sqmr_drop_graph(ctxs[i]);
     }
     double ms = 0.0;
     bilu_status st = factor_batch_run(ctxs, count, droptol, &ms);

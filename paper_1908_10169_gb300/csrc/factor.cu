@@ -109,6 +109,8 @@ struct FactorArgs {
     int32_t trcap;               // most candidate rows per accumulation tile (4..TRMAX)
     int32_t tc;                  // 1: BF16 update tiles on the tensor cores (tcgen05, TMEM)
     int32_t skip_bound;          // 1: skip candidates that the norm bound proves dropped
+    int32_t sym;                 // 1: BILDL (symmetric A): the L side only; U-breve's columns
+                                 // are L's rows, the pivot block and D_K symmetric
     double *Lnrm, *Unrm;         // per kept row of L: ||l_i||; per kept column of U-breve: ||u_j||
     double *dcolsq;              // squared column norms of D_K (b entries)
     uint32_t *pivdone;           // pivot-row tiles finished for the current block
@@ -168,6 +170,27 @@ __device__ __forceinline__ int find_owner(const int32_t *off, int pcnt, int f) {
         if (off[mid] <= f) lo = mid; else hi = mid - 1;
     }
     return lo;
+}
+
+// BILDL has no row-block pass, whose phase A sorts the list of blocks with kept L rows in B_K;
+// the forward sweep folds those producers in list order, so under the tree schedule (appends
+// in any order) the list is sorted here instead.  Shared scratch: 2 PMAX ints.
+__device__ void sort_row_producers(const FactorArgs &a, int K, char *smem) {
+    int32_t *plist = a.prodU + (int64_t)K * a.prodcap;
+    const int pcnt = min(min(ldcg(a.prodUcnt + K), a.prodcap), PMAX);  // an overflow is phase A's to report
+    if (pcnt < 2) return;
+    int32_t *sl = (int32_t *)smem, *st = sl + PMAX;
+    for (int t = threadIdx.x; t < pcnt; t += NT) sl[t] = ldcg(plist + t);
+    __syncthreads();
+    for (int t = threadIdx.x; t < pcnt; t += NT) {  // rank sort: the entries are distinct
+        const int v = sl[t];
+        int r = 0;
+        for (int u = 0; u < pcnt; ++u) r += sl[u] < v;
+        st[r] = v;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < pcnt; t += NT) plist[t] = st[t];
+    __syncthreads();
 }
 
 __device__ void phase_A(const FactorArgs &a, int K, bool Lside, char *smem) {
@@ -1198,6 +1221,13 @@ __device__ void phase_C(const FactorArgs &a, int K, char *smem) {
     }
     if (tid == 0) sh[2] = 0;
     __syncthreads();
+    if (a.sym) {  // BILDL: the lower triangle defines the symmetric pivot block
+        for (int e = tid; e < b * b; e += NT) {
+            const int r = e / b, c = e - r * b;
+            if (c > r) P[r * PS + c] = P[c * PS + r];
+        }
+        __syncthreads();
+    }
     if (a.perturb) {
         // Sec. 3.6: all-zero columns, then all-zero rows, get their diagonal entry perturbed
         // (the diagonal wins the tie with the other, zero, entries).
@@ -1291,7 +1321,7 @@ __device__ void phase_C(const FactorArgs &a, int K, char *smem) {
             int k = 0;
             for (int i = 1; i < b; ++i)
                 if (absbits(P[i * PS + bad]) > absbits(P[k * PS + bad])) k = i;
-            if (2.0 * fabs(P[bad * PS + bad]) >= fabs(P[k * PS + bad])) k = bad;
+            if (2.0 * fabs(P[bad * PS + bad]) >= fabs(P[k * PS + bad]) || a.sym) k = bad;  // BILDL: the diagonal
             P[k * PS + bad] = perturbed(P[k * PS + bad], a.pert_tau, a.pert_rho, a.alpha);
             sh[2] += 1;
         }
@@ -1402,7 +1432,8 @@ __device__ void phase_D(const FactorArgs &a, int K, char *smem) {
     const double *D = a.Dinv + a.Dptr[K];
     for (int e = tid; e < b * b; e += NT) {
         const int r = e / b, c = e - r * b;
-        Ds[r * PS + c] = (TA)ldcg(D + e);
+        // BILDL: D_K = (X + X^T) / 2 (phase E stores it)
+        Ds[r * PS + c] = a.sym ? (TA)((ldcg(D + e) + ldcg(D + c * b + r)) * 0.5) : (TA)ldcg(D + e);
     }
     __syncthreads();
     for (int k = warp; k < b; k += NW) {
@@ -1451,8 +1482,14 @@ __device__ void phase_D(const FactorArgs &a, int K, char *smem) {
             l0 += l0b;
             l1 += l1b;
             const double nrm2 = warp_sum((double)l0 * (double)l0 + (double)l1 * (double)l1);
-            if (lane < b) t[lane] = l0;
-            if (lane + 32 < b) t[lane + 32] = l1;
+            // BILDL keeps t_i (U-breve's column i) and writes l_i beside it
+            TA *dst = a.sym ? (TA *)a.TUh + (int64_t)slot * b : t;
+            if (a.sym) {
+                const double tn2 = warp_sum((double)t0 * (double)t0 + (double)t1 * (double)t1);
+                if (lane == 0) a.nrmU[slot] = sqrt(tn2);
+            }
+            if (lane < b) dst[lane] = l0;
+            if (lane + 32 < b) dst[lane + 32] = l1;
             if (lane == 0) {
                 const double nr = sqrt(nrm2);
                 a.keepL[slot] = nr > a.tau ? 1 : 0;
@@ -1514,8 +1551,19 @@ __device__ void phase_E(const FactorArgs &a, int K, char *smem) {
     const int s0 = a.bstart[K], s1 = a.bstart[K + 1], b = s1 - s0;
     const int mL = ldcg(a.kst + 0), mU = ldcg(a.kst + 1);
     const int nLc = mL - b;
-    const int tL = (nLc + 31) >> 5, tU = (mU + 31) >> 5;
+    const int tL = (nLc + 31) >> 5, tU = a.sym ? tL : (mU + 31) >> 5;  // BILDL: the U side mirrors L
     const int cr = crank(a);
+    if (a.sym && cr == 0) {  // BILDL: store D_K = (X + X^T) / 2, as phase D used it
+        double *D = a.Dinv + a.Dptr[K];
+        for (int e = tid; e < b * b; e += NT) {
+            const int r = e / b, c = e - r * b;
+            if (c > r) {
+                const double v = (ldcg(D + e) + ldcg(D + c * b + r)) * 0.5;
+                D[e] = v;
+                D[c * b + r] = v;
+            }
+        }
+    }
     // tiles of 32 candidates, L side then U side in one sequence: CTA cr takes tiles cr,
     // cr + G, ... of it, so the two sides' tiles go to different CTAs
     const bool has_work = cr == 0 || cr < tL + tU;
@@ -1548,6 +1596,7 @@ __device__ void phase_E(const FactorArgs &a, int K, char *smem) {
         block_excl_scan(uk, ws, &keptU);
         block_excl_scan(sk, ws, &skipped);
         block_excl_scan(bk, ws, &bounded);
+        if (a.sym) keptU = keptL;
     }
     const bool overflow = Lbase + keptL > a.capLrow || LVbase + (int64_t)keptL * b > a.capLval ||
                           Ubase + keptU > a.capUcol || UVbase + (int64_t)keptU * b > a.capUval;
@@ -1587,10 +1636,12 @@ __device__ void phase_E(const FactorArgs &a, int K, char *smem) {
         const int gofs = isL ? 0 : tL;                           // sequence index of the side's first tile
         const int tfirst = ((cr - gofs) % a.G + a.G) % a.G;      // this CTA's first tile of the side
         if (tfirst >= ntile) continue;  // uniform in the CTA
-        const int sfirst = isL ? b : 0, send = isL ? mL : mU;
-        const int32_t *kp = isL ? a.keepL : a.keepU;
-        const int32_t *rows = isL ? a.rowsL : a.rowsU;
-        const TA *Tb = (const TA *)(isL ? a.TL : a.TU);
+        // BILDL: both passes read the L candidates; L takes l_i (in TUh), U-breve t_i (in TL)
+        const bool Lc = isL || a.sym;
+        const int sfirst = Lc ? b : 0, send = Lc ? mL : mU;
+        const int32_t *kp = Lc ? a.keepL : a.keepU;
+        const int32_t *rows = Lc ? a.rowsL : a.rowsU;
+        const TA *Tb = (const TA *)(isL ? (a.sym ? a.TUh : a.TL) : (a.sym ? a.TL : a.TU));
         TS *pool = (TS *)(isL ? a.Lval : a.Uval) + (isL ? LVbase : UVbase);
         const TA *Th = (const TA *)a.TUh;                        // U side: the normalised columns
         TS *hpool = (TS *)a.Uhval + UVbase;
@@ -1798,7 +1849,15 @@ __device__ bool block_step(const FactorArgs &a, int K, char *smem, StepTimers &t
     if (cr == 0) phase_A(a, K, true, smem);
     if (cr == (1 % a.G)) {
         __syncthreads();
-        phase_A(a, K, false, smem);
+        if (!a.sym) {
+            phase_A(a, K, false, smem);
+        } else {  // BILDL: no row block (it is the column block's transpose)
+            if (threadIdx.x == 0) {
+                a.kst[1] = 0;
+                a.kst[3] = 0;
+            }
+            if (a.sortprod) sort_row_producers(a, K, smem);
+        }
     }
     trace_at(a, 2, 1);
     if (!grid_barrier(a.bar, G, a.status, a.spin_limit, a.info, 1, trace_hb(a))) return false;
@@ -1809,7 +1868,7 @@ __device__ bool block_step(const FactorArgs &a, int K, char *smem, StepTimers &t
     const int mL = max(b, min((int)ldcg(a.kst + 0), capT)), mU = max(0, min((int)ldcg(a.kst + 1), capT));
     const int nrestL = mL - b, nrest = nrestL + mU;
     const int npt = (b + TRP - 1) / TRP;
-    if (a.arena && cr == 0 && threadIdx.x == 0) arena_reserve(a, K, nrestL, mU, b);
+    if (a.arena && cr == 0 && threadIdx.x == 0) arena_reserve(a, K, nrestL, a.sym ? nrestL : mU, b);
     {
         const int W = a.G > 1 ? a.G - 1 : 1;  // CTAs taking tiles (CTA 0 factors the pivot block)
         const int np = pivot_parts(W, npt);    // producer slices per pivot-row tile
@@ -2325,6 +2384,29 @@ int g_debug_poison = 0;             // factor storage is filled with NaN before 
 int g_debug_no_trunk = 0;           // the tree schedule leaves no trunk to the whole grid
 int g_debug_trace = 0;              // the tree schedule prints one line per run to stderr
 
+static void hint_key_of(const bilu_ctx *c, int64_t key[5]) {
+    key[0] = c->n;
+    key[1] = c->nnz;
+    key[2] = c->nb;
+    key[3] = c->p.precision;
+    key[4] = c->p.symmetric;
+}
+
+static bool hint_matches(const bilu_ctx *c) {
+    int64_t key[5];
+    hint_key_of(c, key);
+    for (int q = 0; q < 5; ++q)
+        if (key[q] != c->hint_key[q]) return false;
+    return true;
+}
+
+void factor_remember_pools(bilu_ctx *c) {
+    hint_key_of(c, c->hint_key);
+    const int64_t caps[8] = {c->capLrow, c->capLval, c->capUcol, c->capUval, c->capA[0], c->capA[1], c->capA[2], c->capA[3]};
+    for (int q = 0; q < 8; ++q) c->hint_cap[q] = caps[q];
+    c->hint_prodcap = c->prodcap;
+}
+
 bilu_status factor_alloc(bilu_ctx *c) {
     factor_free(c);
     const int64_t n = std::max<int64_t>(c->n, 1), nb = std::max<int64_t>(c->nb, 1);
@@ -2336,6 +2418,14 @@ bilu_status factor_alloc(bilu_ctx *c) {
     c->capT = n + BILU_MAX_BLOCK;
     c->prodcap = 64;
     c->capXS = 4 * c->capT;
+    if (hint_matches(c)) {  // the capacities the same kind of factorization ended with
+        c->capLrow = std::max(c->capLrow, c->hint_cap[0]);
+        c->capLval = std::max(c->capLval, c->hint_cap[1]);
+        c->capUcol = std::max(c->capUcol, c->hint_cap[2]);
+        c->capUval = std::max(c->capUval, c->hint_cap[3]);
+        c->prodcap = std::max(c->prodcap, c->hint_prodcap);
+        c->capXS = std::max<int64_t>(c->capXS, (int64_t)c->capT * (c->prodcap / 16));
+    }
     if (g_debug_small_pools) {  // test hook: exercise the re-run paths
         c->capLval = c->capUval = c->capLrow = c->capUcol = 1024;
         c->prodcap = 4;
@@ -2458,6 +2548,7 @@ FactorArgs make_args(bilu_ctx *c, double droptol, int G) {
     // recording takes exact samples: no skipping while it is on
     const bool rec = c->rec_cap > 0;
     a.skip_bound = c->p.skip == BILU_SKIP_BOUND && !rec ? 1 : 0;
+    a.sym = c->p.symmetric ? 1 : 0;
     a.learned = c->p.skip == BILU_SKIP_LEARNED && !rec && c->d_mlp_w ? 1 : 0;
     a.zhi = (float)c->mlp_logit_hi;
     a.mlp_norm = c->d_mlp_norm;
@@ -2704,8 +2795,10 @@ static bilu_status factor_tree_run(bilu_ctx *c, double droptol) {
     BILU_CUDA(c, cudaEventCreate(&e1));
     bilu_status result = BILU_OK;
     bool finished = false;
+    const bool hinted = hint_matches(c);
     for (int attempt = 0; attempt < 16; ++attempt) {
-        const int64_t need[4] = {c->capLrow, c->capLval, c->capUcol, c->capUval};
+        int64_t need[4] = {c->capLrow, c->capLval, c->capUcol, c->capUval};
+        for (int q = 0; q < 4 && hinted && attempt == 0; ++q) need[q] = std::max(need[q], c->hint_cap[4 + q]);
         if (c->capA[0] < need[0] || c->capA[1] < need[1] || c->capA[2] < need[2] || c->capA[3] < need[3] ||
             c->d_aptr == nullptr) {
             const int64_t cap[4] = {std::max(need[0], c->capA[0]), std::max(need[1], c->capA[1]),
@@ -2842,12 +2935,19 @@ static bilu_status factor_tree_run(bilu_ctx *c, double droptol) {
                 BILU_CUDA(c, cudaMemcpy(&tot[2], c->d_Uptr + nb, sizeof(int64_t), cudaMemcpyDeviceToHost));
                 BILU_CUDA(c, cudaMemcpy(&tot[3], c->d_Uvptr + nb, sizeof(int64_t), cudaMemcpyDeviceToHost));
             }
+            // what the whole factor needs, extrapolated from the blocks the groups had started
+            // (queue head) when the run stopped, at most 16 times the chunks handed out: a heavy
+            // fill then takes one or two re-runs instead of one per doubling
+            int32_t head = 0;
+            BILU_CUDA(c, cudaMemcpy(&head, c->d_tree + 12, sizeof(int32_t), cudaMemcpyDeviceToHost));
+            const double scale = std::min(16.0, (double)std::max(nb, 1) / (double)std::max(1, std::min(head, nb)));
             int64_t *pc[4] = {&c->capLrow, &c->capLval, &c->capUcol, &c->capUval};
             int64_t cap[4];
             for (int q = 0; q < 4; ++q) {
-                cap[q] = std::max(2 * c->capA[q], (int64_t)used[q] + (int64_t)used[q] / 4);
+                const int64_t est = (int64_t)((double)used[q] * scale);
+                cap[q] = std::max({2 * c->capA[q], (int64_t)used[q] + (int64_t)used[q] / 4, est + est / 4});
                 const bool grow = (int64_t)used[q] > c->capA[q] || tot[q] > *pc[q];
-                if (grow) *pc[q] = std::max(2 * *pc[q], tot[q] + tot[q] / 4);
+                if (grow) *pc[q] = std::max({2 * *pc[q], tot[q] + tot[q] / 4, est});
             }
             if (alloc_pools(c) != cudaSuccess || alloc_arena(c, cap) != cudaSuccess) {
                 result = set_err(c, BILU_ERR_OOM, "tree factor: growing the pools failed");

@@ -285,6 +285,13 @@ __global__ void setup_kernel(double *gm, int32_t *gi, const double *part, int G,
 
 }  // namespace
 
+// A new factor invalidates the captured cycle (its sweeps read the factor's buffers); the
+// workspace stays for the next solve.
+void gmres_drop_graph(bilu_ctx *c) {
+    if (c->gm_graph) cudaGraphExecDestroy(c->gm_graph);
+    c->gm_graph = nullptr;
+}
+
 void gmres_free(bilu_ctx *c) {
     if (c->gm_graph) cudaGraphExecDestroy(c->gm_graph);
     c->gm_graph = nullptr;

@@ -1,0 +1,296 @@
+"""GPU parity of the symmetric variant (BILDL, incomplete block L D L^T, Sec. 4.2) and of the
+simplified QMR solver against the oracle.
+
+Bar: the oracle's kept sets exactly and its values of L, U-breve, D and P per block to relative
+max(1e-10, 64 u kappa sqrt(nb)) (FP64; kappa the largest condition number of a pivot block,
+u = 2^-53: the forward error of an inverted block, gamma_b kappa, grown along the chain of
+blocks; these indefinite matrices have pivot blocks with kappa up to 5e5); D_K and P_K
+symmetric bit for bit; U-breve's columns are L's rows; BILU's L-side update work and none of
+its U side; the tree schedule gives the chain's factor bit for bit; SQMR takes the oracle's
+number of steps and ends at its iterate to 1e-8."""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import block_check as BC
+import paper_1908_10169_gb300 as B
+from paper_1908_10169_gb300 import workloads as W
+from tests.gpu_helpers import compare_factors, gpu_factor
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = B.bilu_create(0)
+    yield c
+    B.bilu_destroy(c)
+
+
+def _sym_indefinite(n, seed):
+    rng = np.random.default_rng(seed)
+    Bm = rng.standard_normal((n, n))
+    A = Bm + Bm.T
+    A[np.abs(A) < 1.0] = 0.0
+    A += 6.0 * np.eye(n) * (np.arange(n) % 2)
+    A[np.arange(0, n, 3), np.arange(0, n, 3)] = 0.0
+    return A
+
+
+def _case(name):
+    if name == "shifted elasticity 6^3, blocks of 24":
+        w = W.elasticity3d_shifted(side=6, block=24)
+        return w.A, O.partition_fixed(w.A.n, 24), 1e-2
+    if name == "shifted elasticity 6^3, node blocks":
+        w = W.elasticity3d_shifted(side=6, block=24)
+        return w.A, np.arange(0, w.A.n + 1, 3, dtype=np.int32), 1e-2
+    if name == "shifted elasticity 8^3, blocks of 63":
+        w = W.elasticity3d_shifted(side=8, block=63)
+        return w.A, O.partition_fixed(w.A.n, 63), 1e-3
+    if name == "random symmetric indefinite 120, ragged blocks":
+        A = W.from_dense(_sym_indefinite(120, 2))
+        return A, np.array([0, 5, 12, 20, 27, 33, 64, 65, 90, 120], np.int32), 3e-2
+    raise KeyError(name)
+
+
+CASES = ["shifted elasticity 6^3, blocks of 24", "shifted elasticity 6^3, node blocks",
+         "shifted elasticity 8^3, blocks of 63", "random symmetric indefinite 120, ragged blocks"]
+
+
+def _sym_params(**kw):
+    return B.bilu_params_default(max_block=64, symmetric=1, **kw)
+
+
+def _rtol(Fo):
+    kappa = max(np.linalg.cond(Fo.P_block(K)) for K in range(Fo.nb))
+    return max(1e-10, 64 * 2.0 ** -53 * kappa * np.sqrt(Fo.nb))
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_bildl_factor_matches_oracle(ctx, name):
+    A, bs, tau = _case(name)
+    g = gpu_factor(ctx, A, tau, _sym_params(), bstart=bs)
+    Fo = O.bildl_factor(A, bs, tau)
+    rep = compare_factors(Fo, g, rtol=_rtol(Fo), A=A, tau=tau)
+    print(name, rep)
+    assert np.array_equal(g.Lptr, g.Uptr) and np.array_equal(g.Lrow, g.Ucol)
+    for K in range(len(bs) - 1):
+        D, P = g.D_block(K), g.P_block(K)
+        assert np.array_equal(D, D.T) and np.array_equal(P, P.T), K
+    assert g.stats.flop_upd_u == 0 and g.stats.cand_cols == 0
+    assert g.stats.flop_upd_l == int(Fo.counters["flop_upd_L"])
+
+
+@pytest.mark.parametrize("name", CASES[:3])
+def test_bildl_does_the_l_side_of_bilu(ctx, name):
+    """On a symmetric matrix BILU computes the same factor with both sides: the L-side
+    update work (pivot rows included) is the same, BILDL drops the U side, and the
+    preconditioners agree."""
+    import torch
+    A, bs, tau = _case(name)
+    c2 = B.bilu_create(0)
+    try:
+        gs = gpu_factor(ctx, A, tau, _sym_params(), bstart=bs, export=False)
+        gu = gpu_factor(c2, A, tau, B.bilu_params_default(max_block=64), bstart=bs, export=False)
+        assert gs.stats.flop_upd_l == gu.stats.flop_upd_l and gu.stats.flop_upd_u > 0
+        assert gs.stats.flop_upd_u == 0 and gs.stats.kept_rows == gu.stats.kept_rows == gu.stats.kept_cols
+        r = torch.from_numpy(np.random.default_rng(4).standard_normal(A.n)).cuda()
+        z1, z2 = torch.empty_like(r), torch.empty_like(r)
+        B.bilu_apply(ctx, r, z1)
+        B.bilu_apply(c2, r, z2)
+        torch.cuda.synchronize()
+        Fo = O.bildl_factor(A, bs, tau)
+        assert float((z1 - z2).abs().max()) <= 10 * _rtol(Fo) * float(z2.abs().max())
+    finally:
+        B.bilu_destroy(c2)
+
+
+def test_bildl_preconditioner_is_symmetric(ctx):
+    import torch
+    A, bs, tau = _case("shifted elasticity 6^3, blocks of 24")
+    gpu_factor(ctx, A, tau, _sym_params(), bstart=bs, export=False)
+    n = A.n
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((4, n))
+    Z = []
+    for k in range(4):
+        r = torch.from_numpy(X[k]).cuda()
+        z = torch.empty_like(r)
+        B.bilu_apply(ctx, r, z)
+        torch.cuda.synchronize()
+        Z.append(z.cpu().numpy())
+    # x_j^T M^{-1} x_k = x_k^T M^{-1} x_j
+    for j in range(4):
+        for k in range(j):
+            a, b = X[j] @ Z[k], X[k] @ Z[j]
+            assert abs(a - b) <= 1e-12 * (abs(a) + abs(b) + np.abs(X[j]).sum() * np.abs(Z[k]).max())
+
+
+def test_bildl_tree_schedule_is_the_chain_factor(ctx):
+    w = W.elasticity3d_shifted(side=8, block=63)
+    bs0 = O.partition_fixed(w.A.n, 63)
+    perm, nbs, _ = B.bilu_nd_order(w.A.n, w.A.rowptr, w.A.colind, bs0)
+    A = W.CSR(w.A.n, *B.bilu_permute_csr(w.A.n, w.A.rowptr, w.A.colind, w.A.val, perm))
+    gc = gpu_factor(ctx, A, 1e-3, _sym_params(schedule=B.BILU_SCHED_CHAIN), bstart=nbs)
+    c2 = B.bilu_create(0)
+    try:
+        gt = gpu_factor(c2, A, 1e-3, _sym_params(schedule=B.BILU_SCHED_TREE, group_ctas=5), bstart=nbs)
+    finally:
+        B.bilu_destroy(c2)
+    for k in ("bstart", "Lptr", "Lrow", "Lval", "Uptr", "Ucol", "Uval", "Dinv", "Pblk"):
+        a, b = getattr(gc, k), getattr(gt, k)
+        assert a.shape == b.shape and np.array_equal(a.view(np.uint8), b.view(np.uint8)), k
+    Fo = O.bildl_factor(A, nbs, 1e-3)
+    compare_factors(Fo, gc, rtol=_rtol(Fo), A=A, tau=1e-3)
+
+
+@pytest.mark.parametrize("name,tol", [("shifted elasticity 6^3, blocks of 24", 1e-6),
+                                      ("shifted elasticity 8^3, blocks of 63", 1e-6),
+                                      ("random symmetric indefinite 120, ragged blocks", 1e-10)])
+def test_sqmr_matches_oracle(ctx, name, tol):
+    import torch
+    A, bs, tau = _case(name)
+    gpu_factor(ctx, A, tau, _sym_params(), bstart=bs, export=False)
+    Fo = O.bildl_factor(A, bs, tau)
+    b = O.spmv(A, np.ones(A.n)) + np.random.default_rng(6).standard_normal(A.n) * 0.1
+    ro = O.sqmr(A, Fo, b, tol=tol, maxit=2000)
+    assert ro.status == 0
+    bt = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bt)
+    info = B.sqmr_solve(ctx, bt, x, tol=tol, maxit=2000)
+    xg = x.cpu().numpy()
+    print(name, "steps", info.iters, ro.iters, "backward error", info.backward_error, ro.berr)
+    assert info.status == B.BILU_OK and info.breakdown == 0
+    assert info.iters == ro.iters
+    assert info.backward_error <= tol
+    assert np.abs(xg - ro.x).max() <= 1e-8 * np.abs(ro.x).max()
+
+
+def test_sqmr_edge_cases(ctx):
+    import torch
+    A, bs, tau = _case("shifted elasticity 6^3, blocks of 24")
+    gpu_factor(ctx, A, tau, _sym_params(), bstart=bs, export=False)
+    b = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    x = torch.zeros_like(b)
+    info = B.sqmr_solve(ctx, b, x, tol=1e-6, maxit=50)
+    assert info.status == B.BILU_OK and info.iters == 0 and not bool(x.any())
+    b = torch.from_numpy(O.spmv(A, np.ones(A.n))).cuda()
+    x = torch.zeros_like(b)
+    info = B.sqmr_solve(ctx, b, x, tol=1e-6, maxit=0)  # no step allowed
+    assert info.status == B.BILU_NOT_CONVERGED and info.iters == 0
+    x = torch.zeros_like(b)
+    info = B.sqmr_solve(ctx, b, x, tol=1e-30, maxit=3)  # stops at maxit
+    ro = O.sqmr(A, O.bildl_factor(A, bs, tau), b.cpu().numpy(), tol=1e-30, maxit=3)
+    assert info.status == B.BILU_NOT_CONVERGED and info.iters == 3 == ro.iters
+    assert np.abs(x.cpu().numpy() - ro.x).max() <= 1e-9 * np.abs(ro.x).max()
+    # host vectors through the same call
+    bh, xh = O.spmv(A, np.ones(A.n)), np.zeros(A.n)
+    info = B.sqmr_solve(ctx, bh, xh, tol=1e-6, maxit=500)
+    assert info.status == B.BILU_OK and np.abs(xh - 1.0).max() < 1e-3
+    with pytest.raises(B.BiluError):
+        B.sqmr_solve(ctx, bh, xh, tol=-1.0, maxit=5)
+
+
+def test_symmetric_variant_refuses_unsymmetric_input_and_options(ctx):
+    w = W.cd2d_32()
+    with pytest.raises(B.BiluError) as ei:
+        gpu_factor(ctx, w.A, 1e-2, _sym_params(), export=False)
+    assert ei.value.status == B.BILU_ERR_ARG
+    A, bs, tau = _case("shifted elasticity 6^3, blocks of 24")
+    for kw in ({"skip": B.BILU_SKIP_BOUND}, {"aggregate_max": 8}, {"symmetric": 2}):
+        p = _sym_params()
+        for k, v in kw.items():
+            setattr(p, k, v)
+        with pytest.raises(B.BiluError) as ei:
+            gpu_factor(ctx, A, tau, p, bstart=bs, export=False)
+        assert ei.value.status == B.BILU_ERR_ARG
+
+
+@pytest.mark.parametrize("prec,tol,shift,tau", [(B.BILU_PREC_FP32, 1e-4, 0.0, 1e-2), (B.BILU_PREC_BF16, 3e-2, 0.0, 1e-2),
+                                               (B.BILU_PREC_FP32, None, 0.3, 1e-3)])
+def test_bildl_reduced_precision(ctx, prec, tol, shift, tau):
+    """FP32 / BF16 storage (BF16: updates on the tensor cores) against FP64 BILDL.  On the
+    definite matrix (no shift) the preconditioner agrees to the storage rounding; on the
+    indefinite one (shift 0.3, pivot blocks with condition numbers up to 5e5) FP32 still
+    converges.  SQMR needs at most 10 % more steps.  (BF16 storage does not converge on the
+    indefinite matrix: its rounding, amplified by the near-singular pivot blocks, exceeds
+    what the iteration can correct.)"""
+    import torch
+    w = W.elasticity3d_shifted(side=8, block=63, shift=shift)
+    A, bs = w.A, O.partition_fixed(w.A.n, 63)
+    c2 = B.bilu_create(0)
+    try:
+        gpu_factor(ctx, A, tau, _sym_params(precision=prec), bstart=bs, export=False)
+        gpu_factor(c2, A, tau, _sym_params(), bstart=bs, export=False)
+        r = torch.from_numpy(np.random.default_rng(7).standard_normal(A.n)).cuda()
+        z1, z0 = torch.empty_like(r), torch.empty_like(r)
+        B.bilu_apply(ctx, r, z1)
+        B.bilu_apply(c2, r, z0)
+        torch.cuda.synchronize()
+        if tol is not None:
+            assert float((z1 - z0).abs().max()) <= tol * float(z0.abs().max())
+        b = torch.from_numpy(O.spmv(A, np.ones(A.n))).cuda()
+        x1, x0 = torch.zeros_like(b), torch.zeros_like(b)
+        i1 = B.sqmr_solve(ctx, b, x1, 1e-6, 2000)
+        i0 = B.sqmr_solve(c2, b, x0, 1e-6, 2000)
+        assert i1.status == B.BILU_OK and i1.iters <= 1.1 * i0.iters + 1
+    finally:
+        B.bilu_destroy(c2)
+
+
+def test_bildl_full_size_sampled_blocks(ctx):
+    """32^3 shifted elasticity (n = 98,304), blocks of 63, tau 1e-3, dissection order, tree
+    schedule (the benchmark's launch): sampled blocks recomputed by the oracle's block step
+    from the GPU's own earlier blocks, and SQMR to the backward error 1e-6."""
+    import torch
+    w = W.elasticity3d_shifted(side=32, block=63)
+    bs0 = O.partition_fixed(w.A.n, 63)
+    perm, nbs, _ = B.bilu_nd_order(w.A.n, w.A.rowptr, w.A.colind, bs0)
+    A = W.CSR(w.A.n, *B.bilu_permute_csr(w.A.n, w.A.rowptr, w.A.colind, w.A.val, perm))
+    g = gpu_factor(ctx, A, 1e-3, _sym_params(schedule=B.BILU_SCHED_TREE), bstart=nbs)
+    E = {"bstart": g.bstart, "Lptr": g.Lptr, "Lrow": g.Lrow, "Lval": g.Lval, "Uptr": g.Uptr, "Ucol": g.Ucol,
+         "Uval": g.Uval, "Dinv": g.Dinv, "Pblk": g.Pblk}
+    blocks = BC._blocks(E)
+    nb = len(nbs) - 1
+    flips = 0
+    for K in sorted(set(np.linspace(0, nb - 1, 12).astype(int).tolist())):
+        f, err = BC.compare_block(A, E, K, 1e-3, rtol=1e-10, blocks=blocks, flip_rtol=1e-12)
+        flips += f
+    assert flips == 0
+    b = torch.from_numpy(w.b[perm]).cuda()
+    x = torch.zeros_like(b)
+    info = B.sqmr_solve(ctx, b, x, 1e-6, 3000)
+    print("32^3 BILDL + SQMR: steps", info.iters, "backward error", info.backward_error)
+    assert info.status == B.BILU_OK and info.backward_error <= 1e-6
+
+
+def test_bildl_and_sqmr_are_deterministic(ctx):
+    """Two factorizations of the 24^3 shifted matrix (tree schedule, the library's group size)
+    give the same factor bit for bit, and two SQMR solves the same steps and iterate."""
+    import torch
+    w = W.elasticity3d_shifted(side=24, block=63)
+    bs0 = O.partition_fixed(w.A.n, 63)
+    perm, nbs, _ = B.bilu_nd_order(w.A.n, w.A.rowptr, w.A.colind, bs0)
+    A = W.CSR(w.A.n, *B.bilu_permute_csr(w.A.n, w.A.rowptr, w.A.colind, w.A.val, perm))
+    p = _sym_params(schedule=B.BILU_SCHED_TREE)
+    g1 = gpu_factor(ctx, A, 1e-3, p, bstart=nbs)
+    b = torch.from_numpy(w.b[perm]).cuda()
+    x1, x2 = torch.zeros_like(b), torch.zeros_like(b)
+    i1 = B.sqmr_solve(ctx, b, x1, 1e-6, 3000)
+    i2 = B.sqmr_solve(ctx, b, x2, 1e-6, 3000)
+    c2 = B.bilu_create(0)
+    try:
+        g2 = gpu_factor(c2, A, 1e-3, p, bstart=nbs)
+        x3 = torch.zeros_like(b)
+        i3 = B.sqmr_solve(c2, b, x3, 1e-6, 3000)
+    finally:
+        B.bilu_destroy(c2)
+    diff = [k for k in ("Lptr", "Lrow", "Lval", "Uptr", "Ucol", "Uval", "Dinv", "Pblk")
+            if not np.array_equal(getattr(g1, k).view(np.uint8), getattr(g2, k).view(np.uint8))]
+    print("24^3 BILDL: steps", i1.iters, i2.iters, i3.iters, "arrays that differ:", diff)
+    assert not diff
+    assert i1.iters == i2.iters == i3.iters
+    assert torch.equal(x1, x2) and torch.equal(x1, x3)
