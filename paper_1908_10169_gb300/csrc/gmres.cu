@@ -1,12 +1,13 @@
 // Right-preconditioned restarted GMRES(m) on the GPU (Saad and Schultz; the paper's
 // experiments use GMRES(30), Sec. 4).
 //
-// A x = b is solved as A M^{-1} u = b, x = x0 + M^{-1} V y.  Arnoldi uses modified
-// Gram-Schmidt; the small least-squares problem is reduced with Givens rotations on the
-// device.  One restart cycle (m Arnoldi steps, the update of x and the true residual) is
-// captured once into a CUDA graph; every kernel of a step returns immediately once the
-// cycle has converged, so the host synchronizes once per cycle.  All reductions use
-// per-CTA partial sums combined in a fixed order, so results are bitwise reproducible.
+// A x = b is solved as A M^{-1} u = b, x = x0 + M^{-1} V y.  Arnoldi orthogonalises by
+// classical Gram-Schmidt applied twice; the small least-squares problem is reduced with
+// Givens rotations on the device.  One restart cycle (m Arnoldi steps, the update of x and
+// the true residual) is captured once into a CUDA graph; every kernel of a step returns
+// immediately once the cycle has converged, so the host synchronizes once per cycle.  All
+// reductions use per-CTA partial sums combined in a fixed order, so results are bitwise
+// reproducible.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -16,6 +17,7 @@
 namespace {
 
 constexpr int VT = 256;   // threads per CTA of the vector kernels
+constexpr int GMRES_MAX_RESTART = 1000;  // largest restart length m
 enum { GI_ITS = 0, GI_JDONE, GI_DONE, GI_MAXIT, GI_M, GI_STOP, GI_COUNT = 8 };
 enum { GS_BNORM = 0, GS_BETA, GS_TOL, GS_REL, GS_RELEST, GS_COUNT = 8 };
 
@@ -127,46 +129,68 @@ __global__ void __launch_bounds__(VT) dot_kernel(int64_t n, const double *x, con
     if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
-// MGS step i of Arnoldi column j: apply the previous coefficient, start the next dot.
-__global__ void __launch_bounds__(VT) mgs_kernel(int64_t n, int i, int j, int m, double *V, double *w,
-                                                 double *part, double *gm, const int32_t *gi, int G) {
+// Classical Gram-Schmidt, applied twice (CGS2), for Arnoldi column j: in each pass one kernel
+// forms the partials of the j+1 products V_i^T w in one sweep of the CTA's chunk, the next sums
+// them (every CTA, fixed order), adds them to column j of H and subtracts sum_i h_i v_i from w
+// in one sweep; the second pass also starts ||w||^2.  Four launches per Arnoldi step instead
+// of j+2 for modified Gram-Schmidt; both orthogonalise to working precision and give the same
+// iterates in exact arithmetic.
+constexpr int CGS_SLOT = 4;  // first partial slot of the products (slot i + CGS_SLOT: V_i^T w)
+
+// one warp per product (warp k takes v_k, v_{k+8}, ...), four partial sums per lane, no block
+// barrier: the j+1 products of the CTA's chunk proceed side by side
+__global__ void __launch_bounds__(VT) cgs_dot_kernel(int64_t n, int j, const double *__restrict__ V,
+                                                     const double *__restrict__ w, double *__restrict__ part,
+                                                     const int32_t *gi, int G) {
     if (skipped(gi)) return;
     const Chunk c = chunk_of(n);
-    const double *partPrev = part + ((i - 1) & 1) * G;
-    double *partCur = part + (i & 1) * G;
-    double h = 0.0;
-    if (i > 0) {
-        h = sum_partials(partPrev, G);
-        if (blockIdx.x == 0 && threadIdx.x == 0) gm[(int64_t)(i - 1) * m + j] = h;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = warp; i <= j; i += VT / 32) {
+        const double *vi = V + (int64_t)i * n;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int64_t e = c.lo + lane;
+        for (; e + 96 < c.hi; e += 128) {
+            a0 = fma(vi[e], w[e], a0);
+            a1 = fma(vi[e + 32], w[e + 32], a1);
+            a2 = fma(vi[e + 64], w[e + 64], a2);
+            a3 = fma(vi[e + 96], w[e + 96], a3);
+        }
+        for (; e < c.hi; e += 32) a0 = fma(vi[e], w[e], a0);
+        const double t = warp_sum((a0 + a1) + (a2 + a3));
+        if (lane == 0) part[(int64_t)(CGS_SLOT + i) * G + blockIdx.x] = t;
     }
-    const double *vp = V + (int64_t)(i > 0 ? i - 1 : 0) * n, *vi = V + (int64_t)i * n;
+}
+
+__global__ void __launch_bounds__(VT) cgs_update_kernel(int64_t n, int j, int m, const double *__restrict__ V,
+                                                        double *__restrict__ w, double *part, double *gm,
+                                                        const int32_t *gi, int G, int pass) {
+    if (skipped(gi)) return;
+    __shared__ double h[GMRES_MAX_RESTART];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = warp; i <= j; i += VT / 32) {
+        double v = 0.0;
+        for (int k = lane; k < G; k += 32) v += ldcg(part + (int64_t)(CGS_SLOT + i) * G + k);
+        v = warp_sum(v);
+        if (lane == 0) h[i] = v;
+    }
+    __syncthreads();
+    if (blockIdx.x == 0)
+        for (int i = threadIdx.x; i <= j; i += VT) {
+            double *hij = gm + (int64_t)i * m + j;
+            *hij = pass == 0 ? h[i] : *hij + h[i];
+        }
+    const Chunk c = chunk_of(n);
     double acc = 0.0;
     for (int64_t e = c.lo + threadIdx.x; e < c.hi; e += VT) {
         double we = w[e];
-        if (i > 0) we = fma(-h, vp[e], we);
-        w[e] = we;
-        acc = fma(we, vi[e], acc);
-    }
-    const double t = block_sum(acc);
-    if (threadIdx.x == 0) partCur[blockIdx.x] = t;
-}
-
-// last MGS step of column j: subtract h_jj v_j, start ||w||^2
-__global__ void __launch_bounds__(VT) mgs_last_kernel(int64_t n, int j, int m, double *V, double *w,
-                                                      double *part, double *gm, const int32_t *gi, int G) {
-    if (skipped(gi)) return;
-    const Chunk c = chunk_of(n);
-    const double h = sum_partials(part + (j & 1) * G, G);
-    if (blockIdx.x == 0 && threadIdx.x == 0) gm[(int64_t)j * m + j] = h;
-    const double *vj = V + (int64_t)j * n;
-    double acc = 0.0;
-    for (int64_t e = c.lo + threadIdx.x; e < c.hi; e += VT) {
-        const double we = fma(-h, vj[e], w[e]);
+        for (int i = 0; i <= j; ++i) we = fma(-h[i], V[(int64_t)i * n + e], we);
         w[e] = we;
         acc = fma(we, we, acc);
     }
-    const double t = block_sum(acc);
-    if (threadIdx.x == 0) part[2 * G + blockIdx.x] = t;
+    if (pass == 1) {
+        const double t = block_sum(acc);
+        if (threadIdx.x == 0) part[2 * G + blockIdx.x] = t;
+    }
 }
 
 __global__ void __launch_bounds__(VT) normalize_kernel(int64_t n, int j, double *V, const double *w,
@@ -331,7 +355,7 @@ bilu_status gmres_alloc(bilu_ctx *c, int m) {
     GmLayout L(m);
     if (dev_alloc(&c->d_V, (int64_t)(m + 1) * n) != cudaSuccess || dev_alloc(&c->d_w, n) != cudaSuccess ||
         dev_alloc(&c->d_z, n) != cudaSuccess || dev_alloc(&c->d_r, n) != cudaSuccess ||
-        dev_alloc(&c->d_u, n) != cudaSuccess || dev_alloc(&c->d_part, 4 * vector_grid(c)) != cudaSuccess ||
+        dev_alloc(&c->d_u, n) != cudaSuccess || dev_alloc(&c->d_part, (int64_t)(CGS_SLOT + m + 1) * vector_grid(c)) != cudaSuccess ||
         dev_alloc(&c->d_gm, L.total) != cudaSuccess || dev_alloc(&c->d_gmi, GI_COUNT) != cudaSuccess ||
         dev_alloc(&c->d_gb, n) != cudaSuccess || dev_alloc(&c->d_gx, n) != cudaSuccess ||
         cudaMallocHost((void **)&c->h_gm_pinned, GS_COUNT * sizeof(double)) != cudaSuccess ||
@@ -355,9 +379,10 @@ bilu_status record_cycle(bilu_ctx *c, int m) {
         bilu_status st = apply_launch(c, c->d_V + (int64_t)j * n, c->d_z, gi + GI_DONE);
         if (st != BILU_OK) return st;
         launch_spmv(c, c->d_z, c->d_w, nullptr, nullptr, gi);
-        for (int i = 0; i <= j; ++i)
-            mgs_kernel<<<G, VT, 0, c->stream>>>(n, i, j, m, c->d_V, c->d_w, c->d_part, c->d_gm, gi, G);
-        mgs_last_kernel<<<G, VT, 0, c->stream>>>(n, j, m, c->d_V, c->d_w, c->d_part, c->d_gm, gi, G);
+        for (int pass = 0; pass < 2; ++pass) {
+            cgs_dot_kernel<<<G, VT, 0, c->stream>>>(n, j, c->d_V, c->d_w, c->d_part, gi, G);
+            cgs_update_kernel<<<G, VT, 0, c->stream>>>(n, j, m, c->d_V, c->d_w, c->d_part, c->d_gm, gi, G, pass);
+        }
         normalize_kernel<<<G, VT, 0, c->stream>>>(n, j, c->d_V, c->d_w, c->d_part, gi, G);
         givens_kernel<<<1, 32, 0, c->stream>>>(j, m, c->d_gm, gi, c->d_part, G, L.scal, L.g, L.cs, L.sn);
     }
@@ -405,7 +430,7 @@ bilu_status gmres_batch_run(bilu_ctx *const *ctxs, int count, const double *cons
                             int m, int maxit, gmres_info *info) {
     bilu_ctx *c0 = ctxs[0];
     const cudaStream_t master = c0->stream;  // every context is redirected to it below
-    if (m < 1 || m > 1000 || maxit < 0 || !(tol >= 0.0)) return set_err(c0, BILU_ERR_ARG, "bad gmres arguments");
+    if (m < 1 || m > GMRES_MAX_RESTART || maxit < 0 || !(tol >= 0.0)) return set_err(c0, BILU_ERR_ARG, "bad gmres arguments");
     cudaEvent_t e0, e1;
     BILU_CUDA(c0, cudaEventCreate(&e0));
     BILU_CUDA(c0, cudaEventCreate(&e1));
@@ -521,7 +546,7 @@ bilu_status gmres_batch_run(bilu_ctx *const *ctxs, int count, const double *cons
 }
 
 bilu_status gmres_run(bilu_ctx *c, const double *b, double *x, double tol, int m, int maxit, gmres_info *info) {
-    if (m < 1 || m > 1000 || maxit < 0 || !(tol >= 0.0)) return set_err(c, BILU_ERR_ARG, "bad gmres arguments");
+    if (m < 1 || m > GMRES_MAX_RESTART || maxit < 0 || !(tol >= 0.0)) return set_err(c, BILU_ERR_ARG, "bad gmres arguments");
     if (c->gm_restart != m) {
         bilu_status st = gmres_alloc(c, m);
         if (st != BILU_OK) return st;
