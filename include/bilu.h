@@ -313,7 +313,7 @@ bilu_status bilu_export(bilu_ctx *ctx, int64_t *Lptr, int32_t *Lrow, double *Lva
 
 /* Human-readable description of the last error on this context ("" if none).  With
  * ctx == NULL: the last error of this host thread's context-free calls
- * (bilu_cosine_blocking, bilu_partition_ilu1t, bilu_mwm, bilu_scale_permute_csr,
+ * (bilu_cosine_blocking, bilu_partition_ilu1t, bilu_mwm, bilu_sym_mwm, bilu_scale_permute_csr,
  * bilu_nd_order, bilu_block_etree, bilu_permute_csr). */
 const char *bilu_last_error(const bilu_ctx *ctx);
 
@@ -370,7 +370,30 @@ bilu_status bilu_mwm(int64_t n, const int64_t *rowptr, const int32_t *colind, co
                      double *dl, double *dr);
 
 /*
- * B[k][l] = dl[r_k] * A[r_k][c_l] * dr[c_l] on the host, with r_k = rowperm[k] and
+ * The symmetrised matching of the symmetric variant (Sec. 4.2; Duff and Pralet), host only.
+ * A must equal A^T entry by entry (n x n CSR as in bilu_analyze).  With the matching sigma and
+ * the scalings d_l, d_r of bilu_mwm, ds = sqrt(d_l d_r) is a symmetric scaling with
+ * |ds_i a_ij ds_j| <= 1, and the cycles of sigma give pivot units: a cycle of one index is a
+ * 1 x 1 unit (|a^_ii| = 1), of two indices a 2 x 2 unit (|a^_{i,i+1}| = 1); a longer cycle
+ * c_0 .. c_{k-1} is cut into pairs of neighbours (c_t, c_{t+1}), whose coupling is a matched
+ * entry -- for even k the cut starting at c_0 or c_1 with the larger sum of log |a_pair|, for
+ * odd k the cut leaving c_s alone that maximises log |a_{c_s c_s}| + sum log |a_pair| (the first
+ * on ties, a zero diagonal counting as -inf).  Units are ordered by their smallest index, the
+ * indices of a unit increasing.  Outputs (caller-owned host arrays): perm[n], the original
+ * index at each new position; ds[n], indexed by original index; ustart[n + 1] and *nunits:
+ * the units in the new order, [ustart[u], ustart[u + 1]).  A^ = P^T D A D P is then
+ * bilu_scale_permute_csr(rowperm = colperm = perm, dl = dr = ds), exactly symmetric; to solve
+ * A x = b: solve A^ y = (ds b)[perm], then x[perm] = ds[perm] y.  A partition whose
+ * boundaries are unit boundaries keeps every 2 x 2 pivot inside one diagonal block.
+ * Errors: BILU_ERR_ARG (malformed CSR, A not symmetric, null array), BILU_ERR_SINGULAR (no
+ * perfect matching); message in bilu_last_error(NULL).
+ */
+bilu_status bilu_sym_mwm(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val, int32_t *perm,
+                         double *ds, int32_t *ustart, int32_t *nunits);
+
+/*
+ * B[k][l] = A[r_k][c_l] * (dl[r_k] * dr[c_l]) on the host (one product of the two scalings, so
+ * that dl = dr keeps a symmetric A symmetric bit for bit), with r_k = rowperm[k] and
  * c_l = colperm[l] (a NULL permutation is the identity, a NULL scaling is 1): rowperm = NULL,
  * colperm = sigma and the scalings of bilu_mwm give A^ = D_l A D_r Pi; rowperm = colperm = Q
  * and no scaling give Q^T A Q (the reorderings of Sec. 3.1-3.3).  Output arrays as in

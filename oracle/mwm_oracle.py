@@ -116,3 +116,86 @@ def mwm(A):
     dr = np.array([math.exp(v[j]) / (amax[j] if amax[j] > 0 else 1.0) for j in range(A.n)])
     total = float(sum(C[i, sigma[i]] for i in range(A.n)))
     return sigma, dl, dr, u, v, total
+
+
+# ------------------------------------------------------------------ symmetric matching
+#
+# Sec. 4.2 (the symmetric variant) replaces the matching by a symmetrised one (Duff and
+# Pralet): A^ = P^T D A D P with |a^_ij| <= 1, where the cycles of the matching sigma give
+# pivots of size 1 x 1 (|a^_ii| = 1) and 2 x 2 (|a^_{i,i+1}| = 1) that stay together.  Written
+# out (readings R25, R26):
+#   scaling   D = diag(sqrt(d_l d_r)) from the scalings of the unsymmetric matching above, so
+#             that |a^_ij|^2 = |a^_ij of D_l A D_r| |a^_ji of D_l A D_r| <= 1 for symmetric A;
+#   cycles    i -> sigma(i) -> ... ; a cycle of one index is a 1 x 1 unit, of two a 2 x 2 unit;
+#             a longer cycle c_0 .. c_{k-1} is cut into pairs of neighbours (c_t, c_{t+1}),
+#             whose coupling a_{c_t c_{t+1}} is a matched entry: for even k the one of the two
+#             cuts (starting at c_0 or at c_1) with the larger sum of log |a_pair|, for odd k
+#             the cut leaving c_s alone that maximises log |a_{c_s c_s}| + sum log |a_pair|
+#             (the first on ties; a zero diagonal counts as -inf);
+#   order     units by their smallest index, the indices of a unit increasing.
+
+
+def _abs_entry(A, i, j):
+    for e in range(A.rowptr[i], A.rowptr[i + 1]):
+        if int(A.colind[e]) == j:
+            return abs(float(A.val[e]))
+    return 0.0
+
+
+def _log(x):
+    return math.log(x) if x > 0.0 else -INF
+
+
+def sym_units(A, sigma):
+    """The 1 x 1 / 2 x 2 units from the cycles of the matching sigma (see above)."""
+    n = A.n
+    seen = [False] * n
+    units = []
+    for i in range(n):
+        if seen[i]:
+            continue
+        cyc = [i]
+        seen[i] = True
+        j = int(sigma[i])
+        while j != i:
+            cyc.append(j)
+            seen[j] = True
+            j = int(sigma[j])
+        k = len(cyc)
+        if k <= 2:
+            units.append(sorted(cyc))
+            continue
+        if k % 2 == 0:
+            best_score, first = None, 0
+            for start in (0, 1):
+                score = 0.0
+                for t in range(start, start + k, 2):
+                    score += _log(_abs_entry(A, cyc[t % k], cyc[(t + 1) % k]))
+                if best_score is None or score > best_score:
+                    best_score, first = score, start
+            for t in range(first, first + k, 2):
+                units.append(sorted([cyc[t % k], cyc[(t + 1) % k]]))
+        else:
+            best_score, alone = None, 0
+            for s in range(k):
+                score = _log(_abs_entry(A, cyc[s], cyc[s]))
+                for t in range(s + 1, s + k, 2):
+                    score += _log(_abs_entry(A, cyc[t % k], cyc[(t + 1) % k]))
+                if best_score is None or score > best_score:
+                    best_score, alone = score, s
+            units.append([cyc[alone]])
+            for t in range(alone + 1, alone + k, 2):
+                units.append(sorted([cyc[t % k], cyc[(t + 1) % k]]))
+    units.sort(key=lambda u: u[0])
+    perm = np.array([i for u in units for i in u], dtype=np.int32)
+    ustart = np.concatenate([[0], np.cumsum([len(u) for u in units])]).astype(np.int32)
+    return perm, ustart
+
+
+def sym_matching(A):
+    """(perm, ds, ustart, sigma): the symmetric permutation (original index at each new
+    position), the symmetric scaling, the unit boundaries in the new order, the matching."""
+    sigma, dl, dr, _, _, _ = mwm(A)
+    ds = np.sqrt(dl * dr)
+    perm, ustart = sym_units(A, sigma)
+    return perm, ds, ustart, sigma

@@ -33,7 +33,7 @@ EXPORTED = ["bilu_params_default", "bilu_create", "bilu_analyze", "bilu_factor",
             "bilu_last_error",
             "bilu_debug_set", "bilu_apply_noalloc", "bilu_factor_batch", "gmres_solve_batch",
             "bilu_record_samples", "bilu_get_samples", "bilu_mlp_train", "bilu_mlp_forward", "bilu_mlp_grad",
-            "bilu_set_skip_model", "bilu_cosine_blocking", "bilu_partition_ilu1t", "bilu_mwm", "bilu_scale_permute_csr",
+            "bilu_set_skip_model", "bilu_cosine_blocking", "bilu_partition_ilu1t", "bilu_mwm", "bilu_sym_mwm", "bilu_scale_permute_csr",
             "bilu_nd_order", "bilu_block_etree",
             "bilu_permute_csr",
             "bilu_analyze_partition",
@@ -128,6 +128,7 @@ def lib():
             "bilu_permute_csr": ([i64, P, P, P, P, P, P, P], i32),
             "bilu_partition_ilu1t": ([i64, P, P, P, f64, i32, i32, P, P, ct.POINTER(i32)], i32),
             "bilu_mwm": ([i64, P, P, P, P, P, P], i32),
+            "bilu_sym_mwm": ([i64, P, P, P, P, P, P, P], i32),
             "bilu_nd_order": ([i64, P, P, i32, P, i32, P, P, P], i32),
             "bilu_block_etree": ([i64, P, P, i32, P, P, ct.POINTER(i32)], i32),
             "bilu_scale_permute_csr": ([i64, P, P, P, P, P, P, P, P, P, P], i32),
@@ -348,8 +349,22 @@ def bilu_mwm(n: int, rowptr, colind, val):
     return sigma[:n].copy(), dl[:n].copy(), dr[:n].copy()
 
 
+def bilu_sym_mwm(n: int, rowptr, colind, val):
+    """Sec. 4.2 symmetrised matching of a symmetric A on the host: (perm, ds, ustart), the
+    symmetric permutation, the symmetric scaling (by original index) and the 1 x 1 / 2 x 2
+    pivot units in the new order."""
+    import numpy as np
+    rp, ci, va, _ = _host_csr(n, rowptr, colind, val)
+    perm = np.zeros(max(n, 1), np.int32)
+    ds = np.zeros(max(n, 1))
+    ustart = np.zeros(n + 1, np.int32)
+    nu = ct.c_int32(0)
+    _check(None, lib().bilu_sym_mwm(n, _ptr(rp), _ptr(ci), _ptr(va), _ptr(perm), _ptr(ds), _ptr(ustart), ct.byref(nu)))
+    return perm[:n].copy(), ds[:n].copy(), ustart[: nu.value + 1].copy()
+
+
 def bilu_scale_permute_csr(n: int, rowptr, colind, val, rowperm=None, colperm=None, dl=None, dr=None):
-    """B[k, l] = dl[r_k] A[r_k, c_l] dr[c_l] on the host: returns (rowptr, colind, val)."""
+    """B[k, l] = A[r_k, c_l] (dl[r_k] dr[c_l]) on the host: returns (rowptr, colind, val)."""
     import numpy as np
     rp, ci, va, nnz = _host_csr(n, rowptr, colind, val)
 

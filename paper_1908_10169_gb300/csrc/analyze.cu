@@ -401,6 +401,93 @@ bilu_status mwm_host(int64_t n, const int64_t *rowptr, const int32_t *colind, co
 
 // B[k][l] = dl[r_k] A[r_k][c_l] dr[c_l] with r_k = rowperm[k], c_l = colperm[l] (identity or
 // unit scaling where a pointer is NULL); each row of B sorted by column.
+// Sec. 4.2: the symmetrised matching of the symmetric variant (Duff and Pralet).  The
+// unsymmetric matching sigma with its scalings d_l, d_r gives the symmetric scaling
+// d = sqrt(d_l d_r) (|d_i a_ij d_j| <= 1 for symmetric A) and, from the cycles of sigma, pivot
+// units: a one-index cycle is a 1 x 1 unit, a two-index cycle a 2 x 2 unit; a longer cycle
+// c_0 .. c_{k-1} is cut into pairs of neighbours (c_t, c_{t+1}), whose coupling is a matched
+// entry: for even k the cut starting at c_0 or at c_1 with the larger sum of log |a_pair|, for
+// odd k the cut leaving c_s alone that maximises log |a_{c_s c_s}| + sum log |a_pair| (the first
+// on ties; a zero diagonal counts as -inf).  Units are ordered by their smallest index, the
+// indices of a unit increasing.
+static double abs_entry(const int64_t *rowptr, const int32_t *colind, const double *val, int32_t i, int32_t j) {
+    const int32_t *lo = colind + rowptr[i], *hi = colind + rowptr[i + 1];
+    const int32_t *p = std::lower_bound(lo, hi, j);
+    return (p < hi && *p == j) ? std::fabs(val[rowptr[i] + (p - lo)]) : 0.0;
+}
+
+static double log_or_minus_inf(double x) { return x > 0.0 ? std::log(x) : -INFINITY; }
+
+bilu_status sym_mwm_host(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val, int32_t *perm,
+                         double *ds, int32_t *ustart, int32_t *nunits, std::string *err) {
+    auto fail = [&](bilu_status st, const char *m) { if (err) *err = m; return st; };
+    const std::string bad = check_pattern(n, rowptr, colind);
+    if (!bad.empty()) return fail(BILU_ERR_ARG, bad.c_str());
+    if (!nunits || (n > 0 && (!val || !perm || !ds || !ustart))) return fail(BILU_ERR_ARG, "null array");
+    for (int64_t i = 0; i < n; ++i)  // A = A^T entry by entry
+        for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+            const int32_t j = colind[e];
+            const int32_t *lo = colind + rowptr[j], *hi = colind + rowptr[j + 1];
+            const int32_t *p = std::lower_bound(lo, hi, (int32_t)i);
+            if (p == hi || *p != (int32_t)i || val[rowptr[j] + (p - lo)] != val[e])
+                return fail(BILU_ERR_ARG, "the symmetric matching needs a symmetric matrix");
+        }
+    std::vector<int32_t> sigma(std::max<int64_t>(n, 1));
+    std::vector<double> dl(std::max<int64_t>(n, 1)), dr(std::max<int64_t>(n, 1));
+    const bilu_status st = mwm_host(n, rowptr, colind, val, sigma.data(), dl.data(), dr.data(), err);
+    if (st != BILU_OK) return st;
+    for (int64_t i = 0; i < n; ++i) ds[i] = std::sqrt(dl[i] * dr[i]);
+    std::vector<std::vector<int32_t>> units;
+    std::vector<char> seen(std::max<int64_t>(n, 1), 0);
+    std::vector<int32_t> cyc;
+    auto pair_log = [&](int64_t t, int64_t k) {
+        return log_or_minus_inf(abs_entry(rowptr, colind, val, cyc[t % k], cyc[(t + 1) % k]));
+    };
+    auto add_pair = [&](int32_t a, int32_t b) { units.push_back({std::min(a, b), std::max(a, b)}); };
+    for (int64_t i = 0; i < n; ++i) {
+        if (seen[i]) continue;
+        cyc.clear();
+        for (int32_t j = (int32_t)i; !seen[j]; j = sigma[j]) {
+            seen[j] = 1;
+            cyc.push_back(j);
+        }
+        const int64_t k = (int64_t)cyc.size();
+        if (k == 1) {
+            units.push_back({cyc[0]});
+        } else if (k == 2) {
+            add_pair(cyc[0], cyc[1]);
+        } else if (k % 2 == 0) {
+            double best = 0.0;
+            int64_t first = 0;
+            for (int64_t start = 0; start < 2; ++start) {
+                double score = 0.0;
+                for (int64_t t = start; t < start + k; t += 2) score += pair_log(t, k);
+                if (start == 0 || score > best) { best = score; first = start; }
+            }
+            for (int64_t t = first; t < first + k; t += 2) add_pair(cyc[t % k], cyc[(t + 1) % k]);
+        } else {
+            double best = 0.0;
+            int64_t alone = 0;
+            for (int64_t sx = 0; sx < k; ++sx) {
+                double score = log_or_minus_inf(abs_entry(rowptr, colind, val, cyc[sx], cyc[sx]));
+                for (int64_t t = sx + 1; t < sx + k; t += 2) score += pair_log(t, k);
+                if (sx == 0 || score > best) { best = score; alone = sx; }
+            }
+            units.push_back({cyc[alone]});
+            for (int64_t t = alone + 1; t < alone + k; t += 2) add_pair(cyc[t % k], cyc[(t + 1) % k]);
+        }
+    }
+    std::sort(units.begin(), units.end(), [](const auto &x, const auto &y) { return x[0] < y[0]; });
+    int64_t pos = 0;
+    ustart[0] = 0;
+    for (size_t u = 0; u < units.size(); ++u) {
+        for (int32_t v : units[u]) perm[pos++] = v;
+        ustart[u + 1] = (int32_t)pos;
+    }
+    *nunits = (int32_t)units.size();
+    return BILU_OK;
+}
+
 bilu_status scale_permute_csr_host(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val,
                                    const int32_t *rowperm, const int32_t *colperm, const double *dl,
                                    const double *dr, int64_t *out_rowptr, int32_t *out_colind, double *out_val,
@@ -428,8 +515,8 @@ bilu_status scale_permute_csr_host(int64_t n, const int64_t *rowptr, const int32
         for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
             const int32_t j = colind[e];
             double a = val[e];
-            if (dl) a *= dl[i];
-            if (dr) a *= dr[j];
+            // one product of the two scalings: with dl = dr a symmetric A stays symmetric bit for bit
+            if (dl || dr) a *= (dl ? dl[i] : 1.0) * (dr ? dr[j] : 1.0);
             row.emplace_back(colperm ? icol[j] : j, a);
         }
         std::sort(row.begin(), row.end(), [](const auto &x, const auto &y) { return x.first < y.first; });

@@ -262,6 +262,8 @@ bilu_status partition_ilu1t_host(int64_t n, const int64_t *rowptr, const int32_t
                                  int32_t *bstart, int32_t *nblocks, std::string *err);
 bilu_status mwm_host(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val,
                      int32_t *sigma, double *dl, double *dr, std::string *err);
+bilu_status sym_mwm_host(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val, int32_t *perm,
+                         double *ds, int32_t *ustart, int32_t *nunits, std::string *err);
 bilu_status scale_permute_csr_host(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val,
                                    const int32_t *rowperm, const int32_t *colperm, const double *dl,
                                    const double *dr, int64_t *out_rowptr, int32_t *out_colind, double *out_val,

@@ -125,6 +125,12 @@ bilu_status bilu_mwm(int64_t n, const int64_t *rowptr, const int32_t *colind, co
     return mwm_host(n, rowptr, colind, val, sigma, dl, dr, &g_host_err);
 }
 
+bilu_status bilu_sym_mwm(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val, int32_t *perm,
+                         double *ds, int32_t *ustart, int32_t *nunits) {
+    g_host_err.clear();
+    return sym_mwm_host(n, rowptr, colind, val, perm, ds, ustart, nunits, &g_host_err);
+}
+
 bilu_status bilu_scale_permute_csr(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val,
                                    const int32_t *rowperm, const int32_t *colperm, const double *dl,
                                    const double *dr, int64_t *out_rowptr, int32_t *out_colind, double *out_val) {

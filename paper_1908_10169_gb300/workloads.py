@@ -358,6 +358,34 @@ def elasticity3d_shifted(side: int = 48, seed: int = 2, block: int = 63, shift: 
     return Workload(f"elasticity_q1_shifted_{side}^3x3", A, rhs_ones(A), 1e-2, 63, "fixed", block, gmres_tol=1e-6)
 
 
+def kkt_elasticity(side: int = 16, seed: int = 2, block: int = 63, multipliers_first: bool = True) -> Workload:
+    """Symmetric saddle-point system [[K, B^T], [B, 0]]: K is the exactly symmetric Q1 elasticity
+    matrix (K + K^T) / 2 of elasticity3d (same seed); B holds one row per displacement of every
+    node of the middle plane z = side // 2 (3 side^2 Lagrange multipliers that fix them), the
+    row of the identity scaled by the mean diagonal of K.  The multiplier unknowns have a zero
+    diagonal, the case the symmetric matching of Sec. 4.2 is for; with multipliers_first they
+    come first, so that a block of them has a zero pivot block and no earlier block to fill it.
+    n = 3 side^3 + 3 side^2; b = A * ones; drop tolerance 1e-3."""
+    import scipy.sparse as sp
+    K = elasticity3d(side, seed, block).A
+    Ks = sp.csr_matrix((K.val, K.colind, K.rowptr), shape=(K.n, K.n))
+    Ks = ((Ks + Ks.T) * 0.5).tocsr()
+    z = side // 2
+    nodes = np.array([x + side * (y + side * z) for y in range(side) for x in range(side)], dtype=np.int64)
+    dofs = (3 * nodes[:, None] + np.arange(3)[None, :]).reshape(-1)
+    m = dofs.size
+    beta = float(Ks.diagonal().mean())
+    Bm = sp.csr_matrix((np.full(m, beta), (np.arange(m), dofs)), shape=(m, K.n))
+    if multipliers_first:
+        M = sp.bmat([[None, Bm], [Bm.T, Ks]], format="csr")
+    else:
+        M = sp.bmat([[Ks, Bm.T], [Bm, None]], format="csr")
+    M.sum_duplicates()
+    M.sort_indices()
+    A = CSR(M.shape[0], M.indptr.astype(np.int64), M.indices.astype(np.int32), M.data.astype(np.float64))
+    return Workload(f"kkt_elasticity_{side}^3", A, rhs_ones(A), 1e-3, 63, "fixed", block, gmres_tol=1e-6)
+
+
 def laplace27_4dof(side: int = 64, seed: int = 3, block: int = 64) -> Workload:
     """Q1 27-point scalar diffusion operator (kappa log-uniform in [1e-3, 1e3] per element,
     seed) on side^3 interior nodes, coupled across 4 unknowns per node by the Kronecker product

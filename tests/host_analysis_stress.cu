@@ -1,6 +1,7 @@
 // Random-input stress of the library's host analysis (Sec. 3.1-3.4 helpers), built with the
 // address and undefined-behaviour sanitizers by tests/test_host_analysis_sanitizers.py.  Only host
 // code runs; the stubs stand for the device-side symbols analyze.cu refers to but never reaches here.
+#include <algorithm>
 #include <cstdio>
 #include <limits>
 #include <random>
@@ -12,6 +13,7 @@
 void factor_free(bilu_ctx *) {}
 void apply_free(bilu_ctx *) {}
 void gmres_free(bilu_ctx *) {}
+void sqmr_free(bilu_ctx *) {}
 bilu_status set_err(bilu_ctx *, bilu_status st, const std::string &) { return st; }
 bilu_status cuda_err(bilu_ctx *, cudaError_t, const char *) { return BILU_ERR_CUDA; }
 
@@ -55,6 +57,31 @@ int main() {
         mwm_host(n, rp.data(), ci.data(), va.data(), sigma.data(), dl.data(), dr.data(), &err);
         scale_permute_csr_host(n, rp.data(), ci.data(), va.data(), perm.data(), perm.data(), dl.data(), dr.data(),
                                orp.data(), oci.data(), ova.data(), &err);
+        {
+            // the symmetrised matching: refused on this (mostly unsymmetric) pattern, then run on
+            // its symmetric part (a_ij and a_ji both set to the row-major first of the two)
+            std::vector<int32_t> us(n + 2);
+            int32_t nu = 0;
+            sym_mwm_host(n, rp.data(), ci.data(), va.data(), perm.data(), dl.data(), us.data(), &nu, &err);
+            std::vector<std::vector<std::pair<int32_t, double>>> rows(n);
+            for (int i = 0; i < n; ++i)
+                for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+                    const int j = ci[e];
+                    if (j >= i) {
+                        rows[i].push_back({j, va[e]});
+                        if (j != i) rows[j].push_back({i, va[e]});
+                    }
+                }
+            std::vector<int64_t> srp(n + 1, 0);
+            std::vector<int32_t> sci;
+            std::vector<double> sva;
+            for (int i = 0; i < n; ++i) {
+                std::sort(rows[i].begin(), rows[i].end());
+                for (const auto &rv : rows[i]) { sci.push_back(rv.first); sva.push_back(rv.second); }
+                srp[i + 1] = (int64_t)sci.size();
+            }
+            sym_mwm_host(n, srp.data(), sci.data(), sva.data(), perm.data(), dl.data(), us.data(), &nu, &err);
+        }
         // analysis: validation, CSC copy and partition run on the host; the device upload that
         // follows fails where there is no GPU (or succeeds where there is one)
         {

@@ -294,3 +294,30 @@ def test_bildl_and_sqmr_are_deterministic(ctx):
     assert not diff
     assert i1.iters == i2.iters == i3.iters
     assert torch.equal(x1, x2) and torch.equal(x1, x3)
+
+
+def test_bildl_after_the_symmetric_matching(ctx):
+    """The saddle-point system after the symmetrised matching (units kept inside the blocks):
+    the GPU's BILDL equals the oracle's, perturbs nothing, and SQMR takes the oracle's steps."""
+    import torch
+    w = W.kkt_elasticity(side=6, block=24)
+    A0, n = w.A, w.A.n
+    perm, ds, ustart = B.bilu_sym_mwm(n, A0.rowptr, A0.colind, A0.val)
+    A = W.CSR(n, *B.bilu_scale_permute_csr(n, A0.rowptr, A0.colind, A0.val, perm, perm, ds, ds))
+    bs = [0]
+    for k in range(1, len(ustart)):  # blocks of at most 24 on unit boundaries
+        if ustart[k] - bs[-1] > 24:
+            bs.append(int(ustart[k - 1]))
+    bs = np.array(bs + [n], np.int32)
+    g = gpu_factor(ctx, A, 1e-3, _sym_params(), bstart=bs)
+    Fo = O.bildl_factor(A, bs, 1e-3)
+    compare_factors(Fo, g, rtol=_rtol(Fo), A=A, tau=1e-3)
+    assert g.stats.nperturb == 0 and Fo.counters["nperturb"] == 0
+    bh = (ds * w.b)[perm]
+    ro = O.sqmr(A, Fo, bh, 1e-6, 500)
+    y = torch.zeros(n, dtype=torch.float64, device="cuda")
+    info = B.sqmr_solve(ctx, torch.from_numpy(bh).cuda(), y, 1e-6, 500)
+    assert info.status == B.BILU_OK and abs(info.iters - ro.iters) <= 1
+    x = np.empty(n)
+    x[perm] = ds[perm] * y.cpu().numpy()
+    assert np.abs(x - 1.0).max() < 1e-3

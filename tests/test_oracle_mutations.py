@@ -18,7 +18,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PIN_TESTS = ["test_oracle.py", "test_partition_oracle.py", "test_block_check_oracle.py", "test_skip_oracle.py",
              "test_golden.py", "test_cosine_oracle.py", "test_mwm_oracle.py", "test_nd_oracle.py",
-             "test_aggregation_oracle.py", "test_bildl_oracle.py", "test_sqmr_oracle.py"]
+             "test_aggregation_oracle.py", "test_bildl_oracle.py", "test_sqmr_oracle.py", "test_sym_matching_oracle.py"]
 ORACLE_FILES = ["__init__.py", "bilu_oracle.c", "bilu_oracle.h", "block_check.py", "skip_oracle.py",
                 "cosine_oracle.py", "mwm_oracle.py", "nd_oracle.py"]
 
@@ -163,6 +163,13 @@ MUTANTS = [
      "dr = np.array([math.exp(v[j]) / (amax[j] if amax[j] > 0 else 1.0) for j in range(A.n)])",
      "dr = np.array([math.exp(v[j]) for j in range(A.n)])", 1),
     # block nested dissection and elimination tree (Sec. 3.3)
+    ("symmetric matching: singleton's diagonal ignored", MWM,
+     "                score = _log(_abs_entry(A, cyc[s], cyc[s]))", "                score = 0.0", 1),
+    ("symmetric matching: one-sided scaling", MWM, "    ds = np.sqrt(dl * dr)", "    ds = dl", 1),
+    ("symmetric matching: units in cycle order", MWM, "    units.sort(key=lambda u: u[0])\n", "", 1),
+    ("symmetric matching: odd cycle paired past the neighbour", MWM,
+     "                units.append(sorted([cyc[t % k], cyc[(t + 1) % k]]))\n    units.sort",
+     "                units.append(sorted([cyc[t % k], cyc[(t + 2) % k]]))\n    units.sort", 1),
     ("nd: separator is the first level", ND, "m = len(levels) // 2", "m = 1", 1),
     ("nd: separator ordered first", ND, "order += dissect(adj, first, leaf) + dissect(adj, second, leaf) + sorted(levels[m])",
      "order += sorted(levels[m]) + dissect(adj, first, leaf) + dissect(adj, second, leaf)", 1),
