@@ -153,3 +153,19 @@ def test_batch_sample_covers_both_kinds():
     ws = W.cd_batch(count=4, seed0=100)
     assert "cd2d" in ws[0].name and "cd3d" in ws[1].name
     assert bench.batch_sample(3) == {"2d": [0], "3d": [1]}
+
+
+def test_reference_arm_symmetric_line():
+    """--symmetric: the oracle's BILDL + SQMR on the shifted elasticity matrix, with its own
+    metric; a symmetric line on a nonsymmetric workload is refused."""
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--workload", "elasticity_shifted", "--symmetric", "--droptol", "1e-3", "--side", "4",
+                          "--block", "24", "--steps", "1", "--warmup", "1"], capture_output=True, text=True,
+                         timeout=300, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    d = json.loads([l for l in out.stdout.splitlines() if l.startswith("{")][0])
+    assert d["metric"].startswith("BILDL") and d["config"]["droptol"] == 1e-3
+    assert d["config"]["factorization"].startswith("BILDL") and d["config"]["gmres_iters"] > 0
+    bad = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--symmetric",
+                          "--side", "4"], capture_output=True, text=True, timeout=120, cwd=ROOT)
+    assert bad.returncode != 0 and "symmetric workload" in bad.stderr
