@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--workload", choices=["cd3d", "elasticity", "laplace27x4", "cd3d_rows_scrambled",
-                                           "elasticity_shifted"], default="cd3d",
+                                           "elasticity_shifted", "kkt"], default="cd3d",
                     help="cd3d: 3D upwind convection-diffusion (the benchmark); elasticity: Q1 3-dof/node "
                          "(mixed-precision configuration, --side 48 --block 63); laplace27x4: Q1 27-point, "
                          "4 dof/node (learned-skip evaluation, --side 64)")
@@ -91,6 +91,9 @@ def parse():
                     help="BILDL (incomplete block L D L^T, Sec. 4.2) solved by SQMR to the backward error "
                          "1e-6 instead of BILU + GMRES(30); needs a symmetric workload (elasticity_shifted)")
     ap.add_argument("--droptol", type=float, default=None, help="drop tolerance (default: the workload's)")
+    ap.add_argument("--sym-mwm", action="store_true",
+                    help="symmetric variant: the symmetrised matching of Sec. 4.2 (symmetric scaling, 1 x 1 / "
+                         "2 x 2 pivot units kept inside the blocks) before the blocking and the ordering")
     ap.add_argument("--compare-fp64", action="store_true",
                     help="also time plain FP64 factor + GMRES (no skip) on the same matrix, order and schedule, "
                          "and report the variant's speedup over it")
@@ -144,6 +147,8 @@ def workload(args):
         w = W.rows_scrambled(W.cd3d(side=args.side, seed=1, block=args.block), seed=5)
     elif args.workload == "elasticity_shifted":
         w = W.elasticity3d_shifted(side=args.side, seed=2, block=args.block)
+    elif args.workload == "kkt":
+        w = W.kkt_elasticity(side=args.side, seed=2, block=args.block)
     else:
         w = W.cd3d(side=args.side, seed=1, block=args.block)
     if getattr(args, "droptol", None) is not None:
@@ -189,6 +194,19 @@ def preprocess(args, w):
         maps.append(unmatch)
         steps.append("mwm")
 
+    units = None
+    if getattr(args, "sym_mwm", False):
+        perm, ds, units = B.bilu_sym_mwm(A.n, A.rowptr, A.colind, A.val)
+        A = W.CSR(A.n, *B.bilu_scale_permute_csr(A.n, A.rowptr, A.colind, A.val, perm, perm, ds, ds))
+        b = (ds * b)[perm]
+
+        def unsym(y, perm=perm, ds=ds):
+            x = np.empty_like(y)
+            x[perm] = ds[perm] * y
+            return x
+        maps.append(unsym)
+        steps.append("sym_mwm")
+
     def sym_permute(perm):
         nonlocal A, b
         A = W.CSR(A.n, *B.bilu_permute_csr(A.n, A.rowptr, A.colind, A.val, perm))
@@ -201,7 +219,19 @@ def preprocess(args, w):
         maps.append(unpermute)
 
     blocking = getattr(args, "blocking", "fixed")
-    if blocking.startswith("cosine"):
+    if units is not None:  # blocks made of whole pivot units
+        if blocking.startswith("cosine"):
+            raise SystemExit("--sym-mwm takes --blocking fixed or ilu1t")
+        if blocking == "ilu1t":
+            bstart = B.bilu_partition_ilu1t(A.n, A.rowptr, A.colind, A.val, 1e-2, 64, units)
+            steps.append("ilu1t")
+        else:
+            out = [0]
+            for k in range(1, len(units)):
+                if units[k] - out[-1] > args.block:
+                    out.append(int(units[k - 1]))
+            bstart = np.array(out + ([A.n] if out[-1] != A.n else []), dtype=np.int32)
+    elif blocking.startswith("cosine"):
         perm, groups = B.bilu_cosine_blocking(A.n, A.rowptr, A.colind, 0.8, 64)
         sym_permute(perm)
         bstart = groups
@@ -235,7 +265,7 @@ def config(args, w, extra=None):
     if getattr(args, "precision", "fp64") == "bf16":
         c["update_tiles"] = "FP32 units" if getattr(args, "no_tensor", False) else "tensor cores (tcgen05, BF16 x BF16 -> FP32)"
 
-    pre = [k for k, on in (("mwm", getattr(args, "mwm", False)),
+    pre = [k for k, on in (("mwm", getattr(args, "mwm", False)), ("sym_mwm", getattr(args, "sym_mwm", False)),
                            ("nd", getattr(args, "order", "natural") == "nd")) if on]
     if pre or blocking != "fixed":
         c["host_analysis"] = pre + ([blocking] if blocking != "fixed" else [])
@@ -979,7 +1009,7 @@ def run_batch(args):
 
 def main():
     args = parse()
-    if args.symmetric and args.workload != "elasticity_shifted":
+    if args.symmetric and args.workload not in ("elasticity_shifted", "kkt"):
         raise SystemExit("--symmetric needs a symmetric workload: --workload elasticity_shifted")
     if args.impl == "reference":
         return run_reference(args)

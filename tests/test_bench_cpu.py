@@ -41,7 +41,8 @@ def test_argument_defaults():
 
 def _args(**kw):
     import argparse
-    base = dict(side=8, block=8, workload="cd3d", mwm=False, blocking="fixed", order="natural")
+    base = dict(side=8, block=8, workload="cd3d", mwm=False, blocking="fixed", order="natural", sym_mwm=False,
+                droptol=None)
     base.update(kw)
     return argparse.Namespace(**base)
 
@@ -57,6 +58,9 @@ import pytest  # noqa: E402
     {"blocking": "ilu1t", "order": "nd"},
     {"workload": "cd3d_rows_scrambled", "mwm": True},
     {"workload": "cd3d_rows_scrambled", "mwm": True, "order": "nd"},
+    {"workload": "kkt", "sym_mwm": True, "side": 4, "block": 24},
+    {"workload": "kkt", "sym_mwm": True, "order": "nd", "side": 4, "block": 24},
+    {"workload": "kkt", "sym_mwm": True, "blocking": "ilu1t", "side": 4, "block": 24},
 ])
 def test_preprocessed_system_maps_back(kw):
     """The prepared system (matching, cosine blocking, ILU(1,tau), nested dissection as
@@ -82,6 +86,13 @@ def test_preprocessed_system_maps_back(kw):
         assert bs[0] == 0 and bs[-1] == w.A.n and np.all(np.diff(bs) >= 1) and np.diff(bs).max() <= 64
     if kw.get("mwm"):
         assert np.allclose(np.abs(Ap.diagonal()), 1.0, atol=1e-12)
+    if kw.get("sym_mwm"):  # symmetric bit for bit, |a^| <= 1, no block splits a 2 x 2 unit
+        assert (Ap != Ap.T).nnz == 0 and np.abs(Ap.data).max() <= 1 + 1e-12
+        assert prep.bstart is not None
+        import paper_1908_10169_gb300 as B
+        perm, ds, units = B.bilu_sym_mwm(w.A.n, w.A.rowptr, w.A.colind, w.A.val)
+        if kw.get("order") != "nd":
+            assert set(np.asarray(prep.bstart).tolist()) <= set(units.tolist())
 
 
 def test_reference_arm_with_host_analysis():
