@@ -93,7 +93,8 @@ def parse():
     ap.add_argument("--droptol", type=float, default=None, help="drop tolerance (default: the workload's)")
     ap.add_argument("--sym-mwm", action="store_true",
                     help="symmetric variant: the symmetrised matching of Sec. 4.2 (symmetric scaling, 1 x 1 / "
-                         "2 x 2 pivot units kept inside the blocks) before the blocking and the ordering")
+                         "2 x 2 pivot units kept inside the blocks; cosine blocking on the compressed units) "
+                         "before the blocking and the ordering")
     ap.add_argument("--compare-fp64", action="store_true",
                     help="also time plain FP64 factor + GMRES (no skip) on the same matrix, order and schedule, "
                          "and report the variant's speedup over it")
@@ -220,9 +221,14 @@ def preprocess(args, w):
 
     blocking = getattr(args, "blocking", "fixed")
     if units is not None:  # blocks made of whole pivot units
-        if blocking.startswith("cosine"):
-            raise SystemExit("--sym-mwm takes --blocking fixed or ilu1t")
-        if blocking == "ilu1t":
+        if blocking.startswith("cosine"):  # Sec. 4.2: cosine blocking of the compressed units
+            perm, groups = B.bilu_cosine_blocking_units(A.n, A.rowptr, A.colind, units, 0.8, 64)
+            sym_permute(perm)
+            bstart = groups
+            if blocking == "cosine+ilu1t":
+                bstart = B.bilu_partition_ilu1t(A.n, A.rowptr, A.colind, A.val, 1e-2, 64, groups)
+            steps.append(blocking)
+        elif blocking == "ilu1t":
             bstart = B.bilu_partition_ilu1t(A.n, A.rowptr, A.colind, A.val, 1e-2, 64, units)
             steps.append("ilu1t")
         else:

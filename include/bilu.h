@@ -313,7 +313,8 @@ bilu_status bilu_export(bilu_ctx *ctx, int64_t *Lptr, int32_t *Lrow, double *Lva
 
 /* Human-readable description of the last error on this context ("" if none).  With
  * ctx == NULL: the last error of this host thread's context-free calls
- * (bilu_cosine_blocking, bilu_partition_ilu1t, bilu_mwm, bilu_sym_mwm, bilu_scale_permute_csr,
+ * (bilu_cosine_blocking, bilu_cosine_blocking_units, bilu_partition_ilu1t, bilu_mwm, bilu_sym_mwm,
+ * bilu_scale_permute_csr,
  * bilu_nd_order, bilu_block_etree, bilu_permute_csr). */
 const char *bilu_last_error(const bilu_ctx *ctx);
 
@@ -368,6 +369,22 @@ bilu_status bilu_partition_ilu1t(int64_t n, const int64_t *rowptr, const int32_t
  */
 bilu_status bilu_mwm(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val, int32_t *sigma,
                      double *dl, double *dr);
+
+/*
+ * Cosine blocking of the compressed matrix (Sec. 4.2: after the symmetrised matching the
+ * 2 x 2 pivots are merged before the cosine test), host only.  The consecutive units
+ * [ustart[p], ustart[p + 1]), p < nunits (sizes 1..max_block, from 0 to n), are the indices of
+ * the compressed pattern, whose row p holds the units of the columns of A's rows in unit p;
+ * the blocking of bilu_cosine_blocking runs on it with one change: a unit adds its size to its
+ * block, which holds at most max_block indices of A (a partner that passes the test but does
+ * not fit is passed over).  Outputs as in bilu_cosine_blocking, over the indices of A: perm[n]
+ * (the units of each block in the block's order, the indices of a unit in theirs) and
+ * bstart[nblocks + 1] (every block made of whole units).  Errors: BILU_ERR_ARG (malformed CSR
+ * or units, tau < 0 or not finite, max_block outside 1..64, null array).
+ */
+bilu_status bilu_cosine_blocking_units(int64_t n, const int64_t *rowptr, const int32_t *colind, double tau,
+                                      int32_t max_block, int32_t nunits, const int32_t *ustart, int32_t *perm,
+                                      int32_t *bstart, int32_t *nblocks);
 
 /*
  * The symmetrised matching of the symmetric variant (Sec. 4.2; Duff and Pralet), host only.

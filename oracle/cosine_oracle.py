@@ -62,10 +62,13 @@ def excluded(A) -> np.ndarray:
     return np.array([a or b for a, b in zip(r, c)], dtype=bool)
 
 
-def cosine_blocking(A, tau: float = 0.8, max_block: int = 64):
+def cosine_blocking(A, tau: float = 0.8, max_block: int = 64, weights=None):
     """Returns (perm, bstart): the permutation Q as the original index of every new position
-    and the block starts of A~ = Q^T A Q (Sec. 3.2, readings C1-C5)."""
+    and the block starts of A~ = Q^T A Q (Sec. 3.2, readings C1-C5).  With weights (the sizes
+    of the compressed units, see cosine_blocking_units) a block holds at most max_block of
+    weight: a partner that passes the test but does not fit is passed over."""
     n = A.n
+    w = [1] * n if weights is None else [int(x) for x in weights]
     rows = _row_sets(A)
     # rows having an entry in column k (the pattern of A A^T is reached through them)
     cols = [[] for _ in range(n)]
@@ -80,17 +83,53 @@ def cosine_blocking(A, tau: float = 0.8, max_block: int = 64):
             continue
         placed[i] = True
         block = [i]
+        bw = w[i]
         if not skip[i]:
             partners = sorted({j for k in rows[i] for j in cols[k] if j > i})
             for j in partners:
-                if len(block) >= max_block:
+                if bw >= max_block:
                     break
-                if placed[j] or skip[j]:
+                if placed[j] or skip[j] or bw + w[j] > max_block:
                     continue
                 cnt = len(rows[i] & rows[j])
                 if float(cnt) ** 2 >= (tau * len(rows[i])) * len(rows[j]):
                     block.append(j)
+                    bw += w[j]
                     placed[j] = True
         perm.extend(block)
+        bstart.append(len(perm))
+    return np.array(perm, dtype=np.int32), np.array(bstart, dtype=np.int32)
+
+
+def cosine_blocking_units(A, ustart, tau: float = 0.8, max_block: int = 64):
+    """Cosine blocking of the compressed matrix (Sec. 4.2: after the symmetrised matching the
+    2 x 2 pivots are merged before the cosine test; reading R27).  The consecutive units
+    [ustart[p], ustart[p + 1]) of A are the indices of the compressed matrix, whose row p holds
+    the units of the columns of A's rows in unit p; cosine_blocking runs on it with the unit
+    sizes as weights (a block holds at most max_block indices of A), and the result is
+    expanded: the units of a block in its order, the indices of a unit in theirs.  Returns
+    (perm, bstart) over the indices of A."""
+    ustart = [int(x) for x in ustart]
+    nu = len(ustart) - 1
+    unit_of = [0] * A.n
+    for p in range(nu):
+        for i in range(ustart[p], ustart[p + 1]):
+            unit_of[i] = p
+    rowptr, colind = [0], []
+    for p in range(nu):
+        cols = sorted({unit_of[int(c)] for i in range(ustart[p], ustart[p + 1])
+                       for c in A.colind[A.rowptr[i]:A.rowptr[i + 1]]})
+        colind.extend(cols)
+        rowptr.append(len(colind))
+
+    class _C:
+        pass
+    C = _C()
+    C.n, C.rowptr, C.colind = nu, np.array(rowptr, dtype=np.int64), np.array(colind, dtype=np.int32)
+    uperm, ub = cosine_blocking(C, tau, max_block, weights=[ustart[p + 1] - ustart[p] for p in range(nu)])
+    perm, bstart = [], [0]
+    for b in range(len(ub) - 1):
+        for p in uperm[ub[b]:ub[b + 1]]:
+            perm.extend(range(ustart[p], ustart[p + 1]))
         bstart.append(len(perm))
     return np.array(perm, dtype=np.int32), np.array(bstart, dtype=np.int32)

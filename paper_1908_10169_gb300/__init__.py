@@ -33,7 +33,7 @@ EXPORTED = ["bilu_params_default", "bilu_create", "bilu_analyze", "bilu_factor",
             "bilu_last_error",
             "bilu_debug_set", "bilu_apply_noalloc", "bilu_factor_batch", "gmres_solve_batch",
             "bilu_record_samples", "bilu_get_samples", "bilu_mlp_train", "bilu_mlp_forward", "bilu_mlp_grad",
-            "bilu_set_skip_model", "bilu_cosine_blocking", "bilu_partition_ilu1t", "bilu_mwm", "bilu_sym_mwm", "bilu_scale_permute_csr",
+            "bilu_set_skip_model", "bilu_cosine_blocking", "bilu_partition_ilu1t", "bilu_mwm", "bilu_sym_mwm", "bilu_cosine_blocking_units", "bilu_scale_permute_csr",
             "bilu_nd_order", "bilu_block_etree",
             "bilu_permute_csr",
             "bilu_analyze_partition",
@@ -129,6 +129,7 @@ def lib():
             "bilu_partition_ilu1t": ([i64, P, P, P, f64, i32, i32, P, P, ct.POINTER(i32)], i32),
             "bilu_mwm": ([i64, P, P, P, P, P, P], i32),
             "bilu_sym_mwm": ([i64, P, P, P, P, P, P, P], i32),
+            "bilu_cosine_blocking_units": ([i64, P, P, f64, i32, i32, P, P, P, P], i32),
             "bilu_nd_order": ([i64, P, P, i32, P, i32, P, P, P], i32),
             "bilu_block_etree": ([i64, P, P, i32, P, P, ct.POINTER(i32)], i32),
             "bilu_scale_permute_csr": ([i64, P, P, P, P, P, P, P, P, P, P], i32),
@@ -347,6 +348,29 @@ def bilu_mwm(n: int, rowptr, colind, val):
     dr = np.zeros(max(n, 1))
     _check(None, lib().bilu_mwm(n, _ptr(rp), _ptr(ci), _ptr(va), _ptr(sigma), _ptr(dl), _ptr(dr)))
     return sigma[:n].copy(), dl[:n].copy(), dr[:n].copy()
+
+
+def bilu_cosine_blocking_units(n: int, rowptr, colind, ustart, tau: float = 0.8, max_block: int = 64):
+    """Sec. 4.2 cosine blocking of the pattern compressed by the units ustart (whole units per
+    block, at most max_block indices): (perm, bstart) over the indices of A."""
+    import numpy as np
+    if n < 0:
+        raise ValueError("n < 0")
+    rp = np.ascontiguousarray(rowptr, dtype=np.int64)
+    if rp.size < n + 1:
+        raise ValueError("rowptr needs n + 1 entries")
+    ci = np.ascontiguousarray(colind, dtype=np.int32)
+    if ci.size < (int(rp[n]) if n > 0 else 0):
+        raise ValueError("colind shorter than rowptr[n]")
+    us = np.ascontiguousarray(ustart, dtype=np.int32)
+    if us.size < 1:
+        raise ValueError("ustart needs at least one entry")
+    perm = np.zeros(max(n, 1), np.int32)
+    bs = np.zeros(n + 1, np.int32)
+    nb = ct.c_int32(0)
+    _check(None, lib().bilu_cosine_blocking_units(n, _ptr(rp), _ptr(ci), tau, max_block, len(us) - 1, _ptr(us),
+                                                  _ptr(perm), _ptr(bs), ct.byref(nb)))
+    return perm[:n].copy(), bs[: nb.value + 1].copy()
 
 
 def bilu_sym_mwm(n: int, rowptr, colind, val):

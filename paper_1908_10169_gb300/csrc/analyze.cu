@@ -210,15 +210,11 @@ std::vector<char> above_two_sigma(const std::vector<int64_t> &cnt, int64_t nnz) 
 // max_block.  A row or column with more than mu + 2 sigma entries takes no part: its index is
 // a block of its own.  perm lists the blocks in the order of their leaders (leader first,
 // members ascending); bstart holds the block starts of Q^T A Q.
-bilu_status cosine_blocking_host(int64_t n, const int64_t *rowptr, const int32_t *colind, double tau,
-                                 int32_t max_block, int32_t *perm, int32_t *bstart, int32_t *nblocks,
-                                 std::string *err) {
-    auto fail = [&](const char *m) { if (err) *err = m; return BILU_ERR_ARG; };
-    const std::string bad = check_pattern(n, rowptr, colind);
-    if (!bad.empty()) return fail(bad.c_str());
-    if (!(tau >= 0.0) || !std::isfinite(tau)) return fail("tau must be finite and >= 0");
-    if (max_block < 1 || max_block > BILU_MAX_BLOCK) return fail("max_block must be in 1..64");
-    if (!bstart || !nblocks || (n > 0 && !perm)) return fail("null output array");
+// The sweep of the cosine blocking over a validated pattern; weight (null: 1 per index) is what
+// an index adds to its block, which holds at most max_block of it (a partner that passes the
+// test but does not fit is passed over).
+static void cosine_core(int64_t n, const int64_t *rowptr, const int32_t *colind, double tau, int32_t max_block,
+                        const int32_t *weight, int32_t *perm, int32_t *bstart, int32_t *nblocks) {
     const int64_t nnz = n > 0 ? rowptr[n] : 0;
     // columns of the pattern (rows ascending) and the row / column counts
     std::vector<int64_t> rcnt(n), ccnt(n, 0);
@@ -242,7 +238,7 @@ bilu_status cosine_blocking_host(int64_t n, const int64_t *rowptr, const int32_t
         if (placed[i]) continue;
         placed[i] = 1;
         perm[pos++] = (int32_t)i;
-        int64_t size = 1;
+        int64_t size = weight ? weight[i] : 1;
         if (!xr[i] && !xc[i]) {
             partners.clear();
             for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
@@ -259,7 +255,8 @@ bilu_status cosine_blocking_host(int64_t n, const int64_t *rowptr, const int32_t
             const double ni = (double)rcnt[i];
             for (int32_t j : partners) {
                 if (size >= max_block) break;
-                if (placed[j] || xr[j] || xc[j]) continue;
+                const int64_t wj = weight ? weight[j] : 1;
+                if (placed[j] || xr[j] || xc[j] || size + wj > max_block) continue;
                 // |c_i n c_j| by merging the two sorted rows
                 int64_t a = rowptr[i], b = rowptr[j], cnt = 0;
                 while (a < rowptr[i + 1] && b < rowptr[j + 1]) {
@@ -270,13 +267,79 @@ bilu_status cosine_blocking_host(int64_t n, const int64_t *rowptr, const int32_t
                 if ((double)cnt * (double)cnt >= (tau * ni) * (double)rcnt[j]) {
                     placed[j] = 1;
                     perm[pos++] = j;
-                    ++size;
+                    size += wj;
                 }
             }
         }
         bstart[++nb] = (int32_t)pos;
     }
     *nblocks = nb;
+}
+
+bilu_status cosine_blocking_host(int64_t n, const int64_t *rowptr, const int32_t *colind, double tau,
+                                 int32_t max_block, int32_t *perm, int32_t *bstart, int32_t *nblocks,
+                                 std::string *err) {
+    auto fail = [&](const char *m) { if (err) *err = m; return BILU_ERR_ARG; };
+    const std::string bad = check_pattern(n, rowptr, colind);
+    if (!bad.empty()) return fail(bad.c_str());
+    if (!(tau >= 0.0) || !std::isfinite(tau)) return fail("tau must be finite and >= 0");
+    if (max_block < 1 || max_block > BILU_MAX_BLOCK) return fail("max_block must be in 1..64");
+    if (!bstart || !nblocks || (n > 0 && !perm)) return fail("null output array");
+    cosine_core(n, rowptr, colind, tau, max_block, nullptr, perm, bstart, nblocks);
+    return BILU_OK;
+}
+
+// Sec. 4.2: the cosine blocking of the compressed matrix whose indices are the consecutive
+// units [ustart[p], ustart[p + 1]) (the 2 x 2 pivots of the symmetrised matching merged): row p
+// of the compressed pattern holds the units of the columns of the rows in unit p; the sweep
+// weighs each unit by its size, and the blocks are expanded to the indices of A (units in the
+// block's order, the indices of a unit in theirs).
+bilu_status cosine_blocking_units_host(int64_t n, const int64_t *rowptr, const int32_t *colind, double tau,
+                                       int32_t max_block, int32_t nunits, const int32_t *ustart, int32_t *perm,
+                                       int32_t *bstart, int32_t *nblocks, std::string *err) {
+    auto fail = [&](const char *m) { if (err) *err = m; return BILU_ERR_ARG; };
+    const std::string bad = check_pattern(n, rowptr, colind);
+    if (!bad.empty()) return fail(bad.c_str());
+    if (!(tau >= 0.0) || !std::isfinite(tau)) return fail("tau must be finite and >= 0");
+    if (max_block < 1 || max_block > BILU_MAX_BLOCK) return fail("max_block must be in 1..64");
+    if (!bstart || !nblocks || (n > 0 && (!perm || !ustart))) return fail("null array");
+    if (nunits < 0 || (n > 0 && nunits < 1)) return fail("nunits out of range");
+    if (n > 0 && (ustart[0] != 0 || ustart[nunits] != n)) return fail("units must run from 0 to n");
+    for (int32_t p = 0; p < nunits; ++p)
+        if (ustart[p + 1] <= ustart[p] || ustart[p + 1] - ustart[p] > max_block)
+            return fail("unit sizes must be in 1..max_block");
+    if (n == 0) {
+        bstart[0] = 0;
+        *nblocks = 0;
+        return BILU_OK;
+    }
+    std::vector<int32_t> unit_of(n), weight(nunits);
+    for (int32_t p = 0; p < nunits; ++p) {
+        weight[p] = ustart[p + 1] - ustart[p];
+        for (int32_t i = ustart[p]; i < ustart[p + 1]; ++i) unit_of[i] = p;
+    }
+    std::vector<int64_t> crp(nunits + 1, 0);
+    std::vector<int32_t> cci, row;
+    for (int32_t p = 0; p < nunits; ++p) {
+        row.clear();
+        for (int32_t i = ustart[p]; i < ustart[p + 1]; ++i)
+            for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) row.push_back(unit_of[colind[e]]);
+        std::sort(row.begin(), row.end());
+        row.erase(std::unique(row.begin(), row.end()), row.end());
+        cci.insert(cci.end(), row.begin(), row.end());
+        crp[p + 1] = (int64_t)cci.size();
+    }
+    std::vector<int32_t> uperm(nunits), ub(nunits + 1);
+    int32_t nub = 0;
+    cosine_core(nunits, crp.data(), cci.data(), tau, max_block, weight.data(), uperm.data(), ub.data(), &nub);
+    int64_t pos = 0;
+    bstart[0] = 0;
+    for (int32_t b = 0; b < nub; ++b) {
+        for (int32_t k = ub[b]; k < ub[b + 1]; ++k)
+            for (int32_t i = ustart[uperm[k]]; i < ustart[uperm[k] + 1]; ++i) perm[pos++] = i;
+        bstart[b + 1] = (int32_t)pos;
+    }
+    *nblocks = nub;
     return BILU_OK;
 }
 

@@ -264,6 +264,9 @@ bilu_status mwm_host(int64_t n, const int64_t *rowptr, const int32_t *colind, co
                      int32_t *sigma, double *dl, double *dr, std::string *err);
 bilu_status sym_mwm_host(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val, int32_t *perm,
                          double *ds, int32_t *ustart, int32_t *nunits, std::string *err);
+bilu_status cosine_blocking_units_host(int64_t n, const int64_t *rowptr, const int32_t *colind, double tau,
+                                       int32_t max_block, int32_t nunits, const int32_t *ustart, int32_t *perm,
+                                       int32_t *bstart, int32_t *nblocks, std::string *err);
 bilu_status scale_permute_csr_host(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val,
                                    const int32_t *rowperm, const int32_t *colperm, const double *dl,
                                    const double *dr, int64_t *out_rowptr, int32_t *out_colind, double *out_val,

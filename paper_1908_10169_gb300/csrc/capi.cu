@@ -125,6 +125,14 @@ bilu_status bilu_mwm(int64_t n, const int64_t *rowptr, const int32_t *colind, co
     return mwm_host(n, rowptr, colind, val, sigma, dl, dr, &g_host_err);
 }
 
+bilu_status bilu_cosine_blocking_units(int64_t n, const int64_t *rowptr, const int32_t *colind, double tau,
+                                      int32_t max_block, int32_t nunits, const int32_t *ustart, int32_t *perm,
+                                      int32_t *bstart, int32_t *nblocks) {
+    g_host_err.clear();
+    return cosine_blocking_units_host(n, rowptr, colind, tau, max_block, nunits, ustart, perm, bstart, nblocks,
+                                      &g_host_err);
+}
+
 bilu_status bilu_sym_mwm(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *val, int32_t *perm,
                          double *ds, int32_t *ustart, int32_t *nunits) {
     g_host_err.clear();

@@ -81,6 +81,14 @@ int main() {
                 srp[i + 1] = (int64_t)sci.size();
             }
             sym_mwm_host(n, srp.data(), sci.data(), sva.data(), perm.data(), dl.data(), us.data(), &nu, &err);
+            // the cosine blocking of the pattern compressed by random units (some invalid)
+            std::vector<int32_t> units{0};
+            while (units.back() < n) units.push_back(std::min(n, units.back() + 1 + (int)(rng() % 3)));
+            if (rng() % 8 == 0 && units.size() > 2) units[1] = units[2];  // an empty unit: refused
+            std::vector<int32_t> ub(n + 2);
+            int32_t nub = 0;
+            cosine_blocking_units_host(n, rp.data(), ci.data(), Pr(rng), mb, (int32_t)units.size() - 1, units.data(),
+                                       perm.data(), ub.data(), &nub, &err);
         }
         // analysis: validation, CSC copy and partition run on the host; the device upload that
         // follows fails where there is no GPU (or succeeds where there is one)

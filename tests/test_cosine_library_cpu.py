@@ -84,3 +84,42 @@ def test_host_calls_report_errors():
     bad[0], bad[1] = bad[1], bad[0]
     with pytest.raises(B.BiluError, match="increasing"):
         B.bilu_cosine_blocking(A.n, A.rowptr, bad)
+
+
+def test_unit_blocking_matches_oracle():
+    """bilu_cosine_blocking_units against the oracle on random patterns and random units:
+    the same permutation and blocks, every block made of whole units and at most max_block."""
+    import numpy as np
+    from oracle import cosine_oracle as C
+    import paper_1908_10169_gb300 as B
+    from paper_1908_10169_gb300 import workloads as W
+    rng = np.random.default_rng(11)
+    for trial in range(40):
+        n = int(rng.integers(1, 60))
+        dens = [0.05, 0.15, 0.4][trial % 3]
+        D = (rng.random((n, n)) < dens).astype(float)
+        D[np.arange(n), np.arange(n)] = 1.0
+        A = W.from_dense(D)
+        cuts = sorted(set(rng.choice(np.arange(1, n), size=min(n - 1, int(rng.integers(0, n))), replace=False).tolist())) if n > 1 else []
+        us = np.array([0] + cuts + [n], np.int32)
+        us = us[np.concatenate([[True], np.diff(us) > 0])]
+        mb = int(max(np.diff(us).max(), rng.integers(1, 20)))
+        tau = float(rng.choice([0.3, 0.5, 0.8]))
+        p1, b1 = B.bilu_cosine_blocking_units(n, A.rowptr, A.colind, us, tau, mb)
+        p2, b2 = C.cosine_blocking_units(A, us, tau, mb)
+        assert np.array_equal(p1, p2) and np.array_equal(b1, b2), trial
+        assert set(b1.tolist()) >= {0, n} and np.diff(b1).max() <= mb
+        starts = set(us.tolist())
+        for k in range(len(b1) - 1):  # a block is a run of whole units of the original order
+            assert p1[b1[k]] in starts
+
+
+def test_unit_blocking_refuses_bad_units():
+    import numpy as np
+    import pytest
+    import paper_1908_10169_gb300 as B
+    from paper_1908_10169_gb300 import workloads as W
+    A = W.from_dense(np.eye(6))
+    for us, mb in (([0, 3, 5], 64), ([0, 3, 3, 6], 64), ([0, 4, 6], 3)):
+        with pytest.raises(B.BiluError):
+            B.bilu_cosine_blocking_units(6, A.rowptr, A.colind, us, 0.8, mb)

@@ -169,3 +169,48 @@ def test_exclusion_threshold_is_exact(n, excluded):
     A = W.from_dense(d)
     ex = C.excluded(A)
     assert list(np.nonzero(ex)[0]) == ([n - 1] if excluded else [])
+
+
+# ------------------------------------------------------------ the compressed (unit) form
+
+
+def _pattern(rows, n):
+    import numpy as np
+    from paper_1908_10169_gb300 import workloads as W
+    rp = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int64)
+    ci = np.array([c for r in rows for c in sorted(r)], dtype=np.int32)
+    return W.CSR(n, rp, ci, np.ones(ci.size))
+
+
+def test_units_of_one_index_give_the_plain_blocking():
+    import numpy as np
+    from oracle import cosine_oracle as C
+    from paper_1908_10169_gb300 import workloads as W
+    w = W.cd3d(side=6, seed=2, block=6)
+    for mb in (3, 8, 64):
+        p1, b1 = C.cosine_blocking(w.A, 0.5, mb)
+        p2, b2 = C.cosine_blocking_units(w.A, np.arange(w.A.n + 1), 0.5, mb)
+        assert np.array_equal(p1, p2) and np.array_equal(b1, b2)
+
+
+def test_units_hand_example():
+    """Units {0,1}, {2,3}, {4,5}; rows 0: {0,4}, 1: {1}, 2: {2}, 3: {3}, 4: {1,4}, 5: {5}.  The
+    compressed rows are u0: {u0, u2}, u1: {u1}, u2: {u0, u2}; no count is above mu + 2 sigma
+    (n S - nnz^2 = 27 - 25); u0 and u2 pass (2^2 >= 0.8 * 2 * 2) and hold 4 indices: blocks
+    {0, 1, 4, 5}, {2, 3}.  With at most 3 indices per block the two units do not fit together."""
+    from oracle import cosine_oracle as C
+    A = _pattern([{0, 4}, {1}, {2}, {3}, {1, 4}, {5}], 6)
+    perm, bstart = C.cosine_blocking_units(A, [0, 2, 4, 6], 0.8, 64)
+    assert perm.tolist() == [0, 1, 4, 5, 2, 3] and bstart.tolist() == [0, 4, 6]
+    perm, bstart = C.cosine_blocking_units(A, [0, 2, 4, 6], 0.8, 3)
+    assert perm.tolist() == [0, 1, 2, 3, 4, 5] and bstart.tolist() == [0, 2, 4, 6]
+
+
+def test_units_join_through_their_second_rows():
+    """Units {0,1}, {2,3}; rows 0: {0}, 1: {3}, 2: {2}, 3: {1}: only the units' second rows
+    couple them, so the compressed rows are u0: {u0, u1}, u1: {u0, u1} and the two units form
+    one block."""
+    from oracle import cosine_oracle as C
+    A = _pattern([{0}, {3}, {2}, {1}], 4)
+    perm, bstart = C.cosine_blocking_units(A, [0, 2, 4], 0.8, 64)
+    assert perm.tolist() == [0, 1, 2, 3] and bstart.tolist() == [0, 4]

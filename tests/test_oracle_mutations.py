@@ -139,8 +139,10 @@ MUTANTS = [
      "assert abs(nrm[k] - tau) <= 1e30 * tau", 1),
     # cosine blocking (Sec. 3.2)
     ("cosine: strict test", COS, "float(cnt) ** 2 >= (tau", "float(cnt) ** 2 > (tau", 1),
-    ("cosine: excluded partners join", COS, "if placed[j] or skip[j]:", "if placed[j]:", 1),
-    ("cosine: block one larger than max_block", COS, "if len(block) >= max_block:", "if len(block) > max_block:", 1),
+    ("cosine: excluded partners join", COS, "if placed[j] or skip[j] or bw + w[j] > max_block:",
+     "if placed[j] or bw + w[j] > max_block:", 1),
+    ("cosine: block one larger than max_block", COS, "if placed[j] or skip[j] or bw + w[j] > max_block:",
+     "if placed[j] or skip[j] or bw + w[j] > max_block + 1:", 1),
     ("cosine: exclusion by rows only", COS, "return np.array([a or b for a, b in zip(r, c)], dtype=bool)",
      "return np.array([a for a, b in zip(r, c)], dtype=bool)", 1),
     ("cosine: three sigma", COS, "var4 = 4 * (n * S - nnz * nnz)", "var4 = 9 * (n * S - nnz * nnz)", 1),
@@ -170,6 +172,11 @@ MUTANTS = [
     ("symmetric matching: odd cycle paired past the neighbour", MWM,
      "                units.append(sorted([cyc[t % k], cyc[(t + 1) % k]]))\n    units.sort",
      "                units.append(sorted([cyc[t % k], cyc[(t + 2) % k]]))\n    units.sort", 1),
+    ("cosine units: the block's capacity ignored", COS, "if placed[j] or skip[j] or bw + w[j] > max_block:",
+     "if placed[j] or skip[j]:", 1),
+    ("cosine units: compressed row from the unit's first row only", COS,
+     "cols = sorted({unit_of[int(c)] for i in range(ustart[p], ustart[p + 1])",
+     "cols = sorted({unit_of[int(c)] for i in range(ustart[p], ustart[p] + 1)", 1),
     ("nd: separator is the first level", ND, "m = len(levels) // 2", "m = 1", 1),
     ("nd: separator ordered first", ND, "order += dissect(adj, first, leaf) + dissect(adj, second, leaf) + sorted(levels[m])",
      "order += sorted(levels[m]) + dissect(adj, first, leaf) + dissect(adj, second, leaf)", 1),
