@@ -5,17 +5,19 @@
  * Factorization", arXiv:1908.10169.  The library computes the Crout-type block ILU
  * A ~ L D^{-1} U of a sparse matrix (Sec. 2.2), applies it as a preconditioner by block
  * forward / backward substitution, and solves A x = b with right-preconditioned
- * restarted GMRES (Sec. 4).  Every numerical step runs in CUDA kernels on one GPU.
+ * restarted GMRES (Sec. 4); for a symmetric A it also computes the incomplete block
+ * L D L^T of the symmetric variant and solves with simplified QMR (Sec. 4.2).  Every
+ * numerical step runs in CUDA kernels on one GPU.
  *
  * Conventions (all entry points):
  *   - The caller owns every array it passes; the library copies what it keeps and
  *     never frees caller memory.  A context owns all device memory it allocates.
- *   - Vectors passed to bilu_apply / gmres_solve may be device pointers or host
- *     pointers (pageable or pinned); host vectors are staged through device buffers.
+ *   - Vectors passed to bilu_apply / gmres_solve / sqmr_solve may be device pointers or
+ *     host pointers (pageable or pinned); host vectors are staged through device buffers.
  *     Work is issued on the context's stream; the calls that return numerical status
- *     (bilu_factor, gmres_solve) synchronize that stream once before returning.
+ *     (bilu_factor, gmres_solve, sqmr_solve) synchronize that stream before returning.
  *   - Call order: bilu_create -> bilu_analyze -> bilu_factor -> bilu_apply /
- *     gmres_solve.  A call out of order returns BILU_ERR_STATE.  bilu_factor may be
+ *     gmres_solve / sqmr_solve.  A call out of order returns BILU_ERR_STATE.  bilu_factor may be
  *     repeated (new drop tolerance); bilu_analyze may be repeated (new matrix).
  *   - Status < 0 is an error (the context stays destroyable, bilu_last_error says
  *     why); status > 0 is a warning with a valid result.  No exception, exit() or
