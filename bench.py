@@ -23,7 +23,12 @@ learned-skip configurations' matrices), --batch N (N uneven 2D / 3D systems in o
 one graph per GMRES cycle, sharded over the ranks under torchrun), --mwm / --blocking
 cosine|cosine+ilu1t|ilu1t / --order nd (the host analysis of Sec. 3.1-3.4 before the factorization,
 outside the timed region and inside the end-to-end time; --workload cd3d_rows_scrambled is the
-benchmark matrix with its equations in random order, which needs --mwm). Under torchrun the
+benchmark matrix with its equations in random order, which needs --mwm), --aggregate N
+(progressive aggregation up to N columns), --compare-fp64 (plain FP64 on the same matrix
+beside the line), --droptol T, and the symmetric variant: --symmetric (BILDL + SQMR to the
+backward error 1e-6, metric "BILDL factor+SQMR seconds") on --workload elasticity_shifted
+(symmetric indefinite) or kkt (a saddle-point system, with --sym-mwm: the symmetrised matching
+of Sec. 4.2 and blocks of whole pivot units, optionally their cosine blocking). Under torchrun the
 single-matrix line runs one replica per rank; the reference arm runs on rank 0 only (with
 --batch it times the oracle on every 16th system and scales by the batch's unknowns).
 """
