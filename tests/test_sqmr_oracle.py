@@ -113,3 +113,11 @@ def test_zero_rhs_and_converged_start():
     x = np.linalg.solve(S.toarray(), np.ones(A.n))
     res = O.sqmr(A, None, np.ones(A.n), tol=1e-6, maxit=10, x0=x)
     assert res.status == 0 and res.iters == 0
+
+
+def test_breakdown_is_reported():
+    """[[0, 1], [1, 0]] with b = e_1 and no preconditioner: q = r = e_1 and q^T A q = 0, so the
+    first step cannot be taken (sigma = 0): a breakdown after zero steps, x unchanged."""
+    A = W.from_dense(np.array([[0.0, 1.0], [1.0, 0.0]]))
+    res = O.sqmr(A, None, np.array([1.0, 0.0]), tol=1e-12, maxit=10)
+    assert res.status == 3 and res.iters == 0 and not res.x.any()
