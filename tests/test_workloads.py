@@ -49,3 +49,39 @@ def test_full_size_counts_match_the_configurations():
     # the closed forms at the configured sizes (48^3 elasticity, 64^3 4-dof 27-point)
     assert 9 * (3 * 48 - 2) ** 3 == 25_769_592
     assert 16 * (3 * 64 - 2) ** 3 == 109_744_000
+
+
+def test_shifted_elasticity_is_symmetric_and_indefinite():
+    """(K + K^T) / 2 - 0.3 diag(K): exactly symmetric, a few negative eigenvalues (those of the
+    Jacobi-scaled K below 0.3), b = A * ones."""
+    import numpy as np
+    import scipy.sparse as sp
+    from paper_1908_10169_gb300 import workloads as W
+    w = W.elasticity3d_shifted(side=6, block=24)
+    A = w.A
+    S = sp.csr_matrix((A.val, A.colind, A.rowptr), shape=(A.n, A.n))
+    assert A.n == 3 * 6 ** 3 and (S != S.T).nnz == 0
+    K = W.elasticity3d(side=6, block=24).A
+    Ks = sp.csr_matrix((K.val, K.colind, K.rowptr), shape=(K.n, K.n))
+    d = Ks.diagonal()
+    ev = np.linalg.eigvalsh(S.toarray())
+    evj = np.linalg.eigvalsh((sp.diags(d ** -0.5) @ ((Ks + Ks.T) * 0.5) @ sp.diags(d ** -0.5)).toarray())
+    assert (ev < 0).sum() == (evj < 0.3).sum() > 0  # Sylvester's law of inertia
+    np.testing.assert_allclose(w.b, S @ np.ones(A.n), rtol=1e-14)
+
+
+def test_saddle_point_system_structure():
+    import numpy as np
+    import scipy.sparse as sp
+    from paper_1908_10169_gb300 import workloads as W
+    side = 4
+    w = W.kkt_elasticity(side=side, block=24)
+    A = w.A
+    m = 3 * side * side
+    S = sp.csr_matrix((A.val, A.colind, A.rowptr), shape=(A.n, A.n))
+    assert A.n == 3 * side ** 3 + m and (S != S.T).nnz == 0
+    assert not S.diagonal()[:m].any() and (S.diagonal()[m:] > 0).all()
+    rows = [S[k].indices for k in range(m)]
+    assert all(len(r) == 1 for r in rows) and len({int(r[0]) for r in rows}) == m  # distinct displacements
+    ev = np.linalg.eigvalsh(S.toarray())
+    assert (ev < 0).sum() == m  # inertia of a saddle point with a full-rank constraint block
